@@ -1,0 +1,166 @@
+/*
+ * aln.h — C ABI of the anti-lopsided NNLS library (libaln).
+ *
+ * Solves the non-negative least squares problem of Def. 1 (§2.1, Eq. NNL):
+ *
+ *     minimise ½‖A x − b‖²   subject to  x ⪰ 0,   A ∈ R^{d×n}, b ∈ R^d,
+ *
+ * by the paper's anti-lopsided method:
+ *   Alg. 1 (§3):  H = AᵀA, h = −Aᵀb (Eq. NQP), rescale to the unit-diagonal
+ *                 problem Q_ij = H_ij/√(H_ii H_jj), q_i = h_i/√H_ii (Eq. NQPQ),
+ *                 solve it, then x_i = y_i/√H_ii (Eq. Rescaling).
+ *   Alg. 2 (§3):  projected gradient with exact line search on (Q, q):
+ *                 passive set P = {y_i > 0 or g_i < 0}, ḡ = g on P,
+ *                 α = ‖ḡ‖²/(ḡᵀQḡ), y ← [y − αḡ]₊, g ← g + Q(y_new − y).
+ *
+ * Sign convention: q is the paper's, q = −D⁻¹Aᵀb with D = diag(‖A_i‖), so the
+ * gradient of ½yᵀQy + qᵀy is g = Qy + q.
+ *
+ * Memory: every pointer argument may be device memory or host memory; the
+ * library detects which (cudaPointerGetAttributes) and copies host data
+ * through its own device buffers.  Matrices are column-major: element (t, i)
+ * of A is A[t + i*lda]; right-hand side c is B[c*ldb + t]; solution c is
+ * X[c*ldx + i].  The caller owns A, B, X and X0.  The context owns every
+ * derived array (scale factors, Q, q, split copies of A, iteration state).
+ *
+ * Lifetime: when A was passed as a DEVICE pointer, the context keeps that
+ * pointer (it is needed for the FP64 KKT evaluation and refinement) and the
+ * caller must keep A and B alive and unchanged until the last aln_solve or
+ * aln_kkt_residual on this context returns.  Host inputs are copied.
+ *
+ * Streams: all work is ordered on the stream given to aln_create (NULL means
+ * the legacy default stream).  Calls return after the work they launched has
+ * finished on that stream, because the solve loop reads convergence flags on
+ * the host.
+ *
+ * Errors: every call returns an aln_status; no C++ exception crosses this
+ * boundary.  After ALN_ERR_CUDA the context should be destroyed.
+ * Thread safety: a context must not be used from two threads at once.
+ */
+#ifndef ALN_H
+#define ALN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ALN_VERSION 100
+
+typedef enum aln_status {
+    ALN_OK = 0,
+    ALN_ERR_INVALID_ARG = 1,   /* null pointer, negative size, ld too small, bad enum */
+    ALN_ERR_NOT_PREPARED = 2,  /* aln_solve / aln_kkt_residual before aln_prepare */
+    ALN_ERR_NONFINITE = 3,     /* NaN or Inf found in A, B or X0 */
+    ALN_ERR_OUT_OF_MEMORY = 4, /* a workspace allocation failed */
+    ALN_ERR_CUDA = 5,          /* a CUDA runtime call or kernel launch failed */
+    ALN_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    ALN_ERR_UNSUPPORTED = 7    /* combination not built (e.g. no sm_103a device) */
+} aln_status;
+
+/* Arithmetic of the Gram formation and the iteration. */
+typedef enum aln_precision {
+    /* H = AᵀA in FP64, Alg. 2 in FP64: the plain method. */
+    ALN_PREC_FP64 = 0,
+    /* H from split-BF16 tensor-core products (hi·hi + hi·lo + lo·hi, FP32
+     * accumulation), Alg. 2 in FP32, scale factors / KKT / refinement in FP64. */
+    ALN_PREC_SPLIT_BF16 = 1
+} aln_precision;
+
+typedef enum aln_dtype { ALN_DTYPE_F32 = 0, ALN_DTYPE_F64 = 1 } aln_dtype;
+
+/* Per right-hand-side outcome, reported in aln_solve_info.status. */
+typedef enum aln_rhs_status {
+    ALN_RHS_CONVERGED = 0,     /* ‖ḡ‖ ≤ tol·‖min(q,0)‖ in the FP64 check */
+    ALN_RHS_EMPTY_PASSIVE = 1, /* P(y) = ∅: y is a KKT point (Alg. 2 stop rule) */
+    ALN_RHS_CURVATURE = 2,     /* ḡᵀQḡ ≤ 0 with ḡ ≠ 0: numerically converged */
+    ALN_RHS_MAXITER = 3,       /* max_iter reached; X holds the last iterate */
+    ALN_RHS_NONFINITE = 4      /* the iteration produced NaN/Inf */
+} aln_rhs_status;
+
+typedef struct aln_options {
+    int32_t precision;    /* aln_precision */
+    int32_t max_refine;   /* FP64 refinement rounds after the first FP32
+                             convergence (SPLIT_BF16 only); default 8 */
+    int32_t graph_chunk;  /* Alg. 2 iterations per captured CUDA graph launch;
+                             0 selects a size-dependent default */
+    int32_t row_groups;   /* row groups of the single-RHS matvec; 0 = auto */
+} aln_options;
+
+typedef struct aln_solve_info {
+    int32_t iters;         /* Alg. 2 iterations, summed over refinement rounds */
+    int32_t status;        /* aln_rhs_status */
+    int32_t refine_rounds; /* FP64 refinement rounds used */
+    int32_t reserved;
+    double rel_kkt;        /* FP64 relative KKT residual ‖ḡ‖/‖min(q,0)‖ from A */
+    double objective;      /* ½‖A x − b‖² in FP64 */
+} aln_solve_info;
+
+typedef struct aln_ctx aln_ctx;
+
+/* Fill *opt with the defaults (precision SPLIT_BF16, max_refine 8, auto chunk). */
+void aln_default_options(aln_options* opt);
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  opt may be NULL (defaults).
+ * Errors: INVALID_ARG (ctx NULL or bad option), UNSUPPORTED (device is not
+ * compute capability 10.3 when precision is SPLIT_BF16), CUDA. */
+aln_status aln_create(aln_ctx** ctx, const aln_options* opt, void* stream);
+
+/* Alg. 1 up to the solve: scale factors s_i = ‖A_i‖ (FP64; s_i := 1 for a zero
+ * column, Eq. Rescaling's special case), Q = D⁻¹AᵀAD⁻¹ (Eq. NQPQ) and
+ * q_c = −D⁻¹Aᵀb_c for each of the k right-hand sides.
+ *   A    d×n, column-major, leading dimension lda ≥ d, dtype aln_dtype.
+ *   B    k right-hand sides, B[c*ldb + t], ldb ≥ d, same dtype as A.
+ * Requires d ≥ 1, n ≥ 1, k ≥ 1.  SPLIT_BF16 requires dtype F32 or F64 (F64 is
+ * rounded to F32 before splitting).  Errors: INVALID_ARG, NONFINITE (NaN/Inf
+ * in A or B), OUT_OF_MEMORY, CUDA. */
+aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_t lda,
+                       int32_t dtype, const void* B, int64_t k, int64_t ldb);
+
+/* Alg. 2 on every prepared right-hand side, then x = y/s (Alg. 1).
+ *   tol       relative KKT tolerance: stop when ‖ḡ‖ ≤ tol·‖min(q,0)‖ (FP64,
+ *             evaluated from A); must be > 0.
+ *   max_iter  cap on Alg. 2 iterations per right-hand side (≤ 0: max(5n, 20000),
+ *             the paper's experimental cap).
+ *   X         output, FP64, X[c*ldx + i], ldx ≥ n.
+ *   X0        optional start point in x-space (FP64, same layout, ≥ 0), or NULL
+ *             for Alg. 2's x⁰ = 0.  Mapped to y0 = x0·s.
+ *   info      optional array of k records (host memory).
+ * Errors: NOT_PREPARED, INVALID_ARG, NONFINITE (X0), TIMEOUT, CUDA.  Hitting
+ * max_iter is not an error; it is reported per right-hand side. */
+aln_status aln_solve(aln_ctx* ctx, double tol, int32_t max_iter, double* X, int64_t ldx,
+                     const double* X0, aln_solve_info* info);
+
+/* FP64 KKT residual and objective of given solutions, from A directly:
+ * r = Ax − b, ∇F = Aᵀr, g = ∇F/s, ḡ = g on P(s·x), rel = ‖ḡ‖/‖min(q,0)‖
+ * (absolute ‖ḡ‖ when ‖min(q,0)‖ = 0), objective = ½‖r‖².
+ *   X          k solutions, FP64, X[c*ldx + i].
+ *   rel_kkt    k doubles out (host or device).  objective: k doubles out or NULL.
+ * Errors: NOT_PREPARED, INVALID_ARG, CUDA. */
+aln_status aln_kkt_residual(aln_ctx* ctx, const double* X, int64_t ldx, double* rel_kkt,
+                            double* objective);
+
+/* Copy the prepared scaled problem out as FP64 (for inspection and tests):
+ *   Q  n×n, Q[i*ldq + j] (symmetric), ldq ≥ n; may be NULL.
+ *   q  k×n, q[c*ldqv + i], ldqv ≥ n; may be NULL.
+ *   s  n scale factors; may be NULL.
+ * Errors: NOT_PREPARED, INVALID_ARG, CUDA. */
+aln_status aln_export_scaled(aln_ctx* ctx, double* Q, int64_t ldq, double* q, int64_t ldqv,
+                             double* s);
+
+/* Destroy a context and free its workspace (NULL is accepted). */
+void aln_destroy(aln_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* aln_status_string(aln_status status);
+
+/* ALN_VERSION of the built library. */
+int32_t aln_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALN_H */

@@ -1,0 +1,163 @@
+"""Seeded synthetic NNLS inputs shaped like the paper's large-matrix workloads.
+
+This module only draws random numbers and assembles ``b = A x_true + noise``;
+it contains none of the solver's arithmetic, so both the CUDA path and the CPU
+oracle may consume what it produces.  The paper generates its test cases the
+same way (§5, "Experimental Evaluation": random ``A`` and ``x*``, then
+``b = A x*``), but its saved cases were never published, so these recipes stand
+in for them.
+
+Every generator takes a seed and returns numpy arrays.  ``A`` is column-major in
+the sense the library expects: ``A.T`` is C-contiguous, i.e. the returned array
+is Fortran-ordered ``(d, n)`` so that each column ``A_i`` is contiguous.
+Right-hand sides are returned as ``(k, d)`` C-contiguous (each RHS contiguous).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Problem",
+    "uniform_small",
+    "lopsided_single",
+    "shared_multi_rhs",
+    "uneven_batch",
+    "warmstart_family",
+    "CONFIGS",
+]
+
+
+@dataclass
+class Problem:
+    """One NNLS instance ``min ½‖Ax−b‖²  s.t. x ≥ 0`` (possibly many RHS)."""
+
+    A: np.ndarray            # (d, n), Fortran order, float32 or float64
+    B: np.ndarray            # (k, d), C order; row c is the c-th right-hand side
+    x_true: np.ndarray       # (k, n) generating solution (not the NNLS optimum)
+    tol: float               # relative KKT tolerance the workload is solved to
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def d(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[1]
+
+    @property
+    def k(self) -> int:
+        return self.B.shape[0]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _sparse_rows(rng, k, n, zero_frac, draw):
+    """k rows of length n with round(zero_frac*n) zeros at random positions."""
+    X = draw((k, n))
+    nz = int(round(zero_frac * n))
+    for c in range(k):
+        X[c, rng.permutation(n)[:nz]] = 0.0
+    return X
+
+
+def _noisy_rhs(rng, A64, X, rel_noise):
+    """b_c = A x_c + rel_noise * (‖A x_c‖/√d) * N(0, I), per column c."""
+    d = A64.shape[0]
+    clean = X @ A64.T                                   # (k, d)
+    scale = rel_noise * np.linalg.norm(clean, axis=1, keepdims=True) / np.sqrt(d)
+    return clean + scale * rng.standard_normal(clean.shape)
+
+
+def uniform_small(d=1000, n=200, zero_frac=0.5, noise_sd=0.01, seed=1001, tol=1e-10):
+    """Plain FP64 single-RHS case: A ~ U[0,1], x_true half zeros, rest U[0,1],
+    b = A x_true + N(0, noise_sd²) (absolute noise)."""
+    rng = _rng(seed)
+    A = np.asfortranarray(rng.random((d, n)))
+    x = _sparse_rows(rng, 1, n, zero_frac, lambda s: rng.random(s))
+    b = x @ A.T + noise_sd * rng.standard_normal((1, d))
+    return Problem(A, np.ascontiguousarray(b), x, tol, "uniform_small",
+                   {"d": d, "n": n, "dtype": "f64"})
+
+
+def _lopsided_A(rng, d, n, lo=1e-2, hi=1e2):
+    """A ~ U[0,1] with every column multiplied by a log-uniform factor in [lo, hi]."""
+    A = rng.random((d, n))
+    scale = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+    return A * scale[None, :]
+
+
+def lopsided_single(d=20000, n=5000, zero_frac=0.7, seed=1002, tol=1e-6):
+    """Single large RHS with lopsided column scaling (FP32 inputs):
+    x_true 70% zeros with Exp(1) nonzeros, b = A x_true + 1% Gaussian noise."""
+    rng = _rng(seed)
+    A64 = _lopsided_A(rng, d, n)
+    A = np.asfortranarray(A64.astype(np.float32))
+    x = _sparse_rows(rng, 1, n, zero_frac, lambda s: rng.exponential(1.0, s))
+    b = _noisy_rhs(rng, A.astype(np.float64), x, 0.01).astype(np.float32)
+    return Problem(A, np.ascontiguousarray(b), x, tol, "lopsided_single",
+                   {"d": d, "n": n, "dtype": "f32"})
+
+
+def shared_multi_rhs(d=10000, n=1000, k=4096, zero_frac=0.8, seed=1003, tol=1e-6):
+    """Many RHS sharing one A (NMF inner-solve shape): A ~ U[0,1] FP32,
+    X_true 80% zeros with Gamma(2,1) nonzeros, B = A X_true + 1% noise per column."""
+    rng = _rng(seed)
+    A = np.asfortranarray(rng.random((d, n)).astype(np.float32))
+    X = _sparse_rows(rng, k, n, zero_frac, lambda s: rng.gamma(2.0, 1.0, s))
+    B = _noisy_rhs(rng, A.astype(np.float64), X, 0.01).astype(np.float32)
+    return Problem(A, np.ascontiguousarray(B), X, tol, "shared_multi_rhs",
+                   {"d": d, "n": n, "k": k, "dtype": "f32"})
+
+
+def uneven_batch(count=512, n_lo=32, n_hi=1024, zero_frac=0.6, seed=1004, tol=1e-6):
+    """Independent problems of uneven size: n log-uniform in [n_lo, n_hi],
+    d = n * U{2,3,4}, A = |N(0,1)| FP32, x_true 60% zeros with U[0,1] nonzeros,
+    b with 1% noise.  Problem p draws from seed + p."""
+    probs = []
+    for p in range(count):
+        rng = _rng(seed * 100003 + p)
+        n = int(np.floor(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        n = max(n_lo, min(n, n_hi))
+        d = n * int(rng.integers(2, 5))
+        A = np.asfortranarray(np.abs(rng.standard_normal((d, n))).astype(np.float32))
+        x = _sparse_rows(rng, 1, n, zero_frac, lambda s: rng.random(s))
+        b = _noisy_rhs(rng, A.astype(np.float64), x, 0.01).astype(np.float32)
+        probs.append(Problem(A, np.ascontiguousarray(b), x, tol, f"uneven_{p}",
+                             {"d": d, "n": n, "dtype": "f32"}))
+    return probs
+
+
+def warmstart_family(d=8000, n=2000, k=1024, support=(50, 400), seed=1005, rhs_seed=None,
+                     tol=1e-6):
+    """Fixed lopsided A (U[0,1] times log-uniform column scales, FP32) with k RHS
+    whose x_true has a random support size in [support] and Exp(1) values;
+    b = A x_true + 1% noise.  ``rhs_seed`` selects a disjoint RHS stream so the
+    training and held-out sets share A but not right-hand sides."""
+    rng = _rng(seed)
+    A = np.asfortranarray(_lopsided_A(rng, d, n).astype(np.float32))
+    r2 = _rng(seed if rhs_seed is None else rhs_seed)
+    if rhs_seed is None:
+        r2 = rng
+    X = np.zeros((k, n))
+    for c in range(k):
+        m = int(r2.integers(support[0], support[1] + 1))
+        idx = r2.permutation(n)[:m]
+        X[c, idx] = r2.exponential(1.0, m)
+    B = _noisy_rhs(r2, A.astype(np.float64), X, 0.01).astype(np.float32)
+    return Problem(A, np.ascontiguousarray(B), X, tol, "warmstart_family",
+                   {"d": d, "n": n, "k": k, "dtype": "f32"})
+
+
+CONFIGS = {
+    "uniform_small_1000x200_f64": uniform_small,
+    "lopsided_single_20000x5000_f32": lopsided_single,
+    "shared_multi_rhs_10000x1000_k4096_f32": shared_multi_rhs,
+    "uneven_batch_512": uneven_batch,
+    "warmstart_8000x2000": warmstart_family,
+}
