@@ -76,7 +76,10 @@ typedef enum aln_rhs_status {
     ALN_RHS_EMPTY_PASSIVE = 1, /* P(y) = ∅: y is a KKT point (Alg. 2 stop rule) */
     ALN_RHS_CURVATURE = 2,     /* ḡᵀQḡ ≤ 0 with ḡ ≠ 0: numerically converged */
     ALN_RHS_MAXITER = 3,       /* max_iter reached; X holds the last iterate */
-    ALN_RHS_NONFINITE = 4      /* the iteration produced NaN/Inf */
+    ALN_RHS_NONFINITE = 4,     /* the iteration produced NaN/Inf */
+    ALN_RHS_STAGNATED = 5      /* no new smallest ‖ḡ‖² within the stagnation window and
+                                  the FP64 check still above tol (the paper's
+                                  experimental stop rule, §5) */
 } aln_rhs_status;
 
 typedef struct aln_options {
@@ -86,6 +89,9 @@ typedef struct aln_options {
     int32_t graph_chunk;  /* Alg. 2 iterations per captured CUDA graph launch;
                              0 selects a size-dependent default */
     int32_t row_groups;   /* row groups of the single-RHS matvec; 0 = auto */
+    int32_t stagnation;   /* stop an inner run after this many iterations without a
+                             new smallest ‖ḡ‖² (§5 stop rule); 0 = default 100 */
+    int32_t reserved[3];
 } aln_options;
 
 typedef struct aln_solve_info {
@@ -99,7 +105,8 @@ typedef struct aln_solve_info {
 
 typedef struct aln_ctx aln_ctx;
 
-/* Fill *opt with the defaults (precision SPLIT_BF16, max_refine 8, auto chunk). */
+/* Fill *opt with the defaults (precision SPLIT_BF16, max_refine 8, automatic
+ * graph chunk and row groups, stagnation window 100). */
 void aln_default_options(aln_options* opt);
 
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -149,6 +156,20 @@ aln_status aln_kkt_residual(aln_ctx* ctx, const double* X, int64_t ldx, double* 
  * Errors: NOT_PREPARED, INVALID_ARG, CUDA. */
 aln_status aln_export_scaled(aln_ctx* ctx, double* Q, int64_t ldq, double* q, int64_t ldqv,
                              double* s);
+
+/* Device-time breakdown of the last calls, measured with CUDA events on the
+ * context's stream, and counters (for benchmarks and tracing). */
+typedef struct aln_stats {
+    double prepare_ms;       /* last aln_prepare */
+    double gram_ms;          /*   of which the Gram kernel (H → Q) */
+    double solve_ms;         /* last aln_solve, all right-hand sides */
+    double kkt_ms;           /*   of which the FP64 KKT passes */
+    int64_t kernel_launches; /* kernels this context launched since creation */
+    int64_t iterations;      /* Alg. 2 iterations in the last aln_solve */
+} aln_stats;
+
+/* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */
+aln_status aln_get_stats(aln_ctx* ctx, aln_stats* out);
 
 /* Destroy a context and free its workspace (NULL is accepted). */
 void aln_destroy(aln_ctx* ctx);

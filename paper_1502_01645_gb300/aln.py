@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libaln (include/aln.h).
+
+The functions keep the C names and do argument marshalling only: every step of
+the solver runs in the CUDA library.  Array arguments may be torch tensors
+(device or host) or numpy arrays; their data pointers are passed through.
+Loading fails loudly when the library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libaln.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_NOT_PREPARED, ERR_NONFINITE = 1, 2, 3
+ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = 4, 5, 6, 7
+PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+DTYPE_F32, DTYPE_F64 = 0, 1
+RHS_CONVERGED, RHS_EMPTY_PASSIVE, RHS_CURVATURE = 0, 1, 2
+RHS_MAXITER, RHS_NONFINITE, RHS_STAGNATED = 3, 4, 5
+
+# Every symbol include/aln.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "aln_default_options", "aln_create", "aln_prepare", "aln_solve", "aln_kkt_residual",
+    "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
+)
+
+
+class AlnOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_refine", ctypes.c_int32),
+                ("graph_chunk", ctypes.c_int32), ("row_groups", ctypes.c_int32),
+                ("stagnation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class AlnSolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("refine_rounds", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rel_kkt", ctypes.c_double), ("objective", ctypes.c_double)]
+
+
+class AlnStats(ctypes.Structure):
+    _fields_ = [("prepare_ms", ctypes.c_double), ("gram_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("kkt_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64)]
+
+
+class AlnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where} failed: {status_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libaln (once).  Raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libaln is not built ({p} missing); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    lib.aln_default_options.argtypes = [ctypes.POINTER(AlnOptions)]
+    lib.aln_default_options.restype = None
+    lib.aln_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(AlnOptions), vp]
+    lib.aln_create.restype = ctypes.c_int
+    lib.aln_prepare.argtypes = [vp, vp, i64, i64, i64, i32, vp, i64, i64]
+    lib.aln_prepare.restype = ctypes.c_int
+    lib.aln_solve.argtypes = [vp, ctypes.c_double, i32, dp, i64, dp, ctypes.POINTER(AlnSolveInfo)]
+    lib.aln_solve.restype = ctypes.c_int
+    lib.aln_kkt_residual.argtypes = [vp, dp, i64, dp, dp]
+    lib.aln_kkt_residual.restype = ctypes.c_int
+    lib.aln_export_scaled.argtypes = [vp, dp, i64, dp, i64, dp]
+    lib.aln_export_scaled.restype = ctypes.c_int
+    lib.aln_get_stats.argtypes = [vp, ctypes.POINTER(AlnStats)]
+    lib.aln_get_stats.restype = ctypes.c_int
+    lib.aln_destroy.argtypes = [vp]
+    lib.aln_destroy.restype = None
+    lib.aln_status_string.argtypes = [ctypes.c_int]
+    lib.aln_status_string.restype = ctypes.c_char_p
+    lib.aln_version.argtypes = []
+    lib.aln_version.restype = i32
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().aln_status_string(code).decode()
+    except Exception:  # pragma: no cover - only for messages
+        return f"status {code}"
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise AlnError(code, where)
+
+
+def _ptr(a):
+    """Raw data pointer of a torch tensor or numpy array (None → NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _dtype_code(a) -> int:
+    name = str(a.dtype)
+    if name.endswith("float64"):
+        return DTYPE_F64
+    if name.endswith("float32"):
+        return DTYPE_F32
+    raise ValueError(f"unsupported dtype {a.dtype}")
+
+
+# ------------------------------------------------------------------ C-named calls
+def aln_default_options() -> AlnOptions:
+    o = AlnOptions()
+    load().aln_default_options(ctypes.byref(o))
+    return o
+
+
+def aln_create(opt: AlnOptions | None = None, stream: int | None = None) -> int:
+    ctx = ctypes.c_void_p()
+    _check(load().aln_create(ctypes.byref(ctx), ctypes.byref(opt) if opt is not None else None,
+                             stream or None), "aln_create")
+    return ctx.value
+
+
+def aln_prepare(ctx, A, d, n, lda, dtype, B, k, ldb) -> None:
+    _check(load().aln_prepare(ctx, _ptr(A), d, n, lda, dtype, _ptr(B), k, ldb), "aln_prepare")
+
+
+def aln_solve(ctx, tol, max_iter, X, ldx, X0, k) -> list:
+    info = (AlnSolveInfo * k)()
+    _check(load().aln_solve(ctx, tol, max_iter, _ptr(X), ldx, _ptr(X0), info), "aln_solve")
+    return list(info)
+
+
+def aln_kkt_residual(ctx, X, ldx, rel, obj) -> None:
+    _check(load().aln_kkt_residual(ctx, _ptr(X), ldx, _ptr(rel), _ptr(obj)), "aln_kkt_residual")
+
+
+def aln_export_scaled(ctx, Q, ldq, q, ldqv, s) -> None:
+    _check(load().aln_export_scaled(ctx, _ptr(Q), ldq, _ptr(q), ldqv, _ptr(s)),
+           "aln_export_scaled")
+
+
+def aln_get_stats(ctx) -> AlnStats:
+    st = AlnStats()
+    _check(load().aln_get_stats(ctx, ctypes.byref(st)), "aln_get_stats")
+    return st
+
+
+def aln_destroy(ctx) -> None:
+    if ctx:
+        load().aln_destroy(ctx)
+
+
+def aln_version() -> int:
+    return load().aln_version()
+
+
+# --------------------------------------------------------------- convenience class
+@dataclass
+class SolveInfo:
+    iters: int
+    status: int
+    refine_rounds: int
+    rel_kkt: float
+    objective: float
+
+
+class Solver:
+    """One library context.  ``A`` is (d, n) column-major — a Fortran-ordered
+    numpy array, or a torch tensor whose transpose is contiguous; ``B`` is
+    (k, d) row-major (one right-hand side per row).  Inputs on the host are
+    copied by the library; device inputs must stay alive while in use."""
+
+    def __init__(self, precision: str = "split_bf16", stream=None, **opts):
+        o = aln_default_options()
+        o.precision = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16}[precision]
+        for k, v in opts.items():
+            setattr(o, k, v)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = None
+        self.ctx = aln_create(o, stream)
+        self.precision = precision
+        self._keep = ()
+        self.n = self.k = 0
+
+    def prepare(self, A, B):
+        d, n = A.shape
+        lda = _col_major_ld(A)
+        if B.ndim == 1:
+            B = B.reshape(1, -1)
+        k, dB = B.shape
+        if dB != d:
+            raise ValueError("B rows must have length d")
+        ldb = _row_major_ld(B)
+        self._keep = (A, B)
+        aln_prepare(self.ctx, A, d, n, lda, _dtype_code(A), B, k, ldb)
+        self.n, self.k = n, k
+
+    def solve(self, tol=1e-6, max_iter=0, X=None, X0=None):
+        if X is None:
+            X = np.zeros((self.k, self.n))
+        info = aln_solve(self.ctx, tol, max_iter, X, _row_major_ld(X), X0, self.k)
+        return X, [SolveInfo(i.iters, i.status, i.refine_rounds, i.rel_kkt, i.objective)
+                   for i in info]
+
+    def kkt(self, X):
+        rel = np.zeros(self.k)
+        obj = np.zeros(self.k)
+        aln_kkt_residual(self.ctx, X, _row_major_ld(X), rel, obj)
+        return rel, obj
+
+    def export(self):
+        Q = np.zeros((self.n, self.n))
+        q = np.zeros((self.k, self.n))
+        s = np.zeros(self.n)
+        aln_export_scaled(self.ctx, Q, self.n, q, self.n, s)
+        return Q, q, s
+
+    def stats(self) -> AlnStats:
+        return aln_get_stats(self.ctx)
+
+    def close(self):
+        aln_destroy(self.ctx)
+        self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        if getattr(self, "ctx", None):
+            try:
+                self.close()
+            except Exception:
+                pass
+
+
+def _col_major_ld(A) -> int:
+    """Leading dimension of a (d, n) column-major array (stride of dim 1)."""
+    if isinstance(A, np.ndarray):
+        s0, s1 = A.strides[0] // A.itemsize, A.strides[1] // A.itemsize
+    else:
+        s0, s1 = A.stride()
+    if A.shape[1] == 1:
+        if s0 != 1 and A.shape[0] > 1:
+            raise ValueError("A must be column-major (Fortran order / transposed contiguous)")
+        return max(s1, A.shape[0])
+    if s0 != 1:
+        raise ValueError("A must be column-major (Fortran order / transposed contiguous)")
+    return s1
+
+
+def _row_major_ld(B) -> int:
+    if isinstance(B, np.ndarray):
+        s0, s1 = B.strides[0] // B.itemsize, B.strides[1] // B.itemsize
+    else:
+        s0, s1 = B.stride()
+    if s1 != 1:
+        raise ValueError("rows must be contiguous")
+    return s0 if B.shape[0] > 1 else max(s0, B.shape[1])

@@ -1,0 +1,594 @@
+// C ABI of libaln (include/aln.h): context, workspace, Alg. 1 prepare, the
+// Alg. 2 solve loop with FP64 KKT checks and refinement, and inspection calls.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace aln;
+
+namespace {
+
+#define ALN_TRY(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_status(e_);  \
+    } while (0)
+#define ALN_CHECK(st)                          \
+    do {                                       \
+        aln_status s_ = (st);                  \
+        if (s_ != ALN_OK) return s_;           \
+    } while (0)
+
+aln_status cuda_status(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return ALN_ERR_OUT_OF_MEMORY;
+    }
+    return ALN_ERR_CUDA;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// (Re)allocate a device buffer so that it holds at least `bytes`.
+aln_status ensure(void** p, size_t* cap, size_t bytes) {
+    if (*cap >= bytes && *p) return ALN_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (bytes == 0) return ALN_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ALN_ERR_OUT_OF_MEMORY;
+    }
+    *cap = bytes;
+    return ALN_OK;
+}
+
+size_t elt(int32_t dtype) { return dtype == ALN_DTYPE_F64 ? 8 : 4; }
+bool fp64(const aln_ctx* c) { return c->opt.precision == ALN_PREC_FP64; }
+
+void destroy_graph(aln_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+// Host buffers → device: owned copy; device buffers are used in place.
+aln_status resolve_input(aln_ctx* c, const void* src, int64_t rows, int64_t cols, int64_t ld,
+                         size_t esz, void** copy, size_t* cap, const void** out) {
+    if (is_device_ptr(src)) {
+        *out = src;
+        return ALN_OK;
+    }
+    const size_t bytes = (size_t)((cols - 1) * ld + rows) * esz;
+    ALN_CHECK(ensure(copy, cap, bytes));
+    ALN_TRY(cudaMemcpyAsync(*copy, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    *out = *copy;
+    return ALN_OK;
+}
+
+// Iteration and KKT workspace for the current (n, d, precision).
+aln_status alloc_workspace(aln_ctx* c) {
+    const size_t T = fp64(c) ? 8 : 4;
+    const int64_t ldq = c->ldq, n = c->n, d = c->d;
+    // matvec geometry: tile of 32·VN columns, R row groups
+    const int64_t col_tiles = ldq / (fp64(c) ? 64 : 128);
+    int R = c->opt.row_groups;
+    if (R <= 0) {
+        const int64_t want = 2 * (int64_t)c->num_sms;  // ≈ 2 blocks per SM
+        R = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(want, col_tiles), ceil_div(n, 16)));
+        R = std::min(R, 64);
+    }
+    c->R = R;
+    c->nb = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
+    const size_t vec = (size_t)ldq * T;
+    size_t bytes = 6 * vec + (size_t)R * vec + 2 * (size_t)c->nb * 8 + (size_t)c->nb * 4 + 256;
+    bytes = round_up(bytes, 256);
+    ALN_CHECK(ensure(&c->iter_pool, &c->iter_bytes, bytes + 1024));
+    uint8_t* p = (uint8_t*)c->iter_pool;
+    auto take = [&](size_t b) {
+        uint8_t* r = p;
+        p += round_up(b, 256);
+        return (void*)r;
+    };
+    c->qv = take(vec);
+    c->y = take(vec);
+    c->g = take(vec);
+    c->gb = take(vec);
+    c->w = take(vec);
+    c->e = take(vec);
+    c->part = take((size_t)R * vec);
+    c->gpart = (double*)take((size_t)c->nb * 8);
+    c->kpart = (double*)take((size_t)c->nb * 8);
+    c->cpart = (int*)take((size_t)c->nb * 4);
+    c->st = (IterState*)take(sizeof(IterState));
+    ALN_TRY(cudaMemsetAsync(c->iter_pool, 0, c->iter_bytes, c->stream));
+
+    // KKT: x64 (ldq), g64 (ldq), r64 (d), rpart (CG·d), parts, out
+    const int64_t row_blocks = ceil_div(d, 256);
+    int CG = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * (int64_t)c->num_sms, row_blocks),
+                                                         ceil_div(n, 32)));
+    CG = std::min(CG, 64);
+    c->CG = CG;
+    const int64_t ng = ceil_div(n, 8);
+    size_t kb = 2 * (size_t)ldq * 8 + (size_t)d * 8 + (size_t)CG * d * 8 + (512 + ng) * 8 + 64;
+    kb = round_up(kb, 256) + 2048;
+    ALN_CHECK(ensure(&c->kkt_pool, &c->kkt_bytes, kb));
+    p = (uint8_t*)c->kkt_pool;
+    c->x64 = (double*)take((size_t)ldq * 8);
+    c->g64 = (double*)take((size_t)ldq * 8);
+    c->r64 = (double*)take((size_t)d * 8);
+    c->rpart = (double*)take((size_t)CG * d * 8);
+    c->kkt_part = (double*)take((512 + ng) * 8);
+    c->kkt_out = (double*)take(64);
+    ALN_TRY(cudaMemsetAsync(c->kkt_pool, 0, c->kkt_bytes, c->stream));
+    return ALN_OK;
+}
+
+aln_status build_graph(aln_ctx* c) {
+    destroy_graph(c);
+    cudaGraph_t g = nullptr;
+    ALN_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = fp64(c) ? launch_iter_chunk<double>(c, c->graph_chunk)
+                            : launch_iter_chunk<float>(c, c->graph_chunk);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return ALN_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return ALN_ERR_CUDA;
+    }
+    return ALN_OK;
+}
+
+// Run the captured chunk until the device state says the loop has stopped.
+// Every launch either advances the iteration counter by graph_chunk or stops
+// the loop, so max_iter bounds the number of launches; exceeding that bound
+// means the device state is inconsistent and is reported as a timeout.
+aln_status run_until_done(aln_ctx* c, int max_iter) {
+    const int64_t bound = max_iter / c->graph_chunk + 3;
+    for (int64_t l = 0; l < bound; ++l) {
+        ALN_TRY(cudaGraphLaunch(c->graph, c->stream));
+        c->launches += 5LL * c->graph_chunk;
+        ALN_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(IterState), cudaMemcpyDeviceToHost,
+                                c->stream));
+        ALN_TRY(cudaStreamSynchronize(c->stream));
+        if (c->st_host->done) return ALN_OK;
+    }
+    return ALN_ERR_TIMEOUT;
+}
+
+aln_status kkt_eval(aln_ctx* c, int64_t rhs, const double* x64dev, double* rel, double* F) {
+    const void* b = (const uint8_t*)c->B + (size_t)rhs * c->ldb * elt(c->dtype);
+    ALN_TRY(cudaEventRecord(c->ev[6], c->stream));
+    ALN_TRY(launch_kkt(c, x64dev, b, c->den_host[rhs], c->kkt_out));
+    c->launches += 4;
+    ALN_TRY(cudaEventRecord(c->ev[7], c->stream));
+    ALN_TRY(cudaMemcpyAsync(c->kkt_out_host, c->kkt_out, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess) c->stats.kkt_ms += ms;
+    *rel = c->kkt_out_host[0];
+    *F = c->kkt_out_host[1];
+    return ALN_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// Kernels local to the ABI layer (export / conversions)
+// ----------------------------------------------------------------------------
+template <typename TS>
+__global__ void k_copy_to_f64(const TS* __restrict__ src, int64_t lds, double* __restrict__ dst,
+                              int64_t ldd, int64_t rows, int64_t cols) {
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / cols, c = e - r * cols;
+        dst[r * ldd + c] = (double)src[r * lds + c];
+    }
+}
+
+extern "C" {
+
+void aln_default_options(aln_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = ALN_PREC_SPLIT_BF16;
+    opt->max_refine = 8;
+    opt->graph_chunk = 0;
+    opt->row_groups = 0;
+    opt->stagnation = 100;
+}
+
+int32_t aln_version(void) { return ALN_VERSION; }
+
+const char* aln_status_string(aln_status s) {
+    switch (s) {
+        case ALN_OK: return "ALN_OK";
+        case ALN_ERR_INVALID_ARG: return "ALN_ERR_INVALID_ARG";
+        case ALN_ERR_NOT_PREPARED: return "ALN_ERR_NOT_PREPARED";
+        case ALN_ERR_NONFINITE: return "ALN_ERR_NONFINITE";
+        case ALN_ERR_OUT_OF_MEMORY: return "ALN_ERR_OUT_OF_MEMORY";
+        case ALN_ERR_CUDA: return "ALN_ERR_CUDA";
+        case ALN_ERR_TIMEOUT: return "ALN_ERR_TIMEOUT";
+        case ALN_ERR_UNSUPPORTED: return "ALN_ERR_UNSUPPORTED";
+    }
+    return "ALN_ERR_UNKNOWN";
+}
+
+aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
+    if (!out) return ALN_ERR_INVALID_ARG;
+    *out = nullptr;
+    aln_options o;
+    aln_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != ALN_PREC_FP64 && o.precision != ALN_PREC_SPLIT_BF16)
+        return ALN_ERR_INVALID_ARG;
+    if (o.max_refine < 0 || o.graph_chunk < 0 || o.row_groups < 0 || o.stagnation < 0)
+        return ALN_ERR_INVALID_ARG;
+    if (o.stagnation == 0) o.stagnation = 100;
+    aln_ctx* c = new (std::nothrow) aln_ctx();
+    if (!c) return ALN_ERR_OUT_OF_MEMORY;
+    c->opt = o;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, c->device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return ALN_ERR_CUDA;
+    }
+    if (o.precision == ALN_PREC_SPLIT_BF16 && !tc_supported(c->cc_major, c->cc_minor)) {
+        delete c;
+        return ALN_ERR_UNSUPPORTED;
+    }
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        // A private blocking stream: ordered after legacy-stream work and, unlike
+        // the legacy stream itself, usable for graph capture.
+        if (cudaStreamCreate(&c->own_stream) != cudaSuccess) {
+            delete c;
+            return ALN_ERR_CUDA;
+        }
+        c->stream = c->own_stream;
+    }
+    if (cudaMallocHost(&c->host_pool, 4096) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->own_stream) cudaStreamDestroy(c->own_stream);
+        delete c;
+        return ALN_ERR_OUT_OF_MEMORY;
+    }
+    for (auto& ev : c->ev) {
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+            cudaGetLastError();
+            aln_destroy(c);
+            return ALN_ERR_CUDA;
+        }
+    }
+    uint8_t* h = (uint8_t*)c->host_pool;
+    c->st_host = (IterState*)h;
+    c->kkt_out_host = (double*)(h + 256);
+    c->flags_host = (int*)(h + 512);
+    *out = c;
+    return ALN_OK;
+}
+
+void aln_destroy(aln_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    destroy_graph(c);
+    void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (c->den_host) cudaFreeHost(c->den_host);
+    if (c->host_pool) cudaFreeHost(c->host_pool);
+    for (auto ev : c->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t lda, int32_t dtype,
+                       const void* B, int64_t k, int64_t ldb) {
+    if (!c || !A || !B) return ALN_ERR_INVALID_ARG;
+    if (d < 1 || n < 1 || k < 1 || lda < d || ldb < d) return ALN_ERR_INVALID_ARG;
+    if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
+    if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
+    c->prepared = 0;
+    destroy_graph(c);
+    c->stats.prepare_ms = c->stats.gram_ms = 0.0;
+    const size_t esz = elt(dtype);
+    ALN_CHECK(resolve_input(c, A, d, n, lda, esz, &c->A_copy, &c->A_copy_bytes, &c->A));
+    ALN_CHECK(resolve_input(c, B, d, k, ldb, esz, &c->B_copy, &c->B_copy_bytes, &c->B));
+    c->d = d;
+    c->n = n;
+    c->k = k;
+    c->lda = lda;
+    c->ldb = ldb;
+    c->dtype = dtype;
+    const bool f64 = fp64(c);
+    const int64_t ldq = round_up(n, 128);
+    const size_t qbytes = (size_t)ldq * ldq * (f64 ? 8 : 4);
+    const bool fresh_q = c->Q == nullptr || c->ldq != ldq || c->Q_elt != (f64 ? 8 : 4);
+    ALN_CHECK(ensure(&c->Q, &c->Q_bytes, qbytes));
+    c->ldq = ldq;
+    c->Q_elt = f64 ? 8 : 4;
+    if (fresh_q || c->Q_n != n) ALN_TRY(cudaMemsetAsync(c->Q, 0, c->Q_bytes, c->stream));
+    c->Q_n = n;
+
+    // s, inv_s, q64 (k·ldq), den (k), flags
+    const size_t pb = round_up((size_t)2 * ldq * 8, 256) + round_up((size_t)k * ldq * 8, 256) +
+                      round_up((size_t)k * 8, 256) + 256;
+    ALN_CHECK(ensure(&c->prep_pool, &c->prep_bytes, pb));
+    uint8_t* p = (uint8_t*)c->prep_pool;
+    c->s = (double*)p;
+    c->inv_s = c->s + ldq;
+    p += round_up((size_t)2 * ldq * 8, 256);
+    c->q64 = (double*)p;
+    p += round_up((size_t)k * ldq * 8, 256);
+    c->den = (double*)p;
+    p += round_up((size_t)k * 8, 256);
+    c->flags = (int*)p;
+    ALN_TRY(cudaMemsetAsync(c->prep_pool, 0, c->prep_bytes, c->stream));
+    if (c->den_host_cap < k) {
+        if (c->den_host) cudaFreeHost(c->den_host);
+        c->den_host = nullptr;
+        c->den_host_cap = 0;
+        if (cudaMallocHost(&c->den_host, (size_t)k * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        c->den_host_cap = k;
+    }
+
+    // split copies for the tensor-core Gram
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    if (!f64) {
+        c->ldk = round_up(d, 64);
+        const size_t sb = (size_t)n * c->ldk * 2;
+        ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 2 * round_up(sb, 1024)));
+        hi = c->A_hi;
+        lo = (__nv_bfloat16*)((uint8_t*)c->A_hi + round_up(sb, 1024));
+        c->A_lo = lo;
+    }
+
+    // Alg. 1: scale factors, q, (split), Gram
+    ALN_TRY(cudaEventRecord(c->ev[0], c->stream));
+    ALN_TRY(launch_check_finite(c->B, dtype, d, k, ldb, c->flags, c->stream));
+    const int kc = k <= 4 ? (int)k : 0;
+    ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64, ldq,
+                            c->flags, hi, lo, c->ldk, c->stream));
+    if (kc == 0)
+        ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
+                              c->stream));
+    ALN_TRY(launch_denominators(c->q64, n, ldq, k, c->den, c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
+    if (f64)
+        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
+    else
+        ALN_TRY(launch_gram_tc(hi, lo, d, n, c->ldk, c->inv_s, (float*)c->Q, ldq, c->flags + 1,
+                               c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
+    c->launches += 4 + (kc == 0 ? 1 : 0);
+
+    ALN_CHECK(alloc_workspace(c));
+    ALN_TRY(cudaMemcpyAsync(c->flags_host, c->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaMemcpyAsync(c->den_host, c->den, (size_t)k * 8, cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[3], c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, c->ev[0], c->ev[3]);
+        cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+        c->stats.prepare_ms = a;
+        c->stats.gram_ms = b;
+    }
+    if (c->flags_host[1]) return ALN_ERR_TIMEOUT;
+    if (c->flags_host[0]) return ALN_ERR_NONFINITE;
+
+    int chunk = c->opt.graph_chunk;
+    if (chunk <= 0) chunk = n <= 2048 ? 32 : 16;
+    c->graph_chunk = chunk;
+    ALN_CHECK(build_graph(c));
+    c->prepared = 1;
+    return ALN_OK;
+}
+
+aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_t ldx,
+                     const double* X0, aln_solve_info* info) {
+    if (!c) return ALN_ERR_INVALID_ARG;
+    if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (!X || ldx < c->n || !(tol > 0.0) || !std::isfinite(tol)) return ALN_ERR_INVALID_ARG;
+    const int64_t n = c->n;
+    if (max_iter <= 0) max_iter = (int32_t)std::max<int64_t>(5 * n, 20000);
+    const bool x_dev = is_device_ptr(X);
+    const bool x0_dev = X0 ? is_device_ptr(X0) : false;
+    const bool f64 = fp64(c);
+    c->stats.solve_ms = c->stats.kkt_ms = 0.0;
+    c->stats.iterations = 0;
+    ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
+    // Inner runs stop a little below tol so that the FP64 check usually passes
+    // at once; refinement rounds aim lower still.
+    const double first_factor = 0.5, refine_factor = 0.25;
+
+    for (int64_t rhs = 0; rhs < c->k; ++rhs) {
+        const double den = c->den_host[rhs];
+        auto eps_of = [&](double t) {
+            const double a = t * (den > 0.0 ? den : 1.0);
+            return a * a;
+        };
+        const double* x0 = nullptr;
+        if (X0) {
+            // stage x0 in g64 (free until the first KKT pass)
+            ALN_TRY(cudaMemcpyAsync(c->g64, X0 + rhs * ldx, (size_t)n * 8,
+                                    x0_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    c->stream));
+            int* bad = c->flags;
+            ALN_TRY(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+            ALN_TRY(launch_check_finite(c->g64, ALN_DTYPE_F64, n, 1, n, bad, c->stream));
+            c->launches += 1;
+            ALN_TRY(cudaMemcpyAsync(c->flags_host, bad, sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+            ALN_TRY(cudaStreamSynchronize(c->stream));
+            if (c->flags_host[0]) return ALN_ERR_NONFINITE;
+            x0 = c->g64;
+        }
+        const double* q64 = c->q64 + rhs * c->ldq;
+        int total = 0, rounds = 0, status = ALN_RHS_MAXITER;
+        double rel = 0.0, F = 0.0;
+        ALN_TRY(f64 ? launch_iter_setup<double>(c, q64, x0, eps_of(tol * first_factor), max_iter)
+                    : launch_iter_setup<float>(c, q64, x0, eps_of(tol * first_factor), max_iter));
+        c->launches += x0 ? 4 : 3;
+        for (;;) {
+            ALN_CHECK(run_until_done(c, max_iter - total));
+            total += c->st_host->iter;
+            const int inner = c->st_host->status;
+            ALN_TRY(f64 ? launch_unscale<double>(c, c->x64) : launch_unscale<float>(c, c->x64));
+            c->launches += 1;
+            ALN_CHECK(kkt_eval(c, rhs, c->x64, &rel, &F));
+            if (rel <= tol) {
+                status = inner == ALN_RHS_EMPTY_PASSIVE ? ALN_RHS_EMPTY_PASSIVE : ALN_RHS_CONVERGED;
+                break;
+            }
+            if (inner == ALN_RHS_NONFINITE) {
+                status = ALN_RHS_NONFINITE;
+                break;
+            }
+            if (total >= max_iter || inner == ALN_RHS_MAXITER) {
+                status = ALN_RHS_MAXITER;
+                break;
+            }
+            if (rounds >= c->opt.max_refine) {
+                status = inner == ALN_RHS_STAGNATED ? ALN_RHS_STAGNATED : ALN_RHS_MAXITER;
+                break;
+            }
+            // Refinement: restart the inner loop from the current y with the exact
+            // FP64 gradient g = Qy + q evaluated from A (left in c->g64 by the KKT pass).
+            ++rounds;
+            ALN_TRY(f64 ? launch_iter_refresh_from_g64<double>(c, eps_of(tol * refine_factor),
+                                                               max_iter - total)
+                        : launch_iter_refresh_from_g64<float>(c, eps_of(tol * refine_factor),
+                                                              max_iter - total));
+            c->launches += 2;
+        }
+        c->stats.iterations += total;
+        ALN_TRY(cudaMemcpyAsync(X + rhs * ldx, c->x64, (size_t)n * 8,
+                                x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+        if (info) {
+            info[rhs].iters = total;
+            info[rhs].status = status;
+            info[rhs].refine_rounds = rounds;
+            info[rhs].reserved = 0;
+            info[rhs].rel_kkt = rel;
+            info[rhs].objective = F;
+        }
+    }
+    ALN_TRY(cudaEventRecord(c->ev[5], c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) c->stats.solve_ms = ms;
+    return ALN_OK;
+}
+
+aln_status aln_get_stats(aln_ctx* c, aln_stats* out) {
+    if (!c || !out) return ALN_ERR_INVALID_ARG;
+    *out = c->stats;
+    out->kernel_launches = c->launches;
+    return ALN_OK;
+}
+
+aln_status aln_kkt_residual(aln_ctx* c, const double* X, int64_t ldx, double* rel_kkt,
+                            double* objective) {
+    if (!c) return ALN_ERR_INVALID_ARG;
+    if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (!X || !rel_kkt || ldx < c->n) return ALN_ERR_INVALID_ARG;
+    const bool x_dev = is_device_ptr(X);
+    const bool r_dev = is_device_ptr(rel_kkt);
+    const bool o_dev = objective ? is_device_ptr(objective) : false;
+    for (int64_t rhs = 0; rhs < c->k; ++rhs) {
+        ALN_TRY(cudaMemcpyAsync(c->x64, X + rhs * ldx, (size_t)c->n * 8,
+                                x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+        double rel, F;
+        ALN_CHECK(kkt_eval(c, rhs, c->x64, &rel, &F));
+        ALN_TRY(cudaMemcpy(rel_kkt + rhs, &rel, 8,
+                           r_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+        if (objective)
+            ALN_TRY(cudaMemcpy(objective + rhs, &F, 8,
+                               o_dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost));
+    }
+    return ALN_OK;
+}
+
+aln_status aln_export_scaled(aln_ctx* c, double* Q, int64_t ldq, double* q, int64_t ldqv,
+                             double* s) {
+    if (!c) return ALN_ERR_INVALID_ARG;
+    if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    const int64_t n = c->n;
+    if ((Q && ldq < n) || (q && ldqv < n)) return ALN_ERR_INVALID_ARG;
+    if (Q) {
+        const bool dev = is_device_ptr(Q);
+        double* dst = Q;
+        double* tmp = nullptr;
+        if (!dev) {
+            ALN_TRY(cudaMalloc(&tmp, (size_t)n * n * 8));
+            dst = tmp;
+        }
+        const int64_t ldd = dev ? ldq : n;
+        const int blocks = (int)std::min<int64_t>(ceil_div(n * n, 256), 8192);
+        if (fp64(c))
+            k_copy_to_f64<double><<<blocks, 256, 0, c->stream>>>((const double*)c->Q, c->ldq, dst,
+                                                                 ldd, n, n);
+        else
+            k_copy_to_f64<float><<<blocks, 256, 0, c->stream>>>((const float*)c->Q, c->ldq, dst,
+                                                                ldd, n, n);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !dev)
+            e = cudaMemcpy2DAsync(Q, ldq * 8, tmp, n * 8, n * 8, n, cudaMemcpyDeviceToHost,
+                                  c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (tmp) cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (q) {
+        const bool dev = is_device_ptr(q);
+        ALN_TRY(cudaMemcpy2DAsync(q, ldqv * 8, c->q64, c->ldq * 8, n * 8, c->k,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream));
+    }
+    if (s) {
+        const bool dev = is_device_ptr(s);
+        ALN_TRY(cudaMemcpyAsync(s, c->s, n * 8,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    }
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    return ALN_OK;
+}
+
+}  // extern "C"

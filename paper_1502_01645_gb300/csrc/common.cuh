@@ -1,0 +1,179 @@
+// Shared device helpers and the library context of libaln.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "aln.h"
+
+namespace aln {
+
+constexpr int kWarp = 32;
+
+// Device-resident state of one Alg. 2 run on one right-hand side.  Written by
+// the iteration kernels, read back by the host after each graph launch.
+struct IterState {
+    double eps;       // stop threshold on ‖ḡ‖² (absolute)
+    double gbar2;     // ‖ḡ‖² when the loop stopped
+    double alpha;     // last step size
+    int32_t iter;     // iterations done in this run
+    int32_t max_iter; // iteration cap of this run
+    int32_t done;     // 1 once the loop has stopped
+    int32_t status;   // aln_rhs_status
+    int32_t npassive; // |P| when the loop stopped
+    int32_t window;   // stagnation window (iterations without a new best ‖ḡ‖²)
+    double best_g2;   // smallest ‖ḡ‖² seen in this run
+    int32_t best_iter;
+    int32_t pad;
+};
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    using type = float4;
+    static constexpr int N = 4;
+};
+template <> struct Vec16<double> {
+    using type = double2;
+    static constexpr int N = 2;
+};
+
+__device__ __forceinline__ float vget(const float4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed shuffle tree, then warp 0 over the warp sums).
+// Result is valid in thread 0.  `scratch` needs blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        r = lane < nw ? scratch[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Sum of p[0..count) computed by one warp in a fixed order; valid in all lanes.
+__device__ __forceinline__ double warp_sum_array(const double* __restrict__ p, int count) {
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int i = lane; i < count; i += 32) v += p[i];
+    return warp_sum(v);
+}
+__device__ __forceinline__ int warp_sum_array_i(const int* __restrict__ p, int count) {
+    const int lane = threadIdx.x & 31;
+    int v = 0;
+    for (int i = lane; i < count; i += 32) v += p[i];
+    return warp_sum_i(v);
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+}  // namespace aln
+
+// --------------------------------------------------------------------------
+// Library context (opaque to callers; see include/aln.h)
+// --------------------------------------------------------------------------
+struct aln_ctx {
+    aln_options opt;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;  // created when the caller passes no stream
+    void* host_pool = nullptr;          // pinned: iteration state, KKT result, flags
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+
+    // problem
+    int prepared = 0;
+    int64_t d = 0, n = 0, k = 0;
+    int32_t dtype = ALN_DTYPE_F32;
+    const void* A = nullptr;  // device pointer actually used (caller's or copy)
+    int64_t lda = 0;
+    const void* B = nullptr;
+    int64_t ldb = 0;
+    void* A_copy = nullptr;   // owned copies of host inputs
+    size_t A_copy_bytes = 0;
+    void* B_copy = nullptr;
+    size_t B_copy_bytes = 0;
+
+    // derived problem (Alg. 1)
+    int64_t ldq = 0;          // padded row length of Q and of every n-vector
+    void* Q = nullptr;        // ldq × ldq, float (SPLIT_BF16) or double (FP64)
+    size_t Q_bytes = 0;
+    int Q_elt = 0;            // element size Q was zeroed for
+    int64_t Q_n = 0;          // n Q was zeroed for (padding must stay 0)
+    void* prep_pool = nullptr;  // s, inv_s, q64, den, flags
+    size_t prep_bytes = 0;
+    int64_t den_host_cap = 0;
+    double* s = nullptr;      // n scale factors s_i = ‖A_i‖ (1 for zero columns)
+    double* inv_s = nullptr;  // 1/s_i
+    double* q64 = nullptr;    // k × ldq, q_c = −D⁻¹Aᵀb_c in FP64
+    double* den = nullptr;    // k denominators ‖min(q_c, 0)‖
+    double* den_host = nullptr;
+    int* flags = nullptr;     // [0] nonfinite input, [1] tensor-core timeout
+    int* flags_host = nullptr;
+    // split copies of A for the tensor-core Gram
+    int64_t ldk = 0;
+    __nv_bfloat16* A_hi = nullptr;
+    __nv_bfloat16* A_lo = nullptr;
+    size_t split_bytes = 0;
+
+    // iteration workspace (element type follows the precision)
+    void* qv = nullptr;       // q of the right-hand side being solved (iteration type)
+    void* y = nullptr;
+    void* g = nullptr;
+    void* gb = nullptr;
+    void* w = nullptr;
+    void* e = nullptr;
+    void* part = nullptr;     // R × ldq matvec partials
+    int R = 0;
+    double* gpart = nullptr;  // block partials of ‖ḡ‖²
+    int* cpart = nullptr;     // block partials of |P|
+    double* kpart = nullptr;  // block partials of ḡᵀw
+    int nb = 0;               // number of vector blocks
+    aln::IterState* st = nullptr;
+    aln::IterState* st_host = nullptr;
+    size_t iter_bytes = 0;
+    void* iter_pool = nullptr;
+
+    // KKT workspace
+    double* x64 = nullptr;    // ldq
+    double* r64 = nullptr;    // d
+    double* rpart = nullptr;  // CG × d
+    int CG = 0;
+    double* g64 = nullptr;    // ldq
+    double* kkt_part = nullptr;
+    double* kkt_out = nullptr;     // [rel, F]
+    double* kkt_out_host = nullptr;
+    void* kkt_pool = nullptr;
+    size_t kkt_bytes = 0;
+
+    // captured iteration graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+
+    // statistics (aln_get_stats)
+    cudaEvent_t ev[8] = {};
+    aln_stats stats = {};
+    int64_t launches = 0;
+};

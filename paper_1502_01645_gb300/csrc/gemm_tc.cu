@@ -1,0 +1,370 @@
+// Split-BF16 Gram on the 5th-generation tensor cores (tcgen05 + TMA, sm_103a).
+//
+// Alg. 1 (§3) forms H = AᵀA and Q = D⁻¹HD⁻¹ with D = diag(√H_ii) (Eq. NQPQ).
+// Here every element of A is split into hi = bf16(a) and lo = bf16(a − hi), and
+//     H ≈ hiᵀhi + hiᵀlo + loᵀhi        (the lo·lo term, ≤ 2⁻¹⁸|a_i a_j|, dropped)
+// is accumulated in FP32 in tensor memory.  The epilogue multiplies by the FP64
+// scale factors 1/s_i, 1/s_j (rounded to FP32), sets Q_ii to 1 (0 for a zero
+// column, Eq. Rescaling) and writes each lower-triangle tile and its mirror.
+//
+// Kernel structure (one 128×128 output tile per CTA, 128 threads):
+//   warp 0, one lane: TMA producer — K-major 128×64 BF16 boxes of hi/lo for the
+//                     row tile and the column tile, 128-byte swizzle, into a
+//                     3-stage shared-memory ring guarded by mbarriers;
+//   warp 1, one lane: MMA issuer — 3 products × 4 K-steps of
+//                     tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
+//                     per stage, then tcgen05.commit to free the stage;
+//   all 4 warps:      epilogue — tcgen05.ld 32 lanes × 16 columns at a time,
+//                     scale, store the tile and its transpose.
+// Every wait is bounded (1 s on %globaltimer); on expiry the CTA sets
+// *timeout_flag, waits (bounded) for its own copies and MMAs, frees its tensor
+// memory and exits without storing.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace aln {
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // 64 BF16 = 128 bytes = one swizzle row
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;         // 16 KiB
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;     // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 128;
+constexpr uint64_t WAIT_NS = 1000000000ull;     // 1 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > WAIT_NS) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (SBO), descriptor version 1, tile base 1024-aligned.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+struct GramArgs {
+    int64_t n;
+    int num_kb;
+    const double* inv_s;
+    float* Q;
+    int64_t ldq;
+    int* timeout_flag;
+};
+
+__device__ __forceinline__ void tri_decode(int64_t t, int& I, int& J) {
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    I = (int)r;
+    J = (int)(t - r * (r + 1) / 2);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
+              GramArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    __shared__ float s_cs[BM];
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int tm, tn;
+    tri_decode(blockIdx.x, tm, tn);
+    const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BM;
+    const bool diag = tm == tn;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const int64_t j = n0 + threadIdx.x;
+        s_cs[threadIdx.x] = j < p.n ? (float)p.inv_s[j] : 0.0f;
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int issued = 0;
+        for (int kb = 0; kb < p.num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            uint8_t* sb = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], (diag ? 2 : 4) * TILE_BYTES);
+            tma_load_2d(sb, &m_hi, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sb + TILE_BYTES, &m_lo, &full[s], kb * BK, (int)m0);
+            if (!diag) {
+                tma_load_2d(sb + 2 * TILE_BYTES, &m_hi, &full[s], kb * BK, (int)n0);
+                tma_load_2d(sb + 3 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)n0);
+            }
+            ++issued;
+        }
+        // Our own copies in flight: the last ≤ STAGES loads (bounded wait).
+        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+        for (int kb = 0; kb < p.num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_lo = a_hi + TILE_BYTES;
+            const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TILE_BYTES;
+            const uint32_t b_lo = diag ? a_lo : a_hi + 3 * TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;  // 16 BF16 along K
+                const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+                const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                umma_bf16(tmem, dah, dbl, idesc, 1u);
+                umma_bf16(tmem, dal, dbh, idesc, 1u);
+            }
+            umma_commit(&empty[s]);
+        }
+        // Always commit: `done` then also covers MMAs issued before an abort.
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    // ---------------- epilogue (all 4 warps) ----------------
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ok) s_abort = 1;
+    __syncthreads();
+    if (!s_abort) {
+        const int64_t row = m0 + warp * 32 + lane;
+        const bool rv = row < p.n;
+        const float rs = rv ? (float)p.inv_s[row] : 0.0f;
+        const int cols = (int)(p.n - n0 < (int64_t)BM ? p.n - n0 : (int64_t)BM);
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < cols; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + c0, v);
+            float o[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                o[t] = v[t] * rs * s_cs[c0 + t];
+                if (diag && row == n0 + c0 + t) o[t] = v[t] != 0.0f ? 1.0f : 0.0f;
+            }
+            const int64_t j0 = n0 + c0;
+            if (rv) {
+                float* dst = p.Q + row * p.ldq + j0;
+                if (c0 + 16 <= cols) {
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4)
+                        *reinterpret_cast<float4*>(dst + t) =
+                            make_float4(o[t], o[t + 1], o[t + 2], o[t + 3]);
+                } else {
+                    for (int t = 0; t < cols - c0; ++t) dst[t] = o[t];
+                }
+            }
+            if (!diag && rv) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t)
+                    if (c0 + t < cols) p.Q[(j0 + t) * p.ldq + row] = o[t];
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(p.timeout_flag, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// K-major BF16 matrix [rows][ld] (K contiguous), box 64 (K) × 128 (rows).
+static bool make_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t K, int64_t rows,
+                     int64_t ld) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_minor == 3; }
+
+cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t d,
+                           int64_t n, int64_t ldk, const double* inv_s, float* Q, int64_t ldq,
+                           int* timeout_flag, cudaStream_t st) {
+    using namespace tc;
+    // TMA rules: 16-byte aligned base and row stride; x coordinates are
+    // multiples of 64 BF16 (128 bytes) by construction.
+    if (((uintptr_t)hi & 15) || ((uintptr_t)lo & 15) || (ldk * 2) % 16 != 0 || ldq % 4 != 0)
+        return cudaErrorInvalidValue;
+    CUtensorMap mh, ml;
+    if (!make_map(&mh, hi, ldk, n, ldk) || !make_map(&ml, lo, ldk, n, ldk))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    GramArgs a;
+    a.n = n;
+    a.num_kb = (int)ceil_div(ldk, BK);
+    a.inv_s = inv_s;
+    a.Q = Q;
+    a.ldq = ldq;
+    a.timeout_flag = timeout_flag;
+    const int64_t tiles = ceil_div(n, BM);
+    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, SMEM_BYTES, st>>>(mh, ml, a);
+    return cudaGetLastError();
+}
+
+}  // namespace aln

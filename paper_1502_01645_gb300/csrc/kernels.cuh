@@ -1,0 +1,50 @@
+// Host-side launchers of the libaln kernels (one translation unit each).
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace aln {
+
+constexpr int MODE_GRAM = 0;
+constexpr int MODE_QVEC = 1;
+
+// prep.cu
+cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                            const void* B, int kc, int64_t ldb, double* s, double* inv_s,
+                            double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, int64_t ldk, cudaStream_t st);
+cudaError_t launch_check_finite(const void* X, int32_t dtype, int64_t rows, int64_t cols,
+                                int64_t ld, int* flags, cudaStream_t st);
+cudaError_t launch_denominators(const double* q64, int64_t n, int64_t ldq, int64_t k, double* den,
+                                cudaStream_t st);
+cudaError_t launch_gram64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st);
+cudaError_t launch_qvec64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                          const void* B, int64_t k, int64_t ldb, const double* inv_s, double* q64,
+                          int64_t ldq, cudaStream_t st);
+
+// gemm_tc.cu — split-BF16 tensor-core Gram (tcgen05 + TMA)
+// Q_ij = (Σ_t hi·hi + hi·lo + lo·hi)_ij · inv_s_i · inv_s_j, lower tiles mirrored.
+cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t d,
+                           int64_t n, int64_t ldk, const double* inv_s, float* Q, int64_t ldq,
+                           int* timeout_flag, cudaStream_t st);
+bool tc_supported(int cc_major, int cc_minor);
+
+// iter.cu — Alg. 2 on one right-hand side
+template <typename T>
+cudaError_t launch_iter_setup(aln_ctx* c, const double* q64, const double* x0, double eps,
+                              int max_iter);
+template <typename T>
+cudaError_t launch_iter_chunk(aln_ctx* c, int iters);
+template <typename T>
+cudaError_t launch_iter_refresh_from_g64(aln_ctx* c, double eps, int max_iter);
+template <typename T>
+cudaError_t launch_unscale(aln_ctx* c, double* x64);
+cudaError_t launch_state_reset(aln_ctx* c, double eps, int max_iter);
+
+// kkt.cu — FP64 KKT residual straight from A
+cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);
+
+}  // namespace aln

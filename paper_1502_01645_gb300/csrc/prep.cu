@@ -1,0 +1,260 @@
+// Prepare-phase kernels of Alg. 1 (§3): scale factors, q = −D⁻¹Aᵀb, the
+// split-BF16 copies of A, and the FP64 Gram / AᵀB used by the plain method.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace aln {
+
+// One warp per column A_i:
+//   s_i² = Σ_t A_ti²            (FP64)            — √diag(H) of Alg. 1, Eq. Rescaling
+//   c_ci = Σ_t A_ti B_ct, c < kc (FP64)           — Aᵀb of Eq. NQP
+//   s_i  = √s_i², or 1 when s_i² = 0 (Eq. Rescaling's H_ii = 0 case)
+//   q_ci = −c_ci / s_i                            — q of Eq. NQPQ
+// With SPLIT, also writes hi = bf16(A_ti), lo = bf16(A_ti − hi) into the
+// K-major [n][ldk] arrays read by the tensor-core Gram (zero padding t ≥ d).
+template <typename TA, bool SPLIT>
+__global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int64_t d, int64_t n,
+                                                  int64_t lda, const TA* __restrict__ B, int kc,
+                                                  int64_t ldb, double* __restrict__ s,
+                                                  double* __restrict__ inv_s,
+                                                  double* __restrict__ q64, int64_t ldq,
+                                                  int* __restrict__ flags,
+                                                  __nv_bfloat16* __restrict__ hi,
+                                                  __nv_bfloat16* __restrict__ lo, int64_t ldk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const TA* col = A + i * lda;
+    double s2 = 0.0;
+    bool bad = false;
+#pragma unroll 4
+    for (int64_t t = lane; t < d; t += 32) {
+        const double a = (double)col[t];
+        s2 += a * a;
+        bad |= !isfinite(a);
+        if (SPLIT) {
+            const float af = (float)col[t];
+            const __nv_bfloat16 h = __float2bfloat16_rn(af);
+            const __nv_bfloat16 l = __float2bfloat16_rn(af - __bfloat162float(h));
+            hi[i * ldk + t] = h;
+            lo[i * ldk + t] = l;
+        }
+    }
+    if (SPLIT) {
+        const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+        for (int64_t t = d + lane; t < ldk; t += 32) {
+            hi[i * ldk + t] = z;
+            lo[i * ldk + t] = z;
+        }
+    }
+    s2 = warp_sum(s2);
+    const double si = s2 > 0.0 ? sqrt(s2) : 1.0;
+    for (int c = 0; c < kc; ++c) {
+        const TA* bc = B + (int64_t)c * ldb;
+        double dot = 0.0;
+#pragma unroll 4
+        for (int64_t t = lane; t < d; t += 32) dot += (double)col[t] * (double)bc[t];
+        dot = warp_sum(dot);
+        if (lane == 0) q64[(int64_t)c * ldq + i] = -dot / si;
+    }
+    if (lane == 0) {
+        s[i] = si;
+        inv_s[i] = 1.0 / si;
+        if (bad) atomicOr(flags, 1);
+    }
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                               int* __restrict__ flags) {
+    bool bad = false;
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / rows, r = e - c * rows;
+        bad |= !isfinite((double)X[c * ld + r]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, 1);
+}
+
+// ‖min(q_c, 0)‖ for each right-hand side: the projected gradient at y = 0.
+__global__ void k_denominators(const double* __restrict__ q64, int64_t n, int64_t ldq,
+                               double* __restrict__ den) {
+    __shared__ double scratch[32];
+    const double* q = q64 + (int64_t)blockIdx.x * ldq;
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double m = q[i] < 0.0 ? q[i] : 0.0;
+        v += m * m;
+    }
+    v = block_sum(v, scratch);
+    if (threadIdx.x == 0) den[blockIdx.x] = sqrt(v);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 SIMT product  C[i][j] = Σ_t X[t][i] Y[t][j]  (X, Y column-major, K = d)
+// 64×64 tile per 256-thread block, 4×4 outputs per thread (strided by 16 so
+// shared-memory reads are conflict-free), K staged 16 at a time.
+//   MODE_GRAM: X = Y = A, lower-triangle tiles only; writes
+//              Q_ij = H_ij / (s_i s_j) and its mirror, Q_ii = 1 (0 for a zero
+//              column) — Alg. 1, Eq. NQPQ, Remark of §3.
+//   MODE_QVEC: X = A, Y = B; writes q_ci = −(Aᵀb_c)_i / s_i at out[c*ldo + i].
+// ---------------------------------------------------------------------------
+constexpr int kG64Tile = 64;
+constexpr int kG64K = 16;
+
+__device__ __forceinline__ void tri_decode(int64_t t, int& I, int& J) {
+    // t = I(I+1)/2 + J with 0 ≤ J ≤ I
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    I = (int)r;
+    J = (int)(t - r * (r + 1) / 2);
+}
+
+template <typename TX, typename TY, int MODE>
+__global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t ldx,
+                                               const TY* __restrict__ Y, int64_t ldy, int64_t K,
+                                               int64_t M, int64_t N, int tiles_m,
+                                               const double* __restrict__ inv_s,
+                                               double* __restrict__ out, int64_t ldo) {
+    __shared__ double Xs[kG64K][kG64Tile];
+    __shared__ double Ys[kG64K][kG64Tile];
+    int tm, tn;
+    if (MODE == MODE_GRAM) {
+        tri_decode(blockIdx.x, tm, tn);
+    } else {
+        tm = blockIdx.x % tiles_m;
+        tn = blockIdx.x / tiles_m;
+    }
+    const int64_t i0 = (int64_t)tm * kG64Tile, j0 = (int64_t)tn * kG64Tile;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int64_t k0 = 0; k0 < K; k0 += kG64K) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int kk = e & 15, ii = e >> 4;
+            const int64_t gk = k0 + kk;
+            const int64_t gi = i0 + ii, gj = j0 + ii;
+            Xs[kk][ii] = (gi < M && gk < K) ? (double)X[gi * ldx + gk] : 0.0;
+            Ys[kk][ii] = (gj < N && gk < K) ? (double)Y[gj * ldy + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kG64K; ++kk) {
+            double xa[4], yb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) yb[b] = Ys[kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(xa[a], yb[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t i = i0 + ty + 16 * a;
+        if (i >= M) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int64_t j = j0 + tx + 16 * b;
+            if (j >= N) continue;
+            if (MODE == MODE_GRAM) {
+                double v = acc[a][b] * inv_s[i] * inv_s[j];
+                if (i == j) v = acc[a][b] != 0.0 ? 1.0 : 0.0;
+                out[i * ldo + j] = v;
+                if (tm != tn) out[j * ldo + i] = v;
+            } else {
+                out[j * ldo + i] = -acc[a][b] * inv_s[i];
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Host launchers
+// ----------------------------------------------------------------------------
+cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                            const void* B, int kc, int64_t ldb, double* s, double* inv_s,
+                            double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
+                            __nv_bfloat16* lo, int64_t ldk, cudaStream_t st) {
+    const int warps = 8;
+    const dim3 grid((unsigned)ceil_div(n, warps)), block(32 * warps);
+    const bool split = hi != nullptr;
+    if (dtype == ALN_DTYPE_F32) {
+        if (split)
+            k_colstats<float, true><<<grid, block, 0, st>>>((const float*)A, d, n, lda,
+                                                            (const float*)B, kc, ldb, s, inv_s,
+                                                            q64, ldq, flags, hi, lo, ldk);
+        else
+            k_colstats<float, false><<<grid, block, 0, st>>>((const float*)A, d, n, lda,
+                                                             (const float*)B, kc, ldb, s, inv_s,
+                                                             q64, ldq, flags, hi, lo, ldk);
+    } else {
+        if (split)
+            k_colstats<double, true><<<grid, block, 0, st>>>((const double*)A, d, n, lda,
+                                                             (const double*)B, kc, ldb, s,
+                                                             inv_s, q64, ldq, flags, hi, lo, ldk);
+        else
+            k_colstats<double, false><<<grid, block, 0, st>>>((const double*)A, d, n, lda,
+                                                              (const double*)B, kc, ldb, s,
+                                                              inv_s, q64, ldq, flags, hi, lo,
+                                                              ldk);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const void* X, int32_t dtype, int64_t rows, int64_t cols,
+                                int64_t ld, int* flags, cudaStream_t st) {
+    const int64_t total = rows * cols;
+    const int blocks = (int)std::min<int64_t>(ceil_div(total, 256), 4096);
+    if (dtype == ALN_DTYPE_F32)
+        k_check_finite<float><<<blocks, 256, 0, st>>>((const float*)X, rows, cols, ld, flags);
+    else
+        k_check_finite<double><<<blocks, 256, 0, st>>>((const double*)X, rows, cols, ld, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_denominators(const double* q64, int64_t n, int64_t ldq, int64_t k, double* den,
+                                cudaStream_t st) {
+    k_denominators<<<(unsigned)k, 256, 0, st>>>(q64, n, ldq, den);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st) {
+    const int64_t tm = ceil_div(n, kG64Tile);
+    const int64_t tiles = tm * (tm + 1) / 2;
+    if (dtype == ALN_DTYPE_F32)
+        k_atb64<float, float, MODE_GRAM><<<(unsigned)tiles, 256, 0, st>>>(
+            (const float*)A, lda, (const float*)A, lda, d, n, n, (int)tm, inv_s, Q, ldq);
+    else
+        k_atb64<double, double, MODE_GRAM><<<(unsigned)tiles, 256, 0, st>>>(
+            (const double*)A, lda, (const double*)A, lda, d, n, n, (int)tm, inv_s, Q, ldq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qvec64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
+                          const void* B, int64_t k, int64_t ldb, const double* inv_s, double* q64,
+                          int64_t ldq, cudaStream_t st) {
+    const int64_t tm = ceil_div(n, kG64Tile), tn = ceil_div(k, kG64Tile);
+    if (dtype == ALN_DTYPE_F32)
+        k_atb64<float, float, MODE_QVEC><<<(unsigned)(tm * tn), 256, 0, st>>>(
+            (const float*)A, lda, (const float*)B, ldb, d, n, k, (int)tm, inv_s, q64, ldq);
+    else
+        k_atb64<double, double, MODE_QVEC><<<(unsigned)(tm * tn), 256, 0, st>>>(
+            (const double*)A, lda, (const double*)B, ldb, d, n, k, (int)tm, inv_s, q64, ldq);
+    return cudaGetLastError();
+}
+
+}  // namespace aln

@@ -1,0 +1,283 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (written here, derived in the design notes):
+  * FP64 path: Q, q, s to 1e-12 relative; solutions |ΔF|/F* ≤ 1e-10 and
+    ‖Δx‖∞/‖x*‖∞ ≤ 1e-8 against the oracle's polished optimum.
+  * Split-BF16 Gram: |ΔQ_ij| ≤ 3·2⁻¹⁸ (split) + 3·d·2⁻²⁴ (FP32 accumulation
+    bound) + 2⁻²³ (scaling), mean |ΔQ| ≤ 5e-6; q and s are FP64 (1e-12).
+  * Mixed-precision solutions: FP64 relative KKT ≤ 1e-6 and
+    ‖Δx‖₂/‖x*‖₂ ≤ 1e-5.
+"""
+import numpy as np
+import pytest
+
+from oracle import nnls as O
+from paper_1502_01645_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aln():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_01645_gb300 import build_lib, aln as binding
+    build_lib.build()
+    binding.load()
+    return binding
+
+
+def _oracle_scaled(A, b):
+    H, h = O.nqp_from_nnls(A, b)
+    return O.antilopsided_scaling(H, h)
+
+
+def _split_bound(d):
+    return 3 * 2.0 ** -18 + 3 * d * 2.0 ** -24 + 2.0 ** -23
+
+
+# ----------------------------------------------------------------- Alg. 1 rows
+@pytest.mark.parametrize("d,n", [(300, 200), (129, 65), (50, 1), (40, 257)])
+def test_fp64_scaled_problem_matches_oracle(aln, d, n):
+    r = np.random.default_rng(d * 1000 + n)
+    A = np.asfortranarray(r.random((d, n)))
+    b = r.standard_normal(d)
+    with aln.Solver("fp64") as s:
+        s.prepare(A, b)
+        Q, q, sc = s.export()
+    Qo, qo, so = _oracle_scaled(A, b)
+    np.testing.assert_allclose(sc, so, rtol=1e-13)
+    np.testing.assert_allclose(Q, Qo, atol=1e-12)
+    np.testing.assert_allclose(q[0], qo, atol=1e-12 * np.abs(qo).max())
+    np.testing.assert_array_equal(np.diag(Q), 1.0)
+
+
+@pytest.mark.parametrize("d,n", [(700, 300), (64, 128), (1000, 129), (130, 1), (257, 400)])
+def test_split_bf16_gram_matches_oracle(aln, d, n):
+    """tcgen05 Gram: several 128-tiles plus a ragged tail in n and in d."""
+    r = np.random.default_rng(7 * d + n)
+    A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
+    A = np.asfortranarray(A64.astype(np.float32))
+    b = (A.astype(np.float64) @ r.random(n)).astype(np.float32)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, b)
+        Q, q, sc = s.export()
+    Qo, qo, so = _oracle_scaled(A, b)
+    np.testing.assert_allclose(sc, so, rtol=1e-13)
+    np.testing.assert_allclose(q[0], qo, atol=1e-12 * np.abs(qo).max())
+    err = np.abs(Q - Qo)
+    assert err.max() <= _split_bound(d), err.max()
+    assert err.mean() <= 5e-6
+    np.testing.assert_array_equal(Q, Q.T)
+    np.testing.assert_array_equal(np.diag(Q), 1.0)
+
+
+def test_split_gram_zero_column(aln):
+    r = np.random.default_rng(5)
+    A = np.asfortranarray(r.random((200, 150)).astype(np.float32))
+    A[:, 17] = 0.0
+    b = r.random(200).astype(np.float32)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, b)
+        Q, q, sc = s.export()
+    assert sc[17] == 1.0 and q[0, 17] == 0.0
+    assert np.all(Q[17] == 0.0) and np.all(Q[:, 17] == 0.0)
+
+
+# ----------------------------------------------------------------- Alg. 2 rows
+def _parity_fp64(x, A, b, x_star):
+    F = O.nnls_objective(A, b, x)
+    Fs = O.nnls_objective(A, b, x_star)
+    assert abs(F - Fs) / Fs <= 1e-10
+    assert np.abs(x - x_star).max() / np.abs(x_star).max() <= 1e-8
+
+
+def test_fp64_solve_uniform_small(aln):
+    """The plain FP64 configuration: A 1000×200 U[0,1], half of x_true zero."""
+    p = W.uniform_small()
+    A, b = p.A, p.B[0]
+    x_star, _, _, _ = O.reference_solution(A, b)
+    with aln.Solver("fp64") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-12)
+    assert info[0].status == aln.RHS_CONVERGED
+    assert info[0].rel_kkt <= 1e-12
+    _parity_fp64(X[0], A, b, x_star)
+    rel, F = O.kkt_residual(A, b, X[0])
+    assert rel <= 1e-12
+    np.testing.assert_allclose(info[0].objective, F, rtol=1e-12)
+
+
+@pytest.mark.parametrize("d,n", [(40, 1), (60, 2), (90, 31), (100, 33), (300, 129), (600, 257)])
+def test_fp64_solve_ragged_sizes(aln, d, n):
+    r = np.random.default_rng(d + 17 * n)
+    A = np.asfortranarray(r.random((d, n)))
+    xt = np.where(r.random(n) < 0.5, 0.0, r.random(n))
+    b = A @ xt + 0.01 * r.standard_normal(d)
+    x_star, _, _, _ = O.reference_solution(A, b)
+    with aln.Solver("fp64") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-12)
+    assert info[0].rel_kkt <= 1e-12
+    _parity_fp64(X[0], A, b, x_star)
+
+
+def _mixed_gate(A, b, x, x_star):
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    rel, _ = O.kkt_residual(A64, b64, x)
+    assert rel <= 1e-6, rel
+    assert np.linalg.norm(x - x_star) / np.linalg.norm(x_star) <= 1e-5
+
+
+def test_mixed_solve_lopsided(aln):
+    """Lopsided single-RHS configuration at reduced size (4000×1000)."""
+    p = W.lopsided_single(d=4000, n=1000)
+    A, b = p.A, p.B[0]
+    x_star, _, _, _ = O.reference_solution(A.astype(np.float64), b.astype(np.float64))
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-10)
+        Xb, infob = s.solve(tol=1e-6)
+    assert infob[0].rel_kkt <= 1e-6
+    rel_b, _ = O.kkt_residual(A.astype(np.float64), b.astype(np.float64), Xb[0])
+    assert rel_b <= 1e-6
+    _mixed_gate(A, b, X[0], x_star)
+
+
+@pytest.mark.parametrize("d,n", [(70, 1), (80, 3), (150, 65), (500, 129), (900, 300)])
+def test_mixed_solve_ragged_sizes(aln, d, n):
+    r = np.random.default_rng(3 * d + n)
+    A = np.asfortranarray(r.random((d, n)).astype(np.float32))
+    xt = np.where(r.random(n) < 0.6, 0.0, r.random(n))
+    b = (A.astype(np.float64) @ xt + 0.01 * r.standard_normal(d)).astype(np.float32)
+    x_star, _, _, _ = O.reference_solution(A.astype(np.float64), b.astype(np.float64))
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-10)
+    _mixed_gate(A, b, X[0], x_star)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_zero_solution_when_Atb_nonpositive(aln, prec):
+    r = np.random.default_rng(12)
+    A = np.asfortranarray(r.random((30, 8)))
+    b = -r.random(30)
+    if prec == "split_bf16":
+        A, b = np.asfortranarray(A.astype(np.float32)), b.astype(np.float32)
+    with aln.Solver(prec) as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-10)
+    assert info[0].iters == 0 and info[0].status == aln.RHS_EMPTY_PASSIVE
+    assert np.all(X[0] == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split_bf16"])
+def test_zero_column_solution(aln, prec):
+    r = np.random.default_rng(13)
+    A = r.random((120, 40))
+    A[:, 3] = 0.0
+    b = A @ r.random(40) + 0.01 * r.standard_normal(120)
+    dt = np.float64 if prec == "fp64" else np.float32
+    A, b = np.asfortranarray(A.astype(dt)), b.astype(dt)
+    x_star, _, _, _ = O.reference_solution(A.astype(np.float64), b.astype(np.float64))
+    with aln.Solver(prec) as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-10)
+    assert X[0, 3] == 0.0
+    assert np.linalg.norm(X[0] - x_star) / np.linalg.norm(x_star) <= 1e-5
+
+
+def test_warm_start_at_optimum_takes_no_iterations(aln):
+    p = W.uniform_small(d=300, n=60, seed=77)
+    A, b = p.A, p.B[0]
+    x_star, _, _, _ = O.reference_solution(A, b)
+    with aln.Solver("fp64") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-9, X0=x_star[None, :].copy())
+    assert info[0].iters <= 2
+    _parity_fp64(X[0], A, b, x_star)
+
+
+def test_max_iter_is_reported_not_raised(aln):
+    p = W.uniform_small()
+    with aln.Solver("fp64", max_refine=0) as s:
+        s.prepare(p.A, p.B[0])
+        X, info = s.solve(tol=1e-14, max_iter=5)
+    assert info[0].status == aln.RHS_MAXITER
+    assert info[0].iters == 5
+    assert np.all(X[0] >= 0.0)
+
+
+def test_device_and_host_pointers_agree(aln):
+    import torch
+    p = W.uniform_small(d=400, n=100, seed=9)
+    with aln.Solver("fp64") as s:
+        s.prepare(p.A, p.B[0])
+        Xh, ih = s.solve(tol=1e-12)
+    At = torch.from_numpy(np.ascontiguousarray(p.A.T)).cuda().t()   # column-major view
+    Bt = torch.from_numpy(p.B).cuda()
+    Xd = torch.zeros((1, 100), dtype=torch.float64, device="cuda")
+    with aln.Solver("fp64") as s:
+        s.prepare(At, Bt)
+        s.solve(tol=1e-12, X=Xd)
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(Xd.cpu().numpy(), Xh)
+
+
+def test_errors(aln):
+    r = np.random.default_rng(1)
+    A = np.asfortranarray(r.random((20, 5)))
+    b = r.random(20)
+    with aln.Solver("fp64") as s:
+        with pytest.raises(aln.AlnError) as e:
+            s.solve()
+        assert e.value.code == aln.ERR_NOT_PREPARED
+        A2 = A.copy(order="F")
+        A2[3, 2] = np.nan
+        with pytest.raises(aln.AlnError) as e:
+            s.prepare(A2, b)
+        assert e.value.code == aln.ERR_NONFINITE
+        b2 = b.copy()
+        b2[0] = np.inf
+        with pytest.raises(aln.AlnError) as e:
+            s.prepare(A, b2)
+        assert e.value.code == aln.ERR_NONFINITE
+        s.prepare(A, b)
+        with pytest.raises(aln.AlnError) as e:
+            s.solve(tol=-1.0)
+        assert e.value.code == aln.ERR_INVALID_ARG
+        X0 = np.full((1, 5), np.nan)
+        with pytest.raises(aln.AlnError) as e:
+            s.solve(X0=X0)
+        assert e.value.code == aln.ERR_NONFINITE
+
+
+def test_kkt_entry_point_matches_oracle(aln):
+    p = W.lopsided_single(d=2000, n=500, seed=4)
+    A, b = p.A, p.B[0]
+    r = np.random.default_rng(2)
+    X = np.where(r.random((3, 500)) < 0.5, 0.0, r.random((3, 500)))
+    X[2] = 0.0
+    B = np.stack([b, b * 0.5, b]).astype(np.float32)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, B)
+        rel, F = s.kkt(X)
+    for c in range(3):
+        ro, Fo = O.kkt_residual(A.astype(np.float64), B[c].astype(np.float64), X[c])
+        np.testing.assert_allclose(rel[c], ro, rtol=1e-10)
+        np.testing.assert_allclose(F[c], Fo, rtol=1e-10)
+    np.testing.assert_allclose(rel[2], 1.0, rtol=1e-12)
+
+
+def test_multiple_rhs_each_match_oracle(aln):
+    p = W.shared_multi_rhs(d=1500, n=300, k=6, seed=33)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.A, p.B)
+        X, info = s.solve(tol=1e-10)
+    A64 = p.A.astype(np.float64)
+    for c in range(p.k):
+        b64 = p.B[c].astype(np.float64)
+        x_star, _, _, _ = O.reference_solution(A64, b64)
+        _mixed_gate(p.A, p.B[c], X[c], x_star)
