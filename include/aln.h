@@ -86,8 +86,8 @@ typedef struct aln_options {
     int32_t precision;    /* aln_precision */
     int32_t max_refine;   /* FP64 refinement rounds after the first FP32
                              convergence (SPLIT_BF16 only); default 8 */
-    int32_t graph_chunk;  /* Alg. 2 iterations per captured CUDA graph launch;
-                             0 selects a size-dependent default */
+    int32_t persist_blocks; /* blocks of the persistent Alg. 2 kernel; 0 = one
+                             per SM (capped by co-residency and work items) */
     int32_t row_groups;   /* row groups of the single-RHS matvec; 0 = auto */
     int32_t stagnation;   /* stop an inner run after this many iterations without a
                              new smallest ‖ḡ‖² (§5 stop rule); 0 = default 100 */
@@ -106,7 +106,7 @@ typedef struct aln_solve_info {
 typedef struct aln_ctx aln_ctx;
 
 /* Fill *opt with the defaults (precision SPLIT_BF16, max_refine 8, automatic
- * graph chunk and row groups, stagnation window 100). */
+ * persistent grid and row groups, stagnation window 100). */
 void aln_default_options(aln_options* opt);
 
 /* Create a context on the current CUDA device.  `stream` is a cudaStream_t
@@ -166,6 +166,11 @@ typedef struct aln_stats {
     double kkt_ms;           /*   of which the FP64 KKT passes */
     int64_t kernel_launches; /* kernels this context launched since creation */
     int64_t iterations;      /* Alg. 2 iterations in the last aln_solve */
+    double iterate_ms;       /* of solve_ms: the persistent Alg. 2 kernel(s) */
+    int64_t passive_rows;    /* Σ_k |P_k| over those iterations (rows of Q read for Qḡ) */
+    int64_t clipped_rows;    /* Σ_k |C_k| (rows of Q read for the clipped correction) */
+    int32_t persist_blocks;  /* grid of the persistent kernel */
+    int32_t reserved;
 } aln_stats;
 
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */

@@ -33,7 +33,7 @@ EXPORTS = (
 
 class AlnOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_refine", ctypes.c_int32),
-                ("graph_chunk", ctypes.c_int32), ("row_groups", ctypes.c_int32),
+                ("persist_blocks", ctypes.c_int32), ("row_groups", ctypes.c_int32),
                 ("stagnation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
@@ -46,7 +46,10 @@ class AlnSolveInfo(ctypes.Structure):
 class AlnStats(ctypes.Structure):
     _fields_ = [("prepare_ms", ctypes.c_double), ("gram_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("kkt_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("iterate_ms", ctypes.c_double), ("passive_rows", ctypes.c_int64),
+                ("clipped_rows", ctypes.c_int64), ("persist_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class AlnError(RuntimeError):
@@ -274,6 +277,8 @@ def _col_major_ld(A) -> int:
 
 
 def _row_major_ld(B) -> int:
+    if B.size == 0:
+        return max(1, B.shape[-1])
     if isinstance(B, np.ndarray):
         s0, s1 = B.strides[0] // B.itemsize, B.strides[1] // B.itemsize
     else:

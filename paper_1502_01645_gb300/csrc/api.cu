@@ -59,11 +59,6 @@ aln_status ensure(void** p, size_t* cap, size_t bytes) {
 size_t elt(int32_t dtype) { return dtype == ALN_DTYPE_F64 ? 8 : 4; }
 bool fp64(const aln_ctx* c) { return c->opt.precision == ALN_PREC_FP64; }
 
-void destroy_graph(aln_ctx* c) {
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-}
-
 // Host buffers → device: owned copy; device buffers are used in place.
 aln_status resolve_input(aln_ctx* c, const void* src, int64_t rows, int64_t cols, int64_t ld,
                          size_t esz, void** copy, size_t* cap, const void** out) {
@@ -92,9 +87,26 @@ aln_status alloc_workspace(aln_ctx* c) {
     }
     c->R = R;
     c->nb = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
+
+    // Persistent kernel: column tiles × row groups; about two work items per
+    // block, at least 32 rows per group; one block per SM (or the option).
+    c->p_CT = (int)col_tiles;
+    int pR = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(2 * (int64_t)c->num_sms, col_tiles),
+                                                         ceil_div(n, 32)));
+    c->p_R = std::min(pR, 64);
+    const int maxG = fp64(c) ? persist_max_blocks<double>(c->num_sms)
+                             : persist_max_blocks<float>(c->num_sms);
+    if (maxG <= 0) return ALN_ERR_CUDA;
+    int G = c->opt.persist_blocks > 0 ? c->opt.persist_blocks : c->num_sms;
+    G = (int)std::min<int64_t>({(int64_t)G, (int64_t)maxG, (int64_t)c->p_CT * c->p_R});
+    c->p_G = std::max(G, 1);
+    const int64_t RP = std::max<int64_t>(R, c->p_R);
+
     const size_t vec = (size_t)ldq * T;
-    size_t bytes = 6 * vec + (size_t)R * vec + 2 * (size_t)c->nb * 8 + (size_t)c->nb * 4 + 256;
-    bytes = round_up(bytes, 256);
+    const size_t ct = (size_t)c->p_CT;
+    size_t bytes = 6 * vec + (size_t)RP * vec + 2 * (size_t)c->nb * 8 + (size_t)c->nb * 4 + 256 +
+                   4 * round_up(ct * 8, 256) + 256 + 256;
+    bytes = round_up(bytes, 256) + 16 * 256;
     ALN_CHECK(ensure(&c->iter_pool, &c->iter_bytes, bytes + 1024));
     uint8_t* p = (uint8_t*)c->iter_pool;
     auto take = [&](size_t b) {
@@ -108,20 +120,26 @@ aln_status alloc_workspace(aln_ctx* c) {
     c->gb = take(vec);
     c->w = take(vec);
     c->e = take(vec);
-    c->part = take((size_t)R * vec);
+    c->part = take((size_t)RP * vec);
     c->gpart = (double*)take((size_t)c->nb * 8);
     c->kpart = (double*)take((size_t)c->nb * 8);
     c->cpart = (int*)take((size_t)c->nb * 4);
     c->st = (IterState*)take(sizeof(IterState));
+    c->p_gpart = (double*)take(ct * 8);
+    c->p_kpart = (double*)take(ct * 8);
+    c->p_cpart = (int*)take(ct * 8);
+    c->p_clip = (int*)take(ct * 8);
+    c->p_ticket = (unsigned int*)take(ct * 8);
+    c->p_sync = take(persist_sync_bytes());
     ALN_TRY(cudaMemsetAsync(c->iter_pool, 0, c->iter_bytes, c->stream));
 
     // KKT: x64 (ldq), g64 (ldq), r64 (d), rpart (CG·d), parts, out
-    const int64_t row_blocks = ceil_div(d, 256);
+    const int64_t row_blocks = ceil_div(d, 1024);  // k_kkt_ax: 4 rows × 256 threads
     int CG = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(4 * (int64_t)c->num_sms, row_blocks),
                                                          ceil_div(n, 32)));
     CG = std::min(CG, 64);
     c->CG = CG;
-    const int64_t ng = ceil_div(n, 8);
+    const int64_t ng = n;  // one ḡ² partial per column
     size_t kb = 2 * (size_t)ldq * 8 + (size_t)d * 8 + (size_t)CG * d * 8 + (512 + ng) * 8 + 64;
     kb = round_up(kb, 256) + 2048;
     ALN_CHECK(ensure(&c->kkt_pool, &c->kkt_bytes, kb));
@@ -136,42 +154,27 @@ aln_status alloc_workspace(aln_ctx* c) {
     return ALN_OK;
 }
 
-aln_status build_graph(aln_ctx* c) {
-    destroy_graph(c);
-    cudaGraph_t g = nullptr;
-    ALN_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = fp64(c) ? launch_iter_chunk<double>(c, c->graph_chunk)
-                            : launch_iter_chunk<float>(c, c->graph_chunk);
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        return ALN_ERR_CUDA;
-    }
-    e = cudaGraphInstantiate(&c->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        c->graph = nullptr;
-        return ALN_ERR_CUDA;
-    }
+// One launch of the persistent Alg. 2 kernel: it loops on the device until a
+// stop rule fires (the state's eps, max_iter and stagnation window were set
+// by the set-up kernels) and leaves the outcome in the iteration state.  The
+// barrier words and tile tickets are cleared first, so a previous timeout
+// cannot leak into this run.
+aln_status run_until_done(aln_ctx* c) {
+    ALN_TRY(cudaMemsetAsync(c->p_sync, 0, persist_sync_bytes(), c->stream));
+    ALN_TRY(cudaMemsetAsync(c->p_ticket, 0, (size_t)c->p_CT * sizeof(unsigned int), c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[6], c->stream));
+    ALN_TRY(fp64(c) ? launch_alg2_persist<double>(c) : launch_alg2_persist<float>(c));
+    ALN_TRY(cudaEventRecord(c->ev[7], c->stream));
+    c->launches += 1;
+    ALN_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(IterState), cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess) c->stats.iterate_ms += ms;
+    if (c->st_host->status < 0 || !c->st_host->done) return ALN_ERR_TIMEOUT;
+    c->stats.passive_rows += c->st_host->sum_passive;
+    c->stats.clipped_rows += c->st_host->sum_clip;
     return ALN_OK;
-}
-
-// Run the captured chunk until the device state says the loop has stopped.
-// Every launch either advances the iteration counter by graph_chunk or stops
-// the loop, so max_iter bounds the number of launches; exceeding that bound
-// means the device state is inconsistent and is reported as a timeout.
-aln_status run_until_done(aln_ctx* c, int max_iter) {
-    const int64_t bound = max_iter / c->graph_chunk + 3;
-    for (int64_t l = 0; l < bound; ++l) {
-        ALN_TRY(cudaGraphLaunch(c->graph, c->stream));
-        c->launches += 5LL * c->graph_chunk;
-        ALN_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(IterState), cudaMemcpyDeviceToHost,
-                                c->stream));
-        ALN_TRY(cudaStreamSynchronize(c->stream));
-        if (c->st_host->done) return ALN_OK;
-    }
-    return ALN_ERR_TIMEOUT;
 }
 
 aln_status kkt_eval(aln_ctx* c, int64_t rhs, const double* x64dev, double* rel, double* F) {
@@ -213,7 +216,7 @@ void aln_default_options(aln_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = ALN_PREC_SPLIT_BF16;
     opt->max_refine = 8;
-    opt->graph_chunk = 0;
+    opt->persist_blocks = 0;
     opt->row_groups = 0;
     opt->stagnation = 100;
 }
@@ -242,7 +245,7 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (opt) o = *opt;
     if (o.precision != ALN_PREC_FP64 && o.precision != ALN_PREC_SPLIT_BF16)
         return ALN_ERR_INVALID_ARG;
-    if (o.max_refine < 0 || o.graph_chunk < 0 || o.row_groups < 0 || o.stagnation < 0)
+    if (o.max_refine < 0 || o.persist_blocks < 0 || o.row_groups < 0 || o.stagnation < 0)
         return ALN_ERR_INVALID_ARG;
     if (o.stagnation == 0) o.stagnation = 100;
     aln_ctx* c = new (std::nothrow) aln_ctx();
@@ -267,7 +270,7 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
         c->stream = (cudaStream_t)stream;
     } else {
         // A private blocking stream: ordered after legacy-stream work and, unlike
-        // the legacy stream itself, usable for graph capture.
+        // the legacy stream itself, usable for stream capture by callers.
         if (cudaStreamCreate(&c->own_stream) != cudaSuccess) {
             delete c;
             return ALN_ERR_CUDA;
@@ -298,7 +301,6 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
 void aln_destroy(aln_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    destroy_graph(c);
     void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -317,7 +319,6 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
     if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
     c->prepared = 0;
-    destroy_graph(c);
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     ALN_CHECK(resolve_input(c, A, d, n, lda, esz, &c->A_copy, &c->A_copy_bytes, &c->A));
@@ -410,10 +411,6 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     if (c->flags_host[1]) return ALN_ERR_TIMEOUT;
     if (c->flags_host[0]) return ALN_ERR_NONFINITE;
 
-    int chunk = c->opt.graph_chunk;
-    if (chunk <= 0) chunk = n <= 2048 ? 32 : 16;
-    c->graph_chunk = chunk;
-    ALN_CHECK(build_graph(c));
     c->prepared = 1;
     return ALN_OK;
 }
@@ -428,7 +425,8 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     const bool x_dev = is_device_ptr(X);
     const bool x0_dev = X0 ? is_device_ptr(X0) : false;
     const bool f64 = fp64(c);
-    c->stats.solve_ms = c->stats.kkt_ms = 0.0;
+    c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
+    c->stats.passive_rows = c->stats.clipped_rows = 0;
     c->stats.iterations = 0;
     ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
     // Inner runs stop a little below tol so that the FP64 check usually passes
@@ -464,7 +462,7 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
                     : launch_iter_setup<float>(c, q64, x0, eps_of(tol * first_factor), max_iter));
         c->launches += x0 ? 4 : 3;
         for (;;) {
-            ALN_CHECK(run_until_done(c, max_iter - total));
+            ALN_CHECK(run_until_done(c));
             total += c->st_host->iter;
             const int inner = c->st_host->status;
             ALN_TRY(f64 ? launch_unscale<double>(c, c->x64) : launch_unscale<float>(c, c->x64));
@@ -519,6 +517,7 @@ aln_status aln_get_stats(aln_ctx* c, aln_stats* out) {
     if (!c || !out) return ALN_ERR_INVALID_ARG;
     *out = c->stats;
     out->kernel_launches = c->launches;
+    out->persist_blocks = c->p_G;
     return ALN_OK;
 }
 

@@ -13,7 +13,7 @@ namespace aln {
 constexpr int kWarp = 32;
 
 // Device-resident state of one Alg. 2 run on one right-hand side.  Written by
-// the iteration kernels, read back by the host after each graph launch.
+// the iteration kernels, read back by the host after each persistent launch.
 struct IterState {
     double eps;       // stop threshold on ‖ḡ‖² (absolute)
     double gbar2;     // ‖ḡ‖² when the loop stopped
@@ -27,6 +27,8 @@ struct IterState {
     double best_g2;   // smallest ‖ḡ‖² seen in this run
     int32_t best_iter;
     int32_t pad;
+    int64_t sum_passive;  // Σ_k |P_k|: rows of Q read for w = Qḡ
+    int64_t sum_clip;     // Σ_k |C_k|: rows read for the clipped correction
 };
 
 template <typename T> struct Vec16;
@@ -84,6 +86,28 @@ __device__ __forceinline__ int warp_sum_array_i(const int* __restrict__ p, int c
     int v = 0;
     for (int i = lane; i < count; i += 32) v += p[i];
     return warp_sum_i(v);
+}
+
+// Four consecutive elements at a 16-byte aligned address, widened to FP64.
+__device__ __forceinline__ void load4(const float* p, double* o) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* o) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
+// True when base + k·ld is 16-byte aligned for every k (vector loads allowed).
+inline bool aligned16(const void* base, int64_t ld, size_t esz) {
+    return ((uintptr_t)base % 16 == 0) && ((ld * (int64_t)esz) % 16 == 0);
 }
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -168,9 +192,14 @@ struct aln_ctx {
     void* kkt_pool = nullptr;
     size_t kkt_bytes = 0;
 
-    // captured iteration graph
-    cudaGraphExec_t graph = nullptr;
-    int graph_chunk = 0;
+    // persistent Alg. 2 kernel geometry and its per-tile partials
+    int p_CT = 0, p_R = 0, p_G = 0;
+    double* p_gpart = nullptr;
+    int* p_cpart = nullptr;
+    double* p_kpart = nullptr;
+    int* p_clip = nullptr;
+    unsigned int* p_ticket = nullptr;
+    void* p_sync = nullptr;
 
     // statistics (aln_get_stats)
     cudaEvent_t ev[8] = {};

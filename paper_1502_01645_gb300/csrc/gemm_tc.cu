@@ -280,7 +280,20 @@ __global__ void __launch_bounds__(128, 1)
                 if (diag && row == n0 + c0 + t) o[t] = v[t] != 0.0f ? 1.0f : 0.0f;
             }
             const int64_t j0 = n0 + c0;
-            if (rv) {
+            if (diag) {
+                // Diagonal tile: keep the lower triangle and mirror it, so Q is
+                // exactly symmetric (the two halves round differently).
+                if (rv) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) {
+                        const int64_t j = j0 + t;
+                        if (c0 + t < cols && j <= row) {
+                            p.Q[row * p.ldq + j] = o[t];
+                            p.Q[j * p.ldq + row] = o[t];
+                        }
+                    }
+                }
+            } else if (rv) {
                 float* dst = p.Q + row * p.ldq + j0;
                 if (c0 + 16 <= cols) {
 #pragma unroll
@@ -290,8 +303,6 @@ __global__ void __launch_bounds__(128, 1)
                 } else {
                     for (int t = 0; t < cols - c0; ++t) dst[t] = o[t];
                 }
-            }
-            if (!diag && rv) {
 #pragma unroll
                 for (int t = 0; t < 16; ++t)
                     if (c0 + t < cols) p.Q[(j0 + t) * p.ldq + row] = o[t];

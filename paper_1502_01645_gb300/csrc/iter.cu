@@ -1,24 +1,11 @@
-// Alg. 2 (§3) — gradient method with exact line search — on one right-hand
-// side, as a chain of bandwidth-bound kernels captured in a CUDA graph.
+// Set-up kernels of Alg. 2 (§3) on one right-hand side: the start point,
+// the initial gradient (g = q at y = 0, or g = Qy0 + q with a start point), the
+// gradient refresh from the FP64 KKT pass, and the final x = y/s (Alg. 1).
+// The iteration itself runs in the persistent kernel (persist.cu).
 //
-// One iteration, in the paper's order:
-//   ḡ = g on P(y) = {y_i > 0 or g_i < 0}, γ = ‖ḡ‖²       (k_finish of the previous step)
-//   stop if P = ∅ or γ < ε                                (k_rowmv, check_conv = 1)
-//   w = Qḡ over the passive rows only                     (k_rowmv)
-//   κ = ḡᵀw, α = γ/κ                                      (k_reduce_w, k_update)
-//   y⁺ = [y − αḡ]₊                                        (k_update)
-//   g ← g + Q(y⁺ − y)                                     (k_update, k_rowmv(e), k_finish)
-//
-// The gradient update uses y⁺ − y = −αḡ + e, where e is non-zero only on the
-// clipped set C = {i : y_i − αḡ_i < 0} (e_i = αḡ_i − y_i there).  Hence
-// Q(y⁺ − y) = −αw + Q_{:,C} e_C: the product Qḡ already formed for the step
-// size is reused and only the clipped rows of Q are read a second time.  This
-// is exact algebra; the paper counts a second full O(n·S(n)) product (§4.2).
-//
-// Q is symmetric, so Qv = Σ_j v_j Q[j, :]: the matvec walks the rows j with
-// v_j ≠ 0, each a contiguous, coalesced run of ldq elements.  Rows are split
-// into R groups; each (column tile, row group) block writes a partial that
-// k_reduce_w / k_finish sum in a fixed order (deterministic results).
+// Q is symmetric, so Qv = Σ_j v_j Q[j, :]: k_rowmv walks the rows j with
+// v_j ≠ 0, each a contiguous, coalesced run of ldq elements, and writes one
+// partial per row group that k_finish sums in a fixed order.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -136,92 +123,6 @@ __global__ void __launch_bounds__(kMvWarps * 32) k_rowmv(
     }
 }
 
-// w = Σ_r part[r]; κ partial = ḡᵀw (FP64 accumulation).
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) k_reduce_w(int n, int64_t ldq,
-                                                          const T* __restrict__ part, int R,
-                                                          const T* __restrict__ gb,
-                                                          T* __restrict__ w,
-                                                          double* __restrict__ kpart,
-                                                          const IterState* __restrict__ st) {
-    __shared__ double scratch[32];
-    if (st->done) return;
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        T wi = T(0);
-        for (int r = 0; r < R; ++r) wi += part[(int64_t)r * ldq + i];
-        w[i] = wi;
-        acc += (double)gb[i] * (double)wi;
-    }
-    acc = block_sum(acc, scratch);
-    if (threadIdx.x == 0) kpart[blockIdx.x] = acc;
-}
-
-// α = γ/κ (exact line search), y⁺ = [y − αḡ]₊, e on the clipped set,
-// g ← g − αw (the clipped correction Q e is added by k_finish).
-template <typename T>
-__global__ void __launch_bounds__(kVecThreads) k_update(int n, T* __restrict__ y,
-                                                        T* __restrict__ g,
-                                                        const T* __restrict__ gb,
-                                                        const T* __restrict__ w,
-                                                        T* __restrict__ e,
-                                                        const double* __restrict__ kpart,
-                                                        const double* __restrict__ gpart, int nb,
-                                                        IterState* __restrict__ st) {
-    __shared__ double s_alpha;
-    __shared__ int s_stop;
-    if (st->done) return;
-    if (threadIdx.x < 32) {
-        const double gam = warp_sum_array(gpart, nb);
-        const double kap = warp_sum_array(kpart, nb);
-        if (threadIdx.x == 0) {
-            int stop = 0, status = 0;
-            if (!isfinite(kap)) {
-                stop = 1;
-                status = ALN_RHS_NONFINITE;
-            } else if (kap <= 0.0) {
-                stop = 1;
-                status = ALN_RHS_CURVATURE;
-            }
-            s_stop = stop;
-            s_alpha = stop ? 0.0 : gam / kap;
-            if (blockIdx.x == 0) {
-                if (stop) {
-                    st->done = 1;
-                    st->status = status;
-                    st->gbar2 = gam;
-                } else {
-                    // stagnation bookkeeping (read by the next k_rowmv only)
-                    if (gam < st->best_g2) {
-                        st->best_g2 = gam;
-                        st->best_iter = st->iter;
-                    }
-                    st->iter += 1;
-                    st->alpha = gam / kap;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (s_stop) return;
-    const T a = (T)s_alpha;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const T yi = y[i];
-        const T step = a * gb[i];
-        T yn = yi - step;
-        T ei = T(0);
-        if (yn < T(0)) {
-            ei = step - yi;
-            yn = T(0);
-        }
-        y[i] = yn;
-        e[i] = ei;
-        g[i] = g[i] - a * w[i];
-    }
-}
-
 // g_i = base_i + Σ_r part[r][i], where base is q (init), the FP64 gradient from
 // the KKT pass (refinement), or g itself; then ḡ = g on P(y), and the block
 // partials of ‖ḡ‖² and |P| for the next stop test.
@@ -322,25 +223,6 @@ cudaError_t launch_iter_refresh_from_g64(aln_ctx* c, double eps, int max_iter) {
 }
 
 template <typename T>
-cudaError_t launch_iter_chunk(aln_ctx* c, int iters) {
-    const int n = (int)c->n;
-    for (int it = 0; it < iters; ++it) {
-        rowmv_launch<T>(c, (const T*)c->gb, 1);
-        k_reduce_w<T><<<c->nb, kVecThreads, 0, c->stream>>>(n, c->ldq, (const T*)c->part, c->R,
-                                                           (const T*)c->gb, (T*)c->w, c->kpart,
-                                                           c->st);
-        k_update<T><<<c->nb, kVecThreads, 0, c->stream>>>(n, (T*)c->y, (T*)c->g, (const T*)c->gb,
-                                                         (const T*)c->w, (T*)c->e, c->kpart,
-                                                         c->gpart, c->nb, c->st);
-        rowmv_launch<T>(c, (const T*)c->e, 0);
-        k_finish<T><<<c->nb, kVecThreads, 0, c->stream>>>(
-            n, c->ldq, (const T*)c->part, c->R, (const T*)c->qv, nullptr, 0, (const T*)c->y,
-            (T*)c->g, (T*)c->gb, c->gpart, c->cpart, c->st, 1);
-    }
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_unscale(aln_ctx* c, double* x64) {
     k_unscale<T><<<(unsigned)std::min<int64_t>(ceil_div(c->n, kVecThreads), 1024), kVecThreads, 0,
                    c->stream>>>((int)c->n, (const T*)c->y, c->s, x64);
@@ -350,8 +232,6 @@ cudaError_t launch_unscale(aln_ctx* c, double* x64) {
 template cudaError_t launch_iter_setup<float>(aln_ctx*, const double*, const double*, double, int);
 template cudaError_t launch_iter_setup<double>(aln_ctx*, const double*, const double*, double,
                                                int);
-template cudaError_t launch_iter_chunk<float>(aln_ctx*, int);
-template cudaError_t launch_iter_chunk<double>(aln_ctx*, int);
 template cudaError_t launch_iter_refresh_from_g64<float>(aln_ctx*, double, int);
 template cudaError_t launch_iter_refresh_from_g64<double>(aln_ctx*, double, int);
 template cudaError_t launch_unscale<float>(aln_ctx*, double*);

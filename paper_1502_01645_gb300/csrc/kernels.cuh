@@ -37,12 +37,17 @@ template <typename T>
 cudaError_t launch_iter_setup(aln_ctx* c, const double* q64, const double* x0, double eps,
                               int max_iter);
 template <typename T>
-cudaError_t launch_iter_chunk(aln_ctx* c, int iters);
-template <typename T>
 cudaError_t launch_iter_refresh_from_g64(aln_ctx* c, double eps, int max_iter);
 template <typename T>
 cudaError_t launch_unscale(aln_ctx* c, double* x64);
 cudaError_t launch_state_reset(aln_ctx* c, double eps, int max_iter);
+
+// persist.cu — the whole Alg. 2 loop as one cooperative persistent kernel
+template <typename T>
+cudaError_t launch_alg2_persist(aln_ctx* c);
+template <typename T>
+int persist_max_blocks(int num_sms);
+size_t persist_sync_bytes();
 
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);

@@ -3,44 +3,65 @@
 //   Eq. NQPQ),  ḡ = g on P(y = s·x) (§3),  rel = ‖ḡ‖ / ‖min(q, 0)‖,  F = ½‖r‖².
 // A is read in its input precision and every product is accumulated in FP64,
 // so the residual does not inherit the error of the FP32 / split-BF16 Q.
+// Both passes are HBM-bound; with 16-byte aligned columns they move four
+// elements per load so that enough bytes are in flight per SM.
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace aln {
 
 constexpr int kKktThreads = 256;
+constexpr int kKktRows = 4 * kKktThreads;  // rows of r per block in k_kkt_ax
 
-// rpart[cg][t] = Σ_{i ∈ column group cg, x_i ≠ 0} A_ti x_i  (each thread one row
-// t, consecutive threads consecutive rows: coalesced column reads).
-template <typename TA>
+// rpart[cg][t] = Σ_{i ∈ column group cg, x_i ≠ 0} A_ti x_i.  Each thread owns
+// four consecutive rows; columns with x_i = 0 are skipped (x is sparse at the
+// optimum, so only the support of x is read).
+template <typename TA, bool VEC>
 __global__ void __launch_bounds__(kKktThreads) k_kkt_ax(const TA* __restrict__ A, int64_t d,
                                                         int64_t n, int64_t lda,
                                                         const double* __restrict__ x,
                                                         int64_t cols_per_group,
                                                         double* __restrict__ rpart) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t0 = ((int64_t)blockIdx.x * kKktThreads + threadIdx.x) * 4;
     const int64_t i0 = (int64_t)blockIdx.y * cols_per_group;
     const int64_t i1 = min(n, i0 + cols_per_group);
-    double acc = 0.0;
-    if (t < d) {
-        int64_t i = i0;
-        for (; i + 4 <= i1; i += 4) {
-            const double x0 = x[i], x1 = x[i + 1], x2 = x[i + 2], x3 = x[i + 3];
-            const double a0 = x0 != 0.0 ? (double)A[i * lda + t] : 0.0;
-            const double a1 = x1 != 0.0 ? (double)A[(i + 1) * lda + t] : 0.0;
-            const double a2 = x2 != 0.0 ? (double)A[(i + 2) * lda + t] : 0.0;
-            const double a3 = x3 != 0.0 ? (double)A[(i + 3) * lda + t] : 0.0;
-            acc = fma(a0, x0, acc);
-            acc = fma(a1, x1, acc);
-            acc = fma(a2, x2, acc);
-            acc = fma(a3, x3, acc);
+    if (t0 >= d) return;
+    const bool full = VEC && t0 + 4 <= d;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int64_t i = i0;
+    for (; i + 4 <= i1; i += 4) {
+        double xi[4], a[4][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xi[c] = x[i + c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const TA* p = A + (i + c) * lda + t0;
+            if (xi[c] == 0.0) {
+                a[c][0] = a[c][1] = a[c][2] = a[c][3] = 0.0;
+            } else if (full) {
+                load4(p, a[c]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) a[c][u] = t0 + u < d ? (double)p[u] : 0.0;
+            }
         }
-        for (; i < i1; ++i) {
-            const double xi = x[i];
-            if (xi != 0.0) acc = fma((double)A[i * lda + t], xi, acc);
-        }
-        rpart[(int64_t)blockIdx.y * d + t] = acc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(a[c][u], xi[c], acc[u]);
     }
+    for (; i < i1; ++i) {
+        const double xi = x[i];
+        if (xi == 0.0) continue;
+        const TA* p = A + i * lda + t0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t0 + u < d) acc[u] = fma((double)p[u], xi, acc[u]);
+    }
+    double* out = rpart + (int64_t)blockIdx.y * d + t0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (t0 + u < d) out[u] = acc[u];
 }
 
 // r_t = Σ_cg rpart[cg][t] − b_t ; block partial of ‖r‖².
@@ -56,15 +77,15 @@ __global__ void __launch_bounds__(kKktThreads) k_kkt_r(int64_t d, const double* 
         double v = -(double)b[t];
         for (int cg = 0; cg < CG; ++cg) v += rpart[(int64_t)cg * d + t];
         r[t] = v;
-        acc += v * v;
+        acc = fma(v, v, acc);
     }
     acc = block_sum(acc, scratch);
     if (threadIdx.x == 0) fpart[blockIdx.x] = acc;
 }
 
-// One warp per column: ∇F_i = A_iᵀ r, g_i = ∇F_i / s_i, ḡ on P(s·x);
-// g64 keeps the full gradient (used by the refinement), gpart ‖ḡ‖² per block.
-template <typename TA>
+// One block per column: ∇F_i = A_iᵀ r, g_i = ∇F_i / s_i, ḡ on P(s·x);
+// g64 keeps the full gradient (used by the refinement), gpart[i] = ḡ_i².
+template <typename TA, bool VEC>
 __global__ void __launch_bounds__(kKktThreads) k_kkt_grad(const TA* __restrict__ A, int64_t d,
                                                           int64_t n, int64_t lda,
                                                           const double* __restrict__ r,
@@ -72,78 +93,77 @@ __global__ void __launch_bounds__(kKktThreads) k_kkt_grad(const TA* __restrict__
                                                           const double* __restrict__ x,
                                                           double* __restrict__ g64,
                                                           double* __restrict__ gpart) {
-    __shared__ double wsum[kKktThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-    double gb2 = 0.0;
-    if (i < n) {
-        const TA* col = A + i * lda;
-        double acc0 = 0.0, acc1 = 0.0;
-        int64_t t = lane;
-        for (; t + 32 < d; t += 64) {
-            acc0 = fma((double)col[t], r[t], acc0);
-            acc1 = fma((double)col[t + 32], r[t + 32], acc1);
-        }
-        for (; t < d; t += 32) acc0 = fma((double)col[t], r[t], acc0);
-        const double grad = warp_sum(acc0 + acc1);
-        if (lane == 0) {
-            const double gi = grad / s[i];
-            const double yi = x[i] * s[i];
-            g64[i] = gi;
-            const bool P = yi > 0.0 || gi < 0.0;
-            gb2 = P ? gi * gi : 0.0;
-        }
+    __shared__ double scratch[32];
+    const int64_t i = blockIdx.x;
+    const TA* col = A + i * lda;
+    double acc = 0.0;
+    const int64_t d4 = VEC ? d / 4 : 0;
+#pragma unroll 4
+    for (int64_t q = threadIdx.x; q < d4; q += blockDim.x) {
+        double a[4], rr[4];
+        load4(col + 4 * q, a);
+        load4(r + 4 * q, rr);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fma(a[u], rr[u], acc);
     }
-    if (lane == 0) wsum[wid] = gb2;
-    __syncthreads();
+    for (int64_t t = 4 * d4 + threadIdx.x; t < d; t += blockDim.x)
+        acc = fma((double)col[t], r[t], acc);
+    const double grad = block_sum(acc, scratch);
     if (threadIdx.x == 0) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += wsum[w];
-        gpart[blockIdx.x] = v;
+        const double gi = grad / s[i];
+        const double yi = x[i] * s[i];
+        g64[i] = gi;
+        const bool P = yi > 0.0 || gi < 0.0;
+        gpart[i] = P ? gi * gi : 0.0;
     }
 }
 
 __global__ void k_kkt_final(const double* __restrict__ gpart, int ng,
                             const double* __restrict__ fpart, int nf, double den,
                             double* __restrict__ out) {
-    if (threadIdx.x < 32) {
-        const double gb2 = warp_sum_array(gpart, ng);
-        const double r2 = warp_sum_array(fpart, nf);
-        if (threadIdx.x == 0) {
-            const double num = sqrt(gb2);
-            out[0] = den > 0.0 ? num / den : num;
-            out[1] = 0.5 * r2;
-        }
+    __shared__ double scratch[32];
+    double g = 0.0, f = 0.0;
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) g += gpart[i];
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) f += fpart[i];
+    g = block_sum(g, scratch);
+    f = block_sum(f, scratch);
+    if (threadIdx.x == 0) {
+        const double num = sqrt(g);
+        out[0] = den > 0.0 ? num / den : num;
+        out[1] = 0.5 * f;
     }
 }
 
-// Workspace layout inside c->kkt_pool (sized by the caller of launch_kkt):
-//   r64 (d), rpart (CG·d), g64 (ldq), kkt_part (gparts | fparts), kkt_out (2)
+// Workspace inside c->kkt_pool: r64 (d), rpart (CG·d), g64 (ldq),
+// kkt_part (512 fparts | n gparts), kkt_out (2).
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2) {
     const int64_t d = c->d, n = c->n;
     const int CG = c->CG;
     const int64_t cpg = ceil_div(n, CG);
-    const dim3 g1((unsigned)ceil_div(d, kKktThreads), (unsigned)CG);
+    const dim3 g1((unsigned)ceil_div(d, kKktRows), (unsigned)CG);
     const int nf = (int)std::min<int64_t>(ceil_div(d, kKktThreads), 512);
-    const int ng = (int)ceil_div(n, kKktThreads / 32);
     double* fpart = c->kkt_part;
     double* gpart = c->kkt_part + 512;
+    const size_t esz = c->dtype == ALN_DTYPE_F32 ? 4 : 8;
+    const bool vec = aligned16(c->A, c->lda, esz);
+#define ALN_KKT(TA, VE)                                                                           \
+    do {                                                                                          \
+        k_kkt_ax<TA, VE><<<g1, kKktThreads, 0, c->stream>>>((const TA*)c->A, d, n, c->lda, x64,  \
+                                                            cpg, c->rpart);                       \
+        k_kkt_r<TA><<<nf, kKktThreads, 0, c->stream>>>(d, c->rpart, CG, (const TA*)b, c->r64,    \
+                                                       fpart);                                    \
+        k_kkt_grad<TA, VE><<<(unsigned)n, kKktThreads, 0, c->stream>>>(                           \
+            (const TA*)c->A, d, n, c->lda, c->r64, c->s, x64, c->g64, gpart);                     \
+    } while (0)
     if (c->dtype == ALN_DTYPE_F32) {
-        k_kkt_ax<float><<<g1, kKktThreads, 0, c->stream>>>((const float*)c->A, d, n, c->lda, x64,
-                                                           cpg, c->rpart);
-        k_kkt_r<float><<<nf, kKktThreads, 0, c->stream>>>(d, c->rpart, CG, (const float*)b, c->r64,
-                                                          fpart);
-        k_kkt_grad<float><<<ng, kKktThreads, 0, c->stream>>>((const float*)c->A, d, n, c->lda,
-                                                             c->r64, c->s, x64, c->g64, gpart);
+        if (vec) ALN_KKT(float, true);
+        else ALN_KKT(float, false);
     } else {
-        k_kkt_ax<double><<<g1, kKktThreads, 0, c->stream>>>((const double*)c->A, d, n, c->lda, x64,
-                                                            cpg, c->rpart);
-        k_kkt_r<double><<<nf, kKktThreads, 0, c->stream>>>(d, c->rpart, CG, (const double*)b,
-                                                           c->r64, fpart);
-        k_kkt_grad<double><<<ng, kKktThreads, 0, c->stream>>>((const double*)c->A, d, n, c->lda,
-                                                              c->r64, c->s, x64, c->g64, gpart);
+        if (vec) ALN_KKT(double, true);
+        else ALN_KKT(double, false);
     }
-    k_kkt_final<<<1, 32, 0, c->stream>>>(gpart, ng, fpart, nf, den, out2);
+#undef ALN_KKT
+    k_kkt_final<<<1, 256, 0, c->stream>>>(gpart, (int)n, fpart, nf, den, out2);
     return cudaGetLastError();
 }
 

@@ -5,14 +5,17 @@
 
 namespace aln {
 
-// One warp per column A_i:
+// One 256-thread block per column A_i, one pass over the column:
 //   s_i² = Σ_t A_ti²            (FP64)            — √diag(H) of Alg. 1, Eq. Rescaling
-//   c_ci = Σ_t A_ti B_ct, c < kc (FP64)           — Aᵀb of Eq. NQP
+//   c_ci = Σ_t A_ti B_ct, c < kc ≤ 4 (FP64)       — Aᵀb of Eq. NQP
 //   s_i  = √s_i², or 1 when s_i² = 0 (Eq. Rescaling's H_ii = 0 case)
 //   q_ci = −c_ci / s_i                            — q of Eq. NQPQ
 // With SPLIT, also writes hi = bf16(A_ti), lo = bf16(A_ti − hi) into the
 // K-major [n][ldk] arrays read by the tensor-core Gram (zero padding t ≥ d).
-template <typename TA, bool SPLIT>
+// VEC: the column and B rows are 16-byte aligned, so four consecutive
+// elements move per load (the kernel is HBM-bound; wide loads keep enough
+// bytes in flight).
+template <typename TA, bool SPLIT, bool VEC>
 __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int64_t d, int64_t n,
                                                   int64_t lda, const TA* __restrict__ B, int kc,
                                                   int64_t ldb, double* __restrict__ s,
@@ -21,45 +24,71 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
                                                   int* __restrict__ flags,
                                                   __nv_bfloat16* __restrict__ hi,
                                                   __nv_bfloat16* __restrict__ lo, int64_t ldk) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
+    __shared__ double scratch[32];
+    const int64_t i = blockIdx.x;
     const TA* col = A + i * lda;
-    double s2 = 0.0;
+    double s2 = 0.0, dot[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
+    const int64_t d4 = VEC ? d / 4 : 0;
 #pragma unroll 4
-    for (int64_t t = lane; t < d; t += 32) {
+    for (int64_t q = threadIdx.x; q < d4; q += blockDim.x) {
+        double a[4];
+        load4(col + 4 * q, a);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            s2 = fma(a[u], a[u], s2);
+            bad |= !isfinite(a[u]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (c < kc) {
+                double bb[4];
+                load4(B + (int64_t)c * ldb + 4 * q, bb);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dot[c] = fma(a[u], bb[u], dot[c]);
+            }
+        }
+        if (SPLIT) {
+            __nv_bfloat16 h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float af = (float)a[u];
+                h[u] = __float2bfloat16_rn(af);
+                l[u] = __float2bfloat16_rn(af - __bfloat162float(h[u]));
+            }
+            *reinterpret_cast<uint2*>(hi + i * ldk + 4 * q) = *reinterpret_cast<uint2*>(h);
+            *reinterpret_cast<uint2*>(lo + i * ldk + 4 * q) = *reinterpret_cast<uint2*>(l);
+        }
+    }
+    for (int64_t t = 4 * d4 + threadIdx.x; t < d; t += blockDim.x) {
         const double a = (double)col[t];
-        s2 += a * a;
+        s2 = fma(a, a, s2);
         bad |= !isfinite(a);
+        for (int c = 0; c < kc; ++c) dot[c] = fma(a, (double)B[(int64_t)c * ldb + t], dot[c]);
         if (SPLIT) {
             const float af = (float)col[t];
             const __nv_bfloat16 h = __float2bfloat16_rn(af);
-            const __nv_bfloat16 l = __float2bfloat16_rn(af - __bfloat162float(h));
             hi[i * ldk + t] = h;
-            lo[i * ldk + t] = l;
+            lo[i * ldk + t] = __float2bfloat16_rn(af - __bfloat162float(h));
         }
     }
     if (SPLIT) {
         const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-        for (int64_t t = d + lane; t < ldk; t += 32) {
+        for (int64_t t = d + threadIdx.x; t < ldk; t += blockDim.x) {
             hi[i * ldk + t] = z;
             lo[i * ldk + t] = z;
         }
     }
-    s2 = warp_sum(s2);
-    const double si = s2 > 0.0 ? sqrt(s2) : 1.0;
-    for (int c = 0; c < kc; ++c) {
-        const TA* bc = B + (int64_t)c * ldb;
-        double dot = 0.0;
-#pragma unroll 4
-        for (int64_t t = lane; t < d; t += 32) dot += (double)col[t] * (double)bc[t];
-        dot = warp_sum(dot);
-        if (lane == 0) q64[(int64_t)c * ldq + i] = -dot / si;
-    }
-    if (lane == 0) {
+    s2 = block_sum(s2, scratch);
+    double dsum[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dsum[c] = c < kc ? block_sum(dot[c], scratch) : 0.0;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        const double si = s2 > 0.0 ? sqrt(s2) : 1.0;
         s[i] = si;
         inv_s[i] = 1.0 / si;
+        for (int c = 0; c < kc; ++c) q64[(int64_t)c * ldq + i] = -dsum[c] / si;
         if (bad) atomicOr(flags, 1);
     }
 }
@@ -170,10 +199,13 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
             const int64_t j = j0 + tx + 16 * b;
             if (j >= N) continue;
             if (MODE == MODE_GRAM) {
+                // Lower triangle only (diagonal tiles too), mirrored: Q is
+                // exactly symmetric.
+                if (j > i) continue;
                 double v = acc[a][b] * inv_s[i] * inv_s[j];
                 if (i == j) v = acc[a][b] != 0.0 ? 1.0 : 0.0;
                 out[i * ldo + j] = v;
-                if (tm != tn) out[j * ldo + i] = v;
+                out[j * ldo + i] = v;
             } else {
                 out[j * ldo + i] = -acc[a][b] * inv_s[i];
             }
@@ -188,29 +220,31 @@ cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, 
                             const void* B, int kc, int64_t ldb, double* s, double* inv_s,
                             double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
                             __nv_bfloat16* lo, int64_t ldk, cudaStream_t st) {
-    const int warps = 8;
-    const dim3 grid((unsigned)ceil_div(n, warps)), block(32 * warps);
+    const dim3 grid((unsigned)n), block(256);
     const bool split = hi != nullptr;
+    const size_t esz = dtype == ALN_DTYPE_F32 ? 4 : 8;
+    const bool vec = aligned16(A, lda, esz) && (kc == 0 || aligned16(B, ldb, esz));
+#define ALN_COLSTATS(TA, SP, VE)                                                              \
+    k_colstats<TA, SP, VE><<<grid, block, 0, st>>>((const TA*)A, d, n, lda, (const TA*)B, kc, \
+                                                   ldb, s, inv_s, q64, ldq, flags, hi, lo, ldk)
     if (dtype == ALN_DTYPE_F32) {
-        if (split)
-            k_colstats<float, true><<<grid, block, 0, st>>>((const float*)A, d, n, lda,
-                                                            (const float*)B, kc, ldb, s, inv_s,
-                                                            q64, ldq, flags, hi, lo, ldk);
-        else
-            k_colstats<float, false><<<grid, block, 0, st>>>((const float*)A, d, n, lda,
-                                                             (const float*)B, kc, ldb, s, inv_s,
-                                                             q64, ldq, flags, hi, lo, ldk);
+        if (split) {
+            if (vec) ALN_COLSTATS(float, true, true);
+            else ALN_COLSTATS(float, true, false);
+        } else {
+            if (vec) ALN_COLSTATS(float, false, true);
+            else ALN_COLSTATS(float, false, false);
+        }
     } else {
-        if (split)
-            k_colstats<double, true><<<grid, block, 0, st>>>((const double*)A, d, n, lda,
-                                                             (const double*)B, kc, ldb, s,
-                                                             inv_s, q64, ldq, flags, hi, lo, ldk);
-        else
-            k_colstats<double, false><<<grid, block, 0, st>>>((const double*)A, d, n, lda,
-                                                              (const double*)B, kc, ldb, s,
-                                                              inv_s, q64, ldq, flags, hi, lo,
-                                                              ldk);
+        if (split) {
+            if (vec) ALN_COLSTATS(double, true, true);
+            else ALN_COLSTATS(double, true, false);
+        } else {
+            if (vec) ALN_COLSTATS(double, false, true);
+            else ALN_COLSTATS(double, false, false);
+        }
     }
+#undef ALN_COLSTATS
     return cudaGetLastError();
 }
 
