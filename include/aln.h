@@ -176,6 +176,40 @@ typedef struct aln_stats {
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */
 aln_status aln_get_stats(aln_ctx* ctx, aln_stats* out);
 
+/* Scratch of aln_kkt_residual_noalloc, in doubles (16 MiB). */
+#define ALN_NOALLOC_SCRATCH_DOUBLES (1 << 21)
+
+/* FP64 KKT residual and objective of ONE solution, allocating nothing.
+ * The paper has no counterpart: this is a deployment variant of
+ * aln_kkt_residual for callers that cannot call cudaMalloc — code that runs
+ * under a fixed device-memory budget, a callback invoked while the caller's
+ * own memory pool is exhausted or locked, or a hot path where an allocation
+ * (which can synchronize the device or fail) is not allowed.  It needs no
+ * context: every intermediate (column norms, r = Ax − b, partial sums) lives in
+ * a fixed array of ALN_NOALLOC_SCRATCH_DOUBLES doubles compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The same quantities as aln_kkt_residual are computed:
+ *   out[0] = ‖ḡ‖/‖min(q,0)‖ (absolute ‖ḡ‖ when ‖min(q,0)‖ = 0),
+ *   out[1] = ½‖Ax − b‖².
+ *   A      d×n column-major, lda ≥ d, dtype F32 or F64   (device memory)
+ *   b      d entries, same dtype                         (device memory)
+ *   x      n entries, FP64, x ≥ 0                        (device memory)
+ *   out    2 doubles                                     (device memory)
+ *   stream cudaStream_t the work is enqueued on (NULL = legacy stream); the
+ *          call returns without synchronizing.
+ * Limits: 3n + 2d + 520 ≤ ALN_NOALLOC_SCRATCH_DOUBLES, otherwise
+ * ALN_ERR_INVALID_ARG and nothing is launched (use aln_kkt_residual instead).
+ * A NaN or Inf in A or b makes both outputs NaN.
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * overwrites it, so calls whose work overlaps on the GPU (different streams
+ * with no ordering between them) race and produce wrong results.
+ * Errors: INVALID_ARG, CUDA. */
+aln_status aln_kkt_residual_noalloc(const void* A, int64_t d, int64_t n, int64_t lda,
+                                    int32_t dtype, const void* b, const double* x, double* out,
+                                    void* stream);
+
 /* Destroy a context and free its workspace (NULL is accepted). */
 void aln_destroy(aln_ctx* ctx);
 

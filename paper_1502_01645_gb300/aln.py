@@ -28,6 +28,7 @@ RHS_MAXITER, RHS_NONFINITE, RHS_STAGNATED = 3, 4, 5
 EXPORTS = (
     "aln_default_options", "aln_create", "aln_prepare", "aln_solve", "aln_kkt_residual",
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
+    "aln_kkt_residual_noalloc",
 )
 
 
@@ -92,6 +93,8 @@ def load(path: str | None = None):
     lib.aln_status_string.restype = ctypes.c_char_p
     lib.aln_version.argtypes = []
     lib.aln_version.restype = i32
+    lib.aln_kkt_residual_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, dp, dp, vp]
+    lib.aln_kkt_residual_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -172,6 +175,12 @@ def aln_destroy(ctx) -> None:
 
 def aln_version() -> int:
     return load().aln_version()
+
+
+def aln_kkt_residual_noalloc(A, d, n, lda, dtype, b, x, out, stream=None) -> None:
+    """Allocation-free FP64 KKT residual of one solution (device pointers only)."""
+    _check(load().aln_kkt_residual_noalloc(_ptr(A), d, n, lda, dtype, _ptr(b), _ptr(x), _ptr(out),
+                                           stream or None), "aln_kkt_residual_noalloc")
 
 
 # --------------------------------------------------------------- convenience class

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaln.so")
-SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "iter.cu", "persist.cu", "kkt.cu"]
+SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "iter.cu", "persist.cu", "kkt.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
