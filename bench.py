@@ -29,8 +29,9 @@ sys.path.insert(0, ROOT)
 METRIC = "NNLS solves/s at rel KKT ≤1e-6, chosen form vs plain FP64 on one GB300"
 UNIT = "solves/s"
 D, N, TOL, SEED = 20000, 5000, 1e-6, 1002
-WORKLOAD = ("lopsided_single_20000x5000_f32: A U[0,1] x log-uniform column scales [1e-2,1e2], "
-            "x_true 70% zeros Exp(1), b = A x_true + 1% Gaussian noise")
+WORKLOAD_FMT = ("lopsided_single_{d}x{n}_f32: A U[0,1] x log-uniform column scales [1e-2,1e2], "
+                "x_true 70% zeros Exp(1), b = A x_true + 1% Gaussian noise")
+WORKLOAD = WORKLOAD_FMT.format(d=D, n=N)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -43,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--d", type=int, default=D, help="rows of A (smaller values: profiling cases)")
+    ap.add_argument("--n", type=int, default=N, help="columns of A")
     return ap.parse_args()
 
 
@@ -348,7 +351,10 @@ def run_ours(args):
 
 
 def main():
+    global D, N, WORKLOAD
     args = parse()
+    D, N = args.d, args.n
+    WORKLOAD = WORKLOAD_FMT.format(d=D, n=N)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

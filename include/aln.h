@@ -91,7 +91,9 @@ typedef struct aln_options {
     int32_t row_groups;   /* row groups of the single-RHS matvec; 0 = auto */
     int32_t stagnation;   /* stop an inner run after this many iterations without a
                              new smallest ‖ḡ‖² (§5 stop rule); 0 = default 100 */
-    int32_t reserved[3];
+    int32_t iter_kernel;  /* persistent Alg. 2 kernel: 0 auto (replicated state when
+                             the vectors fit in shared memory), 1 tiled, 2 replicated */
+    int32_t reserved[2];
 } aln_options;
 
 typedef struct aln_solve_info {
@@ -170,7 +172,10 @@ typedef struct aln_stats {
     int64_t passive_rows;    /* Σ_k |P_k| over those iterations (rows of Q read for Qḡ) */
     int64_t clipped_rows;    /* Σ_k |C_k| (rows of Q read for the clipped correction) */
     int32_t persist_blocks;  /* grid of the persistent kernel */
-    int32_t reserved;
+    int32_t clipped_iterations; /* iterations that needed the clipped correction Qe */
+    double phase_us[5];      /* block 0's time in the persistent kernel, per phase:
+                                product Qḡ, grid barrier, update, clipped
+                                correction, mask (replicated-state kernel) */
 } aln_stats;
 
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */

@@ -35,7 +35,8 @@ EXPORTS = (
 class AlnOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_refine", ctypes.c_int32),
                 ("persist_blocks", ctypes.c_int32), ("row_groups", ctypes.c_int32),
-                ("stagnation", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("stagnation", ctypes.c_int32), ("iter_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class AlnSolveInfo(ctypes.Structure):
@@ -50,7 +51,7 @@ class AlnStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("iterate_ms", ctypes.c_double), ("passive_rows", ctypes.c_int64),
                 ("clipped_rows", ctypes.c_int64), ("persist_blocks", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("clipped_iterations", ctypes.c_int32), ("phase_us", ctypes.c_double * 5)]
 
 
 class AlnError(RuntimeError):

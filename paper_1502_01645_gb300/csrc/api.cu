@@ -88,24 +88,30 @@ aln_status alloc_workspace(aln_ctx* c) {
     c->R = R;
     c->nb = (int)std::min<int64_t>(ceil_div(n, 256), 1024);
 
-    // Persistent kernel: column tiles × row groups; about two work items per
-    // block, at least 32 rows per group; one block per SM (or the option).
+    // Persistent kernel: column tiles × row groups, about one work item per
+    // block (one block per SM, or the option), at least 32 rows per group.
     c->p_CT = (int)col_tiles;
-    int pR = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(2 * (int64_t)c->num_sms, col_tiles),
+    const int64_t blocks_wanted = c->opt.persist_blocks > 0 ? c->opt.persist_blocks : c->num_sms;
+    int pR = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_wanted / col_tiles,
                                                          ceil_div(n, 32)));
     c->p_R = std::min(pR, 64);
-    const int maxG = fp64(c) ? persist_max_blocks<double>(c->num_sms)
-                             : persist_max_blocks<float>(c->num_sms);
+    // The replicated-state kernel is used whenever its vectors fit in shared
+    // memory, unless the options ask for the tiled one.
+    c->p_repl = c->opt.iter_kernel == 1 ? 0 : 1;
+    const int maxG = fp64(c) ? persist_max_blocks<double>(c->num_sms, ldq, &c->p_repl)
+                             : persist_max_blocks<float>(c->num_sms, ldq, &c->p_repl);
     if (maxG <= 0) return ALN_ERR_CUDA;
     int G = c->opt.persist_blocks > 0 ? c->opt.persist_blocks : c->num_sms;
     G = (int)std::min<int64_t>({(int64_t)G, (int64_t)maxG, (int64_t)c->p_CT * c->p_R});
     c->p_G = std::max(G, 1);
-    const int64_t RP = std::max<int64_t>(R, c->p_R);
+    // partials: R (chain set-up) / R_p (tiled kernel) / 3·R_p (replicated: two
+    // parity buffers for Qḡ and one for Qe)
+    const int64_t RP = std::max<int64_t>(R, 3 * (int64_t)c->p_R);
 
     const size_t vec = (size_t)ldq * T;
     const size_t ct = (size_t)c->p_CT;
     size_t bytes = 6 * vec + (size_t)RP * vec + 2 * (size_t)c->nb * 8 + (size_t)c->nb * 4 + 256 +
-                   4 * round_up(ct * 8, 256) + 256 + 256;
+                   4 * round_up(ct * 8, 256) + round_up(2 * ct * c->p_R * 8, 256) + 256 + 256;
     bytes = round_up(bytes, 256) + 16 * 256;
     ALN_CHECK(ensure(&c->iter_pool, &c->iter_bytes, bytes + 1024));
     uint8_t* p = (uint8_t*)c->iter_pool;
@@ -126,7 +132,7 @@ aln_status alloc_workspace(aln_ctx* c) {
     c->cpart = (int*)take((size_t)c->nb * 4);
     c->st = (IterState*)take(sizeof(IterState));
     c->p_gpart = (double*)take(ct * 8);
-    c->p_kpart = (double*)take(ct * 8);
+    c->p_kpart = (double*)take(2 * ct * c->p_R * 8);  // curvature share per work item (×2 parity)
     c->p_cpart = (int*)take(ct * 8);
     c->p_clip = (int*)take(ct * 8);
     c->p_ticket = (unsigned int*)take(ct * 8);
@@ -174,6 +180,10 @@ aln_status run_until_done(aln_ctx* c) {
     if (c->st_host->status < 0 || !c->st_host->done) return ALN_ERR_TIMEOUT;
     c->stats.passive_rows += c->st_host->sum_passive;
     c->stats.clipped_rows += c->st_host->sum_clip;
+    if (c->p_repl) {
+        for (int k = 0; k < 5; ++k) c->stats.phase_us[k] += 1e-3 * (double)c->st_host->phase_ns[k];
+        c->stats.clipped_iterations += (int32_t)c->st_host->phase_ns[5];
+    }
     return ALN_OK;
 }
 
@@ -245,7 +255,8 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (opt) o = *opt;
     if (o.precision != ALN_PREC_FP64 && o.precision != ALN_PREC_SPLIT_BF16)
         return ALN_ERR_INVALID_ARG;
-    if (o.max_refine < 0 || o.persist_blocks < 0 || o.row_groups < 0 || o.stagnation < 0)
+    if (o.max_refine < 0 || o.persist_blocks < 0 || o.row_groups < 0 || o.stagnation < 0 ||
+        o.iter_kernel < 0 || o.iter_kernel > 2)
         return ALN_ERR_INVALID_ARG;
     if (o.stagnation == 0) o.stagnation = 100;
     aln_ctx* c = new (std::nothrow) aln_ctx();
@@ -427,6 +438,8 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     const bool f64 = fp64(c);
     c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
     c->stats.passive_rows = c->stats.clipped_rows = 0;
+    c->stats.clipped_iterations = 0;
+    for (double& v : c->stats.phase_us) v = 0.0;
     c->stats.iterations = 0;
     ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
     // Inner runs stop a little below tol so that the FP64 check usually passes

@@ -29,6 +29,8 @@ struct IterState {
     int32_t pad;
     int64_t sum_passive;  // Σ_k |P_k|: rows of Q read for w = Qḡ
     int64_t sum_clip;     // Σ_k |C_k|: rows read for the clipped correction
+    uint64_t phase_ns[6]; // block 0's time per phase: product, barrier, update,
+                          // clipped correction, mask, other
 };
 
 template <typename T> struct Vec16;
@@ -194,6 +196,7 @@ struct aln_ctx {
 
     // persistent Alg. 2 kernel geometry and its per-tile partials
     int p_CT = 0, p_R = 0, p_G = 0;
+    int p_repl = 0;  // 1: replicated-state kernel (vectors fit in shared memory)
     double* p_gpart = nullptr;
     int* p_cpart = nullptr;
     double* p_kpart = nullptr;

@@ -316,6 +316,173 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ---------------------------------------------------------------------------
+// Batched product for many right-hand sides sharing Q (Alg. 2 on k columns):
+//   D[i][p] = Σ_j Q[i][j] V[p][j],   V = the split of ḡ (or of e) for the
+//   compacted set of columns p < *ncols (map[p] = original column).
+// Same pipeline as the Gram (3-stage TMA ring, one MMA thread, 3 split
+// products, FP32 accumulation in TMEM); the CTA grid covers the maximum column
+// count and CTAs past *ncols exit at once.  Epilogues:
+//   BMODE_W: W[p][i] = D, and the curvature partial of the row tile,
+//            kpart[mtile][p] = Σ_{i ∈ tile} ḡ[map[p]][i] · D[i][p];
+//   BMODE_U: g[map[p]][i] += D  (the clipped correction Q e).
+// ---------------------------------------------------------------------------
+constexpr int BMODE_W = 0;
+constexpr int BMODE_U = 1;
+
+struct BatchArgs {
+    int64_t n;            // rows of Q (= M)
+    int num_kb;
+    const int* ncols;     // device: number of compacted columns
+    const int* map;       // compact index → column
+    int64_t ldq;          // row length of every per-column vector
+    float* W;             // [kmax][ldq]   (BMODE_W)
+    const float* gb;      // [k][ldq]      (BMODE_W)
+    double* kpart;        // [mtiles][kmax](BMODE_W)
+    int64_t kmax;
+    float* g;             // [k][ldq]      (BMODE_U)
+    int* timeout_flag;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_bgemm_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
+               const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo,
+               BatchArgs p) {
+    const int ncols = *p.ncols;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BM;
+    if (n0 >= ncols) return;  // uniform: before any barrier or TMEM use
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    __shared__ int s_map[BM];
+    __shared__ double s_red[4][BM];
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const int64_t pp = n0 + threadIdx.x;
+        s_map[threadIdx.x] = pp < ncols ? p.map[pp] : -1;
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int kb = 0; kb < p.num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            uint8_t* sb = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], 4 * TILE_BYTES);
+            tma_load_2d(sb, &a_hi, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sb + TILE_BYTES, &a_lo, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sb + 2 * TILE_BYTES, &b_hi, &full[s], kb * BK, (int)n0);
+            tma_load_2d(sb + 3 * TILE_BYTES, &b_lo, &full[s], kb * BK, (int)n0);
+            ++issued;
+        }
+        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+        for (int kb = 0; kb < p.num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            tc_fence_after();
+            const uint32_t a_h = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_l = a_h + TILE_BYTES;
+            const uint32_t b_h = a_h + 2 * TILE_BYTES;
+            const uint32_t b_l = a_h + 3 * TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint64_t dah = sdesc_sw128(a_h + off), dal = sdesc_sw128(a_l + off);
+                const uint64_t dbh = sdesc_sw128(b_h + off), dbl = sdesc_sw128(b_l + off);
+                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                umma_bf16(tmem, dah, dbl, idesc, 1u);
+                umma_bf16(tmem, dal, dbh, idesc, 1u);
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ok) s_abort = 1;
+    __syncthreads();
+    const bool good = !s_abort;
+    const int64_t row = m0 + warp * 32 + lane;
+    const bool rv = row < p.n;
+    const int cols = (int)(ncols - n0 < (int64_t)BM ? ncols - n0 : (int64_t)BM);
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    if (good) {
+        for (int c0 = 0; c0 < cols; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + c0, v);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int cc = c0 + t;
+                const int col = cc < cols ? s_map[cc] : -1;
+                if (MODE == BMODE_W) {
+                    double kp = 0.0;
+                    if (col >= 0 && rv) {
+                        p.W[(n0 + cc) * p.ldq + row] = v[t];
+                        kp = (double)p.gb[(int64_t)col * p.ldq + row] * (double)v[t];
+                    }
+                    kp = warp_sum(kp);
+                    if (lane == 0) s_red[warp][cc] = kp;
+                } else {
+                    if (col >= 0 && rv) {
+                        float* gp = p.g + (int64_t)col * p.ldq + row;
+                        *gp = *gp + v[t];
+                    }
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(p.timeout_flag, 1);
+    }
+    if (MODE == BMODE_W) {
+        __syncthreads();
+        if (good && threadIdx.x < cols) {
+            const double s = s_red[0][threadIdx.x] + s_red[1][threadIdx.x] +
+                             s_red[2][threadIdx.x] + s_red[3][threadIdx.x];
+            p.kpart[(int64_t)blockIdx.x * p.kmax + n0 + threadIdx.x] = s;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -375,6 +542,47 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
     k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, SMEM_BYTES, st>>>(mh, ml, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bfloat16* q_lo,
+                            int64_t n, int64_t ldk, const __nv_bfloat16* v_hi,
+                            const __nv_bfloat16* v_lo, int64_t kmax, const int* ncols,
+                            const int* map, int64_t ldq, float* W, const float* gb, double* kpart,
+                            float* g, int* timeout_flag, cudaStream_t st) {
+    using namespace tc;
+    if (((uintptr_t)q_hi & 15) || ((uintptr_t)q_lo & 15) || ((uintptr_t)v_hi & 15) ||
+        ((uintptr_t)v_lo & 15) || (ldk * 2) % 16 != 0)
+        return cudaErrorInvalidValue;
+    CUtensorMap ah, al, bh, bl;
+    if (!make_map(&ah, q_hi, ldk, n, ldk) || !make_map(&al, q_lo, ldk, n, ldk) ||
+        !make_map(&bh, v_hi, ldk, kmax, ldk) || !make_map(&bl, v_lo, ldk, kmax, ldk))
+        return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};
+    if (!attr[mode]) {
+        cudaError_t e = cudaFuncSetAttribute(mode == BMODE_W ? k_bgemm_tc<BMODE_W> : k_bgemm_tc<BMODE_U>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr[mode] = true;
+    }
+    BatchArgs a;
+    a.n = n;
+    a.num_kb = (int)ceil_div(ldk, BK);
+    a.ncols = ncols;
+    a.map = map;
+    a.ldq = ldq;
+    a.W = W;
+    a.gb = gb;
+    a.kpart = kpart;
+    a.kmax = kmax;
+    a.g = g;
+    a.timeout_flag = timeout_flag;
+    const dim3 grid((unsigned)ceil_div(n, BM), (unsigned)ceil_div(kmax, BM));
+    if (mode == BMODE_W)
+        k_bgemm_tc<BMODE_W><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+    else
+        k_bgemm_tc<BMODE_U><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
     return cudaGetLastError();
 }
 

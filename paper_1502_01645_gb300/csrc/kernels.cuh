@@ -46,7 +46,7 @@ cudaError_t launch_state_reset(aln_ctx* c, double eps, int max_iter);
 template <typename T>
 cudaError_t launch_alg2_persist(aln_ctx* c);
 template <typename T>
-int persist_max_blocks(int num_sms);
+int persist_max_blocks(int num_sms, int64_t ldq, int* repl);
 size_t persist_sync_bytes();
 
 // kkt.cu — FP64 KKT residual straight from A

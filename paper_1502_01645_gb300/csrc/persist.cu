@@ -1,28 +1,34 @@
 // Alg. 2 (§3) on one right-hand side as ONE persistent cooperative kernel.
 //
 // The vector state (y, g, ḡ, w, e) is owned by column tiles of TILE = 32·VN
-// elements (128 FP32 / 64 FP64); the symmetric product Qv = Σ_j v_j Q[j, :] is
-// split into work items (column tile ct, row group rg).  One iteration:
+// elements (128 FP32 / 64 FP64).  Q is symmetric, so Qv = Σ_j v_j Q[j, :]; the
+// product is split into work items (column tile ct, row group rg), each the
+// sum over the rows j of its group with v_j ≠ 0 (each row a contiguous
+// 16-byte-aligned run).  One iteration:
 //
-//   (a) γ = ‖ḡ‖², |P| from the per-tile partials (every block sums the same
-//       array in the same order, so every block takes the same decision);
-//       stop if P = ∅, γ < ε, the iteration cap, or the stagnation window.
-//   (b) w = Qḡ: every item sums the passive rows of its group into a partial;
-//       the last item of a column tile to finish (atomic ticket) adds the R
-//       partials in fixed order, writes w for the tile and κ_ct = ḡᵀw there.
+//   (a) γ = ‖ḡ‖², |P| from per-tile partials (every block sums the same array
+//       in the same order and takes the same decision); stop if P = ∅,
+//       γ < ε, the iteration cap, or the stagnation window (§5's rule).
+//   (b) w-partials: item (ct, rg) writes part[rg][tile] and its share of the
+//       curvature, κ_item = Σ_{i ∈ tile} ḡ_i part[rg][i]  (κ = ḡᵀQḡ = Σ κ_item).
 //   --- grid barrier ---
-//   (c) κ = Σ κ_ct, α = γ/κ; each tile: y⁺ = [y − αḡ]₊, e = clipped part,
-//       g ← g − αw, and the mask of the next iterate assuming no clipping
-//       (ḡ, γ_ct, |P|_ct); clip_ct = number of clipped entries.
+//   (c) κ = Σ κ_item, α = γ/κ (exact line search).  Each tile: w = Σ_rg part,
+//       y⁺ = [y − αḡ]₊, e = the clipped part (e_i = αḡ_i − y_i where
+//       y_i − αḡ_i < 0), g ← g − αw, and the mask of the new iterate as if
+//       nothing was clipped (ḡ, γ_ct, |P|_ct); clip_ct = number clipped.
 //   --- grid barrier ---
-//   (d) only if Σ clip_ct > 0: u = Qe over the clipped rows (same item
-//       scheme); the last item of a tile adds u to g and recomputes the mask.
-//       --- grid barrier ---
+//   (d) only if Σ clip_ct > 0: u = Qe over the clipped rows with the same
+//       items; the last item of a tile to finish (atomic ticket) adds u to g
+//       and recomputes that tile's mask.  --- grid barrier ---
 //
-// So an iteration costs two grid barriers, three when some variable hits the
-// bound.  All sums are in a fixed order: results are bitwise reproducible.
-// The grid barrier spins with a time limit; on expiry the kernel records
-// ALN_RHS timeout in the state and every block leaves the loop.
+// Since y⁺ − y = −αḡ + e, g + Q(y⁺ − y) = g − αw + Qe: the product Qḡ of the
+// step size is reused and only clipped rows are read a second time (exact
+// algebra; the paper counts a second O(n·S(n)) product, §4.2).
+//
+// Two grid barriers per iteration (three when something is clipped).  Every
+// sum has a fixed order, so results are bitwise reproducible.  Each barrier
+// wait is bounded (2 s on %globaltimer); on expiry the kernel flags a timeout
+// and every block leaves the loop.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -30,9 +36,10 @@ namespace aln {
 
 constexpr int kPThreads = 1024;
 constexpr int kPWarps = kPThreads / 32;
-constexpr int kPU = 4;                        // rows in flight per warp
-constexpr uint64_t kBarrierNs = 2000000000ull; // 2 s per barrier wait
-constexpr int kStatusTimeout = -1;             // state status after a barrier timeout
+constexpr int kPU = 4;                          // Q rows in flight per warp (64 KB per SM)
+constexpr uint64_t kBarrierNs = 2000000000ull;  // 2 s per barrier wait
+constexpr int kStatusTimeout = -1;              // state status after a barrier timeout
+constexpr int kMaxItems = 64 * 1024;
 
 __device__ __forceinline__ uint64_t p_globaltimer() {
     uint64_t t;
@@ -40,54 +47,50 @@ __device__ __forceinline__ uint64_t p_globaltimer() {
     return t;
 }
 
-// Sums over the per-tile partial arrays through L2 (written by other blocks).
-__device__ __forceinline__ double warp_sum_cg(const double* p, int count) {
-    const int lane = threadIdx.x & 31;
-    double v = 0.0;
-    for (int i = lane; i < count; i += 32) v += __ldcg(p + i);
-    return warp_sum(v);
-}
-__device__ __forceinline__ int warp_sum_cg_i(const int* p, int count) {
-    const int lane = threadIdx.x & 31;
-    int v = 0;
-    for (int i = lane; i < count; i += 32) v += __ldcg(p + i);
-    return warp_sum_i(v);
-}
-
 struct PersistSync {
-    unsigned int arrive;
-    unsigned int gen;
-    unsigned int timeout;
-    unsigned int pad;
+    unsigned int count;    // monotonic arrivals: barrier k completes at k·G
+    unsigned int timeout;  // set by the first block whose wait expired
+    unsigned int pad[2];
 };
 
-// Sense-free generation barrier over the co-resident grid (cooperative launch).
-__device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int nblocks) {
-    __syncthreads();
+// Grid barrier over the co-resident grid (cooperative launch).  Arrival is a
+// release reduction, the wait an acquire poll; `target` is this barrier's
+// completion count, tracked identically by every block.
+__device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target) {
     __shared__ int s_ok;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&s->count), "r"(1u)
+                     : "memory");
         int ok = 1;
-        volatile unsigned int* vgen = &s->gen;
-        const unsigned int gen = *vgen;
-        __threadfence();
-        const unsigned int prev = atomicAdd(&s->arrive, 1u);
-        if (prev == nblocks - 1) {
-            atomicExch(&s->arrive, 0u);
-            __threadfence();
-            atomicAdd(&s->gen, 1u);
-        } else {
-            const uint64_t t0 = p_globaltimer();
-            unsigned int spins = 0;
-            while (*vgen == gen) {
-                if ((++spins & 255u) == 0 && p_globaltimer() - t0 > kBarrierNs) {
-                    ok = 0;
+        unsigned int spins = 0;
+        uint64_t t0 = 0;
+        for (;;) {
+            // relaxed polls with a short back-off keep the counter's L2 line
+            // free for the arrivals; one acquire fence once the count is reached
+            unsigned int v;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&s->count)
+                         : "memory");
+            if ((int)(v - target) >= 0) {
+                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                break;
+            }
+            __nanosleep(32);
+            if ((++spins & 1023u) == 0) {
+                const uint64_t t = p_globaltimer();
+                if (t0 == 0) {
+                    t0 = t;
+                } else if (t - t0 > kBarrierNs) {
                     atomicExch(&s->timeout, 1u);
+                    ok = 0;
+                    break;
+                }
+                if (*(volatile unsigned int*)&s->timeout) {
+                    ok = 0;
                     break;
                 }
             }
         }
-        __threadfence();
-        if (*(volatile unsigned int*)&s->timeout) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -110,7 +113,7 @@ struct PersistArgs {
     T* part;         // R × ldq
     double* gpart;   // CT
     int* cpart;      // CT
-    double* kpart;   // CT
+    double* kitem;   // CT·R
     int* clip;       // CT
     unsigned int* ticket;  // CT
     PersistSync* sync;
@@ -118,104 +121,121 @@ struct PersistArgs {
 };
 
 // Partial of Σ_{j ∈ group rg, v_j ≠ 0} v_j Q[j, tile ct] into part[rg][tile].
+// Each warp takes a contiguous chunk of the group's rows, loads 64 entries of
+// v at once, compacts the non-zero ones with a ballot and keeps kPU row loads
+// of Q in flight.  Returns (in threads < TILE) the partial of its column.
 template <typename T>
-__device__ __forceinline__ void mv_item(const PersistArgs<T>& a, const T* __restrict__ v, int ct,
-                                        int rg, T* red) {
+__device__ __forceinline__ T mv_item(const PersistArgs<T>& a, const T* __restrict__ v, int ct,
+                                     int rg, T* red) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t col = (int64_t)ct * TILE + lane * VN;
-    const int j0 = rg * a.rows_per_group;
-    const int j1 = min(a.n, j0 + a.rows_per_group);
+    const int g0 = rg * a.rows_per_group;
+    const int g1 = min(a.n, g0 + a.rows_per_group);
+    const int chunk = (g1 - g0 + kPWarps - 1) / kPWarps;
+    const int r0 = g0 + warp * chunk;
+    const int r1 = min(g1, r0 + chunk);
     T acc[VN];
 #pragma unroll
     for (int c = 0; c < VN; ++c) acc[c] = T(0);
-    for (int jb = j0 + warp; jb < j1; jb += kPWarps * kPU) {
-        T vv[kPU];
-        V qq[kPU];
+    for (int base = r0; base < r1; base += 64) {
+        const int ja = base + lane, jb = base + 32 + lane;
+        const T va = ja < r1 ? __ldcg(v + ja) : T(0);
+        const T vb = jb < r1 ? __ldcg(v + jb) : T(0);
+        unsigned int ma = __ballot_sync(0xffffffffu, va != T(0));
+        unsigned int mb = __ballot_sync(0xffffffffu, vb != T(0));
+        while (ma | mb) {  // warp-uniform
+            T vv[kPU];
+            V qq[kPU];
 #pragma unroll
-        for (int u = 0; u < kPU; ++u) {
-            const int j = jb + kPWarps * u;
-            vv[u] = j < j1 ? __ldcg(v + j) : T(0);
+            for (int u = 0; u < kPU; ++u) {
+                int j = -1;
+                T vj = T(0);
+                if (ma) {
+                    const int src = __ffs(ma) - 1;
+                    ma &= ma - 1;
+                    j = base + src;
+                    vj = __shfl_sync(0xffffffffu, va, src);
+                } else if (mb) {
+                    const int src = __ffs(mb) - 1;
+                    mb &= mb - 1;
+                    j = base + 32 + src;
+                    vj = __shfl_sync(0xffffffffu, vb, src);
+                }
+                vv[u] = vj;
+                qq[u] = j >= 0 ? __ldg(reinterpret_cast<const V*>(a.Q + (int64_t)j * a.ldq + col))
+                               : V{};
+            }
+#pragma unroll
+            for (int u = 0; u < kPU; ++u)
+#pragma unroll
+                for (int c = 0; c < VN; ++c) acc[c] = fma(vv[u], vget(qq[u], c), acc[c]);
         }
-#pragma unroll
-        for (int u = 0; u < kPU; ++u) {
-            const int j = jb + kPWarps * u;
-            if (vv[u] != T(0))
-                qq[u] = __ldg(reinterpret_cast<const V*>(a.Q + (int64_t)j * a.ldq + col));
-            else
-                qq[u] = V{};
-        }
-#pragma unroll
-        for (int u = 0; u < kPU; ++u)
-#pragma unroll
-            for (int c = 0; c < VN; ++c) acc[c] = fma(vv[u], vget(qq[u], c), acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < VN; ++c) red[warp * TILE + lane * VN + c] = acc[c];
     __syncthreads();
+    T s = T(0);
     if (threadIdx.x < TILE) {
-        T s = T(0);
 #pragma unroll 8
         for (int w2 = 0; w2 < kPWarps; ++w2) s += red[w2 * TILE + threadIdx.x];
         __stcg(a.part + (int64_t)rg * a.ldq + (int64_t)ct * TILE + threadIdx.x, s);
     }
+    __syncthreads();
+    return s;
 }
 
-// After an item: take a ticket for its tile; returns true in the block that
-// completes the tile (it then sees every partial of the tile).
-__device__ __forceinline__ bool last_of_tile(unsigned int* ticket, int ct, int R) {
-    __shared__ int s_last;
-    __threadfence();
+// Block sum over the first TILE threads (warps 0..TILE/32-1) in fixed order;
+// result in thread 0.
+template <int TILE>
+__device__ __forceinline__ double tile_sum(double v, double* sd) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0 && wid < TILE / 32) sd[wid] = v;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned int t = atomicAdd(ticket + ct, 1u);
-        s_last = (t == (unsigned int)(R - 1));
-        if (s_last) ticket[ct] = 0u;  // reset for the next product
-    }
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w2 = 0; w2 < TILE / 32; ++w2) s += sd[w2];
     __syncthreads();
-    if (s_last) __threadfence();
-    return s_last != 0;
+    return s;
+}
+template <int TILE>
+__device__ __forceinline__ int tile_sum_i(int v, int* si) {
+    v = warp_sum_i(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0 && wid < TILE / 32) si[wid] = v;
+    __syncthreads();
+    int s = 0;
+    if (threadIdx.x == 0)
+        for (int w2 = 0; w2 < TILE / 32; ++w2) s += si[w2];
+    __syncthreads();
+    return s;
 }
 
-// Mask of one tile: ḡ = g on P(y), partial γ and |P| (threads < TILE).
+// Mask of one tile from (y, g) held in registers by threads < TILE: writes ḡ
+// and the tile's ‖ḡ‖² and |P| partials.
 template <typename T>
-__device__ __forceinline__ void tile_mask(const PersistArgs<T>& a, int ct, double* sd, int* si) {
+__device__ __forceinline__ void tile_mask(const PersistArgs<T>& a, int ct, bool in, T yi, T gi,
+                                          double* sd, int* si) {
     constexpr int TILE = 32 * Vec16<T>::N;
     double v = 0.0;
     int c = 0;
-    if (threadIdx.x < TILE) {
+    if (threadIdx.x < TILE && in) {
         const int64_t i = (int64_t)ct * TILE + threadIdx.x;
-        if (i < a.n) {
-            const T yi = __ldcg(a.y + i), gi = __ldcg(a.g + i);
-            const bool P = yi > T(0) || gi < T(0);
-            const T gbi = P ? gi : T(0);
-            __stcg(a.gb + i, gbi);
-            v = (double)gbi * (double)gbi;
-            c = P ? 1 : 0;
-        }
+        const bool P = yi > T(0) || gi < T(0);
+        const T gbi = P ? gi : T(0);
+        __stcg(a.gb + i, gbi);
+        v = (double)gbi * (double)gbi;
+        c = P ? 1 : 0;
     }
-    // TILE ≤ 128 threads = warps 0..3
-    v = warp_sum(v);
-    c = warp_sum_i(c);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0 && wid < TILE / 32) {
-        sd[wid] = v;
-        si[wid] = c;
-    }
-    __syncthreads();
+    v = tile_sum<TILE>(v, sd);
+    c = tile_sum_i<TILE>(c, si);
     if (threadIdx.x == 0) {
-        double s = 0.0;
-        int k = 0;
-        for (int w2 = 0; w2 < TILE / 32; ++w2) {
-            s += sd[w2];
-            k += si[w2];
-        }
-        __stcg(a.gpart + ct, s);
-        __stcg(a.cpart + ct, k);
+        __stcg(a.gpart + ct, v);
+        __stcg(a.cpart + ct, c);
     }
-    __syncthreads();
 }
 
 template <typename T>
@@ -224,33 +244,42 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
     __shared__ T red[kPWarps * TILE];
     __shared__ double sd[32];
     __shared__ int si[32];
-    __shared__ double s_scal[4];
-    __shared__ int s_flag[4];
+    __shared__ double s_scal[2];
+    __shared__ int s_flag[2];
     const unsigned int G = gridDim.x;
     const int items = a.CT * a.R;
+    unsigned int bar = 0;  // completion count of the next barrier, minus G
 
     // prologue: mask of the start point
-    for (int ct = blockIdx.x; ct < a.CT; ct += G) tile_mask(a, ct, sd, si);
-    if (!grid_barrier(a.sync, G)) return;
+    for (int ct = blockIdx.x; ct < a.CT; ct += G) {
+        const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+        const bool in = threadIdx.x < TILE && i < a.n;
+        const T yi = in ? __ldcg(a.y + i) : T(0), gi = in ? __ldcg(a.g + i) : T(0);
+        tile_mask(a, ct, in, yi, gi, sd, si);
+    }
+    bool ok = grid_barrier(a.sync, bar += G);
 
     IterState* st = a.st;
     const double eps = st->eps;
     const int max_iter = st->max_iter, window = st->window;
     double best = 1.0 / 0.0;
-    int best_iter = 0;
-    int iter = 0;
-    long long sum_passive = 0, sum_clip = 0;
-    int status = ALN_RHS_MAXITER;
+    int best_iter = 0, iter = 0, status = ALN_RHS_MAXITER, cnt = 0;
     double gam = 0.0;
-    int cnt = 0;
-    bool timed_out = false;
+    long long sum_passive = 0, sum_clip = 0;
 
-    for (;;) {
+    while (ok) {
         // (a) stop test, identical in every block
         if (threadIdx.x < 32) {
-            const double g2 = warp_sum_cg(a.gpart, a.CT);
-            const int c2 = warp_sum_cg_i(a.cpart, a.CT);
-            if (threadIdx.x == 0) {
+            const int lane = threadIdx.x;
+            double g2 = 0.0;
+            int c2 = 0;
+            for (int i = lane; i < a.CT; i += 32) {
+                g2 += __ldcg(a.gpart + i);
+                c2 += __ldcg(a.cpart + i);
+            }
+            g2 = warp_sum(g2);
+            c2 = warp_sum_i(c2);
+            if (lane == 0) {
                 s_scal[0] = g2;
                 s_flag[0] = c2;
             }
@@ -271,39 +300,22 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
             best_iter = iter;
         }
 
-        // (b) w = Qḡ with per-tile completion
+        // (b) w-partials and curvature shares
         for (int it = blockIdx.x; it < items; it += G) {
             const int ct = it % a.CT, rg = it / a.CT;
-            mv_item(a, a.gb, ct, rg, red);
-            if (last_of_tile(a.ticket, ct, a.R)) {
-                double kap = 0.0;
-                if (threadIdx.x < TILE) {
-                    const int64_t i = (int64_t)ct * TILE + threadIdx.x;
-                    T wi = T(0);
-                    for (int r = 0; r < a.R; ++r) wi += __ldcg(a.part + (int64_t)r * a.ldq + i);
-                    __stcg(a.w + i, wi);
-                    if (i < a.n) kap = (double)__ldcg(a.gb + i) * (double)wi;
-                }
-                kap = warp_sum(kap);
-                if ((threadIdx.x & 31) == 0 && (threadIdx.x >> 5) < TILE / 32)
-                    sd[threadIdx.x >> 5] = kap;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double s = 0.0;
-                    for (int w2 = 0; w2 < TILE / 32; ++w2) s += sd[w2];
-                    __stcg(a.kpart + ct, s);
-                }
-                __syncthreads();
-            }
+            const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+            const T gbi = (threadIdx.x < TILE && i < a.n) ? __ldcg(a.gb + i) : T(0);
+            const T pw = mv_item(a, a.gb, ct, rg, red);
+            const double k = tile_sum<TILE>((double)gbi * (double)pw, sd);
+            if (threadIdx.x == 0) __stcg(a.kitem + it, k);
         }
-        if (!grid_barrier(a.sync, G)) {
-            timed_out = true;
-            break;
-        }
+        if (!(ok = grid_barrier(a.sync, bar += G))) break;
 
-        // (c) step size, projected update, gradient update, provisional mask
+        // (c) step, projection, gradient update, provisional mask
         if (threadIdx.x < 32) {
-            const double k2 = warp_sum_cg(a.kpart, a.CT);
+            double k2 = 0.0;
+            for (int i = threadIdx.x; i < items; i += 32) k2 += __ldcg(a.kitem + i);
+            k2 = warp_sum(k2);
             if (threadIdx.x == 0) s_scal[1] = k2;
         }
         __syncthreads();
@@ -316,37 +328,36 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
             status = ALN_RHS_CURVATURE;
             break;
         }
-        const double alpha = gam / kap;
+        const T aT = (T)(gam / kap);
         sum_passive += cnt;
-        const T aT = (T)alpha;
         for (int ct = blockIdx.x; ct < a.CT; ct += G) {
+            const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+            const bool in = threadIdx.x < TILE && i < a.n;
+            T yn = T(0), gn = T(0);
             int clipped = 0;
-            if (threadIdx.x < TILE) {
-                const int64_t i = (int64_t)ct * TILE + threadIdx.x;
-                if (i < a.n) {
-                    const T yi = __ldcg(a.y + i);
-                    const T step = aT * __ldcg(a.gb + i);
-                    T yn = yi - step;
-                    T ei = T(0);
-                    if (yn < T(0)) {
-                        ei = step - yi;
-                        yn = T(0);
-                        clipped = 1;
-                    }
-                    __stcg(a.y + i, yn);
-                    __stcg(a.e + i, ei);
-                    __stcg(a.g + i, __ldcg(a.g + i) - aT * __ldcg(a.w + i));
+            if (in) {
+                T wi = T(0);
+                for (int r = 0; r < a.R; ++r) wi += __ldcg(a.part + (int64_t)r * a.ldq + i);
+                const T yi = __ldcg(a.y + i);
+                const T step = aT * __ldcg(a.gb + i);
+                yn = yi - step;
+                T ei = T(0);
+                if (yn < T(0)) {
+                    ei = step - yi;
+                    yn = T(0);
+                    clipped = 1;
                 }
+                gn = __ldcg(a.g + i) - aT * wi;
+                __stcg(a.y + i, yn);
+                __stcg(a.e + i, ei);
+                __stcg(a.g + i, gn);
             }
             clipped = __syncthreads_count(clipped);
             if (threadIdx.x == 0) __stcg(a.clip + ct, clipped);
-            tile_mask(a, ct, sd, si);
+            tile_mask(a, ct, in, yn, gn, sd, si);
         }
         ++iter;
-        if (!grid_barrier(a.sync, G)) {
-            timed_out = true;
-            break;
-        }
+        if (!(ok = grid_barrier(a.sync, bar += G))) break;
 
         // (d) clipped correction g += Q e (only when something was clipped)
         if (threadIdx.x < 32) {
@@ -356,34 +367,47 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
             if (threadIdx.x == 0) s_flag[1] = c3;
         }
         __syncthreads();
-        sum_clip += s_flag[1];
-        if (s_flag[1] > 0) {
+        const int nclip = s_flag[1];
+        sum_clip += nclip;
+        if (nclip > 0) {
+            __shared__ int s_last;
             for (int it = blockIdx.x; it < items; it += G) {
                 const int ct = it % a.CT, rg = it / a.CT;
-                mv_item(a, a.e, ct, rg, red);
-                if (last_of_tile(a.ticket, ct, a.R)) {
-                    if (threadIdx.x < TILE) {
-                        const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+                (void)mv_item(a, a.e, ct, rg, red);
+                if (threadIdx.x == 0) {
+                    unsigned int t;
+                    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                                 : "=r"(t)
+                                 : "l"(a.ticket + ct), "r"(1u)
+                                 : "memory");
+                    s_last = t == (unsigned int)(a.R - 1);
+                    if (s_last) a.ticket[ct] = 0u;  // reset for the next correction
+                }
+                __syncthreads();
+                if (s_last) {
+                    const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+                    const bool in = threadIdx.x < TILE && i < a.n;
+                    T yi = T(0), gi = T(0);
+                    if (in) {
                         T ui = T(0);
                         for (int r = 0; r < a.R; ++r)
                             ui += __ldcg(a.part + (int64_t)r * a.ldq + i);
-                        if (i < a.n) __stcg(a.g + i, __ldcg(a.g + i) + ui);
+                        yi = __ldcg(a.y + i);
+                        gi = __ldcg(a.g + i) + ui;
+                        __stcg(a.g + i, gi);
                     }
-                    __syncthreads();
-                    tile_mask(a, ct, sd, si);
+                    tile_mask(a, ct, in, yi, gi, sd, si);
                 }
+                __syncthreads();
             }
-            if (!grid_barrier(a.sync, G)) {
-                timed_out = true;
-                break;
-            }
+            if (!(ok = grid_barrier(a.sync, bar += G))) break;
         }
     }
 
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->iter = iter;
         st->done = 1;
-        st->status = timed_out ? kStatusTimeout : status;
+        st->status = ok ? status : kStatusTimeout;
         st->gbar2 = gam;
         st->npassive = cnt;
         st->best_g2 = best;
@@ -393,9 +417,449 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
     }
 }
 
+// ===========================================================================
+// Replicated-state variant (n up to a few thousand): every block keeps the
+// whole of y, g, ḡ and w in shared memory and repeats the O(n) elementwise
+// work of (c) and the mask itself, in the same order, so every block holds
+// bitwise-identical vectors.  Only the products cross blocks: each work item
+// writes its partial of Qḡ and its curvature share, one grid barrier later
+// every block reads all partials (R·n values) and continues on its own.  An
+// iteration therefore costs ONE grid barrier (two when something is clipped:
+// Qe crosses blocks too).  The partial and curvature buffers alternate with
+// the iteration parity, because a block may start the next product while a
+// slower block still reads this one's partials; no block can run two
+// iterations ahead, since every iteration passes a barrier.
+// ===========================================================================
+template <typename T>
+struct ReplArgs {
+    const T* Q;
+    int64_t ldq;
+    int n;
+    int CT;
+    int R;
+    int rows_per_group;
+    T* y;            // in/out (global), ldq
+    T* g;            // in/out (global), ldq
+    T* part;         // 2 × R × ldq  (w partials, by iteration parity)
+    T* part2;        // R × ldq      (Qe partials)
+    double* kitem;   // 2 × CT·R     (curvature shares, by parity)
+    PersistSync* sync;
+    IterState* st;
+};
+
+// Partial Σ_{j ∈ group rg, v_j ≠ 0} v_j Q[j, tile ct] with v in shared memory;
+// written to dst[rg][tile]; returns the partial in threads < TILE.
+template <typename T>
+__device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, int n,
+                                         int rows_per_group, const T* v, int ct, int rg,
+                                         T* __restrict__ dst, T* red) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    constexpr int TILE = 32 * VN;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t col = (int64_t)ct * TILE + lane * VN;
+    const int g0 = rg * rows_per_group;
+    const int g1 = min(n, g0 + rows_per_group);
+    const int chunk = (g1 - g0 + kPWarps - 1) / kPWarps;
+    const int r0 = g0 + warp * chunk;
+    const int r1 = min(g1, r0 + chunk);
+    T acc[VN];
+#pragma unroll
+    for (int c = 0; c < VN; ++c) acc[c] = T(0);
+    for (int base = r0; base < r1; base += 32) {
+        const int jl = base + lane;
+        const T vl = jl < r1 ? v[jl] : T(0);
+        unsigned int m = __ballot_sync(0xffffffffu, vl != T(0));
+        while (m) {  // warp-uniform
+            T vv[kPU];
+            V qq[kPU];
+#pragma unroll
+            for (int u = 0; u < kPU; ++u) {
+                if (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    vv[u] = v[base + src];
+                    qq[u] = __ldg(reinterpret_cast<const V*>(Q + (int64_t)(base + src) * ldq + col));
+                } else {
+                    vv[u] = T(0);
+                    qq[u] = V{};
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPU; ++u)
+#pragma unroll
+                for (int c = 0; c < VN; ++c) acc[c] = fma(vv[u], vget(qq[u], c), acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < VN; ++c) red[warp * TILE + lane * VN + c] = acc[c];
+    __syncthreads();
+    T s = T(0);
+    if (threadIdx.x < TILE) {
+#pragma unroll 8
+        for (int w2 = 0; w2 < kPWarps; ++w2) s += red[w2 * TILE + threadIdx.x];
+        __stcg(dst + (int64_t)rg * ldq + (int64_t)ct * TILE + threadIdx.x, s);
+    }
+    __syncthreads();
+    return s;
+}
+
+// Block sums whose result every thread receives (fixed tree: warp shuffles,
+// then the warp sums in warp order).
+__device__ __forceinline__ double block_sum_bcast(double v, double* sc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sc[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sc[w2];
+    return s;
+}
+__device__ __forceinline__ int block_sum_bcast_i(int v, int* sc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_i(v);
+    __syncthreads();
+    if (lane == 0) sc[wid] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sc[w2];
+    return s;
+}
+
+// GB300's FP64 pipe is narrow: an FP64 instruction issued by all 1024
+// threads of a block costs microseconds.  The per-iteration reductions
+// therefore run in the iteration type T across lanes and warps, and only the
+// final sum over the warp partials (and any division) is done in FP64, by one
+// thread, then broadcast through shared memory.
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Sum of v over the block: a shuffle tree in each warp, then warp 0 folds
+// the warp partials with the same tree; every thread receives the result.
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* sc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_t(v);
+    __syncthreads();
+    if (lane == 0) sc[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T x = lane < (int)(blockDim.x >> 5) ? sc[lane] : T(0);
+        x = warp_sum_t(x);
+        if (lane == 0) sc[32] = x;
+    }
+    __syncthreads();
+    return sc[32];
+}
+
+// Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
+// (fixed reduction tree, identical in every block).
+template <typename T>
+__device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, T* st,
+                                         int* si, T* g2_out, int* cnt_out) {
+    T v = T(0);
+    int c = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const T yi = sy[j], gi = sg[j];
+        const bool P = yi > T(0) || gi < T(0);
+        const T gb = P ? gi : T(0);
+        sgb[j] = gb;
+        v = fma(gb, gb, v);
+        c += P ? 1 : 0;
+    }
+    *g2_out = block_sum_t<T>(v, st);
+    *cnt_out = block_sum_bcast_i(c, si);
+    __syncthreads();
+}
+
+constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
+
+// dst[j] (+)= Σ_r part[r][j] for j < n, r in order; four elements per thread
+// per pass so that their R loads are in flight together.
+template <typename T>
+__device__ __forceinline__ void sum_partials(const T* __restrict__ part, int R, int64_t ldq,
+                                             int n, T* dst, bool accumulate) {
+    for (int j0 = threadIdx.x; j0 < n; j0 += 4 * blockDim.x) {
+        T v[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 4
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j < n) v[u] += __ldcg(part + (int64_t)r * ldq + j);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * blockDim.x;
+            if (j < n) dst[j] = accumulate ? dst[j] + v[u] : v[u];
+        }
+    }
+}
+
+// Indices j < n with e_j ≠ 0 in increasing order into list[0..kLocalClip):
+// each warp scans a contiguous range, warp counts are prefix-summed.
+template <typename T>
+__device__ __forceinline__ void clipped_list(int n, const T* e, int* list, int* si) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (n + nw - 1) / nw;
+    const int j0 = wid * per, j1 = min(n, j0 + per);
+    int count = 0;
+    for (int b = j0; b < j1; b += 32) {
+        const int j = b + lane;
+        count += __popc(__ballot_sync(0xffffffffu, j < j1 && e[j] != T(0)));
+    }
+    __syncthreads();
+    if (lane == 0) si[wid] = count;
+    __syncthreads();
+    int base = 0;
+    for (int w2 = 0; w2 < wid; ++w2) base += si[w2];
+    for (int b = j0; b < j1; b += 32) {
+        const int j = b + lane;
+        const bool nz = j < j1 && e[j] != T(0);
+        const unsigned int m = __ballot_sync(0xffffffffu, nz);
+        const int idx = base + __popc(m & ((1u << lane) - 1u));
+        if (nz && idx < kLocalClip) list[idx] = j;
+        base += __popc(m);
+    }
+    __syncthreads();
+}
+
+// g[i] += Σ_k e[list[k]] · Q[list[k]][i] for all i < n (rows in list order).
+template <typename T>
+__device__ __forceinline__ void add_rows(const T* __restrict__ Q, int64_t ldq, int n,
+                                         const int* list, int count, const T* e, T* g) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    for (int i = threadIdx.x * VN; i < n; i += blockDim.x * VN) {
+        T acc[VN];
+#pragma unroll
+        for (int c = 0; c < VN; ++c) acc[c] = T(0);
+#pragma unroll
+        for (int k = 0; k < kLocalClip; ++k) {
+            if (k < count) {
+                const int j = list[k];
+                const V q = __ldg(reinterpret_cast<const V*>(Q + (int64_t)j * ldq + i));
+                const T ej = e[j];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) acc[c] = fma(ej, vget(q, c), acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < VN; ++c)
+            if (i + c < n) g[i + c] += acc[c];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
+    constexpr int TILE = 32 * Vec16<T>::N;
+    extern __shared__ __align__(16) uint8_t smraw[];
+    T* sy = reinterpret_cast<T*>(smraw);
+    T* sg = sy + a.ldq;
+    T* sgb = sg + a.ldq;
+    T* sw = sgb + a.ldq;     // w, then e
+    T* red = sw + a.ldq;     // kPWarps × TILE
+    __shared__ double sd[32];
+    __shared__ int si[32];
+    __shared__ T s_t[33];
+    __shared__ T s_alpha;
+    __shared__ int s_flag;   // 0 continue, 1 stop
+    __shared__ int s_clip[kLocalClip];
+    const unsigned int G = gridDim.x;
+    const int items = a.CT * a.R;
+    const int n = a.n;
+    unsigned int bar = 0;
+
+    for (int j = threadIdx.x; j < a.ldq; j += blockDim.x) {
+        sy[j] = j < n ? __ldcg(a.y + j) : T(0);
+        sg[j] = j < n ? __ldcg(a.g + j) : T(0);
+        sw[j] = T(0);
+    }
+    __syncthreads();
+    T gam;  // scalars in the iteration type: no FP64 chain on the critical path
+    int cnt;
+    mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+
+    // Scalar control state lives in thread 0 (FP64 compares and the division
+    // are issued once, not by every thread).
+    IterState* st = a.st;
+    const T eps = (T)st->eps;
+    const int max_iter = st->max_iter, window = st->window;
+    T best = T(1.0 / 0.0);
+    int best_iter = 0, iter = 0, status = ALN_RHS_MAXITER;
+    long long sum_passive = 0, sum_clip = 0;
+    uint64_t prof[5] = {0, 0, 0, 0, 0};  // block 0's phase times (ns)
+    int nclip_iters = 0;
+    bool ok = true;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int stop = 1;
+            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
+            else if (gam < eps || gam == T(0)) status = ALN_RHS_CONVERGED;
+            else if (iter >= max_iter) status = ALN_RHS_MAXITER;
+            else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
+            else stop = 0;
+            if (!stop && gam < best) {
+                best = gam;
+                best_iter = iter;
+            }
+            s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const int par = iter & 1;
+        T* part = a.part + (int64_t)par * a.R * a.ldq;
+        T* kitem = reinterpret_cast<T*>(a.kitem) + (int64_t)par * items;
+        uint64_t t_prev = timer ? p_globaltimer() : 0;
+        auto lap = [&](int k) {
+            if (timer) {
+                const uint64_t t = p_globaltimer();
+                prof[k] += t - t_prev;
+                t_prev = t;
+            }
+        };
+
+        // w-partials and curvature shares of this block's items
+        for (int it = blockIdx.x; it < items; it += G) {
+            const int ct = it % a.CT, rg = it / a.CT;
+            const T pw = mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red);
+            const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+            const T prod = (threadIdx.x < TILE && i < n) ? sgb[i] * pw : T(0);
+            const T k = block_sum_t<T>(prod, s_t);
+            if (threadIdx.x == 0) __stcg(kitem + it, k);
+        }
+        lap(0);
+        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        lap(1);
+
+        // every block: κ, w, α, projected update, gradient update
+        if (threadIdx.x < 32) {
+            T k2 = T(0);
+            for (int i = threadIdx.x; i < items; i += 32) k2 += __ldcg(kitem + i);
+            k2 = warp_sum_t(k2);
+            if (threadIdx.x == 0) {
+                int stop = 0;
+                if (!isfinite(k2)) {
+                    status = ALN_RHS_NONFINITE;
+                    stop = 1;
+                } else if (k2 <= T(0)) {
+                    status = ALN_RHS_CURVATURE;
+                    stop = 1;
+                }
+                s_alpha = stop ? T(0) : gam / k2;
+                s_flag = stop;
+            }
+        }
+        sum_partials(part, a.R, a.ldq, n, sw, false);
+        __syncthreads();
+        if (s_flag) break;
+        const T aT = s_alpha;
+        sum_passive += cnt;
+        int clipped = 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const T yi = sy[j];
+            const T step = aT * sgb[j];
+            T yn = yi - step;
+            T ej = T(0);
+            if (yn < T(0)) {
+                ej = step - yi;
+                yn = T(0);
+                ++clipped;
+            }
+            sy[j] = yn;
+            sg[j] = sg[j] - aT * sw[j];
+            sw[j] = ej;  // w is consumed; the buffer now holds e
+        }
+        const int nclip = block_sum_bcast_i(clipped, si);  // identical in every block
+        __syncthreads();
+        ++iter;
+        sum_clip += nclip;
+        lap(2);
+
+        if (nclip > 0 && nclip <= kLocalClip) {
+            // Few clipped rows: every block forms Qe itself from those rows
+            // of Q (listed in index order, so all blocks add in the same
+            // order) — no product pass over the grid and no barrier.
+            clipped_list(n, sw, s_clip, si);
+            add_rows(a.Q, a.ldq, n, s_clip, nclip, sw, sg);
+            __syncthreads();
+            ++nclip_iters;
+        } else if (nclip > 0) {
+            // Q e crosses blocks: partials, barrier, every block sums them
+            for (int it = blockIdx.x; it < items; it += G) {
+                const int ct = it % a.CT, rg = it / a.CT;
+                (void)mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2, red);
+            }
+            if (!(ok = grid_barrier(a.sync, bar += G))) break;
+            sum_partials(a.part2, a.R, a.ldq, n, sg, true);
+            __syncthreads();
+            ++nclip_iters;
+        }
+        lap(3);
+        mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+        lap(4);
+    }
+
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            a.y[j] = sy[j];
+            a.g[j] = sg[j];
+        }
+        if (threadIdx.x == 0) {
+            st->iter = iter;
+            st->done = 1;
+            st->status = ok ? status : kStatusTimeout;
+            st->gbar2 = (double)gam;
+            st->npassive = cnt;
+            st->best_g2 = (double)best;
+            st->best_iter = best_iter;
+            st->sum_passive = sum_passive;
+            st->sum_clip = sum_clip;
+            for (int k = 0; k < 5; ++k) st->phase_ns[k] = prof[k];
+            st->phase_ns[5] = (uint64_t)nclip_iters;  // iterations that took the clipped path
+        }
+    }
+}
+
+template <typename T>
+size_t repl_smem_bytes(int64_t ldq) {
+    return (size_t)(4 * ldq + kPWarps * 32 * Vec16<T>::N) * sizeof(T);
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_alg2_persist(aln_ctx* c) {
+    if (c->p_repl) {
+        ReplArgs<T> r;
+        r.Q = (const T*)c->Q;
+        r.ldq = c->ldq;
+        r.n = (int)c->n;
+        r.CT = c->p_CT;
+        r.R = c->p_R;
+        r.rows_per_group = (int)ceil_div(c->n, c->p_R);
+        r.y = (T*)c->y;
+        r.g = (T*)c->g;
+        r.part = (T*)c->part;
+        r.part2 = (T*)c->part + (int64_t)2 * c->p_R * c->ldq;
+        r.kitem = c->p_kpart;
+        r.sync = (PersistSync*)c->p_sync;
+        r.st = c->st;
+        const size_t smem = repl_smem_bytes<T>(c->ldq);
+        cudaError_t e = cudaFuncSetAttribute(k_alg2_repl<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        void* args[] = {&r};
+        return cudaLaunchCooperativeKernel((const void*)k_alg2_repl<T>, dim3(c->p_G),
+                                           dim3(kPThreads), args, smem, c->stream);
+    }
     PersistArgs<T> a;
     a.Q = (const T*)c->Q;
     a.ldq = c->ldq;
@@ -411,19 +875,38 @@ cudaError_t launch_alg2_persist(aln_ctx* c) {
     a.part = (T*)c->part;
     a.gpart = c->p_gpart;
     a.cpart = c->p_cpart;
-    a.kpart = c->p_kpart;
+    a.kitem = c->p_kpart;
     a.clip = c->p_clip;
     a.ticket = c->p_ticket;
     a.sync = (PersistSync*)c->p_sync;
     a.st = c->st;
+    if ((int64_t)a.CT * a.R > kMaxItems) return cudaErrorInvalidValue;
     void* args[] = {&a};
     return cudaLaunchCooperativeKernel((const void*)k_alg2_persist<T>, dim3(c->p_G),
                                        dim3(kPThreads), args, 0, c->stream);
 }
 
+// Co-resident blocks of the persistent kernel for row length ldq.  With
+// `repl`, the replicated-state kernel and its shared-memory footprint are
+// tried first; *repl is cleared when its state does not fit on an SM.
 template <typename T>
-int persist_max_blocks(int num_sms) {
+int persist_max_blocks(int num_sms, int64_t ldq, int* repl) {
     int per_sm = 0;
+    if (*repl) {
+        const size_t smem = repl_smem_bytes<T>(ldq);
+        int optin = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (smem + 4096 <= (size_t)optin &&
+            cudaFuncSetAttribute(k_alg2_repl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_alg2_repl<T>, kPThreads,
+                                                          smem) == cudaSuccess &&
+            per_sm > 0)
+            return per_sm * num_sms;
+        cudaGetLastError();
+        *repl = 0;
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_alg2_persist<T>, kPThreads, 0) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -434,8 +917,8 @@ int persist_max_blocks(int num_sms) {
 
 template cudaError_t launch_alg2_persist<float>(aln_ctx*);
 template cudaError_t launch_alg2_persist<double>(aln_ctx*);
-template int persist_max_blocks<float>(int);
-template int persist_max_blocks<double>(int);
+template int persist_max_blocks<float>(int, int64_t, int*);
+template int persist_max_blocks<double>(int, int64_t, int*);
 
 size_t persist_sync_bytes() { return sizeof(PersistSync); }
 
