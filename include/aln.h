@@ -93,7 +93,10 @@ typedef struct aln_options {
                              new smallest ‖ḡ‖² (§5 stop rule); 0 = default 100 */
     int32_t iter_kernel;  /* persistent Alg. 2 kernel: 0 auto (replicated state when
                              the vectors fit in shared memory), 1 tiled, 2 replicated */
-    int32_t reserved[2];
+    int32_t batch_min;    /* SPLIT_BF16 with at least this many right-hand sides
+                             runs the batched solver (all columns advance together,
+                             tcgen05 products Q·Ḡ); 0 = default 8 */
+    int32_t reserved;
 } aln_options;
 
 typedef struct aln_solve_info {

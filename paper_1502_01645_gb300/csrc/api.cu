@@ -229,6 +229,8 @@ void aln_default_options(aln_options* opt) {
     opt->persist_blocks = 0;
     opt->row_groups = 0;
     opt->stagnation = 100;
+    opt->iter_kernel = 0;
+    opt->batch_min = 8;
 }
 
 int32_t aln_version(void) { return ALN_VERSION; }
@@ -256,9 +258,10 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.precision != ALN_PREC_FP64 && o.precision != ALN_PREC_SPLIT_BF16)
         return ALN_ERR_INVALID_ARG;
     if (o.max_refine < 0 || o.persist_blocks < 0 || o.row_groups < 0 || o.stagnation < 0 ||
-        o.iter_kernel < 0 || o.iter_kernel > 2)
+        o.iter_kernel < 0 || o.iter_kernel > 2 || o.batch_min < 0)
         return ALN_ERR_INVALID_ARG;
     if (o.stagnation == 0) o.stagnation = 100;
+    if (o.batch_min == 0) o.batch_min = 8;
     aln_ctx* c = new (std::nothrow) aln_ctx();
     if (!c) return ALN_ERR_OUT_OF_MEMORY;
     c->opt = o;
@@ -312,6 +315,7 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
 void aln_destroy(aln_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    batch_free(c);
     void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -375,9 +379,14 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
         c->den_host_cap = k;
     }
 
+    // Many right-hand sides in mixed precision: the batched solver (batch.cu)
+    // forms Q in FP64 once (it also serves the FP64 checks) and iterates all
+    // columns together with tensor-core products.
+    c->batched = (!f64 && k >= c->opt.batch_min) ? 1 : 0;
+
     // split copies for the tensor-core Gram
     __nv_bfloat16 *hi = nullptr, *lo = nullptr;
-    if (!f64) {
+    if (!f64 && !c->batched) {
         c->ldk = round_up(d, 64);
         const size_t sb = (size_t)n * c->ldk * 2;
         ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 2 * round_up(sb, 1024)));
@@ -397,7 +406,9 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
                               c->stream));
     ALN_TRY(launch_denominators(c->q64, n, ldq, k, c->den, c->stream));
     ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
-    if (f64)
+    if (c->batched)
+        ALN_CHECK(batch_prepare(c));
+    else if (f64)
         ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
     else
         ALN_TRY(launch_gram_tc(hi, lo, d, n, c->ldk, c->inv_s, (float*)c->Q, ldq, c->flags + 1,
@@ -442,6 +453,14 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     for (double& v : c->stats.phase_us) v = 0.0;
     c->stats.iterations = 0;
     ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
+    if (c->batched) {
+        ALN_CHECK(batch_solve(c, tol, max_iter, X, ldx, X0, info));
+        ALN_TRY(cudaEventRecord(c->ev[5], c->stream));
+        ALN_TRY(cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) c->stats.solve_ms = ms;
+        return ALN_OK;
+    }
     // Inner runs stop a little below tol so that the FP64 check usually passes
     // at once; refinement rounds aim lower still.
     const double first_factor = 0.5, refine_factor = 0.25;

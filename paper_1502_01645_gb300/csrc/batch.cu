@@ -1,0 +1,669 @@
+// Alg. 2 (§3) on many right-hand sides that share A (the multi-RHS inner
+// solve of NMF, §1/§2.2): every column c has its own y_c, g_c, passive set,
+// step size and stop state, and one iteration of all running columns is
+//
+//   k_bmask   (one block per column) ḡ_c = g_c on P(y_c), γ_c = ‖ḡ_c‖²; the
+//             stop rules of Alg. 2 per column; running columns are compacted
+//             (atomic slot p) and ḡ_c is split into BF16 hi/lo row p;
+//   W = Q·Ḡ   (k_bgemm_tc, tcgen05, 3 split products) with the per-column
+//             curvature ḡ_cᵀw_c reduced in the epilogue;
+//   k_bupdate (one block per running column) α_c = γ_c/κ_c, y⁺ = [y − αḡ]₊,
+//             g ← g − α w, e = clipped part; columns with clipping are
+//             compacted again and e_c is split;
+//   U = Q·E   (k_bgemm_tc) added to g for the clipped columns only.
+//
+// The FP64 check of every column uses the FP64 scaled matrix Q64 and the
+// FP64 q: g64 = Q64 y + q (one FP64 product for all columns), then
+// rel_c = ‖ḡ64_c‖/‖min(q_c, 0)‖ and ½‖Ax − b‖² = ½yᵀg64 + ½qᵀy + ½‖b‖².
+// Columns above tol restart from y_c with g_c = g64_c (refinement).
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace aln {
+
+constexpr int kBThreads = 256;
+
+// Q (FP32, [n][ldq]) → hi/lo BF16 [n][ldk], zero-padded columns n..ldk.
+__global__ void k_qsplit(const double* __restrict__ Q64, int64_t ldq, int64_t n, int64_t ldk,
+                         float* __restrict__ Q32, __nv_bfloat16* __restrict__ hi,
+                         __nv_bfloat16* __restrict__ lo) {
+    const int64_t i = blockIdx.x;
+    for (int64_t j = threadIdx.x; j < ldk; j += blockDim.x) {
+        const float v = j < n ? (float)Q64[i * ldq + j] : 0.0f;
+        if (j < ldq) Q32[i * ldq + j] = v;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i * ldk + j] = h;
+        lo[i * ldk + j] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+__global__ void k_bnorm2(const void* __restrict__ B, int32_t dtype, int64_t d, int64_t ldb,
+                         double* __restrict__ out) {
+    __shared__ double sc[32];
+    const int64_t c = blockIdx.x;
+    double v = 0.0;
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+        const double b = dtype == ALN_DTYPE_F32 ? (double)((const float*)B)[c * ldb + t]
+                                                : ((const double*)B)[c * ldb + t];
+        v = fma(b, b, v);
+    }
+    v = block_sum(v, sc);
+    if (threadIdx.x == 0) out[c] = v;
+}
+
+struct BatchState {
+    int64_t n, ldq, ldk, k;
+    float* Y;             // [k][ldq]
+    float* G;             // [k][ldq]
+    float* GB;            // [k][ldq]
+    float* E;             // [k][ldq]
+    float* W;             // [k][ldq]  (compact rows)
+    __nv_bfloat16* Vhi;   // [k][ldk]  (compact rows)
+    __nv_bfloat16* Vlo;
+    double* kpart;        // [mtiles][k]
+    int mtiles;
+    int* colst;           // -1 running, otherwise the final aln_rhs_status
+    int* iters;
+    int* best_iter;
+    double* best;
+    double* eps;
+    double* gamma;
+    int* map_act;
+    int* map_clip;
+    int* counters;        // [0] running columns, [1] clipped columns
+    unsigned long long* rows;  // [0] Σ|P|, [1] Σ|C| over the run
+    int* limits;          // [0] max_iter, [1] stagnation window (set per solve)
+};
+
+__global__ void k_breset(int* counters) {
+    counters[0] = 0;
+    counters[1] = 0;
+}
+
+// One block per column: mask, γ, |P|, stop rules, compaction, split of ḡ.
+__global__ void __launch_bounds__(kBThreads) k_bmask(BatchState s) {
+    __shared__ double sc[32];
+    __shared__ int si[32];
+    __shared__ int s_slot;
+    const int64_t c = blockIdx.x;
+    if (s.colst[c] >= 0) return;
+    const float* y = s.Y + c * s.ldq;
+    const float* g = s.G + c * s.ldq;
+    float* gb = s.GB + c * s.ldq;
+    // FP32 partial sums (GB300's FP64 pipe is narrow); thread 0 adds the
+    // eight warp sums in FP64.
+    float vf = 0.0f;
+    int cnt = 0;
+    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+        const float yi = y[i], gi = g[i];
+        const bool P = yi > 0.0f || gi < 0.0f;
+        const float b = P ? gi : 0.0f;
+        gb[i] = b;
+        vf = fmaf(b, b, vf);
+        cnt += P ? 1 : 0;
+    }
+    double v = 0.0;
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vf += __shfl_xor_sync(0xffffffffu, vf, o);
+        const int x = warp_sum_i(cnt);
+        if (lane == 0) {
+            sc[wid] = (double)vf;
+            si[wid] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+                t += si[w2];
+                v += sc[w2];
+            }
+            cnt = t;
+        }
+    }
+    if (threadIdx.x == 0) {
+        int status = -1;
+        const int it = s.iters[c];
+        if (!isfinite(v)) status = ALN_RHS_NONFINITE;
+        else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
+        else if (v < s.eps[c] || v == 0.0) status = ALN_RHS_CONVERGED;
+        else if (it >= s.limits[0]) status = ALN_RHS_MAXITER;
+        else if (it - s.best_iter[c] > s.limits[1]) status = ALN_RHS_STAGNATED;
+        int slot = -1;
+        if (status >= 0) {
+            s.colst[c] = status;
+        } else {
+            if (v < s.best[c]) {
+                s.best[c] = v;
+                s.best_iter[c] = it;
+            }
+            s.gamma[c] = v;
+            slot = atomicAdd(&s.counters[0], 1);
+            s.map_act[slot] = (int)c;
+            atomicAdd(&s.rows[0], (unsigned long long)cnt);
+        }
+        s_slot = slot;
+    }
+    __syncthreads();
+    const int p = s_slot;
+    if (p < 0) return;
+    __nv_bfloat16* hi = s.Vhi + (int64_t)p * s.ldk;
+    __nv_bfloat16* lo = s.Vlo + (int64_t)p * s.ldk;
+    for (int64_t i = threadIdx.x; i < s.ldk; i += blockDim.x) {
+        const float b = i < s.n ? gb[i] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(b);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn(b - __bfloat162float(h));
+    }
+}
+
+// One block per running column (compact slot p): α, projection, g update, e.
+__global__ void __launch_bounds__(kBThreads) k_bupdate(BatchState s) {
+    __shared__ int si[32];
+    __shared__ int s_slot;
+    __shared__ float s_alpha;
+    const int p = blockIdx.x;
+    if (p >= s.counters[0]) return;
+    const int64_t c = s.map_act[p];
+    if (threadIdx.x == 0) {
+        double kap = 0.0;
+        for (int m = 0; m < s.mtiles; ++m) kap += s.kpart[(int64_t)m * s.k + p];
+        float a = 0.0f;
+        if (!isfinite(kap)) s.colst[c] = ALN_RHS_NONFINITE;
+        else if (kap <= 0.0) s.colst[c] = ALN_RHS_CURVATURE;
+        else a = (float)(s.gamma[c] / kap);
+        s_alpha = a;
+    }
+    __syncthreads();
+    const float a = s_alpha;
+    if (a == 0.0f) return;
+    float* y = s.Y + c * s.ldq;
+    float* g = s.G + c * s.ldq;
+    float* e = s.E + c * s.ldq;
+    const float* gb = s.GB + c * s.ldq;
+    const float* w = s.W + (int64_t)p * s.ldq;
+    int clipped = 0;
+    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+        const float yi = y[i];
+        const float step = a * gb[i];
+        float yn = yi - step, ei = 0.0f;
+        if (yn < 0.0f) {
+            ei = step - yi;
+            yn = 0.0f;
+            ++clipped;
+        }
+        y[i] = yn;
+        e[i] = ei;
+        g[i] = g[i] - a * w[i];
+    }
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int x = warp_sum_i(clipped);
+        if (lane == 0) si[wid] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += si[w2];
+            s.iters[c] += 1;
+            int slot = -1;
+            if (t > 0) {
+                slot = atomicAdd(&s.counters[1], 1);
+                s.map_clip[slot] = (int)c;
+                atomicAdd(&s.rows[1], (unsigned long long)t);
+            }
+            s_slot = slot;
+        }
+        __syncthreads();
+    }
+    const int q = s_slot;
+    if (q < 0) return;
+    __nv_bfloat16* hi = s.Vhi + (int64_t)q * s.ldk;
+    __nv_bfloat16* lo = s.Vlo + (int64_t)q * s.ldk;
+    for (int64_t i = threadIdx.x; i < s.ldk; i += blockDim.x) {
+        const float v = i < s.n ? e[i] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[i] = h;
+        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// Start state of every column: y = s·x0 (0 without a start point), g = q
+// (float), running, per-column ε.
+__global__ void k_binit(BatchState s, const double* __restrict__ q64, const double* __restrict__ x0,
+                        int64_t ldx0, const double* __restrict__ sc, const double* __restrict__ den,
+                        double tol_factor, int* __restrict__ rounds) {
+    const int64_t c = blockIdx.x;
+    for (int64_t i = threadIdx.x; i < s.ldq; i += blockDim.x) {
+        const bool in = i < s.n;
+        s.Y[c * s.ldq + i] = (in && x0) ? (float)(x0[c * ldx0 + i] * sc[i]) : 0.0f;
+        s.G[c * s.ldq + i] = in ? (float)q64[c * s.ldq + i] : 0.0f;
+        s.E[c * s.ldq + i] = 0.0f;
+    }
+    if (threadIdx.x == 0) {
+        const double t = tol_factor * (den[c] > 0.0 ? den[c] : 1.0);
+        s.eps[c] = t * t;
+        s.colst[c] = -1;
+        s.iters[c] = 0;
+        s.best[c] = 1.0 / 0.0;
+        s.best_iter[c] = 0;
+        rounds[c] = 0;
+    }
+}
+
+// x = y/s and y in FP64 for the check (Eq. Rescaling).
+__global__ void k_bunscale(BatchState s, const double* __restrict__ sc, double* __restrict__ X64,
+                           double* __restrict__ Y64) {
+    const int64_t c = blockIdx.x;
+    for (int64_t i = threadIdx.x; i < s.ldq; i += blockDim.x) {
+        const double y = i < s.n ? (double)s.Y[c * s.ldq + i] : 0.0;
+        Y64[c * s.ldq + i] = y;
+        X64[c * s.ldq + i] = i < s.n ? y / sc[i] : 0.0;
+    }
+}
+
+// One block per column: FP64 check from g64 = Q64 y + q.  Final statuses, or
+// refinement (g ← g64, new ε) while rounds remain.
+__global__ void __launch_bounds__(kBThreads) k_bcheck(
+    BatchState s, const double* __restrict__ G64, const double* __restrict__ Y64,
+    const double* __restrict__ q64, const double* __restrict__ bn2, const double* __restrict__ den,
+    double tol, double refine_factor, int max_refine, int* __restrict__ rounds,
+    int* __restrict__ final_status, double* __restrict__ rel_out, double* __restrict__ obj_out,
+    int* __restrict__ reactivated) {
+    __shared__ double sc[32];
+    const int64_t c = blockIdx.x;
+    if (final_status[c] >= 0) return;
+    const double* g = G64 + c * s.ldq;
+    const double* y = Y64 + c * s.ldq;
+    const double* q = q64 + c * s.ldq;
+    double gb2 = 0.0, yg = 0.0, qy = 0.0;
+    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
+        const double gi = g[i], yi = y[i];
+        const bool P = yi > 0.0 || gi < 0.0;
+        if (P) gb2 = fma(gi, gi, gb2);
+        yg = fma(yi, gi, yg);
+        qy = fma(q[i], yi, qy);
+    }
+    gb2 = block_sum(gb2, sc);
+    yg = block_sum(yg, sc);
+    qy = block_sum(qy, sc);
+    __shared__ int s_refine;
+    if (threadIdx.x == 0) {
+        const double num = sqrt(gb2);
+        const double rel = den[c] > 0.0 ? num / den[c] : num;
+        rel_out[c] = rel;
+        // ½‖Ax − b‖² = ½yᵀQy + qᵀy + ½‖b‖² = ½yᵀg64 + ½qᵀy + ½‖b‖²
+        obj_out[c] = 0.5 * yg + 0.5 * qy + 0.5 * bn2[c];
+        const int inner = s.colst[c];
+        int refine = 0;
+        if (rel <= tol) {
+            final_status[c] = inner == ALN_RHS_EMPTY_PASSIVE ? ALN_RHS_EMPTY_PASSIVE
+                                                             : ALN_RHS_CONVERGED;
+        } else if (inner == ALN_RHS_NONFINITE || inner == ALN_RHS_MAXITER ||
+                   s.iters[c] >= s.limits[0]) {
+            final_status[c] = inner == ALN_RHS_NONFINITE ? ALN_RHS_NONFINITE : ALN_RHS_MAXITER;
+        } else if (rounds[c] >= max_refine) {
+            final_status[c] = inner == ALN_RHS_STAGNATED ? ALN_RHS_STAGNATED : ALN_RHS_MAXITER;
+        } else {
+            refine = 1;
+            rounds[c] += 1;
+            const double t = refine_factor * tol * (den[c] > 0.0 ? den[c] : 1.0);
+            s.eps[c] = t * t;
+            s.colst[c] = -1;
+            s.best[c] = 1.0 / 0.0;
+            s.best_iter[c] = s.iters[c];
+            atomicAdd(reactivated, 1);
+        }
+        s_refine = refine;
+    }
+    __syncthreads();
+    if (s_refine)
+        for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) s.G[c * s.ldq + i] = (float)g[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct BatchWork {
+    int64_t k = 0, n = 0, ldq = 0, ldk = 0;
+    int mtiles = 0;
+    void* pool = nullptr;
+    size_t pool_bytes = 0;
+    double* Q64 = nullptr;
+    __nv_bfloat16* Qhi = nullptr;
+    __nv_bfloat16* Qlo = nullptr;
+    double* bn2 = nullptr;
+    double* X64 = nullptr;
+    double* Y64 = nullptr;
+    double* G64 = nullptr;
+    int* rounds = nullptr;
+    int* fin = nullptr;
+    double* rel = nullptr;
+    double* obj = nullptr;
+    int* react = nullptr;
+    int* host = nullptr;          // pinned: [0] running count, [1] re-activated
+    BatchState s{};
+    cudaGraphExec_t graph = nullptr;
+    int chunk = 8;
+};
+
+static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
+    const int64_t k = c->k, n = c->n, ldq = c->ldq, ldk = round_up(n, 64);
+    b->k = k;
+    b->n = n;
+    b->ldq = ldq;
+    b->ldk = ldk;
+    b->mtiles = (int)ceil_div(n, 128);
+    const size_t f = (size_t)k * ldq * 4, d8 = (size_t)k * ldq * 8;
+    // One entry per buffer, in the order they are carved out below; each is
+    // rounded to 256 bytes exactly as take() rounds it.
+    const size_t sizes[] = {
+        (size_t)ldq * ldq * 8,                               // Q64
+        (size_t)n * ldk * 2, (size_t)n * ldk * 2,            // Qhi, Qlo
+        (size_t)k * 8,                                       // bn2
+        d8, d8, d8,                                          // X64, Y64, G64
+        f, f, f, f, f,                                       // Y, G, GB, E, W
+        (size_t)k * ldk * 2, (size_t)k * ldk * 2,            // Vhi, Vlo
+        (size_t)b->mtiles * k * 8,                           // kpart
+        (size_t)k * 4, (size_t)k * 4, (size_t)k * 4,         // colst, iters, best_iter
+        (size_t)k * 4, (size_t)k * 4, (size_t)k * 4,         // map_act, map_clip, rounds
+        (size_t)k * 8, (size_t)k * 8, (size_t)k * 8,         // best, eps, gamma
+        (size_t)k * 4, (size_t)k * 8, (size_t)k * 8,         // fin, rel, obj
+        64, 64, 64, 64};                                     // counters, rows, limits, react
+    size_t total = 0;
+    for (size_t x : sizes) total += round_up(x, 256);
+    if (b->pool_bytes < total) {
+        if (b->pool) cudaFree(b->pool);
+        b->pool = nullptr;
+        b->pool_bytes = 0;
+        if (cudaMalloc(&b->pool, total) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        b->pool_bytes = total;
+    }
+    uint8_t* p = (uint8_t*)b->pool;
+    uint8_t* const end = p + total;
+    int taken = 0;
+    auto take = [&](size_t x) {
+        // the carve-out must follow `sizes` entry by entry
+        if (taken >= (int)(sizeof(sizes) / sizeof(sizes[0])) || sizes[taken] != x) return (void*)nullptr;
+        ++taken;
+        void* r = p;
+        p += round_up(x, 256);
+        return p <= end ? r : (void*)nullptr;
+    };
+    b->Q64 = (double*)take((size_t)ldq * ldq * 8);
+    b->Qhi = (__nv_bfloat16*)take((size_t)n * ldk * 2);
+    b->Qlo = (__nv_bfloat16*)take((size_t)n * ldk * 2);
+    b->bn2 = (double*)take((size_t)k * 8);
+    b->X64 = (double*)take(d8);
+    b->Y64 = (double*)take(d8);
+    b->G64 = (double*)take(d8);
+    BatchState& s = b->s;
+    s.n = n;
+    s.ldq = ldq;
+    s.ldk = ldk;
+    s.k = k;
+    s.mtiles = b->mtiles;
+    s.Y = (float*)take(f);
+    s.G = (float*)take(f);
+    s.GB = (float*)take(f);
+    s.E = (float*)take(f);
+    s.W = (float*)take(f);
+    s.Vhi = (__nv_bfloat16*)take((size_t)k * ldk * 2);
+    s.Vlo = (__nv_bfloat16*)take((size_t)k * ldk * 2);
+    s.kpart = (double*)take((size_t)b->mtiles * k * 8);
+    s.colst = (int*)take((size_t)k * 4);
+    s.iters = (int*)take((size_t)k * 4);
+    s.best_iter = (int*)take((size_t)k * 4);
+    s.map_act = (int*)take((size_t)k * 4);
+    s.map_clip = (int*)take((size_t)k * 4);
+    b->rounds = (int*)take((size_t)k * 4);
+    s.best = (double*)take((size_t)k * 8);
+    s.eps = (double*)take((size_t)k * 8);
+    s.gamma = (double*)take((size_t)k * 8);
+    b->fin = (int*)take((size_t)k * 4);
+    b->rel = (double*)take((size_t)k * 8);
+    b->obj = (double*)take((size_t)k * 8);
+    s.counters = (int*)take(64);
+    s.rows = (unsigned long long*)take(64);
+    s.limits = (int*)take(64);
+    b->react = (int*)take(64);
+    if (!b->react || taken != (int)(sizeof(sizes) / sizeof(sizes[0])))
+        return ALN_ERR_CUDA;  // layout and size table disagree: never launch on it
+    if (cudaMemsetAsync(b->pool, 0, b->pool_bytes, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
+    return ALN_OK;
+}
+
+static cudaError_t bw_iteration(aln_ctx* c, BatchWork* b) {
+    BatchState& s = b->s;
+    k_breset<<<1, 1, 0, c->stream>>>(s.counters);
+    k_bmask<<<(unsigned)b->k, kBThreads, 0, c->stream>>>(s);
+    cudaError_t e = launch_bgemm_tc(0, b->Qhi, b->Qlo, b->n, b->ldk, s.Vhi, s.Vlo, b->k,
+                                    s.counters, s.map_act, b->ldq, s.W, s.GB, s.kpart, nullptr,
+                                    c->flags + 1, c->stream);
+    if (e != cudaSuccess) return e;
+    k_bupdate<<<(unsigned)b->k, kBThreads, 0, c->stream>>>(s);
+    return launch_bgemm_tc(1, b->Qhi, b->Qlo, b->n, b->ldk, s.Vhi, s.Vlo, b->k, s.counters + 1,
+                           s.map_clip, b->ldq, nullptr, nullptr, nullptr, s.G, c->flags + 1,
+                           c->stream);
+}
+
+static aln_status bw_capture(aln_ctx* c, BatchWork* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return ALN_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->chunk && e == cudaSuccess; ++i) e = bw_iteration(c, b);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return ALN_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? ALN_OK : ALN_ERR_CUDA;
+}
+
+void batch_free(aln_ctx* c) {
+    BatchWork* b = (BatchWork*)c->batch;
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->pool) cudaFree(b->pool);
+    if (b->host) cudaFreeHost(b->host);
+    delete b;
+    c->batch = nullptr;
+}
+
+// Alg. 1 for a batch: s and q in FP64 (prepare kernels), Q64 in FP64 (kept for
+// the checks), Q in FP32 and its BF16 split for the tensor-core iteration.
+aln_status batch_prepare(aln_ctx* c) {
+    BatchWork* b = (BatchWork*)c->batch;
+    if (!b) {
+        b = new (std::nothrow) BatchWork();
+        if (!b) return ALN_ERR_OUT_OF_MEMORY;
+        c->batch = b;
+        if (cudaMallocHost(&b->host, 64) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+    }
+    aln_status st = bw_alloc(c, b);
+    if (st != ALN_OK) return st;
+    if (launch_gram64(c->A, c->dtype, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq, c->stream) !=
+        cudaSuccess)
+        return ALN_ERR_CUDA;
+    k_qsplit<<<(unsigned)c->n, kBThreads, 0, c->stream>>>(b->Q64, c->ldq, c->n, b->ldk,
+                                                        (float*)c->Q, b->Qhi, b->Qlo);
+    k_bnorm2<<<(unsigned)c->k, kBThreads, 0, c->stream>>>(c->B, c->dtype, c->d, c->ldb, b->bn2);
+    c->launches += 3;
+    if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
+    return bw_capture(c, b);
+}
+
+// g = float(g64) for every column (start point given).
+__global__ void k_bsetg(BatchState s, const double* __restrict__ G64) {
+    const int64_t c = blockIdx.x;
+    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x)
+        s.G[c * s.ldq + i] = (float)G64[c * s.ldq + i];
+}
+
+static aln_status cuda_st(cudaError_t e) { return e == cudaSuccess ? ALN_OK : ALN_ERR_CUDA; }
+
+// FP64 check of every not-yet-final column; returns how many were restarted.
+static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine, int* restarted) {
+    BatchState& s = b->s;
+    const int64_t k = b->k;
+    cudaEventRecord(c->ev[6], c->stream);
+    k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
+    if (launch_gemm64_axpy(b->Q64, c->ldq, b->Y64, c->ldq, c->n, c->n, k, c->q64, b->G64, c->ldq,
+                           c->stream) != cudaSuccess)
+        return ALN_ERR_CUDA;
+    cudaMemsetAsync(b->react, 0, sizeof(int), c->stream);
+    k_bcheck<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64, b->Y64, c->q64, b->bn2, c->den,
+                                                       tol, 0.25, max_refine, b->rounds, b->fin,
+                                                       b->rel, b->obj, b->react);
+    cudaEventRecord(c->ev[7], c->stream);
+    c->launches += 3;
+    if (cudaMemcpyAsync(b->host + 1, b->react, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return ALN_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]) == cudaSuccess) c->stats.kkt_ms += ms;
+    *restarted = b->host[1];
+    return ALN_OK;
+}
+
+static bool dev_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t ldx,
+                       const double* X0, aln_solve_info* info) {
+    BatchWork* b = (BatchWork*)c->batch;
+    BatchState& s = b->s;
+    const int64_t k = b->k;
+    const double* X0dev = nullptr;
+    if (X0) {  // stage the start points in X64 (ld = ldq) and check them
+        if (cudaMemcpy2DAsync(b->X64, c->ldq * 8, X0, ldx * 8, c->n * 8, k,
+                              dev_ptr(X0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream) != cudaSuccess)
+            return ALN_ERR_CUDA;
+        cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream);
+        if (launch_check_finite(b->X64, ALN_DTYPE_F64, c->n, k, c->ldq, c->flags, c->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(c->flags_host, c->flags, sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return ALN_ERR_CUDA;
+        if (c->flags_host[0]) return ALN_ERR_NONFINITE;
+        X0dev = b->X64;
+    }
+    // per-solve limits live in device memory (the graph holds the state by value)
+    int lim[2] = {max_iter, c->opt.stagnation};
+    if (cudaMemcpyAsync(s.limits, lim, sizeof(lim), cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+        return ALN_ERR_CUDA;
+    k_binit<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->q64, X0dev, c->ldq, c->s, c->den,
+                                                      0.5 * tol, b->rounds);
+    cudaMemsetAsync(b->fin, 0xff, (size_t)k * 4, c->stream);  // -1: not final yet
+    cudaMemsetAsync(s.rows, 0, 16, c->stream);
+    c->launches += 1;
+    if (X0dev) {  // g = Q y0 + q, in FP64, for a start point
+        k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
+        if (launch_gemm64_axpy(b->Q64, c->ldq, b->Y64, c->ldq, c->n, c->n, k, c->q64, b->G64,
+                               c->ldq, c->stream) != cudaSuccess)
+            return ALN_ERR_CUDA;
+        k_bsetg<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64);
+        c->launches += 3;
+    }
+    const int max_refine = c->opt.max_refine;
+    for (int round = 0;; ++round) {
+        // inner runs: the captured chunk until no column is running
+        const int64_t bound = max_iter / b->chunk + 3;
+        int64_t l = 0;
+        cudaEventRecord(c->ev[8], c->stream);
+        for (; l < bound; ++l) {
+            if (cudaGraphLaunch(b->graph, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
+            c->launches += 5LL * b->chunk;
+            if (cudaMemcpyAsync(b->host, s.counters, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return ALN_ERR_CUDA;
+            if (b->host[0] == 0) break;
+        }
+        cudaEventRecord(c->ev[9], c->stream);
+        cudaEventSynchronize(c->ev[9]);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
+            c->stats.iterate_ms += ms;
+        if (l == bound) return ALN_ERR_TIMEOUT;
+        int restarted = 0;
+        aln_status st = bw_check(c, b, tol, max_refine, &restarted);
+        if (st != ALN_OK) return st;
+        if (restarted == 0) break;
+    }
+    // results: x (FP64) and per-column records
+    const bool x_dev = [&] {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, X) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    }();
+    if (cudaMemcpy2DAsync(X, ldx * 8, b->X64, c->ldq * 8, c->n * 8, k,
+                          x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess)
+        return ALN_ERR_CUDA;
+    unsigned long long rows[2] = {0, 0};
+    cudaMemcpyAsync(rows, s.rows, sizeof(rows), cudaMemcpyDeviceToHost, c->stream);
+    if (info) {
+        int* tmp_i = new (std::nothrow) int[3 * k];
+        double* tmp_d = new (std::nothrow) double[2 * k];
+        if (!tmp_i || !tmp_d) {
+            delete[] tmp_i;
+            delete[] tmp_d;
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        cudaMemcpyAsync(tmp_i, s.iters, k * 4, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(tmp_i + k, b->fin, k * 4, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(tmp_i + 2 * k, b->rounds, k * 4, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(tmp_d, b->rel, k * 8, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(tmp_d + k, b->obj, k * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            delete[] tmp_i;
+            delete[] tmp_d;
+            return ALN_ERR_CUDA;
+        }
+        int64_t total = 0;
+        for (int64_t j = 0; j < k; ++j) {
+            info[j].iters = tmp_i[j];
+            info[j].status = tmp_i[k + j];
+            info[j].refine_rounds = tmp_i[2 * k + j];
+            info[j].reserved = 0;
+            info[j].rel_kkt = tmp_d[j];
+            info[j].objective = tmp_d[k + j];
+            total += tmp_i[j];
+        }
+        c->stats.iterations = total;
+        delete[] tmp_i;
+        delete[] tmp_d;
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ALN_ERR_CUDA;
+    c->stats.passive_rows = (int64_t)rows[0];
+    c->stats.clipped_rows = (int64_t)rows[1];
+    return ALN_OK;
+}
+
+}  // namespace aln

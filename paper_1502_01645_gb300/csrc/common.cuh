@@ -204,8 +204,12 @@ struct aln_ctx {
     unsigned int* p_ticket = nullptr;
     void* p_sync = nullptr;
 
+    // many right-hand sides sharing A (batch.cu); null when not in batch mode
+    void* batch = nullptr;
+    int batched = 0;
+
     // statistics (aln_get_stats)
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
     aln_stats stats = {};
     int64_t launches = 0;
 };

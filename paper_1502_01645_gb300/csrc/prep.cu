@@ -206,8 +206,10 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
                 if (i == j) v = acc[a][b] != 0.0 ? 1.0 : 0.0;
                 out[i * ldo + j] = v;
                 out[j * ldo + i] = v;
-            } else {
+            } else if (MODE == MODE_QVEC) {
                 out[j * ldo + i] = -acc[a][b] * inv_s[i];
+            } else {  // MODE_AXPY: out = X^T Y + add (inv_s carries `add`)
+                out[j * ldo + i] = acc[a][b] + inv_s[j * ldo + i];
             }
         }
     }
@@ -275,6 +277,17 @@ cudaError_t launch_gram64(const void* A, int32_t dtype, int64_t d, int64_t n, in
     else
         k_atb64<double, double, MODE_GRAM><<<(unsigned)tiles, 256, 0, st>>>(
             (const double*)A, lda, (const double*)A, lda, d, n, n, (int)tm, inv_s, Q, ldq);
+    return cudaGetLastError();
+}
+
+// out[c][i] = Σ_t X[i][t] Y[c][t] + add[c][i]  (FP64; X = Q64 symmetric, so
+// this is Q·y_c + q_c for every column c).
+cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                               int64_t K, int64_t M, int64_t N, const double* add, double* out,
+                               int64_t ldo, cudaStream_t st) {
+    const int64_t tm = ceil_div(M, kG64Tile), tn = ceil_div(N, kG64Tile);
+    k_atb64<double, double, MODE_AXPY><<<(unsigned)(tm * tn), 256, 0, st>>>(
+        X, ldx, Y, ldy, K, M, N, (int)tm, add, out, ldo);
     return cudaGetLastError();
 }
 

@@ -284,3 +284,56 @@ def test_multiple_rhs_each_match_oracle(aln):
         b64 = p.B[c].astype(np.float64)
         x_star, _, _, _ = O.reference_solution(A64, b64)
         _mixed_gate(p.A, p.B[c], X[c], x_star)
+
+
+# ------------------------------------------------------------- batched solver
+def test_batched_multi_rhs_matches_oracle(aln):
+    """Many RHS sharing A (NMF inner-solve shape): the batched tensor-core
+    solver meets the mixed-precision gates on every column."""
+    p = W.shared_multi_rhs(d=1500, n=300, k=40, seed=34)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.A, p.B)
+        X, info = s.solve(tol=1e-9)
+        Xb, infob = s.solve(tol=1e-6)
+    A64 = p.A.astype(np.float64)
+    for c in range(p.k):
+        b64 = p.B[c].astype(np.float64)
+        x_star, _, _, _ = O.reference_solution(A64, b64)
+        _mixed_gate(p.A, p.B[c], X[c], x_star)
+        rel, F = O.kkt_residual(A64, b64, Xb[c])
+        assert rel <= 1e-6
+        np.testing.assert_allclose(infob[c].rel_kkt, rel, rtol=1e-8, atol=1e-14)
+        np.testing.assert_allclose(infob[c].objective, F, rtol=1e-9)
+
+
+def test_batched_agrees_with_single_rhs_path(aln):
+    p = W.shared_multi_rhs(d=800, n=200, k=12, seed=35)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.A, p.B)
+        Xb, ib = s.solve(tol=1e-9)
+    with aln.Solver("split_bf16", batch_min=10 ** 6) as s:
+        s.prepare(p.A, p.B)
+        Xs, is_ = s.solve(tol=1e-9)
+    for c in range(p.k):
+        assert np.linalg.norm(Xb[c] - Xs[c]) <= 2e-5 * np.linalg.norm(Xs[c])
+
+
+def test_batched_edge_columns(aln):
+    """Zero RHS (x = 0 at once), ragged n across tiles, a start point."""
+    r = np.random.default_rng(36)
+    d, n, k = 500, 131, 20
+    A = np.asfortranarray(r.random((d, n)).astype(np.float32))
+    X_true = np.where(r.random((k, n)) < 0.7, 0.0, r.random((k, n)))
+    B = (X_true @ A.astype(np.float64).T + 0.01 * r.standard_normal((k, d))).astype(np.float32)
+    B[3] = -np.abs(B[3])            # Aᵀb ≤ 0: optimum 0, empty passive set
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, B)
+        X, info = s.solve(tol=1e-8)
+        assert info[3].iters == 0 and info[3].status == aln.RHS_EMPTY_PASSIVE
+        assert np.all(X[3] == 0.0)
+        X2, info2 = s.solve(tol=1e-8, X0=X.copy())
+    A64 = A.astype(np.float64)
+    for c in range(k):
+        rel, _ = O.kkt_residual(A64, B[c].astype(np.float64), X[c])
+        assert rel <= 1e-8
+        assert info2[c].iters <= max(3, info[c].iters // 4)
