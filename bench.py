@@ -1,16 +1,22 @@
 #!/usr/bin/env python
 """Benchmark: NNLS solves/s of the anti-lopsided method on one GB300.
 
-One step = one whole solve of the lopsided single-RHS workload (A 20000×5000
-FP32 with log-uniform column scales, x_true 70% zeros, 1% noise): Alg. 1's
-prepare (scale factors, Aᵀb, split-BF16 tensor-core Gram → Q) plus Alg. 2 in
-FP32 to FP64 relative KKT ≤ 1e-6, including the FP64 KKT evaluation from A.
+Default workload (the one the headline metric is quoted on): one step = one
+whole solve of the lopsided single-RHS problem (A 20000×5000 FP32 with
+log-uniform column scales, x_true 70% zeros, 1% noise): Alg. 1's prepare
+(scale factors, Aᵀb, split-BF16 tensor-core Gram → Q) plus Alg. 2 in FP32 to
+FP64 relative KKT ≤ 1e-6, including the FP64 KKT evaluation from A.
+
+Other workloads (--workload): `shared_multi_rhs` (A 10000×1000 shared by 4096
+right-hand sides; one step = the whole batch) and `uniform_small` (A 1000×200,
+plain FP64 method at rel KKT 1e-10).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
 
 Prints one JSON line (rank 0).  Under torchrun each rank solves its own
-replica (the single-RHS path has no exchange step: replicas only) and `value`
-counts all ranks' solves over the slowest rank's time.
+replica (no exchange step on the data path: replicas only) and `value` counts
+all ranks' solves over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -28,11 +34,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "NNLS solves/s at rel KKT ≤1e-6, chosen form vs plain FP64 on one GB300"
 UNIT = "solves/s"
-D, N, TOL, SEED = 20000, 5000, 1e-6, 1002
-WORKLOAD_FMT = ("lopsided_single_{d}x{n}_f32: A U[0,1] x log-uniform column scales [1e-2,1e2], "
-                "x_true 70% zeros Exp(1), b = A x_true + 1% Gaussian noise")
-WORKLOAD = WORKLOAD_FMT.format(d=D, n=N)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+WORKLOADS = {
+    # name: (generator kwargs, tol, precision of the chosen form, description)
+    "lopsided_single": dict(
+        d=20000, n=5000, k=1, tol=1e-6, seed=1002, prec="split_bf16",
+        desc="lopsided_single_{d}x{n}_f32: A U[0,1] x log-uniform column scales [1e-2,1e2], "
+             "x_true 70% zeros Exp(1), b = A x_true + 1% Gaussian noise"),
+    "shared_multi_rhs": dict(
+        d=10000, n=1000, k=4096, tol=1e-6, seed=1003, prec="split_bf16",
+        desc="shared_multi_rhs_{d}x{n}_k{k}_f32: A U[0,1]; B = A X_true + 1% noise, X_true 80% "
+             "zeros Gamma(2,1); all right-hand sides solved together"),
+    "uniform_small": dict(
+        d=1000, n=200, k=1, tol=1e-10, seed=1001, prec="fp64",
+        desc="uniform_small_{d}x{n}_f64: A U[0,1], x_true half zeros U[0,1], "
+             "b = A x_true + N(0, 0.01^2); plain FP64 method"),
+}
 
 
 def parse():
@@ -41,12 +59,34 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lopsided_single")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--d", type=int, default=D, help="rows of A (smaller values: profiling cases)")
-    ap.add_argument("--n", type=int, default=N, help="columns of A")
+    ap.add_argument("--d", type=int, default=None, help="rows of A (profiling cases)")
+    ap.add_argument("--n", type=int, default=None, help="columns of A")
+    ap.add_argument("--k", type=int, default=None, help="right-hand sides")
     return ap.parse_args()
+
+
+def workload(args):
+    w = dict(WORKLOADS[args.workload])
+    for key in ("d", "n", "k"):
+        v = getattr(args, key)
+        if v is not None:
+            w[key] = v
+    w["name"] = args.workload
+    w["desc"] = w["desc"].format(**w)
+    return w
+
+
+def generate(w, rank=0):
+    from paper_1502_01645_gb300 import workloads as W
+    if w["name"] == "lopsided_single":
+        return W.lopsided_single(d=w["d"], n=w["n"], seed=w["seed"] + rank)
+    if w["name"] == "shared_multi_rhs":
+        return W.shared_multi_rhs(d=w["d"], n=w["n"], k=w["k"], seed=w["seed"] + rank)
+    return W.uniform_small(d=w["d"], n=w["n"], seed=w["seed"] + rank)
 
 
 def peaks():
@@ -109,22 +149,6 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------- CPU oracle
-def cpu_baseline_sample(A, b, m):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    NNLS sub-problem on the first m columns of A (same d, same b) to rel KKT
-    1e-6.  Gram and the dense Alg. 2 products of the oracle scale as n², so the
-    full-size time is estimated as t_sample·(n/m)²."""
-    import numpy as np
-    from oracle import nnls as O
-    A64 = np.asarray(A[:, :m], dtype=np.float64, order="F")
-    b64 = np.asarray(b, dtype=np.float64)
-    t0 = time.perf_counter()
-    x, res, _ = O.antilop(A64, b64, tol=TOL)
-    t = time.perf_counter() - t0
-    scale = (A.shape[1] / m) ** 2
-    return t, scale, res.iters
-
-
 def blas_threads():
     for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(v):
@@ -135,31 +159,59 @@ def blas_threads():
     return os.cpu_count()
 
 
+def cpu_sample(w, p):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload.
+
+    Single RHS: the NNLS sub-problem on the first m = n/2 columns of A (same d
+    and b), solved to the workload's tolerance; the oracle's Gram and dense
+    Alg. 2 products grow as n², so the full-size time is t·(n/m)².
+    Many RHS: the first 16 right-hand sides on the full A, time ×(k/16).
+    Returns (seconds for one full step, description)."""
+    import numpy as np
+    from oracle import nnls as O
+    if w["k"] == 1:
+        m = max(1, w["n"] // 2)
+        A64 = np.asarray(p.A[:, :m], dtype=np.float64, order="F")
+        b64 = np.asarray(p.B[0], dtype=np.float64)
+        t0 = time.perf_counter()
+        O.antilop(A64, b64, tol=w["tol"])
+        t = time.perf_counter() - t0
+        scale = (w["n"] / m) ** 2
+        return t * scale, (f"oracle antilop on A[:, :{m}] (d={w['d']}) in {t:.2f} s, "
+                           f"x (n/m)^2 = {scale:.0f} for the full size")
+    A64 = np.asarray(p.A, dtype=np.float64, order="F")
+    s = 16
+    t0 = time.perf_counter()
+    for c in range(s):
+        O.antilop(A64, p.B[c].astype(np.float64), tol=w["tol"])
+    t = time.perf_counter() - t0
+    return t * w["k"] / s, (f"oracle antilop on the first {s} of {w['k']} right-hand sides "
+                            f"in {t:.2f} s, x k/{s} for the batch")
+
+
 # ------------------------------------------------------------------- reference
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_1502_01645_gb300 import workloads as W
-    p = W.lopsided_single(d=D, n=N, seed=SEED)
-    m = N // 2
-    times = []
+    w = workload(args)
+    p = generate(w)
+    times, desc = [], ""
     for i in range(args.warmup + args.steps):
-        t, scale, iters = cpu_baseline_sample(p.A, p.B[0], m)
+        t, desc = cpu_sample(w, p)
         if i >= args.warmup:
-            times.append(t * scale)
+            times.append(t)
     per = sum(times) / len(times)
-    value = 1.0 / per
-    cores = blas_threads()
+    value = w["k"] / per
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "d": D, "n": N, "tol": TOL, "seed": SEED},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"oracle antilop on A[:, :{m}] (d={D}), time x (n/m)^2 = "
-                                   f"{(N / m) ** 2:.0f}"},
+        "config": {"workload": w["desc"], "d": w["d"], "n": w["n"], "k": w["k"],
+                   "tol": w["tol"], "seed": w["seed"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                         "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -179,23 +231,24 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    from paper_1502_01645_gb300 import aln, build_lib, workloads as W
+    from paper_1502_01645_gb300 import aln, build_lib
     build_lib.build()
     aln.load()
 
-    p = W.lopsided_single(d=D, n=N, seed=SEED + rank)
-    A_np, b_np = p.A, p.B[0]
+    w = workload(args)
+    d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
+    p = generate(w, rank)
+    A_np, B_np = p.A, p.B
     At = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()  # (d, n) column-major
-    bt = torch.from_numpy(np.ascontiguousarray(b_np[None, :])).cuda()
-    Xt = torch.zeros((1, N), dtype=torch.float64, device="cuda")
+    Bt = torch.from_numpy(np.ascontiguousarray(B_np)).cuda()
+    Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver("split_bf16", stream=stream.cuda_stream)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
 
     def step():
-        solver.prepare(At, bt)
-        _, info = solver.solve(tol=TOL, X=Xt)
-        st = solver.stats()
-        return info[0], st
+        solver.prepare(At, Bt)
+        _, info = solver.solve(tol=tol, X=Xt)
+        return info, solver.stats()
 
     for _ in range(args.warmup):
         step()
@@ -213,79 +266,84 @@ def run_ours(args):
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    infos, gram_ms, prep_ms, solve_ms, kkt_ms, iters = [], [], [], [], [], []
-    iter_ms, qrows = [], []
+    stats, worst, iters = [], 0.0, []
     for _ in range(args.steps):
         info, st = step()
-        infos.append(info)
-        gram_ms.append(st.gram_ms)
-        prep_ms.append(st.prepare_ms)
-        solve_ms.append(st.solve_ms)
-        kkt_ms.append(st.kkt_ms)
-        iter_ms.append(st.iterate_ms)
-        qrows.append(st.passive_rows + st.clipped_rows)
-        iters.append(info.iters)
+        stats.append(st)
+        worst = max(worst, max(i.rel_kkt for i in info))
+        iters.append(max(i.iters for i in info))
     ev1.record(stream)
     barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     launches = solver.stats().kernel_launches - launches0
     clocks = sampler.stop()
-    worst = max(i.rel_kkt for i in infos)
-    if worst > TOL:
-        raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {TOL}")
+    if worst > tol:
+        raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
 
     t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     tmax = float(t.item())
-    value = world * args.steps / tmax
+    value = world * args.steps * k / tmax
+
+    def avg(f):
+        return sum(f(s) for s in stats) / len(stats)
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     e2e = None
     if not args.no_e2e:
         A_h = torch.from_numpy(np.ascontiguousarray(A_np.T)).pin_memory().t()
-        b_h = torch.from_numpy(np.ascontiguousarray(b_np[None, :])).pin_memory()
-        X_h = torch.zeros((1, N), dtype=torch.float64).pin_memory()
+        B_h = torch.from_numpy(np.ascontiguousarray(B_np)).pin_memory()
+        X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5))
-        hsolver = aln.Solver("split_bf16", stream=stream.cuda_stream)
-        hsolver.prepare(A_h, b_h)
-        hsolver.solve(tol=TOL, X=X_h)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+        hsolver.prepare(A_h, B_h)
+        hsolver.solve(tol=tol, X=X_h)
         barrier()
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            hsolver.prepare(A_h, b_h)
-            _, hinfo = hsolver.solve(tol=TOL, X=X_h)
+            hsolver.prepare(A_h, B_h)
+            _, hinfo = hsolver.solve(tol=tol, X=X_h)
         barrier()
         te = time.perf_counter() - t0
         hsolver.close()
         te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
         if world > 1:
             dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * k_e2e / float(te_t.item()), "unit": UNIT,
-               "h2d_bytes_per_step": int(A_np.nbytes + b_np.nbytes),
-               "d2h_bytes_per_step": int(N * 8), "steps": k_e2e,
-               "rel_kkt": hinfo[0].rel_kkt}
+        e2e = {"value": world * k_e2e * k / float(te_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(A_np.nbytes + B_np.nbytes),
+               "d2h_bytes_per_step": int(k * n * 8), "steps": k_e2e,
+               "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
 
     # ---- plain FP64 method on the same workload (the metric's comparison) ----
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and w["prec"] != "fp64":
+        kp_rhs = min(k, 16)          # the FP64 method solves one RHS at a time
         psolver = aln.Solver("fp64", stream=stream.cuda_stream)
-        psolver.prepare(At, bt)
-        psolver.solve(tol=TOL, X=Xt)
+        Bp = Bt[:kp_rhs].contiguous()
+        Xp = torch.zeros((kp_rhs, n), dtype=torch.float64, device="cuda")
+        psolver.prepare(At, Bp)
+        psolver.solve(tol=tol, X=Xp)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        kp = 2
+        reps = 2
         e0.record(stream)
-        for _ in range(kp):
-            psolver.prepare(At, bt)
-            _, pinfo = psolver.solve(tol=TOL, X=Xt)
+        for _ in range(reps):
+            psolver.prepare(At, Bp)
+            _, pinfo = psolver.solve(tol=tol, X=Xp)
         e1.record(stream)
         barrier()
-        tp = e0.elapsed_time(e1) / 1e3
+        tp = e0.elapsed_time(e1) / 1e3 / reps          # one prepare + kp_rhs solves
         pst = psolver.stats()
         psolver.close()
-        plain = {"value": kp / tp, "unit": UNIT, "steps": kp, "ms_per_step": tp / kp * 1e3,
-                 "gram_ms": pst.gram_ms, "iters": pinfo[0].iters, "rel_kkt": pinfo[0].rel_kkt}
+        per_rhs = (tp - pst.prepare_ms / 1e3) / kp_rhs
+        full = pst.prepare_ms / 1e3 + per_rhs * k        # the whole workload's solves
+        plain = {"value": k / full, "unit": UNIT, "ms_per_step": full * 1e3,
+                 "gram_ms": pst.gram_ms, "rhs_timed": kp_rhs, "repeats": reps,
+                 "iters_max": max(i.iters for i in pinfo),
+                 "rel_kkt_max": max(i.rel_kkt for i in pinfo),
+                 "note": "FP64 Gram + FP64 Alg. 2 one right-hand side at a time"
+                         + ("" if kp_rhs == k else f"; {kp_rhs} timed, scaled to {k}")}
 
     solver.close()
     if rank != 0:
@@ -294,50 +352,68 @@ def run_ours(args):
         return 0
 
     pk, pk_kind = peaks()
-    gram = sum(gram_ms) / len(gram_ms)
-    flops = 3.0 * D * N * (N + 1)              # three split products over n(n+1)/2 entries
-    achieved = flops / (gram / 1e3) / 1e12
-    peak = float(pk["bf16_tflops_sustained"])
-    roof_gram = {"bound": "tensor", "kernel": "k_gram_tc (split-BF16 Gram)",
-                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                 "frac": achieved / peak, "traffic": None,
-                 "peak_kind": f"{pk_kind} bf16 sustained",
-                 "algorithmic_per_launch": flops, "avg_launch_ms": gram}
-    it_ms = sum(iter_ms) / len(iter_ms)
-    qbytes = 4.0 * N * (sum(qrows) / len(qrows))   # FP32 rows of Q read (§4.2: n·S(n) per product)
     hbm = float(pk["hbm_gbs"])
-    ach_it = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
-    roof_iter = {"bound": "hbm", "kernel": "k_alg2_persist (Alg. 2 loop)",
-                 "achieved": ach_it, "peak": hbm, "unit": "GB/s", "frac": ach_it / hbm,
-                 "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
-                 "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
-                 "note": "Q (FP32, 100 MB) can stay in the 129 MB L2, so frac may exceed 1"}
-    roofline, roof2 = (roof_iter, roof_gram) if it_ms >= gram else (roof_gram, roof_iter)
+    peak_tc = float(pk["bf16_tflops_sustained"])
+    gram = avg(lambda s: s.gram_ms)
+    it_ms = avg(lambda s: s.iterate_ms)
+    rooflines = []
+    if w["prec"] == "split_bf16" and k == 1:
+        flops = 3.0 * d * n * (n + 1)          # three split products over n(n+1)/2 entries
+        ach = flops / (gram / 1e3) / 1e12
+        rooflines.append({"bound": "tensor", "kernel": "k_gram_tc (split-BF16 Gram)",
+                          "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s",
+                          "frac": ach / peak_tc, "traffic": None,
+                          "peak_kind": f"{pk_kind} bf16 sustained",
+                          "algorithmic_per_launch": flops, "avg_launch_ms": gram})
+    if k == 1:
+        esz = 8 if w["prec"] == "fp64" else 4
+        qbytes = esz * n * avg(lambda s: s.passive_rows + s.clipped_rows)  # §4.2: n·S(n)
+        ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
+        rooflines.append({"bound": "hbm", "kernel": "k_alg2_repl (persistent Alg. 2 loop)",
+                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
+                          "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
+                          "note": "the rows of Q read stay in the 129 MB L2 between "
+                                  "iterations, so frac can exceed 1"})
+    else:
+        # tensor FLOPs of the batched products: 3 split products of 2·n² per
+        # running column (W = Qḡ) and per clipped column (U = Qe)
+        colit = avg(lambda s: s.iterations + s.clipped_iterations)
+        flops = 3.0 * 2.0 * n * n * colit
+        ach = flops / (it_ms / 1e3) / 1e12 if it_ms > 0 else 0.0
+        rooflines.append({"bound": "tensor",
+                          "kernel": "batched Alg. 2 phase (k_bgemm_tc W and U + mask/update)",
+                          "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s",
+                          "frac": ach / peak_tc, "traffic": None,
+                          "peak_kind": f"{pk_kind} bf16 sustained",
+                          "algorithmic_per_launch": flops, "avg_launch_ms": it_ms})
+    rooflines.sort(key=lambda r: -r["avg_launch_ms"])
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        m = N // 2
-        ts, scale, _ = cpu_baseline_sample(A_np, b_np, m)
-        cpu = {"value": 1.0 / (ts * scale), "unit": UNIT, "cores": blas_threads(),
-               "kind": "oracle",
-               "sample": f"oracle antilop on A[:, :{m}] (d={D}) in {ts:.2f} s, "
-                         f"x (n/m)^2 = {scale:.0f} for the full size"}
+        ts, desc = cpu_sample(w, p)
+        cpu = {"value": k / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "d": D, "n": N, "tol": TOL, "seed": SEED,
-                   "form": "split-BF16 tcgen05 Gram, FP32 Alg. 2, FP64 scale/KKT/refinement",
+        "dtype": "f64" if w["prec"] == "fp64" else "bf16x3+f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
+                   "seed": w["seed"],
+                   "form": ("FP64 Gram + FP64 Alg. 2" if w["prec"] == "fp64" else
+                            "split-BF16 tcgen05 Gram/products, FP32 Alg. 2, "
+                            "FP64 scale/KKT/refinement"),
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (A 400 MB fp32, split copies 400 MB)",
-                   "prepare_ms": sum(prep_ms) / len(prep_ms),
-                   "gram_ms": gram, "solve_ms": sum(solve_ms) / len(solve_ms),
-                   "iterate_ms": it_ms, "kkt_ms": sum(kkt_ms) / len(kkt_ms),
-                   "iters": iters, "rel_kkt_max": worst},
-        "roofline": roofline,
-        "roofline_secondary": roof2,
+                   "l2": "inputs larger than L2" if A_np.nbytes > 129e6 else
+                         "inputs smaller than L2 (timed as resident data)",
+                   "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
+                   "solve_ms": avg(lambda s: s.solve_ms), "iterate_ms": it_ms,
+                   "kkt_ms": avg(lambda s: s.kkt_ms), "iters_max": iters,
+                   "rel_kkt_max": worst},
+        "roofline": rooflines[0],
+        "roofline_secondary": rooflines[1] if len(rooflines) > 1 else None,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain_fp64": plain,
@@ -351,10 +427,7 @@ def run_ours(args):
 
 
 def main():
-    global D, N, WORKLOAD
     args = parse()
-    D, N = args.d, args.n
-    WORKLOAD = WORKLOAD_FMT.format(d=D, n=N)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kBThreads) k_bupdate(BatchState s) {
                 slot = atomicAdd(&s.counters[1], 1);
                 s.map_clip[slot] = (int)c;
                 atomicAdd(&s.rows[1], (unsigned long long)t);
+                atomicAdd(&s.rows[2], 1ull);  // column-iterations with a Qe product
             }
             s_slot = slot;
         }
@@ -577,7 +578,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     k_binit<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->q64, X0dev, c->ldq, c->s, c->den,
                                                       0.5 * tol, b->rounds);
     cudaMemsetAsync(b->fin, 0xff, (size_t)k * 4, c->stream);  // -1: not final yet
-    cudaMemsetAsync(s.rows, 0, 16, c->stream);
+    cudaMemsetAsync(s.rows, 0, 24, c->stream);
     c->launches += 1;
     if (X0dev) {  // g = Q y0 + q, in FP64, for a start point
         k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
@@ -626,7 +627,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
                           x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           c->stream) != cudaSuccess)
         return ALN_ERR_CUDA;
-    unsigned long long rows[2] = {0, 0};
+    unsigned long long rows[3] = {0, 0, 0};
     cudaMemcpyAsync(rows, s.rows, sizeof(rows), cudaMemcpyDeviceToHost, c->stream);
     if (info) {
         int* tmp_i = new (std::nothrow) int[3 * k];
@@ -663,6 +664,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ALN_ERR_CUDA;
     c->stats.passive_rows = (int64_t)rows[0];
     c->stats.clipped_rows = (int64_t)rows[1];
+    c->stats.clipped_iterations = (int32_t)rows[2];
     return ALN_OK;
 }
 

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t* done = empty + STAGES;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ int s_map[BM];
-    __shared__ double s_red[4][BM];
+    __shared__ float s_red[4][BM];
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -452,12 +452,15 @@ __global__ void __launch_bounds__(128, 1)
                 const int cc = c0 + t;
                 const int col = cc < cols ? s_map[cc] : -1;
                 if (MODE == BMODE_W) {
-                    double kp = 0.0;
+                    // curvature partial in FP32 (the FP64 pipe is narrow on
+                    // this GPU); the row-tile partials are summed in FP64
+                    float kp = 0.0f;
                     if (col >= 0 && rv) {
                         p.W[(n0 + cc) * p.ldq + row] = v[t];
-                        kp = (double)p.gb[(int64_t)col * p.ldq + row] * (double)v[t];
+                        kp = p.gb[(int64_t)col * p.ldq + row] * v[t];
                     }
-                    kp = warp_sum(kp);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
                     if (lane == 0) s_red[warp][cc] = kp;
                 } else {
                     if (col >= 0 && rv) {
@@ -473,9 +476,9 @@ __global__ void __launch_bounds__(128, 1)
     if (MODE == BMODE_W) {
         __syncthreads();
         if (good && threadIdx.x < cols) {
-            const double s = s_red[0][threadIdx.x] + s_red[1][threadIdx.x] +
-                             s_red[2][threadIdx.x] + s_red[3][threadIdx.x];
-            p.kpart[(int64_t)blockIdx.x * p.kmax + n0 + threadIdx.x] = s;
+            const float s = (s_red[0][threadIdx.x] + s_red[1][threadIdx.x]) +
+                            (s_red[2][threadIdx.x] + s_red[3][threadIdx.x]);
+            p.kpart[(int64_t)blockIdx.x * p.kmax + n0 + threadIdx.x] = (double)s;
         }
     }
     tc_fence_before();

@@ -5,11 +5,47 @@
 
 namespace aln {
 
+// Per-thread accumulator of a dot product.  FP32 inputs use Dot2 (Ogita,
+// Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005):
+// the exact product error from an FMA (TwoProduct) and the exact addition
+// error (TwoSum) are carried in a second float, so the result is as accurate
+// as if accumulated in twice the working precision — without the FP64 pipe,
+// which is narrow on this GPU.  FP64 inputs accumulate in FP64.
+template <typename TA> struct DotAcc;
+template <> struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);   // a·b = p + ep exactly
+        const float t = s + p;
+        const float z = t - s;
+        const float es = (s - (t - z)) + (p - z);  // s + p = t + es exactly
+        s = t;
+        c += es + ep;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+__device__ __forceinline__ void load4t(const float* p, float* o) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+__device__ __forceinline__ void load4t(const double* p, double* o) { load4(p, o); }
+
 // One 256-thread block per column A_i, one pass over the column:
-//   s_i² = Σ_t A_ti²            (FP64)            — √diag(H) of Alg. 1, Eq. Rescaling
-//   c_ci = Σ_t A_ti B_ct, c < kc ≤ 4 (FP64)       — Aᵀb of Eq. NQP
+//   s_i² = Σ_t A_ti²                              — √diag(H) of Alg. 1, Eq. Rescaling
+//   c_ci = Σ_t A_ti B_ct, c < kc ≤ 4              — Aᵀb of Eq. NQP
 //   s_i  = √s_i², or 1 when s_i² = 0 (Eq. Rescaling's H_ii = 0 case)
 //   q_ci = −c_ci / s_i                            — q of Eq. NQPQ
+// Sums are accurate to FP64 level (DotAcc) and combined in FP64.
 // With SPLIT, also writes hi = bf16(A_ti), lo = bf16(A_ti − hi) into the
 // K-major [n][ldk] arrays read by the tensor-core Gram (zero padding t ≥ d).
 // VEC: the column and B rows are 16-byte aligned, so four consecutive
@@ -27,25 +63,25 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
     __shared__ double scratch[32];
     const int64_t i = blockIdx.x;
     const TA* col = A + i * lda;
-    double s2 = 0.0, dot[4] = {0.0, 0.0, 0.0, 0.0};
+    DotAcc<TA> sq, dot[4];
     bool bad = false;
     const int64_t d4 = VEC ? d / 4 : 0;
-#pragma unroll 4
+#pragma unroll 2
     for (int64_t q = threadIdx.x; q < d4; q += blockDim.x) {
-        double a[4];
-        load4(col + 4 * q, a);
+        TA a[4];
+        load4t(col + 4 * q, a);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            s2 = fma(a[u], a[u], s2);
+            sq.add(a[u], a[u]);
             bad |= !isfinite(a[u]);
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             if (c < kc) {
-                double bb[4];
-                load4(B + (int64_t)c * ldb + 4 * q, bb);
+                TA bb[4];
+                load4t(B + (int64_t)c * ldb + 4 * q, bb);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) dot[c] = fma(a[u], bb[u], dot[c]);
+                for (int u = 0; u < 4; ++u) dot[c].add(a[u], bb[u]);
             }
         }
         if (SPLIT) {
@@ -61,10 +97,10 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
         }
     }
     for (int64_t t = 4 * d4 + threadIdx.x; t < d; t += blockDim.x) {
-        const double a = (double)col[t];
-        s2 = fma(a, a, s2);
+        const TA a = col[t];
+        sq.add(a, a);
         bad |= !isfinite(a);
-        for (int c = 0; c < kc; ++c) dot[c] = fma(a, (double)B[(int64_t)c * ldb + t], dot[c]);
+        for (int c = 0; c < kc; ++c) dot[c].add(a, B[(int64_t)c * ldb + t]);
         if (SPLIT) {
             const float af = (float)col[t];
             const __nv_bfloat16 h = __float2bfloat16_rn(af);
@@ -79,10 +115,10 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
             lo[i * ldk + t] = z;
         }
     }
-    s2 = block_sum(s2, scratch);
+    const double s2 = block_sum(sq.value(), scratch);
     double dsum[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dsum[c] = c < kc ? block_sum(dot[c], scratch) : 0.0;
+    for (int c = 0; c < 4; ++c) dsum[c] = c < kc ? block_sum(dot[c].value(), scratch) : 0.0;
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0) {
         const double si = s2 > 0.0 ? sqrt(s2) : 1.0;
