@@ -401,9 +401,14 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     const int kc = k <= 4 ? (int)k : 0;
     ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64, ldq,
                             c->flags, hi, lo, c->ldk, c->stream));
-    if (kc == 0)
-        ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
-                              c->stream));
+    if (kc == 0) {
+        if (c->batched && dtype == ALN_DTYPE_F32)  // FP64-accurate, on the FP32 pipe
+            ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
+                                       c->inv_s, c->q64, ldq, c->stream));
+        else
+            ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
+                                  c->stream));
+    }
     ALN_TRY(launch_denominators(c->q64, n, ldq, k, c->den, c->stream));
     ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
     if (c->batched)

@@ -495,9 +495,13 @@ aln_status batch_prepare(aln_ctx* c) {
     }
     aln_status st = bw_alloc(c, b);
     if (st != ALN_OK) return st;
-    if (launch_gram64(c->A, c->dtype, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq, c->stream) !=
-        cudaSuccess)
-        return ALN_ERR_CUDA;
+    const cudaError_t eg =
+        c->dtype == ALN_DTYPE_F32
+            ? launch_gram32_dot2((const float*)c->A, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq,
+                                 c->stream)
+            : launch_gram64(c->A, c->dtype, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq,
+                            c->stream);
+    if (eg != cudaSuccess) return ALN_ERR_CUDA;
     k_qsplit<<<(unsigned)c->n, kBThreads, 0, c->stream>>>(b->Q64, c->ldq, c->n, b->ldk,
                                                         (float*)c->Q, b->Qhi, b->Qlo);
     k_bnorm2<<<(unsigned)c->k, kBThreads, 0, c->stream>>>(c->B, c->dtype, c->d, c->ldb, b->bn2);

@@ -287,6 +287,23 @@ def test_multiple_rhs_each_match_oracle(aln):
 
 
 # ------------------------------------------------------------- batched solver
+def test_batched_prepare_matches_oracle(aln):
+    """Batched prepare: q and the scaled matrix come from FP32-pipe Dot2
+    products (compensated, FP64-level accuracy); q and s to 1e-12, Q (kept
+    in FP32 for the iteration) to FP32 rounding."""
+    p = W.shared_multi_rhs(d=1300, n=257, k=70, seed=37)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.A, p.B)
+        Q, q, sc = s.export()
+    A64 = p.A.astype(np.float64)
+    H, h = O.nqp_from_nnls(A64, p.B.astype(np.float64))
+    Qo, qo, so = O.antilopsided_scaling(H, h)
+    np.testing.assert_allclose(sc, so, rtol=1e-13)
+    np.testing.assert_allclose(q, qo, rtol=0, atol=1e-12 * np.abs(qo).max())
+    np.testing.assert_allclose(Q, Qo, rtol=0, atol=2.0 ** -23)
+    np.testing.assert_array_equal(Q, Q.T)
+
+
 def test_batched_multi_rhs_matches_oracle(aln):
     """Many RHS sharing A (NMF inner-solve shape): the batched tensor-core
     solver meets the mixed-precision gates on every column."""
