@@ -8,8 +8,9 @@ log-uniform column scales, x_true 70% zeros, 1% noise): Alg. 1's prepare
 FP64 relative KKT ≤ 1e-6, including the FP64 KKT evaluation from A.
 
 Other workloads (--workload): `shared_multi_rhs` (A 10000×1000 shared by 4096
-right-hand sides; one step = the whole batch) and `uniform_small` (A 1000×200,
-plain FP64 method at rel KKT 1e-10).
+right-hand sides; one step = the whole batch), `uneven_batch` (512 independent
+problems of uneven size, n in [32, 1024]; one step = prepare and solve all of
+them) and `uniform_small` (A 1000×200, plain FP64 method at rel KKT 1e-10).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME]
@@ -46,6 +47,11 @@ WORKLOADS = {
         d=10000, n=1000, k=4096, tol=1e-6, seed=1003, prec="split_bf16",
         desc="shared_multi_rhs_{d}x{n}_k{k}_f32: A U[0,1]; B = A X_true + 1% noise, X_true 80% "
              "zeros Gamma(2,1); all right-hand sides solved together"),
+    "uneven_batch": dict(
+        d=0, n=0, k=512, tol=1e-6, seed=1004, prec="split_bf16",
+        desc="uneven_batch_{k}: {k} independent problems, n log-uniform in [32,1024], "
+             "d = n*U{{2,3,4}}, A |N(0,1)| FP32, x_true 60% zeros U[0,1], 1% noise; "
+             "all problems prepared and solved together (grouped)"),
     "uniform_small": dict(
         d=1000, n=200, k=1, tol=1e-10, seed=1001, prec="fp64",
         desc="uniform_small_{d}x{n}_f64: A U[0,1], x_true half zeros U[0,1], "
@@ -82,6 +88,8 @@ def workload(args):
 
 def generate(w, rank=0):
     from paper_1502_01645_gb300 import workloads as W
+    if w["name"] == "uneven_batch":
+        return W.uneven_batch(count=w["k"], seed=w["seed"] + rank)
     if w["name"] == "lopsided_single":
         return W.lopsided_single(d=w["d"], n=w["n"], seed=w["seed"] + rank)
     if w["name"] == "shared_multi_rhs":
@@ -189,6 +197,22 @@ def cpu_sample(w, p):
                             f"in {t:.2f} s, x k/{s} for the batch")
 
 
+def cpu_sample_grouped(w, probs, stride=32):
+    """The FP64 oracle on every `stride`-th problem of the uneven batch (a
+    sample across the size range), time × stride for the whole batch."""
+    import numpy as np
+    from oracle import nnls as O
+    sample = probs[::stride]
+    t0 = time.perf_counter()
+    for p in sample:
+        O.antilop(np.asarray(p.A, dtype=np.float64, order="F"), p.B[0].astype(np.float64),
+                  tol=w["tol"])
+    t = time.perf_counter() - t0
+    scale = len(probs) / len(sample)
+    return t * scale, (f"oracle antilop on every {stride}th of {len(probs)} problems "
+                       f"({len(sample)} problems) in {t:.2f} s, x {scale:.0f}")
+
+
 # ------------------------------------------------------------------- reference
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -198,7 +222,7 @@ def run_reference(args):
     p = generate(w)
     times, desc = [], ""
     for i in range(args.warmup + args.steps):
-        t, desc = cpu_sample(w, p)
+        t, desc = cpu_sample_grouped(w, p) if w["name"] == "uneven_batch" else cpu_sample(w, p)
         if i >= args.warmup:
             times.append(t)
     per = sum(times) / len(times)
@@ -236,6 +260,8 @@ def run_ours(args):
     aln.load()
 
     w = workload(args)
+    if w["name"] == "uneven_batch":
+        return run_grouped(args, w, world, rank, local)
     d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
     p = generate(w, rank)
     A_np, B_np = p.A, p.B
@@ -414,6 +440,195 @@ def run_ours(args):
                    "rel_kkt_max": worst},
         "roofline": rooflines[0],
         "roofline_secondary": rooflines[1] if len(rooflines) > 1 else None,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "plain_fp64": plain,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_grouped(args, w, world, rank, local):
+    """The uneven batch: one step = prepare and solve all problems (grouped
+    prepare, one tcgen05 Gram launch, persistent per-problem Alg. 2, FP64
+    KKT / refinement)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1502_01645_gb300 import aln
+
+    tol, k = w["tol"], w["k"]
+    probs = generate(w, rank)
+    sizes = [(p.A.shape[0], p.A.shape[1]) for p in probs]
+    N = sum(n for _, n in sizes)
+    dev = [(torch.from_numpy(np.ascontiguousarray(p.A.T)).cuda().t(),
+            torch.from_numpy(np.ascontiguousarray(p.B[0])).cuda()) for p in probs]
+    Xt = torch.zeros(N, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+    recs = aln.Solver.grouped_records(dev)
+
+    def step():
+        solver.prepare_grouped(records=recs)
+        _, info = solver.solve(tol=tol, X=Xt)
+        return info, solver.stats()
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = solver.stats().kernel_launches
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats, worst, iters = [], 0.0, []
+    for _ in range(args.steps):
+        info, st = step()
+        stats.append(st)
+        worst = max(worst, max(i.rel_kkt for i in info))
+        iters.append(max(i.iters for i in info))
+    ev1.record(stream)
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = solver.stats().kernel_launches - launches0
+    clocks = sampler.stop()
+    if worst > tol:
+        raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = world * args.steps * k / tmax
+
+    def avg(f):
+        return sum(f(s) for s in stats) / len(stats)
+
+    # ---- end to end: host (pinned) inputs, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        host = [(torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory().t(),
+                 torch.from_numpy(np.ascontiguousarray(p.B[0])).pin_memory()) for p in probs]
+        hrecs = aln.Solver.grouped_records(host)
+        X_h = torch.zeros(N, dtype=torch.float64).pin_memory()
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+        hsolver.prepare_grouped(records=hrecs)
+        hsolver.solve(tol=tol, X=X_h)
+        barrier()
+        k_e2e = max(3, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            hsolver.prepare_grouped(records=hrecs)
+            _, hinfo = hsolver.solve(tol=tol, X=X_h)
+        barrier()
+        te = time.perf_counter() - t0
+        hsolver.close()
+        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * k_e2e * k / float(te_t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(p.A.nbytes + p.B.nbytes for p in probs)),
+               "d2h_bytes_per_step": int(N * 8), "steps": k_e2e,
+               "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
+
+    # ---- plain FP64 method, one problem at a time, on a sample ----
+    plain = None
+    if not args.no_plain:
+        stride = 32
+        sample = list(range(0, len(probs), stride))
+        psolver = aln.Solver("fp64", stream=stream.cuda_stream)
+        Xp = torch.zeros(max(n for _, n in sizes), dtype=torch.float64, device="cuda")
+
+        def plain_pass():
+            its = []
+            for i in sample:
+                A_i, b_i = dev[i]
+                psolver.prepare(A_i, b_i.reshape(1, -1))
+                _, pi = psolver.solve(tol=tol, X=Xp[:sizes[i][1]].reshape(1, -1))
+                its.append(pi[0])
+            return its
+
+        plain_pass()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pinfo = plain_pass()
+        e1.record(stream)
+        barrier()
+        tp = e0.elapsed_time(e1) / 1e3
+        psolver.close()
+        full = tp * len(probs) / len(sample)
+        plain = {"value": k / full, "unit": UNIT, "ms_per_step": full * 1e3,
+                 "problems_timed": len(sample),
+                 "iters_max": max(i.iters for i in pinfo),
+                 "rel_kkt_max": max(i.rel_kkt for i in pinfo),
+                 "note": f"FP64 Gram + FP64 Alg. 2 one problem at a time; every {stride}th "
+                         f"problem timed, scaled to {len(probs)}"}
+
+    solver.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+    peak_tc = float(pk["bf16_tflops_sustained"])
+    gram = avg(lambda s: s.gram_ms)
+    it_ms = avg(lambda s: s.iterate_ms)
+    qbytes = avg(lambda s: s.product_bytes)
+    ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
+    rooflines = [{"bound": "hbm", "kernel": "k_galg2<float> (persistent per-problem Alg. 2)",
+                  "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                  "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
+                  "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
+                  "note": "Q_p is staged in shared memory when it fits and otherwise stays in "
+                          "L2 between iterations, so frac can exceed 1"}]
+    flops = sum(3.0 * dd * nn * (nn + 1) for dd, nn in sizes)
+    acht = flops / (gram / 1e3) / 1e12 if gram > 0 else 0.0
+    rooflines.append({"bound": "tensor", "kernel": "k_ggram_tc (grouped split-BF16 Gram)",
+                      "achieved": acht, "peak": peak_tc, "unit": "TFLOP/s",
+                      "frac": acht / peak_tc, "traffic": None,
+                      "peak_kind": f"{pk_kind} bf16 sustained",
+                      "algorithmic_per_launch": flops, "avg_launch_ms": gram})
+    rooflines.sort(key=lambda r: -r["avg_launch_ms"])
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        ts, desc = cpu_sample_grouped(w, probs)
+        cpu = {"value": k / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
+    nbytes = sum(p.A.nbytes for p in probs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if w["prec"] == "fp64" else "bf16x3+f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "problems": k, "sum_n": N,
+                   "sum_d": sum(dd for dd, _ in sizes),
+                   "n_range": [min(n for _, n in sizes), max(n for _, n in sizes)],
+                   "tol": tol, "seed": w["seed"],
+                   "form": "grouped: split-BF16 tcgen05 Gram (bulk-copy tiles), FP32 Alg. 2 "
+                           "one problem per block, FP64 scale/KKT/refinement",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2" if nbytes > 129e6 else
+                         "inputs smaller than L2 (timed as resident data)",
+                   "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
+                   "solve_ms": avg(lambda s: s.solve_ms), "iterate_ms": it_ms,
+                   "kkt_ms": avg(lambda s: s.kkt_ms), "iters_max": iters,
+                   "iterations_total": avg(lambda s: s.iterations),
+                   "rel_kkt_max": worst},
+        "roofline": rooflines[0],
+        "roofline_secondary": rooflines[1],
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain_fp64": plain,

@@ -131,6 +131,32 @@ aln_status aln_create(aln_ctx** ctx, const aln_options* opt, void* stream);
 aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_t lda,
                        int32_t dtype, const void* B, int64_t k, int64_t ldb);
 
+/* One problem of a grouped batch: min ½‖A x − b‖², x ⪰ 0 (Def. 1), with its
+ * own A (d×n, column-major, lda ≥ d) and b (d entries).  A and b may be host
+ * or device memory, independently per problem. */
+typedef struct aln_problem {
+    const void* A;
+    const void* b;
+    int64_t d, n, lda;
+} aln_problem;
+
+/* Alg. 1 for `count` independent problems of different sizes at once (one
+ * Gram launch over every problem's tiles, one persistent Alg. 2 launch whose
+ * blocks take problems largest first).  All problems share `dtype`.
+ * Requires 1 ≤ count ≤ 2^20, and per problem d ≥ 1 and 1 ≤ n ≤ 4096 (larger
+ * problems go through aln_prepare, whose solver spans the whole GPU).
+ * After this call the context is in grouped mode until the next prepare:
+ *   - vectors are PACKED: problem p occupies entries [o_p, o_p + n_p) of X,
+ *     X0, q and s, with o_p = Σ_{r<p} n_r; ldx and ldqv are ignored;
+ *   - info, rel_kkt and objective hold `count` entries, one per problem;
+ *   - aln_export_scaled writes Q as packed row-major n_p×n_p blocks starting
+ *     at Σ_{r<p} n_r² (ldq ignored).
+ * Device inputs are kept by pointer (same lifetime rule as aln_prepare).
+ * Errors: INVALID_ARG, NONFINITE, OUT_OF_MEMORY, TIMEOUT, UNSUPPORTED (no
+ * sm_103a device for SPLIT_BF16), CUDA. */
+aln_status aln_prepare_grouped(aln_ctx* ctx, int32_t count, const aln_problem* probs,
+                               int32_t dtype);
+
 /* Alg. 2 on every prepared right-hand side, then x = y/s (Alg. 1).
  *   tol       relative KKT tolerance: stop when ‖ḡ‖ ≤ tol·‖min(q,0)‖ (FP64,
  *             evaluated from A); must be > 0.
@@ -179,6 +205,9 @@ typedef struct aln_stats {
     double phase_us[5];      /* block 0's time in the persistent kernel, per phase:
                                 product Qḡ, grid barrier, update, clipped
                                 correction, mask (replicated-state kernel) */
+    double product_bytes;    /* algorithmic bytes of Q the Alg. 2 products of the
+                                last aln_solve read: Σ_k n·(|P_k| + |C_k|)·sizeof
+                                (summed over problems in grouped mode) */
 } aln_stats;
 
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */

@@ -28,7 +28,7 @@ RHS_MAXITER, RHS_NONFINITE, RHS_STAGNATED = 3, 4, 5
 EXPORTS = (
     "aln_default_options", "aln_create", "aln_prepare", "aln_solve", "aln_kkt_residual",
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
-    "aln_kkt_residual_noalloc",
+    "aln_kkt_residual_noalloc", "aln_prepare_grouped",
 )
 
 
@@ -51,7 +51,13 @@ class AlnStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("iterate_ms", ctypes.c_double), ("passive_rows", ctypes.c_int64),
                 ("clipped_rows", ctypes.c_int64), ("persist_blocks", ctypes.c_int32),
-                ("clipped_iterations", ctypes.c_int32), ("phase_us", ctypes.c_double * 5)]
+                ("clipped_iterations", ctypes.c_int32), ("phase_us", ctypes.c_double * 5),
+                ("product_bytes", ctypes.c_double)]
+
+
+class AlnProblem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("d", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("lda", ctypes.c_int64)]
 
 
 class AlnError(RuntimeError):
@@ -96,6 +102,8 @@ def load(path: str | None = None):
     lib.aln_version.restype = i32
     lib.aln_kkt_residual_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, dp, dp, vp]
     lib.aln_kkt_residual_noalloc.restype = ctypes.c_int
+    lib.aln_prepare_grouped.argtypes = [vp, i32, ctypes.POINTER(AlnProblem), i32]
+    lib.aln_prepare_grouped.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -146,6 +154,13 @@ def aln_create(opt: AlnOptions | None = None, stream: int | None = None) -> int:
 
 def aln_prepare(ctx, A, d, n, lda, dtype, B, k, ldb) -> None:
     _check(load().aln_prepare(ctx, _ptr(A), d, n, lda, dtype, _ptr(B), k, ldb), "aln_prepare")
+
+
+def aln_prepare_grouped(ctx, problems, dtype) -> None:
+    """problems: a ctypes array of AlnProblem, or a sequence of AlnProblem."""
+    arr = problems if isinstance(problems, ctypes.Array) else (AlnProblem * len(problems))(
+        *problems)
+    _check(load().aln_prepare_grouped(ctx, len(arr), arr, dtype), "aln_prepare_grouped")
 
 
 def aln_solve(ctx, tol, max_iter, X, ldx, X0, k) -> list:
@@ -216,6 +231,7 @@ class Solver:
         self.precision = precision
         self._keep = ()
         self.n = self.k = 0
+        self.sizes = None  # per-problem n after prepare_grouped
 
     def prepare(self, A, B):
         d, n = A.shape
@@ -229,8 +245,56 @@ class Solver:
         self._keep = (A, B)
         aln_prepare(self.ctx, A, d, n, lda, _dtype_code(A), B, k, ldb)
         self.n, self.k = n, k
+        self.sizes = None
+
+    @staticmethod
+    def grouped_records(problems):
+        """Marshal (A, b) pairs — A (d_p, n_p) column-major, b (d_p,), one dtype
+        for all — into the C records once; the result can be passed to
+        prepare_grouped repeatedly while the arrays stay alive."""
+        recs, keep = [], []
+        dtype = None
+        for A, b in problems:
+            d, n = A.shape
+            if b.shape[-1] != d:
+                raise ValueError("b must have length d")
+            code = _dtype_code(A)
+            if dtype is None:
+                dtype = code
+            elif code != dtype or _dtype_code(b) != dtype:
+                raise ValueError("all problems must share one dtype")
+            recs.append(AlnProblem(_ptr(A), _ptr(b), d, n, _col_major_ld(A)))
+            keep.append((A, b))
+        arr = (AlnProblem * len(recs))(*recs)
+        return arr, dtype, [int(r.n) for r in recs], tuple(keep)
+
+    def prepare_grouped(self, problems=None, records=None):
+        """Independent problems (A_p, b_p) of uneven size in one context;
+        solutions come back as a list of vectors."""
+        if records is None:
+            records = self.grouped_records(problems)
+        arr, dtype, sizes, keep = records
+        self._keep = keep
+        aln_prepare_grouped(self.ctx, arr, dtype)
+        self.sizes = sizes
+        self.n, self.k = sum(sizes), len(sizes)
+
+    def _split(self, X):
+        out, o = [], 0
+        for n in self.sizes:
+            out.append(X[o:o + n])
+            o += n
+        return out
 
     def solve(self, tol=1e-6, max_iter=0, X=None, X0=None):
+        if self.sizes is not None:  # grouped: packed vectors
+            Xp = np.zeros(self.n) if X is None else X
+            X0p = None if X0 is None else (np.concatenate(X0) if isinstance(X0, (list, tuple))
+                                           else X0)
+            info = aln_solve(self.ctx, tol, max_iter, Xp, self.n, X0p, self.k)
+            return (self._split(Xp) if X is None else Xp,
+                    [SolveInfo(i.iters, i.status, i.refine_rounds, i.rel_kkt, i.objective)
+                     for i in info])
         if X is None:
             X = np.zeros((self.k, self.n))
         info = aln_solve(self.ctx, tol, max_iter, X, _row_major_ld(X), X0, self.k)
@@ -238,12 +302,25 @@ class Solver:
                    for i in info]
 
     def kkt(self, X):
+        if self.sizes is not None and isinstance(X, (list, tuple)):
+            X = np.concatenate([np.asarray(x, dtype=np.float64) for x in X])
         rel = np.zeros(self.k)
         obj = np.zeros(self.k)
-        aln_kkt_residual(self.ctx, X, _row_major_ld(X), rel, obj)
+        ld = self.n if self.sizes is not None else _row_major_ld(X)
+        aln_kkt_residual(self.ctx, X, ld, rel, obj)
         return rel, obj
 
     def export(self):
+        if self.sizes is not None:  # grouped: per-problem blocks
+            Qp = np.zeros(sum(n * n for n in self.sizes))
+            q = np.zeros(self.n)
+            s = np.zeros(self.n)
+            aln_export_scaled(self.ctx, Qp, 0, q, 0, s)
+            Qs, o = [], 0
+            for n in self.sizes:
+                Qs.append(Qp[o:o + n * n].reshape(n, n))
+                o += n * n
+            return Qs, self._split(q), self._split(s)
         Q = np.zeros((self.n, self.n))
         q = np.zeros((self.k, self.n))
         s = np.zeros(self.n)

@@ -180,6 +180,8 @@ aln_status run_until_done(aln_ctx* c) {
     if (c->st_host->status < 0 || !c->st_host->done) return ALN_ERR_TIMEOUT;
     c->stats.passive_rows += c->st_host->sum_passive;
     c->stats.clipped_rows += c->st_host->sum_clip;
+    c->stats.product_bytes += (double)(fp64(c) ? 8 : 4) * (double)c->n *
+                              (double)(c->st_host->sum_passive + c->st_host->sum_clip);
     if (c->p_repl) {
         for (int k = 0; k < 5; ++k) c->stats.phase_us[k] += 1e-3 * (double)c->st_host->phase_ns[k];
         c->stats.clipped_iterations += (int32_t)c->st_host->phase_ns[5];
@@ -316,6 +318,7 @@ void aln_destroy(aln_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     batch_free(c);
+    group_free(c);
     void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -334,6 +337,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
     if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
     c->prepared = 0;
+    c->grouped = 0;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     ALN_CHECK(resolve_input(c, A, d, n, lda, esz, &c->A_copy, &c->A_copy_bytes, &c->A));
@@ -442,10 +446,50 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     return ALN_OK;
 }
 
+aln_status aln_prepare_grouped(aln_ctx* c, int32_t count, const aln_problem* probs,
+                               int32_t dtype) {
+    if (!c || !probs || count < 1 || count > (1 << 20)) return ALN_ERR_INVALID_ARG;
+    if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
+    int64_t cols = 0;
+    for (int32_t p = 0; p < count; ++p) {
+        const aln_problem& q = probs[p];
+        if (!q.A || !q.b || q.d < 1 || q.n < 1 || q.lda < q.d || q.d > ((int64_t)1 << 30))
+            return ALN_ERR_INVALID_ARG;
+        cols += q.n;
+    }
+    if (cols > ((int64_t)1 << 31) / 128) return ALN_ERR_INVALID_ARG;
+    c->prepared = 0;
+    c->batched = 0;
+    c->grouped = 0;
+    c->stats.prepare_ms = c->stats.gram_ms = 0.0;
+    ALN_CHECK(group_prepare(c, count, probs, dtype));
+    c->k = count;
+    c->dtype = dtype;
+    c->prepared = 1;
+    return ALN_OK;
+}
+
 aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_t ldx,
                      const double* X0, aln_solve_info* info) {
     if (!c) return ALN_ERR_INVALID_ARG;
     if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (c->grouped) {
+        if (!X || !(tol > 0.0) || !std::isfinite(tol)) return ALN_ERR_INVALID_ARG;
+        if (max_iter <= 0) max_iter = 20000;
+        c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
+        c->stats.passive_rows = c->stats.clipped_rows = 0;
+        c->stats.clipped_iterations = 0;
+        c->stats.iterations = 0;
+        c->stats.product_bytes = 0.0;
+        for (double& v : c->stats.phase_us) v = 0.0;
+        ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
+        ALN_CHECK(group_solve(c, tol, max_iter, X, X0, info));
+        ALN_TRY(cudaEventRecord(c->ev[5], c->stream));
+        ALN_TRY(cudaStreamSynchronize(c->stream));
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) c->stats.solve_ms = ms;
+        return ALN_OK;
+    }
     if (!X || ldx < c->n || !(tol > 0.0) || !std::isfinite(tol)) return ALN_ERR_INVALID_ARG;
     const int64_t n = c->n;
     if (max_iter <= 0) max_iter = (int32_t)std::max<int64_t>(5 * n, 20000);
@@ -455,6 +499,7 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
     c->stats.passive_rows = c->stats.clipped_rows = 0;
     c->stats.clipped_iterations = 0;
+    c->stats.product_bytes = 0.0;
     for (double& v : c->stats.phase_us) v = 0.0;
     c->stats.iterations = 0;
     ALN_TRY(cudaEventRecord(c->ev[4], c->stream));
@@ -562,6 +607,10 @@ aln_status aln_kkt_residual(aln_ctx* c, const double* X, int64_t ldx, double* re
                             double* objective) {
     if (!c) return ALN_ERR_INVALID_ARG;
     if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (c->grouped) {
+        if (!X || !rel_kkt) return ALN_ERR_INVALID_ARG;
+        return group_kkt(c, X, rel_kkt, objective);
+    }
     if (!X || !rel_kkt || ldx < c->n) return ALN_ERR_INVALID_ARG;
     const bool x_dev = is_device_ptr(X);
     const bool r_dev = is_device_ptr(rel_kkt);
@@ -585,6 +634,7 @@ aln_status aln_export_scaled(aln_ctx* c, double* Q, int64_t ldq, double* q, int6
                              double* s) {
     if (!c) return ALN_ERR_INVALID_ARG;
     if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (c->grouped) return group_export(c, Q, q, s);
     const int64_t n = c->n;
     if ((Q && ldq < n) || (q && ldqv < n)) return ALN_ERR_INVALID_ARG;
     if (Q) {

@@ -668,6 +668,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return ALN_ERR_CUDA;
     c->stats.passive_rows = (int64_t)rows[0];
     c->stats.clipped_rows = (int64_t)rows[1];
+    c->stats.product_bytes = 4.0 * (double)s.n * (rows[0] + rows[1]);
     c->stats.clipped_iterations = (int32_t)rows[2];
     return ALN_OK;
 }

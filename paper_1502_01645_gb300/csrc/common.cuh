@@ -107,6 +107,37 @@ __device__ __forceinline__ void load4(const double* p, double* o) {
     o[3] = b.y;
 }
 
+// Rounded products that the compiler may not fuse into a following add: the
+// error-free transformations below need fl(a·b) as a separate value.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// Per-thread accumulator of a dot product.  FP32 inputs use Dot2 (Ogita,
+// Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005):
+// the exact product error from an FMA (TwoProduct) and the exact addition
+// error (TwoSum) are carried in a second float, so the result is as accurate
+// as if accumulated in twice the working precision — without the FP64 pipe,
+// which is narrow on this GPU.  FP64 inputs accumulate in FP64.
+template <typename TA> struct DotAcc;
+template <> struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = mul_rn(a, b);
+        const float ep = fmaf(a, b, -p);   // a·b = p + ep exactly
+        const float t = s + p;
+        const float z = t - s;
+        const float es = (s - (t - z)) + (p - z);  // s + p = t + es exactly
+        s = t;
+        c += es + ep;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 // True when base + k·ld is 16-byte aligned for every k (vector loads allowed).
 inline bool aligned16(const void* base, int64_t ld, size_t esz) {
     return ((uintptr_t)base % 16 == 0) && ((ld * (int64_t)esz) % 16 == 0);
@@ -207,6 +238,9 @@ struct aln_ctx {
     // many right-hand sides sharing A (batch.cu); null when not in batch mode
     void* batch = nullptr;
     int batched = 0;
+    // many independent problems (grouped.cu); null unless aln_prepare_grouped
+    void* group = nullptr;
+    int grouped = 0;
 
     // statistics (aln_get_stats)
     cudaEvent_t ev[10] = {};

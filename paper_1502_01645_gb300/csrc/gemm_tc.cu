@@ -165,6 +165,62 @@ __device__ __forceinline__ void tri_decode(int64_t t, int& I, int& J) {
     J = (int)(t - r * (r + 1) / 2);
 }
 
+// Epilogue of one Gram output tile of an n×n matrix Q (row length ldq), rows
+// m0.., columns n0..: accumulator rows from tensor memory (warp w holds rows
+// 32w..32w+31), scaled by inv_s_i·inv_s_j (s_cs holds the column factors in
+// FP32), stored with their mirror.  Diagonal tiles keep the lower triangle and
+// mirror it, so Q is exactly symmetric, and set Q_ii = 1 (0 for a zero
+// column, Eq. Rescaling).
+__device__ __forceinline__ void gram_tile_store(uint32_t tmem, int warp, int lane, int64_t m0,
+                                                int64_t n0, bool diag, int64_t n,
+                                                const double* __restrict__ inv_s,
+                                                const float* s_cs, float* __restrict__ Q,
+                                                int64_t ldq) {
+    const int64_t row = m0 + warp * 32 + lane;
+    const bool rv = row < n;
+    const float rs = rv ? (float)inv_s[row] : 0.0f;
+    const int cols = (int)(n - n0 < (int64_t)BM ? n - n0 : (int64_t)BM);
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < cols; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + c0, v);
+        float o[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            o[t] = v[t] * rs * s_cs[c0 + t];
+            if (diag && row == n0 + c0 + t) o[t] = v[t] != 0.0f ? 1.0f : 0.0f;
+        }
+        const int64_t j0 = n0 + c0;
+        if (diag) {
+            // Diagonal tile: keep the lower triangle and mirror it, so Q is
+            // exactly symmetric (the two halves round differently).
+            if (rv) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int64_t j = j0 + t;
+                    if (c0 + t < cols && j <= row) {
+                        Q[row * ldq + j] = o[t];
+                        Q[j * ldq + row] = o[t];
+                    }
+                }
+            }
+        } else if (rv) {
+            float* dst = Q + row * ldq + j0;
+            if (c0 + 16 <= cols) {
+#pragma unroll
+                for (int t = 0; t < 16; t += 4)
+                    *reinterpret_cast<float4*>(dst + t) =
+                        make_float4(o[t], o[t + 1], o[t + 2], o[t + 3]);
+            } else {
+                for (int t = 0; t < cols - c0; ++t) dst[t] = o[t];
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if (c0 + t < cols) Q[(j0 + t) * ldq + row] = o[t];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
               GramArgs p) {
@@ -265,51 +321,147 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok) s_abort = 1;
     __syncthreads();
     if (!s_abort) {
-        const int64_t row = m0 + warp * 32 + lane;
-        const bool rv = row < p.n;
-        const float rs = rv ? (float)p.inv_s[row] : 0.0f;
-        const int cols = (int)(p.n - n0 < (int64_t)BM ? p.n - n0 : (int64_t)BM);
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < cols; c0 += 16) {
-            float v[16];
-            tmem_ld16(tbase + c0, v);
-            float o[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                o[t] = v[t] * rs * s_cs[c0 + t];
-                if (diag && row == n0 + c0 + t) o[t] = v[t] != 0.0f ? 1.0f : 0.0f;
-            }
-            const int64_t j0 = n0 + c0;
-            if (diag) {
-                // Diagonal tile: keep the lower triangle and mirror it, so Q is
-                // exactly symmetric (the two halves round differently).
-                if (rv) {
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) {
-                        const int64_t j = j0 + t;
-                        if (c0 + t < cols && j <= row) {
-                            p.Q[row * p.ldq + j] = o[t];
-                            p.Q[j * p.ldq + row] = o[t];
-                        }
-                    }
-                }
-            } else if (rv) {
-                float* dst = p.Q + row * p.ldq + j0;
-                if (c0 + 16 <= cols) {
-#pragma unroll
-                    for (int t = 0; t < 16; t += 4)
-                        *reinterpret_cast<float4*>(dst + t) =
-                            make_float4(o[t], o[t + 1], o[t + 2], o[t + 3]);
-                } else {
-                    for (int t = 0; t < cols - c0; ++t) dst[t] = o[t];
-                }
-#pragma unroll
-                for (int t = 0; t < 16; ++t)
-                    if (c0 + t < cols) p.Q[(j0 + t) * p.ldq + row] = o[t];
-            }
-        }
+        gram_tile_store(tmem, warp, lane, m0, n0, diag, p.n, p.inv_s, s_cs, p.Q, p.ldq);
     } else if (threadIdx.x == 0) {
         atomicExch(p.timeout_flag, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped Gram: the lower-triangle tiles of many problems' Q_p in one launch.
+// The operands come pre-tiled (pack_index): every 128×64 BF16 box is 16 KiB
+// contiguous in global memory, already in the 128-byte-swizzled order, so the
+// producer moves it with a 1-D bulk copy (cp.async.bulk) — no tensor map per
+// problem.  The tile table is sorted by K length (longest first) on the host.
+// Pipeline, MMA and epilogue are those of k_gram_tc.
+// ---------------------------------------------------------------------------
+struct GGramArgs {
+    const GProb* gp;
+    const GTile* tiles;
+    const __nv_bfloat16* hi;
+    const __nv_bfloat16* lo;
+    const double* inv_s;  // packed by GProb::voff
+    float* Q;             // pool; problem p at GProb::qoff, row length GProb::ldq
+    int* timeout_flag;
+};
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+    uint64_t gaddr;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(gaddr) : "l"(reinterpret_cast<uint64_t>(src)));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(gaddr), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) k_ggram_tc(GGramArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(done + 1);
+    __shared__ float s_cs[BM];
+    __shared__ int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const GTile tl = a.tiles[blockIdx.x];
+    const GProb P = a.gp[tl.p];
+    const int64_t m0 = (int64_t)tl.tm * BM, n0 = (int64_t)tl.tn * BM;
+    const bool diag = tl.tm == tl.tn;
+    const double* inv_s = a.inv_s + P.voff;
+    const int num_kb = P.KB;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    {
+        const int64_t j = n0 + threadIdx.x;
+        s_cs[threadIdx.x] = j < P.n ? (float)inv_s[j] : 0.0f;
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        const __nv_bfloat16* ah = a.hi + (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
+        const __nv_bfloat16* al = a.lo + (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
+        const __nv_bfloat16* bh = a.hi + (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
+        const __nv_bfloat16* bl = a.lo + (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
+        int issued = 0;
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            uint8_t* sb = smem + s * STAGE_BYTES;
+            const int64_t off = (int64_t)kb * kPackTile;
+            mbar_expect_tx(&full[s], (diag ? 2 : 4) * TILE_BYTES);
+            bulk_load(sb, ah + off, TILE_BYTES, &full[s]);
+            bulk_load(sb + TILE_BYTES, al + off, TILE_BYTES, &full[s]);
+            if (!diag) {
+                bulk_load(sb + 2 * TILE_BYTES, bh + off, TILE_BYTES, &full[s]);
+                bulk_load(sb + 3 * TILE_BYTES, bl + off, TILE_BYTES, &full[s]);
+            }
+            ++issued;
+        }
+        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_lo = a_hi + TILE_BYTES;
+            const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TILE_BYTES;
+            const uint32_t b_lo = diag ? a_lo : a_hi + 3 * TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+                const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
+                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                umma_bf16(tmem, dah, dbl, idesc, 1u);
+                umma_bf16(tmem, dal, dbh, idesc, 1u);
+            }
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ok) s_abort = 1;
+    __syncthreads();
+    if (!s_abort) {
+        gram_tile_store(tmem, warp, lane, m0, n0, diag, P.n, inv_s, s_cs, a.Q + P.qoff, P.ldq);
+    } else if (threadIdx.x == 0) {
+        atomicExch(a.timeout_flag, 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -545,6 +697,32 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
     k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, SMEM_BYTES, st>>>(mh, ml, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
+                            const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                            const double* inv_s, float* Q, int* timeout_flag, cudaStream_t st) {
+    using namespace tc;
+    if (ntiles <= 0) return cudaSuccess;
+    if (((uintptr_t)hi & 15) || ((uintptr_t)lo & 15) || ((uintptr_t)Q & 15))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_ggram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    GGramArgs a;
+    a.gp = gp;
+    a.tiles = tiles;
+    a.hi = hi;
+    a.lo = lo;
+    a.inv_s = inv_s;
+    a.Q = Q;
+    a.timeout_flag = timeout_flag;
+    k_ggram_tc<<<(unsigned)ntiles, 128, SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 

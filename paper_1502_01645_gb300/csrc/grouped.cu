@@ -1,0 +1,1310 @@
+// Alg. 1 and Alg. 2 (§3) on many independent NNLS problems of different sizes
+// in a few launches (the uneven-batch workload: hundreds of problems with n
+// from tens to a thousand).
+//
+//   k_gcolstats    one block per column slot of every problem: s_j = ‖A_j‖,
+//                  q_j = −A_jᵀb/s_j (Dot2, FP64-accurate), and the hi/lo BF16
+//                  split written straight into pre-swizzled 16 KiB operand
+//                  tiles (pack_index); slots past n_p zero their tile rows.
+//   k_ggram_tc     (gemm_tc.cu) every problem's lower-triangle Gram tiles in
+//                  one tcgen05 launch, tiles fed by 1-D bulk copies.
+//   k_galg2<T>     persistent: each 1024-thread block takes the next problem
+//                  from a longest-first queue and runs Alg. 2 on it alone —
+//                  iteration vectors in shared memory, Q_p staged in shared
+//                  memory when it fits (else read from L2), products over the
+//                  compacted passive / clipped index lists, no grid barrier.
+//   k_gkkt_*       FP64 KKT residual from A for every unfinished problem,
+//                  then the refinement decision (restart from the exact
+//                  gradient) in k_gkkt_final.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace aln {
+namespace {
+
+constexpr int kGThreads = 1024;
+constexpr int kGWarps = kGThreads / 32;
+constexpr int kGU = 8;            // columns of Q in flight per lane in the product
+constexpr int kGMaxN = 4096;      // largest n of a grouped problem
+constexpr int kKeySlot = 0, kKeyV = 1, kKeyR = 2;
+
+struct GStat {
+    int32_t iters;        // Alg. 2 iterations, summed over rounds
+    int32_t status;       // inner stop reason of the last run (aln_rhs_status)
+    int32_t clip_iters;   // iterations that needed the clipped correction
+    int32_t npassive;     // |P| at the end of the last run
+    int64_t sum_passive;  // Σ |P_k| (rows of Q read for Qḡ)
+    int64_t sum_clip;     // Σ |C_k|
+    double gbar2;         // ‖ḡ‖² (iteration precision) at the end of the last run
+};
+
+template <int KEY>
+__device__ __forceinline__ int64_t gkey(const GProb& g) {
+    return KEY == kKeySlot ? g.slot : (KEY == kKeyV ? g.voff : g.roff);
+}
+// Largest p with key(p) ≤ x (keys strictly increase with p).
+template <int KEY>
+__device__ __forceinline__ int find_prob(const GProb* __restrict__ gp, int count, int64_t x) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (gkey<KEY>(gp[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Prepare (Alg. 1): scale factors, q, split operand tiles
+// ---------------------------------------------------------------------------
+template <typename TA>
+__global__ void __launch_bounds__(128) k_gcolstats(const GProb* __restrict__ gp, int count,
+                                                   int split, double* __restrict__ s,
+                                                   double* __restrict__ inv_s,
+                                                   double* __restrict__ q64, int* __restrict__ flags,
+                                                   __nv_bfloat16* __restrict__ hi,
+                                                   __nv_bfloat16* __restrict__ lo) {
+    __shared__ double scratch[32];
+    const int p = find_prob<kKeySlot>(gp, count, blockIdx.x);
+    const GProb P = gp[p];
+    const int j = (int)((int64_t)blockIdx.x - P.slot);
+    const int kpad = P.KB * 64;
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+    if (j >= P.n) {  // rows of the last operand tile past n_p: zero
+        if (split)
+            for (int t = threadIdx.x; t < kpad; t += blockDim.x) {
+                const int64_t e = pack_index(P.pack, P.KB, j, t);
+                hi[e] = z;
+                lo[e] = z;
+            }
+        return;
+    }
+    const TA* col = (const TA*)P.A + (int64_t)j * P.lda;
+    const TA* b = (const TA*)P.b;
+    DotAcc<TA> sq, dot;
+    bool bad = false;
+    for (int t0 = threadIdx.x; t0 < P.d; t0 += 4 * blockDim.x) {
+        TA av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * blockDim.x;
+            av[u] = t < P.d ? col[t] : TA(0);
+            bv[u] = t < P.d ? b[t] : TA(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            sq.add(av[u], av[u]);
+            dot.add(av[u], bv[u]);
+            bad |= !isfinite(av[u]) || !isfinite(bv[u]);
+            const int t = t0 + u * blockDim.x;
+            if (split && t < P.d) {
+                const float af = (float)av[u];
+                const __nv_bfloat16 h = __float2bfloat16_rn(af);
+                const int64_t e = pack_index(P.pack, P.KB, j, t);
+                hi[e] = h;
+                lo[e] = __float2bfloat16_rn(af - __bfloat162float(h));
+            }
+        }
+    }
+    if (split)
+        for (int t = P.d + threadIdx.x; t < kpad; t += blockDim.x) {
+            const int64_t e = pack_index(P.pack, P.KB, j, t);
+            hi[e] = z;
+            lo[e] = z;
+        }
+    const double s2 = block_sum(sq.value(), scratch);
+    const double ab = block_sum(dot.value(), scratch);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        // Eq. Rescaling: s_j = √H_jj, and s_j := 1 for a zero column
+        const double sj = s2 > 0.0 ? sqrt(s2) : 1.0;
+        s[P.voff + j] = sj;
+        inv_s[P.voff + j] = 1.0 / sj;
+        q64[P.voff + j] = -ab / sj;  // q = −D⁻¹Aᵀb (Eq. NQPQ)
+        if (bad) atomicOr(flags, 1);
+    }
+}
+
+// ‖min(q_p, 0)‖ per problem (the projected gradient at y = 0) and ‖b_p‖².
+template <typename TA>
+__global__ void __launch_bounds__(256) k_gden(const GProb* __restrict__ gp,
+                                              const double* __restrict__ q64,
+                                              double* __restrict__ den, double* __restrict__ bn2) {
+    __shared__ double scratch[32];
+    const GProb P = gp[blockIdx.x];
+    double v = 0.0, w = 0.0;
+    for (int i = threadIdx.x; i < P.n; i += blockDim.x) {
+        const double qi = q64[P.voff + i];
+        const double m = qi < 0.0 ? qi : 0.0;
+        v = fma(m, m, v);
+    }
+    const TA* b = (const TA*)P.b;
+    for (int t = threadIdx.x; t < P.d; t += blockDim.x) {
+        const double bt = (double)b[t];
+        w = fma(bt, bt, w);
+    }
+    v = block_sum(v, scratch);
+    w = block_sum(w, scratch);
+    if (threadIdx.x == 0) {
+        den[blockIdx.x] = sqrt(v);
+        bn2[blockIdx.x] = w;
+    }
+}
+
+// Q_p (FP32, split-BF16 Gram) → FP64 packed row-major n_p×n_p blocks.
+template <typename T>
+__global__ void k_gexport_q(const GProb* __restrict__ gp, const T* __restrict__ Q,
+                            const int64_t* __restrict__ qout_off, double* __restrict__ out) {
+    const GProb P = gp[blockIdx.x];
+    const int64_t nn = (int64_t)P.n * P.n;
+    double* dst = out + qout_off[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int64_t i = e / P.n, j = e - i * P.n;
+        dst[e] = (double)Q[P.qoff + i * P.ldq + j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 2, one problem per block
+// ---------------------------------------------------------------------------
+template <typename T>
+struct GSolveArgs {
+    const GProb* gp;
+    const int* order;      // problems of this run, largest first
+    int nactive;
+    int* queue;            // next index into order (zeroed before the launch)
+    const T* Q;            // pool
+    const double* q64;     // packed (voff)
+    const double* g64;     // packed (voff): exact gradient for a restart (gmode 1)
+    const double* den;     // per problem ‖min(q,0)‖
+    double* y;             // packed (foff), in/out
+    GStat* stat;
+    double stop_factor;    // inner stop: ‖ḡ‖ < stop_factor·den_p
+    int gmode;             // 0: g = Q y + q here; 1: g = g64
+    int max_iter;
+    int window;
+    int smem_bytes;
+};
+
+template <typename T>
+__device__ __forceinline__ T gwarp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int gwarp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Exclusive prefix over lanes of v; *total receives the sum of all lanes.
+__device__ __forceinline__ int gwarp_scan_excl(int v, int* total) {
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Shared scratch of the block-wide reductions and list builders.
+template <typename T>
+struct GRed {
+    T wsum[kGWarps];
+    int wcnt[kGWarps];
+    int wlist[kGWarps];
+};
+
+// Contiguous range of 32-element chunks scanned by this warp.
+__device__ __forceinline__ void warp_chunks(int n, int& c0, int& c1) {
+    const int nchunk = (n + 31) >> 5;
+    const int per = (nchunk + kGWarps - 1) / kGWarps;
+    c0 = (threadIdx.x >> 5) * per;
+    c1 = min(nchunk, c0 + per);
+}
+
+// Reduce per-warp (value, count, list count) and give each warp its list
+// base; every thread receives the totals (identical in every lane and warp).
+template <typename T>
+__device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, T* vt, int* ct,
+                                            int* lt) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = gwarp_sum(v);
+    __syncthreads();  // earlier readers of r are done
+    if (lane == 0) {
+        r->wsum[wid] = v;
+        r->wcnt[wid] = cnt;
+        r->wlist[wid] = lcnt;
+    }
+    __syncthreads();
+    *vt = gwarp_sum(r->wsum[lane]);
+    *ct = gwarp_sum_i(r->wcnt[lane]);
+    int total;
+    const int ex = gwarp_scan_excl(r->wlist[lane], &total);
+    *lt = total;
+    return __shfl_sync(0xffffffffu, ex, wid);
+}
+
+// Passive set of Alg. 2 (strict: y_i > 0 or g_i < 0), ḡ = g on P, ‖ḡ‖²,
+// |P|, and the ascending list of i with ḡ_i ≠ 0 (the columns of Q the
+// product needs).
+template <typename T>
+__device__ __forceinline__ void gmask(int n, const T* sy, const T* sg, T* sgb, int* list,
+                                      GRed<T>* r, T* gam, int* cntP, int* cntL) {
+    const int lane = threadIdx.x & 31;
+    int c0, c1;
+    warp_chunks(n, c0, c1);
+    T v = T(0);
+    int cp = 0, cl = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int i = c * 32 + lane;
+        T gb = T(0);
+        bool P = false;
+        if (i < n) {
+            const T yi = sy[i], gi = sg[i];
+            P = yi > T(0) || gi < T(0);
+            gb = P ? gi : T(0);
+            sgb[i] = gb;
+        }
+        v = fma(gb, gb, v);
+        cp += __popc(__ballot_sync(0xffffffffu, P));
+        cl += __popc(__ballot_sync(0xffffffffu, gb != T(0)));
+    }
+    int base = block_totals(r, v, cp, cl, gam, cntP, cntL);
+    for (int c = c0; c < c1; ++c) {
+        const int i = c * 32 + lane;
+        const bool nz = i < n && sgb[i] != T(0);
+        const unsigned int m = __ballot_sync(0xffffffffu, nz);
+        if (nz) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+        base += __popc(m);
+    }
+    __syncthreads();
+}
+
+// Ascending list of i < n with v_i ≠ 0; returns its length (all threads).
+template <typename T>
+__device__ __forceinline__ int glist(int n, const T* v, int* list, GRed<T>* r) {
+    const int lane = threadIdx.x & 31;
+    int c0, c1;
+    warp_chunks(n, c0, c1);
+    int cl = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int i = c * 32 + lane;
+        cl += __popc(__ballot_sync(0xffffffffu, i < n && v[i] != T(0)));
+    }
+    T vt;
+    int ct, lt;
+    int base = block_totals(r, T(0), 0, cl, &vt, &ct, &lt);
+    for (int c = c0; c < c1; ++c) {
+        const int i = c * 32 + lane;
+        const bool nz = i < n && v[i] != T(0);
+        const unsigned int m = __ballot_sync(0xffffffffu, nz);
+        if (nz) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+        base += __popc(m);
+    }
+    __syncthreads();
+    return lt;
+}
+
+// out[i] (+)= Σ_k Q[list[k]][i] · v[list[k]] for i < n — the product of Alg. 2
+// restricted to the listed columns (Q is symmetric; row list[k] is read).
+// Warps split the row into 32·VN-wide tiles and the list into S strided
+// subsets; the S partials are added in subset order (deterministic).
+template <typename T>
+__device__ __forceinline__ void gmv(const T* Q, int ldq, int n, const int* list, int cnt,
+                                    const T* v, T* out, bool accumulate, T* red) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    constexpr int TILE = 32 * VN;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int CT = (n + TILE - 1) / TILE;
+    const int CTw = CT < kGWarps ? CT : kGWarps;
+    const int S = kGWarps / CTw;
+    const int sub = wid / CTw;
+    if (sub < S) {
+        for (int ct = wid % CTw; ct < CT; ct += CTw) {
+            const int col = ct * TILE + lane * VN;
+            const bool cv = col < n;  // then col + VN ≤ ldq (ldq is a multiple of 4)
+            T acc[VN];
+#pragma unroll
+            for (int c = 0; c < VN; ++c) acc[c] = T(0);
+            int k = sub;
+            for (; k + (kGU - 1) * S < cnt; k += kGU * S) {
+                V qq[kGU];
+                T vv[kGU];
+#pragma unroll
+                for (int u = 0; u < kGU; ++u) {
+                    const int j = list[k + u * S];
+                    qq[u] = cv ? *reinterpret_cast<const V*>(Q + (int64_t)j * ldq + col) : V{};
+                    vv[u] = v[j];
+                }
+#pragma unroll
+                for (int u = 0; u < kGU; ++u)
+#pragma unroll
+                    for (int c = 0; c < VN; ++c) acc[c] = fma(vv[u], vget(qq[u], c), acc[c]);
+            }
+            for (; k < cnt; k += S) {
+                const int j = list[k];
+                const V q = cv ? *reinterpret_cast<const V*>(Q + (int64_t)j * ldq + col) : V{};
+                const T vj = v[j];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) acc[c] = fma(vj, vget(q, c), acc[c]);
+            }
+            if (S == 1) {
+                if (cv)
+#pragma unroll
+                    for (int c = 0; c < VN; ++c)
+                        if (col + c < n) out[col + c] = accumulate ? out[col + c] + acc[c] : acc[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < VN; ++c) red[(sub * CT + ct) * TILE + lane * VN + c] = acc[c];
+            }
+        }
+    }
+    if (S > 1) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int ct = i / TILE, rr = i - ct * TILE;
+            T s = T(0);
+            for (int s2 = 0; s2 < S; ++s2) s += red[(s2 * CT + ct) * TILE + rr];
+            out[i] = accumulate ? out[i] + s : s;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
+    constexpr int VN = Vec16<T>::N;
+    constexpr int TILE = 32 * VN;
+    __shared__ GRed<T> rs;
+    __shared__ T s_alpha;
+    __shared__ int s_flag;
+    const GProb P = a.gp[p];
+    const int n = P.n, ldq = P.ldq;
+    // The iterate is a pair y = sy + syl (|syl| ≤ ulp(sy)/2), about 48 bits in
+    // the FP32 case: the FP64 refinement rounds then converge to FP64-level
+    // KKT residuals instead of stalling at the rounding of y to FP32.
+    T* sy = reinterpret_cast<T*>(sm);
+    T* syl = sy + ldq;
+    T* sg = syl + ldq;
+    T* sgb = sg + ldq;
+    T* sw = sgb + ldq;  // w = Qḡ, then e (the clipped part of the step)
+    int* lp = reinterpret_cast<int*>(sw + ldq);
+    int* lc = lp + ldq;
+    T* red = reinterpret_cast<T*>(lc + ldq);
+    T* sQ = red + kGWarps * TILE;
+    const int64_t used = (int64_t)((uint8_t*)sQ - sm);
+    const bool qin = (int64_t)n * ldq * (int64_t)sizeof(T) <= (int64_t)a.smem_bytes - used;
+    const T* Qg = a.Q + P.qoff;
+    if (qin) {  // stage Q_p in shared memory for all iterations
+        using V = typename Vec16<T>::type;
+        const int64_t nv = (int64_t)n * ldq / VN;
+        const V* src = reinterpret_cast<const V*>(Qg);
+        V* dst = reinterpret_cast<V*>(sQ);
+        for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) dst[e] = __ldg(src + e);
+    }
+    const T* Qp = qin ? sQ : Qg;
+    const double* q = a.q64 + P.voff;
+    for (int i = threadIdx.x; i < ldq; i += blockDim.x) {
+        const double yv = i < n ? a.y[P.foff + i] : 0.0;
+        const T yh = (T)yv;
+        sy[i] = yh;
+        syl[i] = (T)(yv - (double)yh);
+        sw[i] = T(0);
+        if (a.gmode == 1) sg[i] = i < n ? (T)a.g64[P.voff + i] : T(0);
+    }
+    __syncthreads();
+    if (a.gmode == 0) {
+        // g = Q y + q (Alg. 2 start; y = 0 gives g = q)
+        const int cy = glist(n, sy, lp, &rs);
+        gmv(Qp, ldq, n, lp, cy, sy, sg, false, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sg[i] += (T)q[i];
+        __syncthreads();
+    }
+
+    GStat st = a.stat[p];
+    const double sf = a.stop_factor * a.den[p];
+    const T eps = (T)(sf * sf);
+    const int max_iter = a.max_iter, window = a.window;
+    int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
+    T best = T(1.0 / 0.0);
+    int64_t sum_passive = 0, sum_clip = 0;
+    int clip_iters = 0;
+    T gam;
+    int cntP, cntL;
+    gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int stop = 1;
+            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            else if (cntP == 0) status = ALN_RHS_EMPTY_PASSIVE;
+            else if (gam < eps || gam == T(0)) status = ALN_RHS_CONVERGED;
+            else if (iter >= max_iter) status = ALN_RHS_MAXITER;
+            else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
+            else stop = 0;
+            if (!stop && gam < best) {
+                best = gam;
+                best_iter = iter;
+            }
+            s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) break;
+        // w = Qḡ over the passive columns, κ = ḡᵀw, α = ‖ḡ‖²/κ (exact line search)
+        gmv(Qp, ldq, n, lp, cntL, sgb, sw, false, red);
+        T kp = T(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fma(sgb[i], sw[i], kp);
+        T kap;
+        int unused_c, unused_l;
+        (void)block_totals(&rs, kp, 0, 0, &kap, &unused_c, &unused_l);
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (!isfinite(kap)) {
+                status = ALN_RHS_NONFINITE;
+                stop = 1;
+            } else if (kap <= T(0)) {
+                status = ALN_RHS_CURVATURE;
+                stop = 1;
+            }
+            s_alpha = stop ? T(0) : gam / kap;
+            s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const T alpha = s_alpha;
+        sum_passive += cntP;
+        // y⁺ = [y − αḡ]₊, g ← g − αw, e = y⁺ − (y − αḡ) on the clipped set;
+        // then g ← g + Q e, so that g = Q y⁺ + q (Q(y⁺ − y) = −αw + Qe)
+        int nclip = 0;
+        {
+            const int lane = threadIdx.x & 31;
+            int c0, c1;
+            warp_chunks(n, c0, c1);
+            int cl = 0;
+            for (int c = c0; c < c1; ++c) {
+                const int i = c * 32 + lane;
+                T ei = T(0);
+                if (i < n) {
+                    // (yh, yl) − step, exactly: TwoSum, then renormalise
+                    const T yh = sy[i], yl = syl[i];
+                    const T step = mul_rn(alpha, sgb[i]);
+                    const T s1 = yh - step;
+                    const T bb = s1 - yh;
+                    const T er = (yh - (s1 - bb)) + (-step - bb);
+                    const T t = yl + er;
+                    T nh = s1 + t;
+                    T nl = t - (nh - s1);
+                    if (nh < T(0)) {  // clipped: y⁺ = 0, e = y⁺ − (y − αḡ)
+                        ei = -(nh + nl);
+                        nh = T(0);
+                        nl = T(0);
+                    }
+                    sy[i] = nh;
+                    syl[i] = nl;
+                    sg[i] = sg[i] - alpha * sw[i];
+                    sw[i] = ei;
+                }
+                cl += __popc(__ballot_sync(0xffffffffu, ei != T(0)));
+            }
+            T vt;
+            int ct;
+            int base = block_totals(&rs, T(0), 0, cl, &vt, &ct, &nclip);
+            for (int c = c0; c < c1; ++c) {
+                const int i = c * 32 + lane;
+                const bool nz = i < n && sw[i] != T(0);
+                const unsigned int m = __ballot_sync(0xffffffffu, nz);
+                if (nz) lc[base + __popc(m & ((1u << lane) - 1u))] = i;
+                base += __popc(m);
+            }
+            __syncthreads();
+        }
+        ++iter;
+        sum_clip += nclip;
+        if (nclip > 0) {
+            gmv(Qp, ldq, n, lc, nclip, sw, sg, true, red);
+            ++clip_iters;
+        }
+        gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        a.y[P.foff + i] = (double)sy[i] + (double)syl[i];
+    if (threadIdx.x == 0) {
+        st.iters = iter;
+        st.status = status;
+        st.clip_iters += clip_iters;
+        st.npassive = cntP;
+        st.sum_passive += sum_passive;
+        st.sum_clip += sum_clip;
+        st.gbar2 = (double)gam;
+        a.stat[p] = st;
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGThreads, 1) k_galg2(GSolveArgs<T> a) {
+    extern __shared__ __align__(16) uint8_t gsm[];
+    __shared__ int s_p;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int k = atomicAdd(a.queue, 1);
+            s_p = k < a.nactive ? a.order[k] : -1;
+        }
+        __syncthreads();
+        const int p = s_p;
+        __syncthreads();
+        if (p < 0) break;
+        solve_one<T>(a, p, gsm);
+    }
+}
+
+template <typename T>
+size_t gsolve_static_bytes(int ldq) {
+    constexpr int TILE = 32 * Vec16<T>::N;
+    return (size_t)ldq * (5 * sizeof(T) + 2 * sizeof(int)) + (size_t)kGWarps * TILE * sizeof(T);
+}
+
+// y = x0·s (or 0), per problem.
+__global__ void k_ginit(const GProb* __restrict__ gp, int count, int64_t total,
+                        const double* __restrict__ x0, const double* __restrict__ s,
+                        double* __restrict__ y, GStat* __restrict__ stat, int* __restrict__ fin,
+                        int* __restrict__ rounds) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = find_prob<kKeyV>(gp, count, e);
+        const GProb& P = gp[p];
+        const int j = (int)(e - P.voff);
+        y[P.foff + j] = x0 ? x0[e] * s[e] : 0.0;
+        if (j == 0) {
+            GStat z = {};
+            stat[p] = z;
+            fin[p] = -1;
+            rounds[p] = 0;
+        }
+    }
+}
+
+// x = y/s (Eq. Rescaling), FP64.
+__global__ void k_gunscale(const GProb* __restrict__ gp, int count, int64_t total,
+                           const double* __restrict__ y, const double* __restrict__ s,
+                           double* __restrict__ x) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = find_prob<kKeyV>(gp, count, e);
+        const GProb& P = gp[p];
+        x[e] = y[P.foff + (e - P.voff)] / s[e];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 KKT from A for the problems still open (fin < 0)
+// ---------------------------------------------------------------------------
+// r = A x − b, one thread per row of every open problem.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_gkkt_r(const GProb* __restrict__ gp, int count,
+                                                int64_t total, const double* __restrict__ x,
+                                                const int* __restrict__ fin,
+                                                double* __restrict__ r) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = find_prob<kKeyR>(gp, count, e);
+        if (fin[p] >= 0) continue;
+        const GProb& P = gp[p];
+        const int i = (int)(e - P.roff);
+        const TA* A = (const TA*)P.A;
+        const double* xp = x + P.voff;
+        double acc = -(double)((const TA*)P.b)[i];
+        for (int j = 0; j < P.n; ++j) {
+            const double xj = xp[j];
+            if (xj != 0.0) acc = fma((double)A[(int64_t)j * P.lda + i], xj, acc);
+        }
+        r[e] = acc;
+    }
+}
+
+// ∇F_j = A_jᵀr, g_j = ∇F_j/s_j, ḡ_j² on P(y = s·x): one warp per column.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_gkkt_g(const GProb* __restrict__ gp, int count,
+                                                int64_t total, const double* __restrict__ x,
+                                                const double* __restrict__ s,
+                                                const double* __restrict__ r,
+                                                const int* __restrict__ fin,
+                                                double* __restrict__ g64,
+                                                double* __restrict__ gpart) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total;
+         e += warps) {
+        const int p = find_prob<kKeyV>(gp, count, e);
+        if (fin[p] >= 0) continue;
+        const GProb& P = gp[p];
+        const int j = (int)(e - P.voff);
+        const TA* col = (const TA*)P.A + (int64_t)j * P.lda;
+        const double* rp = r + P.roff;
+        double acc = 0.0;
+        for (int i = lane; i < P.d; i += 32) acc = fma((double)col[i], rp[i], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double gj = acc / s[e];
+            const double yj = x[e] * s[e];
+            const bool Pj = yj > 0.0 || gj < 0.0;
+            g64[e] = gj;
+            gpart[e] = Pj ? gj * gj : 0.0;
+        }
+    }
+}
+
+// Per open problem: rel_kkt = ‖ḡ‖/‖min(q,0)‖, F = ½‖r‖², and the decision:
+// converged, terminal, or one more round from the exact gradient.
+__global__ void __launch_bounds__(256) k_gkkt_final(const GProb* __restrict__ gp,
+                                                    const double* __restrict__ gpart,
+                                                    const double* __restrict__ r,
+                                                    const double* __restrict__ den,
+                                                    const GStat* __restrict__ stat, double tol,
+                                                    int max_iter, int max_refine, int refining,
+                                                    int* __restrict__ fin,
+                                                    int* __restrict__ rounds,
+                                                    int* __restrict__ again,
+                                                    double* __restrict__ rel_out,
+                                                    double* __restrict__ obj_out) {
+    __shared__ double scratch[32];
+    const int p = blockIdx.x;
+    if (fin[p] >= 0) return;
+    const GProb P = gp[p];
+    double g2 = 0.0, r2 = 0.0;
+    for (int j = threadIdx.x; j < P.n; j += blockDim.x) g2 += gpart[P.voff + j];
+    for (int i = threadIdx.x; i < P.d; i += blockDim.x) {
+        const double ri = r[P.roff + i];
+        r2 = fma(ri, ri, r2);
+    }
+    g2 = block_sum(g2, scratch);
+    r2 = block_sum(r2, scratch);
+    if (threadIdx.x == 0) {
+        const double num = sqrt(g2);
+        const double rel = den[p] > 0.0 ? num / den[p] : num;
+        rel_out[p] = rel;
+        obj_out[p] = 0.5 * r2;
+        const int inner = stat[p].status;
+        int f = -1;
+        if (!refining) {
+            f = ALN_RHS_CONVERGED;  // evaluation only (aln_kkt_residual)
+        } else if (rel <= tol) {
+            f = inner == ALN_RHS_EMPTY_PASSIVE ? ALN_RHS_EMPTY_PASSIVE : ALN_RHS_CONVERGED;
+        } else if (inner == ALN_RHS_NONFINITE || inner == ALN_RHS_MAXITER ||
+                   stat[p].iters >= max_iter) {
+            f = inner == ALN_RHS_NONFINITE ? ALN_RHS_NONFINITE : ALN_RHS_MAXITER;
+        } else if (rounds[p] >= max_refine) {
+            f = inner == ALN_RHS_STAGNATED ? ALN_RHS_STAGNATED : ALN_RHS_MAXITER;
+        } else {
+            rounds[p] += 1;
+        }
+        if (f >= 0) fin[p] = f;
+        again[p] = f < 0 ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct GroupWork {
+    int count = 0;
+    int32_t dtype = ALN_DTYPE_F32;
+    int64_t sum_n = 0, sum_d = 0, sum_f = 0, sum_nn = 0;
+    int max_ldq = 0;
+    std::vector<GProb> hp;        // host copy of the records
+    std::vector<int> order_all;   // problems, largest n first
+    std::vector<int64_t> qexp;    // offsets of the exported packed Q blocks
+
+    void* pool = nullptr;         // device: everything below
+    size_t pool_bytes = 0;
+    GProb* gp = nullptr;
+    GTile* tiles = nullptr;
+    int64_t ntiles = 0;
+    int* order = nullptr;
+    int* queue = nullptr;
+    int* fin = nullptr;
+    int* rounds = nullptr;
+    int* again = nullptr;
+    int* flags = nullptr;         // [0] nonfinite input, [1] tensor-core timeout
+    int64_t* qexp_dev = nullptr;
+    GStat* stat = nullptr;
+    double *s = nullptr, *inv_s = nullptr, *q64 = nullptr, *g64 = nullptr, *x64 = nullptr,
+           *gpart = nullptr, *r64 = nullptr, *den = nullptr, *bn2 = nullptr, *rel = nullptr,
+           *obj = nullptr;
+    void* y = nullptr;            // packed (foff), iteration type
+    void* Q = nullptr;            // pool, iteration type
+    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+
+    void* copies = nullptr;       // device copies of host inputs
+    size_t copies_bytes = 0;
+    void* host = nullptr;         // pinned: again/fin/rounds, rel, obj, stat
+    size_t host_bytes = 0;
+    int smem_bytes = 0;
+    int grid = 0;
+    int64_t slots = 0;              // column slots of the prepare grid
+    std::vector<aln_problem> last;  // records of the last layout
+    int last_prec = -1;
+    bool reuse_ok = false;          // last layout used device inputs only
+};
+
+bool is_dev(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+aln_status cuda_err(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return ALN_ERR_OUT_OF_MEMORY;
+    }
+    return ALN_ERR_CUDA;
+}
+#define G_TRY(call)                                    \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_err(e_);    \
+    } while (0)
+#define G_CHECK(call)                 \
+    do {                              \
+        aln_status s_ = (call);       \
+        if (s_ != ALN_OK) return s_;  \
+    } while (0)
+
+aln_status grow(void** p, size_t* cap, size_t bytes) {
+    if (*p && *cap >= bytes) return ALN_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ALN_ERR_OUT_OF_MEMORY;
+    }
+    *cap = bytes;
+    return ALN_OK;
+}
+
+unsigned grid_for(int64_t work, int threads, int cap) {
+    const int64_t b = (work + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+template <typename T>
+aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, double stop_factor, int gmode,
+                      int max_iter) {
+    GSolveArgs<T> a;
+    a.gp = g->gp;
+    a.order = g->order;
+    a.nactive = nactive;
+    a.queue = g->queue;
+    a.Q = (const T*)g->Q;
+    a.q64 = g->q64;
+    a.g64 = g->g64;
+    a.den = g->den;
+    a.y = (double*)g->y;
+    a.stat = g->stat;
+    a.stop_factor = stop_factor;
+    a.gmode = gmode;
+    a.max_iter = max_iter;
+    a.window = c->opt.stagnation;
+    a.smem_bytes = g->smem_bytes;
+    G_TRY(cudaFuncSetAttribute(k_galg2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               g->smem_bytes));
+    G_TRY(cudaMemsetAsync(g->queue, 0, sizeof(int), c->stream));
+    const int grid = std::min(nactive, g->grid);
+    k_galg2<T><<<grid, kGThreads, g->smem_bytes, c->stream>>>(a);
+    G_TRY(cudaGetLastError());
+    c->launches += 1;
+    return ALN_OK;
+}
+
+aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_refine,
+                    int refining) {
+    const unsigned gr = grid_for(g->sum_d, 256, 8 * c->num_sms);
+    const unsigned gg = grid_for(g->sum_n * 32, 256, 16 * c->num_sms);
+    if (g->dtype == ALN_DTYPE_F32) {
+        k_gkkt_r<float><<<gr, 256, 0, c->stream>>>(g->gp, g->count, g->sum_d, g->x64, g->fin,
+                                                   g->r64);
+        k_gkkt_g<float><<<gg, 256, 0, c->stream>>>(g->gp, g->count, g->sum_n, g->x64, g->s,
+                                                   g->r64, g->fin, g->g64, g->gpart);
+    } else {
+        k_gkkt_r<double><<<gr, 256, 0, c->stream>>>(g->gp, g->count, g->sum_d, g->x64, g->fin,
+                                                    g->r64);
+        k_gkkt_g<double><<<gg, 256, 0, c->stream>>>(g->gp, g->count, g->sum_n, g->x64, g->s,
+                                                    g->r64, g->fin, g->g64, g->gpart);
+    }
+    k_gkkt_final<<<g->count, 256, 0, c->stream>>>(g->gp, g->gpart, g->r64, g->den, g->stat, tol,
+                                                  max_iter, max_refine, refining, g->fin,
+                                                  g->rounds, g->again, g->rel, g->obj);
+    G_TRY(cudaGetLastError());
+    c->launches += 3;
+    return ALN_OK;
+}
+
+}  // namespace
+
+void group_free(aln_ctx* c) {
+    GroupWork* g = (GroupWork*)c->group;
+    if (!g) return;
+    if (g->pool) cudaFree(g->pool);
+    if (g->copies) cudaFree(g->copies);
+    if (g->host) cudaFreeHost(g->host);
+    delete g;
+    c->group = nullptr;
+    c->grouped = 0;
+}
+
+// Layout, device pool and records of a new group (host inputs are copied).
+static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const aln_problem* probs,
+                        int32_t dtype) {
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
+    const size_t esz = dtype == ALN_DTYPE_F64 ? 8 : 4;
+    const size_t T = f64 ? 8 : 4;
+    g->count = count;
+    g->dtype = dtype;
+    g->hp.assign(count, GProb{});
+
+    // host inputs → one device block of copies
+    size_t copy_bytes = 0;
+    std::vector<char> a_dev(count), b_dev(count);
+    for (int p = 0; p < count; ++p) {
+        const aln_problem& q = probs[p];
+        a_dev[p] = is_dev(q.A);
+        b_dev[p] = is_dev(q.b);
+        if (!a_dev[p]) copy_bytes += round_up((size_t)((q.n - 1) * q.lda + q.d) * esz, 256);
+        if (!b_dev[p]) copy_bytes += round_up((size_t)q.d * esz, 256);
+    }
+    if (copy_bytes) G_CHECK(grow(&g->copies, &g->copies_bytes, copy_bytes));
+    uint8_t* cp = (uint8_t*)g->copies;
+
+    // layout of every problem
+    int64_t slot = 0, pack = 0, qoff = 0, voff = 0, foff = 0, roff = 0, nn = 0;
+    g->qexp.assign(count, 0);
+    g->max_ldq = 0;
+    std::vector<GTile> tiles;
+    for (int p = 0; p < count; ++p) {
+        const aln_problem& q = probs[p];
+        GProb& P = g->hp[p];
+        P.lda = q.lda;
+        P.d = (int32_t)q.d;
+        P.n = (int32_t)q.n;
+        P.T = (int32_t)ceil_div(q.n, 128);
+        P.KB = (int32_t)ceil_div(q.d, 64);
+        P.ldq = (int32_t)round_up(q.n, 4);
+        P.slot = slot;
+        P.pack = pack;
+        P.qoff = qoff;
+        P.voff = voff;
+        P.foff = foff;
+        P.roff = roff;
+        g->qexp[p] = nn;
+        slot += 128 * (int64_t)P.T;
+        pack += (int64_t)P.T * P.KB;
+        qoff += (int64_t)P.n * P.ldq;
+        voff += P.n;
+        foff += P.ldq;
+        roff += P.d;
+        nn += (int64_t)P.n * P.n;
+        g->max_ldq = std::max(g->max_ldq, P.ldq);
+        if (a_dev[p]) {
+            P.A = q.A;
+        } else {
+            const size_t bytes = (size_t)((q.n - 1) * q.lda + q.d) * esz;
+            G_TRY(cudaMemcpyAsync(cp, q.A, bytes, cudaMemcpyHostToDevice, c->stream));
+            P.A = cp;
+            cp += round_up(bytes, 256);
+        }
+        if (b_dev[p]) {
+            P.b = q.b;
+        } else {
+            const size_t bytes = (size_t)q.d * esz;
+            G_TRY(cudaMemcpyAsync(cp, q.b, bytes, cudaMemcpyHostToDevice, c->stream));
+            P.b = cp;
+            cp += round_up(bytes, 256);
+        }
+        for (int tm = 0; tm < P.T; ++tm)
+            for (int tn = 0; tn <= tm; ++tn) tiles.push_back(GTile{p, tm, tn, 0});
+    }
+    g->sum_n = voff;
+    g->sum_d = roff;
+    g->sum_f = foff;
+    g->sum_nn = nn;
+    // longest K first, so the long tiles do not end up in the last wave
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const GTile& x, const GTile& y) {
+        return g->hp[x.p].KB > g->hp[y.p].KB;
+    });
+    g->ntiles = f64 ? 0 : (int64_t)tiles.size();
+    g->order_all.resize(count);
+    std::iota(g->order_all.begin(), g->order_all.end(), 0);
+    std::stable_sort(g->order_all.begin(), g->order_all.end(), [&](int x, int y) {
+        return g->hp[x].n > g->hp[y].n;
+    });
+
+    // device pool
+    const size_t pack_elems = f64 ? 0 : (size_t)pack * kPackTile;
+    size_t sizes[] = {
+        (size_t)count * sizeof(GProb),                 // gp
+        (size_t)std::max<int64_t>(g->ntiles, 1) * sizeof(GTile),  // tiles
+        (size_t)count * sizeof(int),                   // order
+        sizeof(int) * 4,                               // queue
+        (size_t)count * sizeof(int),                   // fin
+        (size_t)count * sizeof(int),                   // rounds
+        (size_t)count * sizeof(int),                   // again
+        sizeof(int) * 4,                               // flags
+        (size_t)count * sizeof(int64_t),               // qexp
+        (size_t)count * sizeof(GStat),                 // stat
+        (size_t)voff * 8, (size_t)voff * 8, (size_t)voff * 8, (size_t)voff * 8,
+        (size_t)voff * 8, (size_t)voff * 8,            // s, inv_s, q64, g64, x64, gpart
+        (size_t)roff * 8,                              // r64
+        (size_t)count * 8, (size_t)count * 8, (size_t)count * 8, (size_t)count * 8,  // den bn2 rel obj
+        (size_t)foff * 8,                              // y (FP64)
+        (size_t)qoff * T,                              // Q
+        pack_elems * 2, pack_elems * 2,                // hi, lo
+    };
+    const int nsz = (int)(sizeof(sizes) / sizeof(sizes[0]));
+    size_t total = 0;
+    for (int i = 0; i < nsz; ++i) total += round_up(sizes[i], 256);
+    G_CHECK(grow(&g->pool, &g->pool_bytes, total));
+    {
+        uint8_t* p = (uint8_t*)g->pool;
+        int k = 0;
+        auto take = [&]() {
+            void* r = p;
+            p += round_up(sizes[k++], 256);
+            return r;
+        };
+        g->gp = (GProb*)take();
+        g->tiles = (GTile*)take();
+        g->order = (int*)take();
+        g->queue = (int*)take();
+        g->fin = (int*)take();
+        g->rounds = (int*)take();
+        g->again = (int*)take();
+        g->flags = (int*)take();
+        g->qexp_dev = (int64_t*)take();
+        g->stat = (GStat*)take();
+        g->s = (double*)take();
+        g->inv_s = (double*)take();
+        g->q64 = (double*)take();
+        g->g64 = (double*)take();
+        g->x64 = (double*)take();
+        g->gpart = (double*)take();
+        g->r64 = (double*)take();
+        g->den = (double*)take();
+        g->bn2 = (double*)take();
+        g->rel = (double*)take();
+        g->obj = (double*)take();
+        g->y = take();
+        g->Q = take();
+        g->hi = (__nv_bfloat16*)take();
+        g->lo = (__nv_bfloat16*)take();
+        if (k != nsz || (size_t)(p - (uint8_t*)g->pool) != total) return ALN_ERR_CUDA;
+    }
+    // pinned host mirror: again, fin, rounds (ints), rel, obj (doubles), stat
+    const size_t hb = round_up((size_t)count * 12, 64) + (size_t)count * 16 +
+                      (size_t)count * sizeof(GStat) + 64;
+    if (g->host_bytes < hb) {
+        if (g->host) cudaFreeHost(g->host);
+        g->host = nullptr;
+        g->host_bytes = 0;
+        if (cudaMallocHost(&g->host, hb) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        g->host_bytes = hb;
+    }
+
+    // solver geometry: one block per SM, shared memory as large as allowed
+    int optin = 0;
+    G_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    g->smem_bytes = optin - 1024;  // static shared memory of the kernel
+    const size_t need = f64 ? gsolve_static_bytes<double>(g->max_ldq)
+                            : gsolve_static_bytes<float>(g->max_ldq);
+    if ((size_t)g->smem_bytes < need) return ALN_ERR_UNSUPPORTED;
+    g->grid = c->num_sms;
+    g->slots = slot;
+
+    G_TRY(cudaMemcpyAsync(g->gp, g->hp.data(), (size_t)count * sizeof(GProb),
+                          cudaMemcpyHostToDevice, c->stream));
+    if (g->ntiles)
+        G_TRY(cudaMemcpyAsync(g->tiles, tiles.data(), (size_t)g->ntiles * sizeof(GTile),
+                              cudaMemcpyHostToDevice, c->stream));
+    G_TRY(cudaMemcpyAsync(g->qexp_dev, g->qexp.data(), (size_t)count * sizeof(int64_t),
+                          cudaMemcpyHostToDevice, c->stream));
+    G_TRY(cudaMemsetAsync(g->Q, 0, (size_t)qoff * T, c->stream));
+    // remember the records: a later prepare of the same device buffers (new
+    // contents, same shapes and addresses) reuses this layout as it is
+    bool all_dev = true;
+    for (int p = 0; p < count; ++p) all_dev = all_dev && a_dev[p] && b_dev[p];
+    g->reuse_ok = all_dev;
+    g->last.assign(probs, probs + count);
+    g->last_prec = c->opt.precision;
+    return ALN_OK;
+}
+
+aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, int32_t dtype) {
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
+    for (int p = 0; p < count; ++p)
+        if (probs[p].n > kGMaxN) return ALN_ERR_INVALID_ARG;
+    GroupWork* g = (GroupWork*)c->group;
+    if (!g) {
+        g = new (std::nothrow) GroupWork();
+        if (!g) return ALN_ERR_OUT_OF_MEMORY;
+        c->group = g;
+    }
+    const bool same = g->reuse_ok && g->pool && g->count == count && g->dtype == dtype &&
+                      g->last_prec == c->opt.precision && g->last.size() == (size_t)count &&
+                      std::memcmp(g->last.data(), probs, sizeof(aln_problem) * count) == 0;
+    G_TRY(cudaEventRecord(c->ev[0], c->stream));
+    if (!same) {
+        g->reuse_ok = false;
+        G_CHECK(group_layout(c, g, count, probs, dtype));
+    }
+    G_TRY(cudaMemsetAsync(g->flags, 0, 4 * sizeof(int), c->stream));
+    const unsigned slots = (unsigned)g->slots;
+    if (dtype == ALN_DTYPE_F32)
+        k_gcolstats<float><<<slots, 128, 0, c->stream>>>(g->gp, count, f64 ? 0 : 1, g->s,
+                                                         g->inv_s, g->q64, g->flags, g->hi, g->lo);
+    else
+        k_gcolstats<double><<<slots, 128, 0, c->stream>>>(g->gp, count, f64 ? 0 : 1, g->s,
+                                                          g->inv_s, g->q64, g->flags, g->hi,
+                                                          g->lo);
+    if (dtype == ALN_DTYPE_F32)
+        k_gden<float><<<count, 256, 0, c->stream>>>(g->gp, g->q64, g->den, g->bn2);
+    else
+        k_gden<double><<<count, 256, 0, c->stream>>>(g->gp, g->q64, g->den, g->bn2);
+    G_TRY(cudaGetLastError());
+    c->launches += 2;
+    G_TRY(cudaEventRecord(c->ev[1], c->stream));
+    if (f64) {
+        // the plain method: FP64 Gram per problem
+        for (int p = 0; p < count; ++p) {
+            const GProb& P = g->hp[p];
+            G_TRY(launch_gram64(P.A, dtype, P.d, P.n, P.lda, g->inv_s + P.voff,
+                                (double*)g->Q + P.qoff, P.ldq, c->stream));
+        }
+        c->launches += count;
+    } else {
+        G_TRY(launch_ggram_tc(g->gp, g->tiles, g->ntiles, g->hi, g->lo, g->inv_s, (float*)g->Q,
+                              g->flags + 1, c->stream));
+        c->launches += 1;
+    }
+    G_TRY(cudaEventRecord(c->ev[2], c->stream));
+    int* hflags = (int*)g->host;
+    G_TRY(cudaMemcpyAsync(hflags, g->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaEventRecord(c->ev[3], c->stream));
+    G_TRY(cudaStreamSynchronize(c->stream));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, c->ev[0], c->ev[3]);
+    cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+    c->stats.prepare_ms = a;
+    c->stats.gram_ms = b;
+    if (hflags[1]) return ALN_ERR_TIMEOUT;
+    if (hflags[0]) return ALN_ERR_NONFINITE;
+    c->grouped = 1;
+    return ALN_OK;
+}
+
+namespace {
+struct HostView {
+    int* again;
+    int* fin;
+    int* rounds;
+    double* rel;
+    double* obj;
+    GStat* stat;
+};
+HostView host_view(GroupWork* g) {
+    HostView h;
+    uint8_t* p = (uint8_t*)g->host;
+    h.again = (int*)p;
+    h.fin = h.again + g->count;
+    h.rounds = h.fin + g->count;
+    p += round_up((size_t)g->count * 12, 64);
+    h.rel = (double*)p;
+    h.obj = h.rel + g->count;
+    p += (size_t)g->count * 16;
+    h.stat = (GStat*)p;
+    return h;
+}
+}  // namespace
+
+aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const double* X0,
+                       aln_solve_info* info) {
+    GroupWork* g = (GroupWork*)c->group;
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
+    const int count = g->count;
+    const int64_t N = g->sum_n;
+    const bool x_dev = is_dev(X);
+    const double* x0 = nullptr;
+    if (X0) {
+        // stage x0 in x64, check it on the host side of the copy
+        G_TRY(cudaMemcpyAsync(g->x64, X0, (size_t)N * 8,
+                              is_dev(X0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+        G_TRY(cudaMemsetAsync(g->flags, 0, sizeof(int), c->stream));
+        G_TRY(launch_check_finite(g->x64, ALN_DTYPE_F64, N, 1, N, g->flags, c->stream));
+        int* hf = (int*)g->host;
+        G_TRY(cudaMemcpyAsync(hf, g->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        G_TRY(cudaStreamSynchronize(c->stream));
+        if (hf[0]) return ALN_ERR_NONFINITE;
+        x0 = g->x64;
+    }
+    const unsigned gv = grid_for(N, 256, 8 * c->num_sms);
+    k_ginit<<<gv, 256, 0, c->stream>>>(g->gp, count, N, x0, g->s, (double*)g->y, g->stat,
+                                       g->fin, g->rounds);
+    G_TRY(cudaGetLastError());
+    c->launches += 1;
+    G_TRY(cudaMemcpyAsync(g->order, g->order_all.data(), (size_t)count * sizeof(int),
+                          cudaMemcpyHostToDevice, c->stream));
+    HostView h = host_view(g);
+    std::vector<int> next;
+    next.reserve(count);
+    int nactive = count;
+    // Inner runs stop a little below tol so that the FP64 check usually passes
+    // at once; refinement rounds aim lower still, from the exact gradient.
+    double factor = 0.5;
+    int gmode = 0;
+    double iter_ms = 0.0, kkt_ms = 0.0;
+    for (int round = 0;; ++round) {
+        G_TRY(cudaEventRecord(c->ev[6], c->stream));
+        G_CHECK(f64 ? run_solver<double>(c, g, nactive, factor * tol, gmode, max_iter)
+                    : run_solver<float>(c, g, nactive, factor * tol, gmode, max_iter));
+        G_TRY(cudaEventRecord(c->ev[7], c->stream));
+        k_gunscale<<<gv, 256, 0, c->stream>>>(g->gp, count, N, (const double*)g->y, g->s,
+                                              g->x64);
+        G_TRY(cudaGetLastError());
+        c->launches += 1;
+        G_CHECK(kkt_pass(c, g, tol, max_iter, c->opt.max_refine, 1));
+        G_TRY(cudaEventRecord(c->ev[8], c->stream));
+        G_TRY(cudaMemcpyAsync(h.again, g->again, (size_t)count * sizeof(int),
+                              cudaMemcpyDeviceToHost, c->stream));
+        G_TRY(cudaStreamSynchronize(c->stream));
+        float a = 0.f, b = 0.f;
+        if (cudaEventElapsedTime(&a, c->ev[6], c->ev[7]) == cudaSuccess) iter_ms += a;
+        if (cudaEventElapsedTime(&b, c->ev[7], c->ev[8]) == cudaSuccess) kkt_ms += b;
+        next.clear();
+        for (int p : g->order_all)
+            if (h.again[p]) next.push_back(p);
+        if (next.empty()) break;
+        nactive = (int)next.size();
+        G_TRY(cudaMemcpyAsync(g->order, next.data(), (size_t)nactive * sizeof(int),
+                              cudaMemcpyHostToDevice, c->stream));
+        factor = 0.25;
+        gmode = 1;
+    }
+    // results
+    G_TRY(cudaMemcpyAsync(X, g->x64, (size_t)N * 8,
+                          x_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaMemcpyAsync(h.fin, g->fin, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream));
+    G_TRY(cudaMemcpyAsync(h.rounds, g->rounds, (size_t)count * sizeof(int),
+                          cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaMemcpyAsync(h.rel, g->rel, (size_t)count * 8, cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaMemcpyAsync(h.obj, g->obj, (size_t)count * 8, cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaMemcpyAsync(h.stat, g->stat, (size_t)count * sizeof(GStat),
+                          cudaMemcpyDeviceToHost, c->stream));
+    G_TRY(cudaStreamSynchronize(c->stream));
+    int64_t iters = 0, sp = 0, sc = 0;
+    int ci = 0;
+    double qbytes = 0.0;
+    const double tsz = f64 ? 8.0 : 4.0;
+    for (int p = 0; p < count; ++p) {
+        iters += h.stat[p].iters;
+        sp += h.stat[p].sum_passive;
+        sc += h.stat[p].sum_clip;
+        ci += h.stat[p].clip_iters;
+        qbytes += tsz * g->hp[p].n * (double)(h.stat[p].sum_passive + h.stat[p].sum_clip);
+        if (info) {
+            info[p].iters = h.stat[p].iters;
+            info[p].status = h.fin[p];
+            info[p].refine_rounds = h.rounds[p];
+            info[p].reserved = 0;
+            info[p].rel_kkt = h.rel[p];
+            info[p].objective = h.obj[p];
+        }
+    }
+    c->stats.iterations = iters;
+    c->stats.passive_rows = sp;
+    c->stats.clipped_rows = sc;
+    c->stats.clipped_iterations = ci;
+    c->stats.product_bytes = qbytes;
+    c->stats.iterate_ms = iter_ms;
+    c->stats.kkt_ms = kkt_ms;
+    c->p_G = std::min(count, g->grid);
+    return ALN_OK;
+}
+
+aln_status group_kkt(aln_ctx* c, const double* X, double* rel_kkt, double* objective) {
+    GroupWork* g = (GroupWork*)c->group;
+    const int count = g->count;
+    G_TRY(cudaMemcpyAsync(g->x64, X, (size_t)g->sum_n * 8,
+                          is_dev(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          c->stream));
+    G_TRY(cudaMemsetAsync(g->fin, 0xff, (size_t)count * sizeof(int), c->stream));  // all open
+    G_CHECK(kkt_pass(c, g, 0.0, 0, 0, 0));
+    G_TRY(cudaMemcpyAsync(rel_kkt, g->rel, (size_t)count * 8,
+                          is_dev(rel_kkt) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          c->stream));
+    if (objective)
+        G_TRY(cudaMemcpyAsync(objective, g->obj, (size_t)count * 8,
+                              is_dev(objective) ? cudaMemcpyDeviceToDevice
+                                                : cudaMemcpyDeviceToHost,
+                              c->stream));
+    G_TRY(cudaStreamSynchronize(c->stream));
+    return ALN_OK;
+}
+
+aln_status group_export(aln_ctx* c, double* Q, double* q, double* s) {
+    GroupWork* g = (GroupWork*)c->group;
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
+    if (Q) {
+        const bool dev = is_dev(Q);
+        double* dst = Q;
+        double* tmp = nullptr;
+        if (!dev) {
+            G_TRY(cudaMalloc(&tmp, (size_t)g->sum_nn * 8));
+            dst = tmp;
+        }
+        const unsigned grid = (unsigned)g->count;
+        if (f64)
+            k_gexport_q<double><<<grid, 256, 0, c->stream>>>(g->gp, (const double*)g->Q,
+                                                             g->qexp_dev, dst);
+        else
+            k_gexport_q<float><<<grid, 256, 0, c->stream>>>(g->gp, (const float*)g->Q,
+                                                            g->qexp_dev, dst);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && !dev)
+            e = cudaMemcpyAsync(Q, tmp, (size_t)g->sum_nn * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (tmp) cudaFree(tmp);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    if (q)
+        G_TRY(cudaMemcpyAsync(q, g->q64, (size_t)g->sum_n * 8,
+                              is_dev(q) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+    if (s)
+        G_TRY(cudaMemcpyAsync(s, g->s, (size_t)g->sum_n * 8,
+                              is_dev(s) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+    G_TRY(cudaStreamSynchronize(c->stream));
+    return ALN_OK;
+}
+
+}  // namespace aln

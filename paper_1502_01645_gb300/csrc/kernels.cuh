@@ -49,6 +49,48 @@ cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bflo
                             const int* map, int64_t ldq, float* W, const float* gb, double* kpart,
                             float* g, int* timeout_flag, cudaStream_t st);
 
+// grouped.cu — many independent problems of different sizes.
+// Per-problem record, built on the host and read by every grouped kernel.
+struct GProb {
+    const void* A;     // d×n column-major (device), dtype of the group
+    const void* b;     // d entries (device)
+    int64_t lda;
+    int32_t d, n;
+    int32_t T, KB;     // 128-row operand tiles (⌈n/128⌉), 64-wide K blocks (⌈d/64⌉)
+    int32_t ldq, pad;  // row length of Q_p and of the iteration vectors (n rounded up to 4)
+    int64_t pack;      // first 16 KiB tile of the problem in the hi / lo packs
+    int64_t qoff;      // first element of Q_p in the Q pool
+    int64_t voff;      // first entry in packed n-vectors (Σ_{q<p} n_q)
+    int64_t foff;      // first entry in packed iteration vectors (Σ_{q<p} ldq_q)
+    int64_t roff;      // first entry in packed d-vectors (Σ_{q<p} d_q)
+    int64_t slot;      // first column slot of the prepare grid (Σ_{q<p} 128·T_q)
+};
+// One lower-triangle output tile (tm ≥ tn) of one problem's Gram.
+struct GTile {
+    int32_t p, tm, tn, pad;
+};
+// Elements of one pre-swizzled operand tile: 128 rows × 64 BF16 (16 KiB).
+constexpr int kPackTile = 128 * 64;
+// Index of element (row j, K index t) of a problem's operand in the tiled
+// pack: tile (j/128, t/64), rows of 128 bytes, the 16-byte chunks of row r
+// permuted by chunk ^ (r mod 8) — the image of a 128-byte-swizzled TMA box, so
+// a tile copied verbatim into 1024-byte-aligned shared memory is a valid
+// tcgen05 K-major SWIZZLE_128B operand.
+__host__ __device__ __forceinline__ int64_t pack_index(int64_t tile0, int KB, int j, int t) {
+    const int r = j & 127, kk = t & 63;
+    const int64_t tile = tile0 + (int64_t)(j >> 7) * KB + (t >> 6);
+    return tile * kPackTile + r * 64 + ((((kk >> 3) ^ (r & 7)) << 3) | (kk & 7));
+}
+cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
+                            const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                            const double* inv_s, float* Q, int* timeout_flag, cudaStream_t st);
+aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, int32_t dtype);
+aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const double* X0,
+                       aln_solve_info* info);
+aln_status group_kkt(aln_ctx* c, const double* X, double* rel_kkt, double* objective);
+aln_status group_export(aln_ctx* c, double* Q, double* q, double* s);
+void group_free(aln_ctx* c);
+
 // batch.cu — Alg. 2 on many right-hand sides sharing A
 aln_status batch_prepare(aln_ctx* c);
 aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t ldx,

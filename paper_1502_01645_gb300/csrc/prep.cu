@@ -5,32 +5,6 @@
 
 namespace aln {
 
-// Per-thread accumulator of a dot product.  FP32 inputs use Dot2 (Ogita,
-// Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005):
-// the exact product error from an FMA (TwoProduct) and the exact addition
-// error (TwoSum) are carried in a second float, so the result is as accurate
-// as if accumulated in twice the working precision — without the FP64 pipe,
-// which is narrow on this GPU.  FP64 inputs accumulate in FP64.
-template <typename TA> struct DotAcc;
-template <> struct DotAcc<float> {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float a, float b) {
-        const float p = a * b;
-        const float ep = fmaf(a, b, -p);   // a·b = p + ep exactly
-        const float t = s + p;
-        const float z = t - s;
-        const float es = (s - (t - z)) + (p - z);  // s + p = t + es exactly
-        s = t;
-        c += es + ep;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-template <> struct DotAcc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
-};
-
 __device__ __forceinline__ void load4t(const float* p, float* o) {
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     o[0] = v.x;
@@ -313,7 +287,7 @@ __global__ void __launch_bounds__(256) k_atb32_dot2(const float* __restrict__ X,
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const float p = xa[a] * yb[b];
+                    const float p = mul_rn(xa[a], yb[b]);
                     const float ep = fmaf(xa[a], yb[b], -p);
                     const float t = s[a][b] + p;
                     const float z = t - s[a][b];

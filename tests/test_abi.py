@@ -58,6 +58,7 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.aln_kkt_residual(None, None, 1, None, None) == aln.ERR_INVALID_ARG
     assert lib.aln_export_scaled(None, None, 1, None, 1, None) == aln.ERR_INVALID_ARG
     assert lib.aln_get_stats(None, None) == aln.ERR_INVALID_ARG
+    assert lib.aln_prepare_grouped(None, 1, None, 0) == aln.ERR_INVALID_ARG
     o = aln.aln_default_options()
     o.precision = 7
     ctx = ctypes.c_void_p()

@@ -1,0 +1,211 @@
+"""Grouped path (many independent problems of uneven size, one prepare and one
+persistent solve for all of them) against the FP64 CPU oracle, through the C
+ABI.  Tolerances as in the single-problem parity tests:
+  * split-BF16 Gram |ΔQ_ij| ≤ 3·2⁻¹⁸ + 3·d·2⁻²⁴ + 2⁻²³; s to 1e-13, q to
+    2e-12·max|q| (Dot2 column sums, FP64-level);
+  * mixed-precision solutions: FP64 relative KKT ≤ tol and
+    ‖Δx‖₂/‖x*‖₂ ≤ 1e-5 against the polished optimum;
+  * FP64 path: ‖Δx‖∞/‖x*‖∞ ≤ 1e-8 and |ΔF|/F* ≤ 1e-10.
+"""
+import numpy as np
+import pytest
+
+from oracle import nnls as O
+from paper_1502_01645_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def aln():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_01645_gb300 import build_lib, aln as binding
+    build_lib.build()
+    binding.load()
+    return binding
+
+
+def _split_bound(d):
+    return 3 * 2.0 ** -18 + 3 * d * 2.0 ** -24 + 2.0 ** -23
+
+
+def _problems(sizes, seed, dtype=np.float32, zero_frac=0.6):
+    """(A, b) pairs of the uneven-batch kind with the given (d, n)."""
+    r = np.random.default_rng(seed)
+    out = []
+    for d, n in sizes:
+        A = np.asfortranarray(np.abs(r.standard_normal((d, n))).astype(dtype))
+        x = np.where(r.random(n) < zero_frac, 0.0, r.random(n))
+        b0 = A.astype(np.float64) @ x
+        b = (b0 + 0.01 * np.linalg.norm(b0) / np.sqrt(d) * r.standard_normal(d)).astype(dtype)
+        out.append((A, b))
+    return out
+
+
+# Ragged in n (1, inside a tile, tile edges 128/129, several tiles, past the
+# shared-memory staging size) and in d (not multiples of 64, d < 64).
+SIZES = [(3, 1), (70, 5), (62, 31), (100, 32), (300, 127), (256, 128), (400, 129),
+         (500, 200), (777, 257), (900, 300), (2100, 700), (1100, 1030)]
+
+
+def test_grouped_prepare_matches_oracle(aln):
+    probs = _problems(SIZES, 41)
+    A0 = probs[3][0]
+    A0[:, 7] = 0.0  # a zero column (Eq. Rescaling's special case)
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(probs)
+        Qs, qs, ss = s.export()
+    for (A, b), Q, q, sc in zip(probs, Qs, qs, ss):
+        H, h = O.nqp_from_nnls(A.astype(np.float64), b.astype(np.float64))
+        Qo, qo, so = O.antilopsided_scaling(H, h)
+        d = A.shape[0]
+        np.testing.assert_allclose(sc, so, rtol=1e-13)
+        np.testing.assert_allclose(q, qo, rtol=0, atol=2e-12 * max(np.abs(qo).max(), 1e-300))
+        err = np.abs(Q - Qo)
+        assert err.max() <= _split_bound(d), (A.shape, err.max())
+        np.testing.assert_array_equal(Q, Q.T)
+    # the zero column: row/column of Q zero, Q_ii = 0, s = 1, q = 0
+    Q3 = Qs[3]
+    assert np.all(Q3[7] == 0.0) and ss[3][7] == 1.0 and qs[3][7] == 0.0
+    for k, Q in enumerate(Qs):
+        dq = np.diag(Q).copy()
+        if k == 3:
+            dq = np.delete(dq, 7)
+        np.testing.assert_array_equal(dq, 1.0)
+
+
+def test_grouped_solve_matches_oracle(aln):
+    probs = _problems(SIZES, 42)
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(probs)
+        X, info = s.solve(tol=1e-9)
+        Xb, infob = s.solve(tol=1e-6)
+    for p, ((A, b), x, xb) in enumerate(zip(probs, X, Xb)):
+        A64, b64 = A.astype(np.float64), b.astype(np.float64)
+        x_star, _, _, _ = O.reference_solution(A64, b64)
+        rel, _ = O.kkt_residual(A64, b64, x)
+        assert rel <= 1e-9, (p, A.shape, rel, info[p])
+        assert np.linalg.norm(x - x_star) <= 1e-5 * max(np.linalg.norm(x_star), 1e-300), p
+        assert info[p].status in (aln.RHS_CONVERGED, aln.RHS_EMPTY_PASSIVE)
+        np.testing.assert_allclose(info[p].rel_kkt, rel, rtol=1e-6, atol=1e-15)
+        relb, Fb = O.kkt_residual(A64, b64, xb)
+        assert relb <= 1e-6, (p, relb)
+        np.testing.assert_allclose(infob[p].rel_kkt, relb, rtol=1e-6, atol=1e-15)
+        np.testing.assert_allclose(infob[p].objective, Fb, rtol=1e-10)
+        assert np.all(xb >= 0.0)
+
+
+def test_grouped_fp64_matches_oracle(aln):
+    sizes = [(40, 1), (90, 31), (300, 129), (600, 257), (500, 200)]
+    probs = _problems(sizes, 43, dtype=np.float64, zero_frac=0.5)
+    with aln.Solver("fp64") as s:
+        s.prepare_grouped(probs)
+        X, info = s.solve(tol=1e-12)
+    for p, ((A, b), x) in enumerate(zip(probs, X)):
+        x_star, _, _, _ = O.reference_solution(A, b)
+        assert info[p].rel_kkt <= 1e-12, (p, info[p])
+        F = O.nnls_objective(A, b, x)
+        Fs = O.nnls_objective(A, b, x_star)
+        assert abs(F - Fs) <= 1e-10 * Fs + 1e-30  # F* = 0 when b = 0
+        if np.abs(x_star).max() > 0:
+            assert np.abs(x - x_star).max() / np.abs(x_star).max() <= 1e-8
+
+
+def test_grouped_agrees_with_single_problem_path(aln):
+    probs = _problems([(300, 100), (500, 200), (129, 64)], 44)
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(probs)
+        X, _ = s.solve(tol=1e-9)
+    for (A, b), x in zip(probs, X):
+        with aln.Solver("split_bf16") as s1:
+            s1.prepare(A, b)
+            X1, _ = s1.solve(tol=1e-9)
+        assert np.linalg.norm(x - X1[0]) <= 2e-5 * np.linalg.norm(X1[0])
+
+
+def test_grouped_edge_cases(aln):
+    r = np.random.default_rng(45)
+    probs = _problems([(50, 20), (64, 64), (1, 1), (33, 40)], 46)
+    probs[0] = (probs[0][0], np.zeros(50, np.float32))           # b = 0 → x = 0
+    probs[1] = (probs[1][0], -np.abs(probs[1][1]))              # Aᵀb ≤ 0 → x = 0
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(probs)
+        X, info = s.solve(tol=1e-8)
+        assert np.all(X[0] == 0.0) and info[0].status == aln.RHS_EMPTY_PASSIVE
+        assert np.all(X[1] == 0.0) and info[1].status == aln.RHS_EMPTY_PASSIVE
+        A2, b2 = probs[2]
+        np.testing.assert_allclose(X[2][0], max(float(b2[0]) / float(A2[0, 0]), 0.0), rtol=1e-7)
+        # d < n: rank deficient; only the objective is unique
+        A3, b3 = probs[3]
+        rel, F = O.kkt_residual(A3.astype(np.float64), b3.astype(np.float64), X[3])
+        assert rel <= 1e-8
+        # a start point at the solution: far fewer iterations than from 0
+        X2, info2 = s.solve(tol=1e-6, X0=X)
+        assert sum(i.iters for i in info2) <= 0.2 * sum(i.iters for i in info) + 8
+        assert all(i.rel_kkt <= 1e-6 for i in info2)
+        # an iteration cap is a per-problem status, not an error
+        X3, info3 = s.solve(tol=1e-12, max_iter=1)
+        assert any(i.status == aln.RHS_MAXITER for i in info3)
+        assert all(np.all(x >= 0) for x in X3)
+        # the KKT entry point on packed solutions
+        rel_k, obj_k = s.kkt(X)
+        for p, ((A, b), x) in enumerate(zip(probs, X)):
+            relo, Fo = O.kkt_residual(A.astype(np.float64), b.astype(np.float64), x)
+            np.testing.assert_allclose(rel_k[p], relo, rtol=1e-6, atol=1e-15)
+            np.testing.assert_allclose(obj_k[p], Fo, rtol=1e-10, atol=1e-30)
+    # invalid inputs
+    bad = [(np.asfortranarray(np.ones((10, 5000), np.float32)), np.ones(10, np.float32))]
+    with aln.Solver("split_bf16") as s:
+        with pytest.raises(aln.AlnError) as e:
+            s.prepare_grouped(bad)
+        assert e.value.code == aln.ERR_INVALID_ARG
+    nan = _problems([(30, 10)], 47)
+    nan[0][0][3, 4] = np.nan
+    with aln.Solver("split_bf16") as s:
+        with pytest.raises(aln.AlnError) as e:
+            s.prepare_grouped(nan)
+        assert e.value.code == aln.ERR_NONFINITE
+
+
+def test_grouped_device_inputs(aln):
+    torch = pytest.importorskip("torch")
+    probs = _problems([(200, 80), (333, 150)], 48)
+    dev = [(torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t(), torch.from_numpy(b).cuda())
+           for A, b in probs]
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(probs)
+        Xh, _ = s.solve(tol=1e-8)
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(dev)
+        Xd, _ = s.solve(tol=1e-8)
+    for a, b in zip(Xh, Xd):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_uneven_batch_full_size(aln):
+    """The 512-problem uneven batch at full size, in the launch configuration
+    bench.py times: every problem meets rel KKT ≤ 1e-6 by an independent FP64
+    check from A.  At tol 1e-9 a sample of problems (the largest, the smallest
+    and two in between) matches the oracle's polished optimum to 1e-5 (the
+    x-gate needs the tighter tolerance: cond(Q) of these |N(0,1)| matrices
+    reaches the hundreds, so rel KKT 1e-6 alone bounds ‖Δx‖/‖x*‖ only to
+    about 1e-4)."""
+    probs = W.uneven_batch()
+    pairs = [(p.A, p.B[0]) for p in probs]
+    with aln.Solver("split_bf16") as s:
+        s.prepare_grouped(pairs)
+        X, info = s.solve(tol=1e-6)
+        X9, info9 = s.solve(tol=1e-9)
+    ns = np.array([p.A.shape[1] for p in probs])
+    for p, (A, b) in enumerate(pairs):
+        rel, F = O.kkt_residual(A.astype(np.float64), b.astype(np.float64), X[p])
+        assert rel <= 1e-6, (p, A.shape, rel)
+        np.testing.assert_allclose(info[p].rel_kkt, rel, rtol=1e-5, atol=1e-15)
+    order = np.argsort(ns)
+    for p in [order[-1], order[0], order[len(order) // 2], order[3 * len(order) // 4]]:
+        A, b = pairs[p]
+        x_star, _, _, _ = O.reference_solution(A.astype(np.float64), b.astype(np.float64))
+        assert info9[p].rel_kkt <= 1e-9, (p, info9[p])
+        assert np.linalg.norm(X9[p] - x_star) <= 1e-5 * np.linalg.norm(x_star), p
