@@ -9,19 +9,26 @@ The paper starts Alg. 2 at x⁰ = 0 and maps a start point with y⁰ = x⁰·√
 (Eq. Rescaling, Fig. 2).  A learned start point is not in the paper; this
 module defines the one the library implements, in plain numpy float64:
 
-  features   u = [ q/‖q‖ ; z ],  z_j = (log s_j − mean log s)/std log s
+  features   u = [ (q/‖q‖ − μ)/σ ; z ],  z_j = (log s_j − mean log s)/std log s
              (q is the scaled linear term of Eq. NQPQ for one right-hand side,
-             s_j = √H_jj; z depends on A only; std := 1 if it is 0, and the
-             q-part is 0 when q = 0)
+             s_j = √H_jj; μ_j, σ_j are the mean and standard deviation of
+             q_j/‖q‖ over the training set (σ_j := 1 if 0); z depends on A
+             only, std := 1 if it is 0; the q-part is q/‖q‖ = 0 when q = 0)
   network    h1 = relu(W1 u + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3,
              o = [ ŷ ; ℓ ]  (ŷ and the logits ℓ have n entries each)
-  start      y⁰ = ‖q‖ · relu(ŷ) · [ℓ > 0], replaced by 0 when
-             f(y⁰) = ½y⁰ᵀQy⁰ + qᵀy⁰ ≥ 0 = f(0)  (never start worse than x⁰ = 0)
-  loss       L = mean (ŷ − y*/‖q‖)² + mean BCE(ℓ, [y* > 0]),  both means over
-             the batch and the n outputs; BCE(ℓ, c) = log(1 + e^ℓ) − c·ℓ
+  start      direction d = relu(ŷ)·[ℓ > 0], then the exact line search of
+             Alg. 2 along it from 0: y⁰ = α*·d, α* = max(0, −qᵀd / dᵀQd)
+             (0 when dᵀQd = 0).  So f(y⁰) = ½y⁰ᵀQy⁰ + qᵀy⁰ ≤ f(0): the start is
+             never worse than x⁰ = 0, and y⁰ = 0 when the direction does not
+             descend.
+  loss       L = mean (ŷ − y*/(τ‖q‖))² + mean BCE(ℓ, [y* > 0]), both means over
+             the batch and the n outputs; BCE(ℓ, c) = log(1 + e^ℓ) − c·ℓ;
+             τ = RMS of y*/‖q‖ over the training set (1 if 0)
   training   Adam (Kingma & Ba 2015) with bias correction.
 
-Parameters are a dict {W1, b1, W2, b2, W3, b3}; W_l has shape (out, in).
+Parameters are a dict {W1, b1, W2, b2, W3, b3}; W_l has shape (out, in).  The
+normalisation statistics (μ, σ, τ) are a dict {mu, sd, tau}; None means
+μ = 0, σ = 1, τ = 1.
 """
 from __future__ import annotations
 
@@ -30,14 +37,32 @@ import numpy as np
 PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
 
 
-def features(q, s):
-    """u = [q/‖q‖ ; z] for a batch of q (B, n) and the scale factors s (n,)."""
-    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    s = np.asarray(s, dtype=np.float64)
+def _unit(q):
     qn = np.linalg.norm(q, axis=1)
     qpart = np.zeros_like(q)
     nz = qn > 0
     qpart[nz] = q[nz] / qn[nz, None]
+    return qpart, qn
+
+
+def stats(q, Y):
+    """μ, σ of q/‖q‖ per entry and τ = RMS of y*/‖q‖, over a training set."""
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    qpart, qn = _unit(q)
+    sd = qpart.std(axis=0)
+    sd[sd == 0] = 1.0
+    T, _ = targets(Y, qn)
+    tau = float(np.sqrt(np.mean(T ** 2)))
+    return {"mu": qpart.mean(axis=0), "sd": sd, "tau": tau if tau > 0 else 1.0}
+
+
+def features(q, s, st=None):
+    """u = [(q/‖q‖ − μ)/σ ; z] for a batch of q (B, n) and scale factors s (n,)."""
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    s = np.asarray(s, dtype=np.float64)
+    qpart, qn = _unit(q)
+    if st is not None:
+        qpart = (qpart - st["mu"]) / st["sd"]
     ls = np.log(s)
     sd = ls.std()
     z = (ls - ls.mean()) / (sd if sd > 0 else 1.0)
@@ -117,32 +142,39 @@ def adam_step(p, g, st, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     return p
 
 
-def targets(Y, qn):
-    """T = y*/‖q‖ (0 where q = 0) and C = [y* > 0]."""
+def targets(Y, qn, tau=1.0):
+    """T = y*/(τ‖q‖) (0 where q = 0) and C = [y* > 0]."""
     Y = np.atleast_2d(np.asarray(Y, dtype=np.float64))
     T = np.zeros_like(Y)
     nz = qn > 0
-    T[nz] = Y[nz] / qn[nz, None]
+    T[nz] = Y[nz] / (tau * qn[nz, None])
     return T, (Y > 0).astype(np.float64)
 
 
-def predict(p, q, s, Q):
-    """Start points y⁰ (B, n) in the scaled space, with the f(y⁰) ≥ 0 fallback."""
+def predict(p, q, s, Q, st=None):
+    """Start points y⁰ (B, n) in the scaled space: the predicted direction
+    scaled by the exact line search from 0 (α* ≥ 0)."""
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    U, qn = features(q, s)
+    U, _ = features(q, s, st)
     O, _ = forward(p, U)
     n = q.shape[1]
-    y0 = qn[:, None] * np.maximum(O[:, :n], 0.0) * (O[:, n:] > 0)
-    f = 0.5 * np.einsum("bi,ij,bj->b", y0, Q, y0) + np.einsum("bi,bi->b", q, y0)
-    y0[f >= 0] = 0.0
-    return y0
+    d = np.maximum(O[:, :n], 0.0) * (O[:, n:] > 0)
+    num = -np.einsum("bi,bi->b", q, d)
+    den = np.einsum("bi,ij,bj->b", d, Q, d)
+    alpha = np.zeros(len(q))
+    ok = (num > 0) & (den > 0)
+    alpha[ok] = num[ok] / den[ok]
+    return alpha[:, None] * d
 
 
-def train(p, Qs, Ys, s, epochs=1, batch=256, lr=1e-3, seed=0):
-    """Minibatch Adam over (q, y*) pairs; returns the mean loss of each epoch."""
-    U, qn = features(Qs, s)
-    T, C = targets(Ys, qn)
-    st = adam_init(p)
+def train(p, Qs, Ys, s, epochs=1, batch=256, lr=1e-3, seed=0, st=None):
+    """Minibatch Adam over (q, y*) pairs; returns the mean loss of each epoch.
+    ``st`` (normalisation statistics) defaults to stats(Qs, Ys)."""
+    if st is None:
+        st = stats(Qs, Ys)
+    U, qn = features(Qs, s, st)
+    T, C = targets(Ys, qn, st["tau"])
+    ad = adam_init(p)
     r = np.random.default_rng(seed)
     hist = []
     for _ in range(epochs):
@@ -151,7 +183,7 @@ def train(p, Qs, Ys, s, epochs=1, batch=256, lr=1e-3, seed=0):
         for i in range(0, len(U), batch):
             idx = perm[i:i + batch]
             L, g = loss_and_grad(p, U[idx], T[idx], C[idx])
-            adam_step(p, g, st, lr=lr)
+            adam_step(p, g, ad, lr=lr)
             tot += L * len(idx)
             cnt += len(idx)
         hist.append(tot / cnt)

@@ -129,31 +129,74 @@ def test_features_normalisation():
     assert qn4[0] == 0.0 and np.all(U4[0, :n] == 0.0)
 
 
-def test_predict_fallback_rule():
-    n = 4
-    Q = np.eye(n)
-    q = -np.array([[1.0, 2.0, 0.5, 3.0]])
-    s = np.ones(n)
-    U, qn = M.features(q, s)
+def _identity_net(n, sign):
+    """h1 = relu(sign·q/‖q‖) on the first n units, ŷ = h1[:n], logits 5."""
     hidden = 2 * n
-    # a network that reproduces y* = −q exactly (Q = I): keep it
-    # h1 = relu(−q/‖q‖) (q < 0 here), h2 = h1, ŷ = h2[:n] = −q/‖q‖, logits 5
     p = {"W1": np.zeros((2 * n, 2 * n)), "b1": np.zeros(2 * n),
          "W2": np.eye(2 * n), "b2": np.zeros(2 * n),
          "W3": np.zeros((2 * n, hidden)), "b3": np.zeros(2 * n)}
-    p["W1"][:n, :n] = -np.eye(n)
+    p["W1"][:n, :n] = sign * np.eye(n)
     p["W3"][:n, :n] = np.eye(n)
     p["b3"][n:] = 5.0
-    y0 = M.predict(p, q, s, Q)
-    np.testing.assert_allclose(y0[0], -q[0])  # f(y0) = −½‖q‖² < 0 → kept
-    # a start with f(y0) ≥ 0 (far too large) falls back to 0
-    p["W3"] = 10.0 * p["W3"]
-    y0 = M.predict(p, q, s, Q)
-    assert np.all(y0 == 0.0)
-    # logits ≤ 0 switch entries off
-    p["W3"] = p["W3"] / 10.0
+    return p
+
+
+def test_predict_line_search_rule():
+    n = 4
+    Q = np.eye(n)
+    s = np.ones(n)
+    q = -np.array([[1.0, 2.0, 0.5, 3.0]])
+    # direction −q/‖q‖ with Q = I: the exact line search lands on y* = −q
+    p = _identity_net(n, -1.0)
+    np.testing.assert_allclose(M.predict(p, q, s, Q)[0], -q[0])
+    # the start does not depend on the predicted magnitude
+    p10 = dict(p, W3=10.0 * p["W3"])
+    np.testing.assert_allclose(M.predict(p10, q, s, Q), M.predict(p, q, s, Q))
+    # a direction that does not descend (qᵀd ≥ 0) gives y⁰ = 0
+    assert np.all(M.predict(_identity_net(n, 1.0), -q, s, Q) == 0.0)
+    # logits ≤ 0 switch every entry off
     p["b3"][n:] = -5.0
     assert np.all(M.predict(p, q, s, Q) == 0.0)
+
+
+def test_predict_is_the_best_point_on_its_ray():
+    """f(y⁰) ≤ f(α·d) for every α ≥ 0 on a grid, and f(y⁰) ≤ 0 = f(0)."""
+    r = np.random.default_rng(8)
+    n = 12
+    A = np.abs(r.normal(size=(40, n)))
+    H = A.T @ A
+    sc = np.sqrt(np.diag(H))
+    Q = H / np.outer(sc, sc)
+    q = -(r.random((16, n)) @ A.T @ A) / sc + 0.3 * r.normal(size=(16, n))
+    p = M.init_params(2 * n, 32, 2 * n, seed=9)
+    p["b3"][n:] = 2.0
+    y0 = M.predict(p, q, sc, Q)
+    U, _ = M.features(q, sc)
+    O, _ = M.forward(p, U)
+    d = np.maximum(O[:, :n], 0.0) * (O[:, n:] > 0)
+
+    def f(y, qq):
+        return 0.5 * y @ Q @ y + qq @ y
+
+    for b in range(len(q)):
+        fy = f(y0[b], q[b])
+        assert fy <= 1e-14
+        for a in np.linspace(0.0, 3.0, 61) * max(np.abs(y0[b]).max(), 1e-3) / max(
+                np.abs(d[b]).max(), 1e-12):
+            assert fy <= f(a * d[b], q[b]) + 1e-12
+
+
+def test_normalisation_statistics():
+    r = np.random.default_rng(10)
+    n, m = 5, 300
+    q = r.normal(size=(m, n)) + np.array([3.0, 0, 0, 0, -1.0])
+    Y = np.maximum(r.normal(size=(m, n)), 0.0) * 7.0
+    st = M.stats(q, Y)
+    U, qn = M.features(q, np.ones(n), st)
+    np.testing.assert_allclose(U[:, :n].mean(axis=0), 0.0, atol=1e-12)
+    np.testing.assert_allclose(U[:, :n].std(axis=0), 1.0, rtol=1e-12)
+    T, _ = M.targets(Y, qn, st["tau"])
+    assert abs(np.sqrt(np.mean(T ** 2)) - 1.0) < 1e-12
 
 
 def test_training_lowers_the_loss():
