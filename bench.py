@@ -52,6 +52,11 @@ WORKLOADS = {
         desc="uneven_batch_{k}: {k} independent problems, n log-uniform in [32,1024], "
              "d = n*U{{2,3,4}}, A |N(0,1)| FP32, x_true 60% zeros U[0,1], 1% noise; "
              "all problems prepared and solved together (grouped)"),
+    "warmstart": dict(
+        d=8000, n=2000, k=4096, tol=1e-6, seed=1005, prec="split_bf16", train=16384,
+        desc="warmstart_{d}x{n}: A U[0,1] x log-uniform column scales FP32; x_true support "
+             "U{{50..400}}, Exp(1) values, 1% noise; network trained on {train} solved "
+             "right-hand sides, {k} held-out right-hand sides started from its prediction"),
     "uniform_small": dict(
         d=1000, n=200, k=1, tol=1e-10, seed=1001, prec="fp64",
         desc="uniform_small_{d}x{n}_f64: A U[0,1], x_true half zeros U[0,1], "
@@ -72,13 +77,16 @@ def parse():
     ap.add_argument("--d", type=int, default=None, help="rows of A (profiling cases)")
     ap.add_argument("--n", type=int, default=None, help="columns of A")
     ap.add_argument("--k", type=int, default=None, help="right-hand sides")
+    ap.add_argument("--train", type=int, default=None,
+                    help="training right-hand sides of the warm-start workload")
+    ap.add_argument("--epochs", type=int, default=20, help="warm-start training epochs")
     return ap.parse_args()
 
 
 def workload(args):
     w = dict(WORKLOADS[args.workload])
-    for key in ("d", "n", "k"):
-        v = getattr(args, key)
+    for key in ("d", "n", "k", "train"):
+        v = getattr(args, key, None)
         if v is not None:
             w[key] = v
     w["name"] = args.workload
@@ -90,6 +98,11 @@ def generate(w, rank=0):
     from paper_1502_01645_gb300 import workloads as W
     if w["name"] == "uneven_batch":
         return W.uneven_batch(count=w["k"], seed=w["seed"] + rank)
+    if w["name"] == "warmstart":
+        train = W.warmstart_family(d=w["d"], n=w["n"], k=w["train"], seed=w["seed"])
+        held = W.warmstart_family(d=w["d"], n=w["n"], k=w["k"], seed=w["seed"],
+                                  rhs_seed=w["seed"] + 7919 + rank)
+        return train, held
     if w["name"] == "lopsided_single":
         return W.lopsided_single(d=w["d"], n=w["n"], seed=w["seed"] + rank)
     if w["name"] == "shared_multi_rhs":
@@ -222,7 +235,12 @@ def run_reference(args):
     p = generate(w)
     times, desc = [], ""
     for i in range(args.warmup + args.steps):
-        t, desc = cpu_sample_grouped(w, p) if w["name"] == "uneven_batch" else cpu_sample(w, p)
+        if w["name"] == "uneven_batch":
+            t, desc = cpu_sample_grouped(w, p)
+        elif w["name"] == "warmstart":
+            t, desc = cpu_sample(w, p[1])
+        else:
+            t, desc = cpu_sample(w, p)
         if i >= args.warmup:
             times.append(t)
     per = sum(times) / len(times)
@@ -262,6 +280,8 @@ def run_ours(args):
     w = workload(args)
     if w["name"] == "uneven_batch":
         return run_grouped(args, w, world, rank, local)
+    if w["name"] == "warmstart":
+        return run_warmstart(args, w, world, rank, local)
     d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
     p = generate(w, rank)
     A_np, B_np = p.A, p.B
@@ -629,6 +649,200 @@ def run_grouped(args, w, world, rank, local):
                    "rel_kkt_max": worst},
         "roofline": rooflines[0],
         "roofline_secondary": rooflines[1],
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "plain_fp64": plain,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_warmstart(args, w, world, rank, local):
+    """Held-out right-hand sides of a fixed A started from the learned
+    prediction.  Outside the timed region: solve the training right-hand
+    sides, train the network.  One step = prepare (Gram, q) + predict +
+    batched solve of all held-out right-hand sides; the same step without
+    the prediction (cold) is timed beside it."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1502_01645_gb300 import aln
+
+    d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
+    train, held = generate(w, rank)
+    At = torch.from_numpy(np.ascontiguousarray(held.A.T)).cuda().t()
+    Btr = torch.from_numpy(np.ascontiguousarray(train.B)).cuda()
+    Bt = torch.from_numpy(np.ascontiguousarray(held.B)).cuda()
+    stream = torch.cuda.Stream()
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+
+    # ---- training set and training (not timed) ----
+    t0 = time.perf_counter()
+    solver.prepare(At, Btr)
+    Xtr = torch.zeros((w["train"], n), dtype=torch.float64, device="cuda")
+    solver.solve(tol=tol, X=Xtr)
+    Qtr = torch.zeros((w["train"], n), dtype=torch.float64, device="cuda")
+    s_dev = torch.zeros(n, dtype=torch.float64, device="cuda")
+    aln.aln_export_scaled(solver.ctx, None, n, Qtr, n, s_dev)
+    Ytr = Xtr * s_dev[None, :]
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = solver.warmstart_train(Qtr, Ytr, epochs=args.epochs, batch=1024, hidden=1024,
+                                  lr=1e-3, seed=5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del Qtr, Ytr, Xtr
+
+    X0 = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+    Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+
+    def step(warm):
+        solver.prepare(At, Bt)
+        if warm:
+            solver.warmstart_predict(X0)
+        _, info = solver.solve(tol=tol, X=Xt, X0=X0 if warm else None)
+        return info, solver.stats()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(warm, steps):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos, sts = [], []
+        for _ in range(steps):
+            info, st = step(warm)
+            infos.append(info)
+            sts.append(st)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / 1e3, infos, sts
+
+    for _ in range(args.warmup):
+        step(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = solver.stats().kernel_launches
+    elapsed, infos, stats = timed(True, args.steps)
+    launches = solver.stats().kernel_launches - launches0
+    clocks = sampler.stop()
+    worst = max(max(i.rel_kkt for i in info) for info in infos)
+    if worst > tol:
+        raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    value = world * args.steps * k / tmax
+    warm_iters = float(np.mean([i.iters for i in infos[-1]]))
+    X0_host = X0.cpu().numpy()
+    kept_frac = float(np.mean(np.abs(X0_host).sum(axis=1) > 0))
+
+    # ---- the same step from x0 = 0 (cold) ----
+    step(False)
+    tc_, cinfos, _ = timed(False, max(1, min(args.steps, 2)))
+    cold = {"value": world * max(1, min(args.steps, 2)) * k / tc_, "unit": UNIT,
+            "mean_iters": float(np.mean([i.iters for i in cinfos[-1]])),
+            "rel_kkt_max": max(i.rel_kkt for i in cinfos[-1])}
+
+    def avg(f):
+        return sum(f(s) for s in stats) / len(stats)
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.from_numpy(np.ascontiguousarray(held.A.T)).pin_memory().t()
+        B_h = torch.from_numpy(np.ascontiguousarray(held.B)).pin_memory()
+        X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
+        X0_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
+        k_e2e = 3
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            solver.prepare(A_h, B_h)
+            solver.warmstart_predict(X0_h)
+            _, hinfo = solver.solve(tol=tol, X=X_h, X0=X0_h)
+        barrier()
+        te = time.perf_counter() - t0
+        e2e = {"value": world * k_e2e * k / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(held.A.nbytes + held.B.nbytes),
+               "d2h_bytes_per_step": int(2 * k * n * 8), "steps": k_e2e,
+               "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
+
+    # ---- plain FP64 method on a sample of right-hand sides ----
+    plain = None
+    if not args.no_plain:
+        kp = 16
+        psolver = aln.Solver("fp64", stream=stream.cuda_stream)
+        Bp = Bt[:kp].contiguous()
+        Xp = torch.zeros((kp, n), dtype=torch.float64, device="cuda")
+        psolver.prepare(At, Bp)
+        psolver.solve(tol=tol, X=Xp)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        psolver.prepare(At, Bp)
+        _, pinfo = psolver.solve(tol=tol, X=Xp)
+        e1.record(stream)
+        barrier()
+        tp = e0.elapsed_time(e1) / 1e3
+        pst = psolver.stats()
+        psolver.close()
+        full = pst.prepare_ms / 1e3 + (tp - pst.prepare_ms / 1e3) / kp * k
+        plain = {"value": k / full, "unit": UNIT, "ms_per_step": full * 1e3, "rhs_timed": kp,
+                 "iters_max": max(i.iters for i in pinfo),
+                 "note": f"FP64 Gram + FP64 Alg. 2 from x0 = 0, one right-hand side at a time; "
+                         f"{kp} timed, scaled to {k}"}
+    solver.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    pk, pk_kind = peaks()
+    peak_tc = float(pk["bf16_tflops_sustained"])
+    it_ms = avg(lambda s: s.iterate_ms)
+    colit = avg(lambda s: s.iterations + s.clipped_iterations)
+    flops = 3.0 * 2.0 * n * n * colit
+    ach = flops / (it_ms / 1e3) / 1e12 if it_ms > 0 else 0.0
+    roof = {"bound": "tensor", "kernel": "batched Alg. 2 phase (k_bgemm_tc W and U + mask/update)",
+            "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s", "frac": ach / peak_tc,
+            "traffic": None, "peak_kind": f"{pk_kind} bf16 sustained",
+            "algorithmic_per_launch": flops, "avg_launch_ms": it_ms}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        ts, desc = cpu_sample(w, held)
+        cpu = {"value": k / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": desc + " (from x0 = 0)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3+f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
+                   "seed": w["seed"], "train_rhs": w["train"], "epochs": args.epochs,
+                   "train_loss": [float(hist[0]), float(hist[-1])],
+                   "train_set_s": t_gen, "train_s": t_train,
+                   "form": "learned start (tcgen05 BF16 network) + split-BF16 tcgen05 Gram and "
+                           "batched products, FP32 Alg. 2, FP64 KKT/refinement",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs smaller than L2 (timed as resident data)",
+                   "prepare_ms": avg(lambda s: s.prepare_ms), "iterate_ms": it_ms,
+                   "kkt_ms": avg(lambda s: s.kkt_ms), "solve_ms": avg(lambda s: s.solve_ms),
+                   "warm_mean_iters": warm_iters, "warm_started_fraction": kept_frac,
+                   "rel_kkt_max": worst},
+        "cold": cold,
+        "roofline": roof,
+        "roofline_secondary": None,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain_fp64": plain,

@@ -188,6 +188,75 @@ aln_status aln_kkt_residual(aln_ctx* ctx, const double* X, int64_t ldx, double* 
 aln_status aln_export_scaled(aln_ctx* ctx, double* Q, int64_t ldq, double* q, int64_t ldqv,
                              double* s);
 
+/* ---------------------------------------------------------------------------
+ * Learned start point (not in the paper: Alg. 2 starts at x⁰ = 0 in §3, and a
+ * given x⁰ maps to y⁰ = x⁰·√H_ii by Eq. Rescaling).  A network predicts y⁰ in
+ * the scaled space from q for a fixed A:
+ *   u  = [ (q/‖q‖ − μ)/σ ; z ],  μ, σ per entry over the training set,
+ *        z_j = (log s_j − mean)/std over j (std := 1 if 0)
+ *   h1 = relu(W1 u + b1), h2 = relu(W2 h1 + b2), [ŷ ; ℓ] = W3 h2 + b3
+ *   d  = relu(ŷ)·[ℓ > 0], y⁰ = α*·d with α* = max(0, −qᵀd/dᵀQd), the exact
+ *        line search of Alg. 2 from 0 along d, so f(y⁰) ≤ f(0) = 0
+ * W1 is hidden×2n, W2 hidden×hidden, W3 2n×hidden (row-major, FP32 master
+ * copies; products in BF16 on the tensor cores with FP32 accumulation).
+ * Training minimises mean (ŷ − y* / (τ‖q‖))² + mean BCE(ℓ, [y* > 0]) with
+ * Adam; τ is the RMS of y* / ‖q‖ over the training set.
+ * All calls need a context prepared with aln_prepare (not grouped); the
+ * network belongs to that A (its n and scale factors) and survives later
+ * aln_prepare calls with new right-hand sides.
+ * ------------------------------------------------------------------------- */
+typedef struct aln_train_opts {
+    int32_t epochs;   /* passes over the training pairs; default 10 */
+    int32_t batch;    /* pairs per Adam step; default 1024 */
+    int32_t hidden;   /* width of both hidden layers (used when the network is
+                         created by this call); default 1024 */
+    int32_t reserved;
+    double lr;        /* Adam step size; default 1e-3 */
+    double beta1;     /* default 0.9 */
+    double beta2;     /* default 0.999 */
+    double eps;       /* default 1e-8 */
+    uint64_t seed;    /* initial weights and shuffling; default 0 */
+} aln_train_opts;
+
+void aln_default_train_opts(aln_train_opts* opts);
+
+/* Create (or re-create) the network for the prepared n with He-uniform
+ * weights from `seed` and zero biases.  hidden ≥ 1.
+ * Errors: INVALID_ARG, NOT_PREPARED, OUT_OF_MEMORY, CUDA. */
+aln_status aln_warmstart_init(aln_ctx* ctx, int32_t hidden, uint64_t seed);
+
+/* Copy the FP32 parameters in (set = 1) or out (set = 0); any pointer may be
+ * NULL to skip that tensor; host or device memory.  Shapes as above, biases
+ * of length hidden, hidden, 2n; mu, sd (n each) and tau (1) are the feature
+ * and target normalisation (defaults 0, 1, 1; the first aln_warmstart_train
+ * sets them from its training set unless they were set here).
+ * Errors: INVALID_ARG (no network), CUDA. */
+aln_status aln_warmstart_params(aln_ctx* ctx, int32_t set, float* W1, float* b1, float* W2,
+                                float* b2, float* W3, float* b3, float* mu, float* sd,
+                                float* tau);
+
+/* One forward and backward pass without an update, on `count` pairs:
+ * Qb (count×n, the scaled q of each right-hand side, row-major FP64) and Yb
+ * (count×n, the scaled solutions y* = s·x*).  Writes the loss and the
+ * gradients (same shapes as the parameters; NULL skips).  For tests.
+ * Errors: INVALID_ARG, TIMEOUT, OUT_OF_MEMORY, CUDA. */
+aln_status aln_warmstart_grad(aln_ctx* ctx, const double* Qb, const double* Yb, int64_t count,
+                              double* loss, float* gW1, float* gb1, float* gW2, float* gb2,
+                              float* gW3, float* gb3);
+
+/* Train on `count` pairs (Qtrain, Ytrain as in aln_warmstart_grad; host or
+ * device).  Creates the network first when there is none.  epoch_loss: NULL
+ * or `epochs` doubles, the mean loss of each epoch.
+ * Errors: INVALID_ARG, NOT_PREPARED, TIMEOUT, OUT_OF_MEMORY, CUDA. */
+aln_status aln_warmstart_train(aln_ctx* ctx, const double* Qtrain, const double* Ytrain,
+                               int64_t count, const aln_train_opts* opts, double* epoch_loss);
+
+/* Start points for the prepared right-hand sides: X0 (k×n, X0[c*ldx + i],
+ * x-space, ready for aln_solve) and, when kept is not NULL, kept[c] = 1 if
+ * α* > 0 and 0 if the start is 0 (the direction does not descend).
+ * Errors: INVALID_ARG (no network, or n differs), NOT_PREPARED, TIMEOUT, CUDA. */
+aln_status aln_warmstart_predict(aln_ctx* ctx, double* X0, int64_t ldx, int32_t* kept);
+
 /* Device-time breakdown of the last calls, measured with CUDA events on the
  * context's stream, and counters (for benchmarks and tracing). */
 typedef struct aln_stats {

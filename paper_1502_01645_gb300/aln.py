@@ -28,7 +28,9 @@ RHS_MAXITER, RHS_NONFINITE, RHS_STAGNATED = 3, 4, 5
 EXPORTS = (
     "aln_default_options", "aln_create", "aln_prepare", "aln_solve", "aln_kkt_residual",
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
-    "aln_kkt_residual_noalloc", "aln_prepare_grouped",
+    "aln_kkt_residual_noalloc", "aln_prepare_grouped", "aln_default_train_opts",
+    "aln_warmstart_init", "aln_warmstart_params", "aln_warmstart_grad", "aln_warmstart_train",
+    "aln_warmstart_predict",
 )
 
 
@@ -58,6 +60,12 @@ class AlnStats(ctypes.Structure):
 class AlnProblem(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("d", ctypes.c_int64),
                 ("n", ctypes.c_int64), ("lda", ctypes.c_int64)]
+
+
+class AlnTrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("hidden", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class AlnError(RuntimeError):
@@ -104,6 +112,18 @@ def load(path: str | None = None):
     lib.aln_kkt_residual_noalloc.restype = ctypes.c_int
     lib.aln_prepare_grouped.argtypes = [vp, i32, ctypes.POINTER(AlnProblem), i32]
     lib.aln_prepare_grouped.restype = ctypes.c_int
+    lib.aln_default_train_opts.argtypes = [ctypes.POINTER(AlnTrainOpts)]
+    lib.aln_default_train_opts.restype = None
+    lib.aln_warmstart_init.argtypes = [vp, i32, ctypes.c_uint64]
+    lib.aln_warmstart_init.restype = ctypes.c_int
+    lib.aln_warmstart_params.argtypes = [vp, i32] + [vp] * 9
+    lib.aln_warmstart_params.restype = ctypes.c_int
+    lib.aln_warmstart_grad.argtypes = [vp, dp, dp, i64, dp] + [vp] * 6
+    lib.aln_warmstart_grad.restype = ctypes.c_int
+    lib.aln_warmstart_train.argtypes = [vp, dp, dp, i64, ctypes.POINTER(AlnTrainOpts), dp]
+    lib.aln_warmstart_train.restype = ctypes.c_int
+    lib.aln_warmstart_predict.argtypes = [vp, dp, i64, vp]
+    lib.aln_warmstart_predict.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -176,6 +196,35 @@ def aln_kkt_residual(ctx, X, ldx, rel, obj) -> None:
 def aln_export_scaled(ctx, Q, ldq, q, ldqv, s) -> None:
     _check(load().aln_export_scaled(ctx, _ptr(Q), ldq, _ptr(q), ldqv, _ptr(s)),
            "aln_export_scaled")
+
+
+def aln_default_train_opts() -> AlnTrainOpts:
+    o = AlnTrainOpts()
+    load().aln_default_train_opts(ctypes.byref(o))
+    return o
+
+
+def aln_warmstart_init(ctx, hidden, seed) -> None:
+    _check(load().aln_warmstart_init(ctx, hidden, seed), "aln_warmstart_init")
+
+
+def aln_warmstart_params(ctx, set_, tensors) -> None:
+    _check(load().aln_warmstart_params(ctx, set_, *[_ptr(t) for t in tensors]),
+           "aln_warmstart_params")
+
+
+def aln_warmstart_grad(ctx, Qb, Yb, count, loss, grads) -> None:
+    _check(load().aln_warmstart_grad(ctx, _ptr(Qb), _ptr(Yb), count, _ptr(loss),
+                                     *[_ptr(g) for g in grads]), "aln_warmstart_grad")
+
+
+def aln_warmstart_train(ctx, Qt, Yt, count, opts, epoch_loss) -> None:
+    _check(load().aln_warmstart_train(ctx, _ptr(Qt), _ptr(Yt), count, ctypes.byref(opts),
+                                      _ptr(epoch_loss)), "aln_warmstart_train")
+
+
+def aln_warmstart_predict(ctx, X0, ldx, kept) -> None:
+    _check(load().aln_warmstart_predict(ctx, _ptr(X0), ldx, _ptr(kept)), "aln_warmstart_predict")
 
 
 def aln_get_stats(ctx) -> AlnStats:
@@ -329,6 +378,62 @@ class Solver:
 
     def stats(self) -> AlnStats:
         return aln_get_stats(self.ctx)
+
+    # ------------------------------------------------------------ warm start
+    def warmstart_shapes(self, hidden):
+        n2 = 2 * self.n
+        return [(hidden, n2), (hidden,), (hidden, hidden), (hidden,), (n2, hidden), (n2,)]
+
+    def warmstart_init(self, hidden=1024, seed=0):
+        aln_warmstart_init(self.ctx, hidden, seed)
+        self.hidden = hidden
+
+    _WS_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "mu", "sd", "tau")
+
+    def warmstart_set(self, params):
+        """params: dict with any of W1, b1, W2, b2, W3, b3 (oracle shapes), mu,
+        sd (n) and tau (scalar); missing keys are left as they are."""
+        ts = []
+        for k in self._WS_KEYS:
+            v = params.get(k)
+            ts.append(None if v is None else
+                      np.ascontiguousarray(np.atleast_1d(v), dtype=np.float32))
+        aln_warmstart_params(self.ctx, 1, ts)
+
+    def warmstart_get(self):
+        shapes = self.warmstart_shapes(self.hidden) + [(self.n,), (self.n,), (1,)]
+        ts = [np.zeros(sh, np.float32) for sh in shapes]
+        aln_warmstart_params(self.ctx, 0, ts)
+        out = dict(zip(self._WS_KEYS, ts))
+        out["tau"] = float(out["tau"][0])
+        return out
+
+    def warmstart_grad(self, Qb, Yb):
+        Qb = np.ascontiguousarray(Qb, dtype=np.float64)
+        Yb = np.ascontiguousarray(Yb, dtype=np.float64)
+        loss = np.zeros(1)
+        gs = [np.zeros(sh, np.float32) for sh in self.warmstart_shapes(self.hidden)]
+        aln_warmstart_grad(self.ctx, Qb, Yb, Qb.shape[0], loss, gs)
+        return float(loss[0]), dict(zip(("W1", "b1", "W2", "b2", "W3", "b3"), gs))
+
+    def warmstart_train(self, Qt, Yt, **opts):
+        o = aln_default_train_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.hidden = o.hidden if not hasattr(self, "hidden") else self.hidden
+        if isinstance(Qt, np.ndarray):
+            Qt = np.ascontiguousarray(Qt, dtype=np.float64)
+            Yt = np.ascontiguousarray(Yt, dtype=np.float64)
+        hist = np.zeros(max(o.epochs, 1))
+        aln_warmstart_train(self.ctx, Qt, Yt, Qt.shape[0], o, hist)
+        return hist[:o.epochs]
+
+    def warmstart_predict(self, X0=None):
+        if X0 is None:
+            X0 = np.zeros((self.k, self.n))
+        kept = np.zeros(self.k, np.int32)
+        aln_warmstart_predict(self.ctx, X0, _row_major_ld(X0), kept)
+        return X0, kept
 
     def close(self):
         aln_destroy(self.ctx)

@@ -319,6 +319,7 @@ void aln_destroy(aln_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     batch_free(c);
     group_free(c);
+    mlp_free(c);
     void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -675,6 +676,72 @@ aln_status aln_export_scaled(aln_ctx* c, double* Q, int64_t ldq, double* q, int6
     }
     ALN_TRY(cudaStreamSynchronize(c->stream));
     return ALN_OK;
+}
+
+void aln_default_train_opts(aln_train_opts* o) {
+    if (!o) return;
+    o->epochs = 10;
+    o->batch = 1024;
+    o->hidden = 1024;
+    o->reserved = 0;
+    o->lr = 1e-3;
+    o->beta1 = 0.9;
+    o->beta2 = 0.999;
+    o->eps = 1e-8;
+    o->seed = 0;
+}
+
+static aln_status ws_ready(aln_ctx* c) {
+    if (!c) return ALN_ERR_INVALID_ARG;
+    if (!c->prepared) return ALN_ERR_NOT_PREPARED;
+    if (c->grouped) return ALN_ERR_INVALID_ARG;
+    return ALN_OK;
+}
+
+aln_status aln_warmstart_init(aln_ctx* c, int32_t hidden, uint64_t seed) {
+    ALN_CHECK(ws_ready(c));
+    if (hidden < 1 || hidden > (1 << 16)) return ALN_ERR_INVALID_ARG;
+    return mlp_init(c, hidden, seed);
+}
+
+aln_status aln_warmstart_params(aln_ctx* c, int32_t set, float* W1, float* b1, float* W2,
+                                float* b2, float* W3, float* b3, float* mu, float* sd,
+                                float* tau) {
+    ALN_CHECK(ws_ready(c));
+    if (mlp_n(c) != c->n) return ALN_ERR_INVALID_ARG;
+    float* t[9] = {W1, b1, W2, b2, W3, b3, mu, sd, tau};
+    return mlp_params(c, set ? 1 : 0, t);
+}
+
+aln_status aln_warmstart_grad(aln_ctx* c, const double* Qb, const double* Yb, int64_t count,
+                              double* loss, float* gW1, float* gb1, float* gW2, float* gb2,
+                              float* gW3, float* gb3) {
+    ALN_CHECK(ws_ready(c));
+    if (!Qb || !Yb || count < 1 || count > (1 << 20) || mlp_n(c) != c->n)
+        return ALN_ERR_INVALID_ARG;
+    float* g[6] = {gW1, gb1, gW2, gb2, gW3, gb3};
+    return mlp_grad(c, Qb, Yb, count, loss, g);
+}
+
+aln_status aln_warmstart_train(aln_ctx* c, const double* Qtrain, const double* Ytrain,
+                               int64_t count, const aln_train_opts* opts, double* epoch_loss) {
+    ALN_CHECK(ws_ready(c));
+    aln_train_opts o;
+    aln_default_train_opts(&o);
+    if (opts) o = *opts;
+    if (!Qtrain || !Ytrain || count < 1 || count > ((int64_t)1 << 31) - 1 || o.epochs < 0 ||
+        o.batch < 1 || o.batch > (1 << 16) || o.hidden < 1 || !(o.lr > 0.0) ||
+        !(o.beta1 >= 0.0 && o.beta1 < 1.0) || !(o.beta2 >= 0.0 && o.beta2 < 1.0) ||
+        !(o.eps > 0.0))
+        return ALN_ERR_INVALID_ARG;
+    if (mlp_n(c) != c->n) ALN_CHECK(mlp_init(c, o.hidden, o.seed));
+    return mlp_train(c, Qtrain, Ytrain, count, o, epoch_loss);
+}
+
+aln_status aln_warmstart_predict(aln_ctx* c, double* X0, int64_t ldx, int32_t* kept) {
+    ALN_CHECK(ws_ready(c));
+    if (!X0 || ldx < c->n || mlp_n(c) != c->n) return ALN_ERR_INVALID_ARG;
+    return mlp_predict(c, X0, ldx, kept);
 }
 
 }  // extern "C"

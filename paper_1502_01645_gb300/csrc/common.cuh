@@ -241,6 +241,8 @@ struct aln_ctx {
     // many independent problems (grouped.cu); null unless aln_prepare_grouped
     void* group = nullptr;
     int grouped = 0;
+    // learned start point (mlp.cu); null until created
+    void* mlp = nullptr;
 
     // statistics (aln_get_stats)
     cudaEvent_t ev[10] = {};

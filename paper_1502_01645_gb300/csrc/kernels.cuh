@@ -91,6 +91,17 @@ aln_status group_kkt(aln_ctx* c, const double* X, double* rel_kkt, double* objec
 aln_status group_export(aln_ctx* c, double* Q, double* q, double* s);
 void group_free(aln_ctx* c);
 
+// mlp.cu — learned start point
+aln_status mlp_init(aln_ctx* c, int hidden, uint64_t seed);
+aln_status mlp_params(aln_ctx* c, int set, float* const* t);
+aln_status mlp_grad(aln_ctx* c, const double* Qs, const double* Ys, int64_t count, double* loss,
+                    float* const* grads);
+aln_status mlp_train(aln_ctx* c, const double* Qs, const double* Ys, int64_t count,
+                     const aln_train_opts& o, double* epoch_loss);
+aln_status mlp_predict(aln_ctx* c, double* X0, int64_t ldx, int* kept);
+int mlp_n(const aln_ctx* c);
+void mlp_free(aln_ctx* c);
+
 // batch.cu — Alg. 2 on many right-hand sides sharing A
 aln_status batch_prepare(aln_ctx* c);
 aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t ldx,
