@@ -53,7 +53,7 @@ WORKLOADS = {
              "d = n*U{{2,3,4}}, A |N(0,1)| FP32, x_true 60% zeros U[0,1], 1% noise; "
              "all problems prepared and solved together (grouped)"),
     "warmstart": dict(
-        d=8000, n=2000, k=4096, tol=1e-6, seed=1005, prec="split_bf16", train=16384,
+        d=8000, n=2000, k=4096, tol=1e-6, seed=1005, prec="split_bf16", train=131072,
         desc="warmstart_{d}x{n}: A U[0,1] x log-uniform column scales FP32; x_true support "
              "U{{50..400}}, Exp(1) values, 1% noise; network trained on {train} solved "
              "right-hand sides, {k} held-out right-hand sides started from its prediction"),
@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--k", type=int, default=None, help="right-hand sides")
     ap.add_argument("--train", type=int, default=None,
                     help="training right-hand sides of the warm-start workload")
-    ap.add_argument("--epochs", type=int, default=20, help="warm-start training epochs")
+    ap.add_argument("--epochs", type=int, default=60, help="warm-start training epochs")
     return ap.parse_args()
 
 
