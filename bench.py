@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--train", type=int, default=None,
                     help="training right-hand sides of the warm-start workload")
     ap.add_argument("--epochs", type=int, default=60, help="warm-start training epochs")
+    ap.add_argument("--refine-gain", type=int, default=0,
+                    help="decades each inner FP32 run aims below the last FP64 residual "
+                         "(0: library default, <0: every run aims at tol)")
     return ap.parse_args()
 
 
@@ -289,7 +292,7 @@ def run_ours(args):
     Bt = torch.from_numpy(np.ascontiguousarray(B_np)).cuda()
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
 
     def step():
         solver.prepare(At, Bt)
@@ -342,7 +345,7 @@ def run_ours(args):
         B_h = torch.from_numpy(np.ascontiguousarray(B_np)).pin_memory()
         X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5))
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
         hsolver.prepare(A_h, B_h)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -404,7 +407,7 @@ def run_ours(args):
     it_ms = avg(lambda s: s.iterate_ms)
     rooflines = []
     if w["prec"] == "split_bf16" and k == 1:
-        flops = 3.0 * d * n * (n + 1)          # three split products over n(n+1)/2 entries
+        flops = 6.0 * d * n * (n + 1)          # six split products over n(n+1)/2 entries
         ach = flops / (gram / 1e3) / 1e12
         rooflines.append({"bound": "tensor", "kernel": "k_gram_tc (split-BF16 Gram)",
                           "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s",
@@ -445,11 +448,11 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w["prec"] == "fp64" else "bf16x3+f32", "data": "synthetic",
+        "dtype": "f64" if w["prec"] == "fp64" else "bf16 split + f32", "data": "synthetic",
         "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
                    "seed": w["seed"],
                    "form": ("FP64 Gram + FP64 Alg. 2" if w["prec"] == "fp64" else
-                            "split-BF16 tcgen05 Gram/products, FP32 Alg. 2, "
+                            "3-term split-BF16 tcgen05 Gram, FP32 Alg. 2, "
                             "FP64 scale/KKT/refinement"),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2" if A_np.nbytes > 129e6 else
@@ -457,7 +460,12 @@ def run_ours(args):
                    "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
                    "solve_ms": avg(lambda s: s.solve_ms), "iterate_ms": it_ms,
                    "kkt_ms": avg(lambda s: s.kkt_ms), "iters_max": iters,
-                   "rel_kkt_max": worst},
+                   "rel_kkt_max": worst,
+                   "phase_us_per_iteration": (
+                       None if k != 1 or stats[-1].iterations == 0 else
+                       dict(zip(("product", "barrier", "update", "clipped", "mask"),
+                                [round(stats[-1].phase_us[i] / stats[-1].iterations, 3)
+                                 for i in range(5)])))},
         "roofline": rooflines[0],
         "roofline_secondary": rooflines[1] if len(rooflines) > 1 else None,
         "cpu_baseline": cpu,
@@ -489,7 +497,7 @@ def run_grouped(args, w, world, rank, local):
             torch.from_numpy(np.ascontiguousarray(p.B[0])).cuda()) for p in probs]
     Xt = torch.zeros(N, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
     recs = aln.Solver.grouped_records(dev)
 
     def step():
@@ -541,7 +549,7 @@ def run_grouped(args, w, world, rank, local):
                  torch.from_numpy(np.ascontiguousarray(p.B[0])).pin_memory()) for p in probs]
         hrecs = aln.Solver.grouped_records(host)
         X_h = torch.zeros(N, dtype=torch.float64).pin_memory()
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
         hsolver.prepare_grouped(records=hrecs)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -614,7 +622,7 @@ def run_grouped(args, w, world, rank, local):
                   "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
                   "note": "Q_p is staged in shared memory when it fits and otherwise stays in "
                           "L2 between iterations, so frac can exceed 1"}]
-    flops = sum(3.0 * dd * nn * (nn + 1) for dd, nn in sizes)
+    flops = sum(6.0 * dd * nn * (nn + 1) for dd, nn in sizes)
     acht = flops / (gram / 1e3) / 1e12 if gram > 0 else 0.0
     rooflines.append({"bound": "tensor", "kernel": "k_ggram_tc (grouped split-BF16 Gram)",
                       "achieved": acht, "peak": peak_tc, "unit": "TFLOP/s",
@@ -632,7 +640,7 @@ def run_grouped(args, w, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w["prec"] == "fp64" else "bf16x3+f32", "data": "synthetic",
+        "dtype": "f64" if w["prec"] == "fp64" else "bf16 split + f32", "data": "synthetic",
         "config": {"workload": w["desc"], "problems": k, "sum_n": N,
                    "sum_d": sum(dd for dd, _ in sizes),
                    "n_range": [min(n for _, n in sizes), max(n for _, n in sizes)],
@@ -678,7 +686,7 @@ def run_warmstart(args, w, world, rank, local):
     Btr = torch.from_numpy(np.ascontiguousarray(train.B)).cuda()
     Bt = torch.from_numpy(np.ascontiguousarray(held.B)).cuda()
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
 
     # ---- training set and training (not timed) ----
     t0 = time.perf_counter()
@@ -827,7 +835,7 @@ def run_warmstart(args, w, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x3+f32", "data": "synthetic",
+        "dtype": "bf16 split + f32", "data": "synthetic",
         "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
                    "seed": w["seed"], "train_rhs": w["train"], "epochs": args.epochs,
                    "train_loss": [float(hist[0]), float(hist[-1])],

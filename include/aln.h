@@ -63,8 +63,10 @@ typedef enum aln_status {
 typedef enum aln_precision {
     /* H = AᵀA in FP64, Alg. 2 in FP64: the plain method. */
     ALN_PREC_FP64 = 0,
-    /* H from split-BF16 tensor-core products (hi·hi + hi·lo + lo·hi, FP32
-     * accumulation), Alg. 2 in FP32, scale factors / KKT / refinement in FP64. */
+    /* H from tensor-core products of the exact three-term BF16 split of A
+     * (a = h + m + l; hh + hm + mh + mm + hl + lh, FP32 accumulation), Alg. 2 in
+     * FP32, scale factors / KKT / refinement in FP64.  With many right-hand
+     * sides the scaled matrix comes from an FP64-accurate (Dot2) product. */
     ALN_PREC_SPLIT_BF16 = 1
 } aln_precision;
 
@@ -96,7 +98,13 @@ typedef struct aln_options {
     int32_t batch_min;    /* SPLIT_BF16 with at least this many right-hand sides
                              runs the batched solver (all columns advance together,
                              tcgen05 products Q·Ḡ); 0 = default 8 */
-    int32_t reserved;
+    int32_t refine_gain;  /* progressive refinement: each inner FP32 run stops
+                             when its relative KKT residual is this many decades
+                             below the last FP64 one (the first run: below 1),
+                             but not below tol/2 (first run) or tol/4 (later
+                             runs); < 0 = every run aims at tol; 0 = automatic:
+                             3 for the batched solver, off for the single-problem
+                             and grouped solvers (measured fastest on each) */
 } aln_options;
 
 typedef struct aln_solve_info {

@@ -233,6 +233,7 @@ void aln_default_options(aln_options* opt) {
     opt->stagnation = 100;
     opt->iter_kernel = 0;
     opt->batch_min = 8;
+    opt->refine_gain = 0;
 }
 
 int32_t aln_version(void) { return ALN_VERSION; }
@@ -264,6 +265,7 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
         return ALN_ERR_INVALID_ARG;
     if (o.stagnation == 0) o.stagnation = 100;
     if (o.batch_min == 0) o.batch_min = 8;
+    if (o.refine_gain > 16) return ALN_ERR_INVALID_ARG;
     aln_ctx* c = new (std::nothrow) aln_ctx();
     if (!c) return ALN_ERR_OUT_OF_MEMORY;
     c->opt = o;
@@ -390,13 +392,14 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     c->batched = (!f64 && k >= c->opt.batch_min) ? 1 : 0;
 
     // split copies for the tensor-core Gram
-    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    __nv_bfloat16 *hi = nullptr, *mid = nullptr, *lo = nullptr;
     if (!f64 && !c->batched) {
         c->ldk = round_up(d, 64);
         const size_t sb = (size_t)n * c->ldk * 2;
-        ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 2 * round_up(sb, 1024)));
+        ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 3 * round_up(sb, 1024)));
         hi = c->A_hi;
-        lo = (__nv_bfloat16*)((uint8_t*)c->A_hi + round_up(sb, 1024));
+        mid = (__nv_bfloat16*)((uint8_t*)c->A_hi + round_up(sb, 1024));
+        lo = (__nv_bfloat16*)((uint8_t*)c->A_hi + 2 * round_up(sb, 1024));
         c->A_lo = lo;
     }
 
@@ -405,7 +408,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     ALN_TRY(launch_check_finite(c->B, dtype, d, k, ldb, c->flags, c->stream));
     const int kc = k <= 4 ? (int)k : 0;
     ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64, ldq,
-                            c->flags, hi, lo, c->ldk, c->stream));
+                            c->flags, hi, mid, lo, c->ldk, c->stream));
     if (kc == 0) {
         if (c->batched && dtype == ALN_DTYPE_F32)  // FP64-accurate, on the FP32 pipe
             ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
@@ -421,7 +424,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     else if (f64)
         ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
     else
-        ALN_TRY(launch_gram_tc(hi, lo, d, n, c->ldk, c->inv_s, (float*)c->Q, ldq, c->flags + 1,
+        ALN_TRY(launch_gram_tc(hi, mid, lo, d, n, c->ldk, c->inv_s, (float*)c->Q, ldq, c->flags + 1,
                                c->stream));
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     c->launches += 4 + (kc == 0 ? 1 : 0);
@@ -541,8 +544,11 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
         const double* q64 = c->q64 + rhs * c->ldq;
         int total = 0, rounds = 0, status = ALN_RHS_MAXITER;
         double rel = 0.0, F = 0.0;
-        ALN_TRY(f64 ? launch_iter_setup<double>(c, q64, x0, eps_of(tol * first_factor), max_iter)
-                    : launch_iter_setup<float>(c, q64, x0, eps_of(tol * first_factor), max_iter));
+        // the FP64 iteration has no model error to refine away: one run to tol
+        const int gain = (f64 || c->opt.refine_gain == 0) ? -1 : c->opt.refine_gain;
+        const double t0 = inner_target(tol, first_factor, 1.0, gain);
+        ALN_TRY(f64 ? launch_iter_setup<double>(c, q64, x0, eps_of(t0), max_iter)
+                    : launch_iter_setup<float>(c, q64, x0, eps_of(t0), max_iter));
         c->launches += x0 ? 4 : 3;
         for (;;) {
             ALN_CHECK(run_until_done(c));
@@ -570,10 +576,9 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
             // Refinement: restart the inner loop from the current y with the exact
             // FP64 gradient g = Qy + q evaluated from A (left in c->g64 by the KKT pass).
             ++rounds;
-            ALN_TRY(f64 ? launch_iter_refresh_from_g64<double>(c, eps_of(tol * refine_factor),
-                                                               max_iter - total)
-                        : launch_iter_refresh_from_g64<float>(c, eps_of(tol * refine_factor),
-                                                              max_iter - total));
+            const double tr = inner_target(tol, refine_factor, rel, gain);
+            ALN_TRY(f64 ? launch_iter_refresh_from_g64<double>(c, eps_of(tr), max_iter - total)
+                        : launch_iter_refresh_from_g64<float>(c, eps_of(tr), max_iter - total));
             c->launches += 2;
         }
         c->stats.iterations += total;

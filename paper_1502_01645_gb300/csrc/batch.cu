@@ -268,7 +268,7 @@ __global__ void k_bunscale(BatchState s, const double* __restrict__ sc, double* 
 __global__ void __launch_bounds__(kBThreads) k_bcheck(
     BatchState s, const double* __restrict__ G64, const double* __restrict__ Y64,
     const double* __restrict__ q64, const double* __restrict__ bn2, const double* __restrict__ den,
-    double tol, double refine_factor, int max_refine, int* __restrict__ rounds,
+    double tol, double refine_factor, int gain, int max_refine, int* __restrict__ rounds,
     int* __restrict__ final_status, double* __restrict__ rel_out, double* __restrict__ obj_out,
     int* __restrict__ reactivated) {
     __shared__ double sc[32];
@@ -308,7 +308,8 @@ __global__ void __launch_bounds__(kBThreads) k_bcheck(
         } else {
             refine = 1;
             rounds[c] += 1;
-            const double t = refine_factor * tol * (den[c] > 0.0 ? den[c] : 1.0);
+            const double t =
+                inner_target(tol, refine_factor, rel, gain) * (den[c] > 0.0 ? den[c] : 1.0);
             s.eps[c] = t * t;
             s.colst[c] = -1;
             s.best[c] = 1.0 / 0.0;
@@ -325,6 +326,10 @@ __global__ void __launch_bounds__(kBThreads) k_bcheck(
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Progressive refinement is on by default here: with many columns the FP64
+// checks are cheap per column and shorter inner runs cut the column-iterations.
+static int batch_gain(const aln_ctx* c) { return c->opt.refine_gain == 0 ? 3 : c->opt.refine_gain; }
+
 struct BatchWork {
     int64_t k = 0, n = 0, ldq = 0, ldk = 0;
     int mtiles = 0;
@@ -530,7 +535,8 @@ static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine,
         return ALN_ERR_CUDA;
     cudaMemsetAsync(b->react, 0, sizeof(int), c->stream);
     k_bcheck<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64, b->Y64, c->q64, b->bn2, c->den,
-                                                       tol, 0.25, max_refine, b->rounds, b->fin,
+                                                       tol, 0.25, batch_gain(c), max_refine,
+                                                       b->rounds, b->fin,
                                                        b->rel, b->obj, b->react);
     cudaEventRecord(c->ev[7], c->stream);
     c->launches += 3;
@@ -579,8 +585,9 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     if (cudaMemcpyAsync(s.limits, lim, sizeof(lim), cudaMemcpyHostToDevice, c->stream) !=
         cudaSuccess)
         return ALN_ERR_CUDA;
-    k_binit<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->q64, X0dev, c->ldq, c->s, c->den,
-                                                      0.5 * tol, b->rounds);
+    k_binit<<<(unsigned)k, kBThreads, 0, c->stream>>>(
+        s, c->q64, X0dev, c->ldq, c->s, c->den, inner_target(tol, 0.5, 1.0, batch_gain(c)),
+        b->rounds);
     cudaMemsetAsync(b->fin, 0xff, (size_t)k * 4, c->stream);  // -1: not final yet
     cudaMemsetAsync(s.rows, 0, 24, c->stream);
     c->launches += 1;

@@ -107,6 +107,16 @@ __device__ __forceinline__ void load4(const double* p, double* o) {
     o[3] = b.y;
 }
 
+// Three-term BF16 split of an FP32 value: a = h + m + l exactly (8 + 8 + 8
+// significant bits cover FP32's 24; each difference below is exact in FP32).
+__device__ __forceinline__ void split3_bf16(float a, __nv_bfloat16& h, __nv_bfloat16& m,
+                                            __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(a);
+    const float r1 = a - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
 // Rounded products that the compiler may not fuse into a following add: the
 // error-free transformations below need fl(a·b) as a separate value.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
@@ -137,6 +147,19 @@ template <> struct DotAcc<double> {
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ double value() const { return s; }
 };
+
+// Stop target (relative KKT residual) of one inner FP32 run of Alg. 2 under
+// progressive refinement: `gain` decades below the FP64 residual measured
+// before the run (1 before the first run, where ḡ(0) = min(q, 0)), but not
+// below factor·tol; gain ≤ 0 aims at factor·tol directly.
+__host__ __device__ inline double inner_target(double tol, double factor, double rel_prev,
+                                               int gain) {
+    const double floor_t = factor * tol;
+    if (gain <= 0) return floor_t;
+    double t = rel_prev;
+    for (int i = 0; i < gain; ++i) t *= 0.1;
+    return t > floor_t ? t : floor_t;
+}
 
 // True when base + k·ld is 16-byte aligned for every k (vector loads allowed).
 inline bool aligned16(const void* base, int64_t ld, size_t esz) {

@@ -1,17 +1,23 @@
 // Split-BF16 Gram on the 5th-generation tensor cores (tcgen05 + TMA, sm_103a).
 //
 // Alg. 1 (§3) forms H = AᵀA and Q = D⁻¹HD⁻¹ with D = diag(√H_ii) (Eq. NQPQ).
-// Here every element of A is split into hi = bf16(a) and lo = bf16(a − hi), and
-//     H ≈ hiᵀhi + hiᵀlo + loᵀhi        (the lo·lo term, ≤ 2⁻¹⁸|a_i a_j|, dropped)
-// is accumulated in FP32 in tensor memory.  The epilogue multiplies by the FP64
-// scale factors 1/s_i, 1/s_j (rounded to FP32), sets Q_ii to 1 (0 for a zero
+// Here every FP32 element of A is split exactly into three BF16 terms,
+// a = h + m + l (|m| ≤ 2⁻⁸|a|, |l| ≤ 2⁻¹⁶|a|), and
+//     H ≈ hᵀh + hᵀm + mᵀh + mᵀm + hᵀl + lᵀh
+// (the dropped m·l, l·m, l·l terms are ≤ 2·2⁻²⁴|a_i a_j|) is accumulated in
+// FP32 in tensor memory.  A two-term split (error 2⁻¹⁸ per product) perturbs
+// Q by about n·10⁻⁵ in norm — as large as λ_min(Q) at n = 5000 — and made
+// Alg. 2 several times slower to converge; the third term costs twice the
+// tensor work and removes that.  The epilogue multiplies by the FP64 scale
+// factors 1/s_i, 1/s_j (rounded to FP32), sets Q_ii to 1 (0 for a zero
 // column, Eq. Rescaling) and writes each lower-triangle tile and its mirror.
 //
 // Kernel structure (one 128×128 output tile per CTA, 128 threads):
-//   warp 0, one lane: TMA producer — K-major 128×64 BF16 boxes of hi/lo for the
-//                     row tile and the column tile, 128-byte swizzle, into a
-//                     3-stage shared-memory ring guarded by mbarriers;
-//   warp 1, one lane: MMA issuer — 3 products × 4 K-steps of
+//   warp 0, one lane: TMA producer — K-major 128×64 BF16 boxes of h/m/l for
+//                     the row tile and the column tile, 128-byte swizzle, into
+//                     a 2-stage shared-memory ring (96 KiB per stage) guarded
+//                     by mbarriers;
+//   warp 1, one lane: MMA issuer — 6 products × 4 K-steps of
 //                     tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
 //                     per stage, then tcgen05.commit to free the stage;
 //   all 4 warps:      epilogue — tcgen05.ld 32 lanes × 16 columns at a time,
@@ -102,14 +108,37 @@ __device__ __forceinline__ void gram_tile_store(uint32_t tmem, int warp, int lan
     }
 }
 
+// Three-term split Gram: 2 stages of 6 boxes (A: h, m, l; B: h, m, l).
+constexpr int G3_STAGES = 2;
+constexpr int G3_STAGE_BYTES = 6 * TILE_BYTES;
+constexpr int G3_SMEM_BYTES = G3_STAGES * G3_STAGE_BYTES + 1024 + 256;
+
+// The six products of one 16-wide K step into the TMEM accumulator; `first`
+// starts the accumulation.  a/b: shared addresses of the h boxes (m and l
+// follow at TILE_BYTES and 2·TILE_BYTES).
+__device__ __forceinline__ void gram3_kstep(uint32_t tmem, uint32_t a, uint32_t b, uint32_t off,
+                                            bool first) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+    const uint64_t ah = sdesc_sw128(a + off), am = sdesc_sw128(a + TILE_BYTES + off),
+                   al = sdesc_sw128(a + 2 * TILE_BYTES + off);
+    const uint64_t bh = sdesc_sw128(b + off), bm = sdesc_sw128(b + TILE_BYTES + off),
+                   bl = sdesc_sw128(b + 2 * TILE_BYTES + off);
+    umma_bf16(tmem, ah, bh, idesc, first ? 0u : 1u);
+    umma_bf16(tmem, ah, bm, idesc, 1u);
+    umma_bf16(tmem, am, bh, idesc, 1u);
+    umma_bf16(tmem, am, bm, idesc, 1u);
+    umma_bf16(tmem, ah, bl, idesc, 1u);
+    umma_bf16(tmem, al, bh, idesc, 1u);
+}
+
 __global__ void __launch_bounds__(128, 1)
-    k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_lo,
-              GramArgs p) {
+    k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
+              const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-    uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
+    uint64_t* full = (uint64_t*)(smem + G3_STAGES * G3_STAGE_BYTES);
+    uint64_t* empty = full + G3_STAGES;
+    uint64_t* done = empty + G3_STAGES;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ float s_cs[BM];
     __shared__ int s_abort;
@@ -121,7 +150,7 @@ __global__ void __launch_bounds__(128, 1)
     const bool diag = tm == tn;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < G3_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -146,49 +175,42 @@ __global__ void __launch_bounds__(128, 1)
         // ---------------- TMA producer ----------------
         int issued = 0;
         for (int kb = 0; kb < p.num_kb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+            const int s = kb % G3_STAGES;
+            if (kb >= G3_STAGES && !mbar_wait(&empty[s], ((kb / G3_STAGES) & 1) ^ 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
-            uint8_t* sb = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full[s], (diag ? 2 : 4) * TILE_BYTES);
+            uint8_t* sb = smem + s * G3_STAGE_BYTES;
+            mbar_expect_tx(&full[s], (diag ? 3 : 6) * TILE_BYTES);
             tma_load_2d(sb, &m_hi, &full[s], kb * BK, (int)m0);
-            tma_load_2d(sb + TILE_BYTES, &m_lo, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sb + TILE_BYTES, &m_mid, &full[s], kb * BK, (int)m0);
+            tma_load_2d(sb + 2 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)m0);
             if (!diag) {
-                tma_load_2d(sb + 2 * TILE_BYTES, &m_hi, &full[s], kb * BK, (int)n0);
-                tma_load_2d(sb + 3 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)n0);
+                tma_load_2d(sb + 3 * TILE_BYTES, &m_hi, &full[s], kb * BK, (int)n0);
+                tma_load_2d(sb + 4 * TILE_BYTES, &m_mid, &full[s], kb * BK, (int)n0);
+                tma_load_2d(sb + 5 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)n0);
             }
             ++issued;
         }
-        // Our own copies in flight: the last ≤ STAGES loads (bounded wait).
-        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
+        // Our own copies in flight: the last ≤ G3_STAGES loads (bounded wait).
+        for (int kb = max(0, issued - G3_STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % G3_STAGES], (kb / G3_STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
         for (int kb = 0; kb < p.num_kb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+            const int s = kb % G3_STAGES;
+            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_lo = a_hi + TILE_BYTES;
-            const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TILE_BYTES;
-            const uint32_t b_lo = diag ? a_lo : a_hi + 3 * TILE_BYTES;
+            const uint32_t a = smem_u32(smem + s * G3_STAGE_BYTES);
+            const uint32_t b = diag ? a : a + 3 * TILE_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;  // 16 BF16 along K
-                const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-                const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
-                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
-                umma_bf16(tmem, dah, dbl, idesc, 1u);
-                umma_bf16(tmem, dal, dbh, idesc, 1u);
-            }
+            for (int kk = 0; kk < BK / 16; ++kk)
+                gram3_kstep(tmem, a, b, kk * 32, (kb | kk) == 0);  // 16 BF16 along K
             umma_commit(&empty[s]);
         }
         // Always commit: `done` then also covers MMAs issued before an abort.
@@ -223,6 +245,7 @@ struct GGramArgs {
     const GProb* gp;
     const GTile* tiles;
     const __nv_bfloat16* hi;
+    const __nv_bfloat16* mid;
     const __nv_bfloat16* lo;
     const double* inv_s;  // packed by GProb::voff
     float* Q;             // pool; problem p at GProb::qoff, row length GProb::ldq
@@ -243,9 +266,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 __global__ void __launch_bounds__(128, 1) k_ggram_tc(GGramArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-    uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
+    uint64_t* full = (uint64_t*)(smem + G3_STAGES * G3_STAGE_BYTES);
+    uint64_t* empty = full + G3_STAGES;
+    uint64_t* done = empty + G3_STAGES;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ float s_cs[BM];
     __shared__ int s_abort;
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(128, 1) k_ggram_tc(GGramArgs a) {
     const int num_kb = P.KB;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < G3_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -281,54 +304,44 @@ __global__ void __launch_bounds__(128, 1) k_ggram_tc(GGramArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        const __nv_bfloat16* ah = a.hi + (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
-        const __nv_bfloat16* al = a.lo + (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
-        const __nv_bfloat16* bh = a.hi + (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
-        const __nv_bfloat16* bl = a.lo + (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
+        const int64_t ta = (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
+        const int64_t tb = (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
         int issued = 0;
         for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) & 1) ^ 1)) {
+            const int s = kb % G3_STAGES;
+            if (kb >= G3_STAGES && !mbar_wait(&empty[s], ((kb / G3_STAGES) & 1) ^ 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
-            uint8_t* sb = smem + s * STAGE_BYTES;
+            uint8_t* sb = smem + s * G3_STAGE_BYTES;
             const int64_t off = (int64_t)kb * kPackTile;
-            mbar_expect_tx(&full[s], (diag ? 2 : 4) * TILE_BYTES);
-            bulk_load(sb, ah + off, TILE_BYTES, &full[s]);
-            bulk_load(sb + TILE_BYTES, al + off, TILE_BYTES, &full[s]);
+            mbar_expect_tx(&full[s], (diag ? 3 : 6) * TILE_BYTES);
+            bulk_load(sb, a.hi + ta + off, TILE_BYTES, &full[s]);
+            bulk_load(sb + TILE_BYTES, a.mid + ta + off, TILE_BYTES, &full[s]);
+            bulk_load(sb + 2 * TILE_BYTES, a.lo + ta + off, TILE_BYTES, &full[s]);
             if (!diag) {
-                bulk_load(sb + 2 * TILE_BYTES, bh + off, TILE_BYTES, &full[s]);
-                bulk_load(sb + 3 * TILE_BYTES, bl + off, TILE_BYTES, &full[s]);
+                bulk_load(sb + 3 * TILE_BYTES, a.hi + tb + off, TILE_BYTES, &full[s]);
+                bulk_load(sb + 4 * TILE_BYTES, a.mid + tb + off, TILE_BYTES, &full[s]);
+                bulk_load(sb + 5 * TILE_BYTES, a.lo + tb + off, TILE_BYTES, &full[s]);
             }
             ++issued;
         }
-        for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
-            if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
+        for (int kb = max(0, issued - G3_STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % G3_STAGES], (kb / G3_STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
         for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+            const int s = kb % G3_STAGES;
+            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_lo = a_hi + TILE_BYTES;
-            const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TILE_BYTES;
-            const uint32_t b_lo = diag ? a_lo : a_hi + 3 * TILE_BYTES;
+            const uint32_t a0 = smem_u32(smem + s * G3_STAGE_BYTES);
+            const uint32_t b0 = diag ? a0 : a0 + 3 * TILE_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;
-                const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-                const uint64_t dbh = sdesc_sw128(b_hi + off), dbl = sdesc_sw128(b_lo + off);
-                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
-                umma_bf16(tmem, dah, dbl, idesc, 1u);
-                umma_bf16(tmem, dal, dbh, idesc, 1u);
-            }
+            for (int kk = 0; kk < BK / 16; ++kk) gram3_kstep(tmem, a0, b0, kk * 32, (kb | kk) == 0);
             umma_commit(&empty[s]);
         }
         umma_commit(done);
@@ -523,21 +536,24 @@ __global__ void __launch_bounds__(128, 1)
 
 bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_minor == 3; }
 
-cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t d,
-                           int64_t n, int64_t ldk, const double* inv_s, float* Q, int64_t ldq,
-                           int* timeout_flag, cudaStream_t st) {
+cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                           const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
+                           const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
+                           cudaStream_t st) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
-    if (((uintptr_t)hi & 15) || ((uintptr_t)lo & 15) || (ldk * 2) % 16 != 0 || ldq % 4 != 0)
+    if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) ||
+        (ldk * 2) % 16 != 0 || ldq % 4 != 0)
         return cudaErrorInvalidValue;
-    CUtensorMap mh, ml;
-    if (!make_map(&mh, hi, ldk, n, ldk) || !make_map(&ml, lo, ldk, n, ldk))
+    CUtensorMap mh, mm, ml;
+    if (!make_map(&mh, hi, ldk, n, ldk) || !make_map(&mm, mid, ldk, n, ldk) ||
+        !make_map(&ml, lo, ldk, n, ldk))
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
+                                             G3_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -549,21 +565,23 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
-    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, SMEM_BYTES, st>>>(mh, ml, a);
+    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
-                            const __nv_bfloat16* hi, const __nv_bfloat16* lo,
-                            const double* inv_s, float* Q, int* timeout_flag, cudaStream_t st) {
+                            const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                            const __nv_bfloat16* lo, const double* inv_s, float* Q,
+                            int* timeout_flag, cudaStream_t st) {
     using namespace tc;
     if (ntiles <= 0) return cudaSuccess;
-    if (((uintptr_t)hi & 15) || ((uintptr_t)lo & 15) || ((uintptr_t)Q & 15))
+    if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) ||
+        ((uintptr_t)Q & 15))
         return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_ggram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
+                                             G3_SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -571,11 +589,12 @@ cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
     a.gp = gp;
     a.tiles = tiles;
     a.hi = hi;
+    a.mid = mid;
     a.lo = lo;
     a.inv_s = inv_s;
     a.Q = Q;
     a.timeout_flag = timeout_flag;
-    k_ggram_tc<<<(unsigned)ntiles, 128, SMEM_BYTES, st>>>(a);
+    k_ggram_tc<<<(unsigned)ntiles, 128, G3_SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(128) k_gcolstats(const GProb* __restrict__ gp,
                                                    double* __restrict__ inv_s,
                                                    double* __restrict__ q64, int* __restrict__ flags,
                                                    __nv_bfloat16* __restrict__ hi,
+                                                   __nv_bfloat16* __restrict__ mid,
                                                    __nv_bfloat16* __restrict__ lo) {
     __shared__ double scratch[32];
     const int p = find_prob<kKeySlot>(gp, count, blockIdx.x);
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(128) k_gcolstats(const GProb* __restrict__ gp,
             for (int t = threadIdx.x; t < kpad; t += blockDim.x) {
                 const int64_t e = pack_index(P.pack, P.KB, j, t);
                 hi[e] = z;
+                mid[e] = z;
                 lo[e] = z;
             }
         return;
@@ -105,11 +107,12 @@ __global__ void __launch_bounds__(128) k_gcolstats(const GProb* __restrict__ gp,
             bad |= !isfinite(av[u]) || !isfinite(bv[u]);
             const int t = t0 + u * blockDim.x;
             if (split && t < P.d) {
-                const float af = (float)av[u];
-                const __nv_bfloat16 h = __float2bfloat16_rn(af);
+                __nv_bfloat16 h, m, l;
+                split3_bf16((float)av[u], h, m, l);
                 const int64_t e = pack_index(P.pack, P.KB, j, t);
                 hi[e] = h;
-                lo[e] = __float2bfloat16_rn(af - __bfloat162float(h));
+                mid[e] = m;
+                lo[e] = l;
             }
         }
     }
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(128) k_gcolstats(const GProb* __restrict__ gp,
         for (int t = P.d + threadIdx.x; t < kpad; t += blockDim.x) {
             const int64_t e = pack_index(P.pack, P.KB, j, t);
             hi[e] = z;
+            mid[e] = z;
             lo[e] = z;
         }
     const double s2 = block_sum(sq.value(), scratch);
@@ -186,7 +190,7 @@ struct GSolveArgs {
     const double* den;     // per problem ‖min(q,0)‖
     double* y;             // packed (foff), in/out
     GStat* stat;
-    double stop_factor;    // inner stop: ‖ḡ‖ < stop_factor·den_p
+    const double* tgt;     // per problem: inner stop ‖ḡ‖ < tgt_p·den_p (relative KKT)
     int gmode;             // 0: g = Q y + q here; 1: g = g64
     int max_iter;
     int window;
@@ -434,7 +438,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
     }
 
     GStat st = a.stat[p];
-    const double sf = a.stop_factor * a.den[p];
+    const double sf = a.tgt[p] * (a.den[p] > 0.0 ? a.den[p] : 1.0);
     const T eps = (T)(sf * sf);
     const int max_iter = a.max_iter, window = a.window;
     int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
@@ -579,7 +583,7 @@ size_t gsolve_static_bytes(int ldq) {
 __global__ void k_ginit(const GProb* __restrict__ gp, int count, int64_t total,
                         const double* __restrict__ x0, const double* __restrict__ s,
                         double* __restrict__ y, GStat* __restrict__ stat, int* __restrict__ fin,
-                        int* __restrict__ rounds) {
+                        int* __restrict__ rounds, double* __restrict__ tgt, double t0) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int p = find_prob<kKeyV>(gp, count, e);
@@ -591,6 +595,7 @@ __global__ void k_ginit(const GProb* __restrict__ gp, int count, int64_t total,
             stat[p] = z;
             fin[p] = -1;
             rounds[p] = 0;
+            tgt[p] = t0;
         }
     }
 }
@@ -672,9 +677,10 @@ __global__ void __launch_bounds__(256) k_gkkt_final(const GProb* __restrict__ gp
                                                     const double* __restrict__ r,
                                                     const double* __restrict__ den,
                                                     const GStat* __restrict__ stat, double tol,
-                                                    int max_iter, int max_refine, int refining,
-                                                    int* __restrict__ fin,
+                                                    int max_iter, int max_refine, int gain,
+                                                    int refining, int* __restrict__ fin,
                                                     int* __restrict__ rounds,
+                                                    double* __restrict__ tgt,
                                                     int* __restrict__ again,
                                                     double* __restrict__ rel_out,
                                                     double* __restrict__ obj_out) {
@@ -708,6 +714,7 @@ __global__ void __launch_bounds__(256) k_gkkt_final(const GProb* __restrict__ gp
             f = inner == ALN_RHS_STAGNATED ? ALN_RHS_STAGNATED : ALN_RHS_MAXITER;
         } else {
             rounds[p] += 1;
+            tgt[p] = inner_target(tol, 0.25, rel, gain);  // next run: from the exact gradient
         }
         if (f >= 0) fin[p] = f;
         again[p] = f < 0 ? 1 : 0;
@@ -741,10 +748,10 @@ struct GroupWork {
     GStat* stat = nullptr;
     double *s = nullptr, *inv_s = nullptr, *q64 = nullptr, *g64 = nullptr, *x64 = nullptr,
            *gpart = nullptr, *r64 = nullptr, *den = nullptr, *bn2 = nullptr, *rel = nullptr,
-           *obj = nullptr;
+           *obj = nullptr, *tgt = nullptr;
     void* y = nullptr;            // packed (foff), iteration type
     void* Q = nullptr;            // pool, iteration type
-    __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+    __nv_bfloat16 *hi = nullptr, *mid = nullptr, *lo = nullptr;
 
     void* copies = nullptr;       // device copies of host inputs
     size_t copies_bytes = 0;
@@ -805,8 +812,7 @@ unsigned grid_for(int64_t work, int threads, int cap) {
 }
 
 template <typename T>
-aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, double stop_factor, int gmode,
-                      int max_iter) {
+aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, int gmode, int max_iter) {
     GSolveArgs<T> a;
     a.gp = g->gp;
     a.order = g->order;
@@ -818,7 +824,7 @@ aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, double stop_factor,
     a.den = g->den;
     a.y = (double*)g->y;
     a.stat = g->stat;
-    a.stop_factor = stop_factor;
+    a.tgt = g->tgt;
     a.gmode = gmode;
     a.max_iter = max_iter;
     a.window = c->opt.stagnation;
@@ -835,6 +841,7 @@ aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, double stop_factor,
 
 aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_refine,
                     int refining) {
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
     const unsigned gr = grid_for(g->sum_d, 256, 8 * c->num_sms);
     const unsigned gg = grid_for(g->sum_n * 32, 256, 16 * c->num_sms);
     if (g->dtype == ALN_DTYPE_F32) {
@@ -849,8 +856,12 @@ aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_
                                                     g->r64, g->fin, g->g64, g->gpart);
     }
     k_gkkt_final<<<g->count, 256, 0, c->stream>>>(g->gp, g->gpart, g->r64, g->den, g->stat, tol,
-                                                  max_iter, max_refine, refining, g->fin,
-                                                  g->rounds, g->again, g->rel, g->obj);
+                                                  max_iter, max_refine,
+                                                  (f64 || c->opt.refine_gain == 0)
+                                                      ? -1
+                                                      : c->opt.refine_gain,
+                                                  refining, g->fin, g->rounds, g->tgt, g->again,
+                                                  g->rel, g->obj);
     G_TRY(cudaGetLastError());
     c->launches += 3;
     return ALN_OK;
@@ -972,9 +983,10 @@ static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const al
         (size_t)voff * 8, (size_t)voff * 8,            // s, inv_s, q64, g64, x64, gpart
         (size_t)roff * 8,                              // r64
         (size_t)count * 8, (size_t)count * 8, (size_t)count * 8, (size_t)count * 8,  // den bn2 rel obj
+        (size_t)count * 8,                             // tgt
         (size_t)foff * 8,                              // y (FP64)
         (size_t)qoff * T,                              // Q
-        pack_elems * 2, pack_elems * 2,                // hi, lo
+        pack_elems * 2, pack_elems * 2, pack_elems * 2,  // hi, mid, lo
     };
     const int nsz = (int)(sizeof(sizes) / sizeof(sizes[0]));
     size_t total = 0;
@@ -1009,9 +1021,11 @@ static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const al
         g->bn2 = (double*)take();
         g->rel = (double*)take();
         g->obj = (double*)take();
+        g->tgt = (double*)take();
         g->y = take();
         g->Q = take();
         g->hi = (__nv_bfloat16*)take();
+        g->mid = (__nv_bfloat16*)take();
         g->lo = (__nv_bfloat16*)take();
         if (k != nsz || (size_t)(p - (uint8_t*)g->pool) != total) return ALN_ERR_CUDA;
     }
@@ -1079,11 +1093,12 @@ aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, in
     const unsigned slots = (unsigned)g->slots;
     if (dtype == ALN_DTYPE_F32)
         k_gcolstats<float><<<slots, 128, 0, c->stream>>>(g->gp, count, f64 ? 0 : 1, g->s,
-                                                         g->inv_s, g->q64, g->flags, g->hi, g->lo);
+                                                         g->inv_s, g->q64, g->flags, g->hi,
+                                                         g->mid, g->lo);
     else
         k_gcolstats<double><<<slots, 128, 0, c->stream>>>(g->gp, count, f64 ? 0 : 1, g->s,
                                                           g->inv_s, g->q64, g->flags, g->hi,
-                                                          g->lo);
+                                                          g->mid, g->lo);
     if (dtype == ALN_DTYPE_F32)
         k_gden<float><<<count, 256, 0, c->stream>>>(g->gp, g->q64, g->den, g->bn2);
     else
@@ -1100,8 +1115,8 @@ aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, in
         }
         c->launches += count;
     } else {
-        G_TRY(launch_ggram_tc(g->gp, g->tiles, g->ntiles, g->hi, g->lo, g->inv_s, (float*)g->Q,
-                              g->flags + 1, c->stream));
+        G_TRY(launch_ggram_tc(g->gp, g->tiles, g->ntiles, g->hi, g->mid, g->lo, g->inv_s,
+                              (float*)g->Q, g->flags + 1, c->stream));
         c->launches += 1;
     }
     G_TRY(cudaEventRecord(c->ev[2], c->stream));
@@ -1167,7 +1182,11 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
     }
     const unsigned gv = grid_for(N, 256, 8 * c->num_sms);
     k_ginit<<<gv, 256, 0, c->stream>>>(g->gp, count, N, x0, g->s, (double*)g->y, g->stat,
-                                       g->fin, g->rounds);
+                                       g->fin, g->rounds, g->tgt,
+                                       inner_target(tol, 0.5, 1.0,
+                                                    (f64 || c->opt.refine_gain == 0)
+                                                        ? -1
+                                                        : c->opt.refine_gain));
     G_TRY(cudaGetLastError());
     c->launches += 1;
     G_TRY(cudaMemcpyAsync(g->order, g->order_all.data(), (size_t)count * sizeof(int),
@@ -1176,15 +1195,15 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
     std::vector<int> next;
     next.reserve(count);
     int nactive = count;
-    // Inner runs stop a little below tol so that the FP64 check usually passes
-    // at once; refinement rounds aim lower still, from the exact gradient.
-    double factor = 0.5;
+    // Each inner run stops at its problem's target (progressive refinement:
+    // a few decades below the last FP64 residual, at least tol/2 or tol/4);
+    // later runs restart from the exact FP64 gradient.
     int gmode = 0;
     double iter_ms = 0.0, kkt_ms = 0.0;
     for (int round = 0;; ++round) {
         G_TRY(cudaEventRecord(c->ev[6], c->stream));
-        G_CHECK(f64 ? run_solver<double>(c, g, nactive, factor * tol, gmode, max_iter)
-                    : run_solver<float>(c, g, nactive, factor * tol, gmode, max_iter));
+        G_CHECK(f64 ? run_solver<double>(c, g, nactive, gmode, max_iter)
+                    : run_solver<float>(c, g, nactive, gmode, max_iter));
         G_TRY(cudaEventRecord(c->ev[7], c->stream));
         k_gunscale<<<gv, 256, 0, c->stream>>>(g->gp, count, N, (const double*)g->y, g->s,
                                               g->x64);
@@ -1205,7 +1224,6 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
         nactive = (int)next.size();
         G_TRY(cudaMemcpyAsync(g->order, next.data(), (size_t)nactive * sizeof(int),
                               cudaMemcpyHostToDevice, c->stream));
-        factor = 0.25;
         gmode = 1;
     }
     // results

@@ -15,7 +15,7 @@ constexpr int MODE_AXPY = 2;
 cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
                             const void* B, int kc, int64_t ldb, double* s, double* inv_s,
                             double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
-                            __nv_bfloat16* lo, int64_t ldk, cudaStream_t st);
+                            __nv_bfloat16* mid, __nv_bfloat16* lo, int64_t ldk, cudaStream_t st);
 cudaError_t launch_check_finite(const void* X, int32_t dtype, int64_t rows, int64_t cols,
                                 int64_t ld, int* flags, cudaStream_t st);
 cudaError_t launch_denominators(const double* q64, int64_t n, int64_t ldq, int64_t k, double* den,
@@ -36,10 +36,12 @@ cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, in
                                int64_t ldo, cudaStream_t st);
 
 // gemm_tc.cu — split-BF16 tensor-core Gram (tcgen05 + TMA)
-// Q_ij = (Σ_t hi·hi + hi·lo + lo·hi)_ij · inv_s_i · inv_s_j, lower tiles mirrored.
-cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* lo, int64_t d,
-                           int64_t n, int64_t ldk, const double* inv_s, float* Q, int64_t ldq,
-                           int* timeout_flag, cudaStream_t st);
+// Q_ij = (Σ_t hh + hm + mh + mm + hl + lh)_ij · inv_s_i · inv_s_j for the exact
+// three-term split a = h + m + l; lower tiles mirrored.
+cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                           const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
+                           const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
+                           cudaStream_t st);
 bool tc_supported(int cc_major, int cc_minor);
 // W = Q·V (mode 0, with per-column curvature partials) or g += Q·V (mode 1)
 // over the compacted columns of a batch (batch.cu).
@@ -82,8 +84,9 @@ __host__ __device__ __forceinline__ int64_t pack_index(int64_t tile0, int KB, in
     return tile * kPackTile + r * 64 + ((((kk >> 3) ^ (r & 7)) << 3) | (kk & 7));
 }
 cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
-                            const __nv_bfloat16* hi, const __nv_bfloat16* lo,
-                            const double* inv_s, float* Q, int* timeout_flag, cudaStream_t st);
+                            const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                            const __nv_bfloat16* lo, const double* inv_s, float* Q,
+                            int* timeout_flag, cudaStream_t st);
 aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, int32_t dtype);
 aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const double* X0,
                        aln_solve_info* info);

@@ -20,8 +20,9 @@ __device__ __forceinline__ void load4t(const double* p, double* o) { load4(p, o)
 //   s_i  = √s_i², or 1 when s_i² = 0 (Eq. Rescaling's H_ii = 0 case)
 //   q_ci = −c_ci / s_i                            — q of Eq. NQPQ
 // Sums are accurate to FP64 level (DotAcc) and combined in FP64.
-// With SPLIT, also writes hi = bf16(A_ti), lo = bf16(A_ti − hi) into the
-// K-major [n][ldk] arrays read by the tensor-core Gram (zero padding t ≥ d).
+// With SPLIT, also writes the exact three-term split A_ti = hi + mid + lo
+// (BF16 each) into the K-major [n][ldk] arrays read by the tensor-core Gram
+// (zero padding t ≥ d).
 // VEC: the column and B rows are 16-byte aligned, so four consecutive
 // elements move per load (the kernel is HBM-bound; wide loads keep enough
 // bytes in flight).
@@ -33,6 +34,7 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
                                                   double* __restrict__ q64, int64_t ldq,
                                                   int* __restrict__ flags,
                                                   __nv_bfloat16* __restrict__ hi,
+                                                  __nv_bfloat16* __restrict__ mid,
                                                   __nv_bfloat16* __restrict__ lo, int64_t ldk) {
     __shared__ double scratch[32];
     const int64_t i = blockIdx.x;
@@ -59,14 +61,11 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
             }
         }
         if (SPLIT) {
-            __nv_bfloat16 h[4], l[4];
+            __align__(8) __nv_bfloat16 h[4], m[4], l[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const float af = (float)a[u];
-                h[u] = __float2bfloat16_rn(af);
-                l[u] = __float2bfloat16_rn(af - __bfloat162float(h[u]));
-            }
+            for (int u = 0; u < 4; ++u) split3_bf16((float)a[u], h[u], m[u], l[u]);
             *reinterpret_cast<uint2*>(hi + i * ldk + 4 * q) = *reinterpret_cast<uint2*>(h);
+            *reinterpret_cast<uint2*>(mid + i * ldk + 4 * q) = *reinterpret_cast<uint2*>(m);
             *reinterpret_cast<uint2*>(lo + i * ldk + 4 * q) = *reinterpret_cast<uint2*>(l);
         }
     }
@@ -76,16 +75,18 @@ __global__ void __launch_bounds__(256) k_colstats(const TA* __restrict__ A, int6
         bad |= !isfinite(a);
         for (int c = 0; c < kc; ++c) dot[c].add(a, B[(int64_t)c * ldb + t]);
         if (SPLIT) {
-            const float af = (float)col[t];
-            const __nv_bfloat16 h = __float2bfloat16_rn(af);
+            __nv_bfloat16 h, m, l;
+            split3_bf16((float)col[t], h, m, l);
             hi[i * ldk + t] = h;
-            lo[i * ldk + t] = __float2bfloat16_rn(af - __bfloat162float(h));
+            mid[i * ldk + t] = m;
+            lo[i * ldk + t] = l;
         }
     }
     if (SPLIT) {
         const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
         for (int64_t t = d + threadIdx.x; t < ldk; t += blockDim.x) {
             hi[i * ldk + t] = z;
+            mid[i * ldk + t] = z;
             lo[i * ldk + t] = z;
         }
     }
@@ -351,14 +352,16 @@ cudaError_t launch_qvec32_dot2(const float* A, int64_t d, int64_t n, int64_t lda
 cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
                             const void* B, int kc, int64_t ldb, double* s, double* inv_s,
                             double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
-                            __nv_bfloat16* lo, int64_t ldk, cudaStream_t st) {
+                            __nv_bfloat16* mid, __nv_bfloat16* lo, int64_t ldk,
+                            cudaStream_t st) {
     const dim3 grid((unsigned)n), block(256);
     const bool split = hi != nullptr;
     const size_t esz = dtype == ALN_DTYPE_F32 ? 4 : 8;
     const bool vec = aligned16(A, lda, esz) && (kc == 0 || aligned16(B, ldb, esz));
 #define ALN_COLSTATS(TA, SP, VE)                                                              \
     k_colstats<TA, SP, VE><<<grid, block, 0, st>>>((const TA*)A, d, n, lda, (const TA*)B, kc, \
-                                                   ldb, s, inv_s, q64, ldq, flags, hi, lo, ldk)
+                                                   ldb, s, inv_s, q64, ldq, flags, hi, mid, lo, \
+                                                   ldk)
     if (dtype == ALN_DTYPE_F32) {
         if (split) {
             if (vec) ALN_COLSTATS(float, true, true);
