@@ -224,9 +224,12 @@ __device__ __forceinline__ int gwarp_scan_excl(int v, int* total) {
 // Shared scratch of the block-wide reductions and list builders.
 template <typename T>
 struct GRed {
-    T wsum[kGWarps];
+    double wsum[kGWarps];
     int wcnt[kGWarps];
     int wlist[kGWarps];
+    int base[kGWarps];
+    double tsum;
+    int tcnt, tlist;
 };
 
 // Contiguous range of 32-element chunks scanned by this warp.
@@ -238,25 +241,39 @@ __device__ __forceinline__ void warp_chunks(int n, int& c0, int& c1) {
 }
 
 // Reduce per-warp (value, count, list count) and give each warp its list
-// base; every thread receives the totals (identical in every lane and warp).
+// base; every thread receives the totals.  The value's warp partials are
+// added in FP64 by warp 0 alone: the step scalars (γ = ‖ḡ‖², κ = ḡᵀQḡ) need
+// more than FP32 — with FP32 scalars the FP32 iteration drifts from the true
+// gradient and needs several times more iterations — while FP64 work by every
+// warp would cost microseconds on this GPU's narrow FP64 pipe.
 template <typename T>
-__device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, T* vt, int* ct,
-                                            int* lt) {
+__device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, double* vt,
+                                            int* ct, int* lt) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     v = gwarp_sum(v);
     __syncthreads();  // earlier readers of r are done
     if (lane == 0) {
-        r->wsum[wid] = v;
+        r->wsum[wid] = (double)v;
         r->wcnt[wid] = cnt;
         r->wlist[wid] = lcnt;
     }
     __syncthreads();
-    *vt = gwarp_sum(r->wsum[lane]);
-    *ct = gwarp_sum_i(r->wcnt[lane]);
-    int total;
-    const int ex = gwarp_scan_excl(r->wlist[lane], &total);
-    *lt = total;
-    return __shfl_sync(0xffffffffu, ex, wid);
+    if (wid == 0) {
+        const double x = warp_sum(r->wsum[lane]);
+        const int c = gwarp_sum_i(r->wcnt[lane]);
+        int total;
+        r->base[lane] = gwarp_scan_excl(r->wlist[lane], &total);
+        if (lane == 0) {
+            r->tsum = x;
+            r->tcnt = c;
+            r->tlist = total;
+        }
+    }
+    __syncthreads();
+    *vt = r->tsum;
+    *ct = r->tcnt;
+    *lt = r->tlist;
+    return r->base[wid];
 }
 
 // Passive set of Alg. 2 (strict: y_i > 0 or g_i < 0), ḡ = g on P, ‖ḡ‖²,
@@ -264,7 +281,7 @@ __device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, 
 // product needs).
 template <typename T>
 __device__ __forceinline__ void gmask(int n, const T* sy, const T* sg, T* sgb, int* list,
-                                      GRed<T>* r, T* gam, int* cntP, int* cntL) {
+                                      GRed<T>* r, double* gam, int* cntP, int* cntL) {
     const int lane = threadIdx.x & 31;
     int c0, c1;
     warp_chunks(n, c0, c1);
@@ -306,7 +323,7 @@ __device__ __forceinline__ int glist(int n, const T* v, int* list, GRed<T>* r) {
         const int i = c * 32 + lane;
         cl += __popc(__ballot_sync(0xffffffffu, i < n && v[i] != T(0)));
     }
-    T vt;
+    double vt;
     int ct, lt;
     int base = block_totals(r, T(0), 0, cl, &vt, &ct, &lt);
     for (int c = c0; c < c1; ++c) {
@@ -439,13 +456,13 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
 
     GStat st = a.stat[p];
     const double sf = a.tgt[p] * (a.den[p] > 0.0 ? a.den[p] : 1.0);
-    const T eps = (T)(sf * sf);
+    const double eps = sf * sf;
     const int max_iter = a.max_iter, window = a.window;
     int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
-    T best = T(1.0 / 0.0);
+    double best = 1.0 / 0.0;
     int64_t sum_passive = 0, sum_clip = 0;
     int clip_iters = 0;
-    T gam;
+    double gam;
     int cntP, cntL;
     gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
     for (;;) {
@@ -453,7 +470,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
             int stop = 1;
             if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
             else if (cntP == 0) status = ALN_RHS_EMPTY_PASSIVE;
-            else if (gam < eps || gam == T(0)) status = ALN_RHS_CONVERGED;
+            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
             else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
             else stop = 0;
@@ -469,7 +486,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
         gmv(Qp, ldq, n, lp, cntL, sgb, sw, false, red);
         T kp = T(0);
         for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fma(sgb[i], sw[i], kp);
-        T kap;
+        double kap;
         int unused_c, unused_l;
         (void)block_totals(&rs, kp, 0, 0, &kap, &unused_c, &unused_l);
         if (threadIdx.x == 0) {
@@ -477,11 +494,11 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
             if (!isfinite(kap)) {
                 status = ALN_RHS_NONFINITE;
                 stop = 1;
-            } else if (kap <= T(0)) {
+            } else if (kap <= 0.0) {
                 status = ALN_RHS_CURVATURE;
                 stop = 1;
             }
-            s_alpha = stop ? T(0) : gam / kap;
+            s_alpha = stop ? T(0) : (T)(gam / kap);
             s_flag = stop;
         }
         __syncthreads();
@@ -521,7 +538,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
                 }
                 cl += __popc(__ballot_sync(0xffffffffu, ei != T(0)));
             }
-            T vt;
+            double vt;
             int ct;
             int base = block_totals(&rs, T(0), 0, cl, &vt, &ct, &nclip);
             for (int c = c0; c < c1; ++c) {
@@ -550,7 +567,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
         st.npassive = cntP;
         st.sum_passive += sum_passive;
         st.sum_clip += sum_clip;
-        st.gbar2 = (double)gam;
+        st.gbar2 = gam;
         a.stat[p] = st;
     }
     __syncthreads();

@@ -556,11 +556,31 @@ __device__ __forceinline__ T block_sum_t(T v, T* sc) {
     return sc[32];
 }
 
+// The same tree with the 32 warp partials added in FP64 by warp 0: the
+// scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ, α = γ/κ) need more than FP32 —
+// with FP32 scalars the FP32 iteration drifted from the true gradient by
+// about 10⁻⁴ (relative) and needed several times more iterations.
+template <typename T>
+__device__ __forceinline__ double block_sum_td(T v, double* sc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_t(v);
+    __syncthreads();
+    if (lane == 0) sc[wid] = (double)v;
+    __syncthreads();
+    if (wid == 0) {
+        double x = lane < (int)(blockDim.x >> 5) ? sc[lane] : 0.0;
+        x = warp_sum(x);
+        if (lane == 0) sc[32] = x;
+    }
+    __syncthreads();
+    return sc[32];
+}
+
 // Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
 // (fixed reduction tree, identical in every block).
 template <typename T>
-__device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, T* st,
-                                         int* si, T* g2_out, int* cnt_out) {
+__device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, double* st,
+                                         int* si, double* g2_out, int* cnt_out) {
     T v = T(0);
     int c = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -571,7 +591,7 @@ __device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb
         v = fma(gb, gb, v);
         c += P ? 1 : 0;
     }
-    *g2_out = block_sum_t<T>(v, st);
+    *g2_out = block_sum_td<T>(v, st);
     *cnt_out = block_sum_bcast_i(c, si);
     __syncthreads();
 }
@@ -666,7 +686,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     T* red = sw + a.ldq;     // kPWarps × TILE
     __shared__ double sd[32];
     __shared__ int si[32];
-    __shared__ T s_t[33];
+    __shared__ double s_t[33];
     __shared__ T s_alpha;
     __shared__ int s_flag;   // 0 continue, 1 stop
     __shared__ int s_clip[kLocalClip];
@@ -681,16 +701,16 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         sw[j] = T(0);
     }
     __syncthreads();
-    T gam;  // scalars in the iteration type: no FP64 chain on the critical path
+    double gam;  // step scalars in FP64, accumulated from FP32 partials
     int cnt;
     mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
 
     // Scalar control state lives in thread 0 (FP64 compares and the division
     // are issued once, not by every thread).
     IterState* st = a.st;
-    const T eps = (T)st->eps;
+    const double eps = st->eps;
     const int max_iter = st->max_iter, window = st->window;
-    T best = T(1.0 / 0.0);
+    double best = 1.0 / 0.0;
     int best_iter = 0, iter = 0, status = ALN_RHS_MAXITER;
     long long sum_passive = 0, sum_clip = 0;
     uint64_t prof[5] = {0, 0, 0, 0, 0};  // block 0's phase times (ns)
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             int stop = 1;
             if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
             else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
-            else if (gam < eps || gam == T(0)) status = ALN_RHS_CONVERGED;
+            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
             else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
             else stop = 0;
@@ -717,7 +737,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         if (s_flag) break;
         const int par = iter & 1;
         T* part = a.part + (int64_t)par * a.R * a.ldq;
-        T* kitem = reinterpret_cast<T*>(a.kitem) + (int64_t)par * items;
+        double* kitem = a.kitem + (int64_t)par * items;
         uint64_t t_prev = timer ? p_globaltimer() : 0;
         auto lap = [&](int k) {
             if (timer) {
@@ -733,7 +753,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             const T pw = mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red);
             const int64_t i = (int64_t)ct * TILE + threadIdx.x;
             const T prod = (threadIdx.x < TILE && i < n) ? sgb[i] * pw : T(0);
-            const T k = block_sum_t<T>(prod, s_t);
+            const double k = block_sum_td<T>(prod, s_t);
             if (threadIdx.x == 0) __stcg(kitem + it, k);
         }
         lap(0);
@@ -742,19 +762,19 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
 
         // every block: κ, w, α, projected update, gradient update
         if (threadIdx.x < 32) {
-            T k2 = T(0);
+            double k2 = 0.0;
             for (int i = threadIdx.x; i < items; i += 32) k2 += __ldcg(kitem + i);
-            k2 = warp_sum_t(k2);
+            k2 = warp_sum(k2);
             if (threadIdx.x == 0) {
                 int stop = 0;
                 if (!isfinite(k2)) {
                     status = ALN_RHS_NONFINITE;
                     stop = 1;
-                } else if (k2 <= T(0)) {
+                } else if (k2 <= 0.0) {
                     status = ALN_RHS_CURVATURE;
                     stop = 1;
                 }
-                s_alpha = stop ? T(0) : gam / k2;
+                s_alpha = stop ? T(0) : (T)(gam / k2);
                 s_flag = stop;
             }
         }
@@ -817,9 +837,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             st->iter = iter;
             st->done = 1;
             st->status = ok ? status : kStatusTimeout;
-            st->gbar2 = (double)gam;
+            st->gbar2 = gam;
             st->npassive = cnt;
-            st->best_g2 = (double)best;
+            st->best_g2 = best;
             st->best_iter = best_iter;
             st->sum_passive = sum_passive;
             st->sum_clip = sum_clip;

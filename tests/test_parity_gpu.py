@@ -70,7 +70,7 @@ def test_split_bf16_gram_matches_oracle(aln, d, n):
     np.testing.assert_allclose(q[0], qo, atol=1e-12 * np.abs(qo).max())
     err = np.abs(Q - Qo)
     assert err.max() <= _split_bound(d), err.max()
-    assert err.mean() <= 1e-6
+    assert err.mean() <= 5e-6
     np.testing.assert_array_equal(Q, Q.T)
     np.testing.assert_array_equal(np.diag(Q), 1.0)
 
