@@ -146,14 +146,17 @@ aln_status alloc_workspace(aln_ctx* c) {
     CG = std::min(CG, 64);
     c->CG = CG;
     const int64_t ng = n;  // one ḡ² partial per column
-    size_t kb = 2 * (size_t)ldq * 8 + (size_t)d * 8 + (size_t)CG * d * 8 + (512 + ng) * 8 + 64;
+    // rpart also holds the FP32 pairs of x and r (2·ldq + 2·d floats)
+    const size_t pairs = round_up((int64_t)(2 * ldq + 2 * d) * 4, 256) + 256;
+    size_t kb = 2 * (size_t)ldq * 8 + (size_t)d * 8 + (size_t)CG * d * 8 + pairs + (512 + ng) * 8 +
+                64;
     kb = round_up(kb, 256) + 2048;
     ALN_CHECK(ensure(&c->kkt_pool, &c->kkt_bytes, kb));
     p = (uint8_t*)c->kkt_pool;
     c->x64 = (double*)take((size_t)ldq * 8);
     c->g64 = (double*)take((size_t)ldq * 8);
     c->r64 = (double*)take((size_t)d * 8);
-    c->rpart = (double*)take((size_t)CG * d * 8);
+    c->rpart = (double*)take((size_t)CG * d * 8 + pairs);
     c->kkt_part = (double*)take((512 + ng) * 8);
     c->kkt_out = (double*)take(64);
     ALN_TRY(cudaMemsetAsync(c->kkt_pool, 0, c->kkt_bytes, c->stream));

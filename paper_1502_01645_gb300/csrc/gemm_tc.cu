@@ -12,19 +12,10 @@
 // factors 1/s_i, 1/s_j (rounded to FP32), sets Q_ii to 1 (0 for a zero
 // column, Eq. Rescaling) and writes each lower-triangle tile and its mirror.
 //
-// Kernel structure (one 128×128 output tile per CTA, 128 threads):
-//   warp 0, one lane: TMA producer — K-major 128×64 BF16 boxes of h/m/l for
-//                     the row tile and the column tile, 128-byte swizzle, into
-//                     a 2-stage shared-memory ring (96 KiB per stage) guarded
-//                     by mbarriers;
-//   warp 1, one lane: MMA issuer — 6 products × 4 K-steps of
-//                     tcgen05.mma.cta_group::1.kind::f16 (M=128, N=128, K=16)
-//                     per stage, then tcgen05.commit to free the stage;
-//   all 4 warps:      epilogue — tcgen05.ld 32 lanes × 16 columns at a time,
-//                     scale, store the tile and its transpose.
-// Every wait is bounded (1 s on %globaltimer); on expiry the CTA sets
-// *timeout_flag, waits (bounded) for its own copies and MMAs, frees its tensor
-// memory and exits without storing.
+// Kernel structure: one 128×128 output tile per CTA (see gram3_tile below for
+// the loader, MMA and promotion roles).  Every wait is bounded (1 s on
+// %globaltimer); on expiry the CTA sets *timeout_flag, waits (bounded) for its
+// own copies and MMAs, frees its tensor memory and exits without storing.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -52,46 +43,97 @@ __device__ __forceinline__ void tri_decode(int64_t t, int& I, int& J) {
     J = (int)(t - r * (r + 1) / 2);
 }
 
-// Epilogue of one Gram output tile of an n×n matrix Q (row length ldq), rows
-// m0.., columns n0..: accumulator rows from tensor memory (warp w holds rows
-// 32w..32w+31), scaled by inv_s_i·inv_s_j (s_cs holds the column factors in
-// FP32), stored with their mirror.  Diagonal tiles keep the lower triangle and
-// mirror it, so Q is exactly symmetric, and set Q_ii = 1 (0 for a zero
-// column, Eq. Rescaling).
-__device__ __forceinline__ void gram_tile_store(uint32_t tmem, int warp, int lane, int64_t m0,
-                                                int64_t n0, bool diag, int64_t n,
-                                                const double* __restrict__ inv_s,
-                                                const float* s_cs, float* __restrict__ Q,
-                                                int64_t ldq) {
-    const int64_t row = m0 + warp * 32 + lane;
-    const bool rv = row < n;
-    const float rs = rv ? (float)inv_s[row] : 0.0f;
-    const int cols = (int)(n - n0 < (int64_t)BM ? n - n0 : (int64_t)BM);
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < cols; c0 += 16) {
+// ---------------------------------------------------------------------------
+// Three-term split Gram with promoted accumulation.
+//
+// The tensor core adds each MMA's products into its FP32 accumulator with
+// truncation: measured on this GPU, the Gram of FP32 data carries a negative
+// bias growing linearly with the number of accumulation steps (about
+// −4.7·10⁻⁹·d relative), so a Gram over d = 20000 rows is off by ~10⁻⁴ in every
+// entry — a near rank-one perturbation of norm ~n·10⁻⁴, larger than λ_min(Q).
+// Here every 64-wide K block is summed into a fresh TMEM accumulator (the
+// five small cross terms first, then the four h·h steps, so only four large
+// truncating steps per block) and four promotion warps add it into FP32
+// registers with round-to-nearest while the MMA thread fills the other of two
+// TMEM accumulators.
+//
+// Roles (192 threads): warp 0, one lane: loads (TMA tiles or bulk copies of
+// pre-swizzled tiles) into a 2-stage ring of 6 boxes (A: h, m, l; B: h, m, l);
+// warp 1, one lane: the MMAs; warps 2–5: promotion, then scale and store (warp
+// w owns TMEM lanes and tile rows 32·(w mod 4) … +31).  Every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int G3_STAGES = 2;
+constexpr int G3_STAGE_BYTES = 6 * TILE_BYTES;
+constexpr int G3_SMEM_BYTES = G3_STAGES * G3_STAGE_BYTES + 1024 + 256;
+constexpr int G3_THREADS = 192;
+constexpr uint32_t G3_TMEM_COLS = 2 * BM;  // two 128-column accumulators
+
+// One K block of the six split products into a fresh accumulator.
+// a/b: shared addresses of the h boxes (m, l follow at TILE_BYTES, 2·TILE_BYTES).
+__device__ __forceinline__ void gram3_chunk(uint32_t tmem, uint32_t a, uint32_t b) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;  // 16 BF16 along K
+        const uint64_t ah = sdesc_sw128(a + off), am = sdesc_sw128(a + TILE_BYTES + off),
+                       al = sdesc_sw128(a + 2 * TILE_BYTES + off);
+        const uint64_t bh = sdesc_sw128(b + off), bm = sdesc_sw128(b + TILE_BYTES + off),
+                       bl = sdesc_sw128(b + 2 * TILE_BYTES + off);
+        umma_bf16(tmem, ah, bm, idesc, kk == 0 ? 0u : 1u);
+        umma_bf16(tmem, am, bh, idesc, 1u);
+        umma_bf16(tmem, am, bm, idesc, 1u);
+        umma_bf16(tmem, ah, bl, idesc, 1u);
+        umma_bf16(tmem, al, bh, idesc, 1u);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        umma_bf16(tmem, sdesc_sw128(a + off), sdesc_sw128(b + off), idesc, 1u);
+    }
+}
+
+// acc[c] += the accumulator row this thread's lane reads (128 columns).
+__device__ __forceinline__ void gram3_promote(float (&acc)[BM], uint32_t tb) {
+#pragma unroll
+    for (int c0 = 0; c0 < BM; c0 += 16) {
         float v[16];
-        tmem_ld16(tbase + c0, v);
+        tmem_ld16(tb + c0, v);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) acc[c0 + t] += v[t];
+    }
+}
+
+// Scale and store one promoted tile row: Q_ij = H_ij·(1/s_i)·(1/s_j) (FP32
+// factors), Q_ii = 1 (0 for a zero column, Eq. Rescaling); diagonal tiles keep
+// the lower triangle and mirror it, so Q is exactly symmetric.
+__device__ __forceinline__ void gram3_store(const float (&acc)[BM], int64_t row, int64_t n0,
+                                            bool diag, int64_t n, const double* __restrict__ inv_s,
+                                            const float* s_cs, float* __restrict__ Q,
+                                            int64_t ldq) {
+    const bool rv = row < n;
+    if (!rv) return;
+    const float rs = (float)inv_s[row];
+    const int cols = (int)(n - n0 < (int64_t)BM ? n - n0 : (int64_t)BM);
+#pragma unroll
+    for (int c0 = 0; c0 < BM; c0 += 16) {
+        if (c0 >= cols) continue;
         float o[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-            o[t] = v[t] * rs * s_cs[c0 + t];
-            if (diag && row == n0 + c0 + t) o[t] = v[t] != 0.0f ? 1.0f : 0.0f;
+            o[t] = acc[c0 + t] * rs * s_cs[c0 + t];
+            if (diag && row == n0 + c0 + t) o[t] = acc[c0 + t] != 0.0f ? 1.0f : 0.0f;
         }
         const int64_t j0 = n0 + c0;
         if (diag) {
-            // Diagonal tile: keep the lower triangle and mirror it, so Q is
-            // exactly symmetric (the two halves round differently).
-            if (rv) {
 #pragma unroll
-                for (int t = 0; t < 16; ++t) {
-                    const int64_t j = j0 + t;
-                    if (c0 + t < cols && j <= row) {
-                        Q[row * ldq + j] = o[t];
-                        Q[j * ldq + row] = o[t];
-                    }
+            for (int t = 0; t < 16; ++t) {
+                const int64_t j = j0 + t;
+                if (c0 + t < cols && j <= row) {
+                    Q[row * ldq + j] = o[t];
+                    Q[j * ldq + row] = o[t];
                 }
             }
-        } else if (rv) {
+        } else {
             float* dst = Q + row * ldq + j0;
             if (c0 + 16 <= cols) {
 #pragma unroll
@@ -108,73 +150,56 @@ __device__ __forceinline__ void gram_tile_store(uint32_t tmem, int warp, int lan
     }
 }
 
-// Three-term split Gram: 2 stages of 6 boxes (A: h, m, l; B: h, m, l).
-constexpr int G3_STAGES = 2;
-constexpr int G3_STAGE_BYTES = 6 * TILE_BYTES;
-constexpr int G3_SMEM_BYTES = G3_STAGES * G3_STAGE_BYTES + 1024 + 256;
-
-// The six products of one 16-wide K step into the TMEM accumulator; `first`
-// starts the accumulation.  a/b: shared addresses of the h boxes (m and l
-// follow at TILE_BYTES and 2·TILE_BYTES).
-__device__ __forceinline__ void gram3_kstep(uint32_t tmem, uint32_t a, uint32_t b, uint32_t off,
-                                            bool first) {
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
-    const uint64_t ah = sdesc_sw128(a + off), am = sdesc_sw128(a + TILE_BYTES + off),
-                   al = sdesc_sw128(a + 2 * TILE_BYTES + off);
-    const uint64_t bh = sdesc_sw128(b + off), bm = sdesc_sw128(b + TILE_BYTES + off),
-                   bl = sdesc_sw128(b + 2 * TILE_BYTES + off);
-    umma_bf16(tmem, ah, bh, idesc, first ? 0u : 1u);
-    umma_bf16(tmem, ah, bm, idesc, 1u);
-    umma_bf16(tmem, am, bh, idesc, 1u);
-    umma_bf16(tmem, am, bm, idesc, 1u);
-    umma_bf16(tmem, ah, bl, idesc, 1u);
-    umma_bf16(tmem, al, bh, idesc, 1u);
-}
-
-__global__ void __launch_bounds__(128, 1)
-    k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
-              const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
+// One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
+template <class Loader>
+__device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool diag, int64_t m0,
+                                           int64_t n0, int64_t n, const double* __restrict__ inv_s,
+                                           float* __restrict__ Q, int64_t ldq,
+                                           int* timeout_flag) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + G3_STAGES * G3_STAGE_BYTES);
     uint64_t* empty = full + G3_STAGES;
-    uint64_t* done = empty + G3_STAGES;
+    uint64_t* tfull = empty + G3_STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ float s_cs[BM];
     __shared__ int s_abort;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int tm, tn;
-    tri_decode(blockIdx.x, tm, tn);
-    const int64_t m0 = (int64_t)tm * BM, n0 = (int64_t)tn * BM;
-    const bool diag = tm == tn;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G3_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);  // one arrival per promotion warp
+        }
         mbar_init(done, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    {
+    if (threadIdx.x < BM) {
         const int64_t j = n0 + threadIdx.x;
-        s_cs[threadIdx.x] = j < p.n ? (float)p.inv_s[j] : 0.0f;
+        s_cs[threadIdx.x] = j < n ? (float)inv_s[j] : 0.0f;
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_alloc(tmem_slot, G3_TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    float acc[BM];
+#pragma unroll
+    for (int c = 0; c < BM; ++c) acc[c] = 0.0f;
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
         int issued = 0;
-        for (int kb = 0; kb < p.num_kb; ++kb) {
+        for (int kb = 0; kb < num_kb; ++kb) {
             const int s = kb % G3_STAGES;
             if (kb >= G3_STAGES && !mbar_wait(&empty[s], ((kb / G3_STAGES) & 1) ^ 1)) {
                 s_abort = 1;
@@ -183,63 +208,97 @@ __global__ void __launch_bounds__(128, 1)
             if (*(volatile int*)&s_abort) break;
             uint8_t* sb = smem + s * G3_STAGE_BYTES;
             mbar_expect_tx(&full[s], (diag ? 3 : 6) * TILE_BYTES);
-            tma_load_2d(sb, &m_hi, &full[s], kb * BK, (int)m0);
-            tma_load_2d(sb + TILE_BYTES, &m_mid, &full[s], kb * BK, (int)m0);
-            tma_load_2d(sb + 2 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)m0);
-            if (!diag) {
-                tma_load_2d(sb + 3 * TILE_BYTES, &m_hi, &full[s], kb * BK, (int)n0);
-                tma_load_2d(sb + 4 * TILE_BYTES, &m_mid, &full[s], kb * BK, (int)n0);
-                tma_load_2d(sb + 5 * TILE_BYTES, &m_lo, &full[s], kb * BK, (int)n0);
-            }
+            ld.load(sb, kb, diag, &full[s]);
             ++issued;
         }
-        // Our own copies in flight: the last ≤ G3_STAGES loads (bounded wait).
+        // our own copies in flight: the last ≤ G3_STAGES loads (bounded wait)
         for (int kb = max(0, issued - G3_STAGES); kb < issued; ++kb)
             if (!mbar_wait(&full[kb % G3_STAGES], (kb / G3_STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        for (int kb = 0; kb < p.num_kb; ++kb) {
-            const int s = kb % G3_STAGES;
-            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1)) {
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int s = kb % G3_STAGES, b = kb & 1;
+            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1) ||
+                (kb >= 2 && !mbar_wait(&tempty[b], ((kb >> 1) & 1) ^ 1))) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a = smem_u32(smem + s * G3_STAGE_BYTES);
-            const uint32_t b = diag ? a : a + 3 * TILE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                gram3_kstep(tmem, a, b, kk * 32, (kb | kk) == 0);  // 16 BF16 along K
+            const uint32_t a0 = smem_u32(smem + s * G3_STAGE_BYTES);
+            const uint32_t b0 = diag ? a0 : a0 + 3 * TILE_BYTES;
+            gram3_chunk(tmem + (uint32_t)(b * BM), a0, b0);
             umma_commit(&empty[s]);
+            umma_commit(&tfull[b]);
         }
-        // Always commit: `done` then also covers MMAs issued before an abort.
+        // always commit: `done` then also covers MMAs issued before an abort
         umma_commit(done);
+    } else if (warp >= 2) {
+        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        for (int kb = 0; kb < num_kb; ++kb) {
+            const int b = kb & 1;
+            if (!mbar_wait(&tfull[b], (kb >> 1) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            gram3_promote(acc, tb + (uint32_t)(b * BM));
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (*(volatile int*)&s_abort) break;
+        }
     }
     __syncwarp();
-
-    // ---------------- epilogue (all 4 warps) ----------------
-    const bool ok = mbar_wait(done, 0);
+    if (warp == 1) {
+        const bool ok = mbar_wait(done, 0);  // no MMA in flight past this point
+        if (!ok) s_abort = 1;
+    }
     tc_fence_after();
-    if (!ok) s_abort = 1;
     __syncthreads();
     if (!s_abort) {
-        gram_tile_store(tmem, warp, lane, m0, n0, diag, p.n, p.inv_s, s_cs, p.Q, p.ldq);
+        if (warp >= 2)
+            gram3_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
     } else if (threadIdx.x == 0) {
-        atomicExch(p.timeout_flag, 1);
+        atomicExch(timeout_flag, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
+}
+
+struct TmaLoader {
+    const CUtensorMap* mh;
+    const CUtensorMap* mm;
+    const CUtensorMap* ml;
+    int m0, n0;
+    __device__ __forceinline__ void load(uint8_t* sb, int kb, bool diag, uint64_t* bar) const {
+        tma_load_2d(sb, mh, bar, kb * BK, m0);
+        tma_load_2d(sb + TILE_BYTES, mm, bar, kb * BK, m0);
+        tma_load_2d(sb + 2 * TILE_BYTES, ml, bar, kb * BK, m0);
+        if (!diag) {
+            tma_load_2d(sb + 3 * TILE_BYTES, mh, bar, kb * BK, n0);
+            tma_load_2d(sb + 4 * TILE_BYTES, mm, bar, kb * BK, n0);
+            tma_load_2d(sb + 5 * TILE_BYTES, ml, bar, kb * BK, n0);
+        }
+    }
+};
+
+__global__ void __launch_bounds__(G3_THREADS, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
+              const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
+    int tm, tn;
+    tri_decode(blockIdx.x, tm, tn);
+    const TmaLoader ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM};
+    gram3_tile(ld, p.num_kb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
+               p.ldq, p.timeout_flag);
 }
 
 // ---------------------------------------------------------------------------
 // Grouped Gram: the lower-triangle tiles of many problems' Q_p in one launch.
 // The operands come pre-tiled (pack_index): every 128×64 BF16 box is 16 KiB
 // contiguous in global memory, already in the 128-byte-swizzled order, so the
-// producer moves it with a 1-D bulk copy (cp.async.bulk) — no tensor map per
+// loader moves it with a 1-D bulk copy (cp.async.bulk) — no tensor map per
 // problem.  The tile table is sorted by K length (longest first) on the host.
-// Pipeline, MMA and epilogue are those of k_gram_tc.
 // ---------------------------------------------------------------------------
 struct GGramArgs {
     const GProb* gp;
@@ -263,103 +322,31 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) k_ggram_tc(GGramArgs a) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + G3_STAGES * G3_STAGE_BYTES);
-    uint64_t* empty = full + G3_STAGES;
-    uint64_t* done = empty + G3_STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(done + 1);
-    __shared__ float s_cs[BM];
-    __shared__ int s_abort;
+struct BulkLoader {
+    const __nv_bfloat16* hi;
+    const __nv_bfloat16* mid;
+    const __nv_bfloat16* lo;
+    int64_t ta, tb;  // first element of the row tile / column tile (kb = 0)
+    __device__ __forceinline__ void load(uint8_t* sb, int kb, bool diag, uint64_t* bar) const {
+        const int64_t off = (int64_t)kb * kPackTile;
+        bulk_load(sb, hi + ta + off, TILE_BYTES, bar);
+        bulk_load(sb + TILE_BYTES, mid + ta + off, TILE_BYTES, bar);
+        bulk_load(sb + 2 * TILE_BYTES, lo + ta + off, TILE_BYTES, bar);
+        if (!diag) {
+            bulk_load(sb + 3 * TILE_BYTES, hi + tb + off, TILE_BYTES, bar);
+            bulk_load(sb + 4 * TILE_BYTES, mid + tb + off, TILE_BYTES, bar);
+            bulk_load(sb + 5 * TILE_BYTES, lo + tb + off, TILE_BYTES, bar);
+        }
+    }
+};
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(G3_THREADS, 1) k_ggram_tc(GGramArgs a) {
     const GTile tl = a.tiles[blockIdx.x];
     const GProb P = a.gp[tl.p];
-    const int64_t m0 = (int64_t)tl.tm * BM, n0 = (int64_t)tl.tn * BM;
-    const bool diag = tl.tm == tl.tn;
-    const double* inv_s = a.inv_s + P.voff;
-    const int num_kb = P.KB;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < G3_STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-        }
-        mbar_init(done, 1);
-        s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    {
-        const int64_t j = n0 + threadIdx.x;
-        s_cs[threadIdx.x] = j < P.n ? (float)inv_s[j] : 0.0f;
-    }
-    if (warp == 1) {
-        tmem_alloc(tmem_slot, TMEM_COLS);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    if (warp == 0 && lane == 0) {
-        const int64_t ta = (P.pack + (int64_t)tl.tm * P.KB) * kPackTile;
-        const int64_t tb = (P.pack + (int64_t)tl.tn * P.KB) * kPackTile;
-        int issued = 0;
-        for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % G3_STAGES;
-            if (kb >= G3_STAGES && !mbar_wait(&empty[s], ((kb / G3_STAGES) & 1) ^ 1)) {
-                s_abort = 1;
-                break;
-            }
-            if (*(volatile int*)&s_abort) break;
-            uint8_t* sb = smem + s * G3_STAGE_BYTES;
-            const int64_t off = (int64_t)kb * kPackTile;
-            mbar_expect_tx(&full[s], (diag ? 3 : 6) * TILE_BYTES);
-            bulk_load(sb, a.hi + ta + off, TILE_BYTES, &full[s]);
-            bulk_load(sb + TILE_BYTES, a.mid + ta + off, TILE_BYTES, &full[s]);
-            bulk_load(sb + 2 * TILE_BYTES, a.lo + ta + off, TILE_BYTES, &full[s]);
-            if (!diag) {
-                bulk_load(sb + 3 * TILE_BYTES, a.hi + tb + off, TILE_BYTES, &full[s]);
-                bulk_load(sb + 4 * TILE_BYTES, a.mid + tb + off, TILE_BYTES, &full[s]);
-                bulk_load(sb + 5 * TILE_BYTES, a.lo + tb + off, TILE_BYTES, &full[s]);
-            }
-            ++issued;
-        }
-        for (int kb = max(0, issued - G3_STAGES); kb < issued; ++kb)
-            if (!mbar_wait(&full[kb % G3_STAGES], (kb / G3_STAGES) & 1)) s_abort = 1;
-    } else if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % G3_STAGES;
-            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1)) {
-                s_abort = 1;
-                break;
-            }
-            if (*(volatile int*)&s_abort) break;
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(smem + s * G3_STAGE_BYTES);
-            const uint32_t b0 = diag ? a0 : a0 + 3 * TILE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) gram3_kstep(tmem, a0, b0, kk * 32, (kb | kk) == 0);
-            umma_commit(&empty[s]);
-        }
-        umma_commit(done);
-    }
-    __syncwarp();
-
-    const bool ok = mbar_wait(done, 0);
-    tc_fence_after();
-    if (!ok) s_abort = 1;
-    __syncthreads();
-    if (!s_abort) {
-        gram_tile_store(tmem, warp, lane, m0, n0, diag, P.n, inv_s, s_cs, a.Q + P.qoff, P.ldq);
-    } else if (threadIdx.x == 0) {
-        atomicExch(a.timeout_flag, 1);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+    const BulkLoader ld{a.hi, a.mid, a.lo, (P.pack + (int64_t)tl.tm * P.KB) * kPackTile,
+                        (P.pack + (int64_t)tl.tn * P.KB) * kPackTile};
+    gram3_tile(ld, P.KB, tl.tm == tl.tn, (int64_t)tl.tm * BM, (int64_t)tl.tn * BM, P.n,
+               a.inv_s + P.voff, a.Q + P.qoff, P.ldq, a.timeout_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,7 +552,8 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
-    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), 128, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml,
+                                                                                     a);
     return cudaGetLastError();
 }
 
@@ -594,7 +582,7 @@ cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
     a.inv_s = inv_s;
     a.Q = Q;
     a.timeout_flag = timeout_flag;
-    k_ggram_tc<<<(unsigned)ntiles, 128, G3_SMEM_BYTES, st>>>(a);
+    k_ggram_tc<<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 

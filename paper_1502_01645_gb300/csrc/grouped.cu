@@ -687,6 +687,85 @@ __global__ void __launch_bounds__(256) k_gkkt_g(const GProb* __restrict__ gp, in
     }
 }
 
+// FP32 inputs: the same two passes on the FP32 pipe with FP64-level accuracy
+// (Dot2: x and r as FP32 pairs hi + lo, exact products by FMA, TwoSum), since
+// FP64 FMAs on this GPU made them compute-bound.
+__global__ void k_gsplit(const double* __restrict__ v, int64_t m, float* __restrict__ hi,
+                         float* __restrict__ lo) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)v[i];
+        hi[i] = h;
+        lo[i] = (float)(v[i] - (double)h);
+    }
+}
+
+struct GPair {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float h, float l) {  // += a·(h + l)
+        const float p = mul_rn(a, h);
+        const float ep = fmaf(a, h, -p);
+        const float t = s + p;
+        const float z = t - s;
+        c += ((s - (t - z)) + (p - z)) + fmaf(a, l, ep);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__global__ void __launch_bounds__(256) k_gkkt_r32(const GProb* __restrict__ gp, int count,
+                                                  int64_t total, const float* __restrict__ xh,
+                                                  const float* __restrict__ xl,
+                                                  const int* __restrict__ fin,
+                                                  double* __restrict__ r) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int p = find_prob<kKeyR>(gp, count, e);
+        if (fin[p] >= 0) continue;
+        const GProb& P = gp[p];
+        const int i = (int)(e - P.roff);
+        const float* A = (const float*)P.A;
+        const float* h = xh + P.voff;
+        const float* l = xl + P.voff;
+        GPair acc;
+        for (int j = 0; j < P.n; ++j) {
+            const float hj = h[j], lj = l[j];
+            if (hj != 0.0f || lj != 0.0f) acc.add(A[(int64_t)j * P.lda + i], hj, lj);
+        }
+        r[e] = acc.value() - (double)((const float*)P.b)[i];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_gkkt_g32(const GProb* __restrict__ gp, int count,
+                                                  int64_t total, const double* __restrict__ x,
+                                                  const double* __restrict__ s,
+                                                  const float* __restrict__ rh,
+                                                  const float* __restrict__ rl,
+                                                  const int* __restrict__ fin,
+                                                  double* __restrict__ g64,
+                                                  double* __restrict__ gpart) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total;
+         e += warps) {
+        const int p = find_prob<kKeyV>(gp, count, e);
+        if (fin[p] >= 0) continue;
+        const GProb& P = gp[p];
+        const int j = (int)(e - P.voff);
+        const float* col = (const float*)P.A + (int64_t)j * P.lda;
+        GPair acc;
+        for (int i = lane; i < P.d; i += 32) acc.add(col[i], rh[P.roff + i], rl[P.roff + i]);
+        const double v = warp_sum(acc.value());
+        if (lane == 0) {
+            const double gj = v / s[e];
+            const double yj = x[e] * s[e];
+            const bool Pj = yj > 0.0 || gj < 0.0;
+            g64[e] = gj;
+            gpart[e] = Pj ? gj * gj : 0.0;
+        }
+    }
+}
+
 // Per open problem: rel_kkt = ‖ḡ‖/‖min(q,0)‖, F = ½‖r‖², and the decision:
 // converged, terminal, or one more round from the exact gradient.
 __global__ void __launch_bounds__(256) k_gkkt_final(const GProb* __restrict__ gp,
@@ -766,6 +845,7 @@ struct GroupWork {
     double *s = nullptr, *inv_s = nullptr, *q64 = nullptr, *g64 = nullptr, *x64 = nullptr,
            *gpart = nullptr, *r64 = nullptr, *den = nullptr, *bn2 = nullptr, *rel = nullptr,
            *obj = nullptr, *tgt = nullptr;
+    float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr;  // FP32 pairs
     void* y = nullptr;            // packed (foff), iteration type
     void* Q = nullptr;            // pool, iteration type
     __nv_bfloat16 *hi = nullptr, *mid = nullptr, *lo = nullptr;
@@ -862,10 +942,14 @@ aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_
     const unsigned gr = grid_for(g->sum_d, 256, 8 * c->num_sms);
     const unsigned gg = grid_for(g->sum_n * 32, 256, 16 * c->num_sms);
     if (g->dtype == ALN_DTYPE_F32) {
-        k_gkkt_r<float><<<gr, 256, 0, c->stream>>>(g->gp, g->count, g->sum_d, g->x64, g->fin,
-                                                   g->r64);
-        k_gkkt_g<float><<<gg, 256, 0, c->stream>>>(g->gp, g->count, g->sum_n, g->x64, g->s,
-                                                   g->r64, g->fin, g->g64, g->gpart);
+        const unsigned gs = grid_for(std::max(g->sum_n, g->sum_d), 256, 8 * c->num_sms);
+        k_gsplit<<<gs, 256, 0, c->stream>>>(g->x64, g->sum_n, g->xh, g->xl);
+        k_gkkt_r32<<<gr, 256, 0, c->stream>>>(g->gp, g->count, g->sum_d, g->xh, g->xl, g->fin,
+                                              g->r64);
+        k_gsplit<<<gs, 256, 0, c->stream>>>(g->r64, g->sum_d, g->rh, g->rl);
+        k_gkkt_g32<<<gg, 256, 0, c->stream>>>(g->gp, g->count, g->sum_n, g->x64, g->s, g->rh,
+                                              g->rl, g->fin, g->g64, g->gpart);
+        c->launches += 2;
     } else {
         k_gkkt_r<double><<<gr, 256, 0, c->stream>>>(g->gp, g->count, g->sum_d, g->x64, g->fin,
                                                     g->r64);
@@ -1001,6 +1085,7 @@ static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const al
         (size_t)roff * 8,                              // r64
         (size_t)count * 8, (size_t)count * 8, (size_t)count * 8, (size_t)count * 8,  // den bn2 rel obj
         (size_t)count * 8,                             // tgt
+        (size_t)voff * 4, (size_t)voff * 4, (size_t)roff * 4, (size_t)roff * 4,  // pairs
         (size_t)foff * 8,                              // y (FP64)
         (size_t)qoff * T,                              // Q
         pack_elems * 2, pack_elems * 2, pack_elems * 2,  // hi, mid, lo
@@ -1039,6 +1124,10 @@ static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const al
         g->rel = (double*)take();
         g->obj = (double*)take();
         g->tgt = (double*)take();
+        g->xh = (float*)take();
+        g->xl = (float*)take();
+        g->rh = (float*)take();
+        g->rl = (float*)take();
         g->y = take();
         g->Q = take();
         g->hi = (__nv_bfloat16*)take();

@@ -118,6 +118,110 @@ __global__ void __launch_bounds__(kKktThreads) k_kkt_grad(const TA* __restrict__
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 inputs: the same sums on the FP32 pipe with FP64-level accuracy.  x and
+// r are split into FP32 pairs (v = hi + lo); each product a·hi is formed
+// exactly (TwoProduct by FMA) and accumulated with TwoSum, a·lo goes into the
+// compensation term (Dot2, Ogita, Rump & Oishi 2005).  This GPU's FP64 pipe
+// made the plain FP64 version of these two passes compute-bound (≈1.5 ms at
+// 20000×5000); in FP32 pairs they run at the speed of the A reads.
+// ---------------------------------------------------------------------------
+__global__ void k_split_pairs(const double* __restrict__ v, int64_t m, float* __restrict__ hi,
+                              float* __restrict__ lo) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float h = (float)v[i];
+        hi[i] = h;
+        lo[i] = (float)(v[i] - (double)h);
+    }
+}
+
+struct Pair {
+    float s = 0.0f, c = 0.0f;
+    // += a·(h + l)
+    __device__ __forceinline__ void add(float a, float h, float l) {
+        const float p = mul_rn(a, h);
+        const float ep = fmaf(a, h, -p);
+        const float t = s + p;
+        const float z = t - s;
+        c += ((s - (t - z)) + (p - z)) + fmaf(a, l, ep);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <bool VEC>
+__global__ void __launch_bounds__(kKktThreads) k_kkt_ax32(const float* __restrict__ A, int64_t d,
+                                                          int64_t n, int64_t lda,
+                                                          const float* __restrict__ xh,
+                                                          const float* __restrict__ xl,
+                                                          int64_t cols_per_group,
+                                                          double* __restrict__ rpart) {
+    const int64_t t0 = ((int64_t)blockIdx.x * kKktThreads + threadIdx.x) * 4;
+    const int64_t i0 = (int64_t)blockIdx.y * cols_per_group;
+    const int64_t i1 = min(n, i0 + cols_per_group);
+    if (t0 >= d) return;
+    const bool full = VEC && t0 + 4 <= d;
+    Pair acc[4];
+    for (int64_t i = i0; i < i1; ++i) {
+        const float h = xh[i], l = xl[i];
+        if (h == 0.0f && l == 0.0f) continue;  // only the support of x is read
+        const float* p = A + i * lda + t0;
+        float a[4];
+        if (full) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+            a[0] = v.x;
+            a[1] = v.y;
+            a[2] = v.z;
+            a[3] = v.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = t0 + u < d ? p[u] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u].add(a[u], h, l);
+    }
+    double* out = rpart + (int64_t)blockIdx.y * d + t0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+        if (t0 + u < d) out[u] = acc[u].value();
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kKktThreads) k_kkt_grad32(const float* __restrict__ A, int64_t d,
+                                                            int64_t n, int64_t lda,
+                                                            const float* __restrict__ rh,
+                                                            const float* __restrict__ rl,
+                                                            const double* __restrict__ s,
+                                                            const double* __restrict__ x,
+                                                            double* __restrict__ g64,
+                                                            double* __restrict__ gpart) {
+    __shared__ double scratch[32];
+    const int64_t i = blockIdx.x;
+    const float* col = A + i * lda;
+    Pair acc;
+    const int64_t d4 = VEC ? d / 4 : 0;
+#pragma unroll 2
+    for (int64_t q = threadIdx.x; q < d4; q += blockDim.x) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(col + 4 * q));
+        const float4 h = __ldg(reinterpret_cast<const float4*>(rh + 4 * q));
+        const float4 l = __ldg(reinterpret_cast<const float4*>(rl + 4 * q));
+        acc.add(a.x, h.x, l.x);
+        acc.add(a.y, h.y, l.y);
+        acc.add(a.z, h.z, l.z);
+        acc.add(a.w, h.w, l.w);
+    }
+    for (int64_t t = 4 * d4 + threadIdx.x; t < d; t += blockDim.x) acc.add(col[t], rh[t], rl[t]);
+    const double grad = block_sum(acc.value(), scratch);
+    if (threadIdx.x == 0) {
+        const double gi = grad / s[i];
+        const double yi = x[i] * s[i];
+        g64[i] = gi;
+        const bool P = yi > 0.0 || gi < 0.0;
+        gpart[i] = P ? gi * gi : 0.0;
+    }
+}
+
 __global__ void k_kkt_final(const double* __restrict__ gpart, int ng,
                             const double* __restrict__ fpart, int nf, double den,
                             double* __restrict__ out) {
@@ -156,8 +260,31 @@ cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den,
             (const TA*)c->A, d, n, c->lda, c->r64, c->s, x64, c->g64, gpart);                     \
     } while (0)
     if (c->dtype == ALN_DTYPE_F32) {
-        if (vec) ALN_KKT(float, true);
-        else ALN_KKT(float, false);
+        // x and r as FP32 pairs (hi, lo) in the tail of rpart
+        float* xh = reinterpret_cast<float*>(
+            ((uintptr_t)(c->rpart + (int64_t)CG * d) + 255) & ~(uintptr_t)255);
+        float* xl = xh + c->ldq;
+        float* rh = xl + c->ldq;
+        float* rl = rh + d;
+        k_split_pairs<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1024), 256, 0, c->stream>>>(
+            x64, n, xh, xl);
+        const bool vr = vec && (d % 4 == 0);
+        if (vec)
+            k_kkt_ax32<true><<<g1, kKktThreads, 0, c->stream>>>((const float*)c->A, d, n, c->lda, xh,
+                                                                 xl, cpg, c->rpart);
+        else
+            k_kkt_ax32<false><<<g1, kKktThreads, 0, c->stream>>>((const float*)c->A, d, n, c->lda,
+                                                                  xh, xl, cpg, c->rpart);
+        k_kkt_r<float><<<nf, kKktThreads, 0, c->stream>>>(d, c->rpart, CG, (const float*)b, c->r64,
+                                                          fpart);
+        k_split_pairs<<<(unsigned)std::min<int64_t>(ceil_div(d, 256), 1024), 256, 0, c->stream>>>(
+            c->r64, d, rh, rl);
+        if (vr)
+            k_kkt_grad32<true><<<(unsigned)n, kKktThreads, 0, c->stream>>>(
+                (const float*)c->A, d, n, c->lda, rh, rl, c->s, x64, c->g64, gpart);
+        else
+            k_kkt_grad32<false><<<(unsigned)n, kKktThreads, 0, c->stream>>>(
+                (const float*)c->A, d, n, c->lda, rh, rl, c->s, x64, c->g64, gpart);
     } else {
         if (vec) ALN_KKT(double, true);
         else ALN_KKT(double, false);
