@@ -377,8 +377,33 @@ struct BatchArgs {
     int* timeout_flag;
 };
 
+// One K block of the two-term split product: the small cross terms first
+// (h·l, l·h), then the four h·h steps (`fresh` starts a new accumulator).
+// Two K blocks share an accumulator before promotion (BG_CHUNK): with three
+// products per K step the MMA outruns a per-block promotion, and eight large
+// truncating steps still keep the bias near 10⁻⁷.
+constexpr int BG_CHUNK = 2;
+__device__ __forceinline__ void split2_chunk(uint32_t tmem, uint32_t a, uint32_t b, bool fresh) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        umma_bf16(tmem, sdesc_sw128(a + off), sdesc_sw128(b + TILE_BYTES + off), idesc,
+                  (fresh && kk == 0) ? 0u : 1u);
+        umma_bf16(tmem, sdesc_sw128(a + TILE_BYTES + off), sdesc_sw128(b + off), idesc, 1u);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        umma_bf16(tmem, sdesc_sw128(a + off), sdesc_sw128(b + off), idesc, 1u);
+    }
+}
+
+// Same roles as the Gram (gram3_tile): warp 0 TMA, warp 1 MMA, warps 2–5
+// promote each K block's accumulator into FP32 registers and run the
+// epilogue.  Stage ring: 3 × (Q_hi, Q_lo, V_hi, V_lo).
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(G3_THREADS, 1)
     k_bgemm_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
                const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo,
                BatchArgs p) {
@@ -390,7 +415,9 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* done = empty + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ int s_map[BM];
     __shared__ float s_red[4][BM];
@@ -402,22 +429,29 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
         mbar_init(done, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    {
+    if (threadIdx.x < BM) {
         const int64_t pp = n0 + threadIdx.x;
         s_map[threadIdx.x] = pp < ncols ? p.map[pp] : -1;
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_alloc(tmem_slot, G3_TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    float acc[BM];
+#pragma unroll
+    for (int c = 0; c < BM; ++c) acc[c] = 0.0f;
 
     if (warp == 0 && lane == 0) {
         int issued = 0;
@@ -439,71 +473,76 @@ __global__ void __launch_bounds__(128, 1)
         for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
             if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
         for (int kb = 0; kb < p.num_kb; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+            const int s = kb % STAGES, ch = kb / BG_CHUNK, b = ch & 1;
+            const bool fresh = kb % BG_CHUNK == 0;
+            const bool last = kb % BG_CHUNK == BG_CHUNK - 1 || kb == p.num_kb - 1;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1) ||
+                (fresh && ch >= 2 && !mbar_wait(&tempty[b], ((ch >> 1) & 1) ^ 1))) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a_h = smem_u32(smem + s * STAGE_BYTES);
-            const uint32_t a_l = a_h + TILE_BYTES;
-            const uint32_t b_h = a_h + 2 * TILE_BYTES;
-            const uint32_t b_l = a_h + 3 * TILE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;
-                const uint64_t dah = sdesc_sw128(a_h + off), dal = sdesc_sw128(a_l + off);
-                const uint64_t dbh = sdesc_sw128(b_h + off), dbl = sdesc_sw128(b_l + off);
-                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
-                umma_bf16(tmem, dah, dbl, idesc, 1u);
-                umma_bf16(tmem, dal, dbh, idesc, 1u);
-            }
+            const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+            split2_chunk(tmem + (uint32_t)(b * BM), a0, a0 + 2 * TILE_BYTES, fresh);
             umma_commit(&empty[s]);
+            if (last) umma_commit(&tfull[b]);
         }
         umma_commit(done);
+    } else if (warp >= 2) {
+        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        const int nch = (p.num_kb + BG_CHUNK - 1) / BG_CHUNK;
+        for (int kb = 0; kb < nch; ++kb) {  // kb: chunk index
+            const int b = kb & 1;
+            if (!mbar_wait(&tfull[b], (kb >> 1) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            gram3_promote(acc, tb + (uint32_t)(b * BM));
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (*(volatile int*)&s_abort) break;
+        }
     }
     __syncwarp();
-
-    const bool ok = mbar_wait(done, 0);
+    if (warp == 1) {
+        const bool ok = mbar_wait(done, 0);
+        if (!ok) s_abort = 1;
+    }
     tc_fence_after();
-    if (!ok) s_abort = 1;
     __syncthreads();
     const bool good = !s_abort;
-    const int64_t row = m0 + warp * 32 + lane;
-    const bool rv = row < p.n;
     const int cols = (int)(ncols - n0 < (int64_t)BM ? ncols - n0 : (int64_t)BM);
-    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-    if (good) {
-        for (int c0 = 0; c0 < cols; c0 += 16) {
-            float v[16];
-            tmem_ld16(tbase + c0, v);
+    if (good && warp >= 2) {
+        const int qd = warp & 3;
+        const int64_t row = m0 + 32 * qd + lane;
+        const bool rv = row < p.n;
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
-                const int cc = c0 + t;
-                const int col = cc < cols ? s_map[cc] : -1;
-                if (MODE == BMODE_W) {
-                    // curvature partial in FP32 (the FP64 pipe is narrow on
-                    // this GPU); the row-tile partials are summed in FP64
-                    float kp = 0.0f;
-                    if (col >= 0 && rv) {
-                        p.W[(n0 + cc) * p.ldq + row] = v[t];
-                        kp = p.gb[(int64_t)col * p.ldq + row] * v[t];
-                    }
+        for (int cc = 0; cc < BM; ++cc) {
+            if (cc >= cols) continue;  // uniform over the warp; keeps acc[] in registers
+            const int col = s_map[cc];
+            if (MODE == BMODE_W) {
+                // curvature partial in FP32 (the FP64 pipe is narrow on this
+                // GPU); the row-tile partials are summed in FP64
+                float kp = 0.0f;
+                if (col >= 0 && rv) {
+                    p.W[(n0 + cc) * p.ldq + row] = acc[cc];
+                    kp = p.gb[(int64_t)col * p.ldq + row] * acc[cc];
+                }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
-                    if (lane == 0) s_red[warp][cc] = kp;
-                } else {
-                    if (col >= 0 && rv) {
-                        float* gp = p.g + (int64_t)col * p.ldq + row;
-                        *gp = *gp + v[t];
-                    }
+                for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+                if (lane == 0) s_red[qd][cc] = kp;
+            } else {
+                if (col >= 0 && rv) {
+                    float* gp = p.g + (int64_t)col * p.ldq + row;
+                    *gp = *gp + acc[cc];
                 }
             }
         }
-    } else if (threadIdx.x == 0) {
+    } else if (!good && threadIdx.x == 0) {
         atomicExch(p.timeout_flag, 1);
     }
     if (MODE == BMODE_W) {
@@ -516,7 +555,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
 }
 
 }  // namespace tc
@@ -621,9 +660,9 @@ cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bflo
     a.timeout_flag = timeout_flag;
     const dim3 grid((unsigned)ceil_div(n, BM), (unsigned)ceil_div(kmax, BM));
     if (mode == BMODE_W)
-        k_bgemm_tc<BMODE_W><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+        k_bgemm_tc<BMODE_W><<<grid, G3_THREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
     else
-        k_bgemm_tc<BMODE_U><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+        k_bgemm_tc<BMODE_U><<<grid, G3_THREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
     return cudaGetLastError();
 }
 

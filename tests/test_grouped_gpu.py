@@ -91,7 +91,9 @@ def test_grouped_solve_matches_oracle(aln):
         assert rel <= 1e-9, (p, A.shape, rel, info[p])
         assert np.linalg.norm(x - x_star) <= 1e-5 * max(np.linalg.norm(x_star), 1e-300), p
         assert info[p].status in (aln.RHS_CONVERGED, aln.RHS_EMPTY_PASSIVE)
-        np.testing.assert_allclose(info[p].rel_kkt, rel, rtol=1e-6, atol=1e-15)
+        # the GPU's KKT sums run in Dot2 (FP32 pairs, about 48 bits): at rel
+        # ~1e-10 its ḡ carries ~1e-5 relative error against the FP64 oracle
+        np.testing.assert_allclose(info[p].rel_kkt, rel, rtol=1e-4, atol=1e-15)
         relb, Fb = O.kkt_residual(A64, b64, xb)
         assert relb <= 1e-6, (p, relb)
         np.testing.assert_allclose(infob[p].rel_kkt, relb, rtol=1e-6, atol=1e-15)
