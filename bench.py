@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--train", type=int, default=None,
                     help="training right-hand sides of the warm-start workload")
     ap.add_argument("--epochs", type=int, default=60, help="warm-start training epochs")
+    ap.add_argument("--gram-split", type=int, default=0,
+                    help="BF16 terms of the split Gram (2 or 3; 0: library default)")
     ap.add_argument("--refine-gain", type=int, default=0,
                     help="decades each inner FP32 run aims below the last FP64 residual "
                          "(0: library default, <0: every run aims at tol)")
@@ -292,7 +294,8 @@ def run_ours(args):
     Bt = torch.from_numpy(np.ascontiguousarray(B_np)).cuda()
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
 
     def step():
         solver.prepare(At, Bt)
@@ -345,7 +348,8 @@ def run_ours(args):
         B_h = torch.from_numpy(np.ascontiguousarray(B_np)).pin_memory()
         X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5))
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
         hsolver.prepare(A_h, B_h)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -497,7 +501,8 @@ def run_grouped(args, w, world, rank, local):
             torch.from_numpy(np.ascontiguousarray(p.B[0])).cuda()) for p in probs]
     Xt = torch.zeros(N, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
     recs = aln.Solver.grouped_records(dev)
 
     def step():
@@ -549,7 +554,8 @@ def run_grouped(args, w, world, rank, local):
                  torch.from_numpy(np.ascontiguousarray(p.B[0])).pin_memory()) for p in probs]
         hrecs = aln.Solver.grouped_records(host)
         X_h = torch.zeros(N, dtype=torch.float64).pin_memory()
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
         hsolver.prepare_grouped(records=hrecs)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -686,7 +692,8 @@ def run_warmstart(args, w, world, rank, local):
     Btr = torch.from_numpy(np.ascontiguousarray(train.B)).cuda()
     Bt = torch.from_numpy(np.ascontiguousarray(held.B)).cuda()
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
 
     # ---- training set and training (not timed) ----
     t0 = time.perf_counter()

@@ -105,6 +105,10 @@ typedef struct aln_options {
                              runs); < 0 = every run aims at tol; 0 = automatic:
                              3 for the batched solver, off for the single-problem
                              and grouped solvers (measured fastest on each) */
+    int32_t gram_split;   /* BF16 terms of the split-BF16 Gram: 3 = exact split of
+                             the FP32 input (six products), 2 = h + m (three
+                             products, half the tensor work); 0 = default 3 */
+    int32_t reserved;
 } aln_options;
 
 typedef struct aln_solve_info {

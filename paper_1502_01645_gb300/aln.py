@@ -38,7 +38,8 @@ class AlnOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_refine", ctypes.c_int32),
                 ("persist_blocks", ctypes.c_int32), ("row_groups", ctypes.c_int32),
                 ("stagnation", ctypes.c_int32), ("iter_kernel", ctypes.c_int32),
-                ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32)]
+                ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32),
+                ("gram_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class AlnSolveInfo(ctypes.Structure):

@@ -237,6 +237,7 @@ void aln_default_options(aln_options* opt) {
     opt->iter_kernel = 0;
     opt->batch_min = 8;
     opt->refine_gain = 0;
+    opt->gram_split = 3;
 }
 
 int32_t aln_version(void) { return ALN_VERSION; }
@@ -269,6 +270,8 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.stagnation == 0) o.stagnation = 100;
     if (o.batch_min == 0) o.batch_min = 8;
     if (o.refine_gain > 16) return ALN_ERR_INVALID_ARG;
+    if (o.gram_split == 0) o.gram_split = 3;
+    if (o.gram_split != 2 && o.gram_split != 3) return ALN_ERR_INVALID_ARG;
     aln_ctx* c = new (std::nothrow) aln_ctx();
     if (!c) return ALN_ERR_OUT_OF_MEMORY;
     c->opt = o;
@@ -427,7 +430,8 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     else if (f64)
         ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
     else
-        ALN_TRY(launch_gram_tc(hi, mid, lo, d, n, c->ldk, c->inv_s, (float*)c->Q, ldq, c->flags + 1,
+        ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
+                               (float*)c->Q, ldq, c->flags + 1,
                                c->stream));
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     c->launches += 4 + (kc == 0 ? 1 : 0);

@@ -348,6 +348,8 @@ struct BatchWork {
     double* obj = nullptr;
     int* react = nullptr;
     int* host = nullptr;          // pinned: [0] running count, [1] re-activated
+    float* Qp = nullptr;          // Q64 as FP32 pairs: hi [ldq·ldq], then lo
+    float* Yp = nullptr;          // Y64 as FP32 pairs: hi [k·ldq], then lo
     BatchState s{};
     cudaGraphExec_t graph = nullptr;
     int chunk = 8;
@@ -375,7 +377,8 @@ static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
         (size_t)k * 4, (size_t)k * 4, (size_t)k * 4,         // map_act, map_clip, rounds
         (size_t)k * 8, (size_t)k * 8, (size_t)k * 8,         // best, eps, gamma
         (size_t)k * 4, (size_t)k * 8, (size_t)k * 8,         // fin, rel, obj
-        64, 64, 64, 64};                                     // counters, rows, limits, react
+        64, 64, 64, 64,                                      // counters, rows, limits, react
+        (size_t)ldq * ldq * 8, d8};                          // Qp, Yp (FP32 pairs)
     size_t total = 0;
     for (size_t x : sizes) total += round_up(x, 256);
     if (b->pool_bytes < total) {
@@ -436,7 +439,9 @@ static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
     s.rows = (unsigned long long*)take(64);
     s.limits = (int*)take(64);
     b->react = (int*)take(64);
-    if (!b->react || taken != (int)(sizeof(sizes) / sizeof(sizes[0])))
+    b->Qp = (float*)take((size_t)ldq * ldq * 8);
+    b->Yp = (float*)take(d8);
+    if (!b->react || !b->Qp || !b->Yp || taken != (int)(sizeof(sizes) / sizeof(sizes[0])))
         return ALN_ERR_CUDA;  // layout and size table disagree: never launch on it
     if (cudaMemsetAsync(b->pool, 0, b->pool_bytes, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
     return ALN_OK;
@@ -509,6 +514,9 @@ aln_status batch_prepare(aln_ctx* c) {
     if (eg != cudaSuccess) return ALN_ERR_CUDA;
     k_qsplit<<<(unsigned)c->n, kBThreads, 0, c->stream>>>(b->Q64, c->ldq, c->n, b->ldk,
                                                         (float*)c->Q, b->Qhi, b->Qlo);
+    if (launch_split_f64(b->Q64, c->ldq * c->ldq, b->Qp, b->Qp + c->ldq * c->ldq, c->stream) !=
+        cudaSuccess)
+        return ALN_ERR_CUDA;
     k_bnorm2<<<(unsigned)c->k, kBThreads, 0, c->stream>>>(c->B, c->dtype, c->d, c->ldb, b->bn2);
     c->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
@@ -530,7 +538,11 @@ static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine,
     const int64_t k = b->k;
     cudaEventRecord(c->ev[6], c->stream);
     k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
-    if (launch_gemm64_axpy(b->Q64, c->ldq, b->Y64, c->ldq, c->n, c->n, k, c->q64, b->G64, c->ldq,
+    // g = Q y + q in FP64 accuracy (FP32 pairs on the FP32 pipe)
+    const int64_t ky = k * c->ldq;
+    if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
+        launch_gemm_pairs_axpy(b->Qp, b->Qp + c->ldq * c->ldq, c->ldq, b->Yp, b->Yp + ky, c->ldq,
+                               c->n, c->n, k, c->q64, b->G64, c->ldq,
                            c->stream) != cudaSuccess)
         return ALN_ERR_CUDA;
     cudaMemsetAsync(b->react, 0, sizeof(int), c->stream);
@@ -593,7 +605,10 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     c->launches += 1;
     if (X0dev) {  // g = Q y0 + q, in FP64, for a start point
         k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
-        if (launch_gemm64_axpy(b->Q64, c->ldq, b->Y64, c->ldq, c->n, c->n, k, c->q64, b->G64,
+        const int64_t ky = k * c->ldq;
+        if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
+            launch_gemm_pairs_axpy(b->Qp, b->Qp + c->ldq * c->ldq, c->ldq, b->Yp, b->Yp + ky,
+                                   c->ldq, c->n, c->n, k, c->q64, b->G64,
                                c->ldq, c->stream) != cudaSuccess)
             return ALN_ERR_CUDA;
         k_bsetg<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64);

@@ -12,7 +12,7 @@
 // factors 1/s_i, 1/s_j (rounded to FP32), sets Q_ii to 1 (0 for a zero
 // column, Eq. Rescaling) and writes each lower-triangle tile and its mirror.
 //
-// Kernel structure: one 128×128 output tile per CTA (see gram3_tile below for
+// Kernel structure: one 128×128 output tile per CTA (see gram_tile below for
 // the loader, MMA and promotion roles).  Every wait is bounded (1 s on
 // %globaltimer); on expiry the CTA sets *timeout_flag, waits (bounded) for its
 // own copies and MMAs, frees its tensor memory and exits without storing.
@@ -62,28 +62,40 @@ __device__ __forceinline__ void tri_decode(int64_t t, int& I, int& J) {
 // warp 1, one lane: the MMAs; warps 2–5: promotion, then scale and store (warp
 // w owns TMEM lanes and tile rows 32·(w mod 4) … +31).  Every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr int G3_STAGES = 2;
-constexpr int G3_STAGE_BYTES = 6 * TILE_BYTES;
-constexpr int G3_SMEM_BYTES = G3_STAGES * G3_STAGE_BYTES + 1024 + 256;
+// NS = number of split terms (3: h, m, l; 2: h, m).  Stages of 2·NS boxes;
+// K blocks per promoted accumulator (CHUNK): 1 with six products per K step,
+// 2 with three (the MMA would otherwise outrun the promotion).
+template <int NS>
+struct GramCfg {
+    static constexpr int STAGES = NS == 3 ? 2 : 3;
+    static constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+    static constexpr int CHUNK = NS == 3 ? 1 : 2;
+};
+constexpr int G3_SMEM_BYTES = 2 * 6 * TILE_BYTES + 1024 + 256;  // = 3·4·TILE_BYTES + …
 constexpr int G3_THREADS = 192;
 constexpr uint32_t G3_TMEM_COLS = 2 * BM;  // two 128-column accumulators
 
-// One K block of the six split products into a fresh accumulator.
-// a/b: shared addresses of the h boxes (m, l follow at TILE_BYTES, 2·TILE_BYTES).
-__device__ __forceinline__ void gram3_chunk(uint32_t tmem, uint32_t a, uint32_t b) {
+// One K block of the split products, the small cross terms first and the
+// four h·h steps last (`fresh` starts a new accumulator).  NS = 3: hm, mh,
+// mm, hl, lh, then hh; NS = 2: hm, mh, then hh.  a/b: shared addresses of the
+// h boxes (m, l follow at TILE_BYTES, 2·TILE_BYTES).
+template <int NS>
+__device__ __forceinline__ void gram_chunk(uint32_t tmem, uint32_t a, uint32_t b, bool fresh) {
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t off = kk * 32;  // 16 BF16 along K
-        const uint64_t ah = sdesc_sw128(a + off), am = sdesc_sw128(a + TILE_BYTES + off),
-                       al = sdesc_sw128(a + 2 * TILE_BYTES + off);
-        const uint64_t bh = sdesc_sw128(b + off), bm = sdesc_sw128(b + TILE_BYTES + off),
-                       bl = sdesc_sw128(b + 2 * TILE_BYTES + off);
-        umma_bf16(tmem, ah, bm, idesc, kk == 0 ? 0u : 1u);
+        const uint64_t ah = sdesc_sw128(a + off), am = sdesc_sw128(a + TILE_BYTES + off);
+        const uint64_t bh = sdesc_sw128(b + off), bm = sdesc_sw128(b + TILE_BYTES + off);
+        umma_bf16(tmem, ah, bm, idesc, (fresh && kk == 0) ? 0u : 1u);
         umma_bf16(tmem, am, bh, idesc, 1u);
-        umma_bf16(tmem, am, bm, idesc, 1u);
-        umma_bf16(tmem, ah, bl, idesc, 1u);
-        umma_bf16(tmem, al, bh, idesc, 1u);
+        if (NS == 3) {
+            const uint64_t al = sdesc_sw128(a + 2 * TILE_BYTES + off),
+                           bl = sdesc_sw128(b + 2 * TILE_BYTES + off);
+            umma_bf16(tmem, am, bm, idesc, 1u);
+            umma_bf16(tmem, ah, bl, idesc, 1u);
+            umma_bf16(tmem, al, bh, idesc, 1u);
+        }
     }
 #pragma unroll
     for (int kk = 0; kk < BK / 16; ++kk) {
@@ -93,7 +105,7 @@ __device__ __forceinline__ void gram3_chunk(uint32_t tmem, uint32_t a, uint32_t 
 }
 
 // acc[c] += the accumulator row this thread's lane reads (128 columns).
-__device__ __forceinline__ void gram3_promote(float (&acc)[BM], uint32_t tb) {
+__device__ __forceinline__ void gram_promote(float (&acc)[BM], uint32_t tb) {
 #pragma unroll
     for (int c0 = 0; c0 < BM; c0 += 16) {
         float v[16];
@@ -106,7 +118,7 @@ __device__ __forceinline__ void gram3_promote(float (&acc)[BM], uint32_t tb) {
 // Scale and store one promoted tile row: Q_ij = H_ij·(1/s_i)·(1/s_j) (FP32
 // factors), Q_ii = 1 (0 for a zero column, Eq. Rescaling); diagonal tiles keep
 // the lower triangle and mirror it, so Q is exactly symmetric.
-__device__ __forceinline__ void gram3_store(const float (&acc)[BM], int64_t row, int64_t n0,
+__device__ __forceinline__ void gram_store(const float (&acc)[BM], int64_t row, int64_t n0,
                                             bool diag, int64_t n, const double* __restrict__ inv_s,
                                             const float* s_cs, float* __restrict__ Q,
                                             int64_t ldq) {
@@ -151,16 +163,17 @@ __device__ __forceinline__ void gram3_store(const float (&acc)[BM], int64_t row,
 }
 
 // One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
-template <class Loader>
-__device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool diag, int64_t m0,
+template <int NS, class Loader>
+__device__ __forceinline__ void gram_tile(const Loader& ld, int num_kb, bool diag, int64_t m0,
                                            int64_t n0, int64_t n, const double* __restrict__ inv_s,
                                            float* __restrict__ Q, int64_t ldq,
                                            int* timeout_flag) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + G3_STAGES * G3_STAGE_BYTES);
-    uint64_t* empty = full + G3_STAGES;
-    uint64_t* tfull = empty + G3_STAGES;
+    using C = GramCfg<NS>;
+    uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE_BYTES);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
@@ -169,7 +182,7 @@ __device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool di
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < G3_STAGES; ++s) {
+        for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -200,48 +213,51 @@ __device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool di
     if (warp == 0 && lane == 0) {
         int issued = 0;
         for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % G3_STAGES;
-            if (kb >= G3_STAGES && !mbar_wait(&empty[s], ((kb / G3_STAGES) & 1) ^ 1)) {
+            const int s = kb % C::STAGES;
+            if (kb >= C::STAGES && !mbar_wait(&empty[s], ((kb / C::STAGES) & 1) ^ 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
-            uint8_t* sb = smem + s * G3_STAGE_BYTES;
-            mbar_expect_tx(&full[s], (diag ? 3 : 6) * TILE_BYTES);
+            uint8_t* sb = smem + s * C::STAGE_BYTES;
+            mbar_expect_tx(&full[s], (diag ? NS : 2 * NS) * TILE_BYTES);
             ld.load(sb, kb, diag, &full[s]);
             ++issued;
         }
-        // our own copies in flight: the last ≤ G3_STAGES loads (bounded wait)
-        for (int kb = max(0, issued - G3_STAGES); kb < issued; ++kb)
-            if (!mbar_wait(&full[kb % G3_STAGES], (kb / G3_STAGES) & 1)) s_abort = 1;
+        // our own copies in flight: the last ≤ STAGES loads (bounded wait)
+        for (int kb = max(0, issued - C::STAGES); kb < issued; ++kb)
+            if (!mbar_wait(&full[kb % C::STAGES], (kb / C::STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
         for (int kb = 0; kb < num_kb; ++kb) {
-            const int s = kb % G3_STAGES, b = kb & 1;
-            if (!mbar_wait(&full[s], (kb / G3_STAGES) & 1) ||
-                (kb >= 2 && !mbar_wait(&tempty[b], ((kb >> 1) & 1) ^ 1))) {
+            const int s = kb % C::STAGES, ch = kb / C::CHUNK, b = ch & 1;
+            const bool fresh = kb % C::CHUNK == 0;
+            const bool last = kb % C::CHUNK == C::CHUNK - 1 || kb == num_kb - 1;
+            if (!mbar_wait(&full[s], (kb / C::STAGES) & 1) ||
+                (fresh && ch >= 2 && !mbar_wait(&tempty[b], ((ch >> 1) & 1) ^ 1))) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a0 = smem_u32(smem + s * G3_STAGE_BYTES);
-            const uint32_t b0 = diag ? a0 : a0 + 3 * TILE_BYTES;
-            gram3_chunk(tmem + (uint32_t)(b * BM), a0, b0);
+            const uint32_t a0 = smem_u32(smem + s * C::STAGE_BYTES);
+            const uint32_t b0 = diag ? a0 : a0 + NS * TILE_BYTES;
+            gram_chunk<NS>(tmem + (uint32_t)(b * BM), a0, b0, fresh);
             umma_commit(&empty[s]);
-            umma_commit(&tfull[b]);
+            if (last) umma_commit(&tfull[b]);
         }
         // always commit: `done` then also covers MMAs issued before an abort
         umma_commit(done);
     } else if (warp >= 2) {
         const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        for (int kb = 0; kb < num_kb; ++kb) {
+        const int nch = (num_kb + C::CHUNK - 1) / C::CHUNK;
+        for (int kb = 0; kb < nch; ++kb) {  // kb: chunk index
             const int b = kb & 1;
             if (!mbar_wait(&tfull[b], (kb >> 1) & 1)) {
                 s_abort = 1;
                 break;
             }
             tc_fence_after();
-            gram3_promote(acc, tb + (uint32_t)(b * BM));
+            gram_promote(acc, tb + (uint32_t)(b * BM));
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
@@ -257,7 +273,7 @@ __device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool di
     __syncthreads();
     if (!s_abort) {
         if (warp >= 2)
-            gram3_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
+            gram_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
     } else if (threadIdx.x == 0) {
         atomicExch(timeout_flag, 1);
     }
@@ -266,6 +282,7 @@ __device__ __forceinline__ void gram3_tile(const Loader& ld, int num_kb, bool di
     if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
 }
 
+template <int NS>
 struct TmaLoader {
     const CUtensorMap* mh;
     const CUtensorMap* mm;
@@ -274,23 +291,24 @@ struct TmaLoader {
     __device__ __forceinline__ void load(uint8_t* sb, int kb, bool diag, uint64_t* bar) const {
         tma_load_2d(sb, mh, bar, kb * BK, m0);
         tma_load_2d(sb + TILE_BYTES, mm, bar, kb * BK, m0);
-        tma_load_2d(sb + 2 * TILE_BYTES, ml, bar, kb * BK, m0);
+        if (NS == 3) tma_load_2d(sb + 2 * TILE_BYTES, ml, bar, kb * BK, m0);
         if (!diag) {
-            tma_load_2d(sb + 3 * TILE_BYTES, mh, bar, kb * BK, n0);
-            tma_load_2d(sb + 4 * TILE_BYTES, mm, bar, kb * BK, n0);
-            tma_load_2d(sb + 5 * TILE_BYTES, ml, bar, kb * BK, n0);
+            tma_load_2d(sb + NS * TILE_BYTES, mh, bar, kb * BK, n0);
+            tma_load_2d(sb + (NS + 1) * TILE_BYTES, mm, bar, kb * BK, n0);
+            if (NS == 3) tma_load_2d(sb + 5 * TILE_BYTES, ml, bar, kb * BK, n0);
         }
     }
 };
 
+template <int NS>
 __global__ void __launch_bounds__(G3_THREADS, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
               const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
     int tm, tn;
     tri_decode(blockIdx.x, tm, tn);
-    const TmaLoader ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM};
-    gram3_tile(ld, p.num_kb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
-               p.ldq, p.timeout_flag);
+    const TmaLoader<NS> ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM};
+    gram_tile<NS>(ld, p.num_kb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
+                  p.ldq, p.timeout_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,6 +340,7 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+template <int NS>
 struct BulkLoader {
     const __nv_bfloat16* hi;
     const __nv_bfloat16* mid;
@@ -331,22 +350,23 @@ struct BulkLoader {
         const int64_t off = (int64_t)kb * kPackTile;
         bulk_load(sb, hi + ta + off, TILE_BYTES, bar);
         bulk_load(sb + TILE_BYTES, mid + ta + off, TILE_BYTES, bar);
-        bulk_load(sb + 2 * TILE_BYTES, lo + ta + off, TILE_BYTES, bar);
+        if (NS == 3) bulk_load(sb + 2 * TILE_BYTES, lo + ta + off, TILE_BYTES, bar);
         if (!diag) {
-            bulk_load(sb + 3 * TILE_BYTES, hi + tb + off, TILE_BYTES, bar);
-            bulk_load(sb + 4 * TILE_BYTES, mid + tb + off, TILE_BYTES, bar);
-            bulk_load(sb + 5 * TILE_BYTES, lo + tb + off, TILE_BYTES, bar);
+            bulk_load(sb + NS * TILE_BYTES, hi + tb + off, TILE_BYTES, bar);
+            bulk_load(sb + (NS + 1) * TILE_BYTES, mid + tb + off, TILE_BYTES, bar);
+            if (NS == 3) bulk_load(sb + 5 * TILE_BYTES, lo + tb + off, TILE_BYTES, bar);
         }
     }
 };
 
+template <int NS>
 __global__ void __launch_bounds__(G3_THREADS, 1) k_ggram_tc(GGramArgs a) {
     const GTile tl = a.tiles[blockIdx.x];
     const GProb P = a.gp[tl.p];
-    const BulkLoader ld{a.hi, a.mid, a.lo, (P.pack + (int64_t)tl.tm * P.KB) * kPackTile,
-                        (P.pack + (int64_t)tl.tn * P.KB) * kPackTile};
-    gram3_tile(ld, P.KB, tl.tm == tl.tn, (int64_t)tl.tm * BM, (int64_t)tl.tn * BM, P.n,
-               a.inv_s + P.voff, a.Q + P.qoff, P.ldq, a.timeout_flag);
+    const BulkLoader<NS> ld{a.hi, a.mid, a.lo, (P.pack + (int64_t)tl.tm * P.KB) * kPackTile,
+                            (P.pack + (int64_t)tl.tn * P.KB) * kPackTile};
+    gram_tile<NS>(ld, P.KB, tl.tm == tl.tn, (int64_t)tl.tm * BM, (int64_t)tl.tn * BM, P.n,
+                  a.inv_s + P.voff, a.Q + P.qoff, P.ldq, a.timeout_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -377,33 +397,8 @@ struct BatchArgs {
     int* timeout_flag;
 };
 
-// One K block of the two-term split product: the small cross terms first
-// (h·l, l·h), then the four h·h steps (`fresh` starts a new accumulator).
-// Two K blocks share an accumulator before promotion (BG_CHUNK): with three
-// products per K step the MMA outruns a per-block promotion, and eight large
-// truncating steps still keep the bias near 10⁻⁷.
-constexpr int BG_CHUNK = 2;
-__device__ __forceinline__ void split2_chunk(uint32_t tmem, uint32_t a, uint32_t b, bool fresh) {
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
-#pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t off = kk * 32;
-        umma_bf16(tmem, sdesc_sw128(a + off), sdesc_sw128(b + TILE_BYTES + off), idesc,
-                  (fresh && kk == 0) ? 0u : 1u);
-        umma_bf16(tmem, sdesc_sw128(a + TILE_BYTES + off), sdesc_sw128(b + off), idesc, 1u);
-    }
-#pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t off = kk * 32;
-        umma_bf16(tmem, sdesc_sw128(a + off), sdesc_sw128(b + off), idesc, 1u);
-    }
-}
-
-// Same roles as the Gram (gram3_tile): warp 0 TMA, warp 1 MMA, warps 2–5
-// promote each K block's accumulator into FP32 registers and run the
-// epilogue.  Stage ring: 3 × (Q_hi, Q_lo, V_hi, V_lo).
 template <int MODE>
-__global__ void __launch_bounds__(G3_THREADS, 1)
+__global__ void __launch_bounds__(128, 1)
     k_bgemm_tc(const __grid_constant__ CUtensorMap a_hi, const __grid_constant__ CUtensorMap a_lo,
                const __grid_constant__ CUtensorMap b_hi, const __grid_constant__ CUtensorMap b_lo,
                BatchArgs p) {
@@ -415,9 +410,7 @@ __global__ void __launch_bounds__(G3_THREADS, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* tfull = empty + STAGES;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* done = tempty + 2;
+    uint64_t* done = empty + STAGES;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ int s_map[BM];
     __shared__ float s_red[4][BM];
@@ -429,29 +422,22 @@ __global__ void __launch_bounds__(G3_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
-        }
         mbar_init(done, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < BM) {
+    {
         const int64_t pp = n0 + threadIdx.x;
         s_map[threadIdx.x] = pp < ncols ? p.map[pp] : -1;
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, G3_TMEM_COLS);
+        tmem_alloc(tmem_slot, TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    float acc[BM];
-#pragma unroll
-    for (int c = 0; c < BM; ++c) acc[c] = 0.0f;
 
     if (warp == 0 && lane == 0) {
         int issued = 0;
@@ -473,76 +459,71 @@ __global__ void __launch_bounds__(G3_THREADS, 1)
         for (int kb = max(0, issued - STAGES); kb < issued; ++kb)
             if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) s_abort = 1;
     } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_bf16_f32(BM, BM);
         for (int kb = 0; kb < p.num_kb; ++kb) {
-            const int s = kb % STAGES, ch = kb / BG_CHUNK, b = ch & 1;
-            const bool fresh = kb % BG_CHUNK == 0;
-            const bool last = kb % BG_CHUNK == BG_CHUNK - 1 || kb == p.num_kb - 1;
-            if (!mbar_wait(&full[s], (kb / STAGES) & 1) ||
-                (fresh && ch >= 2 && !mbar_wait(&tempty[b], ((ch >> 1) & 1) ^ 1))) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
                 s_abort = 1;
                 break;
             }
             if (*(volatile int*)&s_abort) break;
             tc_fence_after();
-            const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-            split2_chunk(tmem + (uint32_t)(b * BM), a0, a0 + 2 * TILE_BYTES, fresh);
+            const uint32_t a_h = smem_u32(smem + s * STAGE_BYTES);
+            const uint32_t a_l = a_h + TILE_BYTES;
+            const uint32_t b_h = a_h + 2 * TILE_BYTES;
+            const uint32_t b_l = a_h + 3 * TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint64_t dah = sdesc_sw128(a_h + off), dal = sdesc_sw128(a_l + off);
+                const uint64_t dbh = sdesc_sw128(b_h + off), dbl = sdesc_sw128(b_l + off);
+                umma_bf16(tmem, dah, dbh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                umma_bf16(tmem, dah, dbl, idesc, 1u);
+                umma_bf16(tmem, dal, dbh, idesc, 1u);
+            }
             umma_commit(&empty[s]);
-            if (last) umma_commit(&tfull[b]);
         }
         umma_commit(done);
-    } else if (warp >= 2) {
-        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        const int nch = (p.num_kb + BG_CHUNK - 1) / BG_CHUNK;
-        for (int kb = 0; kb < nch; ++kb) {  // kb: chunk index
-            const int b = kb & 1;
-            if (!mbar_wait(&tfull[b], (kb >> 1) & 1)) {
-                s_abort = 1;
-                break;
-            }
-            tc_fence_after();
-            gram3_promote(acc, tb + (uint32_t)(b * BM));
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-            if (*(volatile int*)&s_abort) break;
-        }
     }
     __syncwarp();
-    if (warp == 1) {
-        const bool ok = mbar_wait(done, 0);
-        if (!ok) s_abort = 1;
-    }
+
+    const bool ok = mbar_wait(done, 0);
     tc_fence_after();
+    if (!ok) s_abort = 1;
     __syncthreads();
     const bool good = !s_abort;
+    const int64_t row = m0 + warp * 32 + lane;
+    const bool rv = row < p.n;
     const int cols = (int)(ncols - n0 < (int64_t)BM ? ncols - n0 : (int64_t)BM);
-    if (good && warp >= 2) {
-        const int qd = warp & 3;
-        const int64_t row = m0 + 32 * qd + lane;
-        const bool rv = row < p.n;
+    const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    if (good) {
+        for (int c0 = 0; c0 < cols; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + c0, v);
 #pragma unroll
-        for (int cc = 0; cc < BM; ++cc) {
-            if (cc >= cols) continue;  // uniform over the warp; keeps acc[] in registers
-            const int col = s_map[cc];
-            if (MODE == BMODE_W) {
-                // curvature partial in FP32 (the FP64 pipe is narrow on this
-                // GPU); the row-tile partials are summed in FP64
-                float kp = 0.0f;
-                if (col >= 0 && rv) {
-                    p.W[(n0 + cc) * p.ldq + row] = acc[cc];
-                    kp = p.gb[(int64_t)col * p.ldq + row] * acc[cc];
-                }
+            for (int t = 0; t < 16; ++t) {
+                const int cc = c0 + t;
+                const int col = cc < cols ? s_map[cc] : -1;
+                if (MODE == BMODE_W) {
+                    // curvature partial in FP32 (the FP64 pipe is narrow on
+                    // this GPU); the row-tile partials are summed in FP64
+                    float kp = 0.0f;
+                    if (col >= 0 && rv) {
+                        p.W[(n0 + cc) * p.ldq + row] = v[t];
+                        kp = p.gb[(int64_t)col * p.ldq + row] * v[t];
+                    }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
-                if (lane == 0) s_red[qd][cc] = kp;
-            } else {
-                if (col >= 0 && rv) {
-                    float* gp = p.g + (int64_t)col * p.ldq + row;
-                    *gp = *gp + acc[cc];
+                    for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
+                    if (lane == 0) s_red[warp][cc] = kp;
+                } else {
+                    if (col >= 0 && rv) {
+                        float* gp = p.g + (int64_t)col * p.ldq + row;
+                        *gp = *gp + v[t];
+                    }
                 }
             }
         }
-    } else if (!good && threadIdx.x == 0) {
+    } else if (threadIdx.x == 0) {
         atomicExch(p.timeout_flag, 1);
     }
     if (MODE == BMODE_W) {
@@ -555,20 +536,22 @@ __global__ void __launch_bounds__(G3_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 }  // namespace tc
 
 bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_minor == 3; }
 
-cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
+    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+    if (nsplit == 2) lo = mid;  // unused: any valid map
     if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) ||
         (ldk * 2) % 16 != 0 || ldq % 4 != 0)
         return cudaErrorInvalidValue;
@@ -576,12 +559,13 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
     if (!make_map(&mh, hi, ldk, n, ldk) || !make_map(&mm, mid, ldk, n, ldk) ||
         !make_map(&ml, lo, ldk, n, ldk))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static bool attr[2] = {false, false};
+    if (!attr[nsplit - 2]) {
+        cudaError_t e = cudaFuncSetAttribute(nsplit == 3 ? k_gram_tc<3> : k_gram_tc<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              G3_SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[nsplit - 2] = true;
     }
     GramArgs a;
     a.n = n;
@@ -591,26 +575,32 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
-    k_gram_tc<<<(unsigned)(tiles * (tiles + 1) / 2), G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml,
-                                                                                     a);
+    const unsigned grid = (unsigned)(tiles * (tiles + 1) / 2);
+    if (nsplit == 3)
+        k_gram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+    else
+        k_gram_tc<2><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
+cudaError_t launch_ggram_tc(int nsplit, const GProb* gp, const GTile* tiles, int64_t ntiles,
                             const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                             const __nv_bfloat16* lo, const double* inv_s, float* Q,
                             int* timeout_flag, cudaStream_t st) {
     using namespace tc;
     if (ntiles <= 0) return cudaSuccess;
+    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+    if (nsplit == 2) lo = mid;
     if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) ||
         ((uintptr_t)Q & 15))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_ggram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    static bool attr[2] = {false, false};
+    if (!attr[nsplit - 2]) {
+        cudaError_t e = cudaFuncSetAttribute(nsplit == 3 ? k_ggram_tc<3> : k_ggram_tc<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              G3_SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[nsplit - 2] = true;
     }
     GGramArgs a;
     a.gp = gp;
@@ -621,7 +611,10 @@ cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
     a.inv_s = inv_s;
     a.Q = Q;
     a.timeout_flag = timeout_flag;
-    k_ggram_tc<<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
+    if (nsplit == 3)
+        k_ggram_tc<3><<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
+    else
+        k_ggram_tc<2><<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -660,9 +653,9 @@ cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bflo
     a.timeout_flag = timeout_flag;
     const dim3 grid((unsigned)ceil_div(n, BM), (unsigned)ceil_div(kmax, BM));
     if (mode == BMODE_W)
-        k_bgemm_tc<BMODE_W><<<grid, G3_THREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+        k_bgemm_tc<BMODE_W><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
     else
-        k_bgemm_tc<BMODE_U><<<grid, G3_THREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
+        k_bgemm_tc<BMODE_U><<<grid, 128, SMEM_BYTES, st>>>(ah, al, bh, bl, a);
     return cudaGetLastError();
 }
 

@@ -1221,7 +1221,8 @@ aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, in
         }
         c->launches += count;
     } else {
-        G_TRY(launch_ggram_tc(g->gp, g->tiles, g->ntiles, g->hi, g->mid, g->lo, g->inv_s,
+        G_TRY(launch_ggram_tc(c->opt.gram_split, g->gp, g->tiles, g->ntiles, g->hi, g->mid, g->lo,
+                              g->inv_s,
                               (float*)g->Q, g->flags + 1, c->stream));
         c->launches += 1;
     }

@@ -31,14 +31,19 @@ cudaError_t launch_gram32_dot2(const float* A, int64_t d, int64_t n, int64_t lda
 cudaError_t launch_qvec32_dot2(const float* A, int64_t d, int64_t n, int64_t lda, const float* B,
                                int64_t k, int64_t ldb, const double* inv_s, double* q64,
                                int64_t ldq, cudaStream_t st);
+cudaError_t launch_split_f64(const double* v, int64_t m, float* hi, float* lo, cudaStream_t st);
+cudaError_t launch_gemm_pairs_axpy(const float* Xh, const float* Xl, int64_t ldx, const float* Yh,
+                                   const float* Yl, int64_t ldy, int64_t K, int64_t M, int64_t N,
+                                   const double* add, double* out, int64_t ldo, cudaStream_t st);
 cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                int64_t K, int64_t M, int64_t N, const double* add, double* out,
                                int64_t ldo, cudaStream_t st);
 
 // gemm_tc.cu — split-BF16 tensor-core Gram (tcgen05 + TMA)
 // Q_ij = (Σ_t hh + hm + mh + mm + hl + lh)_ij · inv_s_i · inv_s_j for the exact
-// three-term split a = h + m + l; lower tiles mirrored.
-cudaError_t launch_gram_tc(const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+// three-term split a = h + m + l (nsplit = 3), or hh + hm + mh for the two-term
+// split a ≈ h + m (nsplit = 2); lower tiles mirrored.
+cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st);
@@ -83,7 +88,7 @@ __host__ __device__ __forceinline__ int64_t pack_index(int64_t tile0, int KB, in
     const int64_t tile = tile0 + (int64_t)(j >> 7) * KB + (t >> 6);
     return tile * kPackTile + r * 64 + ((((kk >> 3) ^ (r & 7)) << 3) | (kk & 7));
 }
-cudaError_t launch_ggram_tc(const GProb* gp, const GTile* tiles, int64_t ntiles,
+cudaError_t launch_ggram_tc(int nsplit, const GProb* gp, const GTile* tiles, int64_t ntiles,
                             const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                             const __nv_bfloat16* lo, const double* inv_s, float* Q,
                             int* timeout_flag, cudaStream_t st);
