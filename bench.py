@@ -652,7 +652,8 @@ def run_grouped(args, w, world, rank, local):
                    "n_range": [min(n for _, n in sizes), max(n for _, n in sizes)],
                    "tol": tol, "seed": w["seed"],
                    "form": "grouped: split-BF16 tcgen05 Gram (bulk-copy tiles), FP32 Alg. 2 "
-                           "one problem per block, FP64 scale/KKT/refinement",
+                           "one problem per block, n >= 512 out of shared memory on "
+                           "4-block clusters (concurrent stream), FP64 scale/KKT/refinement",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2" if nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",

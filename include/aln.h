@@ -108,7 +108,11 @@ typedef struct aln_options {
     int32_t gram_split;   /* BF16 terms of the split-BF16 Gram: 3 = exact split of
                              the FP32 input (six products), 2 = h + m (three
                              products, half the tensor work); 0 = default 3 */
-    int32_t reserved;
+    int32_t group_cluster; /* grouped solver: blocks of the thread-block cluster
+                             that solves each large problem (n ≥ 512 and Q_p
+                             larger than one block's shared memory) while
+                             single blocks take the rest; 1 = no clusters, 2, 4
+                             or 8; 0 = default 4 */
 } aln_options;
 
 typedef struct aln_solve_info {

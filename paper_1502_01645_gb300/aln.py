@@ -39,7 +39,7 @@ class AlnOptions(ctypes.Structure):
                 ("persist_blocks", ctypes.c_int32), ("row_groups", ctypes.c_int32),
                 ("stagnation", ctypes.c_int32), ("iter_kernel", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32),
-                ("gram_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("gram_split", ctypes.c_int32), ("group_cluster", ctypes.c_int32)]
 
 
 class AlnSolveInfo(ctypes.Structure):

@@ -238,6 +238,7 @@ void aln_default_options(aln_options* opt) {
     opt->batch_min = 8;
     opt->refine_gain = 0;
     opt->gram_split = 3;
+    opt->group_cluster = 4;
 }
 
 int32_t aln_version(void) { return ALN_VERSION; }
@@ -272,6 +273,10 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.refine_gain > 16) return ALN_ERR_INVALID_ARG;
     if (o.gram_split == 0) o.gram_split = 3;
     if (o.gram_split != 2 && o.gram_split != 3) return ALN_ERR_INVALID_ARG;
+    if (o.group_cluster == 0) o.group_cluster = 4;
+    if (o.group_cluster != 1 && o.group_cluster != 2 && o.group_cluster != 4 &&
+        o.group_cluster != 8)
+        return ALN_ERR_INVALID_ARG;
     aln_ctx* c = new (std::nothrow) aln_ctx();
     if (!c) return ALN_ERR_OUT_OF_MEMORY;
     c->opt = o;

@@ -34,6 +34,13 @@ constexpr int kGWarps = kGThreads / 32;
 constexpr int kGU = 8;            // columns of Q in flight per lane in the product
 constexpr int kGMaxN = 4096;      // largest n of a grouped problem
 constexpr int kKeySlot = 0, kKeyV = 1, kKeyR = 2;
+// Problems with n ≥ kGClusterMinN whose Q_p does not fit in one block's
+// shared memory are solved by a cluster of blocks (k_galg2c; kGCluster unless
+// the options say otherwise): each iteration of such a problem is bound by one
+// SM's read rate of Q_p from L2, and the largest of them sets the length of
+// the whole run.
+constexpr int kGCluster = 4;
+constexpr int kGClusterMinN = 512;
 
 struct GStat {
     int32_t iters;        // Alg. 2 iterations, summed over rounds
@@ -337,25 +344,30 @@ __device__ __forceinline__ int glist(int n, const T* v, int* list, GRed<T>* r) {
     return lt;
 }
 
-// out[i] (+)= Σ_k Q[list[k]][i] · v[list[k]] for i < n — the product of Alg. 2
-// restricted to the listed columns (Q is symmetric; row list[k] is read).
-// Warps split the row into 32·VN-wide tiles and the list into S strided
-// subsets; the S partials are added in subset order (deterministic).
+// out[i] (+)= Σ_k Q[list[k]][i] · v[list[k]] for lo ≤ i < hi — the product of
+// Alg. 2 restricted to the listed columns (Q is symmetric; row list[k] is
+// read) and to a range of rows (lo a multiple of 32·VN).  Warps split the
+// range into 32·VN-wide tiles and the list into S strided subsets; the S
+// partials are added in subset order (deterministic).
 template <typename T>
-__device__ __forceinline__ void gmv(const T* Q, int ldq, int n, const int* list, int cnt,
+__device__ __forceinline__ void gmv(const T* Q, int ldq, int lo, int hi, const int* list, int cnt,
                                     const T* v, T* out, bool accumulate, T* red) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int CT = (n + TILE - 1) / TILE;
+    const int CT = hi > lo ? (hi - lo + TILE - 1) / TILE : 0;
+    if (CT == 0) {  // uniform: nothing in range
+        __syncthreads();
+        return;
+    }
     const int CTw = CT < kGWarps ? CT : kGWarps;
     const int S = kGWarps / CTw;
     const int sub = wid / CTw;
     if (sub < S) {
         for (int ct = wid % CTw; ct < CT; ct += CTw) {
-            const int col = ct * TILE + lane * VN;
-            const bool cv = col < n;  // then col + VN ≤ ldq (ldq is a multiple of 4)
+            const int col = lo + ct * TILE + lane * VN;
+            const bool cv = col < hi;  // then col + VN ≤ ldq (ldq is a multiple of 4)
             T acc[VN];
 #pragma unroll
             for (int c = 0; c < VN; ++c) acc[c] = T(0);
@@ -385,7 +397,7 @@ __device__ __forceinline__ void gmv(const T* Q, int ldq, int n, const int* list,
                 if (cv)
 #pragma unroll
                     for (int c = 0; c < VN; ++c)
-                        if (col + c < n) out[col + c] = accumulate ? out[col + c] + acc[c] : acc[c];
+                        if (col + c < hi) out[col + c] = accumulate ? out[col + c] + acc[c] : acc[c];
             } else {
 #pragma unroll
                 for (int c = 0; c < VN; ++c) red[(sub * CT + ct) * TILE + lane * VN + c] = acc[c];
@@ -394,18 +406,83 @@ __device__ __forceinline__ void gmv(const T* Q, int ldq, int n, const int* list,
     }
     if (S > 1) {
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int ct = i / TILE, rr = i - ct * TILE;
+        for (int ii = threadIdx.x; ii < hi - lo; ii += blockDim.x) {
+            const int ct = ii / TILE, rr = ii - ct * TILE;
             T s = T(0);
             for (int s2 = 0; s2 < S; ++s2) s += red[(s2 * CT + ct) * TILE + rr];
+            const int i = lo + ii;
             out[i] = accumulate ? out[i] + s : s;
         }
     }
     __syncthreads();
 }
 
-template <typename T>
-__device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
+// --- thread-block clusters (large problems, several CTAs per problem) ------
+__device__ __forceinline__ int cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_ctas() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return (int)r;
+}
+// Address of `p` (this CTA's shared memory) in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
+    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float ld_cluster(uint32_t addr, float) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_cluster(uint32_t addr, double) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, int v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// Hardware barrier over every thread of every CTA in the cluster, with
+// release/acquire ordering of shared-memory writes across the cluster.  All
+// CTAs of a cluster take the same branches (their state is replicated
+// bit-for-bit and every decision is derived from it), so each reaches every
+// barrier.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+// w (+)= Q·v over the listed columns for every row.  With CL, CTA `rank` of
+// the cluster computes rows [rank·S, rank·S + S) into its exchange buffer xb,
+// and after a cluster barrier every CTA gathers all slices (distributed
+// shared memory), so all CTAs hold the same w.
+template <typename T, bool CL>
+__device__ __forceinline__ void product(const T* Q, int ldq, int n, const int* list, int cnt,
+                                        const T* v, T* out, bool accumulate, T* red, T* xb,
+                                        int rank, int S) {
+    if (!CL) {
+        gmv(Q, ldq, 0, n, list, cnt, v, out, accumulate, red);
+        return;
+    }
+    const int lo = min(n, rank * S), hi = min(n, lo + S);
+    gmv(Q, ldq, lo, hi, list, cnt, v, xb, false, red);
+    cluster_sync();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int r = i / S;
+        const T val = r == rank ? xb[i] : ld_cluster(cluster_addr(xb + i, r), T(0));
+        out[i] = accumulate ? out[i] + val : val;
+    }
+    __syncthreads();
+}
+
+// Alg. 2 on problem p by one CTA (CL = false) or by the CTAs of a cluster (CL).
+template <typename T, bool CL>
+__device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, int C) {
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
     __shared__ GRed<T> rs;
@@ -424,9 +501,15 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
     int* lp = reinterpret_cast<int*>(sw + ldq);
     int* lc = lp + ldq;
     T* red = reinterpret_cast<T*>(lc + ldq);
-    T* sQ = red + kGWarps * TILE;
+    T* xb0 = red + kGWarps * TILE;  // cluster exchange buffers (two, used in turn)
+    T* xb1 = xb0 + ldq;
+    T* sQ = CL ? xb1 + ldq : xb0;
     const int64_t used = (int64_t)((uint8_t*)sQ - sm);
-    const bool qin = (int64_t)n * ldq * (int64_t)sizeof(T) <= (int64_t)a.smem_bytes - used;
+    const bool qin =
+        !CL && (int64_t)n * ldq * (int64_t)sizeof(T) <= (int64_t)a.smem_bytes - used;
+    const int S = CL ? ((n + C - 1) / C + TILE - 1) / TILE * TILE : n;
+    int pc = 0;  // products so far: selects the exchange buffer
+    auto xb = [&]() { return (pc++ & 1) ? xb1 : xb0; };
     const T* Qg = a.Q + P.qoff;
     if (qin) {  // stage Q_p in shared memory for all iterations
         using V = typename Vec16<T>::type;
@@ -437,6 +520,8 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
     }
     const T* Qp = qin ? sQ : Qg;
     const double* q = a.q64 + P.voff;
+    GStat st = a.stat[p];
+    const double sf = a.tgt[p] * (a.den[p] > 0.0 ? a.den[p] : 1.0);
     for (int i = threadIdx.x; i < ldq; i += blockDim.x) {
         const double yv = i < n ? a.y[P.foff + i] : 0.0;
         const T yh = (T)yv;
@@ -446,16 +531,17 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
         if (a.gmode == 1) sg[i] = i < n ? (T)a.g64[P.voff + i] : T(0);
     }
     __syncthreads();
+    // With a cluster, rank 0 alone writes y and the statistics back: no CTA
+    // may still be reading them then, or the replicas would start apart.
+    if (CL) cluster_sync();
     if (a.gmode == 0) {
         // g = Q y + q (Alg. 2 start; y = 0 gives g = q)
         const int cy = glist(n, sy, lp, &rs);
-        gmv(Qp, ldq, n, lp, cy, sy, sg, false, red);
+        product<T, CL>(Qp, ldq, n, lp, cy, sy, sg, false, red, xb(), rank, S);
         for (int i = threadIdx.x; i < n; i += blockDim.x) sg[i] += (T)q[i];
         __syncthreads();
     }
 
-    GStat st = a.stat[p];
-    const double sf = a.tgt[p] * (a.den[p] > 0.0 ? a.den[p] : 1.0);
     const double eps = sf * sf;
     const int max_iter = a.max_iter, window = a.window;
     int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
@@ -483,7 +569,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
         __syncthreads();
         if (s_flag) break;
         // w = Qḡ over the passive columns, κ = ḡᵀw, α = ‖ḡ‖²/κ (exact line search)
-        gmv(Qp, ldq, n, lp, cntL, sgb, sw, false, red);
+        product<T, CL>(Qp, ldq, n, lp, cntL, sgb, sw, false, red, xb(), rank, S);
         T kp = T(0);
         for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fma(sgb[i], sw[i], kp);
         double kap;
@@ -553,14 +639,18 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm) {
         ++iter;
         sum_clip += nclip;
         if (nclip > 0) {
-            gmv(Qp, ldq, n, lc, nclip, sw, sg, true, red);
+            if (CL && nclip <= 8)  // a few rows: every CTA forms Qe itself, no exchange
+                gmv(Qp, ldq, 0, n, lc, nclip, sw, sg, true, red);
+            else
+                product<T, CL>(Qp, ldq, n, lc, nclip, sw, sg, true, red, xb(), rank, S);
             ++clip_iters;
         }
         gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-        a.y[P.foff + i] = (double)sy[i] + (double)syl[i];
-    if (threadIdx.x == 0) {
+    if (!CL || rank == 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            a.y[P.foff + i] = (double)sy[i] + (double)syl[i];
+    if (threadIdx.x == 0 && (!CL || rank == 0)) {
         st.iters = iter;
         st.status = status;
         st.clip_iters += clip_iters;
@@ -586,14 +676,42 @@ __global__ void __launch_bounds__(kGThreads, 1) k_galg2(GSolveArgs<T> a) {
         const int p = s_p;
         __syncthreads();
         if (p < 0) break;
-        solve_one<T>(a, p, gsm);
+        solve_one<T, false>(a, p, gsm, 0, 1);
     }
 }
 
+// Large problems: one problem per thread-block cluster (launched with a
+// cluster dimension); rank 0 takes the next problem and writes its index
+// into every CTA of the cluster.
 template <typename T>
-size_t gsolve_static_bytes(int ldq) {
+__global__ void __launch_bounds__(kGThreads, 1) k_galg2c(GSolveArgs<T> a) {
+    extern __shared__ __align__(16) uint8_t gsm[];
+    __shared__ int s_p;
+    const int rank = cluster_rank(), C = cluster_ctas();
+    cluster_sync();  // every CTA of the cluster has started
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int k = atomicAdd(a.queue, 1);
+            const int p = k < a.nactive ? a.order[k] : -1;
+            for (int r = 0; r < C; ++r) st_cluster(cluster_addr(&s_p, r), p);
+        }
+        cluster_sync();
+        const int p = s_p;
+        if (p < 0) break;
+        solve_one<T, true>(a, p, gsm, rank, C);
+        // every CTA is done with s_p and with the exchange buffers before
+        // rank 0 writes the next index and the next problem reuses them
+        cluster_sync();
+    }
+}
+
+// Shared memory of solve_one besides Q_p (the cluster variant adds its two
+// exchange buffers).
+template <typename T>
+size_t gsolve_static_bytes(int ldq, bool cluster) {
     constexpr int TILE = 32 * Vec16<T>::N;
-    return (size_t)ldq * (5 * sizeof(T) + 2 * sizeof(int)) + (size_t)kGWarps * TILE * sizeof(T);
+    return (size_t)ldq * ((cluster ? 7 : 5) * sizeof(T) + 2 * sizeof(int)) +
+           (size_t)kGWarps * TILE * sizeof(T);
 }
 
 // y = x0·s (or 0), per problem.
@@ -827,6 +945,7 @@ struct GroupWork {
     int max_ldq = 0;
     std::vector<GProb> hp;        // host copy of the records
     std::vector<int> order_all;   // problems, largest n first
+    std::vector<int> run_order;   // host copy of order for the current run
     std::vector<int64_t> qexp;    // offsets of the exported packed Q blocks
 
     void* pool = nullptr;         // device: everything below
@@ -856,6 +975,11 @@ struct GroupWork {
     size_t host_bytes = 0;
     int smem_bytes = 0;
     int grid = 0;
+    int nbig = 0;                   // leading entries of order solved by clusters
+    int max_clusters = -1;          // co-resident clusters of k_galg2c (-1: not asked yet)
+    int cluster_size = 0;           // blocks per cluster that max_clusters is for
+    cudaStream_t side = nullptr;    // second stream: k_galg2 beside k_galg2c
+    cudaEvent_t fork = nullptr, join = nullptr;
     int64_t slots = 0;              // column slots of the prepare grid
     std::vector<aln_problem> last;  // records of the last layout
     int last_prec = -1;
@@ -928,11 +1052,118 @@ aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, int gmode, int max_
     a.smem_bytes = g->smem_bytes;
     G_TRY(cudaFuncSetAttribute(k_galg2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                g->smem_bytes));
-    G_TRY(cudaMemsetAsync(g->queue, 0, sizeof(int), c->stream));
+    G_TRY(cudaMemsetAsync(g->queue, 0, 2 * sizeof(int), c->stream));
+    const int nbig = std::min(g->nbig, nactive), nsmall = nactive - nbig;
+    const int CS = g->cluster_size;
+    int ncl = 0;
+    if (nbig > 0) {
+        G_TRY(cudaFuncSetAttribute(k_galg2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   g->smem_bytes));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kGThreads);
+        cfg.dynamicSmemBytes = g->smem_bytes;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (g->max_clusters < 0) {
+            cfg.gridDim = dim3(CS * (c->num_sms / CS));
+            int m = 0;
+            if (cudaOccupancyMaxActiveClusters(&m, k_galg2c<T>, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                m = 0;
+            }
+            g->max_clusters = m;
+        }
+        // clusters for the large problems in proportion to their share of
+        // the work (Σ n² per iteration), the other SMs for the rest
+        double wb = 0.0, wt = 0.0;
+        for (int k = 0; k < nactive; ++k) {
+            const double n = (double)g->hp[g->run_order[k]].n;
+            wt += n * n;
+            if (k < nbig) wb += n * n;
+        }
+        ncl = (int)std::lround(wb / std::max(wt, 1.0) * c->num_sms / CS);
+        ncl = std::max(1, std::min({ncl, nbig, g->max_clusters}));
+        if (nsmall == 0) ncl = std::min(nbig, g->max_clusters);
+        if (g->max_clusters <= 0) ncl = 0;  // no cluster fits: one kernel for all
+    }
+    if (ncl > 0) {
+        if (!g->side) {
+            G_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+            G_TRY(cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming));
+            G_TRY(cudaEventCreateWithFlags(&g->join, cudaEventDisableTiming));
+        }
+        G_TRY(cudaEventRecord(g->fork, c->stream));
+        GSolveArgs<T> b = a;
+        b.nactive = nbig;
+        b.queue = g->queue + 1;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(CS * ncl);
+        cfg.blockDim = dim3(kGThreads);
+        cfg.dynamicSmemBytes = g->smem_bytes;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        G_TRY(cudaLaunchKernelEx(&cfg, k_galg2c<T>, b));
+        c->launches += 1;
+        if (nsmall > 0) {
+            G_TRY(cudaStreamWaitEvent(g->side, g->fork, 0));
+            a.order = g->order + nbig;
+            a.nactive = nsmall;
+            const int grid = std::max(1, std::min(nsmall, g->grid - CS * ncl));
+            k_galg2<T><<<grid, kGThreads, g->smem_bytes, g->side>>>(a);
+            G_TRY(cudaGetLastError());
+            c->launches += 1;
+            G_TRY(cudaEventRecord(g->join, g->side));
+            G_TRY(cudaStreamWaitEvent(c->stream, g->join, 0));
+        }
+        return ALN_OK;
+    }
     const int grid = std::min(nactive, g->grid);
     k_galg2<T><<<grid, kGThreads, g->smem_bytes, c->stream>>>(a);
     G_TRY(cudaGetLastError());
     c->launches += 1;
+    return ALN_OK;
+}
+
+// Upload the order of the next run: the problems that clusters solve
+// (largest first) ahead of the rest (largest first); sets g->nbig.
+aln_status upload_order(aln_ctx* c, GroupWork* g, const std::vector<int>& list) {
+    const bool f64 = c->opt.precision == ALN_PREC_FP64;
+    g->run_order.clear();
+    g->nbig = 0;
+    const int cs = c->opt.group_cluster ? c->opt.group_cluster : kGCluster;
+    if (cs != g->cluster_size) {
+        g->cluster_size = cs;
+        g->max_clusters = -1;
+    }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int p : list) {
+            const GProb& P = g->hp[p];
+            const size_t T = f64 ? 8 : 4;
+            const size_t st = f64 ? gsolve_static_bytes<double>(P.ldq, true)
+                                  : gsolve_static_bytes<float>(P.ldq, true);
+            const size_t st1 = f64 ? gsolve_static_bytes<double>(P.ldq, false)
+                                   : gsolve_static_bytes<float>(P.ldq, false);
+            const bool fits = (size_t)P.n * P.ldq * T + st1 <= (size_t)g->smem_bytes;
+            const bool big = cs > 1 && P.n >= kGClusterMinN && !fits &&
+                             st <= (size_t)g->smem_bytes && g->max_clusters != 0;
+            if (big == (pass == 0)) g->run_order.push_back(p);
+            if (pass == 0 && big) g->nbig = (int)g->run_order.size();
+        }
+    if (g->run_order.empty()) return ALN_OK;
+    G_TRY(cudaMemcpyAsync(g->order, g->run_order.data(), g->run_order.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, c->stream));
     return ALN_OK;
 }
 
@@ -976,6 +1207,9 @@ void group_free(aln_ctx* c) {
     if (g->pool) cudaFree(g->pool);
     if (g->copies) cudaFree(g->copies);
     if (g->host) cudaFreeHost(g->host);
+    if (g->fork) cudaEventDestroy(g->fork);
+    if (g->join) cudaEventDestroy(g->join);
+    if (g->side) cudaStreamDestroy(g->side);
     delete g;
     c->group = nullptr;
     c->grouped = 0;
@@ -1153,8 +1387,8 @@ static aln_status group_layout(aln_ctx* c, GroupWork* g, int32_t count, const al
     int optin = 0;
     G_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     g->smem_bytes = optin - 1024;  // static shared memory of the kernel
-    const size_t need = f64 ? gsolve_static_bytes<double>(g->max_ldq)
-                            : gsolve_static_bytes<float>(g->max_ldq);
+    const size_t need = f64 ? gsolve_static_bytes<double>(g->max_ldq, false)
+                            : gsolve_static_bytes<float>(g->max_ldq, false);
     if ((size_t)g->smem_bytes < need) return ALN_ERR_UNSUPPORTED;
     g->grid = c->num_sms;
     g->slots = slot;
@@ -1296,8 +1530,7 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
                                                         : c->opt.refine_gain));
     G_TRY(cudaGetLastError());
     c->launches += 1;
-    G_TRY(cudaMemcpyAsync(g->order, g->order_all.data(), (size_t)count * sizeof(int),
-                          cudaMemcpyHostToDevice, c->stream));
+    G_CHECK(upload_order(c, g, g->order_all));
     HostView h = host_view(g);
     std::vector<int> next;
     next.reserve(count);
@@ -1329,8 +1562,7 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
             if (h.again[p]) next.push_back(p);
         if (next.empty()) break;
         nactive = (int)next.size();
-        G_TRY(cudaMemcpyAsync(g->order, next.data(), (size_t)nactive * sizeof(int),
-                              cudaMemcpyHostToDevice, c->stream));
+        G_CHECK(upload_order(c, g, next));
         gmode = 1;
     }
     // results

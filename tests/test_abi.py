@@ -63,6 +63,12 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     o.precision = 7
     ctx = ctypes.c_void_p()
     assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
+    # option checks come before any CUDA call
+    for field, bad in (("gram_split", 4), ("group_cluster", 3), ("group_cluster", 16),
+                       ("refine_gain", 17), ("iter_kernel", 3)):
+        o = aln.aln_default_options()
+        setattr(o, field, bad)
+        assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
     lib.aln_destroy(None)  # accepted
 
 

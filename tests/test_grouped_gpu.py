@@ -45,7 +45,9 @@ def _problems(sizes, seed, dtype=np.float32, zero_frac=0.6):
 
 
 # Ragged in n (1, inside a tile, tile edges 128/129, several tiles, past the
-# shared-memory staging size) and in d (not multiples of 64, d < 64).
+# shared-memory staging size) and in d (not multiples of 64, d < 64).  The two
+# problems with n ≥ 512 whose Q does not fit in one block's shared memory
+# (700, 1030) are solved by thread-block clusters, concurrently with the rest.
 SIZES = [(3, 1), (70, 5), (62, 31), (100, 32), (300, 127), (256, 128), (400, 129),
          (500, 200), (777, 257), (900, 300), (2100, 700), (1100, 1030)]
 
@@ -102,7 +104,7 @@ def test_grouped_solve_matches_oracle(aln):
 
 
 def test_grouped_fp64_matches_oracle(aln):
-    sizes = [(40, 1), (90, 31), (300, 129), (600, 257), (500, 200)]
+    sizes = [(40, 1), (90, 31), (300, 129), (600, 257), (500, 200), (1300, 600)]
     probs = _problems(sizes, 43, dtype=np.float64, zero_frac=0.5)
     with aln.Solver("fp64") as s:
         s.prepare_grouped(probs)
@@ -115,6 +117,24 @@ def test_grouped_fp64_matches_oracle(aln):
         assert abs(F - Fs) <= 1e-10 * Fs + 1e-30  # F* = 0 when b = 0
         if np.abs(x_star).max() > 0:
             assert np.abs(x - x_star).max() / np.abs(x_star).max() <= 1e-8
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_grouped_cluster_sizes(aln, cluster):
+    """Every cluster size (1 = single blocks only) meets the tolerance by the
+    oracle's KKT residual and reaches the oracle's optimum; the large problems
+    (n = 700, 1030, 1500) run on clusters beside the small ones."""
+    probs = _problems([(2100, 700), (1100, 1030), (60, 20), (3000, 1500), (400, 129),
+                       (1200, 513)], 47)
+    with aln.Solver("split_bf16", group_cluster=cluster) as s:
+        s.prepare_grouped(probs)
+        X, info = s.solve(tol=1e-9, max_iter=200000)
+    for p, ((A, b), x) in enumerate(zip(probs, X)):
+        A64, b64 = A.astype(np.float64), b.astype(np.float64)
+        rel, _ = O.kkt_residual(A64, b64, x)
+        assert rel <= 1e-9, (cluster, p, A.shape, rel, info[p])
+        x_star, _, _, _ = O.reference_solution(A64, b64)
+        assert np.linalg.norm(x - x_star) <= 1e-5 * max(np.linalg.norm(x_star), 1e-300), p
 
 
 def test_grouped_agrees_with_single_problem_path(aln):
