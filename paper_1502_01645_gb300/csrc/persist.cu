@@ -596,27 +596,77 @@ __device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb
     __syncthreads();
 }
 
+// One block reduction for the update step: the FP32 value v (partials in T
+// within warps, the 32 warp partials added in FP64 by warp 0, the same tree
+// as block_sum_td) and two counts.  sd holds 33 doubles, si 66 ints.
+template <typename T>
+__device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* si, double* v_out,
+                                           int* a_out, int* b_out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum_t(v);
+    a = warp_sum_i(a);
+    b = warp_sum_i(b);
+    __syncthreads();  // earlier readers of sd / si are done
+    if (lane == 0) {
+        sd[wid] = (double)v;
+        si[wid] = a;
+        si[32 + wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        double x = lane < nw ? sd[lane] : 0.0;
+        int xa = lane < nw ? si[lane] : 0, xb = lane < nw ? si[32 + lane] : 0;
+        x = warp_sum(x);
+        xa = warp_sum_i(xa);
+        xb = warp_sum_i(xb);
+        if (lane == 0) {
+            sd[32] = x;
+            si[64] = xa;
+            si[65] = xb;
+        }
+    }
+    __syncthreads();
+    *v_out = sd[32];
+    *a_out = si[64];
+    *b_out = si[65];
+}
+
 constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
 
-// dst[j] (+)= Σ_r part[r][j] for j < n, r in order; four elements per thread
-// per pass so that their R loads are in flight together.
+// dst[j] (+)= Σ_r part[r][j] for j < n, r in order.  16-byte loads, two
+// vectors per thread per pass, so that for n up to 8·blockDim.x (FP32) one
+// pass issues all of a thread's loads at once (the partials were written by
+// other SMs: each round trip is a full L2 latency).  Rows of part are ldq
+// long (a multiple of the vector width) and fully written, so the vector
+// loads stay in bounds.
 template <typename T>
 __device__ __forceinline__ void sum_partials(const T* __restrict__ part, int R, int64_t ldq,
                                              int n, T* dst, bool accumulate) {
-    for (int j0 = threadIdx.x; j0 < n; j0 += 4 * blockDim.x) {
-        T v[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 4
-        for (int r = 0; r < R; ++r) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    const int nv = (n + VN - 1) / VN;
+    for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
+        const int v1 = v0 + blockDim.x;
+        T a0[VN], a1[VN];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = j0 + u * blockDim.x;
-                if (j < n) v[u] += __ldcg(part + (int64_t)r * ldq + j);
+        for (int c = 0; c < VN; ++c) a0[c] = a1[c] = T(0);
+#pragma unroll 2
+        for (int r = 0; r < R; ++r) {
+            const V* row = reinterpret_cast<const V*>(part + (int64_t)r * ldq);
+            const V x0 = __ldcg(row + v0);
+            const V x1 = v1 < nv ? __ldcg(row + v1) : V{};
+#pragma unroll
+            for (int c = 0; c < VN; ++c) {
+                a0[c] += vget(x0, c);
+                a1[c] += vget(x1, c);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u * blockDim.x;
-            if (j < n) dst[j] = accumulate ? dst[j] + v[u] : v[u];
+        for (int c = 0; c < VN; ++c) {
+            const int j0 = v0 * VN + c, j1 = v1 * VN + c;
+            if (j0 < n) dst[j0] = accumulate ? dst[j0] + a0[c] : a0[c];
+            if (v1 < nv && j1 < n) dst[j1] = accumulate ? dst[j1] + a1[c] : a1[c];
         }
     }
 }
@@ -687,6 +737,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     __shared__ double sd[32];
     __shared__ int si[32];
     __shared__ double s_t[33];
+    __shared__ int s_i3[66];
     __shared__ T s_alpha;
     __shared__ int s_flag;   // 0 continue, 1 stop
     __shared__ int s_clip[kLocalClip];
@@ -783,7 +834,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         if (s_flag) break;
         const T aT = s_alpha;
         sum_passive += cnt;
-        int clipped = 0;
+        // The mask of the new point is formed in the same pass; it is final
+        // when nothing was clipped (then g needs no correction).
+        int clipped = 0, cP = 0;
+        T v2 = T(0);
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const T yi = sy[j];
             const T step = aT * sgb[j];
@@ -794,12 +848,19 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 yn = T(0);
                 ++clipped;
             }
+            const T gn = sg[j] - aT * sw[j];
             sy[j] = yn;
-            sg[j] = sg[j] - aT * sw[j];
+            sg[j] = gn;
             sw[j] = ej;  // w is consumed; the buffer now holds e
+            const bool P = yn > T(0) || gn < T(0);
+            const T gb = P ? gn : T(0);
+            sgb[j] = gb;
+            v2 = fma(gb, gb, v2);
+            cP += P ? 1 : 0;
         }
-        const int nclip = block_sum_bcast_i(clipped, si);  // identical in every block
-        __syncthreads();
+        double gam2;
+        int cnt2, nclip;
+        block_sum3<T>(v2, cP, clipped, s_t, s_i3, &gam2, &cnt2, &nclip);  // identical in every block
         ++iter;
         sum_clip += nclip;
         lap(2);
@@ -824,7 +885,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             ++nclip_iters;
         }
         lap(3);
-        mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+        if (nclip > 0) {
+            mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+        } else {
+            gam = gam2;
+            cnt = cnt2;
+        }
         lap(4);
     }
 
