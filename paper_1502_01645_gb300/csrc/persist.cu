@@ -576,26 +576,6 @@ __device__ __forceinline__ double block_sum_td(T v, double* sc) {
     return sc[32];
 }
 
-// Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
-// (fixed reduction tree, identical in every block).
-template <typename T>
-__device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, double* st,
-                                         int* si, double* g2_out, int* cnt_out) {
-    T v = T(0);
-    int c = 0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const T yi = sy[j], gi = sg[j];
-        const bool P = yi > T(0) || gi < T(0);
-        const T gb = P ? gi : T(0);
-        sgb[j] = gb;
-        v = fma(gb, gb, v);
-        c += P ? 1 : 0;
-    }
-    *g2_out = block_sum_td<T>(v, st);
-    *cnt_out = block_sum_bcast_i(c, si);
-    __syncthreads();
-}
-
 // One block reduction for the update step: the FP32 value v (partials in T
 // within warps, the 32 warp partials added in FP64 by warp 0, the same tree
 // as block_sum_td) and two counts.  sd holds 33 doubles, si 66 ints.
@@ -632,6 +612,25 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
     *b_out = si[65];
 }
 
+// Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
+// (fixed reduction tree, identical in every block; si holds 66 ints).
+template <typename T>
+__device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, double* st,
+                                         int* si, double* g2_out, int* cnt_out) {
+    T v = T(0);
+    int c = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const T yi = sy[j], gi = sg[j];
+        const bool P = yi > T(0) || gi < T(0);
+        const T gb = P ? gi : T(0);
+        sgb[j] = gb;
+        v = fma(gb, gb, v);
+        c += P ? 1 : 0;
+    }
+    int unused;
+    block_sum3<T>(v, c, 0, st, si, g2_out, cnt_out, &unused);
+}
+
 constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
 
 // dst[j] (+)= Σ_r part[r][j] for j < n, r in order.  16-byte loads, two
@@ -642,12 +641,14 @@ constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
 // loads stay in bounds.
 template <typename T>
 __device__ __forceinline__ void sum_partials(const T* __restrict__ part, int R, int64_t ldq,
-                                             int n, T* dst, bool accumulate) {
+                                             int n, T* dst, bool accumulate, int t0 = 0) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     const int nv = (n + VN - 1) / VN;
-    for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * blockDim.x) {
-        const int v1 = v0 + blockDim.x;
+    const int tid = (int)threadIdx.x - t0, nt = (int)blockDim.x - t0;  // threads t0.. take part
+    if (tid < 0) return;
+    for (int v0 = tid; v0 < nv; v0 += 2 * nt) {
+        const int v1 = v0 + nt;
         T a0[VN], a1[VN];
 #pragma unroll
         for (int c = 0; c < VN; ++c) a0[c] = a1[c] = T(0);
@@ -754,7 +755,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     __syncthreads();
     double gam;  // step scalars in FP64, accumulated from FP32 partials
     int cnt;
-    mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+    mask_all(n, sy, sg, sgb, s_t, s_i3, &gam, &cnt);
 
     // Scalar control state lives in thread 0 (FP64 compares and the division
     // are issued once, not by every thread).
@@ -811,7 +812,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         if (!(ok = grid_barrier(a.sync, bar += G))) break;
         lap(1);
 
-        // every block: κ, w, α, projected update, gradient update
+        // every block: κ (warp 0) while the other warps gather w, α,
+        // projected update, gradient update
         if (threadIdx.x < 32) {
             double k2 = 0.0;
             for (int i = threadIdx.x; i < items; i += 32) k2 += __ldcg(kitem + i);
@@ -829,7 +831,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 s_flag = stop;
             }
         }
-        sum_partials(part, a.R, a.ldq, n, sw, false);
+        sum_partials(part, a.R, a.ldq, n, sw, false, 32);
         __syncthreads();
         if (s_flag) break;
         const T aT = s_alpha;
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         }
         lap(3);
         if (nclip > 0) {
-            mask_all(n, sy, sg, sgb, s_t, si, &gam, &cnt);
+            mask_all(n, sy, sg, sgb, s_t, s_i3, &gam, &cnt);
         } else {
             gam = gam2;
             cnt = cnt2;
