@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lopsided_single")
+    ap.add_argument("--algorithm", choices=["antilop", "anti_acc"], default="antilop",
+                    help="solver after the scaling: Alg. 2 (antilop) or Anti+Acc (§5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
@@ -199,11 +201,17 @@ def cpu_sample(w, p):
         m = max(1, w["n"] // 2)
         A64 = np.asarray(p.A[:, :m], dtype=np.float64, order="F")
         b64 = np.asarray(p.B[0], dtype=np.float64)
+        acc = w.get("algorithm") == "anti_acc"
         t0 = time.perf_counter()
-        O.antilop(A64, b64, tol=w["tol"])
+        if acc:
+            from oracle import acc as AC
+            AC.anti_acc(A64, b64, tol=w["tol"], max_iter=400000)
+        else:
+            O.antilop(A64, b64, tol=w["tol"])
         t = time.perf_counter() - t0
         scale = (w["n"] / m) ** 2
-        return t * scale, (f"oracle antilop on A[:, :{m}] (d={w['d']}) in {t:.2f} s, "
+        name = "anti_acc" if acc else "antilop"
+        return t * scale, (f"oracle {name} on A[:, :{m}] (d={w['d']}) in {t:.2f} s, "
                            f"x (n/m)^2 = {scale:.0f} for the full size")
     A64 = np.asarray(p.A, dtype=np.float64, order="F")
     s = 16
@@ -283,6 +291,9 @@ def run_ours(args):
     aln.load()
 
     w = workload(args)
+    w["algorithm"] = args.algorithm
+    if args.algorithm == "anti_acc" and w["name"] in ("uneven_batch", "warmstart"):
+        raise SystemExit("--algorithm anti_acc runs on the single-problem workloads only")
     if w["name"] == "uneven_batch":
         return run_grouped(args, w, world, rank, local)
     if w["name"] == "warmstart":
@@ -294,8 +305,9 @@ def run_ours(args):
     Bt = torch.from_numpy(np.ascontiguousarray(B_np)).cuda()
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
+    alg = aln.ALG_ANTI_ACC if args.algorithm == "anti_acc" else aln.ALG_ANTILOP
     solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+                        gram_split=args.gram_split, algorithm=alg)
 
     def step():
         solver.prepare(At, Bt)
@@ -349,7 +361,7 @@ def run_ours(args):
         X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5))
         hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+                             gram_split=args.gram_split, algorithm=alg)
         hsolver.prepare(A_h, B_h)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -422,7 +434,9 @@ def run_ours(args):
         esz = 8 if w["prec"] == "fp64" else 4
         qbytes = esz * n * avg(lambda s: s.passive_rows + s.clipped_rows)  # §4.2: n·S(n)
         ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
-        rooflines.append({"bound": "hbm", "kernel": "k_alg2_repl (persistent Alg. 2 loop)",
+        kname = ("k_acc_repl (persistent Anti+Acc loop)" if alg == aln.ALG_ANTI_ACC else
+                 "k_alg2_repl (persistent Alg. 2 loop)")
+        rooflines.append({"bound": "hbm", "kernel": kname,
                           "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                           "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
                           "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
@@ -455,9 +469,16 @@ def run_ours(args):
         "dtype": "f64" if w["prec"] == "fp64" else "bf16 split + f32", "data": "synthetic",
         "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
                    "seed": w["seed"],
-                   "form": ("FP64 Gram + FP64 Alg. 2" if w["prec"] == "fp64" else
-                            "3-term split-BF16 tcgen05 Gram, FP32 Alg. 2, "
-                            "FP64 scale/KKT/refinement"),
+                   "form": (("FP64 Gram + FP64 " if w["prec"] == "fp64" else
+                             "3-term split-BF16 tcgen05 Gram, FP32 ")
+                            + ("Anti+Acc (power iteration for L, Nesterov projected "
+                               "gradient step 1/L)" if alg == aln.ALG_ANTI_ACC else "Alg. 2")
+                            + ("" if w["prec"] == "fp64" else
+                               ", FP64 scale/KKT/refinement")),
+                   "algorithm": args.algorithm,
+                   "lipschitz": (stats[-1].lipschitz if alg == aln.ALG_ANTI_ACC else None),
+                   "power_products": (int(stats[-1].power_products)
+                                      if alg == aln.ALG_ANTI_ACC else None),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2" if A_np.nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",
@@ -467,7 +488,9 @@ def run_ours(args):
                    "rel_kkt_max": worst,
                    "phase_us_per_iteration": (
                        None if k != 1 or stats[-1].iterations == 0 else
-                       dict(zip(("product", "barrier", "update", "clipped", "mask"),
+                       dict(zip(("step", "product", "barrier", "gather_mask", "unused")
+                                if alg == aln.ALG_ANTI_ACC else
+                                ("product", "barrier", "update", "clipped", "mask"),
                                 [round(stats[-1].phase_us[i] / stats[-1].iterations, 3)
                                  for i in range(5)])))},
         "roofline": rooflines[0],

@@ -72,6 +72,29 @@ typedef enum aln_precision {
 
 typedef enum aln_dtype { ALN_DTYPE_F32 = 0, ALN_DTYPE_F64 = 1 } aln_dtype;
 
+/* Solver run after the scaling of Alg. 1 (§3). */
+typedef enum aln_algorithm {
+    /* Alg. 2 (§3): projected gradient on the passive set with the exact line
+     * search α = ‖ḡ‖²/ḡᵀQḡ (the paper's method; default). */
+    ALN_ALG_ANTILOP = 0,
+    /* Anti+Acc (§5): Nesterov's accelerated projected gradient with the
+     * constant step 1/L, L = λ_max(Q) from a power iteration; the paper names
+     * it as a compared variant without printing its update rule, which is
+     * read as the optimal gradient method it cites (Guan et al., 2012):
+     * x_k = [Y_k − ∇f(Y_k)/L]₊, α_{k+1} = (1 + √(4α_k² + 1))/2,
+     * Y_{k+1} = x_k + ((α_k − 1)/α_{k+1})(x_k − x_{k−1}), α_0 = 1.  Same stop
+     * rule and FP64 refinement as Alg. 2 (a refinement round restarts the
+     * momentum); since ‖ḡ‖ of this method is not monotone, an FP32 inner run
+     * takes 10 × stagnation iterations without a new best ‖ḡ‖² to stagnate,
+     * and the FP64 iteration never stagnates.  Single-problem path only (aln_prepare with fewer than
+     * batch_min right-hand sides, or FP64), and only while x_k, x_{k−1}, both
+     * gradients (and in SPLIT_BF16 the low parts of the double-float x and
+     * the step) fit in one SM's shared memory (n up to about 7 500 in
+     * SPLIT_BF16, 6 000 in FP64); otherwise aln_solve returns
+     * ALN_ERR_UNSUPPORTED. */
+    ALN_ALG_ANTI_ACC = 1
+} aln_algorithm;
+
 /* Per right-hand-side outcome, reported in aln_solve_info.status. */
 typedef enum aln_rhs_status {
     ALN_RHS_CONVERGED = 0,     /* ‖ḡ‖ ≤ tol·‖min(q,0)‖ in the FP64 check */
@@ -113,6 +136,8 @@ typedef struct aln_options {
                              larger than one block's shared memory) while
                              single blocks take the rest; 1 = no clusters, 2, 4
                              or 8; 0 = default 4 */
+    int32_t algorithm;    /* aln_algorithm; default ALN_ALG_ANTILOP */
+    int32_t reserved;
 } aln_options;
 
 typedef struct aln_solve_info {
@@ -293,6 +318,9 @@ typedef struct aln_stats {
     double product_bytes;    /* algorithmic bytes of Q the Alg. 2 products of the
                                 last aln_solve read: Σ_k n·(|P_k| + |C_k|)·sizeof
                                 (summed over problems in grouped mode) */
+    double lipschitz;        /* ALN_ALG_ANTI_ACC: L = λ_max(Q) estimate of the power
+                                iteration for the prepared Q (0 before the first solve) */
+    int64_t power_products;  /* products Qv that power iteration took */
 } aln_stats;
 
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */

@@ -20,6 +20,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_NOT_PREPARED, ERR_NONFINITE = 1, 2, 3
 ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = 4, 5, 6, 7
 PREC_FP64, PREC_SPLIT_BF16 = 0, 1
+ALG_ANTILOP, ALG_ANTI_ACC = 0, 1
 DTYPE_F32, DTYPE_F64 = 0, 1
 RHS_CONVERGED, RHS_EMPTY_PASSIVE, RHS_CURVATURE = 0, 1, 2
 RHS_MAXITER, RHS_NONFINITE, RHS_STAGNATED = 3, 4, 5
@@ -39,7 +40,8 @@ class AlnOptions(ctypes.Structure):
                 ("persist_blocks", ctypes.c_int32), ("row_groups", ctypes.c_int32),
                 ("stagnation", ctypes.c_int32), ("iter_kernel", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32),
-                ("gram_split", ctypes.c_int32), ("group_cluster", ctypes.c_int32)]
+                ("gram_split", ctypes.c_int32), ("group_cluster", ctypes.c_int32),
+                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class AlnSolveInfo(ctypes.Structure):
@@ -55,7 +57,8 @@ class AlnStats(ctypes.Structure):
                 ("iterate_ms", ctypes.c_double), ("passive_rows", ctypes.c_int64),
                 ("clipped_rows", ctypes.c_int64), ("persist_blocks", ctypes.c_int32),
                 ("clipped_iterations", ctypes.c_int32), ("phase_us", ctypes.c_double * 5),
-                ("product_bytes", ctypes.c_double)]
+                ("product_bytes", ctypes.c_double), ("lipschitz", ctypes.c_double),
+                ("power_products", ctypes.c_int64)]
 
 
 class AlnProblem(ctypes.Structure):

@@ -163,16 +163,19 @@ aln_status alloc_workspace(aln_ctx* c) {
     return ALN_OK;
 }
 
-// One launch of the persistent Alg. 2 kernel: it loops on the device until a
-// stop rule fires (the state's eps, max_iter and stagnation window were set
-// by the set-up kernels) and leaves the outcome in the iteration state.  The
-// barrier words and tile tickets are cleared first, so a previous timeout
-// cannot leak into this run.
+// One launch of the persistent Alg. 2 (or Anti+Acc) kernel: it loops on the
+// device until a stop rule fires (the state's eps, max_iter and stagnation
+// window were set by the set-up kernels) and leaves the outcome in the
+// iteration state.  The barrier words and tile tickets are cleared first, so
+// a previous timeout cannot leak into this run.
 aln_status run_until_done(aln_ctx* c) {
     ALN_TRY(cudaMemsetAsync(c->p_sync, 0, persist_sync_bytes(), c->stream));
     ALN_TRY(cudaMemsetAsync(c->p_ticket, 0, (size_t)c->p_CT * sizeof(unsigned int), c->stream));
     ALN_TRY(cudaEventRecord(c->ev[6], c->stream));
-    ALN_TRY(fp64(c) ? launch_alg2_persist<double>(c) : launch_alg2_persist<float>(c));
+    if (c->opt.algorithm == ALN_ALG_ANTI_ACC)
+        ALN_TRY(fp64(c) ? launch_acc_persist<double>(c) : launch_acc_persist<float>(c));
+    else
+        ALN_TRY(fp64(c) ? launch_alg2_persist<double>(c) : launch_alg2_persist<float>(c));
     ALN_TRY(cudaEventRecord(c->ev[7], c->stream));
     c->launches += 1;
     ALN_TRY(cudaMemcpyAsync(c->st_host, c->st, sizeof(IterState), cudaMemcpyDeviceToHost,
@@ -189,6 +192,33 @@ aln_status run_until_done(aln_ctx* c) {
         for (int k = 0; k < 5; ++k) c->stats.phase_us[k] += 1e-3 * (double)c->st_host->phase_ns[k];
         c->stats.clipped_iterations += (int32_t)c->st_host->phase_ns[5];
     }
+    return ALN_OK;
+}
+
+// Anti+Acc: L = λ_max(Q) of the prepared Q by the power iteration, once per
+// prepare.  Needs the replicated layout (else ALN_ERR_UNSUPPORTED).
+aln_status ensure_lipschitz(aln_ctx* c) {
+    if (c->lipschitz > 0.0) return ALN_OK;
+    const bool f64 = fp64(c);
+    const size_t need = acc_smem_need(f64, c->ldq) + 4096;
+    int optin = 0;
+    ALN_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (!c->p_repl || need > (size_t)optin) return ALN_ERR_UNSUPPORTED;
+    ALN_TRY(cudaMemsetAsync(c->p_sync, 0, persist_sync_bytes(), c->stream));
+    const double tol = f64 ? 1e-7 : 1e-6;  // FP32 quotients carry ~1e-7 noise
+    ALN_TRY(f64 ? launch_power<double>(c, tol, 500, c->kkt_out)
+                : launch_power<float>(c, tol, 500, c->kkt_out));
+    c->launches += 1;
+    ALN_TRY(cudaMemcpyAsync(c->kkt_out_host, c->kkt_out, 2 * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    const double rho = c->kkt_out_host[0], steps = c->kkt_out_host[1];
+    if (steps < 0.0) return ALN_ERR_TIMEOUT;
+    if (!std::isfinite(rho)) return ALN_ERR_NONFINITE;
+    c->lipschitz = rho > 0.0 ? rho : 1.0;  // Q = 0: any step (the gradient is q)
+    c->power_products = (int)steps;
+    c->stats.lipschitz = c->lipschitz;
+    c->stats.power_products = c->power_products;
     return ALN_OK;
 }
 
@@ -239,6 +269,7 @@ void aln_default_options(aln_options* opt) {
     opt->refine_gain = 0;
     opt->gram_split = 3;
     opt->group_cluster = 4;
+    opt->algorithm = ALN_ALG_ANTILOP;
 }
 
 int32_t aln_version(void) { return ALN_VERSION; }
@@ -273,6 +304,8 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.refine_gain > 16) return ALN_ERR_INVALID_ARG;
     if (o.gram_split == 0) o.gram_split = 3;
     if (o.gram_split != 2 && o.gram_split != 3) return ALN_ERR_INVALID_ARG;
+    if (o.algorithm != ALN_ALG_ANTILOP && o.algorithm != ALN_ALG_ANTI_ACC)
+        return ALN_ERR_INVALID_ARG;
     if (o.group_cluster == 0) o.group_cluster = 4;
     if (o.group_cluster != 1 && o.group_cluster != 2 && o.group_cluster != 4 &&
         o.group_cluster != 8)
@@ -400,7 +433,11 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     // Many right-hand sides in mixed precision: the batched solver (batch.cu)
     // forms Q in FP64 once (it also serves the FP64 checks) and iterates all
     // columns together with tensor-core products.
-    c->batched = (!f64 && k >= c->opt.batch_min) ? 1 : 0;
+    c->batched = (!f64 && k >= c->opt.batch_min && c->opt.algorithm == ALN_ALG_ANTILOP) ? 1 : 0;
+    c->lipschitz = -1.0;  // Q changes: the Anti+Acc step is estimated again
+    c->power_products = 0;
+    c->stats.lipschitz = 0.0;
+    c->stats.power_products = 0;
 
     // split copies for the tensor-core Gram
     __nv_bfloat16 *hi = nullptr, *mid = nullptr, *lo = nullptr;
@@ -474,6 +511,7 @@ aln_status aln_prepare_grouped(aln_ctx* c, int32_t count, const aln_problem* pro
         cols += q.n;
     }
     if (cols > ((int64_t)1 << 31) / 128) return ALN_ERR_INVALID_ARG;
+    if (c->opt.algorithm != ALN_ALG_ANTILOP) return ALN_ERR_UNSUPPORTED;
     c->prepared = 0;
     c->batched = 0;
     c->grouped = 0;
@@ -527,6 +565,7 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
         if (cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) c->stats.solve_ms = ms;
         return ALN_OK;
     }
+    if (c->opt.algorithm == ALN_ALG_ANTI_ACC) ALN_CHECK(ensure_lipschitz(c));
     // Inner runs stop a little below tol so that the FP64 check usually passes
     // at once; refinement rounds aim lower still.
     const double first_factor = 0.5, refine_factor = 0.25;

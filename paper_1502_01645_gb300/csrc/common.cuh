@@ -251,6 +251,8 @@ struct aln_ctx {
     // persistent Alg. 2 kernel geometry and its per-tile partials
     int p_CT = 0, p_R = 0, p_G = 0;
     int p_repl = 0;  // 1: replicated-state kernel (vectors fit in shared memory)
+    double lipschitz = -1.0;  // Anti+Acc: L = λ_max(Q) estimate (< 0: not computed)
+    int power_products = 0;   // products of the power iteration that gave it
     double* p_gpart = nullptr;
     int* p_cpart = nullptr;
     double* p_kpart = nullptr;

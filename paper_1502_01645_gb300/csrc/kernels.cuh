@@ -129,6 +129,14 @@ cudaError_t launch_state_reset(aln_ctx* c, double eps, int max_iter);
 // persist.cu — the whole Alg. 2 loop as one cooperative persistent kernel
 template <typename T>
 cudaError_t launch_alg2_persist(aln_ctx* c);
+// Anti+Acc (§5) iteration on the prepared state (persist.cu).
+template <typename T>
+cudaError_t launch_acc_persist(aln_ctx* c);
+// Shared memory the Anti+Acc kernel needs for row length ldq (persist.cu).
+size_t acc_smem_need(bool f64, int64_t ldq);
+// Power iteration for λ_max(Q): out[0] = ρ, out[1] = products (persist.cu).
+template <typename T>
+cudaError_t launch_power(aln_ctx* c, double tol, int max_steps, double* out);
 template <typename T>
 int persist_max_blocks(int num_sms, int64_t ldq, int* repl);
 size_t persist_sync_bytes();

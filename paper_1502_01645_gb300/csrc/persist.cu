@@ -449,10 +449,12 @@ struct ReplArgs {
 
 // Partial Σ_{j ∈ group rg, v_j ≠ 0} v_j Q[j, tile ct] with v in shared memory;
 // written to dst[rg][tile]; returns the partial in threads < TILE.
-template <typename T>
+template <typename T, bool DIFF = false>
 __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, int n,
                                          int rows_per_group, const T* v, int ct, int rg,
-                                         T* __restrict__ dst, T* red) {
+                                         T* __restrict__ dst, T* red,
+                                         const double* __restrict__ add = nullptr,
+                                         const T* vsub = nullptr) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
@@ -468,7 +470,8 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
     for (int c = 0; c < VN; ++c) acc[c] = T(0);
     for (int base = r0; base < r1; base += 32) {
         const int jl = base + lane;
-        const T vl = jl < r1 ? v[jl] : T(0);
+        // the multiplied vector is v, or v − vsub (DIFF)
+        const T vl = jl < r1 ? (DIFF ? v[jl] - vsub[jl] : v[jl]) : T(0);
         unsigned int m = __ballot_sync(0xffffffffu, vl != T(0));
         while (m) {  // warp-uniform
             T vv[kPU];
@@ -478,7 +481,7 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
                 if (m) {
                     const int src = __ffs(m) - 1;
                     m &= m - 1;
-                    vv[u] = v[base + src];
+                    vv[u] = DIFF ? __shfl_sync(0xffffffffu, vl, src) : v[base + src];
                     qq[u] = __ldg(reinterpret_cast<const V*>(Q + (int64_t)(base + src) * ldq + col));
                 } else {
                     vv[u] = T(0);
@@ -498,7 +501,10 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
     if (threadIdx.x < TILE) {
 #pragma unroll 8
         for (int w2 = 0; w2 < kPWarps; ++w2) s += red[w2 * TILE + threadIdx.x];
-        __stcg(dst + (int64_t)rg * ldq + (int64_t)ct * TILE + threadIdx.x, s);
+        // `add` (a vector of n entries) joins the partial of row group 0
+        const int64_t i = (int64_t)ct * TILE + threadIdx.x;
+        if (add && rg == 0 && i < n) s += (T)add[i];
+        __stcg(dst + (int64_t)rg * ldq + i, s);
     }
     __syncthreads();
     return s;
@@ -1002,6 +1008,397 @@ int persist_max_blocks(int num_sms, int64_t ldq, int* repl) {
     }
     return per_sm * num_sms;
 }
+
+// ===========================================================================
+// Anti+Acc (§5): the scaling of Alg. 1 followed by Nesterov's accelerated
+// projected gradient with the constant step 1/L (the optimal gradient method
+// the paper cites for its accelerated baselines), in the replicated-state
+// layout of k_alg2_repl: every block keeps x_k, x_{k−1}, ∇f(x_k), ∇f(x_{k−1})
+// in shared memory and repeats the elementwise work; only the product
+// ∇f(x_k) = Qx_k + q crosses blocks (partials, one grid barrier, gather).
+//
+//   Y_k     = x_{k−1} + β (x_{k−1} − x_{k−2}),  β = (α_{k−1} − 1)/α_k
+//   ∇f(Y_k) = ∇f(x_{k−1}) + β (∇f(x_{k−1}) − ∇f(x_{k−2}))   (f is quadratic)
+//   x_k     = [Y_k − ∇f(Y_k)/L]₊,  α_{k+1} = (1 + √(4α_k² + 1))/2
+//
+// with x_{−1} = x_{−2} = y⁰ and α_0 = 1 (so the first two steps carry no
+// momentum).  The stop rule is Alg. 2's at x_k: ‖ḡ(x_k)‖² < ε or P = ∅.  The
+// momentum scalars are FP64 in thread 0.  The gradient is carried the way
+// Alg. 2 carries it, ∇f(x_k) = ∇f(x_{k−1}) + Q(x_k − x_{k−1}): in FP32 a
+// fresh Qx_k + q would put a floor of about 10⁻⁷·‖Q‖‖x‖ under ‖ḡ‖ that the
+// FP64 refinement could not lower, whereas the increments shrink with the
+// steps, so each refinement round (restarting from the exact FP64 gradient)
+// gains accuracy.
+// ===========================================================================
+template <typename T>
+struct AccArgs {
+    const T* Q;
+    int64_t ldq;
+    int n;
+    int CT;
+    int R;
+    int rows_per_group;
+    T* y;             // in/out (global): start point, then x at the stop
+    T* g;             // in/out (global): ∇f there
+    T* part;          // 2 × R × ldq (partials of Qx + q, by iteration parity)
+    double inv_L;     // 1/L
+    int window;       // stagnation window (iterations without a new best ‖ḡ‖²)
+    PersistSync* sync;
+    IterState* st;
+};
+
+// ḡ over the replicated vectors: ‖ḡ‖², |P| and the number of non-zero
+// entries of the last step d (the rows of Q its product read).
+template <typename T>
+__device__ __forceinline__ void acc_mask(int n, const T* sx, const T* sg, const T* sd_or_x,
+                                         const T* sxp, double* sd, int* si, double* g2, int* cnt,
+                                         int* nnz) {
+    T v = T(0);
+    int cp = 0, cz = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const T xj = sx[j], gj = sg[j];
+        const bool P = xj > T(0) || gj < T(0);
+        const T gb = P ? gj : T(0);
+        v = fma(gb, gb, v);
+        cp += P ? 1 : 0;
+        const T dj = sxp ? sd_or_x[j] - sxp[j] : sd_or_x[j];
+        cz += dj != T(0) ? 1 : 0;
+    }
+    block_sum3<T>(v, cp, cz, sd, si, g2, cnt, nnz);
+}
+
+// FP32: the iterate is a pair x = xh + xl (|xl| ≤ ulp(xh)/2), as in the
+// grouped Alg. 2 kernel: the steps ∇f/L of the accelerated method are far
+// below ulp(x) near the optimum and would be lost in an FP32 x.  The step
+// d = x_k − x_{k−1} is kept in its own vector for the gradient product.
+// FP64: plain x; the product takes x_k − x_{k−1} on the fly.
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_acc_repl(AccArgs<T> a) {
+    constexpr bool DF = sizeof(T) == 4;
+    extern __shared__ __align__(16) uint8_t smraw[];
+    T* sx = reinterpret_cast<T*>(smraw);  // x_{k−1} (high part)
+    T* sxp = sx + a.ldq;                  // x_{k−2} (high part)
+    T* sg = sxp + a.ldq;                  // ∇f(x_{k−1})
+    T* sgp = sg + a.ldq;                  // ∇f(x_{k−2})
+    T* red = sgp + a.ldq;                 // kPWarps × TILE
+    T* sxl = red + kPWarps * 32 * Vec16<T>::N;  // DF: low parts of x_{k−1}, x_{k−2}; step d
+    T* sxpl = sxl + a.ldq;
+    T* sdd = sxpl + a.ldq;
+    __shared__ double s_t[33];
+    __shared__ int s_i3[66];
+    __shared__ T s_beta;
+    __shared__ int s_flag;
+    const unsigned int G = gridDim.x;
+    const int items = a.CT * a.R;
+    const int n = a.n;
+    unsigned int bar = 0;
+
+    for (int j = threadIdx.x; j < a.ldq; j += blockDim.x) {
+        const T x = j < n ? __ldcg(a.y + j) : T(0);
+        const T g = j < n ? __ldcg(a.g + j) : T(0);
+        sx[j] = x;
+        sxp[j] = x;
+        sg[j] = g;
+        sgp[j] = g;
+        if (DF) {
+            sxl[j] = T(0);
+            sxpl[j] = T(0);
+            sdd[j] = T(0);
+        }
+    }
+    __syncthreads();
+    double gam;
+    int cnt, nnz;
+    acc_mask(n, sx, sg, DF ? sdd : sx, DF ? nullptr : sxp, s_t, s_i3, &gam, &cnt, &nnz);
+
+    IterState* st = a.st;
+    const double eps = st->eps;
+    const int max_iter = st->max_iter, window = a.window;
+    double best = 1.0 / 0.0;
+    int best_iter = 0, iter = 0, status = ALN_RHS_MAXITER;
+    double a_prev = 1.0, a_cur = 1.0;  // α_{k−1}, α_k (thread 0)
+    long long sum_rows = 0;
+    uint64_t prof[5] = {0, 0, 0, 0, 0};
+    bool ok = true;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    const T invL = (T)a.inv_L;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int stop = 1;
+            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
+            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
+            else if (iter >= max_iter) status = ALN_RHS_MAXITER;
+            else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
+            else stop = 0;
+            if (!stop && gam < best) {
+                best = gam;
+                best_iter = iter;
+            }
+            if (!stop) {
+                s_beta = (T)((a_prev - 1.0) / a_cur);
+                a_prev = a_cur;
+                a_cur = 0.5 * (1.0 + sqrt(4.0 * a_cur * a_cur + 1.0));
+            }
+            s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) break;
+        uint64_t t_prev = timer ? p_globaltimer() : 0;
+        auto lap = [&](int k) {
+            if (timer) {
+                const uint64_t t = p_globaltimer();
+                prof[k] += t - t_prev;
+                t_prev = t;
+            }
+        };
+        const T beta = s_beta;
+        // x_k = [Y − ∇f(Y)/L]₊ = [x + β(x − x_p) − (g + β(g − g_p))/L]₊; the
+        // history shifts by one
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const T xh = sx[j], xph = sxp[j], g = sg[j], gp = sgp[j];
+            const T gY = g + beta * (g - gp);
+            if (DF) {
+                const T xl = sxl[j], xpl = sxpl[j];
+                const T d = (xh - xph) + (xl - xpl);
+                const T u = beta * d - gY * invL;  // Y − ∇f(Y)/L − x
+                // (xh, xl) + u: TwoSum, then renormalise
+                const T s = xh + u;
+                const T bb = s - xh;
+                const T er = (xh - (s - bb)) + (u - bb);
+                const T t = xl + er;
+                T nh = s + t;
+                T nl = t - (nh - s);
+                if (nh < T(0) || (nh == T(0) && nl < T(0))) {
+                    nh = T(0);
+                    nl = T(0);
+                }
+                sxp[j] = xh;
+                sxpl[j] = xl;
+                sx[j] = nh;
+                sxl[j] = nl;
+                sdd[j] = (nh - xh) + (nl - xl);  // x_k − x_{k−1}
+            } else {
+                const T Y = xh + beta * (xh - xph);
+                const T xn = Y - gY * invL;
+                sxp[j] = xh;
+                sx[j] = xn > T(0) ? xn : T(0);
+            }
+            sgp[j] = g;
+        }
+        __syncthreads();
+        lap(0);
+        // ∇f(x_k) = ∇f(x_{k−1}) + Q(x_k − x_{k−1}): partials, barrier, gather
+        T* part = a.part + (int64_t)(iter & 1) * a.R * a.ldq;
+        for (int it = blockIdx.x; it < items; it += G) {
+            const int ct = it % a.CT, rg = it / a.CT;
+            if (DF)
+                (void)mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sdd, ct, rg, part, red);
+            else
+                (void)mv_item_rep<T, true>(a.Q, a.ldq, n, a.rows_per_group, sx, ct, rg, part,
+                                           red, nullptr, sxp);
+        }
+        ++iter;
+        lap(1);
+        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        lap(2);
+        sum_partials(part, a.R, a.ldq, n, sg, true);  // sg still holds ∇f(x_{k−1})
+        __syncthreads();
+        acc_mask(n, sx, sg, DF ? sdd : sx, DF ? nullptr : sxp, s_t, s_i3, &gam, &cnt, &nnz);
+        sum_rows += nnz;  // rows of Q this product read: nnz(x_k − x_{k−1})
+        lap(3);
+    }
+    if (blockIdx.x == 0) {
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            a.y[j] = DF ? sx[j] + sxl[j] : sx[j];
+            a.g[j] = sg[j];
+        }
+        if (threadIdx.x == 0) {
+            st->iter = iter;
+            st->done = 1;
+            st->status = ok ? status : kStatusTimeout;
+            st->gbar2 = gam;
+            st->npassive = cnt;
+            st->best_g2 = best;
+            st->best_iter = best_iter;
+            st->sum_passive = sum_rows;
+            st->sum_clip = 0;
+            for (int k = 0; k < 5; ++k) st->phase_ns[k] = prof[k];
+            st->phase_ns[5] = 0;
+        }
+    }
+}
+
+// Power iteration for L = λ_max(Q) (the Anti+Acc step 1/L): v⁰_i = 1 + (i mod
+// 5)/8 normalised; u = Qv, ρ = vᵀu, v ← u/‖u‖; stops when two successive ρ
+// agree to `tol` (relative) or after max_steps products.  Same replicated
+// layout: one grid barrier per product.  out[0] = ρ, out[1] = products.
+template <typename T>
+struct PowerArgs {
+    const T* Q;
+    int64_t ldq;
+    int n;
+    int CT;
+    int R;
+    int rows_per_group;
+    T* part;  // 2 × R × ldq
+    double tol;
+    int max_steps;
+    PersistSync* sync;
+    double* out;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads, 1) k_power_repl(PowerArgs<T> a) {
+    extern __shared__ __align__(16) uint8_t smraw[];
+    T* sv = reinterpret_cast<T*>(smraw);
+    T* su = sv + a.ldq;
+    T* red = su + a.ldq;
+    __shared__ double s_t[33];
+    __shared__ double s_scale;
+    __shared__ int s_flag;
+    const unsigned int G = gridDim.x;
+    const int items = a.CT * a.R;
+    const int n = a.n;
+    unsigned int bar = 0;
+    double part2 = 0.0;
+    for (int j = threadIdx.x; j < a.ldq; j += blockDim.x) {
+        const double v = j < n ? 1.0 + (double)(j % 5) / 8.0 : 0.0;
+        part2 += v * v;
+    }
+    const double nv2 = block_sum_bcast(part2, s_t);
+    const double inv0 = 1.0 / sqrt(nv2);
+    for (int j = threadIdx.x; j < a.ldq; j += blockDim.x)
+        sv[j] = j < n ? (T)((1.0 + (double)(j % 5) / 8.0) * inv0) : T(0);
+    __syncthreads();
+    double rho = 0.0, rho_prev = 0.0;
+    int t = 0;
+    bool ok = true;
+    for (;;) {
+        T* part = a.part + (int64_t)(t & 1) * a.R * a.ldq;
+        for (int it = blockIdx.x; it < items; it += G) {
+            const int ct = it % a.CT, rg = it / a.CT;
+            (void)mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sv, ct, rg, part, red);
+        }
+        ++t;
+        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        sum_partials(part, a.R, a.ldq, n, su, false);
+        __syncthreads();
+        T pr = T(0), pu = T(0);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            pr = fma(sv[j], su[j], pr);
+            pu = fma(su[j], su[j], pu);
+        }
+        rho = block_sum_td<T>(pr, s_t);
+        const double nu2 = block_sum_td<T>(pu, s_t);
+        if (threadIdx.x == 0) {
+            int stop = 0;
+            if (t > 1 && fabs(rho - rho_prev) <= a.tol * fabs(rho)) stop = 1;
+            else if (!(nu2 > 0.0) || !isfinite(nu2) || t >= a.max_steps) stop = 1;
+            rho_prev = rho;
+            s_scale = stop ? 0.0 : 1.0 / sqrt(nu2);
+            s_flag = stop;
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const T sc = (T)s_scale;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) sv[j] = su[j] * sc;
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.out[0] = ok ? rho : -1.0;
+        a.out[1] = ok ? (double)t : -1.0;
+    }
+}
+
+template <typename T>
+size_t acc_smem_bytes(int64_t ldq) {  // FP32 adds the low parts and the step vector
+    return (size_t)((sizeof(T) == 4 ? 7 : 4) * ldq + kPWarps * 32 * Vec16<T>::N) * sizeof(T);
+}
+template <typename T>
+size_t power_smem_bytes(int64_t ldq) {
+    return (size_t)(2 * ldq + kPWarps * 32 * Vec16<T>::N) * sizeof(T);
+}
+
+// Anti+Acc iteration for the state set up by launch_iter_setup (y, g = ∇f(y),
+// eps, max_iter).  Needs the replicated layout (the vectors in shared
+// memory); otherwise cudaErrorInvalidValue.
+template <typename T>
+cudaError_t launch_acc_persist(aln_ctx* c) {
+    const size_t smem = acc_smem_bytes<T>(c->ldq);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (!c->p_repl || smem + 4096 > (size_t)optin || !(c->lipschitz > 0.0))
+        return cudaErrorInvalidValue;
+    AccArgs<T> r;
+    r.Q = (const T*)c->Q;
+    r.ldq = c->ldq;
+    r.n = (int)c->n;
+    r.CT = c->p_CT;
+    r.R = c->p_R;
+    r.rows_per_group = (int)ceil_div(c->n, c->p_R);
+    r.y = (T*)c->y;
+    r.g = (T*)c->g;
+    r.part = (T*)c->part;
+    r.inv_L = 1.0 / c->lipschitz;
+    // The accelerated method's ‖ḡ‖ is not monotone: an FP32 run ends after
+    // 10× the stagnation window without a new best (the FP64 refinement then
+    // restarts it from the exact gradient, with fresh momentum); the FP64
+    // iteration has no such stop.
+    r.window = sizeof(T) == 8 ? (1 << 30) : 10 * c->opt.stagnation;
+    r.sync = (PersistSync*)c->p_sync;
+    r.st = c->st;
+    cudaError_t e = cudaFuncSetAttribute(k_acc_repl<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_acc_repl<T>, kPThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm * c->num_sms < c->p_G) return cudaErrorInvalidValue;
+    void* args[] = {&r};
+    return cudaLaunchCooperativeKernel((const void*)k_acc_repl<T>, dim3(c->p_G), dim3(kPThreads),
+                                       args, smem, c->stream);
+}
+
+// Power iteration on the prepared Q; out (device) receives ρ and the number
+// of products.  Same layout requirements as launch_acc_persist.
+template <typename T>
+cudaError_t launch_power(aln_ctx* c, double tol, int max_steps, double* out) {
+    const size_t smem = power_smem_bytes<T>(c->ldq);
+    if (!c->p_repl) return cudaErrorInvalidValue;
+    PowerArgs<T> r;
+    r.Q = (const T*)c->Q;
+    r.ldq = c->ldq;
+    r.n = (int)c->n;
+    r.CT = c->p_CT;
+    r.R = c->p_R;
+    r.rows_per_group = (int)ceil_div(c->n, c->p_R);
+    r.part = (T*)c->part;
+    r.tol = tol;
+    r.max_steps = max_steps;
+    r.sync = (PersistSync*)c->p_sync;
+    r.out = out;
+    cudaError_t e = cudaFuncSetAttribute(k_power_repl<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_power_repl<T>, kPThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm * c->num_sms < c->p_G) return cudaErrorInvalidValue;
+    void* args[] = {&r};
+    return cudaLaunchCooperativeKernel((const void*)k_power_repl<T>, dim3(c->p_G),
+                                       dim3(kPThreads), args, smem, c->stream);
+}
+
+size_t acc_smem_need(bool f64, int64_t ldq) {
+    return f64 ? acc_smem_bytes<double>(ldq) : acc_smem_bytes<float>(ldq);
+}
+
+template cudaError_t launch_acc_persist<float>(aln_ctx*);
+template cudaError_t launch_acc_persist<double>(aln_ctx*);
+template cudaError_t launch_power<float>(aln_ctx*, double, int, double*);
+template cudaError_t launch_power<double>(aln_ctx*, double, int, double*);
 
 template cudaError_t launch_alg2_persist<float>(aln_ctx*);
 template cudaError_t launch_alg2_persist<double>(aln_ctx*);
