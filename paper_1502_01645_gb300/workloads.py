@@ -25,6 +25,8 @@ __all__ = [
     "shared_multi_rhs",
     "uneven_batch",
     "warmstart_family",
+    "TCASES",
+    "tcase",
     "CONFIGS",
 ]
 
@@ -152,6 +154,58 @@ def warmstart_family(d=8000, n=2000, k=1024, support=(50, 400), seed=1005, rhs_s
     B = _noisy_rhs(r2, A.astype(np.float64), X, 0.01).astype(np.float32)
     return Problem(A, np.ascontiguousarray(B), X, tol, "warmstart_family",
                    {"d": d, "n": n, "k": k, "dtype": "f32"})
+
+
+# §5, Table 1: the six test-case kinds — sign of A and x* (+ non-negative,
+# ± mixed) and the lengths of the vectors A_k (SAM same, RAN random, VAR
+# various).
+TCASES = {
+    "T1": ("+", "SAM"), "T2": ("±", "RAN"), "T3": ("+", "VAR"),
+    "T4": ("±", "SAM"), "T5": ("+", "RAN"), "T6": ("±", "VAR"),
+}
+TCASE_SPARSITY = (0.0, 0.1, 0.2, 0.3, 0.4)   # the five sub-tests of each case
+
+
+def tcase(kind="T1", sub=0, n=4000, d=6000, seed=1006, dtype=np.float32):
+    """One sub-test of the paper's test-case design (§5, Table 1): n = 4000,
+    d = 1.5n, b = A x* with no noise.
+
+    Readings (the paper prints the design, not the generator):
+      * entries of A and x*: U[0, 1] for "+", U[−1, 1] for "±";
+      * sparsity of sub-test ``sub`` (0…4): 0, 10, …, 40% of the entries of
+        every column A_k and of x* set to zero;
+      * the vectors A_k are the columns (Table 1 indexes them by k, and the
+        method's scaling acts on column lengths): SAM rescales every column
+        to length 1, RAN to a length U(0, 1], VAR to 10^U[−1, 1] (two
+        decades: the lopsided case the scaling is for).  A column left all
+        zero by the sparsity stays zero.
+    Problem p's draws come from seed·100003 + 10·case + sub."""
+    sign, length = TCASES[kind]
+    frac = TCASE_SPARSITY[sub]
+    rng = _rng(seed * 100003 + 10 * int(kind[1]) + sub)
+    if sign == "+":
+        A = rng.random((d, n))
+        x = rng.random(n)
+    else:
+        A = rng.uniform(-1.0, 1.0, (d, n))
+        x = rng.uniform(-1.0, 1.0, n)
+    if frac > 0.0:
+        A[rng.random((d, n)) < frac] = 0.0
+        x[rng.random(n) < frac] = 0.0
+    norms = np.linalg.norm(A, axis=0)
+    if length == "SAM":
+        target = np.ones(n)
+    elif length == "RAN":
+        target = 1.0 - rng.random(n)               # (0, 1]
+    else:
+        target = 10.0 ** rng.uniform(-1.0, 1.0, n)
+    scale = np.where(norms > 0.0, target / np.where(norms > 0.0, norms, 1.0), 0.0)
+    A = np.asfortranarray((A * scale[None, :]).astype(dtype))
+    b = A.astype(np.float64) @ x                   # b = A x* for the A returned
+    return Problem(A, np.ascontiguousarray(b.astype(dtype))[None, :], x[None, :], 1e-6,
+                   f"{kind}_s{int(round(frac * 100))}",
+                   {"d": d, "n": n, "kind": kind, "sign": sign, "length": length,
+                    "sparsity": frac, "dtype": np.dtype(dtype).name})
 
 
 CONFIGS = {
