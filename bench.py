@@ -62,6 +62,11 @@ WORKLOADS = {
         desc="paper_tcases_{d}x{n}: the six test-case kinds of §5 Table 1 (sign of A, x* "
              "+ or +-, column lengths SAM / RAN / VAR) x five sparsities 0-40% = {k} "
              "sub-tests, b = A x* (no noise), FP32"),
+    "nmf": dict(
+        d=4096, n=4096, k=64, outer=5, tol=1e-6, seed=1007, prec="split_bf16",
+        desc="nmf_{d}x{n}_r{k}: V = W*H* + 1% noise (W*, H* 70% non-zero U[0,1]), FP32; "
+             "{outer} ANLS outer iterations from a seeded U[0,1] start, each sub-problem "
+             "to rel KKT {tol}"),
     "uniform_small": dict(
         d=1000, n=200, k=1, tol=1e-10, seed=1001, prec="fp64",
         desc="uniform_small_{d}x{n}_f64: A U[0,1], x_true half zeros U[0,1], "
@@ -270,13 +275,15 @@ def run_reference(args):
         return 0
     w = workload(args)
     w["algorithm"] = args.algorithm
-    p = generate(w)
+    p = None if w["name"] == "nmf" else generate(w)
     times, desc = [], ""
     for i in range(args.warmup + args.steps):
         if w["name"] == "uneven_batch":
             t, desc = cpu_sample_grouped(w, p)
         elif w["name"] == "paper_tcases":
             t, desc = cpu_sample_tcases(w, p)
+        elif w["name"] == "nmf":
+            t, desc = cpu_sample_nmf(w)
         elif w["name"] == "warmstart":
             t, desc = cpu_sample(w, p[1])
         else:
@@ -319,12 +326,14 @@ def run_ours(args):
 
     w = workload(args)
     w["algorithm"] = args.algorithm
-    if args.algorithm == "anti_acc" and w["name"] in ("uneven_batch", "warmstart"):
+    if args.algorithm == "anti_acc" and w["name"] in ("uneven_batch", "warmstart", "nmf"):
         raise SystemExit("--algorithm anti_acc runs on the single-problem workloads only")
     if w["name"] == "uneven_batch":
         return run_grouped(args, w, world, rank, local)
     if w["name"] == "paper_tcases":
         return run_tcases(args, w, world, rank, local)
+    if w["name"] == "nmf":
+        return run_nmf(args, w, world, rank, local)
     if w["name"] == "warmstart":
         return run_warmstart(args, w, world, rank, local)
     d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
@@ -465,9 +474,16 @@ def run_ours(args):
         ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
         kname = ("k_acc_repl (persistent Anti+Acc loop)" if alg == aln.ALG_ANTI_ACC else
                  "k_alg2_repl (persistent Alg. 2 loop)")
+        # DRAM traffic per launch of k_alg2_repl<float>: one ncu capture at
+        # 12000x3000 read 36.94 MB = 1.002 x n*ldq*4 (Q once; later iterations
+        # hit L2), so a launch moves 1.002 x n*ldq*4 bytes at any size
+        traffic = None
+        if alg == aln.ALG_ANTILOP and w["prec"] == "split_bf16":
+            ldq = (n + 127) // 128 * 128
+            traffic = 1.002 * n * ldq * 4
         rooflines.append({"bound": "hbm", "kernel": kname,
                           "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                          "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
+                          "traffic": traffic, "peak_kind": f"{pk_kind} hbm copy",
                           "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
                           "note": "the rows of Q read stay in the 129 MB L2 between "
                                   "iterations, so frac can exceed 1"})
@@ -888,6 +904,136 @@ def run_tcases(args, w, world, rank, local):
 def W_TCASES():
     from paper_1502_01645_gb300 import workloads as W
     return W.TCASES
+
+
+def cpu_sample_nmf(w):
+    """The FP64 ANLS oracle for one outer iteration on the leading m/8 × n/8
+    block of V (same r); each sub-problem's cost grows with its length, so
+    the full outer iteration is t·(solves ratio)·(length ratio) = t·8·8."""
+    import numpy as np
+    from oracle import nmf as N
+    from paper_1502_01645_gb300 import workloads as W
+    m, n, r = w["d"] // 8, w["n"] // 8, w["k"]
+    V, W0, H0 = W.nmf_matrix(m, n, r, seed=w["seed"])
+    t0 = time.perf_counter()
+    N.anls(V.astype(np.float64), W0, H0, outer=1, tol=w["tol"])
+    t = time.perf_counter() - t0
+    scale = 64.0 * w["outer"]
+    return t * scale, (f"oracle ANLS, 1 outer iteration on a {m}x{n} (r={r}) matrix in "
+                       f"{t:.2f} s, x 8 (solves) x 8 (length) x {w['outer']} outer iterations")
+
+
+def run_nmf(args, w, world, rank, local):
+    """NMF V ≈ W·H by alternating NNLS: one step = aln_nmf with `outer`
+    iterations from the same seeded start (2·outer batched solves of m and n
+    right-hand sides)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1502_01645_gb300 import aln, workloads as Wl
+
+    m, n, r, outer, tol = w["d"], w["n"], w["k"], w["outer"], w["tol"]
+    V, W0, H0 = Wl.nmf_matrix(m, n, r, seed=w["seed"] + rank)
+    Vd = torch.from_numpy(np.ascontiguousarray(V.T)).cuda().t()
+    Wd = torch.from_numpy(np.ascontiguousarray(W0.T)).cuda().t()
+    Hd = torch.from_numpy(np.ascontiguousarray(H0.T)).cuda().t()
+    stream = torch.cuda.Stream()
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
+
+    def step():
+        return solver.nmf(Vd, Wd, Hd, outer=outer, tol=tol)
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = solver.stats().kernel_launches
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    objs = [step()[2] for _ in range(args.steps)]
+    ev1.record(stream)
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    launches = solver.stats().kernel_launches - launches0
+    clocks = sampler.stop()
+    obj = objs[-1]
+    if any(b > a * (1 + 1e-6) for a, b in zip(obj, obj[1:])):
+        raise SystemExit(f"invalid run: objective rose {list(obj)}")
+    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    solves = (m + n) * outer
+    value = world * args.steps * solves / tmax
+
+    e2e = None
+    if not args.no_e2e:
+        Vh = torch.from_numpy(np.ascontiguousarray(V.T)).pin_memory().t()
+        Wh = torch.from_numpy(np.ascontiguousarray(W0.T)).pin_memory().t()
+        Hh = torch.from_numpy(np.ascontiguousarray(H0.T)).pin_memory().t()
+        barrier()
+        t0 = time.perf_counter()
+        solver.nmf(Vh, Wh, Hh, outer=outer, tol=tol)
+        barrier()
+        te = time.perf_counter() - t0
+        e2e = {"value": solves / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(V.nbytes + W0.nbytes + H0.nbytes),
+               "d2h_bytes_per_step": int(W0.nbytes + H0.nbytes), "steps": 1}
+    st = solver.stats()
+    solver.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+    # the dominant data movement of an outer iteration: V read by the two
+    # prepares (Aᵀb for every right-hand side) — 2·4·m·n bytes
+    vbytes = 2.0 * 4 * m * n * outer * args.steps
+    ach = vbytes / tmax / 1e9
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        ts, desc = cpu_sample_nmf(w)
+        cpu = {"value": solves / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 split + f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "n": n, "r": r, "outer": outer, "tol": tol,
+                   "seed": w["seed"], "solves_per_step": solves,
+                   "form": "aln_nmf: H-step and W-step each a batched multi-RHS solve "
+                           "(split-BF16 Gram, tcgen05 products, FP64 checks), warm-started",
+                   "objective": [float(v) for v in obj],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2" if V.nbytes > 129e6 else
+                         "inputs smaller than L2 (timed as resident data)",
+                   "last_w_step_iterations": int(st.iterations)},
+        "roofline": {"bound": "hbm", "kernel": "whole outer iteration (V streamed by both "
+                     "prepares)", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "traffic": None, "peak_kind": f"{pk_kind} hbm copy",
+                     "algorithmic_per_launch": 2.0 * 4 * m * n,
+                     "avg_launch_ms": tmax / (outer * args.steps) * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "plain_fp64": None,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_warmstart(args, w, world, rank, local):

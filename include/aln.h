@@ -298,6 +298,33 @@ aln_status aln_warmstart_train(aln_ctx* ctx, const double* Qtrain, const double*
  * Errors: INVALID_ARG (no network, or n differs), NOT_PREPARED, TIMEOUT, CUDA. */
 aln_status aln_warmstart_predict(aln_ctx* ctx, double* X0, int64_t ldx, int32_t* kept);
 
+/* Non-negative matrix factorisation V ≈ W·H (W m×r ⪰ 0, H r×n ⪰ 0) by
+ * alternating NNLS, the use the paper motivates its solver with (§1; §2.2 on
+ * the many right-hand sides of such factorisations).  Each of `outer`
+ * iterations runs Alg. 1 + Alg. 2 (this context's options: precision,
+ * algorithm, refinement) twice:
+ *   H-step: matrix W, the n columns of V as right-hand sides, started from
+ *           the previous H;
+ *   W-step: matrix Hᵀ, the m rows of V as right-hand sides, started from the
+ *           previous W;
+ * each sub-problem to relative KKT tolerance `tol` (max_iter per sub-problem,
+ * 0 = default).  With n, m ≥ batch_min both steps take the batched solver.
+ *   V         FP32, column-major m×n (V[i + j*ldv]), host or device; read only.
+ *   W         FP64, column-major m×r (ldw ≥ m): the start on entry (negative
+ *             entries are taken as 0), the result on return.  Host or device.
+ *   H         FP64, column-major r×n (ldh ≥ r): likewise.
+ *   objective host array of `outer` doubles or NULL: ½‖V − W·H‖_F² after each
+ *             outer iteration (the sum of the W-step's FP64 sub-problem
+ *             objectives).
+ * The context's prepared problem is replaced (it ends prepared with the last
+ * W-step); work buffers are kept in the context for later calls.
+ * Errors: INVALID_ARG (null pointer, r > min(m, n), r > 4096, ld too small,
+ * outer < 1, tol not positive), NONFINITE, UNSUPPORTED (as aln_solve),
+ * OUT_OF_MEMORY, TIMEOUT, CUDA. */
+aln_status aln_nmf(aln_ctx* ctx, const float* V, int64_t m, int64_t n, int64_t ldv, int64_t r,
+                   double* W, int64_t ldw, double* H, int64_t ldh, int32_t outer, double tol,
+                   int32_t max_iter, double* objective);
+
 /* Device-time breakdown of the last calls, measured with CUDA events on the
  * context's stream, and counters (for benchmarks and tracing). */
 typedef struct aln_stats {

@@ -31,7 +31,7 @@ EXPORTS = (
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
     "aln_kkt_residual_noalloc", "aln_prepare_grouped", "aln_default_train_opts",
     "aln_warmstart_init", "aln_warmstart_params", "aln_warmstart_grad", "aln_warmstart_train",
-    "aln_warmstart_predict",
+    "aln_warmstart_predict", "aln_nmf",
 )
 
 
@@ -128,6 +128,9 @@ def load(path: str | None = None):
     lib.aln_warmstart_train.restype = ctypes.c_int
     lib.aln_warmstart_predict.argtypes = [vp, dp, i64, vp]
     lib.aln_warmstart_predict.restype = ctypes.c_int
+    lib.aln_nmf.argtypes = [vp, vp, i64, i64, i64, i64, dp, i64, dp, i64, i32, ctypes.c_double,
+                            i32, dp]
+    lib.aln_nmf.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -225,6 +228,11 @@ def aln_warmstart_grad(ctx, Qb, Yb, count, loss, grads) -> None:
 def aln_warmstart_train(ctx, Qt, Yt, count, opts, epoch_loss) -> None:
     _check(load().aln_warmstart_train(ctx, _ptr(Qt), _ptr(Yt), count, ctypes.byref(opts),
                                       _ptr(epoch_loss)), "aln_warmstart_train")
+
+
+def aln_nmf(ctx, V, m, n, ldv, r, W, ldw, H, ldh, outer, tol, max_iter, objective) -> None:
+    _check(load().aln_nmf(ctx, _ptr(V), m, n, ldv, r, _ptr(W), ldw, _ptr(H), ldh, outer, tol,
+                          max_iter, _ptr(objective)), "aln_nmf")
 
 
 def aln_warmstart_predict(ctx, X0, ldx, kept) -> None:
@@ -438,6 +446,29 @@ class Solver:
         kept = np.zeros(self.k, np.int32)
         aln_warmstart_predict(self.ctx, X0, _row_major_ld(X0), kept)
         return X0, kept
+
+    def nmf(self, V, W0, H0, outer=10, tol=1e-6, max_iter=0):
+        """V ≈ W·H by alternating NNLS (aln_nmf).  V (m, n) float32 and the
+        starts W0 (m, r), H0 (r, n) float64 are column-major (Fortran numpy
+        arrays or transposed-contiguous tensors).  Returns (W, H, objective
+        after each outer iteration); W0 and H0 are not modified."""
+        m, n = V.shape
+        r = W0.shape[1]
+        if W0.shape[0] != m or H0.shape != (r, n):
+            raise ValueError("W0 must be (m, r) and H0 (r, n)")
+        if isinstance(W0, np.ndarray):
+            W = np.asfortranarray(W0, dtype=np.float64).copy(order="F")
+            H = np.asfortranarray(H0, dtype=np.float64).copy(order="F")
+        else:
+            W = W0.detach().t().contiguous().t().clone()
+            H = H0.detach().t().contiguous().t().clone()
+        obj = np.zeros(outer)
+        self._keep = (V, W, H)
+        aln_nmf(self.ctx, V, m, n, _col_major_ld(V), r, W, _col_major_ld(W), H,
+                _col_major_ld(H), outer, tol, max_iter, obj)
+        self.n, self.k = r, m
+        self.sizes = None
+        return W, H, obj
 
     def close(self):
         aln_destroy(self.ctx)

@@ -366,6 +366,7 @@ void aln_destroy(aln_ctx* c) {
     batch_free(c);
     group_free(c);
     mlp_free(c);
+    nmf_free(c);
     void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);

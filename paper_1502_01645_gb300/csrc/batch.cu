@@ -237,9 +237,13 @@ __global__ void k_binit(BatchState s, const double* __restrict__ q64, const doub
     const int64_t c = blockIdx.x;
     for (int64_t i = threadIdx.x; i < s.ldq; i += blockDim.x) {
         const bool in = i < s.n;
-        s.Y[c * s.ldq + i] = (in && x0) ? (float)(x0[c * ldx0 + i] * sc[i]) : 0.0f;
+        const double y0 = (in && x0) ? x0[c * ldx0 + i] * sc[i] : 0.0;
+        const float yh = (float)y0;
+        s.Y[c * s.ldq + i] = yh;
         s.G[c * s.ldq + i] = in ? (float)q64[c * s.ldq + i] : 0.0f;
-        s.E[c * s.ldq + i] = 0.0f;
+        // the low part of the start (read only by the small-n float-pair path;
+        // the batched phase overwrites E with e before using it)
+        s.E[c * s.ldq + i] = (float)(y0 - (double)yh);
     }
     if (threadIdx.x == 0) {
         const double t = tol_factor * (den[c] > 0.0 ? den[c] : 1.0);
@@ -252,12 +256,15 @@ __global__ void k_binit(BatchState s, const double* __restrict__ q64, const doub
     }
 }
 
-// x = y/s and y in FP64 for the check (Eq. Rescaling).
+// x = y/s and y in FP64 for the check (Eq. Rescaling).  ylo: the low parts
+// of a float-pair iterate (the small-n kernel keeps them in E), or null.
 __global__ void k_bunscale(BatchState s, const double* __restrict__ sc, double* __restrict__ X64,
-                           double* __restrict__ Y64) {
+                           double* __restrict__ Y64, const float* __restrict__ ylo) {
     const int64_t c = blockIdx.x;
     for (int64_t i = threadIdx.x; i < s.ldq; i += blockDim.x) {
-        const double y = i < s.n ? (double)s.Y[c * s.ldq + i] : 0.0;
+        const double y = i < s.n ? (double)s.Y[c * s.ldq + i] +
+                                       (ylo ? (double)ylo[c * s.ldq + i] : 0.0)
+                                 : 0.0;
         Y64[c * s.ldq + i] = y;
         X64[c * s.ldq + i] = i < s.n ? y / sc[i] : 0.0;
     }
@@ -324,6 +331,172 @@ __global__ void __launch_bounds__(kBThreads) k_bcheck(
 }
 
 // ---------------------------------------------------------------------------
+// Small n (≤ 128): one warp per column, the whole Alg. 2 loop in one launch.
+// The batched phase above pays several launches and tcgen05 tiles per
+// iteration; for n this small each column's products are a few thousand
+// FMAs, so a warp runs the loop alone: Q (FP32, n × n) staged in shared
+// memory once per block, y and g in registers (VPL entries per lane),
+// ḡ_j broadcast by shuffles, the sums of γ and κ in FP64 across lanes.  The
+// iterate is a float pair y = yh + yl (yh in Y, yl in E, which this path
+// does not otherwise use): the FP64 refinement then converges below the
+// FP32 rounding of y, as in the grouped kernel.
+// Same stop rules and per-column state as k_bmask / k_bupdate, so the FP64
+// checks and refinement (k_bcheck) follow unchanged.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int VPL>
+__global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __restrict__ Q32) {
+    constexpr int NS = VPL * 32;  // row stride of the staged Q
+    extern __shared__ float sq[];
+    const int n = (int)s.n;
+    for (int e = threadIdx.x; e < NS * NS; e += blockDim.x) {
+        const int j = e / NS, i = e - j * NS;
+        sq[e] = (i < n && j < n) ? Q32[(int64_t)j * s.ldq + i] : 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < s.k;
+         c += nwarps) {
+        if (s.colst[c] >= 0) continue;  // warp-uniform
+        float* Yc = s.Y + c * s.ldq;
+        float* Lc = s.E + c * s.ldq;
+        float* Gc = s.G + c * s.ldq;
+        float y[VPL], yl[VPL], g[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int i = lane + 32 * v;
+            y[v] = i < n ? Yc[i] : 0.0f;
+            yl[v] = i < n ? Lc[i] : 0.0f;
+            g[v] = i < n ? Gc[i] : 0.0f;
+        }
+        int it = s.iters[c], best_iter = s.best_iter[c];
+        double best = s.best[c];
+        const double eps = s.eps[c];
+        const int max_iter = s.limits[0], window = s.limits[1];
+        unsigned long long rowsP = 0, rowsC = 0, clipIt = 0;
+        int status;
+        for (;;) {
+            float gb[VPL];
+            float v2 = 0.0f;
+            int cntP = 0;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                const int i = lane + 32 * v;
+                const bool P = i < n && (y[v] > 0.0f || g[v] < 0.0f);
+                gb[v] = P ? g[v] : 0.0f;
+                v2 = fmaf(gb[v], gb[v], v2);
+                cntP += __popc(__ballot_sync(0xffffffffu, P));
+            }
+            const double gam = warp_sum_d((double)v2);
+            status = -1;
+            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            else if (cntP == 0) status = ALN_RHS_EMPTY_PASSIVE;
+            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
+            else if (it >= max_iter) status = ALN_RHS_MAXITER;
+            else if (it - best_iter > window) status = ALN_RHS_STAGNATED;
+            if (status >= 0) break;
+            if (gam < best) {
+                best = gam;
+                best_iter = it;
+            }
+            rowsP += (unsigned long long)cntP;
+            // w = Qḡ over the j with ḡ_j ≠ 0 (Q symmetric: row j of the staged Q)
+            float w[VPL];
+#pragma unroll
+            for (int u = 0; u < VPL; ++u) w[u] = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                unsigned int m = __ballot_sync(0xffffffffu, gb[v] != 0.0f);
+                while (m) {  // warp-uniform
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float gj = __shfl_sync(0xffffffffu, gb[v], src);
+                    const float* row = sq + (v * 32 + src) * NS;
+#pragma unroll
+                    for (int u = 0; u < VPL; ++u) w[u] = fmaf(row[lane + 32 * u], gj, w[u]);
+                }
+            }
+            float kp = 0.0f;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) kp = fmaf(gb[v], w[v], kp);
+            const double kap = warp_sum_d((double)kp);
+            if (!isfinite(kap)) {
+                status = ALN_RHS_NONFINITE;
+                break;
+            }
+            if (kap <= 0.0) {
+                status = ALN_RHS_CURVATURE;
+                break;
+            }
+            const float a = (float)(gam / kap);
+            // y⁺ = [y − αḡ]₊, e on the clipped set, g ← g − αw (+ Qe below)
+            float e[VPL];
+            int nclip = 0;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                // (yh, yl) − αḡ exactly: TwoSum, then renormalise
+                const float step = __fmul_rn(a, gb[v]);
+                const float s1 = y[v] - step;
+                const float bb = s1 - y[v];
+                const float er = (y[v] - (s1 - bb)) + (-step - bb);
+                const float t = yl[v] + er;
+                float nh = s1 + t, nl = t - ((s1 + t) - s1), ev = 0.0f;
+                if (nh < 0.0f) {  // clipped: y⁺ = 0, e = y⁺ − (y − αḡ)
+                    ev = -(nh + nl);
+                    nh = 0.0f;
+                    nl = 0.0f;
+                }
+                y[v] = nh;
+                yl[v] = nl;
+                e[v] = ev;
+                g[v] = g[v] - a * w[v];
+                nclip += __popc(__ballot_sync(0xffffffffu, ev != 0.0f));
+            }
+            ++it;
+            if (nclip > 0) {
+                rowsC += (unsigned long long)nclip;
+                ++clipIt;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    unsigned int m = __ballot_sync(0xffffffffu, e[v] != 0.0f);
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float ej = __shfl_sync(0xffffffffu, e[v], src);
+                        const float* row = sq + (v * 32 + src) * NS;
+#pragma unroll
+                        for (int u = 0; u < VPL; ++u) g[u] = fmaf(row[lane + 32 * u], ej, g[u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            const int i = lane + 32 * v;
+            if (i < n) {
+                Yc[i] = y[v];
+                Lc[i] = yl[v];
+                Gc[i] = g[v];
+            }
+        }
+        if (lane == 0) {
+            s.colst[c] = status;
+            s.iters[c] = it;
+            s.best[c] = best;
+            s.best_iter[c] = best_iter;
+            atomicAdd(&s.rows[0], rowsP);
+            atomicAdd(&s.rows[1], rowsC);
+            atomicAdd(&s.rows[2], clipIt);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 // Progressive refinement is on by default here: with many columns the FP64
@@ -353,6 +526,7 @@ struct BatchWork {
     BatchState s{};
     cudaGraphExec_t graph = nullptr;
     int chunk = 8;
+    int small_vpl = 0;            // n ≤ 128: entries per lane of k_bsmall (1, 2, 4), else 0
 };
 
 static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
@@ -520,6 +694,8 @@ aln_status batch_prepare(aln_ctx* c) {
     k_bnorm2<<<(unsigned)c->k, kBThreads, 0, c->stream>>>(c->B, c->dtype, c->d, c->ldb, b->bn2);
     c->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
+    b->small_vpl = c->n <= 32 ? 1 : c->n <= 64 ? 2 : c->n <= 128 ? 4 : 0;
+    if (b->small_vpl) return ALN_OK;  // the warp-per-column kernel needs no graph
     return bw_capture(c, b);
 }
 
@@ -537,7 +713,8 @@ static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine,
     BatchState& s = b->s;
     const int64_t k = b->k;
     cudaEventRecord(c->ev[6], c->stream);
-    k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
+    k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64,
+                                                         b->small_vpl ? s.E : nullptr);
     // g = Q y + q in FP64 accuracy (FP32 pairs on the FP32 pipe)
     const int64_t ky = k * c->ldq;
     if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
@@ -604,7 +781,8 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     cudaMemsetAsync(s.rows, 0, 24, c->stream);
     c->launches += 1;
     if (X0dev) {  // g = Q y0 + q, in FP64, for a start point
-        k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64);
+        k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64,
+                                                             b->small_vpl ? s.E : nullptr);
         const int64_t ky = k * c->ldq;
         if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
             launch_gemm_pairs_axpy(b->Qp, b->Qp + c->ldq * c->ldq, c->ldq, b->Yp, b->Yp + ky,
@@ -616,10 +794,28 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     }
     const int max_refine = c->opt.max_refine;
     for (int round = 0;; ++round) {
-        // inner runs: the captured chunk until no column is running
-        const int64_t bound = max_iter / b->chunk + 3;
+        // inner runs: the captured chunk until no column is running (small n:
+        // one warp-per-column launch runs every column to its stop)
+        const int64_t bound = b->small_vpl ? 1 : max_iter / b->chunk + 3;
         int64_t l = 0;
         cudaEventRecord(c->ev[8], c->stream);
+        if (b->small_vpl) {
+            const int vpl = b->small_vpl;
+            const size_t smem = (size_t)(vpl * 32) * (vpl * 32) * 4;
+            const unsigned grid = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((k + 7) / 8, 16LL * c->num_sms));
+            if (vpl == 1) k_bsmall<1><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
+            else if (vpl == 2) k_bsmall<2><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
+            else {
+                if (cudaFuncSetAttribute(k_bsmall<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem) != cudaSuccess)
+                    return ALN_ERR_CUDA;
+                k_bsmall<4><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
+            }
+            if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
+            c->launches += 1;
+            l = 1;
+        }
         for (; l < bound; ++l) {
             if (cudaGraphLaunch(b->graph, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
             c->launches += 5LL * b->chunk;
@@ -634,7 +830,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
             c->stats.iterate_ms += ms;
-        if (l == bound) return ALN_ERR_TIMEOUT;
+        if (!b->small_vpl && l == bound) return ALN_ERR_TIMEOUT;
         int restarted = 0;
         aln_status st = bw_check(c, b, tol, max_refine, &restarted);
         if (st != ALN_OK) return st;

@@ -268,6 +268,7 @@ struct aln_ctx {
     int grouped = 0;
     // learned start point (mlp.cu); null until created
     void* mlp = nullptr;
+    void* nmf = nullptr;     // aln_nmf work buffers (nmf.cu)
 
     // statistics (aln_get_stats)
     cudaEvent_t ev[10] = {};

@@ -109,6 +109,7 @@ aln_status mlp_train(aln_ctx* c, const double* Qs, const double* Ys, int64_t cou
 aln_status mlp_predict(aln_ctx* c, double* X0, int64_t ldx, int* kept);
 int mlp_n(const aln_ctx* c);
 void mlp_free(aln_ctx* c);
+void nmf_free(aln_ctx* c);  // nmf.cu
 
 // batch.cu — Alg. 2 on many right-hand sides sharing A
 aln_status batch_prepare(aln_ctx* c);

@@ -27,6 +27,7 @@ __all__ = [
     "warmstart_family",
     "TCASES",
     "tcase",
+    "nmf_matrix",
     "CONFIGS",
 ]
 
@@ -206,6 +207,24 @@ def tcase(kind="T1", sub=0, n=4000, d=6000, seed=1006, dtype=np.float32):
                    f"{kind}_s{int(round(frac * 100))}",
                    {"d": d, "n": n, "kind": kind, "sign": sign, "length": length,
                     "sparsity": frac, "dtype": np.dtype(dtype).name})
+
+
+def nmf_matrix(m=4096, n=4096, r=64, seed=1007, noise=0.01):
+    """A non-negative data matrix for NMF: V = W* H* + noise, W* (m×r) and
+    H* (r×n) with 70% non-zero U[0,1] entries, Gaussian noise of ``noise`` ×
+    the RMS entry of W*H*, clipped at 0; FP32, column-major.  Also returns a
+    seeded non-negative start (W0, H0) of U[0,1] entries (FP64, column-major)
+    scaled so that W0·H0 has V's mean."""
+    rng = _rng(seed)
+    Ws = rng.random((m, r)) * (rng.random((m, r)) < 0.7)
+    Hs = rng.random((r, n)) * (rng.random((r, n)) < 0.7)
+    V = Ws @ Hs
+    V = V + noise * np.sqrt(np.mean(V * V)) * rng.standard_normal((m, n))
+    V = np.asfortranarray(np.maximum(V, 0.0).astype(np.float32))
+    W0 = rng.random((m, r))
+    H0 = rng.random((r, n))
+    c = np.sqrt(V.astype(np.float64).mean() / (W0 @ H0).mean())
+    return V, np.asfortranarray(W0 * c), np.asfortranarray(H0 * c)
 
 
 CONFIGS = {

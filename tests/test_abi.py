@@ -59,6 +59,8 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.aln_export_scaled(None, None, 1, None, 1, None) == aln.ERR_INVALID_ARG
     assert lib.aln_get_stats(None, None) == aln.ERR_INVALID_ARG
     assert lib.aln_prepare_grouped(None, 1, None, 0) == aln.ERR_INVALID_ARG
+    assert lib.aln_nmf(None, None, 4, 4, 4, 2, None, 4, None, 2, 1, 1e-6, 0, None) == \
+        aln.ERR_INVALID_ARG
     o = aln.aln_default_options()
     o.precision = 7
     ctx = ctypes.c_void_p()

@@ -337,6 +337,39 @@ def test_batched_agrees_with_single_rhs_path(aln):
         assert np.linalg.norm(Xb[c] - Xs[c]) <= 2e-5 * np.linalg.norm(Xs[c])
 
 
+@pytest.mark.parametrize("d,n,k", [(600, 100, 40), (300, 33, 24), (200, 7, 16), (500, 128, 20),
+                                   (90, 32, 9)])
+def test_batched_small_n_matches_oracle(aln, d, n, k):
+    """n ≤ 128: the warp-per-column kernel runs each column's Alg. 2 loop
+    (VPL = 1, 2, 4 entries per lane, ragged n); every column meets the FP64
+    KKT gate from A and the x-gate against the oracle's optimum at tol 1e-9,
+    a zero right-hand side stops at once, and a start point at the solution
+    needs (almost) no iteration."""
+    r = np.random.default_rng(d + n + k)
+    A = np.asfortranarray((r.random((d, n)) * np.exp(r.uniform(-1, 1, n))).astype(np.float32))
+    X_true = np.where(r.random((k, n)) < 0.6, 0.0, r.random((k, n)))
+    B = (X_true @ A.astype(np.float64).T + 0.01 * r.standard_normal((k, d))).astype(np.float32)
+    B[1] = -np.abs(B[1]) if n > 1 else B[1]
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, B)
+        X, info = s.solve(tol=1e-9)
+        X2, info2 = s.solve(tol=1e-9, X0=X.copy())
+    A64 = A.astype(np.float64)
+    for c in range(k):
+        b64 = B[c].astype(np.float64)
+        rel, F = O.kkt_residual(A64, b64, X[c])
+        assert rel <= 1e-9, (c, rel, info[c])
+        # the batched FP64 check forms g64 = Q64·y + q as Dot2 products on FP32
+        # pairs (≈ 2⁻⁴⁸ per entry): about 1e-14 absolute in the relative residual
+        np.testing.assert_allclose(info[c].rel_kkt, rel, rtol=1e-6, atol=5e-14)
+        if c != 1:                       # column 1 has the optimum x = 0
+            x_star, _, _, _ = O.reference_solution(A64, b64)
+            _mixed_gate(A, B[c], X[c], x_star)
+        assert info2[c].iters <= max(3, info[c].iters // 4)
+    assert info[1].iters == 0 and info[1].status == aln.RHS_EMPTY_PASSIVE
+    assert np.all(X[1] == 0.0)
+
+
 def test_batched_edge_columns(aln):
     """Zero RHS (x = 0 at once), ragged n across tiles, a start point."""
     r = np.random.default_rng(36)
