@@ -348,20 +348,76 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// Σ_{k < cnt} v[list[k]] · Q[list[k], i] for the lane's rows i = lane + 32u:
+// the listed rows of the staged Q, four list entries in flight per step.
+template <int VPL>
+__device__ __forceinline__ void bsmall_rows(const float* sq, const int* list, const float* vals,
+                                            int cnt, int lane, float (&acc)[VPL]) {
+    constexpr int NS = VPL * 32;
+    float a2[VPL];
+#pragma unroll
+    for (int u = 0; u < VPL; ++u) a2[u] = 0.0f;
+    int k = 0;
+    for (; k + 1 < cnt; k += 2) {
+        const int j0 = list[k], j1 = list[k + 1];
+        const float v0 = vals[j0], v1 = vals[j1];
+        const float* r0 = sq + j0 * NS;
+        const float* r1 = sq + j1 * NS;
+#pragma unroll
+        for (int u = 0; u < VPL; ++u) {
+            acc[u] = fmaf(r0[lane + 32 * u], v0, acc[u]);
+            a2[u] = fmaf(r1[lane + 32 * u], v1, a2[u]);
+        }
+    }
+    if (k < cnt) {
+        const int j0 = list[k];
+        const float v0 = vals[j0];
+        const float* r0 = sq + j0 * NS;
+#pragma unroll
+        for (int u = 0; u < VPL; ++u) acc[u] = fmaf(r0[lane + 32 * u], v0, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < VPL; ++u) acc[u] += a2[u];
+}
+
+// Lane-order list of the indices lane + 32v with x[v] ≠ 0 (increasing), and
+// the values by index; returns the count (warp-uniform).
+template <int VPL>
+__device__ __forceinline__ int bsmall_list(const float (&x)[VPL], int lane, int* list,
+                                           float* vals) {
+    int base = 0;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const bool nz = x[v] != 0.0f;
+        const unsigned int m = __ballot_sync(0xffffffffu, nz);
+        if (nz) list[base + __popc(m & ((1u << lane) - 1u))] = lane + 32 * v;
+        vals[lane + 32 * v] = x[v];
+        base += __popc(m);
+    }
+    __syncwarp();
+    return base;
+}
+
 template <int VPL>
 __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __restrict__ Q32) {
     constexpr int NS = VPL * 32;  // row stride of the staged Q
-    extern __shared__ float sq[];
+    extern __shared__ float sq[];  // NS × NS staged Q, then per warp: list[NS], vals[NS]
     const int n = (int)s.n;
+    int* wlist = reinterpret_cast<int*>(sq + NS * NS) + (threadIdx.x >> 5) * 2 * NS;
+    float* wvals = reinterpret_cast<float*>(wlist + NS);
     for (int e = threadIdx.x; e < NS * NS; e += blockDim.x) {
         const int j = e / NS, i = e - j * NS;
         sq[e] = (i < n && j < n) ? Q32[(int64_t)j * s.ldq + i] : 0.0f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < s.k;
-         c += nwarps) {
+    // columns are dealt dynamically (counters[2]): a warp that finishes a
+    // short column takes the next one, so long columns do not hold others
+    for (;;) {
+        int64_t c = 0;
+        if (lane == 0) c = atomicAdd(&s.counters[2], 1);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= s.k) break;
         if (s.colst[c] >= 0) continue;  // warp-uniform
         float* Yc = s.Y + c * s.ldq;
         float* Lc = s.E + c * s.ldq;
@@ -409,17 +465,10 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
             float w[VPL];
 #pragma unroll
             for (int u = 0; u < VPL; ++u) w[u] = 0.0f;
-#pragma unroll
-            for (int v = 0; v < VPL; ++v) {
-                unsigned int m = __ballot_sync(0xffffffffu, gb[v] != 0.0f);
-                while (m) {  // warp-uniform
-                    const int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    const float gj = __shfl_sync(0xffffffffu, gb[v], src);
-                    const float* row = sq + (v * 32 + src) * NS;
-#pragma unroll
-                    for (int u = 0; u < VPL; ++u) w[u] = fmaf(row[lane + 32 * u], gj, w[u]);
-                }
+            {
+                const int cnt = bsmall_list<VPL>(gb, lane, wlist, wvals);
+                bsmall_rows<VPL>(sq, wlist, wvals, cnt, lane, w);
+                __syncwarp();
             }
             float kp = 0.0f;
 #pragma unroll
@@ -461,18 +510,14 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
             if (nclip > 0) {
                 rowsC += (unsigned long long)nclip;
                 ++clipIt;
+                float qe[VPL];
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    unsigned int m = __ballot_sync(0xffffffffu, e[v] != 0.0f);
-                    while (m) {
-                        const int src = __ffs(m) - 1;
-                        m &= m - 1;
-                        const float ej = __shfl_sync(0xffffffffu, e[v], src);
-                        const float* row = sq + (v * 32 + src) * NS;
+                for (int u = 0; u < VPL; ++u) qe[u] = 0.0f;
+                const int cnt = bsmall_list<VPL>(e, lane, wlist, wvals);
+                bsmall_rows<VPL>(sq, wlist, wvals, cnt, lane, qe);
+                __syncwarp();
 #pragma unroll
-                        for (int u = 0; u < VPL; ++u) g[u] = fmaf(row[lane + 32 * u], ej, g[u]);
-                    }
-                }
+                for (int u = 0; u < VPL; ++u) g[u] += qe[u];
             }
         }
 #pragma unroll
@@ -801,17 +846,24 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         cudaEventRecord(c->ev[8], c->stream);
         if (b->small_vpl) {
             const int vpl = b->small_vpl;
-            const size_t smem = (size_t)(vpl * 32) * (vpl * 32) * 4;
-            const unsigned grid = (unsigned)std::max<int64_t>(
-                1, std::min<int64_t>((k + 7) / 8, 16LL * c->num_sms));
-            if (vpl == 1) k_bsmall<1><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
-            else if (vpl == 2) k_bsmall<2><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
-            else {
-                if (cudaFuncSetAttribute(k_bsmall<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem) != cudaSuccess)
-                    return ALN_ERR_CUDA;
-                k_bsmall<4><<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
+            const size_t smem = (size_t)(vpl * 32) * (vpl * 32) * 4 + 8 * 2 * (vpl * 32) * 4;
+            // a resident grid (the column queue feeds it)
+            auto fn = vpl == 1 ? k_bsmall<1> : vpl == 2 ? k_bsmall<2> : k_bsmall<4>;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return ALN_ERR_CUDA;
+            int per_sm = 1;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem) !=
+                    cudaSuccess ||
+                per_sm < 1) {
+                cudaGetLastError();
+                per_sm = 1;
             }
+            const unsigned grid = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((k + 7) / 8, (int64_t)per_sm * c->num_sms));
+            if (cudaMemsetAsync(s.counters + 2, 0, sizeof(int), c->stream) != cudaSuccess)
+                return ALN_ERR_CUDA;
+            fn<<<grid, 256, smem, c->stream>>>(s, (const float*)c->Q);
             if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
             c->launches += 1;
             l = 1;
