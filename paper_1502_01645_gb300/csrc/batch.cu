@@ -16,6 +16,7 @@
 // FP64 q: g64 = Q64 y + q (one FP64 product for all columns), then
 // rel_c = ‖ḡ64_c‖/‖min(q_c, 0)‖ and ½‖Ax − b‖² = ½yᵀg64 + ½qᵀy + ½‖b‖².
 // Columns above tol restart from y_c with g_c = g64_c (refinement).
+#include "blockops.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -542,6 +543,152 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
 }
 
 // ---------------------------------------------------------------------------
+// Tail of the batched phase: one 1024-thread block per running column.
+// Once few columns are still running, each batched iteration is dominated by
+// launch and tile latency (about 30-90 µs per iteration whatever the count),
+// while one block runs a column's iteration from L2-resident Q32 in a few
+// µs.  The block takes the next running column from a queue (counters[2]),
+// runs Alg. 2 on it to its stop with the same rules and per-column state as
+// k_bmask / k_bupdate (FP32 iterate, FP64 sums of the step scalars), and
+// writes y, g and the state back for the FP64 check.
+__global__ void __launch_bounds__(kGThreads, 1) k_bblock(BatchState s, const float* __restrict__ Q32) {
+    extern __shared__ __align__(16) uint8_t bsm[];
+    __shared__ GRed<float> rs;
+    __shared__ int s_c, s_flag;
+    __shared__ float s_alpha;
+    const int n = (int)s.n;
+    const int ldq = (int)s.ldq;
+    float* sy = reinterpret_cast<float*>(bsm);
+    float* sg = sy + ldq;
+    float* sgb = sg + ldq;
+    float* sw = sgb + ldq;  // w = Qḡ, then e
+    int* lp = reinterpret_cast<int*>(sw + ldq);
+    int* lc = lp + ldq;
+    float* red = reinterpret_cast<float*>(lc + ldq);
+    for (;;) {
+        if (threadIdx.x == 0) s_c = atomicAdd(&s.counters[2], 1);
+        __syncthreads();
+        const int64_t c = s_c;
+        __syncthreads();
+        if (c >= s.k) break;
+        if (s.colst[c] >= 0) continue;  // block-uniform
+        for (int i = threadIdx.x; i < ldq; i += blockDim.x) {
+            sy[i] = i < n ? s.Y[c * s.ldq + i] : 0.0f;
+            sg[i] = i < n ? s.G[c * s.ldq + i] : 0.0f;
+            sw[i] = 0.0f;
+        }
+        __syncthreads();
+        int it = s.iters[c], best_iter = s.best_iter[c], status = -1;
+        double best = s.best[c];
+        const double eps = s.eps[c];
+        const int max_iter = s.limits[0], window = s.limits[1];
+        unsigned long long rowsP = 0, rowsC = 0, clipIt = 0;
+        double gam;
+        int cntP, cntL;
+        gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int st = -1;
+                if (!isfinite(gam)) st = ALN_RHS_NONFINITE;
+                else if (cntP == 0) st = ALN_RHS_EMPTY_PASSIVE;
+                else if (gam < eps || gam == 0.0) st = ALN_RHS_CONVERGED;
+                else if (it >= max_iter) st = ALN_RHS_MAXITER;
+                else if (it - best_iter > window) st = ALN_RHS_STAGNATED;
+                if (st < 0 && gam < best) {
+                    best = gam;
+                    best_iter = it;
+                }
+                status = st;
+                s_flag = st >= 0;
+            }
+            __syncthreads();
+            if (s_flag) break;
+            rowsP += (unsigned long long)cntP;
+            // w = Qḡ over the listed rows, κ = ḡᵀw, α = γ/κ
+            gmv(Q32, ldq, 0, n, lp, cntL, sgb, sw, false, red);
+            float kp = 0.0f;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fmaf(sgb[i], sw[i], kp);
+            double kap;
+            int u1, u2;
+            (void)block_totals(&rs, kp, 0, 0, &kap, &u1, &u2);
+            if (threadIdx.x == 0) {
+                int st = -1;
+                if (!isfinite(kap)) st = ALN_RHS_NONFINITE;
+                else if (kap <= 0.0) st = ALN_RHS_CURVATURE;
+                s_alpha = st >= 0 ? 0.0f : (float)(gam / kap);
+                if (st >= 0) status = st;
+                s_flag = st >= 0;
+            }
+            __syncthreads();
+            if (s_flag) break;
+            const float a = s_alpha;
+            // y⁺ = [y − αḡ]₊, g ← g − αw, e on the clipped set (then g += Qe)
+            int nclip = 0;
+            {
+                const int lane = threadIdx.x & 31;
+                int c0, c1;
+                warp_chunks(n, c0, c1);
+                int cl = 0;
+                for (int ch = c0; ch < c1; ++ch) {
+                    const int i = ch * 32 + lane;
+                    float ei = 0.0f;
+                    if (i < n) {
+                        const float yi = sy[i];
+                        const float step = a * sgb[i];
+                        float yn = yi - step;
+                        if (yn < 0.0f) {
+                            ei = step - yi;
+                            yn = 0.0f;
+                        }
+                        sy[i] = yn;
+                        sg[i] = sg[i] - a * sw[i];
+                        sw[i] = ei;
+                    }
+                    cl += __popc(__ballot_sync(0xffffffffu, ei != 0.0f));
+                }
+                double vt;
+                int ct;
+                int base = block_totals(&rs, 0.0f, 0, cl, &vt, &ct, &nclip);
+                for (int ch = c0; ch < c1; ++ch) {
+                    const int i = ch * 32 + lane;
+                    const bool nz = i < n && sw[i] != 0.0f;
+                    const unsigned int m = __ballot_sync(0xffffffffu, nz);
+                    if (nz) lc[base + __popc(m & ((1u << lane) - 1u))] = i;
+                    base += __popc(m);
+                }
+                __syncthreads();
+            }
+            ++it;
+            if (nclip > 0) {
+                rowsC += (unsigned long long)nclip;
+                ++clipIt;
+                gmv(Q32, ldq, 0, n, lc, nclip, sw, sg, true, red);
+            }
+            gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            s.Y[c * s.ldq + i] = sy[i];
+            s.G[c * s.ldq + i] = sg[i];
+        }
+        if (threadIdx.x == 0) {
+            s.colst[c] = status;
+            s.iters[c] = it;
+            s.best[c] = best;
+            s.best_iter[c] = best_iter;
+            atomicAdd(&s.rows[0], rowsP);
+            atomicAdd(&s.rows[1], rowsC);
+            atomicAdd(&s.rows[2], clipIt);
+        }
+        __syncthreads();
+    }
+}
+
+static size_t bblock_smem(int64_t ldq) {
+    return (size_t)ldq * (4 * sizeof(float) + 2 * sizeof(int)) +
+           (size_t)kGWarps * 32 * 4 * sizeof(float);
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 // Progressive refinement is on by default here: with many columns the FP64
@@ -838,6 +985,24 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         c->launches += 3;
     }
     const int max_refine = c->opt.max_refine;
+    // tail: at most tail_max running columns go to k_bblock (one block each)
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    const size_t tsmem = bblock_smem(c->ldq);
+    const bool tail_ok = !b->small_vpl && tsmem + 1024 <= (size_t)optin;
+    const int64_t tail_max = 2LL * c->num_sms;
+    auto run_tail = [&](int64_t running) -> aln_status {
+        if (cudaFuncSetAttribute(k_bblock, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tsmem) != cudaSuccess ||
+            cudaMemsetAsync(s.counters + 2, 0, sizeof(int), c->stream) != cudaSuccess)
+            return ALN_ERR_CUDA;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(running, c->num_sms));
+        k_bblock<<<grid, kGThreads, tsmem, c->stream>>>(s, (const float*)c->Q);
+        if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
+        c->launches += 1;
+        return ALN_OK;
+    };
+    int64_t active = k;  // running columns at the start of a round
     for (int round = 0;; ++round) {
         // inner runs: the captured chunk until no column is running (small n:
         // one warp-per-column launch runs every column to its stop)
@@ -868,6 +1033,13 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
             c->launches += 1;
             l = 1;
         }
+        bool handed = false;
+        if (tail_ok && active <= tail_max) {  // few columns: no batched chunk at all
+            aln_status ts = run_tail(active);
+            if (ts != ALN_OK) return ts;
+            handed = true;
+            l = bound;
+        }
         for (; l < bound; ++l) {
             if (cudaGraphLaunch(b->graph, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
             c->launches += 5LL * b->chunk;
@@ -876,17 +1048,24 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
                 cudaStreamSynchronize(c->stream) != cudaSuccess)
                 return ALN_ERR_CUDA;
             if (b->host[0] == 0) break;
+            if (tail_ok && b->host[0] <= tail_max) {  // the rest, one block per column
+                aln_status ts = run_tail(b->host[0]);
+                if (ts != ALN_OK) return ts;
+                handed = true;
+                break;
+            }
         }
         cudaEventRecord(c->ev[9], c->stream);
         cudaEventSynchronize(c->ev[9]);
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
             c->stats.iterate_ms += ms;
-        if (!b->small_vpl && l == bound) return ALN_ERR_TIMEOUT;
+        if (!b->small_vpl && !handed && l == bound) return ALN_ERR_TIMEOUT;
         int restarted = 0;
         aln_status st = bw_check(c, b, tol, max_refine, &restarted);
         if (st != ALN_OK) return st;
         if (restarted == 0) break;
+        active = restarted;
     }
     // results: x (FP64) and per-column records
     const bool x_dev = [&] {

@@ -325,6 +325,26 @@ def test_batched_multi_rhs_matches_oracle(aln):
         np.testing.assert_allclose(infob[c].objective, F, rtol=1e-9)
 
 
+def test_batched_phase_then_tail(aln):
+    """More columns than the tail threshold (2 per SM): the tcgen05 batched
+    phase runs first and hands the last columns to the per-column block
+    kernel; every column meets the FP64 KKT gate and agrees with the single
+    right-hand-side path."""
+    p = W.shared_multi_rhs(d=1200, n=180, k=420, seed=38)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.A, p.B)
+        X, info = s.solve(tol=1e-8)
+    A64 = p.A.astype(np.float64)
+    for c in range(0, p.k, 7):
+        rel, _ = O.kkt_residual(A64, p.B[c].astype(np.float64), X[c])
+        assert rel <= 1e-8, (c, rel, info[c])
+    with aln.Solver("split_bf16", batch_min=10 ** 6) as s:
+        s.prepare(p.A, p.B[:20])
+        Xs, _ = s.solve(tol=1e-8)
+    for c in range(20):
+        assert np.linalg.norm(X[c] - Xs[c]) <= 1e-4 * max(np.linalg.norm(Xs[c]), 1e-30)
+
+
 def test_batched_agrees_with_single_rhs_path(aln):
     p = W.shared_multi_rhs(d=800, n=200, k=12, seed=35)
     with aln.Solver("split_bf16") as s:
