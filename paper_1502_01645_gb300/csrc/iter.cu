@@ -164,13 +164,16 @@ __global__ void __launch_bounds__(kVecThreads) k_finish(
     if (threadIdx.x == 0) gpart[blockIdx.x] = acc;
 }
 
+// x = (y + ylo)/s (Eq. Rescaling); ylo: the low part of a float-pair
+// iterate, or null.
 template <typename T>
 __global__ void __launch_bounds__(kVecThreads) k_unscale(int n, const T* __restrict__ y,
+                                                         const T* __restrict__ ylo,
                                                          const double* __restrict__ s,
                                                          double* __restrict__ x) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (double)y[i] / s[i];
+        x[i] = ((double)y[i] + (ylo ? (double)ylo[i] : 0.0)) / s[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -224,8 +227,12 @@ cudaError_t launch_iter_refresh_from_g64(aln_ctx* c, double eps, int max_iter) {
 
 template <typename T>
 cudaError_t launch_unscale(aln_ctx* c, double* x64) {
+    // the replicated FP32 kernel keeps the low part of y in e (zero from the
+    // set-up, and never written by Anti+Acc); the tiled kernel uses e for
+    // its clipped corrections
+    const T* ylo = (c->p_repl && sizeof(T) == 4) ? (const T*)c->e : nullptr;
     k_unscale<T><<<(unsigned)std::min<int64_t>(ceil_div(c->n, kVecThreads), 1024), kVecThreads, 0,
-                   c->stream>>>((int)c->n, (const T*)c->y, c->s, x64);
+                   c->stream>>>((int)c->n, (const T*)c->y, ylo, c->s, x64);
     return cudaGetLastError();
 }
 

@@ -439,6 +439,7 @@ struct ReplArgs {
     int R;
     int rows_per_group;
     T* y;            // in/out (global), ldq
+    T* ylo;          // in/out (global), ldq: low part of the float-pair y (FP32 only)
     T* g;            // in/out (global), ldq
     T* part;         // 2 × R × ldq  (w partials, by iteration parity)
     T* part2;        // R × ldq      (Qe partials)
@@ -741,6 +742,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     T* sgb = sg + a.ldq;
     T* sw = sgb + a.ldq;     // w, then e
     T* red = sw + a.ldq;     // kPWarps × TILE
+    // FP32: the iterate is a pair y = sy + syl (|syl| ≤ ulp(sy)/2), so the
+    // FP64 refinement converges below the FP32 rounding of y (the steps αḡ
+    // near the optimum are far below ulp(y)); FP64 needs no low part.
+    constexpr bool DF = sizeof(T) == 4;
+    T* syl = red + kPWarps * TILE;
     __shared__ double sd[32];
     __shared__ int si[32];
     __shared__ double s_t[33];
@@ -755,6 +761,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
 
     for (int j = threadIdx.x; j < a.ldq; j += blockDim.x) {
         sy[j] = j < n ? __ldcg(a.y + j) : T(0);
+        if (DF) syl[j] = j < n ? __ldcg(a.ylo + j) : T(0);
         sg[j] = j < n ? __ldcg(a.g + j) : T(0);
         sw[j] = T(0);
     }
@@ -848,13 +855,31 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         T v2 = T(0);
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const T yi = sy[j];
-            const T step = aT * sgb[j];
-            T yn = yi - step;
-            T ej = T(0);
-            if (yn < T(0)) {
-                ej = step - yi;
-                yn = T(0);
-                ++clipped;
+            T yn, ej = T(0);
+            if (DF) {
+                // (sy, syl) − αḡ exactly: TwoSum, then renormalise
+                const T step = __fmul_rn((float)aT, (float)sgb[j]);
+                const T s1 = yi - step;
+                const T bb = s1 - yi;
+                const T er = (yi - (s1 - bb)) + (-step - bb);
+                const T t = syl[j] + er;
+                yn = s1 + t;
+                T nl = t - (yn - s1);
+                if (yn < T(0)) {  // clipped: y⁺ = 0, e = y⁺ − (y − αḡ)
+                    ej = -(yn + nl);
+                    yn = T(0);
+                    nl = T(0);
+                    ++clipped;
+                }
+                syl[j] = nl;
+            } else {
+                const T step = aT * sgb[j];
+                yn = yi - step;
+                if (yn < T(0)) {
+                    ej = step - yi;
+                    yn = T(0);
+                    ++clipped;
+                }
             }
             const T gn = sg[j] - aT * sw[j];
             sy[j] = yn;
@@ -905,6 +930,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     if (blockIdx.x == 0) {
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             a.y[j] = sy[j];
+            if (DF) a.ylo[j] = syl[j];
             a.g[j] = sg[j];
         }
         if (threadIdx.x == 0) {
@@ -924,8 +950,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
 }
 
 template <typename T>
-size_t repl_smem_bytes(int64_t ldq) {
-    return (size_t)(4 * ldq + kPWarps * 32 * Vec16<T>::N) * sizeof(T);
+size_t repl_smem_bytes(int64_t ldq) {  // FP32 adds the low part of y
+    return (size_t)((sizeof(T) == 4 ? 5 : 4) * ldq + kPWarps * 32 * Vec16<T>::N) * sizeof(T);
 }
 
 // ---------------------------------------------------------------------------
@@ -940,6 +966,7 @@ cudaError_t launch_alg2_persist(aln_ctx* c) {
         r.R = c->p_R;
         r.rows_per_group = (int)ceil_div(c->n, c->p_R);
         r.y = (T*)c->y;
+        r.ylo = (T*)c->e;  // the tiled kernel's e buffer, unused by this one
         r.g = (T*)c->g;
         r.part = (T*)c->part;
         r.part2 = (T*)c->part + (int64_t)2 * c->p_R * c->ldq;

@@ -135,6 +135,23 @@ def _mixed_gate(A, b, x, x_star):
     assert np.linalg.norm(x - x_star) / np.linalg.norm(x_star) <= 1e-5
 
 
+@pytest.mark.parametrize("d,n", [(3000, 800), (900, 300)])
+def test_single_rhs_tight_tolerance(aln, d, n):
+    """The replicated kernel keeps y as a float pair, so the FP64 refinement
+    reaches relative KKT 1e-11, far below the FP32 rounding of y."""
+    p = W.lopsided_single(d=d, n=n, seed=40 + n)
+    A, b = p.A, p.B[0]
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-11)
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    rel, _ = O.kkt_residual(A64, b64, X[0])
+    assert rel <= 1e-11, (rel, info[0])
+    assert info[0].status == aln.RHS_CONVERGED
+    x_star, _, _, _ = O.reference_solution(A64, b64)
+    assert np.linalg.norm(X[0] - x_star) <= 1e-7 * np.linalg.norm(x_star)
+
+
 def test_mixed_solve_lopsided(aln):
     """Lopsided single-RHS configuration at reduced size (4000×1000)."""
     p = W.lopsided_single(d=4000, n=1000)
