@@ -92,6 +92,7 @@ def parse():
     ap.add_argument("--train", type=int, default=None,
                     help="training right-hand sides of the warm-start workload")
     ap.add_argument("--epochs", type=int, default=60, help="warm-start training epochs")
+    ap.add_argument("--hidden", type=int, default=4096, help="warm-start network width")
     ap.add_argument("--gram-split", type=int, default=0,
                     help="BF16 terms of the split Gram (2 or 3; 0: library default)")
     ap.add_argument("--refine-gain", type=int, default=0,
@@ -1068,7 +1069,7 @@ def run_warmstart(args, w, world, rank, local):
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = solver.warmstart_train(Qtr, Ytr, epochs=args.epochs, batch=1024, hidden=1024,
+    hist = solver.warmstart_train(Qtr, Ytr, epochs=args.epochs, batch=1024, hidden=args.hidden,
                                   lr=1e-3, seed=5)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
