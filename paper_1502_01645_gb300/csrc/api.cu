@@ -374,6 +374,9 @@ void aln_destroy(aln_ctx* c) {
     if (c->host_pool) cudaFreeHost(c->host_pool);
     for (auto ev : c->ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto ev : c->copy_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -388,7 +391,18 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     c->grouped = 0;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
-    ALN_CHECK(resolve_input(c, A, d, n, lda, esz, &c->A_copy, &c->A_copy_bytes, &c->A));
+    // A on the host, single-problem split path with q fused in the column
+    // statistics: copy A in column chunks and overlap the copy with the
+    // statistics and Gram tile rows of the chunks already on the device
+    const bool pipelined = !is_device_ptr(A) && c->opt.precision == ALN_PREC_SPLIT_BF16 &&
+                           k <= 4 && k < c->opt.batch_min && n > 256;
+    if (pipelined) {
+        const size_t bytes = (size_t)((n - 1) * lda + d) * esz;
+        ALN_CHECK(ensure(&c->A_copy, &c->A_copy_bytes, bytes));
+        c->A = c->A_copy;
+    } else {
+        ALN_CHECK(resolve_input(c, A, d, n, lda, esz, &c->A_copy, &c->A_copy_bytes, &c->A));
+    }
     ALN_CHECK(resolve_input(c, B, d, k, ldb, esz, &c->B_copy, &c->B_copy_bytes, &c->B));
     c->d = d;
     c->n = n;
@@ -456,8 +470,40 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     ALN_TRY(cudaEventRecord(c->ev[0], c->stream));
     ALN_TRY(launch_check_finite(c->B, dtype, d, k, ldb, c->flags, c->stream));
     const int kc = k <= 4 ? (int)k : 0;
-    ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64, ldq,
-                            c->flags, hi, mid, lo, c->ldk, c->stream));
+    if (pipelined) {
+        if (!c->copy_stream) {
+            ALN_TRY(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            for (auto& ev : c->copy_ev)
+                ALN_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
+        // the copy stream starts after the main stream's earlier work (the
+        // previous users of the A buffer)
+        ALN_TRY(cudaEventRecord(c->copy_ev[0], c->stream));
+        ALN_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[0], 0));
+        const int64_t per = std::max<int64_t>(1024, round_up(ceil_div(n, 63), 128));
+        const int64_t tiles = ceil_div(n, 128);
+        int e = 1;
+        for (int64_t c0 = 0; c0 < n; c0 += per, ++e) {
+            const int64_t c1 = std::min(n, c0 + per);
+            const uint8_t* src = (const uint8_t*)A + (size_t)c0 * lda * esz;
+            uint8_t* dst = (uint8_t*)c->A_copy + (size_t)c0 * lda * esz;
+            ALN_TRY(cudaMemcpy2DAsync(dst, (size_t)lda * esz, src, (size_t)lda * esz, (size_t)d * esz,
+                                      (size_t)(c1 - c0), cudaMemcpyHostToDevice, c->copy_stream));
+            ALN_TRY(cudaEventRecord(c->copy_ev[e], c->copy_stream));
+            ALN_TRY(cudaStreamWaitEvent(c->stream, c->copy_ev[e], 0));
+            ALN_TRY(launch_colstats(dst, dtype, d, c1 - c0, lda, c->B, kc, ldb, c->s + c0,
+                                    c->inv_s + c0, c->q64 + c0, ldq, c->flags, hi + c0 * c->ldk,
+                                    mid + c0 * c->ldk, lo + c0 * c->ldk, c->ldk, c->stream));
+            if (c0 == 0) ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
+            ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
+                                   (float*)c->Q, ldq, c->flags + 1, c->stream, c0 / 128,
+                                   c1 == n ? tiles : c1 / 128));
+            c->launches += 2;
+        }
+    } else {
+        ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64,
+                                ldq, c->flags, hi, mid, lo, c->ldk, c->stream));
+    }
     if (kc == 0) {
         if (c->batched && dtype == ALN_DTYPE_F32)  // FP64-accurate, on the FP32 pipe
             ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
@@ -467,8 +513,10 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
                                   c->stream));
     }
     ALN_TRY(launch_denominators(c->q64, n, ldq, k, c->den, c->stream));
-    ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
-    if (c->batched)
+    if (!pipelined) ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
+    if (pipelined)
+        ;  // the Gram ran chunk by chunk above
+    else if (c->batched)
         ALN_CHECK(batch_prepare(c));
     else if (f64)
         ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));

@@ -272,6 +272,10 @@ struct aln_ctx {
 
     // statistics (aln_get_stats)
     cudaEvent_t ev[10] = {};
+    // host-input prepare: A copied in column chunks on copy_stream, each
+    // chunk's column statistics and Gram tile rows run as it lands
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[64] = {};
     aln_stats stats = {};
     int64_t launches = 0;
 };

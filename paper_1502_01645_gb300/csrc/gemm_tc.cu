@@ -28,6 +28,7 @@ namespace tc {
 
 struct GramArgs {
     int64_t n;
+    int64_t t0;  // first lower-triangle tile of this launch (a range of tile rows)
     int num_kb;
     const double* inv_s;
     float* Q;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(G3_THREADS, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
               const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
     int tm, tn;
-    tri_decode(blockIdx.x, tm, tn);
+    tri_decode(blockIdx.x + p.t0, tm, tn);
     const TmaLoader<NS> ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM};
     gram_tile<NS>(ld, p.num_kb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
                   p.ldq, p.timeout_flag);
@@ -546,7 +547,7 @@ bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_mino
 cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
-                           cudaStream_t st) {
+                           cudaStream_t st, int64_t row0, int64_t row1) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
@@ -575,7 +576,12 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
     const int64_t tiles = ceil_div(n, BM);
-    const unsigned grid = (unsigned)(tiles * (tiles + 1) / 2);
+    if (row1 < 0 || row1 > tiles) row1 = tiles;
+    if (row0 < 0 || row0 >= row1) return cudaSuccess;
+    // tiles (I, J ≤ I) with row0 ≤ I < row1 are the contiguous range
+    // [row0(row0+1)/2, row1(row1+1)/2) of the triangle order
+    a.t0 = row0 * (row0 + 1) / 2;
+    const unsigned grid = (unsigned)(row1 * (row1 + 1) / 2 - a.t0);
     if (nsplit == 3)
         k_gram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
     else

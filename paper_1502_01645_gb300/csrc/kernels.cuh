@@ -46,7 +46,7 @@ cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, in
 cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
-                           cudaStream_t st);
+                           cudaStream_t st, int64_t row0 = 0, int64_t row1 = -1);
 bool tc_supported(int cc_major, int cc_minor);
 // W = Q·V (mode 0, with per-column curvature partials) or g += Q·V (mode 1)
 // over the compacted columns of a batch (batch.cu).
