@@ -480,6 +480,8 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
         // previous users of the A buffer)
         ALN_TRY(cudaEventRecord(c->copy_ev[0], c->stream));
         ALN_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[0], 0));
+        // chunks of at least 1024 columns: a Gram launch lasts at least one
+        // tile's full K loop (about 0.4 ms at d = 20000) whatever its size
         const int64_t per = std::max<int64_t>(1024, round_up(ceil_div(n, 63), 128));
         const int64_t tiles = ceil_div(n, 128);
         int e = 1;
