@@ -898,7 +898,6 @@ __global__ void k_bsetg(BatchState s, const double* __restrict__ G64) {
         s.G[c * s.ldq + i] = (float)G64[c * s.ldq + i];
 }
 
-static aln_status cuda_st(cudaError_t e) { return e == cudaSuccess ? ALN_OK : ALN_ERR_CUDA; }
 
 // FP64 check of every not-yet-final column; returns how many were restarted.
 static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine, int* restarted) {

@@ -523,16 +523,6 @@ __device__ __forceinline__ double block_sum_bcast(double v, double* sc) {
     for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sc[w2];
     return s;
 }
-__device__ __forceinline__ int block_sum_bcast_i(int v, int* sc) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum_i(v);
-    __syncthreads();
-    if (lane == 0) sc[wid] = v;
-    __syncthreads();
-    int s = 0;
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += sc[w2];
-    return s;
-}
 
 // GB300's FP64 pipe is narrow: an FP64 instruction issued by all 1024
 // threads of a block costs microseconds.  The per-iteration reductions
@@ -545,24 +535,6 @@ __device__ __forceinline__ T warp_sum_t(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
-// Sum of v over the block: a shuffle tree in each warp, then warp 0 folds
-// the warp partials with the same tree; every thread receives the result.
-template <typename T>
-__device__ __forceinline__ T block_sum_t(T v, T* sc) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = warp_sum_t(v);
-    __syncthreads();
-    if (lane == 0) sc[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        T x = lane < (int)(blockDim.x >> 5) ? sc[lane] : T(0);
-        x = warp_sum_t(x);
-        if (lane == 0) sc[32] = x;
-    }
-    __syncthreads();
-    return sc[32];
-}
-
 // The same tree with the 32 warp partials added in FP64 by warp 0: the
 // scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ, α = γ/κ) need more than FP32 —
 // with FP32 scalars the FP32 iteration drifted from the true gradient by
