@@ -139,6 +139,25 @@ def peaks():
     return FALLBACK_PEAKS, "fallback"
 
 
+# ------------------------------------------------------------------ multi-rank
+def max_over_ranks(x, world, device="cuda"):
+    """The largest x over the ranks: a job's time is its slowest rank's.
+    With one rank, x itself (no process group needed)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, steps, world, seconds):
+    """Whole-job throughput: every rank solves its own units each step (weak
+    scaling: replicas with no data-path collective)."""
+    return world * steps * units_per_rank_step / seconds
+
+
 # ----------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clocks/throttle reasons sampled every 200 ms in the background."""
@@ -383,11 +402,8 @@ def run_ours(args):
     if worst > tol:
         raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
 
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * args.steps * k / tmax
+    tmax = max_over_ranks(elapsed, world)
+    value = job_rate(k, args.steps, world, tmax)
 
     def avg(f):
         return sum(f(s) for s in stats) / len(stats)
@@ -411,10 +427,7 @@ def run_ours(args):
         barrier()
         te = time.perf_counter() - t0
         hsolver.close()
-        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * k_e2e * k / float(te_t.item()), "unit": UNIT,
+        e2e = {"value": job_rate(k, k_e2e, world, max_over_ranks(te, world)), "unit": UNIT,
                "h2d_bytes_per_step": int(A_np.nbytes + B_np.nbytes),
                "d2h_bytes_per_step": int(k * n * 8), "steps": k_e2e,
                "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
@@ -607,11 +620,8 @@ def run_grouped(args, w, world, rank, local):
     clocks = sampler.stop()
     if worst > tol:
         raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * args.steps * k / tmax
+    tmax = max_over_ranks(elapsed, world)
+    value = job_rate(k, args.steps, world, tmax)
 
     def avg(f):
         return sum(f(s) for s in stats) / len(stats)
@@ -636,10 +646,7 @@ def run_grouped(args, w, world, rank, local):
         barrier()
         te = time.perf_counter() - t0
         hsolver.close()
-        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * k_e2e * k / float(te_t.item()), "unit": UNIT,
+        e2e = {"value": job_rate(k, k_e2e, world, max_over_ranks(te, world)), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(p.A.nbytes + p.B.nbytes for p in probs)),
                "d2h_bytes_per_step": int(N * 8), "steps": k_e2e,
                "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
@@ -807,11 +814,8 @@ def run_tcases(args, w, world, rank, local):
     bad = [p.name for p, r in zip(probs, runs[-1]) if r[0].rel_kkt > tol]
     if bad:
         raise SystemExit(f"invalid run: rel KKT above {tol} for {bad}")
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * args.steps * k / tmax
+    tmax = max_over_ranks(elapsed, world)
+    value = job_rate(k, args.steps, world, tmax)
 
     # ---- end to end: pinned host inputs and result, copies inside the region ----
     e2e = None
@@ -969,12 +973,9 @@ def run_nmf(args, w, world, rank, local):
     obj = objs[-1]
     if any(b > a * (1 + 1e-6) for a, b in zip(obj, obj[1:])):
         raise SystemExit(f"invalid run: objective rose {list(obj)}")
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
+    tmax = max_over_ranks(elapsed, world)
     solves = (m + n) * outer
-    value = world * args.steps * solves / tmax
+    value = job_rate(solves, args.steps, world, tmax)
 
     e2e = None
     if not args.no_e2e:
@@ -1115,11 +1116,8 @@ def run_warmstart(args, w, world, rank, local):
     worst = max(max(i.rel_kkt for i in info) for info in infos)
     if worst > tol:
         raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
-    t = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    tmax = float(t.item())
-    value = world * args.steps * k / tmax
+    tmax = max_over_ranks(elapsed, world)
+    value = job_rate(k, args.steps, world, tmax)
     warm_iters = float(np.mean([i.iters for i in infos[-1]]))
     X0_host = X0.cpu().numpy()
     kept_frac = float(np.mean(np.abs(X0_host).sum(axis=1) > 0))
