@@ -13,6 +13,11 @@
  *                 passive set P = {y_i > 0 or g_i < 0}, ḡ = g on P,
  *                 α = ‖ḡ‖²/(ḡᵀQḡ), y ← [y − αḡ]₊, g ← g + Q(y_new − y).
  *
+ * Also: the Anti+Acc variant of §5 (aln_options.algorithm), non-negative
+ * matrix factorisation by alternating NNLS on the multi-RHS solver (aln_nmf),
+ * and a learned start point for families of right-hand sides that share A
+ * (aln_warmstart_*).
+ *
  * Sign convention: q is the paper's, q = −D⁻¹Aᵀb with D = diag(‖A_i‖), so the
  * gradient of ½yᵀQy + qᵀy is g = Qy + q.
  *
@@ -207,8 +212,10 @@ aln_status aln_prepare_grouped(aln_ctx* ctx, int32_t count, const aln_problem* p
  *   X0        optional start point in x-space (FP64, same layout, ≥ 0), or NULL
  *             for Alg. 2's x⁰ = 0.  Mapped to y0 = x0·s.
  *   info      optional array of k records (host memory).
- * Errors: NOT_PREPARED, INVALID_ARG, NONFINITE (X0), TIMEOUT, CUDA.  Hitting
- * max_iter is not an error; it is reported per right-hand side. */
+ * Errors: NOT_PREPARED, INVALID_ARG, NONFINITE (X0), TIMEOUT, UNSUPPORTED
+ * (ALN_ALG_ANTI_ACC outside the single-problem path, or n too large for its
+ * shared-memory state), CUDA.  Hitting max_iter is not an error; it is
+ * reported per right-hand side. */
 aln_status aln_solve(aln_ctx* ctx, double tol, int32_t max_iter, double* X, int64_t ldx,
                      const double* X0, aln_solve_info* info);
 
