@@ -171,3 +171,20 @@ def test_full_size_lopsided_single(aln):
     assert rel <= 1e-6 and np.all(X[0] >= 0.0)
     np.testing.assert_allclose(info[0].rel_kkt, rel, rtol=1e-4)
     assert st.lipschitz > 0.0 and st.power_products >= 2
+
+
+def test_fp64_warm_start_and_several_rhs(aln):
+    """FP64 Anti+Acc with three right-hand sides solved in turn, then
+    restarted from the solutions (no step needed)."""
+    A, _ = _lopsided(300, 90, seed=17, dtype=np.float64)
+    r = np.random.default_rng(18)
+    Xt = np.where(r.random((3, 90)) < 0.6, 0.0, r.random((3, 90)))
+    B = Xt @ A.T
+    with aln.Solver("fp64", algorithm=aln.ALG_ANTI_ACC) as sv:
+        sv.prepare(A, B)
+        X, info = sv.solve(tol=1e-10, max_iter=400000)
+        X2, info2 = sv.solve(tol=1e-10, X0=X)
+    for c in range(3):
+        rel, _ = O.kkt_residual(A, B[c], X[c])
+        assert rel <= 1e-10, (c, rel)
+        assert info2[c].iters == 0

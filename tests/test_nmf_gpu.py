@@ -109,3 +109,20 @@ def test_full_size(aln):
     for i in range(0, 4096, 512):
         rel, _ = O.kkt_residual(Hg.T, V64[i, :], Wg[i, :])
         assert rel <= 1e-6 * 1.01, (i, rel)
+
+
+def test_rank_one_and_fp64_context(aln):
+    """r = 1 (scalar sub-problems), and a context in FP64 precision (each
+    sub-problem by the FP64 method, one right-hand side at a time)."""
+    V, W0, H0 = W.nmf_matrix(40, 30, 1, seed=31)
+    Wo, Ho, objo = N.anls(V.astype(np.float64), W0, H0, outer=3, tol=1e-10)
+    with aln.Solver("split_bf16") as s:
+        Wg, Hg, obj = s.nmf(V, W0, H0, outer=3, tol=1e-8)
+    np.testing.assert_allclose(obj, objo, rtol=1e-6)
+    V2, W2, H2 = W.nmf_matrix(30, 20, 3, seed=32)
+    Wo2, Ho2, objo2 = N.anls(V2.astype(np.float64), W2, H2, outer=2, tol=1e-11)
+    with aln.Solver("fp64") as s:
+        Wg2, Hg2, obj2 = s.nmf(V2, W2, H2, outer=2, tol=1e-11)
+    # each half-step's matrix is the other factor rounded to FP32 (the input
+    # type of V), so the sub-problems differ from the oracle's by ~6e-8
+    np.testing.assert_allclose(obj2, objo2, rtol=1e-6)

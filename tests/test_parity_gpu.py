@@ -375,7 +375,7 @@ def test_batched_agrees_with_single_rhs_path(aln):
 
 
 @pytest.mark.parametrize("d,n,k", [(600, 100, 40), (300, 33, 24), (200, 7, 16), (500, 128, 20),
-                                   (90, 32, 9)])
+                                   (90, 32, 9), (260, 64, 12), (270, 65, 12)])
 def test_batched_small_n_matches_oracle(aln, d, n, k):
     """n ≤ 128: the warp-per-column kernel runs each column's Alg. 2 loop
     (VPL = 1, 2, 4 entries per lane, ragged n); every column meets the FP64
