@@ -501,26 +501,33 @@ __global__ void __launch_bounds__(128, 1)
         for (int c0 = 0; c0 < cols; c0 += 16) {
             float v[16];
             tmem_ld16(tbase + c0, v);
+            // the 16 columns' global operands are loaded before any is used,
+            // so their latencies overlap (one dependent load per column put a
+            // full L2 round trip on the critical path of every column)
+            int colv[16];
+            float xv[16];
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 const int cc = c0 + t;
-                const int col = cc < cols ? s_map[cc] : -1;
+                colv[t] = cc < cols ? s_map[cc] : -1;
+                const bool in = colv[t] >= 0 && rv;
+                const int64_t off = (int64_t)(in ? colv[t] : 0) * p.ldq + (in ? row : 0);
+                xv[t] = in ? (MODE == BMODE_W ? __ldg(p.gb + off) : p.g[off]) : 0.0f;
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int cc = c0 + t;
+                const bool in = colv[t] >= 0 && rv;
                 if (MODE == BMODE_W) {
                     // curvature partial in FP32 (the FP64 pipe is narrow on
                     // this GPU); the row-tile partials are summed in FP64
-                    float kp = 0.0f;
-                    if (col >= 0 && rv) {
-                        p.W[(n0 + cc) * p.ldq + row] = v[t];
-                        kp = p.gb[(int64_t)col * p.ldq + row] * v[t];
-                    }
+                    if (in) p.W[(n0 + cc) * p.ldq + row] = v[t];
+                    float kp = in ? xv[t] * v[t] : 0.0f;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) kp += __shfl_xor_sync(0xffffffffu, kp, o);
                     if (lane == 0) s_red[warp][cc] = kp;
                 } else {
-                    if (col >= 0 && rv) {
-                        float* gp = p.g + (int64_t)col * p.ldq + row;
-                        *gp = *gp + v[t];
-                    }
+                    if (in) p.g[(int64_t)colv[t] * p.ldq + row] = xv[t] + v[t];
                 }
             }
         }
