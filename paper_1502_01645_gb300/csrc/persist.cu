@@ -47,51 +47,67 @@ __device__ __forceinline__ uint64_t p_globaltimer() {
     return t;
 }
 
+constexpr int kSyncLanes = 8;  // arrival counters, one 128-byte line each
+
 struct PersistSync {
-    unsigned int count;    // monotonic arrivals: barrier k completes at k·G
+    // monotonic arrivals spread over kSyncLanes counters (block b adds to
+    // counter b mod kSyncLanes, so the arrivals do not queue on one L2 line);
+    // barrier k completes when their sum reaches k·G
+    unsigned int count[kSyncLanes][32];
     unsigned int timeout;  // set by the first block whose wait expired
-    unsigned int pad[2];
+    unsigned int pad[31];
 };
 
 // Grid barrier over the co-resident grid (cooperative launch).  Arrival is a
-// release reduction, the wait an acquire poll; `target` is this barrier's
-// completion count, tracked identically by every block.
+// release reduction on the block's counter; warp 0 then polls all counters
+// (relaxed loads, one per lane), and once their sum reaches `target` (this
+// barrier's completion count, tracked identically by every block) each
+// polling lane issues an acquire fence before the block continues.
 __device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target) {
     __shared__ int s_ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&s->count), "r"(1u)
-                     : "memory");
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0)
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(
+                             &s->count[blockIdx.x % kSyncLanes][0]),
+                         "r"(1u)
+                         : "memory");
         int ok = 1;
         unsigned int spins = 0;
         uint64_t t0 = 0;
         for (;;) {
-            // relaxed polls with a short back-off keep the counter's L2 line
-            // free for the arrivals; one acquire fence once the count is reached
-            unsigned int v;
-            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&s->count)
-                         : "memory");
+            unsigned int v = 0;
+            if (lane < kSyncLanes)
+                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v)
+                             : "l"(&s->count[lane][0])
+                             : "memory");
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            v = __shfl_sync(0xffffffffu, v, 0);
             if ((int)(v - target) >= 0) {
-                asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                if (lane < kSyncLanes) asm volatile("fence.acq_rel.gpu;" ::: "memory");
                 break;
             }
             __nanosleep(32);
-            if ((++spins & 1023u) == 0) {
+            int stop = 0;
+            if (lane == 0 && (++spins & 1023u) == 0) {
                 const uint64_t t = p_globaltimer();
                 if (t0 == 0) {
                     t0 = t;
                 } else if (t - t0 > kBarrierNs) {
                     atomicExch(&s->timeout, 1u);
-                    ok = 0;
-                    break;
+                    stop = 1;
                 }
-                if (*(volatile unsigned int*)&s->timeout) {
-                    ok = 0;
-                    break;
-                }
+                if (*(volatile unsigned int*)&s->timeout) stop = 1;
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) {
+                ok = 0;
+                break;
             }
         }
-        s_ok = ok;
+        __syncwarp();
+        if (lane == 0) s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
