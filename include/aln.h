@@ -177,6 +177,28 @@ aln_status aln_create(aln_ctx** ctx, const aln_options* opt, void* stream);
 aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_t lda,
                        int32_t dtype, const void* B, int64_t k, int64_t ldb);
 
+/* Alg. 1 as aln_prepare, for A given in compressed sparse column form:
+ *   col_ptr  n+1 offsets (int64): column j holds entries col_ptr[j] ≤ t <
+ *            col_ptr[j+1]; col_ptr[0] = 0, non-decreasing, nnz = col_ptr[n].
+ *   row_idx  nnz row indices (int32), in [0, d), strictly increasing within a
+ *            column (no duplicates).
+ *   vals     nnz values of dtype aln_dtype.
+ *   B        k right-hand sides as in aln_prepare (dense).
+ * The three CSC arrays are all host memory or all device memory; row_idx and
+ * vals may be NULL when nnz = 0.  Only the stored entries are read: the column
+ * statistics and Aᵀb come from them, and with SPLIT_BF16 and a single-RHS
+ * solver the Gram multiplies, per pair of 128-column tiles, only the 64-row
+ * blocks stored in both — the same Q as from the dense matrix, for work
+ * proportional to the occupied block pairs.  A dense column-major copy of A
+ * is kept on the device for the FP64 KKT check (d·n elements).  The call
+ * synchronises the stream twice (structure check; sizing of the packed
+ * blocks).  Afterwards the context is prepared exactly as by aln_prepare.
+ * Errors: INVALID_ARG (also a malformed structure), NONFINITE, OUT_OF_MEMORY,
+ * TIMEOUT, CUDA. */
+aln_status aln_prepare_csc(aln_ctx* ctx, int64_t d, int64_t n, const int64_t* col_ptr,
+                           const int32_t* row_idx, const void* vals, int32_t dtype,
+                           const void* B, int64_t k, int64_t ldb);
+
 /* One problem of a grouped batch: min ½‖A x − b‖², x ⪰ 0 (Def. 1), with its
  * own A (d×n, column-major, lda ≥ d) and b (d entries).  A and b may be host
  * or device memory, independently per problem. */

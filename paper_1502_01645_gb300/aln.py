@@ -31,7 +31,7 @@ EXPORTS = (
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
     "aln_kkt_residual_noalloc", "aln_prepare_grouped", "aln_default_train_opts",
     "aln_warmstart_init", "aln_warmstart_params", "aln_warmstart_grad", "aln_warmstart_train",
-    "aln_warmstart_predict", "aln_nmf",
+    "aln_warmstart_predict", "aln_nmf", "aln_prepare_csc",
 )
 
 
@@ -98,6 +98,8 @@ def load(path: str | None = None):
     lib.aln_create.restype = ctypes.c_int
     lib.aln_prepare.argtypes = [vp, vp, i64, i64, i64, i32, vp, i64, i64]
     lib.aln_prepare.restype = ctypes.c_int
+    lib.aln_prepare_csc.argtypes = [vp, i64, i64, vp, vp, vp, i32, vp, i64, i64]
+    lib.aln_prepare_csc.restype = ctypes.c_int
     lib.aln_solve.argtypes = [vp, ctypes.c_double, i32, dp, i64, dp, ctypes.POINTER(AlnSolveInfo)]
     lib.aln_solve.restype = ctypes.c_int
     lib.aln_kkt_residual.argtypes = [vp, dp, i64, dp, dp]
@@ -181,6 +183,11 @@ def aln_create(opt: AlnOptions | None = None, stream: int | None = None) -> int:
 
 def aln_prepare(ctx, A, d, n, lda, dtype, B, k, ldb) -> None:
     _check(load().aln_prepare(ctx, _ptr(A), d, n, lda, dtype, _ptr(B), k, ldb), "aln_prepare")
+
+
+def aln_prepare_csc(ctx, d, n, col_ptr, row_idx, vals, dtype, B, k, ldb) -> None:
+    _check(load().aln_prepare_csc(ctx, d, n, _ptr(col_ptr), _ptr(row_idx), _ptr(vals), dtype,
+                                  _ptr(B), k, ldb), "aln_prepare_csc")
 
 
 def aln_prepare_grouped(ctx, problems, dtype) -> None:
@@ -305,6 +312,28 @@ class Solver:
         ldb = _row_major_ld(B)
         self._keep = (A, B)
         aln_prepare(self.ctx, A, d, n, lda, _dtype_code(A), B, k, ldb)
+        self.n, self.k = n, k
+        self.sizes = None
+
+    def prepare_csc(self, d, col_ptr, row_idx, vals, B):
+        """A (d × n) in compressed sparse column form: col_ptr int64 (n+1),
+        row_idx int32 (strictly increasing within a column), vals float32 or
+        float64 — all three on the host or all on the device; B as in
+        prepare."""
+        n = int(col_ptr.shape[0]) - 1
+        if str(col_ptr.dtype).split(".")[-1] != "int64" or \
+                str(row_idx.dtype).split(".")[-1] != "int32":
+            raise ValueError("col_ptr must be int64 and row_idx int32")
+        if B.ndim == 1:
+            B = B.reshape(1, -1)
+        k, dB = B.shape
+        if dB != d:
+            raise ValueError("B rows must have length d")
+        ldb = _row_major_ld(B)
+        nnz = int(row_idx.shape[0])
+        self._keep = (col_ptr, row_idx, vals, B)
+        aln_prepare_csc(self.ctx, d, n, col_ptr, row_idx if nnz else None,
+                        vals if nnz else None, _dtype_code(vals), B, k, ldb)
         self.n, self.k = n, k
         self.sizes = None
 

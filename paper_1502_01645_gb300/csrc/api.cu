@@ -254,6 +254,80 @@ __global__ void k_copy_to_f64(const TS* __restrict__ src, int64_t lds, double* _
     }
 }
 
+// Shared by aln_prepare and aln_prepare_csc (c->d, c->dtype set): Q (zeroed
+// when its shape changes), s, inv_s, q64, den, flags, the pinned copy of den,
+// and the choice of the many-right-hand-side solver.
+static aln_status prep_buffers(aln_ctx* c, int64_t n, int64_t k) {
+    const bool f64 = fp64(c);
+    const int64_t ldq = round_up(n, 128);
+    const size_t qbytes = (size_t)ldq * ldq * (f64 ? 8 : 4);
+    const bool fresh_q = c->Q == nullptr || c->ldq != ldq || c->Q_elt != (f64 ? 8 : 4);
+    ALN_CHECK(ensure(&c->Q, &c->Q_bytes, qbytes));
+    c->ldq = ldq;
+    c->Q_elt = f64 ? 8 : 4;
+    if (fresh_q || c->Q_n != n) ALN_TRY(cudaMemsetAsync(c->Q, 0, c->Q_bytes, c->stream));
+    c->Q_n = n;
+
+    // s, inv_s, q64 (k·ldq), den (k), flags
+    const size_t pb = round_up((size_t)2 * ldq * 8, 256) + round_up((size_t)k * ldq * 8, 256) +
+                      round_up((size_t)k * 8, 256) + 256;
+    ALN_CHECK(ensure(&c->prep_pool, &c->prep_bytes, pb));
+    uint8_t* p = (uint8_t*)c->prep_pool;
+    c->s = (double*)p;
+    c->inv_s = c->s + ldq;
+    p += round_up((size_t)2 * ldq * 8, 256);
+    c->q64 = (double*)p;
+    p += round_up((size_t)k * ldq * 8, 256);
+    c->den = (double*)p;
+    p += round_up((size_t)k * 8, 256);
+    c->flags = (int*)p;
+    ALN_TRY(cudaMemsetAsync(c->prep_pool, 0, c->prep_bytes, c->stream));
+    if (c->den_host_cap < k) {
+        if (c->den_host) cudaFreeHost(c->den_host);
+        c->den_host = nullptr;
+        c->den_host_cap = 0;
+        if (cudaMallocHost(&c->den_host, (size_t)k * 8) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        c->den_host_cap = k;
+    }
+
+    // Many right-hand sides in mixed precision: the batched solver (batch.cu)
+    // forms Q in FP64 once (it also serves the FP64 checks) and iterates all
+    // columns together with tensor-core products.
+    c->batched = (!f64 && k >= c->opt.batch_min && c->opt.algorithm == ALN_ALG_ANTILOP) ? 1 : 0;
+    c->lipschitz = -1.0;  // Q changes: the Anti+Acc step is estimated again
+    c->power_products = 0;
+    c->stats.lipschitz = 0.0;
+    c->stats.power_products = 0;
+
+    return ALN_OK;
+}
+
+// Shared tail of the prepare calls: workspace, flags and denominators to the
+// host, timings (ev[0]..ev[3] recorded by the caller), input status.
+static aln_status prep_finish(aln_ctx* c, int64_t k) {
+    ALN_CHECK(alloc_workspace(c));
+    ALN_TRY(cudaMemcpyAsync(c->flags_host, c->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaMemcpyAsync(c->den_host, c->den, (size_t)k * 8, cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[3], c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, c->ev[0], c->ev[3]);
+        cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
+        c->stats.prepare_ms = a;
+        c->stats.gram_ms = b;
+    }
+    if (c->flags_host[1]) return ALN_ERR_TIMEOUT;
+    if (c->flags_host[0]) return ALN_ERR_NONFINITE;
+
+    return ALN_OK;
+}
+
 extern "C" {
 
 void aln_default_options(aln_options* opt) {
@@ -367,7 +441,8 @@ void aln_destroy(aln_ctx* c) {
     group_free(c);
     mlp_free(c);
     nmf_free(c);
-    void* bufs[] = {c->A_copy, c->B_copy, c->Q, c->prep_pool, c->A_hi, c->iter_pool, c->kkt_pool};
+    void* bufs[] = {c->A_copy,   c->B_copy,    c->Q,        c->prep_pool,
+                    c->A_hi,     c->iter_pool, c->kkt_pool, c->csc_pool};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->den_host) cudaFreeHost(c->den_host);
@@ -410,49 +485,9 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     c->lda = lda;
     c->ldb = ldb;
     c->dtype = dtype;
+    ALN_CHECK(prep_buffers(c, n, k));
     const bool f64 = fp64(c);
-    const int64_t ldq = round_up(n, 128);
-    const size_t qbytes = (size_t)ldq * ldq * (f64 ? 8 : 4);
-    const bool fresh_q = c->Q == nullptr || c->ldq != ldq || c->Q_elt != (f64 ? 8 : 4);
-    ALN_CHECK(ensure(&c->Q, &c->Q_bytes, qbytes));
-    c->ldq = ldq;
-    c->Q_elt = f64 ? 8 : 4;
-    if (fresh_q || c->Q_n != n) ALN_TRY(cudaMemsetAsync(c->Q, 0, c->Q_bytes, c->stream));
-    c->Q_n = n;
-
-    // s, inv_s, q64 (k·ldq), den (k), flags
-    const size_t pb = round_up((size_t)2 * ldq * 8, 256) + round_up((size_t)k * ldq * 8, 256) +
-                      round_up((size_t)k * 8, 256) + 256;
-    ALN_CHECK(ensure(&c->prep_pool, &c->prep_bytes, pb));
-    uint8_t* p = (uint8_t*)c->prep_pool;
-    c->s = (double*)p;
-    c->inv_s = c->s + ldq;
-    p += round_up((size_t)2 * ldq * 8, 256);
-    c->q64 = (double*)p;
-    p += round_up((size_t)k * ldq * 8, 256);
-    c->den = (double*)p;
-    p += round_up((size_t)k * 8, 256);
-    c->flags = (int*)p;
-    ALN_TRY(cudaMemsetAsync(c->prep_pool, 0, c->prep_bytes, c->stream));
-    if (c->den_host_cap < k) {
-        if (c->den_host) cudaFreeHost(c->den_host);
-        c->den_host = nullptr;
-        c->den_host_cap = 0;
-        if (cudaMallocHost(&c->den_host, (size_t)k * 8) != cudaSuccess) {
-            cudaGetLastError();
-            return ALN_ERR_OUT_OF_MEMORY;
-        }
-        c->den_host_cap = k;
-    }
-
-    // Many right-hand sides in mixed precision: the batched solver (batch.cu)
-    // forms Q in FP64 once (it also serves the FP64 checks) and iterates all
-    // columns together with tensor-core products.
-    c->batched = (!f64 && k >= c->opt.batch_min && c->opt.algorithm == ALN_ALG_ANTILOP) ? 1 : 0;
-    c->lipschitz = -1.0;  // Q changes: the Anti+Acc step is estimated again
-    c->power_products = 0;
-    c->stats.lipschitz = 0.0;
-    c->stats.power_products = 0;
+    const int64_t ldq = c->ldq;
 
     // split copies for the tensor-core Gram
     __nv_bfloat16 *hi = nullptr, *mid = nullptr, *lo = nullptr;
@@ -529,23 +564,145 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     c->launches += 4 + (kc == 0 ? 1 : 0);
 
-    ALN_CHECK(alloc_workspace(c));
-    ALN_TRY(cudaMemcpyAsync(c->flags_host, c->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                            c->stream));
-    ALN_TRY(cudaMemcpyAsync(c->den_host, c->den, (size_t)k * 8, cudaMemcpyDeviceToHost,
-                            c->stream));
-    ALN_TRY(cudaEventRecord(c->ev[3], c->stream));
-    ALN_TRY(cudaStreamSynchronize(c->stream));
-    {
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, c->ev[0], c->ev[3]);
-        cudaEventElapsedTime(&b, c->ev[1], c->ev[2]);
-        c->stats.prepare_ms = a;
-        c->stats.gram_ms = b;
+    ALN_CHECK(prep_finish(c, k));
+    c->prepared = 1;
+    return ALN_OK;
+}
+
+aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_ptr,
+                           const int32_t* row_idx, const void* vals, int32_t dtype,
+                           const void* B, int64_t k, int64_t ldb) {
+    if (!c || !col_ptr || !B) return ALN_ERR_INVALID_ARG;
+    if (d < 1 || n < 1 || k < 1 || ldb < d) return ALN_ERR_INVALID_ARG;
+    if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
+    if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
+    c->prepared = 0;
+    c->grouped = 0;
+    c->stats.prepare_ms = c->stats.gram_ms = 0.0;
+    const size_t esz = elt(dtype);
+    const bool dev_ptr = is_device_ptr(col_ptr);
+    int64_t* pin = (int64_t*)((uint8_t*)c->host_pool + 1024);  // pinned scratch
+    int64_t nnz;
+    if (dev_ptr) {
+        ALN_TRY(cudaMemcpyAsync(pin, col_ptr + n, 8, cudaMemcpyDeviceToHost, c->stream));
+        ALN_TRY(cudaStreamSynchronize(c->stream));
+        nnz = pin[0];
+    } else {
+        nnz = col_ptr[n];
     }
-    if (c->flags_host[1]) return ALN_ERR_TIMEOUT;
+    if (nnz < 0 || nnz > d * n) return ALN_ERR_INVALID_ARG;
+    if (nnz > 0 && (!row_idx || !vals)) return ALN_ERR_INVALID_ARG;
+    // the three arrays live on the same side (host or device)
+    if (nnz > 0 && (is_device_ptr(row_idx) != dev_ptr || is_device_ptr(vals) != dev_ptr))
+        return ALN_ERR_INVALID_ARG;
+
+    c->d = d;
+    c->n = n;
+    c->k = k;
+    c->dtype = dtype;
+    ALN_CHECK(prep_buffers(c, n, k));
+    const bool f64 = fp64(c);
+    const int64_t ldq = c->ldq;
+    // the sparse Gram serves the single-right-hand-side mixed-precision path;
+    // FP64 and the many-right-hand-side solver form Q from the dense copy
+    const bool sparse_gram = !f64 && !c->batched;
+    const int64_t T = ceil_div(n, 128), KB = ceil_div(d, 64);
+    const int W = (int)ceil_div(KB, 32);
+
+    // CSC arrays on the device (host inputs copied; device inputs in place)
+    // followed by the occupancy words, word prefixes, tile counts and offsets
+    const size_t b_cp = round_up((size_t)(n + 1) * 8, 256);
+    const size_t b_ri = round_up((size_t)nnz * 4, 256);
+    const size_t b_v = round_up((size_t)nnz * esz, 256);
+    const size_t b_occ = sparse_gram ? round_up((size_t)T * W * 4, 256) : 0;
+    const size_t b_cnt = sparse_gram ? round_up((size_t)(2 * T + 1) * 8, 256) : 0;
+    const size_t b_copy = dev_ptr ? 0 : b_cp + b_ri + b_v;
+    ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes, b_copy + 2 * b_occ + b_cnt + 256));
+    uint8_t* cp8 = (uint8_t*)c->csc_pool;
+    const int64_t* cp = col_ptr;
+    const int32_t* ri = row_idx;
+    const void* vv = vals;
+    if (!dev_ptr) {
+        ALN_TRY(cudaMemcpyAsync(cp8, col_ptr, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice,
+                                c->stream));
+        cp = (const int64_t*)cp8;
+        if (nnz > 0) {
+            ALN_TRY(cudaMemcpyAsync(cp8 + b_cp, row_idx, (size_t)nnz * 4, cudaMemcpyHostToDevice,
+                                    c->stream));
+            ALN_TRY(cudaMemcpyAsync(cp8 + b_cp + b_ri, vals, (size_t)nnz * esz,
+                                    cudaMemcpyHostToDevice, c->stream));
+        }
+        ri = (const int32_t*)(cp8 + b_cp);
+        vv = cp8 + b_cp + b_ri;
+        cp8 += b_copy;
+    }
+    uint32_t* occ = (uint32_t*)cp8;
+    int32_t* wbase = (int32_t*)(cp8 + b_occ);
+    int64_t* cnt = (int64_t*)(cp8 + 2 * b_occ);
+    int64_t* toff = cnt + T;
+
+    // dense column-major copy of A for the FP64 KKT check (16-byte columns)
+    const int64_t lda = round_up(d, (int64_t)(16 / esz));
+    ALN_CHECK(ensure(&c->A_copy, &c->A_copy_bytes, (size_t)n * lda * esz));
+    c->A = c->A_copy;
+    c->lda = lda;
+    ALN_CHECK(resolve_input(c, B, d, k, ldb, esz, &c->B_copy, &c->B_copy_bytes, &c->B));
+    c->ldb = ldb;
+
+    // structure first: every later kernel indexes with col_ptr and row_idx
+    ALN_TRY(cudaEventRecord(c->ev[0], c->stream));
+    ALN_TRY(launch_csc_check(cp, ri, vv, dtype, d, n, nnz, c->flags, c->stream));
+    ALN_TRY(launch_check_finite(c->B, dtype, d, k, ldb, c->flags, c->stream));
+    ALN_TRY(cudaMemcpyAsync(c->flags_host, c->flags, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream));
+    ALN_TRY(cudaStreamSynchronize(c->stream));
+    if (c->flags_host[2]) return ALN_ERR_INVALID_ARG;
     if (c->flags_host[0]) return ALN_ERR_NONFINITE;
 
+    // Alg. 1: scatter, scale factors, q, occupancy
+    ALN_TRY(cudaMemsetAsync(c->A_copy, 0, (size_t)n * lda * esz, c->stream));
+    if (sparse_gram) ALN_TRY(cudaMemsetAsync(occ, 0, b_occ, c->stream));
+    const int kc = k <= 4 ? (int)k : 0;
+    ALN_TRY(launch_csc_colstats(cp, ri, vv, dtype, n, c->B, kc, ldb, c->A_copy, lda, c->s,
+                                c->inv_s, c->q64, ldq, sparse_gram ? occ : nullptr, W,
+                                c->stream));
+    c->launches += 3;
+    if (kc == 0) {
+        if (c->batched && dtype == ALN_DTYPE_F32)
+            ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
+                                       c->inv_s, c->q64, ldq, c->stream));
+        else
+            ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
+                                  c->stream));
+        ++c->launches;
+    }
+    ALN_TRY(launch_denominators(c->q64, n, ldq, k, c->den, c->stream));
+    ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
+    if (sparse_gram) {
+        // number the occupied boxes, size the pack, scatter the split terms
+        ALN_TRY(launch_csc_number(occ, W, T, wbase, cnt, toff, c->stream));
+        ALN_TRY(cudaMemcpyAsync(pin, toff + T, 8, cudaMemcpyDeviceToHost, c->stream));
+        ALN_TRY(cudaStreamSynchronize(c->stream));
+        const int64_t boxes = pin[0];
+        const size_t sb = round_up((size_t)std::max<int64_t>(boxes, 1) * 128 * 64 * 2, 1024);
+        ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 3 * sb));
+        __nv_bfloat16* hi = c->A_hi;
+        __nv_bfloat16* mid = (__nv_bfloat16*)((uint8_t*)c->A_hi + sb);
+        __nv_bfloat16* lo = (__nv_bfloat16*)((uint8_t*)c->A_hi + 2 * sb);
+        ALN_TRY(cudaMemsetAsync(c->A_hi, 0, 3 * sb, c->stream));
+        ALN_TRY(launch_csc_pack(cp, ri, vv, dtype, n, occ, W, wbase, toff, hi, mid, lo,
+                                c->stream));
+        ALN_TRY(launch_sgram_tc(c->opt.gram_split, occ, W, wbase, toff, hi, mid, lo, n, c->inv_s,
+                                (float*)c->Q, ldq, c->flags + 1, c->stream));
+        c->launches += 4;
+    } else if (c->batched) {
+        ALN_CHECK(batch_prepare(c));
+    } else {
+        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
+        ++c->launches;
+    }
+    ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
+    ALN_CHECK(prep_finish(c, k));
     c->prepared = 1;
     return ALN_OK;
 }

@@ -216,7 +216,10 @@ struct aln_ctx {
     int64_t ldk = 0;
     __nv_bfloat16* A_hi = nullptr;
     __nv_bfloat16* A_lo = nullptr;
-    size_t split_bytes = 0;
+    size_t split_bytes = 0;  // also holds the packed boxes of a CSC prepare
+    // CSC prepare: device copies of host CSC arrays, occupancy, box numbering
+    void* csc_pool = nullptr;
+    size_t csc_bytes = 0;
 
     // iteration workspace (element type follows the precision)
     void* qv = nullptr;       // q of the right-hand side being solved (iteration type)

@@ -164,8 +164,10 @@ __device__ __forceinline__ void gram_store(const float (&acc)[BM], int64_t row, 
 }
 
 // One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
+// The loader is taken by value: a loader may keep a cursor over the K blocks
+// it copies (k_sgram_tc); load() is called for the blocks in order.
 template <int NS, class Loader>
-__device__ __forceinline__ void gram_tile(const Loader& ld, int num_kb, bool diag, int64_t m0,
+__device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
                                            int64_t n0, int64_t n, const double* __restrict__ inv_s,
                                            float* __restrict__ Q, int64_t ldq,
                                            int* timeout_flag) {
@@ -246,8 +248,9 @@ __device__ __forceinline__ void gram_tile(const Loader& ld, int num_kb, bool dia
             umma_commit(&empty[s]);
             if (last) umma_commit(&tfull[b]);
         }
-        // always commit: `done` then also covers MMAs issued before an abort
-        umma_commit(done);
+        // always commit (but for an empty K range): `done` then also covers
+        // MMAs issued before an abort
+        if (num_kb > 0) umma_commit(done);
     } else if (warp >= 2) {
         const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
         const int nch = (num_kb + C::CHUNK - 1) / C::CHUNK;
@@ -266,7 +269,7 @@ __device__ __forceinline__ void gram_tile(const Loader& ld, int num_kb, bool dia
         }
     }
     __syncwarp();
-    if (warp == 1) {
+    if (warp == 1 && num_kb > 0) {
         const bool ok = mbar_wait(done, 0);  // no MMA in flight past this point
         if (!ok) s_abort = 1;
     }
@@ -368,6 +371,86 @@ __global__ void __launch_bounds__(G3_THREADS, 1) k_ggram_tc(GGramArgs a) {
                             (P.pack + (int64_t)tl.tn * P.KB) * kPackTile};
     gram_tile<NS>(ld, P.KB, tl.tm == tl.tn, (int64_t)tl.tm * BM, (int64_t)tl.tn * BM, P.n,
                   a.inv_s + P.voff, a.Q + P.qoff, P.ldq, a.timeout_flag);
+}
+
+// ---------------------------------------------------------------------------
+// Block-sparse Gram (sparse.cu builds the operands): the occupied 128×64 boxes
+// of each column tile are packed in K order (pack_index layout) from box
+// toff[tile]; occupancy bit kb of word occ[tile·W + kb/32] marks K block kb,
+// and wbase[tile·W + w] counts the tile's boxes in the words before w.  A CTA
+// multiplies, for its tile pair (I, J ≤ I), only the K blocks occupied in
+// both tiles, in increasing K order; a pair with none stores zeros.
+// ---------------------------------------------------------------------------
+struct SGramArgs {
+    int64_t n;
+    int64_t t0;
+    int W;
+    const uint32_t* occ;
+    const int32_t* wbase;
+    const int64_t* toff;
+    const __nv_bfloat16* hi;
+    const __nv_bfloat16* mid;
+    const __nv_bfloat16* lo;
+    const double* inv_s;
+    float* Q;
+    int64_t ldq;
+    int* timeout_flag;
+};
+
+template <int NS>
+struct SparseLoader {
+    const __nv_bfloat16* hi;
+    const __nv_bfloat16* mid;
+    const __nv_bfloat16* lo;
+    const uint32_t* oa;  // occupancy words of the row tile I / column tile J
+    const uint32_t* ob;
+    const int32_t* wa;
+    const int32_t* wb;
+    int64_t ta, tb;      // first box of tile I / J
+    int W;
+    int w;               // cursor: current word, and its common bits not yet copied
+    uint32_t m;
+    __device__ __forceinline__ void load(uint8_t* sb, int, bool diag, uint64_t* bar) {
+        while (m == 0u && w + 1 < W) {
+            ++w;
+            m = oa[w] & ob[w];
+        }
+        if (m == 0u) return;  // cannot happen (load() runs once per common bit); the
+                              // consumer's bounded wait on the stage then ends the tile
+        const int bit = __ffs(m) - 1;
+        m &= m - 1u;
+        const uint32_t below = (1u << bit) - 1u;
+        const int64_t xa = (ta + wa[w] + __popc(oa[w] & below)) * kPackTile;
+        bulk_load(sb, hi + xa, TILE_BYTES, bar);
+        bulk_load(sb + TILE_BYTES, mid + xa, TILE_BYTES, bar);
+        if (NS == 3) bulk_load(sb + 2 * TILE_BYTES, lo + xa, TILE_BYTES, bar);
+        if (!diag) {
+            const int64_t xb = (tb + wb[w] + __popc(ob[w] & below)) * kPackTile;
+            bulk_load(sb + NS * TILE_BYTES, hi + xb, TILE_BYTES, bar);
+            bulk_load(sb + (NS + 1) * TILE_BYTES, mid + xb, TILE_BYTES, bar);
+            if (NS == 3) bulk_load(sb + 5 * TILE_BYTES, lo + xb, TILE_BYTES, bar);
+        }
+    }
+};
+
+template <int NS>
+__global__ void __launch_bounds__(G3_THREADS, 1) k_sgram_tc(SGramArgs a) {
+    __shared__ int s_nkb;
+    int tm, tn;
+    tri_decode(blockIdx.x + a.t0, tm, tn);
+    const uint32_t* oa = a.occ + (int64_t)tm * a.W;
+    const uint32_t* ob = a.occ + (int64_t)tn * a.W;
+    if (threadIdx.x < 32) {  // K blocks occupied in both tiles
+        int c = 0;
+        for (int w = threadIdx.x; w < a.W; w += 32) c += __popc(oa[w] & ob[w]);
+        c = warp_sum_i(c);
+        if (threadIdx.x == 0) s_nkb = c;
+    }
+    __syncthreads();
+    const SparseLoader<NS> ld{a.hi, a.mid, a.lo, oa, ob, a.wbase + (int64_t)tm * a.W,
+                              a.wbase + (int64_t)tn * a.W, a.toff[tm], a.toff[tn], a.W, -1, 0u};
+    gram_tile<NS>(ld, s_nkb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, a.n, a.inv_s, a.Q,
+                  a.ldq, a.timeout_flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -628,6 +711,46 @@ cudaError_t launch_ggram_tc(int nsplit, const GProb* gp, const GTile* tiles, int
         k_ggram_tc<3><<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
     else
         k_ggram_tc<2><<<(unsigned)ntiles, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_t* wbase,
+                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                            const __nv_bfloat16* lo, int64_t n, const double* inv_s, float* Q,
+                            int64_t ldq, int* timeout_flag, cudaStream_t st) {
+    using namespace tc;
+    if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
+    if (nsplit == 2) lo = mid;
+    if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) || W < 1)
+        return cudaErrorInvalidValue;
+    static bool attr[2] = {false, false};
+    if (!attr[nsplit - 2]) {
+        cudaError_t e = cudaFuncSetAttribute(nsplit == 3 ? k_sgram_tc<3> : k_sgram_tc<2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             G3_SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr[nsplit - 2] = true;
+    }
+    SGramArgs a;
+    a.n = n;
+    a.t0 = 0;
+    a.W = W;
+    a.occ = occ;
+    a.wbase = wbase;
+    a.toff = toff;
+    a.hi = hi;
+    a.mid = mid;
+    a.lo = lo;
+    a.inv_s = inv_s;
+    a.Q = Q;
+    a.ldq = ldq;
+    a.timeout_flag = timeout_flag;
+    const int64_t tiles = ceil_div(n, BM);
+    const unsigned grid = (unsigned)(tiles * (tiles + 1) / 2);
+    if (nsplit == 3)
+        k_sgram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
+    else
+        k_sgram_tc<2><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,13 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0 = 0, int64_t row1 = -1);
 bool tc_supported(int cc_major, int cc_minor);
+// Block-sparse Gram over the occupied boxes packed by sparse.cu: for every
+// lower tile pair only the K blocks occupied in both column tiles.
+cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_t* wbase,
+                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                            const __nv_bfloat16* lo, int64_t n, const double* inv_s, float* Q,
+                            int64_t ldq, int* timeout_flag, cudaStream_t st);
+
 // W = Q·V (mode 0, with per-column curvature partials) or g += Q·V (mode 1)
 // over the compacted columns of a batch (batch.cu).
 cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bfloat16* q_lo,
@@ -141,6 +148,21 @@ cudaError_t launch_power(aln_ctx* c, double tol, int max_steps, double* out);
 template <typename T>
 int persist_max_blocks(int num_sms, int64_t ldq, int* repl);
 size_t persist_sync_bytes();
+
+// sparse.cu — Alg. 1 from a CSC matrix (col_ptr int64[n+1], row_idx int32,
+// values of dtype); see the kernels there.
+cudaError_t launch_csc_check(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
+                             int64_t d, int64_t n, int64_t nnz, int* flags, cudaStream_t st);
+cudaError_t launch_csc_colstats(const int64_t* cp, const int32_t* ri, const void* v,
+                                int32_t dtype, int64_t n, const void* B, int kc, int64_t ldb,
+                                void* A, int64_t lda, double* s, double* inv_s, double* q64,
+                                int64_t ldq, uint32_t* occ, int W, cudaStream_t st);
+cudaError_t launch_csc_number(const uint32_t* occ, int W, int64_t T, int32_t* wbase, int64_t* cnt,
+                              int64_t* toff, cudaStream_t st);
+cudaError_t launch_csc_pack(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
+                            int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
+                            const int64_t* toff, __nv_bfloat16* hi, __nv_bfloat16* mid,
+                            __nv_bfloat16* lo, cudaStream_t st);
 
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);

@@ -1,0 +1,246 @@
+// Alg. 1 (§3) for a sparse, possibly tall A given in compressed sparse
+// column (CSC) form: column j holds the entries vals[t], rows row_idx[t] for
+// col_ptr[j] ≤ t < col_ptr[j+1], rows strictly increasing.
+//
+// Every step reads only the stored entries:
+//   k_csc_check     the structure (bounds, order) and finiteness;
+//   k_csc_colstats  s_j² = Σ a_tj², (Aᵀb_c)_j for up to four right-hand
+//                   sides, the scatter into the dense column-major A that the
+//                   FP64 KKT check reads, and the occupancy bitmap of the
+//                   Gram's operand boxes (64 rows × 128 columns);
+//   k_csc_tiles / k_csc_offsets  number the occupied boxes, column tile by
+//                   column tile (a popcount prefix per bitmap word);
+//   k_csc_pack      the exact three-term BF16 split of every entry, written
+//                   into its box in the pre-swizzled layout the tensor-core
+//                   Gram copies verbatim (pack_index).
+// The Gram (launch_sgram_tc, gemm_tc.cu) multiplies, for each tile pair, only
+// the K blocks occupied in both column tiles: a block that is zero in either
+// operand adds exactly zero to H = AᵀA, so Q is the same as from the dense A.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace aln {
+
+namespace {
+
+constexpr int kCscThreads = 256;
+constexpr int kCscWarps = kCscThreads / 32;
+
+// Exclusive prefix sum over a 256-thread block; *total gets the block sum.
+__device__ __forceinline__ int64_t block_scan_excl(int64_t v, int64_t* s_w, int64_t* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[wid] = x;
+    __syncthreads();
+    int64_t before = 0, all = 0;
+    for (int w = 0; w < kCscWarps; ++w) {
+        if (w < wid) before += s_w[w];
+        all += s_w[w];
+    }
+    __syncthreads();
+    *total = all;
+    return before + x - v;
+}
+
+// One warp per column.  flags[2] |= 1 for a malformed structure (col_ptr not
+// non-decreasing within [0, nnz], col_ptr[0] ≠ 0, col_ptr[n] ≠ nnz, a row out
+// of [0, d), rows not strictly increasing); flags[0] |= 1 for a NaN/Inf value.
+// A column whose bounds are malformed is not read further.
+template <typename T>
+__global__ void __launch_bounds__(kCscThreads) k_csc_check(const int64_t* __restrict__ cp,
+                                                           const int32_t* __restrict__ ri,
+                                                           const T* __restrict__ v, int64_t d,
+                                                           int64_t n, int64_t nnz,
+                                                           int* __restrict__ flags) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const int64_t p0 = cp[j], p1 = cp[j + 1];
+    bool bad = p0 < 0 || p1 < p0 || p1 > nnz || (j == 0 && p0 != 0) || (j == n - 1 && p1 != nnz);
+    if (bad) {
+        if (lane == 0) atomicOr(&flags[2], 1);
+        return;
+    }
+    bool nonfinite = false;
+    for (int64_t t = p0 + lane; t < p1; t += 32) {
+        const int32_t r = ri[t];
+        bad |= r < 0 || (int64_t)r >= d || (t > p0 && ri[t - 1] >= r);
+        nonfinite |= !isfinite(v[t]);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&flags[2], 1);
+    if (__any_sync(0xffffffffu, nonfinite) && lane == 0) atomicOr(&flags[0], 1);
+}
+
+// One warp per column j: the column statistics of Alg. 1 from the stored
+// entries (same definitions as the dense k_colstats: s_j = √Σa², or 1 for an
+// empty column; q_cj = −(Aᵀb_c)_j / s_j for c < kc ≤ 4), the scatter
+// A[j·lda + row] = a (A zeroed beforehand), and with OCC the occupancy bit of
+// box (column tile j/128, K block row/64) in occ[tile·W + kb/32].
+template <typename T, bool OCC>
+__global__ void __launch_bounds__(kCscThreads)
+    k_csc_colstats(const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                   const T* __restrict__ v, int64_t n, const T* __restrict__ B, int kc,
+                   int64_t ldb, T* __restrict__ A, int64_t lda, double* __restrict__ s,
+                   double* __restrict__ inv_s, double* __restrict__ q64, int64_t ldq,
+                   uint32_t* __restrict__ occ, int W) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const int64_t p0 = cp[j], p1 = cp[j + 1];
+    DotAcc<T> sq, dot[4];
+    T* col = A + j * lda;
+    uint32_t* occ_t = OCC ? occ + (j >> 7) * (int64_t)W : nullptr;
+    for (int64_t t = p0 + lane; t < p1; t += 32) {
+        const int32_t r = ri[t];
+        const T a = v[t];
+        sq.add(a, a);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c < kc) dot[c].add(a, B[(int64_t)c * ldb + r]);
+        col[r] = a;
+        if (OCC) {
+            const int kb = r >> 6;
+            // rows are increasing: only the first entry of a K block sets its bit
+            if (t == p0 || (ri[t - 1] >> 6) != kb) atomicOr(&occ_t[kb >> 5], 1u << (kb & 31));
+        }
+    }
+    const double s2 = warp_sum(sq.value());
+    double ds[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ds[c] = c < kc ? warp_sum(dot[c].value()) : 0.0;
+    if (lane == 0) {
+        const double sj = s2 > 0.0 ? sqrt(s2) : 1.0;
+        s[j] = sj;
+        inv_s[j] = 1.0 / sj;
+        for (int c = 0; c < kc; ++c) q64[(int64_t)c * ldq + j] = -ds[c] / sj;
+    }
+}
+
+// One block per column tile: wbase[tile·W + w] = occupied boxes of the tile
+// in words before w; cnt[tile] = occupied boxes of the tile.
+__global__ void __launch_bounds__(kCscThreads) k_csc_tiles(const uint32_t* __restrict__ occ, int W,
+                                                           int32_t* __restrict__ wbase,
+                                                           int64_t* __restrict__ cnt) {
+    __shared__ int64_t s_w[kCscWarps];
+    const int64_t base = (int64_t)blockIdx.x * W;
+    int64_t run = 0;
+    for (int w0 = 0; w0 < W; w0 += kCscThreads) {
+        const int w = w0 + threadIdx.x;
+        const int64_t c = w < W ? __popc(occ[base + w]) : 0;
+        int64_t tot;
+        const int64_t ex = block_scan_excl(c, s_w, &tot);
+        if (w < W) wbase[base + w] = (int32_t)(run + ex);
+        run += tot;
+    }
+    if (threadIdx.x == 0) cnt[blockIdx.x] = run;
+}
+
+// One block: toff[I] = Σ_{J<I} cnt[J] for I ≤ T (toff[T] = all boxes).
+__global__ void __launch_bounds__(kCscThreads) k_csc_offsets(const int64_t* __restrict__ cnt,
+                                                             int64_t T,
+                                                             int64_t* __restrict__ toff) {
+    __shared__ int64_t s_w[kCscWarps];
+    int64_t run = 0;
+    for (int64_t i0 = 0; i0 < T; i0 += kCscThreads) {
+        const int64_t i = i0 + threadIdx.x;
+        const int64_t c = i < T ? cnt[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_scan_excl(c, s_w, &tot);
+        if (i < T) toff[i] = run + ex;
+        run += tot;
+    }
+    if (threadIdx.x == 0) toff[T] = run;
+}
+
+// One warp per column: every entry's three BF16 terms into its box (boxes
+// zeroed beforehand; rows ≥ d and columns ≥ n stay zero).
+template <typename T>
+__global__ void __launch_bounds__(kCscThreads)
+    k_csc_pack(const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
+               const T* __restrict__ v, int64_t n, const uint32_t* __restrict__ occ, int W,
+               const int32_t* __restrict__ wbase, const int64_t* __restrict__ toff,
+               __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ mid,
+               __nv_bfloat16* __restrict__ lo) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const int64_t p0 = cp[j], p1 = cp[j + 1];
+    const int64_t tw = (j >> 7) * (int64_t)W;
+    const int64_t t0 = toff[j >> 7];
+    for (int64_t t = p0 + lane; t < p1; t += 32) {
+        const int32_t r = ri[t];
+        const int kb = r >> 6, w = kb >> 5;
+        const uint32_t below = (1u << (kb & 31)) - 1u;
+        const int64_t box = t0 + wbase[tw + w] + __popc(occ[tw + w] & below);
+        const int64_t at = pack_index(box, 0, (int)(j & 127), r & 63);
+        __nv_bfloat16 h, m, l;
+        split3_bf16((float)v[t], h, m, l);
+        hi[at] = h;
+        mid[at] = m;
+        lo[at] = l;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_csc_check(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
+                             int64_t d, int64_t n, int64_t nnz, int* flags, cudaStream_t st) {
+    const unsigned grid = (unsigned)ceil_div(n, kCscWarps);
+    if (dtype == ALN_DTYPE_F64)
+        k_csc_check<double><<<grid, kCscThreads, 0, st>>>(cp, ri, (const double*)v, d, n, nnz, flags);
+    else
+        k_csc_check<float><<<grid, kCscThreads, 0, st>>>(cp, ri, (const float*)v, d, n, nnz, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_colstats(const int64_t* cp, const int32_t* ri, const void* v,
+                                int32_t dtype, int64_t n, const void* B, int kc, int64_t ldb,
+                                void* A, int64_t lda, double* s, double* inv_s, double* q64,
+                                int64_t ldq, uint32_t* occ, int W, cudaStream_t st) {
+    const unsigned grid = (unsigned)ceil_div(n, kCscWarps);
+#define ALN_CSC_STATS(T, OCC)                                                                    \
+    k_csc_colstats<T, OCC><<<grid, kCscThreads, 0, st>>>(cp, ri, (const T*)v, n, (const T*)B, kc, \
+                                                         ldb, (T*)A, lda, s, inv_s, q64, ldq,    \
+                                                         occ, W)
+    if (dtype == ALN_DTYPE_F64) {
+        if (occ)
+            ALN_CSC_STATS(double, true);
+        else
+            ALN_CSC_STATS(double, false);
+    } else {
+        if (occ)
+            ALN_CSC_STATS(float, true);
+        else
+            ALN_CSC_STATS(float, false);
+    }
+#undef ALN_CSC_STATS
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_number(const uint32_t* occ, int W, int64_t T, int32_t* wbase, int64_t* cnt,
+                              int64_t* toff, cudaStream_t st) {
+    k_csc_tiles<<<(unsigned)T, kCscThreads, 0, st>>>(occ, W, wbase, cnt);
+    k_csc_offsets<<<1, kCscThreads, 0, st>>>(cnt, T, toff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_pack(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
+                            int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
+                            const int64_t* toff, __nv_bfloat16* hi, __nv_bfloat16* mid,
+                            __nv_bfloat16* lo, cudaStream_t st) {
+    const unsigned grid = (unsigned)ceil_div(n, kCscWarps);
+    if (dtype == ALN_DTYPE_F64)
+        k_csc_pack<double><<<grid, kCscThreads, 0, st>>>(cp, ri, (const double*)v, n, occ, W, wbase,
+                                                         toff, hi, mid, lo);
+    else
+        k_csc_pack<float><<<grid, kCscThreads, 0, st>>>(cp, ri, (const float*)v, n, occ, W, wbase,
+                                                        toff, hi, mid, lo);
+    return cudaGetLastError();
+}
+
+}  // namespace aln

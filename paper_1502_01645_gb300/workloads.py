@@ -28,6 +28,9 @@ __all__ = [
     "TCASES",
     "tcase",
     "nmf_matrix",
+    "SparseProblem",
+    "banded_tall",
+    "to_csc",
     "CONFIGS",
 ]
 
@@ -225,6 +228,79 @@ def nmf_matrix(m=4096, n=4096, r=64, seed=1007, noise=0.01):
     H0 = rng.random((r, n))
     c = np.sqrt(V.astype(np.float64).mean() / (W0 @ H0).mean())
     return V, np.asfortranarray(W0 * c), np.asfortranarray(H0 * c)
+
+
+@dataclass
+class SparseProblem:
+    """An NNLS instance with A (d×n) in compressed sparse column form:
+    ``col_ptr`` int64 (n+1), ``row_idx`` int32 (strictly increasing within a
+    column), ``vals`` of the problem's dtype; B (k, d) as in ``Problem``."""
+
+    d: int
+    n: int
+    col_ptr: np.ndarray
+    row_idx: np.ndarray
+    vals: np.ndarray
+    B: np.ndarray
+    x_true: np.ndarray
+    tol: float
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_ptr[-1])
+
+    def dense(self) -> np.ndarray:
+        """The same matrix stored densely (Fortran order, the values' dtype)."""
+        A = np.zeros((self.d, self.n), dtype=self.vals.dtype, order="F")
+        cols = np.repeat(np.arange(self.n), np.diff(self.col_ptr))
+        A[self.row_idx, cols] = self.vals
+        return A
+
+
+def to_csc(A) -> tuple:
+    """(col_ptr, row_idx, vals) of the non-zero entries of a dense (d, n) array."""
+    n = A.shape[1]
+    col_ptr = np.zeros(n + 1, np.int64)
+    rows, vals = [], []
+    for j in range(n):
+        nz = np.flatnonzero(A[:, j])
+        rows.append(nz.astype(np.int32))
+        vals.append(np.asarray(A[nz, j]))
+        col_ptr[j + 1] = col_ptr[j] + nz.size
+    return col_ptr, np.concatenate(rows), np.concatenate(vals).astype(A.dtype)
+
+
+def banded_tall(d=200000, n=5000, band=6000, density=0.1, zero_frac=0.7, seed=1008, tol=1e-6,
+                dtype=np.float32):
+    """A tall sparse A whose columns' supports drift down the rows: column j
+    holds round(density·band) entries at distinct random rows of the window
+    [r_j, r_j + band), r_j = round(j·(d − band)/(n − 1)) — the structure of a
+    design matrix of local, overlapping features (e.g. shifted copies of a
+    kernel in a deconvolution).  Values U(0, 1] times a log-uniform column
+    factor in [10⁻², 10²] (lopsided, as in ``lopsided_single``); x_true 70%
+    zeros with Exp(1) non-zeros; b = A x_true + 1% Gaussian noise."""
+    rng = _rng(seed)
+    per = max(1, int(round(density * band)))
+    col_ptr = np.arange(n + 1, dtype=np.int64) * per
+    row_idx = np.empty(n * per, np.int32)
+    vals = np.empty(n * per, np.float64)
+    scale = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), size=n))
+    for j in range(n):
+        r0 = int(round(j * (d - band) / max(n - 1, 1)))
+        rows = np.sort(rng.choice(band, size=per, replace=False)) + r0
+        row_idx[j * per:(j + 1) * per] = rows
+        vals[j * per:(j + 1) * per] = (1.0 - rng.random(per)) * scale[j]
+    vals = vals.astype(dtype)
+    x = _sparse_rows(rng, 1, n, zero_frac, lambda s: rng.exponential(1.0, s))
+    cols = np.repeat(np.arange(n), per)
+    clean = np.bincount(row_idx, weights=vals.astype(np.float64) * x[0, cols], minlength=d)
+    b = clean + 0.01 * np.linalg.norm(clean) / np.sqrt(d) * rng.standard_normal(d)
+    return SparseProblem(d, n, col_ptr, row_idx, vals, np.ascontiguousarray(b.astype(dtype))[None, :],
+                         x, tol, "banded_tall",
+                         {"d": d, "n": n, "band": band, "density": density, "nnz": n * per,
+                          "dtype": np.dtype(dtype).name})
 
 
 CONFIGS = {

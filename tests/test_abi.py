@@ -61,6 +61,8 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.aln_prepare_grouped(None, 1, None, 0) == aln.ERR_INVALID_ARG
     assert lib.aln_nmf(None, None, 4, 4, 4, 2, None, 4, None, 2, 1, 1e-6, 0, None) == \
         aln.ERR_INVALID_ARG
+    assert lib.aln_prepare_csc(None, 4, 2, None, None, None, 0, None, 1, 4) == \
+        aln.ERR_INVALID_ARG
     o = aln.aln_default_options()
     o.precision = 7
     ctx = ctypes.c_void_p()
