@@ -189,10 +189,15 @@ aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_
  * statistics and Aᵀb come from them, and with SPLIT_BF16 and a single-RHS
  * solver the Gram multiplies, per pair of 128-column tiles, only the 64-row
  * blocks stored in both — the same Q as from the dense matrix, for work
- * proportional to the occupied block pairs.  A dense column-major copy of A
- * is kept on the device for the FP64 KKT check (d·n elements).  The call
- * synchronises the stream twice (structure check; sizing of the packed
- * blocks).  Afterwards the context is prepared exactly as by aln_prepare.
+ * proportional to the occupied block pairs.  With F32 values, SPLIT_BF16, a
+ * single-RHS solver and k ≤ 4, no dense copy of A is made: the FP64 KKT pass
+ * reads the CSC arrays and the packed blocks (whose split terms add up exactly
+ * to the entries), so device CSC arrays are kept by pointer and must stay
+ * valid until the next prepare or aln_destroy.  Otherwise (F64 values, FP64
+ * precision, the many-right-hand-side solver, k > 4) a dense column-major copy
+ * of A (d·n elements) is made on the device.  The call synchronises the
+ * stream twice (structure check; sizing of the packed blocks).  Afterwards
+ * the context is prepared as by aln_prepare.
  * Errors: INVALID_ARG (also a malformed structure), NONFINITE, OUT_OF_MEMORY,
  * TIMEOUT, CUDA. */
 aln_status aln_prepare_csc(aln_ctx* ctx, int64_t d, int64_t n, const int64_t* col_ptr,

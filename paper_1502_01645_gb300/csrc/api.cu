@@ -464,6 +464,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
     c->prepared = 0;
     c->grouped = 0;
+    c->csc_kkt = 0;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     // A on the host, single-problem split path with q fused in the column
@@ -578,6 +579,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     if (n > (int64_t)1 << 20 || d > ((int64_t)1 << 31) - 64) return ALN_ERR_INVALID_ARG;
     c->prepared = 0;
     c->grouped = 0;
+    c->csc_kkt = 0;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     const bool dev_ptr = is_device_ptr(col_ptr);
@@ -608,6 +610,10 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     const bool sparse_gram = !f64 && !c->batched;
     const int64_t T = ceil_div(n, 128), KB = ceil_div(d, 64);
     const int W = (int)ceil_div(KB, 32);
+    // FP32 values and at most four right-hand sides: nothing after the prepare
+    // needs a dense copy of A (the KKT pass reads the CSC arrays and the
+    // packed boxes, whose split terms add up exactly to the FP32 entries)
+    const bool no_dense = sparse_gram && dtype == ALN_DTYPE_F32 && k <= 4;
 
     // CSC arrays on the device (host inputs copied; device inputs in place)
     // followed by the occupancy words, word prefixes, tile counts and offsets
@@ -616,8 +622,9 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     const size_t b_v = round_up((size_t)nnz * esz, 256);
     const size_t b_occ = sparse_gram ? round_up((size_t)T * W * 4, 256) : 0;
     const size_t b_cnt = sparse_gram ? round_up((size_t)(2 * T + 1) * 8, 256) : 0;
+    const size_t b_fp = no_dense ? round_up((size_t)KB * 8, 256) : 0;
     const size_t b_copy = dev_ptr ? 0 : b_cp + b_ri + b_v;
-    ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes, b_copy + 2 * b_occ + b_cnt + 256));
+    ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes, b_copy + 2 * b_occ + b_cnt + b_fp + 256));
     uint8_t* cp8 = (uint8_t*)c->csc_pool;
     const int64_t* cp = col_ptr;
     const int32_t* ri = row_idx;
@@ -640,11 +647,18 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     int32_t* wbase = (int32_t*)(cp8 + b_occ);
     int64_t* cnt = (int64_t*)(cp8 + 2 * b_occ);
     int64_t* toff = cnt + T;
+    double* fpart = (double*)(cp8 + 2 * b_occ + b_cnt);
 
-    // dense column-major copy of A for the FP64 KKT check (16-byte columns)
+    // dense column-major copy of A (16-byte columns) where a later step reads
+    // it: the FP64 Gram, the many-right-hand-side solver, q for k > 4, or the
+    // KKT pass of FP64 values
     const int64_t lda = round_up(d, (int64_t)(16 / esz));
-    ALN_CHECK(ensure(&c->A_copy, &c->A_copy_bytes, (size_t)n * lda * esz));
-    c->A = c->A_copy;
+    if (!no_dense) {
+        ALN_CHECK(ensure(&c->A_copy, &c->A_copy_bytes, (size_t)n * lda * esz));
+        c->A = c->A_copy;
+    } else {
+        c->A = nullptr;
+    }
     c->lda = lda;
     ALN_CHECK(resolve_input(c, B, d, k, ldb, esz, &c->B_copy, &c->B_copy_bytes, &c->B));
     c->ldb = ldb;
@@ -659,11 +673,12 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     if (c->flags_host[2]) return ALN_ERR_INVALID_ARG;
     if (c->flags_host[0]) return ALN_ERR_NONFINITE;
 
-    // Alg. 1: scatter, scale factors, q, occupancy
-    ALN_TRY(cudaMemsetAsync(c->A_copy, 0, (size_t)n * lda * esz, c->stream));
+    // Alg. 1: scale factors, q, occupancy (and the scatter)
+    if (!no_dense) ALN_TRY(cudaMemsetAsync(c->A_copy, 0, (size_t)n * lda * esz, c->stream));
     if (sparse_gram) ALN_TRY(cudaMemsetAsync(occ, 0, b_occ, c->stream));
     const int kc = k <= 4 ? (int)k : 0;
-    ALN_TRY(launch_csc_colstats(cp, ri, vv, dtype, n, c->B, kc, ldb, c->A_copy, lda, c->s,
+    ALN_TRY(launch_csc_colstats(cp, ri, vv, dtype, n, c->B, kc, ldb,
+                                no_dense ? nullptr : c->A_copy, lda, c->s,
                                 c->inv_s, c->q64, ldq, sparse_gram ? occ : nullptr, W,
                                 c->stream));
     c->launches += 3;
@@ -695,6 +710,17 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
         ALN_TRY(launch_sgram_tc(c->opt.gram_split, occ, W, wbase, toff, hi, mid, lo, n, c->inv_s,
                                 (float*)c->Q, ldq, c->flags + 1, c->stream));
         c->launches += 4;
+        if (no_dense) {  // the KKT pass reads these until the next prepare
+            c->csc_cp = cp;
+            c->csc_ri = ri;
+            c->csc_v = (const float*)vv;
+            c->csc_occ = occ;
+            c->csc_wbase = wbase;
+            c->csc_toff = toff;
+            c->csc_fpart = fpart;
+            c->csc_W = W;
+            c->csc_box_bytes = sb;
+        }
     } else if (c->batched) {
         ALN_CHECK(batch_prepare(c));
     } else {
@@ -703,6 +729,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     }
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     ALN_CHECK(prep_finish(c, k));
+    c->csc_kkt = no_dense ? 1 : 0;
     c->prepared = 1;
     return ALN_OK;
 }
@@ -711,6 +738,7 @@ aln_status aln_prepare_grouped(aln_ctx* c, int32_t count, const aln_problem* pro
                                int32_t dtype) {
     if (!c || !probs || count < 1 || count > (1 << 20)) return ALN_ERR_INVALID_ARG;
     if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
+    c->csc_kkt = 0;
     int64_t cols = 0;
     for (int32_t p = 0; p < count; ++p) {
         const aln_problem& q = probs[p];

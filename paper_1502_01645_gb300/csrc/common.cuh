@@ -220,6 +220,18 @@ struct aln_ctx {
     // CSC prepare: device copies of host CSC arrays, occupancy, box numbering
     void* csc_pool = nullptr;
     size_t csc_bytes = 0;
+    // 1 when A lives only as CSC arrays + packed boxes (no dense copy): the
+    // KKT pass then reads those (launch_csc_kkt)
+    int csc_kkt = 0;
+    const int64_t* csc_cp = nullptr;
+    const int32_t* csc_ri = nullptr;
+    const float* csc_v = nullptr;
+    uint32_t* csc_occ = nullptr;
+    int32_t* csc_wbase = nullptr;
+    int64_t* csc_toff = nullptr;
+    double* csc_fpart = nullptr;
+    int csc_W = 0;
+    size_t csc_box_bytes = 0;  // one split term's packed boxes in A_hi
 
     // iteration workspace (element type follows the precision)
     void* qv = nullptr;       // q of the right-hand side being solved (iteration type)

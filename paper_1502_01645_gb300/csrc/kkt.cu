@@ -242,6 +242,21 @@ __global__ void k_kkt_final(const double* __restrict__ gpart, int ng,
 // kkt_part (512 fparts | n gparts), kkt_out (2).
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2) {
     const int64_t d = c->d, n = c->n;
+    if (c->csc_kkt) {  // A held as CSC arrays and packed boxes (sparse.cu)
+        const __nv_bfloat16* hi = c->A_hi;
+        const __nv_bfloat16* mid = (const __nv_bfloat16*)((const uint8_t*)c->A_hi + c->csc_box_bytes);
+        const __nv_bfloat16* lo =
+            (const __nv_bfloat16*)((const uint8_t*)c->A_hi + 2 * c->csc_box_bytes);
+        double* gpart = c->kkt_part + 512;
+        cudaError_t e = launch_csc_kkt(c->csc_cp, c->csc_ri, c->csc_v, d, n, c->csc_occ, c->csc_W,
+                                       c->csc_wbase, c->csc_toff, hi, mid, lo, x64,
+                                       (const float*)b, c->s, c->r64, c->csc_fpart, c->g64, gpart,
+                                       c->stream);
+        if (e != cudaSuccess) return e;
+        k_kkt_final<<<1, 256, 0, c->stream>>>(gpart, (int)n, c->csc_fpart, (int)ceil_div(d, 64),
+                                              den, out2);
+        return cudaGetLastError();
+    }
     const int CG = c->CG;
     const int64_t cpg = ceil_div(n, CG);
     const dim3 g1((unsigned)ceil_div(d, kKktRows), (unsigned)CG);

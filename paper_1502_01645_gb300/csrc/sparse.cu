@@ -5,9 +5,9 @@
 // Every step reads only the stored entries:
 //   k_csc_check     the structure (bounds, order) and finiteness;
 //   k_csc_colstats  s_j² = Σ a_tj², (Aᵀb_c)_j for up to four right-hand
-//                   sides, the scatter into the dense column-major A that the
-//                   FP64 KKT check reads, and the occupancy bitmap of the
-//                   Gram's operand boxes (64 rows × 128 columns);
+//                   sides, the occupancy bitmap of the Gram's operand boxes
+//                   (64 rows × 128 columns), and where a path still needs it
+//                   the scatter into a dense column-major copy of A;
 //   k_csc_tiles / k_csc_offsets  number the occupied boxes, column tile by
 //                   column tile (a popcount prefix per bitmap word);
 //   k_csc_pack      the exact three-term BF16 split of every entry, written
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCscThreads)
     if (j >= n) return;
     const int64_t p0 = cp[j], p1 = cp[j + 1];
     DotAcc<T> sq, dot[4];
-    T* col = A + j * lda;
+    T* col = A ? A + j * lda : nullptr;  // no dense copy when A is null
     uint32_t* occ_t = OCC ? occ + (j >> 7) * (int64_t)W : nullptr;
     for (int64_t t = p0 + lane; t < p1; t += 32) {
         const int32_t r = ri[t];
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kCscThreads)
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             if (c < kc) dot[c].add(a, B[(int64_t)c * ldb + r]);
-        col[r] = a;
+        if (col) col[r] = a;
         if (OCC) {
             const int kb = r >> 6;
             // rows are increasing: only the first entry of a K block sets its bit
@@ -186,7 +186,127 @@ __global__ void __launch_bounds__(kCscThreads)
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 KKT residual of Def. 1 from the CSC form (FP32 values), the same
+// quantities as the dense pass (kkt.cu) without a dense copy of A:
+//   k_csc_kkt_ax   one block per 64-row block kb: r = A x − b over the occupied
+//                  boxes of the packed operand — their three BF16 terms add up
+//                  exactly to the FP32 entry (h + (m + l) = a) — visiting the
+//                  column tiles in increasing order (a fixed summation order),
+//                  and fpart[kb] = Σ r² over the block;
+//   k_csc_kkt_grad one warp per column: ∇F_j = A_jᵀ r from the stored entries,
+//                  g_j = ∇F_j / s_j (kept for the refinement), ḡ_j² on P(s·x).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCscThreads)
+    k_csc_kkt_ax(const uint32_t* __restrict__ occ, int W, const int32_t* __restrict__ wbase,
+                 const int64_t* __restrict__ toff, int64_t T, const __nv_bfloat16* __restrict__ hi,
+                 const __nv_bfloat16* __restrict__ mid, const __nv_bfloat16* __restrict__ lo,
+                 const double* __restrict__ x, int64_t n, const float* __restrict__ b, int64_t d,
+                 double* __restrict__ r, double* __restrict__ fpart) {
+    __shared__ double s_x[128];
+    __shared__ double s_acc[4][64];
+    __shared__ int s_list[kCscThreads];
+    __shared__ int s_wc[kCscWarps];
+    __shared__ double s_red[kCscWarps];
+    const int kb = blockIdx.x, wq = kb >> 5;
+    const uint32_t bit = 1u << (kb & 31);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int rr = threadIdx.x & 63, grp = threadIdx.x >> 6;  // row of the block, column group
+    double acc = 0.0;
+    for (int64_t I0 = 0; I0 < T; I0 += kCscThreads) {
+        // the tiles of this chunk that hold block kb, in increasing order
+        const int64_t I = I0 + threadIdx.x;
+        const bool has = I < T && (occ[I * W + wq] & bit);
+        const unsigned bal = __ballot_sync(0xffffffffu, has);
+        if (lane == 0) s_wc[wid] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kCscWarps; ++w) {
+            before += w < wid ? s_wc[w] : 0;
+            total += s_wc[w];
+        }
+        if (has) s_list[before + __popc(bal & ((1u << lane) - 1u))] = (int)(I - I0);
+        __syncthreads();
+        for (int u = 0; u < total; ++u) {
+            const int64_t tI = I0 + s_list[u];
+            const int64_t ow = tI * W + wq;
+            const int64_t box = toff[tI] + wbase[ow] + __popc(occ[ow] & (bit - 1u));
+            if (threadIdx.x < 128) {
+                const int64_t j = tI * 128 + threadIdx.x;
+                s_x[threadIdx.x] = j < n ? x[j] : 0.0;
+            }
+            __syncthreads();
+            const int64_t base = box * kPackTile;
+#pragma unroll 4
+            for (int c = grp * 32; c < grp * 32 + 32; ++c) {
+                const double xj = s_x[c];
+                if (xj == 0.0) continue;  // x is sparse at the optimum
+                const int64_t at = base + c * 64 + ((((rr >> 3) ^ (c & 7)) << 3) | (rr & 7));
+                const float a = __bfloat162float(hi[at]) +
+                                (__bfloat162float(mid[at]) + __bfloat162float(lo[at]));
+                acc = fma((double)a, xj, acc);
+            }
+            __syncthreads();
+        }
+    }
+    s_acc[grp][rr] = acc;
+    __syncthreads();
+    double v2 = 0.0;
+    if (threadIdx.x < 64) {
+        const int64_t row = (int64_t)kb * 64 + threadIdx.x;
+        if (row < d) {
+            const double v = ((s_acc[0][threadIdx.x] + s_acc[1][threadIdx.x]) +
+                              (s_acc[2][threadIdx.x] + s_acc[3][threadIdx.x])) -
+                             (double)b[row];
+            r[row] = v;
+            v2 = v * v;
+        }
+    }
+    v2 = warp_sum(v2);
+    if (lane == 0) s_red[wid] = v2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kCscWarps; ++w) t += s_red[w];
+        fpart[kb] = t;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCscThreads)
+    k_csc_kkt_grad(const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
+                   const T* __restrict__ v, int64_t n, const double* __restrict__ r,
+                   const double* __restrict__ s, const double* __restrict__ x,
+                   double* __restrict__ g64, double* __restrict__ gpart) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
+    if (j >= n) return;
+    double acc = 0.0;
+    for (int64_t t = cp[j] + lane; t < cp[j + 1]; t += 32) acc = fma((double)v[t], r[ri[t]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+        const double gj = acc / s[j];
+        const double yj = x[j] * s[j];
+        g64[j] = gj;
+        gpart[j] = (yj > 0.0 || gj < 0.0) ? gj * gj : 0.0;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_csc_kkt(const int64_t* cp, const int32_t* ri, const float* v, int64_t d,
+                           int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
+                           const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                           const __nv_bfloat16* lo, const double* x, const float* b,
+                           const double* s, double* r, double* fpart, double* g64, double* gpart,
+                           cudaStream_t st) {
+    const int64_t T = ceil_div(n, 128), KB = ceil_div(d, 64);
+    k_csc_kkt_ax<<<(unsigned)KB, kCscThreads, 0, st>>>(occ, W, wbase, toff, T, hi, mid, lo, x, n, b,
+                                                       d, r, fpart);
+    k_csc_kkt_grad<float><<<(unsigned)ceil_div(n, kCscWarps), kCscThreads, 0, st>>>(
+        cp, ri, v, n, r, s, x, g64, gpart);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_csc_check(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
                              int64_t d, int64_t n, int64_t nnz, int* flags, cudaStream_t st) {

@@ -243,3 +243,30 @@ def test_csc_full_size_sampled(aln):
         qo = -S.atb_entry(p.col_ptr, p.row_idx, p.vals, b, int(j)) / np.sqrt(h_jj)
         assert abs(q[0, j] - qo) <= 1e-12 * max(1.0, abs(qo))
     assert np.all(X[0] >= 0.0)
+
+
+@pytest.mark.parametrize("d,n,band,density", [(3000, 700, 400, 0.2), (130, 129, 40, 0.5)])
+def test_csc_kkt_pass_matches_oracle(aln, d, n, band, density):
+    """The FP64 KKT pass of a CSC context with FP32 values reads the CSC
+    arrays and the packed blocks (no dense copy): residual and objective of
+    arbitrary non-negative points against the oracle's, computed from the
+    dense matrix, and against the dense context's pass."""
+    p = W.banded_tall(d=d, n=n, band=band, density=density, seed=d - n)
+    A64 = S.csc_to_dense(p.d, p.n, p.col_ptr, p.row_idx, p.vals)
+    b64 = p.B[0].astype(np.float64)
+    r = np.random.default_rng(d)
+    X = np.where(r.random((3, n)) < 0.5, 0.0, r.exponential(1.0, (3, n)))
+    X[2] = 0.0                                   # the origin: ḡ = min(q, 0)
+    with aln.Solver("split_bf16") as s:
+        s.prepare_csc(p.d, p.col_ptr, p.row_idx, p.vals, p.B)
+        got = [s.kkt(np.ascontiguousarray(X[c:c + 1])) for c in range(3)]
+    with aln.Solver("split_bf16") as s:
+        s.prepare(p.dense(), p.B)
+        ref = [s.kkt(np.ascontiguousarray(X[c:c + 1])) for c in range(3)]
+    for c in range(3):
+        rel_o, F_o = O.kkt_residual(A64, b64, X[c])
+        assert got[c][0][0] == pytest.approx(rel_o, rel=1e-10), c
+        assert got[c][1][0] == pytest.approx(F_o, rel=1e-12), c
+        assert got[c][0][0] == pytest.approx(ref[c][0][0], rel=1e-10), c
+        assert got[c][1][0] == pytest.approx(ref[c][1][0], rel=1e-12), c
+    assert got[2][0][0] == pytest.approx(1.0, rel=1e-12)
