@@ -10,7 +10,10 @@ FP64 relative KKT ≤ 1e-6, including the FP64 KKT evaluation from A.
 Other workloads (--workload): `shared_multi_rhs` (A 10000×1000 shared by 4096
 right-hand sides; one step = the whole batch), `uneven_batch` (512 independent
 problems of uneven size, n in [32, 1024]; one step = prepare and solve all of
-them) and `uniform_small` (A 1000×200, plain FP64 method at rel KKT 1e-10).
+them), `paper_tcases` (the 30 sub-tests of §5's test-case design), `nmf`
+(alternating NNLS), `warmstart` (learned start points), `banded_tall` (a
+sparse 200000×5000 A in CSC form through aln_prepare_csc) and `uniform_small`
+(A 1000×200, plain FP64 method at rel KKT 1e-10).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload NAME]
@@ -67,6 +70,12 @@ WORKLOADS = {
         desc="nmf_{d}x{n}_r{k}: V = W*H* + 1% noise (W*, H* 70% non-zero U[0,1]), FP32; "
              "{outer} ANLS outer iterations from a seeded U[0,1] start, each sub-problem "
              "to rel KKT {tol}"),
+    "banded_tall": dict(
+        d=200000, n=5000, k=1, band=6000, density=0.1, tol=1e-6, seed=1008, prec="split_bf16",
+        desc="banded_tall_{d}x{n}_f32: sparse tall A in CSC form, column j holds {density} x "
+             "{band} entries at random rows of a {band}-row window sliding down the rows, "
+             "U(0,1] x log-uniform column scales [1e-2,1e2]; x_true 70% zeros Exp(1), "
+             "b = A x_true + 1% noise"),
     "uniform_small": dict(
         d=1000, n=200, k=1, tol=1e-10, seed=1001, prec="fp64",
         desc="uniform_small_{d}x{n}_f64: A U[0,1], x_true half zeros U[0,1], "
@@ -126,6 +135,9 @@ def generate(w, rank=0):
     if w["name"] == "paper_tcases":
         return [W.tcase(kind, sub, n=w["n"], d=w["d"], seed=w["seed"] + rank)
                 for kind in sorted(W.TCASES) for sub in range(len(W.TCASE_SPARSITY))]
+    if w["name"] == "banded_tall":
+        return W.banded_tall(d=w["d"], n=w["n"], band=w["band"], density=w["density"],
+                             seed=w["seed"] + rank)
     if w["name"] == "shared_multi_rhs":
         return W.shared_multi_rhs(d=w["d"], n=w["n"], k=w["k"], seed=w["seed"] + rank)
     return W.uniform_small(d=w["d"], n=w["n"], seed=w["seed"] + rank)
@@ -306,6 +318,8 @@ def run_reference(args):
             t, desc = cpu_sample_nmf(w)
         elif w["name"] == "warmstart":
             t, desc = cpu_sample(w, p[1])
+        elif w["name"] == "banded_tall":
+            t, desc = cpu_sample_banded(w, p)
         else:
             t, desc = cpu_sample(w, p)
         if i >= args.warmup:
@@ -356,6 +370,8 @@ def run_ours(args):
         return run_nmf(args, w, world, rank, local)
     if w["name"] == "warmstart":
         return run_warmstart(args, w, world, rank, local)
+    if w["name"] == "banded_tall":
+        return run_banded(args, w, world, rank, local)
     d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
     p = generate(w, rank)
     A_np, B_np = p.A, p.B
@@ -1032,6 +1048,246 @@ def run_nmf(args, w, world, rank, local):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "plain_fp64": None,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def sgram_block_products(p):
+    """Occupied 64-row block pairs the block-sparse Gram multiplies: for the
+    128-column tiles I ≥ J, the K blocks holding entries of both tiles
+    (diagonal tiles counted once).  Host bookkeeping for the roofline."""
+    import numpy as np
+    cols = np.repeat(np.arange(p.n), np.diff(p.col_ptr))
+    tiles = (p.n + 127) // 128
+    kb = (p.d + 63) // 64
+    occ = np.zeros((tiles, kb), dtype=bool)
+    occ[cols // 128, p.row_idx // 64] = True
+    occ = occ.astype(np.int64)
+    common = occ @ occ.T                      # common[I, J] = shared K blocks
+    off = int(np.tril(common, -1).sum())
+    diag = int(np.trace(common))
+    return off, diag
+
+
+def cpu_sample_banded(w, p):
+    """The FP64 oracle on the first m = n/5 columns of the sparse A (expanded
+    to dense, all d rows, same b), scaled by (n/m)² as for the dense workload
+    (the oracle works on the dense matrix: its Gram and Alg. 2 products grow
+    as n²)."""
+    import numpy as np
+    from oracle import nnls as O
+    from oracle import sparse as S
+    m = max(1, w["n"] // 5)
+    cp = p.col_ptr[:m + 1]
+    A64 = np.asfortranarray(S.csc_to_dense(p.d, m, cp, p.row_idx, p.vals))
+    b64 = np.asarray(p.B[0], dtype=np.float64)
+    t0 = time.perf_counter()
+    O.antilop(A64, b64, tol=w["tol"])
+    t = time.perf_counter() - t0
+    scale = (w["n"] / m) ** 2
+    return t * scale, (f"oracle antilop on the first {m} columns (dense, d={p.d}) in {t:.2f} s, "
+                       f"x (n/m)^2 = {scale:.0f} for the full size")
+
+
+def run_banded(args, w, world, rank, local):
+    """Sparse tall A in CSC form: one step = aln_prepare_csc (column statistics
+    from the stored entries, occupied operand blocks packed, block-sparse
+    tcgen05 Gram) + Alg. 2 + FP64 KKT from A, one right-hand side."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1502_01645_gb300 import aln
+
+    d, n, tol = w["d"], w["n"], w["tol"]
+    p = generate(w, rank)
+    cp = torch.from_numpy(p.col_ptr).cuda()
+    ri = torch.from_numpy(p.row_idx).cuda()
+    vv = torch.from_numpy(p.vals).cuda()
+    Bt = torch.from_numpy(np.ascontiguousarray(p.B)).cuda()
+    Xt = torch.zeros((1, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                        gram_split=args.gram_split)
+
+    def step():
+        solver.prepare_csc(d, cp, ri, vv, Bt)
+        _, info = solver.solve(tol=tol, X=Xt)
+        return info, solver.stats()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # the CSC inputs (≈25 MB) fit in L2: a 256 MB buffer is written before
+    # every step (outside the step's event pair) so each step starts cold
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = solver.stats().kernel_launches
+    barrier()
+    stats, worst, iters, evs = [], 0.0, [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info, st = step()
+        e1.record(stream)
+        evs.append((e0, e1))
+        stats.append(st)
+        worst = max(worst, info[0].rel_kkt)
+        iters.append(info[0].iters)
+    barrier()
+    elapsed = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    launches = solver.stats().kernel_launches - launches0
+    clocks = sampler.stop()
+    if worst > tol:
+        raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
+    tmax = max_over_ranks(elapsed, world)
+    value = job_rate(1, args.steps, world, tmax)
+
+    def avg(f):
+        return sum(f(s) for s in stats) / len(stats)
+
+    csc_bytes = int(p.col_ptr.nbytes + p.row_idx.nbytes + p.vals.nbytes + p.B.nbytes)
+    e2e = None
+    if not args.no_e2e:
+        hcp = torch.from_numpy(p.col_ptr).pin_memory()
+        hri = torch.from_numpy(p.row_idx).pin_memory()
+        hvv = torch.from_numpy(p.vals).pin_memory()
+        hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
+        X_h = torch.zeros((1, n), dtype=torch.float64).pin_memory()
+        k_e2e = max(3, min(args.steps, 5))
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                             gram_split=args.gram_split)
+        hsolver.prepare_csc(d, hcp, hri, hvv, hB)
+        hsolver.solve(tol=tol, X=X_h)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            hsolver.prepare_csc(d, hcp, hri, hvv, hB)
+            _, hinfo = hsolver.solve(tol=tol, X=X_h)
+        barrier()
+        te = time.perf_counter() - t0
+        hsolver.close()
+        e2e = {"value": job_rate(1, k_e2e, world, max_over_ranks(te, world)), "unit": UNIT,
+               "h2d_bytes_per_step": csc_bytes, "d2h_bytes_per_step": int(n * 8),
+               "steps": k_e2e, "rel_kkt_max": hinfo[0].rel_kkt}
+
+    # the same chosen form from the dense matrix (aln_prepare: dense Gram over
+    # every K block) and the plain FP64 method, on the same problem
+    dense = plain = None
+    if not args.no_plain:
+        Ad = torch.from_numpy(np.ascontiguousarray(p.dense().T)).cuda().t()
+        dsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
+                             gram_split=args.gram_split)
+        dsolver.prepare(Ad, Bt)
+        dsolver.solve(tol=tol, X=Xt)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            dsolver.prepare(Ad, Bt)
+            _, dinfo = dsolver.solve(tol=tol, X=Xt)
+        e1.record(stream)
+        barrier()
+        td = e0.elapsed_time(e1) / 1e3 / reps
+        dst = dsolver.stats()
+        dsolver.close()
+        dense = {"value": 1.0 / td, "unit": UNIT, "ms_per_step": td * 1e3,
+                 "gram_ms": dst.gram_ms, "prepare_ms": dst.prepare_ms,
+                 "rel_kkt": dinfo[0].rel_kkt, "iters": dinfo[0].iters,
+                 "note": "aln_prepare on the dense matrix (split-BF16 Gram over every "
+                         "K block) + the same Alg. 2"}
+        psolver = aln.Solver("fp64", stream=stream.cuda_stream)
+        psolver.prepare_csc(d, cp, ri, vv, Bt)
+        psolver.solve(tol=tol, X=Xt)
+        barrier()
+        e0.record(stream)
+        psolver.prepare_csc(d, cp, ri, vv, Bt)
+        _, pinfo = psolver.solve(tol=tol, X=Xt)
+        e1.record(stream)
+        barrier()
+        tp = e0.elapsed_time(e1) / 1e3
+        pst = psolver.stats()
+        psolver.close()
+        del Ad
+        plain = {"value": 1.0 / tp, "unit": UNIT, "ms_per_step": tp * 1e3,
+                 "gram_ms": pst.gram_ms, "rel_kkt_max": pinfo[0].rel_kkt,
+                 "iters_max": pinfo[0].iters, "repeats": 1,
+                 "note": "FP64 Gram of the scattered dense matrix + FP64 Alg. 2"}
+
+    solver.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+    peak_tc = float(pk["bf16_tflops_sustained"])
+    gram = avg(lambda s: s.gram_ms)
+    it_ms = avg(lambda s: s.iterate_ms)
+    off, diag = sgram_block_products(p)
+    flops = 12.0 * 64 * (off * 128.0 * 128.0 + diag * 128.0 * 129.0 / 2)
+    ach_g = flops / (gram / 1e3) / 1e12
+    rooflines = [{"bound": "tensor",
+                  "kernel": "block-sparse prepare (pack + k_sgram_tc; gram_ms spans numbering, "
+                            "packing and the Gram)",
+                  "achieved": ach_g, "peak": peak_tc, "unit": "TFLOP/s", "frac": ach_g / peak_tc,
+                  "traffic": None, "peak_kind": f"{pk_kind} bf16 sustained",
+                  "algorithmic_per_launch": flops, "avg_launch_ms": gram,
+                  "block_pairs": {"off_diagonal": off, "diagonal": diag,
+                                  "dense_equivalent": ((n + 127) // 128) * ((n + 127) // 128 + 1)
+                                  // 2 * ((d + 63) // 64)}}]
+    qbytes = 4 * n * avg(lambda s: s.passive_rows + s.clipped_rows)
+    ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
+    ldq = (n + 127) // 128 * 128
+    rooflines.append({"bound": "hbm", "kernel": "k_alg2_repl (persistent Alg. 2 loop)",
+                      "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                      "traffic": 1.002 * n * ldq * 4, "peak_kind": f"{pk_kind} hbm copy",
+                      "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
+                      "note": "the rows of Q read stay in the 129 MB L2 between iterations"})
+    rooflines.sort(key=lambda r: -r["avg_launch_ms"])
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        ts, desc = cpu_sample_banded(w, p)
+        cpu = {"value": 1.0 / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+               "sample": desc}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 split + f32", "data": "synthetic",
+        "config": {"workload": w["desc"], "d": d, "n": n, "k": 1, "nnz": p.nnz, "tol": tol,
+                   "seed": w["seed"],
+                   "form": "aln_prepare_csc: block-sparse 3-term split-BF16 tcgen05 Gram, "
+                           "FP32 Alg. 2, FP64 scale/KKT/refinement",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs ({csc_bytes / 1e6:.1f} MB of CSC arrays and b) smaller "
+                         "than L2: a 256 MB buffer is written before every step, outside "
+                         "the per-step CUDA event pairs that are summed",
+                   "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
+                   "solve_ms": avg(lambda s: s.solve_ms), "iterate_ms": it_ms,
+                   "kkt_ms": avg(lambda s: s.kkt_ms), "iters_max": iters,
+                   "rel_kkt_max": worst},
+        "roofline": rooflines[0],
+        "roofline_secondary": rooflines[1],
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "plain_fp64": plain,
+        "dense_prepare": dense,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

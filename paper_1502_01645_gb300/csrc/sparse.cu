@@ -197,6 +197,9 @@ __global__ void __launch_bounds__(kCscThreads)
 //   k_csc_kkt_grad one warp per column: ∇F_j = A_jᵀ r from the stored entries,
 //                  g_j = ∇F_j / s_j (kept for the refinement), ḡ_j² on P(s·x).
 // ---------------------------------------------------------------------------
+// Thread t owns rows 8·(t mod 8) … +7 of the block (one 16-byte chunk of
+// eight BF16 per split term and column) for the four columns 4·(t / 8) … +3 of
+// every tile; the 32 column groups' partial rows are added in a fixed order.
 __global__ void __launch_bounds__(kCscThreads)
     k_csc_kkt_ax(const uint32_t* __restrict__ occ, int W, const int32_t* __restrict__ wbase,
                  const int64_t* __restrict__ toff, int64_t T, const __nv_bfloat16* __restrict__ hi,
@@ -204,15 +207,17 @@ __global__ void __launch_bounds__(kCscThreads)
                  const double* __restrict__ x, int64_t n, const float* __restrict__ b, int64_t d,
                  double* __restrict__ r, double* __restrict__ fpart) {
     __shared__ double s_x[128];
-    __shared__ double s_acc[4][64];
+    __shared__ double s_part[32][65];
     __shared__ int s_list[kCscThreads];
     __shared__ int s_wc[kCscWarps];
     __shared__ double s_red[kCscWarps];
     const int kb = blockIdx.x, wq = kb >> 5;
     const uint32_t bit = 1u << (kb & 31);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int rr = threadIdx.x & 63, grp = threadIdx.x >> 6;  // row of the block, column group
-    double acc = 0.0;
+    const int ch = threadIdx.x & 7, cg = threadIdx.x >> 3;  // row chunk, column group
+    double acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
     for (int64_t I0 = 0; I0 < T; I0 += kCscThreads) {
         // the tiles of this chunk that hold block kb, in increasing order
         const int64_t I = I0 + threadIdx.x;
@@ -237,27 +242,46 @@ __global__ void __launch_bounds__(kCscThreads)
             }
             __syncthreads();
             const int64_t base = box * kPackTile;
-#pragma unroll 4
-            for (int c = grp * 32; c < grp * 32 + 32; ++c) {
-                const double xj = s_x[c];
-                if (xj == 0.0) continue;  // x is sparse at the optimum
-                const int64_t at = base + c * 64 + ((((rr >> 3) ^ (c & 7)) << 3) | (rr & 7));
-                const float a = __bfloat162float(hi[at]) +
-                                (__bfloat162float(mid[at]) + __bfloat162float(lo[at]));
-                acc = fma((double)a, xj, acc);
+            uint4 vh[4], vm[4], vl[4];
+            double xj[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = cg * 4 + q;
+                xj[q] = s_x[c];
+                // 16-byte chunk ch of column c sits at chunk position ch ^ (c mod 8)
+                const int64_t at = base + c * 64 + ((ch ^ (c & 7)) << 3);
+                if (xj[q] != 0.0) {  // x is sparse at the optimum
+                    vh[q] = __ldg(reinterpret_cast<const uint4*>(hi + at));
+                    vm[q] = __ldg(reinterpret_cast<const uint4*>(mid + at));
+                    vl[q] = __ldg(reinterpret_cast<const uint4*>(lo + at));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (xj[q] == 0.0) continue;
+                const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&vh[q]);
+                const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&vm[q]);
+                const __nv_bfloat16* l8 = reinterpret_cast<const __nv_bfloat16*>(&vl[q]);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float a = __bfloat162float(h8[e]) +
+                                    (__bfloat162float(m8[e]) + __bfloat162float(l8[e]));
+                    acc[e] = fma((double)a, xj[q], acc[e]);
+                }
             }
             __syncthreads();
         }
     }
-    s_acc[grp][rr] = acc;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s_part[cg][ch * 8 + e] = acc[e];
     __syncthreads();
     double v2 = 0.0;
     if (threadIdx.x < 64) {
         const int64_t row = (int64_t)kb * 64 + threadIdx.x;
+        double v = 0.0;
+        for (int g = 0; g < 32; ++g) v += s_part[g][threadIdx.x];
         if (row < d) {
-            const double v = ((s_acc[0][threadIdx.x] + s_acc[1][threadIdx.x]) +
-                              (s_acc[2][threadIdx.x] + s_acc[3][threadIdx.x])) -
-                             (double)b[row];
+            v -= (double)b[row];
             r[row] = v;
             v2 = v * v;
         }
