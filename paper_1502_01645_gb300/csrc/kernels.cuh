@@ -165,13 +165,14 @@ cudaError_t launch_csc_pack(const int64_t* cp, const int32_t* ri, const void* v,
                             __nv_bfloat16* lo, cudaStream_t st);
 
 // FP64 KKT pass from the CSC arrays and the packed boxes (FP32 values):
-// r (d), fpart (⌈d/64⌉ block sums of r²), g64 and gpart (n) as in launch_kkt.
+// r (d; also as FP32 pairs rh, rl), fpart (⌈d/64⌉ block sums of r²), g64 and
+// gpart (n) as in launch_kkt.
 cudaError_t launch_csc_kkt(const int64_t* cp, const int32_t* ri, const float* v, int64_t d,
                            int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, const double* x, const float* b,
-                           const double* s, double* r, double* fpart, double* g64, double* gpart,
-                           cudaStream_t st);
+                           const double* s, double* r, float* rh, float* rl, double* fpart,
+                           double* g64, double* gpart, cudaStream_t st);
 
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);

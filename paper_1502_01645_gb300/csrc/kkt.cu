@@ -248,10 +248,11 @@ cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den,
         const __nv_bfloat16* lo =
             (const __nv_bfloat16*)((const uint8_t*)c->A_hi + 2 * c->csc_box_bytes);
         double* gpart = c->kkt_part + 512;
+        float* rh = reinterpret_cast<float*>(c->rpart);  // rpart holds ≥ d doubles
         cudaError_t e = launch_csc_kkt(c->csc_cp, c->csc_ri, c->csc_v, d, n, c->csc_occ, c->csc_W,
                                        c->csc_wbase, c->csc_toff, hi, mid, lo, x64,
-                                       (const float*)b, c->s, c->r64, c->csc_fpart, c->g64, gpart,
-                                       c->stream);
+                                       (const float*)b, c->s, c->r64, rh, rh + d, c->csc_fpart,
+                                       c->g64, gpart, c->stream);
         if (e != cudaSuccess) return e;
         k_kkt_final<<<1, 256, 0, c->stream>>>(gpart, (int)n, c->csc_fpart, (int)ceil_div(d, 64),
                                               den, out2);

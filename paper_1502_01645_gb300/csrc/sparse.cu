@@ -197,16 +197,35 @@ __global__ void __launch_bounds__(kCscThreads)
 //   k_csc_kkt_grad one warp per column: ∇F_j = A_jᵀ r from the stored entries,
 //                  g_j = ∇F_j / s_j (kept for the refinement), ḡ_j² on P(s·x).
 // ---------------------------------------------------------------------------
+// Float-pair accumulator on the FP32 pipe (this GPU's FP64 pipe is narrow):
+// += a·(h + l) with the product's rounding error from an FMA (TwoProduct) and
+// the addition's from TwoSum kept in c (Ogita, Rump & Oishi 2005).
+struct FPair {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a, float h, float l) {
+        const float p = __fmul_rn(a, h);
+        const float ep = fmaf(a, h, -p);
+        const float t = s + p;
+        const float z = t - s;
+        c += ((s - (t - z)) + (p - z)) + fmaf(a, l, ep);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Thread t owns rows 8·(t mod 8) … +7 of the block (one 16-byte chunk of
 // eight BF16 per split term and column) for the four columns 4·(t / 8) … +3 of
-// every tile; the 32 column groups' partial rows are added in a fixed order.
+// every tile; x_j enters as the FP32 pair (hi, lo) and each row sums in a
+// float pair, flushed to FP64 every 16 tiles; the 32 column groups' partial
+// rows are then added in a fixed order.  Writes r in FP64 and as FP32 pairs.
 __global__ void __launch_bounds__(kCscThreads)
     k_csc_kkt_ax(const uint32_t* __restrict__ occ, int W, const int32_t* __restrict__ wbase,
                  const int64_t* __restrict__ toff, int64_t T, const __nv_bfloat16* __restrict__ hi,
                  const __nv_bfloat16* __restrict__ mid, const __nv_bfloat16* __restrict__ lo,
                  const double* __restrict__ x, int64_t n, const float* __restrict__ b, int64_t d,
-                 double* __restrict__ r, double* __restrict__ fpart) {
-    __shared__ double s_x[128];
+                 double* __restrict__ r, float* __restrict__ rh, float* __restrict__ rl,
+                 double* __restrict__ fpart) {
+    __shared__ float2 s_x[128];
     __shared__ double s_part[32][65];
     __shared__ int s_list[kCscThreads];
     __shared__ int s_wc[kCscWarps];
@@ -215,9 +234,11 @@ __global__ void __launch_bounds__(kCscThreads)
     const uint32_t bit = 1u << (kb & 31);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int ch = threadIdx.x & 7, cg = threadIdx.x >> 3;  // row chunk, column group
-    double acc[8];
+    double accd[8];
+    FPair acc[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+    for (int e = 0; e < 8; ++e) accd[e] = 0.0;
+    int since = 0;  // tiles added into the pairs since their last flush
     for (int64_t I0 = 0; I0 < T; I0 += kCscThreads) {
         // the tiles of this chunk that hold block kb, in increasing order
         const int64_t I = I0 + threadIdx.x;
@@ -238,19 +259,21 @@ __global__ void __launch_bounds__(kCscThreads)
             const int64_t box = toff[tI] + wbase[ow] + __popc(occ[ow] & (bit - 1u));
             if (threadIdx.x < 128) {
                 const int64_t j = tI * 128 + threadIdx.x;
-                s_x[threadIdx.x] = j < n ? x[j] : 0.0;
+                const double xv = j < n ? x[j] : 0.0;
+                const float xh = (float)xv;
+                s_x[threadIdx.x] = make_float2(xh, (float)(xv - (double)xh));
             }
             __syncthreads();
             const int64_t base = box * kPackTile;
             uint4 vh[4], vm[4], vl[4];
-            double xj[4];
+            float2 xq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int c = cg * 4 + q;
-                xj[q] = s_x[c];
+                xq[q] = s_x[c];
                 // 16-byte chunk ch of column c sits at chunk position ch ^ (c mod 8)
                 const int64_t at = base + c * 64 + ((ch ^ (c & 7)) << 3);
-                if (xj[q] != 0.0) {  // x is sparse at the optimum
+                if (xq[q].x != 0.0f) {  // x is sparse at the optimum
                     vh[q] = __ldg(reinterpret_cast<const uint4*>(hi + at));
                     vm[q] = __ldg(reinterpret_cast<const uint4*>(mid + at));
                     vl[q] = __ldg(reinterpret_cast<const uint4*>(lo + at));
@@ -258,7 +281,7 @@ __global__ void __launch_bounds__(kCscThreads)
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (xj[q] == 0.0) continue;
+                if (xq[q].x == 0.0f) continue;
                 const __nv_bfloat16* h8 = reinterpret_cast<const __nv_bfloat16*>(&vh[q]);
                 const __nv_bfloat16* m8 = reinterpret_cast<const __nv_bfloat16*>(&vm[q]);
                 const __nv_bfloat16* l8 = reinterpret_cast<const __nv_bfloat16*>(&vl[q]);
@@ -266,14 +289,22 @@ __global__ void __launch_bounds__(kCscThreads)
                 for (int e = 0; e < 8; ++e) {
                     const float a = __bfloat162float(h8[e]) +
                                     (__bfloat162float(m8[e]) + __bfloat162float(l8[e]));
-                    acc[e] = fma((double)a, xj[q], acc[e]);
+                    acc[e].add(a, xq[q].x, xq[q].y);
                 }
+            }
+            if (++since == 16) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    accd[e] += acc[e].value();
+                    acc[e] = FPair();
+                }
+                since = 0;
             }
             __syncthreads();
         }
     }
 #pragma unroll
-    for (int e = 0; e < 8; ++e) s_part[cg][ch * 8 + e] = acc[e];
+    for (int e = 0; e < 8; ++e) s_part[cg][ch * 8 + e] = accd[e] + acc[e].value();
     __syncthreads();
     double v2 = 0.0;
     if (threadIdx.x < 64) {
@@ -283,6 +314,9 @@ __global__ void __launch_bounds__(kCscThreads)
         if (row < d) {
             v -= (double)b[row];
             r[row] = v;
+            const float h = (float)v;
+            rh[row] = h;
+            rl[row] = (float)(v - (double)h);
             v2 = v * v;
         }
     }
@@ -296,20 +330,25 @@ __global__ void __launch_bounds__(kCscThreads)
     }
 }
 
-template <typename T>
+// One warp per column: ∇F_j = A_jᵀ r from the stored entries, in float pairs
+// (r as FP32 pairs) per lane, lanes added in FP64.
 __global__ void __launch_bounds__(kCscThreads)
     k_csc_kkt_grad(const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
-                   const T* __restrict__ v, int64_t n, const double* __restrict__ r,
-                   const double* __restrict__ s, const double* __restrict__ x,
-                   double* __restrict__ g64, double* __restrict__ gpart) {
+                   const float* __restrict__ v, int64_t n, const float* __restrict__ rh,
+                   const float* __restrict__ rl, const double* __restrict__ s,
+                   const double* __restrict__ x, double* __restrict__ g64,
+                   double* __restrict__ gpart) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
     if (j >= n) return;
-    double acc = 0.0;
-    for (int64_t t = cp[j] + lane; t < cp[j + 1]; t += 32) acc = fma((double)v[t], r[ri[t]], acc);
-    acc = warp_sum(acc);
+    FPair acc;
+    for (int64_t t = cp[j] + lane; t < cp[j + 1]; t += 32) {
+        const int32_t row = ri[t];
+        acc.add(v[t], rh[row], rl[row]);
+    }
+    const double grad = warp_sum(acc.value());
     if (lane == 0) {
-        const double gj = acc / s[j];
+        const double gj = grad / s[j];
         const double yj = x[j] * s[j];
         g64[j] = gj;
         gpart[j] = (yj > 0.0 || gj < 0.0) ? gj * gj : 0.0;
@@ -322,13 +361,13 @@ cudaError_t launch_csc_kkt(const int64_t* cp, const int32_t* ri, const float* v,
                            int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, const double* x, const float* b,
-                           const double* s, double* r, double* fpart, double* g64, double* gpart,
-                           cudaStream_t st) {
+                           const double* s, double* r, float* rh, float* rl, double* fpart,
+                           double* g64, double* gpart, cudaStream_t st) {
     const int64_t T = ceil_div(n, 128), KB = ceil_div(d, 64);
     k_csc_kkt_ax<<<(unsigned)KB, kCscThreads, 0, st>>>(occ, W, wbase, toff, T, hi, mid, lo, x, n, b,
-                                                       d, r, fpart);
-    k_csc_kkt_grad<float><<<(unsigned)ceil_div(n, kCscWarps), kCscThreads, 0, st>>>(
-        cp, ri, v, n, r, s, x, g64, gpart);
+                                                       d, r, rh, rl, fpart);
+    k_csc_kkt_grad<<<(unsigned)ceil_div(n, kCscWarps), kCscThreads, 0, st>>>(cp, ri, v, n, rh, rl, s,
+                                                                            x, g64, gpart);
     return cudaGetLastError();
 }
 
