@@ -441,8 +441,8 @@ void aln_destroy(aln_ctx* c) {
     group_free(c);
     mlp_free(c);
     nmf_free(c);
-    void* bufs[] = {c->A_copy,   c->B_copy,    c->Q,        c->prep_pool,
-                    c->A_hi,     c->iter_pool, c->kkt_pool, c->csc_pool};
+    void* bufs[] = {c->A_copy, c->B_copy,    c->Q,        c->prep_pool, c->A_hi,
+                    c->iter_pool, c->kkt_pool, c->csc_pool, c->sp_part};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->den_host) cudaFreeHost(c->den_host);
@@ -623,8 +623,14 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     const size_t b_occ = sparse_gram ? round_up((size_t)T * W * 4, 256) : 0;
     const size_t b_cnt = sparse_gram ? round_up((size_t)(2 * T + 1) * 8, 256) : 0;
     const size_t b_fp = no_dense ? round_up((size_t)KB * 8, 256) : 0;
+    // work list of the block-sparse Gram: pair counts, items, tickets, totals
+    const int64_t P = T * (T + 1) / 2;
+    const size_t b_lp = sparse_gram ? round_up((size_t)P * 4, 256) : 0;
+    const size_t b_it = sparse_gram ? round_up((size_t)(P + c->num_sms + 1) * sizeof(SItem), 256) : 0;
+    const size_t b_tk = sparse_gram ? round_up((size_t)P * 4, 256) + 256 : 0;
     const size_t b_copy = dev_ptr ? 0 : b_cp + b_ri + b_v;
-    ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes, b_copy + 2 * b_occ + b_cnt + b_fp + 256));
+    ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes,
+                     b_copy + 2 * b_occ + b_cnt + b_fp + b_lp + b_it + b_tk + 256));
     uint8_t* cp8 = (uint8_t*)c->csc_pool;
     const int64_t* cp = col_ptr;
     const int32_t* ri = row_idx;
@@ -648,6 +654,10 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     int64_t* cnt = (int64_t*)(cp8 + 2 * b_occ);
     int64_t* toff = cnt + T;
     double* fpart = (double*)(cp8 + 2 * b_occ + b_cnt);
+    int32_t* Lp = (int32_t*)(cp8 + 2 * b_occ + b_cnt + b_fp);
+    SItem* items = (SItem*)(cp8 + 2 * b_occ + b_cnt + b_fp + b_lp);
+    unsigned int* ticket = (unsigned int*)(cp8 + 2 * b_occ + b_cnt + b_fp + b_lp + b_it);
+    int64_t* meta = (int64_t*)((uint8_t*)ticket + round_up((size_t)P * 4, 256));
 
     // dense column-major copy of A (16-byte columns) where a later step reads
     // it: the FP64 Gram, the many-right-hand-side solver, q for k > 4, or the
@@ -696,9 +706,17 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     if (sparse_gram) {
         // number the occupied boxes, size the pack, scatter the split terms
         ALN_TRY(launch_csc_number(occ, W, T, wbase, cnt, toff, c->stream));
+        ALN_TRY(launch_csc_worklist(occ, W, T, c->num_sms, Lp, items, meta, c->stream));
         ALN_TRY(cudaMemcpyAsync(pin, toff + T, 8, cudaMemcpyDeviceToHost, c->stream));
+        ALN_TRY(cudaMemcpyAsync(pin + 1, meta, 16, cudaMemcpyDeviceToHost, c->stream));
         ALN_TRY(cudaStreamSynchronize(c->stream));
-        const int64_t boxes = pin[0];
+        const int64_t boxes = pin[0], nitems = pin[1], nslots = pin[2];
+        // partial tiles of the pairs split over several CTAs (≤ 2·num_sms)
+        ALN_CHECK(ensure(&c->sp_part, &c->sp_part_bytes,
+                         (size_t)std::max<int64_t>(nslots, 1) * 128 * 128 * 4));
+        ALN_TRY(cudaMemsetAsync(ticket, 0, (size_t)P * 4, c->stream));
+        // tile pairs without a common block have no work item: Q starts at zero
+        ALN_TRY(cudaMemsetAsync(c->Q, 0, c->Q_bytes, c->stream));
         const size_t sb = round_up((size_t)std::max<int64_t>(boxes, 1) * 128 * 64 * 2, 1024);
         ALN_CHECK(ensure((void**)&c->A_hi, &c->split_bytes, 3 * sb));
         __nv_bfloat16* hi = c->A_hi;
@@ -707,9 +725,10 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
         ALN_TRY(cudaMemsetAsync(c->A_hi, 0, 3 * sb, c->stream));
         ALN_TRY(launch_csc_pack(cp, ri, vv, dtype, n, occ, W, wbase, toff, hi, mid, lo,
                                 c->stream));
-        ALN_TRY(launch_sgram_tc(c->opt.gram_split, occ, W, wbase, toff, hi, mid, lo, n, c->inv_s,
-                                (float*)c->Q, ldq, c->flags + 1, c->stream));
-        c->launches += 4;
+        ALN_TRY(launch_sgram_tc(c->opt.gram_split, items, nitems, occ, W, wbase, toff, hi, mid, lo,
+                                n, c->inv_s, (float*)c->Q, ldq, (float*)c->sp_part, ticket,
+                                c->flags + 1, c->stream));
+        c->launches += 6;
         if (no_dense) {  // the KKT pass reads these until the next prepare
             c->csc_cp = cp;
             c->csc_ri = ri;

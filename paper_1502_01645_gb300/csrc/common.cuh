@@ -232,6 +232,8 @@ struct aln_ctx {
     double* csc_fpart = nullptr;
     int csc_W = 0;
     size_t csc_box_bytes = 0;  // one split term's packed boxes in A_hi
+    void* sp_part = nullptr;   // split-K partial tiles of the block-sparse Gram
+    size_t sp_part_bytes = 0;
 
     // iteration workspace (element type follows the precision)
     void* qv = nullptr;       // q of the right-hand side being solved (iteration type)

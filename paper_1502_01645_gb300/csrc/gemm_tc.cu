@@ -166,11 +166,17 @@ __device__ __forceinline__ void gram_store(const float (&acc)[BM], int64_t row, 
 // One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
 // The loader is taken by value: a loader may keep a cursor over the K blocks
 // it copies (k_sgram_tc); load() is called for the blocks in order.
+//
+// Split K (part ≠ null): this CTA is chunk c of S of its tile pair; it writes
+// its unscaled partial tile to part + c·128² (part points at the pair's first
+// slot), and the pair's last chunk to arrive on *ticket adds the S partials
+// in slot order — a fixed order, whichever CTA is last — and stores the tile.
 template <int NS, class Loader>
 __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
                                            int64_t n0, int64_t n, const double* __restrict__ inv_s,
                                            float* __restrict__ Q, int64_t ldq,
-                                           int* timeout_flag) {
+                                           int* timeout_flag, float* part = nullptr, int S = 1,
+                                           int c = 0, unsigned int* ticket = nullptr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     using C = GramCfg<NS>;
@@ -182,6 +188,7 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
     __shared__ float s_cs[BM];
     __shared__ int s_abort;
+    __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -275,9 +282,42 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
     }
     tc_fence_after();
     __syncthreads();
-    if (!s_abort) {
+    if (!s_abort && part == nullptr) {
         if (warp >= 2)
             gram_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
+    } else if (!s_abort) {
+        const int row = 32 * (warp & 3) + lane;
+        if (warp >= 2) {
+            float4* dst = reinterpret_cast<float4*>(part + ((int64_t)c * BM + row) * BM);
+#pragma unroll
+            for (int t = 0; t < BM / 4; ++t)
+                __stcg(dst + t, make_float4(acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                                            acc[4 * t + 3]));
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (unsigned int)(S - 1);
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            if (warp >= 2) {
+#pragma unroll
+                for (int t = 0; t < BM; ++t) acc[t] = 0.0f;
+                for (int q = 0; q < S; ++q) {
+                    const float4* src =
+                        reinterpret_cast<const float4*>(part + ((int64_t)q * BM + row) * BM);
+#pragma unroll
+                    for (int t = 0; t < BM / 4; ++t) {
+                        const float4 v = __ldcg(src + t);
+                        acc[4 * t] += v.x;
+                        acc[4 * t + 1] += v.y;
+                        acc[4 * t + 2] += v.z;
+                        acc[4 * t + 3] += v.w;
+                    }
+                }
+                gram_store(acc, m0 + row, n0, diag, n, inv_s, s_cs, Q, ldq);
+            }
+        }
     } else if (threadIdx.x == 0) {
         atomicExch(timeout_flag, 1);
     }
@@ -378,12 +418,16 @@ __global__ void __launch_bounds__(G3_THREADS, 1) k_ggram_tc(GGramArgs a) {
 // of each column tile are packed in K order (pack_index layout) from box
 // toff[tile]; occupancy bit kb of word occ[tile·W + kb/32] marks K block kb,
 // and wbase[tile·W + w] counts the tile's boxes in the words before w.  A CTA
-// multiplies, for its tile pair (I, J ≤ I), only the K blocks occupied in
-// both tiles, in increasing K order; a pair with none stores zeros.
+// takes one work item (SItem): a chunk of the K blocks occupied in both tiles
+// of its pair (I, J ≤ I), in increasing K order; pairs with no common block
+// have no item (their tiles of Q are zeroed beforehand), and a pair with more
+// blocks than the chunk size is split over several CTAs (split K).
 // ---------------------------------------------------------------------------
 struct SGramArgs {
     int64_t n;
-    int64_t t0;
+    const SItem* items;
+    float* part;
+    unsigned int* ticket;
     int W;
     const uint32_t* occ;
     const int32_t* wbase;
@@ -408,9 +452,28 @@ struct SparseLoader {
     const int32_t* wb;
     int64_t ta, tb;      // first box of tile I / J
     int W;
+    int skip;            // common blocks before this chunk (< 0: cursor placed)
     int w;               // cursor: current word, and its common bits not yet copied
     uint32_t m;
     __device__ __forceinline__ void load(uint8_t* sb, int, bool diag, uint64_t* bar) {
+        if (skip >= 0) {  // first call: move past the chunk's first `skip` common blocks
+            int k = skip;
+            skip = -1;
+            w = 0;
+            m = oa[0] & ob[0];
+            for (;;) {
+                const int pc = __popc(m);
+                if (k < pc) break;
+                k -= pc;
+                if (w + 1 >= W) {
+                    m = 0u;
+                    break;
+                }
+                ++w;
+                m = oa[w] & ob[w];
+            }
+            for (; k > 0 && m != 0u; --k) m &= m - 1u;
+        }
         while (m == 0u && w + 1 < W) {
             ++w;
             m = oa[w] & ob[w];
@@ -435,22 +498,16 @@ struct SparseLoader {
 
 template <int NS>
 __global__ void __launch_bounds__(G3_THREADS, 1) k_sgram_tc(SGramArgs a) {
-    __shared__ int s_nkb;
-    int tm, tn;
-    tri_decode(blockIdx.x + a.t0, tm, tn);
+    const SItem it = a.items[blockIdx.x];
+    const int tm = it.I, tn = it.J;
     const uint32_t* oa = a.occ + (int64_t)tm * a.W;
     const uint32_t* ob = a.occ + (int64_t)tn * a.W;
-    if (threadIdx.x < 32) {  // K blocks occupied in both tiles
-        int c = 0;
-        for (int w = threadIdx.x; w < a.W; w += 32) c += __popc(oa[w] & ob[w]);
-        c = warp_sum_i(c);
-        if (threadIdx.x == 0) s_nkb = c;
-    }
-    __syncthreads();
-    const SparseLoader<NS> ld{a.hi, a.mid, a.lo, oa, ob, a.wbase + (int64_t)tm * a.W,
-                              a.wbase + (int64_t)tn * a.W, a.toff[tm], a.toff[tn], a.W, -1, 0u};
-    gram_tile<NS>(ld, s_nkb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, a.n, a.inv_s, a.Q,
-                  a.ldq, a.timeout_flag);
+    const SparseLoader<NS> ld{a.hi,       a.mid, a.lo, oa, ob, a.wbase + (int64_t)tm * a.W,
+                              a.wbase + (int64_t)tn * a.W, a.toff[tm], a.toff[tn], a.W, it.k0,
+                              0,          0u};
+    float* part = it.S > 1 ? a.part + (int64_t)(it.slot - it.c) * BM * BM : nullptr;
+    gram_tile<NS>(ld, it.nk, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, a.n, a.inv_s, a.Q,
+                  a.ldq, a.timeout_flag, part, it.S, it.c, a.ticket + it.pair);
 }
 
 // ---------------------------------------------------------------------------
@@ -714,11 +771,14 @@ cudaError_t launch_ggram_tc(int nsplit, const GProb* gp, const GTile* tiles, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_t* wbase,
-                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+cudaError_t launch_sgram_tc(int nsplit, const SItem* items, int64_t nitems, const uint32_t* occ,
+                            int W, const int32_t* wbase, const int64_t* toff,
+                            const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                             const __nv_bfloat16* lo, int64_t n, const double* inv_s, float* Q,
-                            int64_t ldq, int* timeout_flag, cudaStream_t st) {
+                            int64_t ldq, float* part, unsigned int* ticket, int* timeout_flag,
+                            cudaStream_t st) {
     using namespace tc;
+    if (nitems <= 0) return cudaSuccess;
     if (nsplit != 2 && nsplit != 3) return cudaErrorInvalidValue;
     if (nsplit == 2) lo = mid;
     if (((uintptr_t)hi & 15) || ((uintptr_t)mid & 15) || ((uintptr_t)lo & 15) || W < 1)
@@ -733,7 +793,9 @@ cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_
     }
     SGramArgs a;
     a.n = n;
-    a.t0 = 0;
+    a.items = items;
+    a.part = part;
+    a.ticket = ticket;
     a.W = W;
     a.occ = occ;
     a.wbase = wbase;
@@ -745,8 +807,7 @@ cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_
     a.Q = Q;
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
-    const int64_t tiles = ceil_div(n, BM);
-    const unsigned grid = (unsigned)(tiles * (tiles + 1) / 2);
+    const unsigned grid = (unsigned)nitems;
     if (nsplit == 3)
         k_sgram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(a);
     else

@@ -48,12 +48,23 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0 = 0, int64_t row1 = -1);
 bool tc_supported(int cc_major, int cc_minor);
-// Block-sparse Gram over the occupied boxes packed by sparse.cu: for every
-// lower tile pair only the K blocks occupied in both column tiles.
-cudaError_t launch_sgram_tc(int nsplit, const uint32_t* occ, int W, const int32_t* wbase,
-                            const int64_t* toff, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+// One CTA of the block-sparse Gram: positions [k0, k0 + nk) of the K blocks
+// occupied in both column tiles I ≥ J (pair index `pair` in the lower-triangle
+// order), chunk c of the pair's S.  With S > 1 the chunk's unscaled partial
+// tile goes to slot `slot` and the pair's last chunk to finish adds slots
+// slot − c … slot − c + S − 1 in that order and stores the tile of Q.
+struct SItem {
+    int32_t I, J, k0, nk, S, c, slot, pair;
+};
+// Block-sparse Gram over the occupied boxes packed by sparse.cu, one CTA per
+// work item; tiles of Q without an item stay as they are (zeroed by the caller).
+// part: 128·128 floats per slot; ticket: one zeroed counter per pair.
+cudaError_t launch_sgram_tc(int nsplit, const SItem* items, int64_t nitems, const uint32_t* occ,
+                            int W, const int32_t* wbase, const int64_t* toff,
+                            const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                             const __nv_bfloat16* lo, int64_t n, const double* inv_s, float* Q,
-                            int64_t ldq, int* timeout_flag, cudaStream_t st);
+                            int64_t ldq, float* part, unsigned int* ticket, int* timeout_flag,
+                            cudaStream_t st);
 
 // W = Q·V (mode 0, with per-column curvature partials) or g += Q·V (mode 1)
 // over the compacted columns of a batch (batch.cu).
@@ -159,6 +170,12 @@ cudaError_t launch_csc_colstats(const int64_t* cp, const int32_t* ri, const void
                                 int64_t ldq, uint32_t* occ, int W, cudaStream_t st);
 cudaError_t launch_csc_number(const uint32_t* occ, int W, int64_t T, int32_t* wbase, int64_t* cnt,
                               int64_t* toff, cudaStream_t st);
+// Work list of the block-sparse Gram: Lp[p] = K blocks occupied in both tiles
+// of pair p; pairs with Lp > 0 split into chunks of ≤ KC = max(16, ⌈ΣLp /
+// num_sms⌉) blocks.  meta[0] = items written (≤ P + num_sms), meta[1] =
+// partial slots used (≤ 2·num_sms).
+cudaError_t launch_csc_worklist(const uint32_t* occ, int W, int64_t T, int num_sms, int32_t* Lp,
+                                SItem* items, int64_t* meta, cudaStream_t st);
 cudaError_t launch_csc_pack(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,
                             int64_t n, const uint32_t* occ, int W, const int32_t* wbase,
                             const int64_t* toff, __nv_bfloat16* hi, __nv_bfloat16* mid,

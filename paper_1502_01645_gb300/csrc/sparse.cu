@@ -197,6 +197,81 @@ __global__ void __launch_bounds__(kCscThreads)
 //   k_csc_kkt_grad one warp per column: ∇F_j = A_jᵀ r from the stored entries,
 //                  g_j = ∇F_j / s_j (kept for the refinement), ḡ_j² on P(s·x).
 // ---------------------------------------------------------------------------
+// Lower-triangle pair index t → (I, J), J ≤ I, t = I(I+1)/2 + J.
+__device__ __forceinline__ void tri_pair(int64_t t, int& I, int& J) {
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    I = (int)r;
+    J = (int)(t - r * (r + 1) / 2);
+}
+
+// One warp per tile pair: the K blocks occupied in both tiles.
+__global__ void __launch_bounds__(kCscThreads) k_csc_pairs(const uint32_t* __restrict__ occ, int W,
+                                                           int64_t P, int32_t* __restrict__ Lp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kCscWarps + (threadIdx.x >> 5);
+    if (p >= P) return;
+    int I, J;
+    tri_pair(p, I, J);
+    const uint32_t* oa = occ + (int64_t)I * W;
+    const uint32_t* ob = occ + (int64_t)J * W;
+    int c = 0;
+    for (int w = lane; w < W; w += 32) c += __popc(oa[w] & ob[w]);
+    c = warp_sum_i(c);
+    if (lane == 0) Lp[p] = c;
+}
+
+// One block: the chunk size KC from the total work, then every non-empty
+// pair's chunks (even split of its Lp blocks) and partial slots for the pairs
+// split in more than one chunk, in pair order.
+__global__ void __launch_bounds__(kCscThreads) k_csc_items(const int32_t* __restrict__ Lp, int64_t P,
+                                                           int num_sms, SItem* __restrict__ items,
+                                                           int64_t* __restrict__ meta) {
+    __shared__ int64_t s_w[kCscWarps];
+    int64_t tot = 0;
+    for (int64_t p0 = 0; p0 < P; p0 += kCscThreads) {
+        const int64_t p = p0 + threadIdx.x;
+        int64_t t;
+        block_scan_excl(p < P ? Lp[p] : 0, s_w, &t);
+        tot += t;
+    }
+    const int64_t kc0 = (tot + num_sms - 1) / num_sms;
+    const int64_t KC = kc0 > 16 ? kc0 : 16;
+    int64_t run_i = 0, run_s = 0;
+    for (int64_t p0 = 0; p0 < P; p0 += kCscThreads) {
+        const int64_t p = p0 + threadIdx.x;
+        const int64_t L = p < P ? Lp[p] : 0;
+        const int64_t S = L > 0 ? (L + KC - 1) / KC : 0;
+        int64_t ti, ts;
+        const int64_t ei = block_scan_excl(S, s_w, &ti);
+        const int64_t es = block_scan_excl(S > 1 ? S : 0, s_w, &ts);
+        if (S > 0) {
+            int I, J;
+            tri_pair(p, I, J);
+            for (int64_t c = 0; c < S; ++c) {
+                const int64_t k0 = c * L / S, k1 = (c + 1) * L / S;
+                SItem it;
+                it.I = I;
+                it.J = J;
+                it.k0 = (int32_t)k0;
+                it.nk = (int32_t)(k1 - k0);
+                it.S = (int32_t)S;
+                it.c = (int32_t)c;
+                it.slot = S > 1 ? (int32_t)(run_s + es + c) : -1;
+                it.pair = (int32_t)p;
+                items[run_i + ei + c] = it;
+            }
+        }
+        run_i += ti;
+        run_s += ts;
+    }
+    if (threadIdx.x == 0) {
+        meta[0] = run_i;
+        meta[1] = run_s;
+    }
+}
+
 // Float-pair accumulator on the FP32 pipe (this GPU's FP64 pipe is narrow):
 // += a·(h + l) with the product's rounding error from an FMA (TwoProduct) and
 // the addition's from TwoSum kept in c (Ogita, Rump & Oishi 2005).
@@ -409,6 +484,14 @@ cudaError_t launch_csc_number(const uint32_t* occ, int W, int64_t T, int32_t* wb
                               int64_t* toff, cudaStream_t st) {
     k_csc_tiles<<<(unsigned)T, kCscThreads, 0, st>>>(occ, W, wbase, cnt);
     k_csc_offsets<<<1, kCscThreads, 0, st>>>(cnt, T, toff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_worklist(const uint32_t* occ, int W, int64_t T, int num_sms, int32_t* Lp,
+                                SItem* items, int64_t* meta, cudaStream_t st) {
+    const int64_t P = T * (T + 1) / 2;
+    k_csc_pairs<<<(unsigned)ceil_div(P, kCscWarps), kCscThreads, 0, st>>>(occ, W, P, Lp);
+    k_csc_items<<<1, kCscThreads, 0, st>>>(Lp, P, num_sms, items, meta);
     return cudaGetLastError();
 }
 
