@@ -30,6 +30,9 @@ struct GramArgs {
     int64_t n;
     int64_t t0;  // first lower-triangle tile of this launch (a range of tile rows)
     int num_kb;
+    int S;                 // chunks of the K range per tile pair (split K; 1 = none)
+    float* part;           // S partial tiles per pair (S > 1)
+    unsigned int* ticket;  // one counter per pair of the launch (S > 1)
     const double* inv_s;
     float* Q;
     int64_t ldq;
@@ -317,6 +320,7 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
                 }
                 gram_store(acc, m0 + row, n0, diag, n, inv_s, s_cs, Q, ldq);
             }
+            if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
         }
     } else if (threadIdx.x == 0) {
         atomicExch(timeout_flag, 1);
@@ -332,14 +336,16 @@ struct TmaLoader {
     const CUtensorMap* mm;
     const CUtensorMap* ml;
     int m0, n0;
+    int k0;  // first K block of this CTA's chunk
     __device__ __forceinline__ void load(uint8_t* sb, int kb, bool diag, uint64_t* bar) const {
-        tma_load_2d(sb, mh, bar, kb * BK, m0);
-        tma_load_2d(sb + TILE_BYTES, mm, bar, kb * BK, m0);
-        if (NS == 3) tma_load_2d(sb + 2 * TILE_BYTES, ml, bar, kb * BK, m0);
+        const int x = (kb + k0) * BK;
+        tma_load_2d(sb, mh, bar, x, m0);
+        tma_load_2d(sb + TILE_BYTES, mm, bar, x, m0);
+        if (NS == 3) tma_load_2d(sb + 2 * TILE_BYTES, ml, bar, x, m0);
         if (!diag) {
-            tma_load_2d(sb + NS * TILE_BYTES, mh, bar, kb * BK, n0);
-            tma_load_2d(sb + (NS + 1) * TILE_BYTES, mm, bar, kb * BK, n0);
-            if (NS == 3) tma_load_2d(sb + 5 * TILE_BYTES, ml, bar, kb * BK, n0);
+            tma_load_2d(sb + NS * TILE_BYTES, mh, bar, x, n0);
+            tma_load_2d(sb + (NS + 1) * TILE_BYTES, mm, bar, x, n0);
+            if (NS == 3) tma_load_2d(sb + 5 * TILE_BYTES, ml, bar, x, n0);
         }
     }
 };
@@ -348,11 +354,17 @@ template <int NS>
 __global__ void __launch_bounds__(G3_THREADS, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
               const __grid_constant__ CUtensorMap m_lo, GramArgs p) {
+    // CTA = (tile pair, chunk c of S): K blocks [c·num_kb/S, (c+1)·num_kb/S)
+    const int64_t pi = blockIdx.x / p.S;
+    const int c = (int)(blockIdx.x - pi * p.S);
     int tm, tn;
-    tri_decode(blockIdx.x + p.t0, tm, tn);
-    const TmaLoader<NS> ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM};
-    gram_tile<NS>(ld, p.num_kb, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
-                  p.ldq, p.timeout_flag);
+    tri_decode(pi + p.t0, tm, tn);
+    const int k0 = (int)((int64_t)c * p.num_kb / p.S);
+    const int k1 = (int)((int64_t)(c + 1) * p.num_kb / p.S);
+    const TmaLoader<NS> ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM, k0};
+    float* part = p.S > 1 ? p.part + pi * p.S * (int64_t)(BM * BM) : nullptr;
+    gram_tile<NS>(ld, k1 - k0, tm == tn, (int64_t)tm * BM, (int64_t)tn * BM, p.n, p.inv_s, p.Q,
+                  p.ldq, p.timeout_flag, part, p.S, c, p.ticket + pi);
 }
 
 // ---------------------------------------------------------------------------
@@ -694,7 +706,8 @@ bool tc_supported(int cc_major, int cc_minor) { return cc_major == 10 && cc_mino
 cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
-                           cudaStream_t st, int64_t row0, int64_t row1) {
+                           cudaStream_t st, int64_t row0, int64_t row1, float* part,
+                           unsigned int* ticket, int num_sms) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
@@ -728,7 +741,11 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     // tiles (I, J ≤ I) with row0 ≤ I < row1 are the contiguous range
     // [row0(row0+1)/2, row1(row1+1)/2) of the triangle order
     a.t0 = row0 * (row0 + 1) / 2;
-    const unsigned grid = (unsigned)(row1 * (row1 + 1) / 2 - a.t0);
+    const int64_t pairs = row1 * (row1 + 1) / 2 - a.t0;
+    a.S = (part && ticket && num_sms > 0) ? gram_split_k(pairs, a.num_kb, num_sms) : 1;
+    a.part = part;
+    a.ticket = ticket;
+    const unsigned grid = (unsigned)(pairs * a.S);
     if (nsplit == 3)
         k_gram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
     else

@@ -75,6 +75,39 @@ def test_split_bf16_gram_matches_oracle(aln, d, n):
     np.testing.assert_array_equal(np.diag(Q), 1.0)
 
 
+@pytest.mark.parametrize("device_a", [False, True])
+def test_split_bf16_gram_tall_narrow_split_k(aln, device_a):
+    """d = 20000, n = 300: 6 tile pairs for ~150 SMs, so each pair's 313 K
+    blocks run as 19 chunks on separate CTAs whose partial tiles the pair's
+    last CTA adds in a fixed order.  Host A takes the chunked-copy prepare,
+    device A the single launch; Q within the split-Gram bound of the oracle's,
+    the same bits on a second prepare, and a solve to FP64 KKT 1e-9."""
+    import torch
+    r = np.random.default_rng(31)
+    d, n = 20000, 300
+    A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
+    A = np.asfortranarray(A64.astype(np.float32))
+    xt = np.where(r.random(n) < 0.5, 0.0, r.random(n))
+    b = (A.astype(np.float64) @ xt + 0.01 * r.standard_normal(d)).astype(np.float32)
+    A_in, b_in = A, b
+    if device_a:
+        A_in = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+        b_in = torch.from_numpy(b).cuda()
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A_in, b_in)
+        Q, q, sc = s.export()
+        X, info = s.solve(tol=1e-9)
+        s.prepare(A_in, b_in)
+        Q2, _, _ = s.export()
+    np.testing.assert_array_equal(Q2, Q)
+    np.testing.assert_array_equal(Q, Q.T)
+    Qo, qo, so = _oracle_scaled(A, b)
+    assert np.abs(Q - Qo).max() <= _split_bound(d)
+    np.testing.assert_allclose(q[0], qo, atol=1e-12 * np.abs(qo).max())
+    rel, _ = O.kkt_residual(A.astype(np.float64), b.astype(np.float64), X[0])
+    assert rel <= 1e-9, rel
+
+
 def test_split_gram_zero_column(aln):
     r = np.random.default_rng(5)
     A = np.asfortranarray(r.random((200, 150)).astype(np.float32))

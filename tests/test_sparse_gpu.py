@@ -71,36 +71,30 @@ def test_csc_scaled_problem_matches_oracle(aln, d, n, band, density):
     np.testing.assert_array_equal(Q[Qo == 0.0], 0.0)
 
 
-# (d, n, band, density, split): with split, some tile pairs have more common
-# blocks than the chunk size max(16, ⌈total/SMs⌉) and run as several CTAs
-# whose partial tiles are added at the end (split K)
-DENSE_CMP = [(3000, 700, 400, 0.2, False), (5000, 300, 200, 0.5, True),
-             (20000, 256, 20000, 0.05, True)]
+# (d, n, band, density): tile pairs whose common blocks exceed the chunk size
+# run as several CTAs whose partial tiles are added at the end (split K); the
+# dense Gram splits K too when it has fewer tile pairs than SMs
+DENSE_CMP = [(3000, 700, 400, 0.2), (5000, 300, 200, 0.5), (20000, 256, 20000, 0.05)]
 
 
-@pytest.mark.parametrize("d,n,band,density,split", DENSE_CMP)
-def test_csc_gram_equals_dense_gram(aln, d, n, band, density, split):
-    """Without split K the CSC Gram adds the same block products in the same
-    order as the dense one (the skipped blocks add exact zeros).  With split
-    K each chunk sums its blocks in FP32 and the chunks are added in order:
-    two FP32 summations of at most ⌈d/64⌉ block terms whose scaled magnitudes
-    add up to at most 1 (Cauchy–Schwarz), so |ΔQ| ≤ 2·⌈d/64⌉·2⁻²⁴, plus one
-    FP32 rounding of each scale factor."""
+@pytest.mark.parametrize("d,n,band,density", DENSE_CMP)
+def test_csc_gram_equals_dense_gram(aln, d, n, band, density):
+    """Both Grams add the same block products (a skipped block adds exact
+    zeros); they differ only in how the FP32 sums are grouped (each chunk
+    sums its blocks, the chunks are added in order).  Each is an FP32
+    summation of at most ⌈d/64⌉ block terms whose scaled magnitudes add up to
+    at most 1 (Cauchy–Schwarz), so |ΔQ| ≤ 2·⌈d/64⌉·2⁻²⁴, plus one FP32
+    rounding of each scale factor."""
     p = W.banded_tall(d=d, n=n, band=band, density=density, seed=7 * d + n)
     Qc, qc, sc = _export_csc(aln, p)
     Qd, qd, sd = _export_dense(aln, p.dense(), p.B)
     np.testing.assert_allclose(sc, sd, rtol=1e-14)
     np.testing.assert_allclose(qc, qd, rtol=1e-13, atol=1e-300)
     np.testing.assert_array_equal(Qc, Qc.T)
-    if not split:
-        diff = Qc != Qd
-        assert diff.mean() <= 1e-3, diff.mean()
-        np.testing.assert_allclose(Qc, Qd, rtol=2.0 ** -22, atol=0.0)
-    else:
-        bound = (2 * -(-d // 64) + 2) * 2.0 ** -24
-        assert np.abs(Qc - Qd).max() <= bound, np.abs(Qc - Qd).max()
-        Qo, _, _ = _oracle(p)
-        assert np.abs(Qc - Qo).max() <= _split_bound(d)
+    bound = (2 * -(-d // 64) + 2) * 2.0 ** -24
+    assert np.abs(Qc - Qd).max() <= bound, np.abs(Qc - Qd).max()
+    Qo, _, _ = _oracle(p)
+    assert np.abs(Qc - Qo).max() <= _split_bound(d)
     # deterministic: a second prepare gives the same bits
     Qc2, _, _ = _export_csc(aln, p)
     np.testing.assert_array_equal(Qc2, Qc)
