@@ -502,36 +502,24 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
         c->A_lo = lo;
     }
 
-    // split-K buffers of the tensor-core Gram: a launch with fewer tile pairs
-    // than SMs (tall, narrow A) spreads each pair's K range over several CTAs
+    // split K in the tensor-core Gram: with fewer tile pairs than SMs (tall,
+    // narrow A) each pair's K range runs over several CTAs.  The split is fixed
+    // by the whole matrix, so host input (launched chunk by chunk below) and
+    // device input (one launch) give the same Q
     const int64_t chunk_cols = std::max<int64_t>(1024, round_up(ceil_div(n, 63), 128));
     float* gpart = nullptr;
     unsigned int* gticket = nullptr;
+    int gsplit = 1;
     if (!f64 && !c->batched) {
-        const int64_t tiles = ceil_div(n, 128), nkb = ceil_div(c->ldk, 64);
-        int64_t maxp = 0, maxps = 0;
-        auto need = [&](int64_t r0, int64_t r1) {
-            const int64_t P = r1 * (r1 + 1) / 2 - r0 * (r0 + 1) / 2;
-            const int S = gram_split_k(P, nkb, c->num_sms);
-            if (S > 1) {
-                maxp = std::max(maxp, P);
-                maxps = std::max(maxps, P * S);
-            }
-        };
-        if (pipelined) {
-            for (int64_t c0 = 0; c0 < n; c0 += chunk_cols) {
-                const int64_t c1 = std::min(n, c0 + chunk_cols);
-                need(c0 / 128, c1 == n ? tiles : c1 / 128);
-            }
-        } else {
-            need(0, tiles);
-        }
-        if (maxps > 0) {
-            const size_t pb = (size_t)maxps * 128 * 128 * 4;
-            ALN_CHECK(ensure(&c->sp_part, &c->sp_part_bytes, pb + round_up((size_t)maxp * 4, 256)));
+        const int64_t tiles = ceil_div(n, 128);
+        const int64_t pairs = tiles * (tiles + 1) / 2;
+        gsplit = gram_split_k(pairs, ceil_div(c->ldk, 64), c->num_sms);
+        if (gsplit > 1) {  // a chunked launch covers at most all pairs
+            const size_t pb = (size_t)pairs * gsplit * 128 * 128 * 4;
+            ALN_CHECK(ensure(&c->sp_part, &c->sp_part_bytes, pb + round_up((size_t)pairs * 4, 256)));
             gpart = (float*)c->sp_part;
             gticket = (unsigned int*)((uint8_t*)c->sp_part + pb);
-            ALN_TRY(cudaMemsetAsync(gticket, 0, (size_t)maxp * 4, c->stream));
+            ALN_TRY(cudaMemsetAsync(gticket, 0, (size_t)pairs * 4, c->stream));
         }
     }
 
@@ -568,7 +556,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
             if (c0 == 0) ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
             ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
                                    (float*)c->Q, ldq, c->flags + 1, c->stream, c0 / 128,
-                                   c1 == n ? tiles : c1 / 128, gpart, gticket, c->num_sms));
+                                   c1 == n ? tiles : c1 / 128, gpart, gticket, gsplit));
             c->launches += 2;
         }
     } else {
@@ -594,7 +582,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     else
         ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
                                (float*)c->Q, ldq, c->flags + 1, c->stream, 0, -1, gpart, gticket,
-                               c->num_sms));
+                               gsplit));
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     c->launches += 4 + (kc == 0 ? 1 : 0);
 

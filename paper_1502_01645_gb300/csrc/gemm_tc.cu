@@ -707,7 +707,7 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0, int64_t row1, float* part,
-                           unsigned int* ticket, int num_sms) {
+                           unsigned int* ticket, int split) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
@@ -742,7 +742,7 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     // [row0(row0+1)/2, row1(row1+1)/2) of the triangle order
     a.t0 = row0 * (row0 + 1) / 2;
     const int64_t pairs = row1 * (row1 + 1) / 2 - a.t0;
-    a.S = (part && ticket && num_sms > 0) ? gram_split_k(pairs, a.num_kb, num_sms) : 1;
+    a.S = (part && ticket && split > 1) ? split : 1;
     a.part = part;
     a.ticket = ticket;
     const unsigned grid = (unsigned)(pairs * a.S);

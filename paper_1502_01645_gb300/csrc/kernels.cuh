@@ -43,19 +43,20 @@ cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, in
 // Q_ij = (Σ_t hh + hm + mh + mm + hl + lh)_ij · inv_s_i · inv_s_j for the exact
 // three-term split a = h + m + l (nsplit = 3), or hh + hm + mh for the two-term
 // split a ≈ h + m (nsplit = 2); lower tiles mirrored.
-// Tile rows [row0, row1) of Q (all by default).  With part, ticket and
-// num_sms given, a launch of fewer tile pairs than SMs (tall, narrow A) splits
-// each pair's K range over gram_split_k chunks: part then needs
-// pairs·S·128² floats and ticket one zeroed counter per pair (left zeroed).
+// Tile rows [row0, row1) of Q (all by default).  With split > 1 (and part,
+// ticket given) each tile pair's K range runs as `split` chunks on separate
+// CTAs: part then needs pairs·split·128² floats and ticket one zeroed counter
+// per pair of the launch (left zeroed).  The chunking, and so the rounding of
+// every entry, depends only on `split`: launches over different row ranges
+// with the same split give the same Q as one launch over all rows.
 cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0 = 0, int64_t row1 = -1,
-                           float* part = nullptr, unsigned int* ticket = nullptr,
-                           int num_sms = 0);
-// Chunks per tile pair for a Gram launch of `pairs` pairs over num_kb K
-// blocks: enough CTAs to cover the SMs when the pairs alone do not, with at
-// least 16 K blocks per chunk.
+                           float* part = nullptr, unsigned int* ticket = nullptr, int split = 1);
+// Chunks per tile pair for the Gram of a matrix with `pairs` tile pairs over
+// num_kb K blocks: enough CTAs to cover the SMs when the pairs alone do not
+// (tall, narrow A), with at least 16 K blocks per chunk.
 inline int gram_split_k(int64_t pairs, int64_t num_kb, int num_sms) {
     if (pairs <= 0 || pairs >= num_sms) return 1;
     const int64_t s = std::min<int64_t>(num_sms / pairs, num_kb / 16);

@@ -108,6 +108,34 @@ def test_split_bf16_gram_tall_narrow_split_k(aln, device_a):
     assert rel <= 1e-9, rel
 
 
+@pytest.mark.parametrize("d,n", [(3000, 2300), (20000, 300), (40000, 1300)])
+def test_host_and_device_input_give_the_same_result(aln, d, n):
+    """Host A is copied in column chunks and each chunk's Gram tile rows run
+    as it lands; device A takes one launch.  The tiles' K chunking (split K
+    for tall, narrow A) is fixed by the whole matrix, so both give the same
+    Q bits, the same iterations and the same solution: 3 chunk launches
+    without split K, 1 with, and 2 with."""
+    import torch
+    r = np.random.default_rng(d + n)
+    A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
+    A = np.asfortranarray(A64.astype(np.float32))
+    xt = np.where(r.random(n) < 0.6, 0.0, r.random(n))
+    b = (A.astype(np.float64) @ xt + 0.01 * r.standard_normal(d)).astype(np.float32)
+    out = []
+    for dev in (False, True):
+        A_in = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t() if dev else A
+        b_in = torch.from_numpy(b).cuda() if dev else b
+        with aln.Solver("split_bf16") as s:
+            s.prepare(A_in, b_in)
+            Q, q, sc = s.export()
+            X, info = s.solve(tol=1e-7)
+        out.append((Q, q, X, info[0].iters))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][3] == out[1][3]
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+
+
 def test_split_gram_zero_column(aln):
     r = np.random.default_rng(5)
     A = np.asfortranarray(r.random((200, 150)).astype(np.float32))
