@@ -60,6 +60,40 @@ def _pin_entries():
     np.testing.assert_allclose(s, sd, rtol=1e-14)
 
 
+def _pin_kkt_csc():
+    # the CSC residual against the dense oracle's on the expanded matrix, at
+    # random points, the origin and the optimum, with an empty column
+    M, cp, ri, v = _random_csc(21, 60, 25, 0.3)
+    M[:, 7] = 0.0
+    cp, ri, v = _csc_of(M)
+    g = np.random.default_rng(22)
+    b = M @ np.abs(g.standard_normal(25)) + 0.1 * g.standard_normal(60)
+    x_star, _, _, _ = O.reference_solution(M, b)
+    for x in (np.zeros(25), np.abs(g.standard_normal(25)) * (g.random(25) < 0.5), x_star):
+        rel, F = S.kkt_residual_csc(60, 25, cp, ri, v, b, x)
+        rel_d, F_d = O.kkt_residual(M, b, x)
+        assert rel == pytest.approx(rel_d, rel=1e-10, abs=1e-14)
+        assert F == pytest.approx(F_d, rel=1e-12)
+    assert S.kkt_residual_csc(60, 25, cp, ri, v, b, np.zeros(25))[0] == pytest.approx(1.0)
+    assert S.kkt_residual_csc(60, 25, cp, ri, v, b, x_star)[0] <= 1e-10
+
+
+def _csc_of(M):
+    n = M.shape[1]
+    cp = np.zeros(n + 1, np.int64)
+    rows, vals = [], []
+    for j in range(n):
+        nz = np.flatnonzero(M[:, j])
+        rows.extend(nz.tolist())
+        vals.extend(M[nz, j].tolist())
+        cp[j + 1] = len(rows)
+    return cp, np.array(rows, np.int32), np.array(vals, np.float64)
+
+
+def test_kkt_residual_from_csc_matches_dense():
+    _pin_kkt_csc()
+
+
 def test_hand_matrix():
     _pin_hand()
 
@@ -99,6 +133,7 @@ def _pins_pass():
         _pin_hand()
         _pin_scipy()
         _pin_entries()
+        _pin_kkt_csc()
     except (AssertionError, ValueError, IndexError):
         return False
     return True
@@ -132,4 +167,16 @@ def test_planted_mistakes_are_caught(monkeypatch):
                         (good_g(cp, ri, v, i, i) if i != j else 0.0))
     assert not _pins_pass(), "Gram entry with an extra term"
     monkeypatch.setattr(S, "gram_entry", good_g)
+    good_k = S.kkt_residual_csc
+
+    def no_mask(d, n, cp, ri, v, b, x):  # ḡ without the passive-set mask
+        saved = O.passive_mask
+        O.passive_mask = lambda y, g: np.ones_like(g, dtype=bool)
+        try:
+            return good_k(d, n, cp, ri, v, b, x)
+        finally:
+            O.passive_mask = saved
+    monkeypatch.setattr(S, "kkt_residual_csc", no_mask)
+    assert not _pins_pass(), "KKT residual without the passive-set mask"
+    monkeypatch.setattr(S, "kkt_residual_csc", good_k)
     assert _pins_pass()

@@ -260,6 +260,50 @@ def test_csc_full_size_sampled(aln):
         qo = -S.atb_entry(p.col_ptr, p.row_idx, p.vals, b, int(j)) / np.sqrt(h_jj)
         assert abs(q[0, j] - qo) <= 1e-12 * max(1.0, abs(qo))
     assert np.all(X[0] >= 0.0)
+    rel, F = S.kkt_residual_csc(p.d, p.n, p.col_ptr, p.row_idx, p.vals, b, X[0])
+    assert rel <= p.tol, rel
+    assert rel == pytest.approx(info[0].rel_kkt, rel=1e-6)
+    assert F == pytest.approx(info[0].objective, rel=1e-10)
+
+
+def test_csc_extreme_tall(aln):
+    """20 000 000 × 300 with 40 entries per column (8·10⁹ elements dense,
+    12 000 stored): row indices beyond 2²⁴ and 312 500 K blocks.  The columns
+    draw their rows from a pool of 2000 rows spread over the whole range, so
+    they overlap and every tile pair has ~2000 common blocks (split K over
+    ~25 CTAs per pair).  Sampled Q and q entries against the oracle's
+    single-entry products; the solution's KKT residual and objective by the
+    oracle, evaluated from the CSC arrays."""
+    d, n, per = 20_000_000, 300, 40
+    g = np.random.default_rng(41)
+    pool = np.sort(g.choice(d, 2000, replace=False))
+    cp = np.arange(n + 1, dtype=np.int64) * per
+    ri = np.concatenate([np.sort(g.choice(pool, per, replace=False)) for _ in range(n)])
+    ri = ri.astype(np.int32)
+    v = (1.0 - g.random(n * per)).astype(np.float32)
+    cols = np.repeat(np.arange(n), per)
+    x_true = np.where(g.random(n) < 0.5, 0.0, g.random(n))
+    b = np.bincount(ri, weights=v.astype(np.float64) * x_true[cols], minlength=d)
+    b[pool] += 0.01 * g.standard_normal(pool.size)
+    b = b.astype(np.float32)
+    tol = 1e-8
+    with aln.Solver("split_bf16") as s:
+        s.prepare_csc(d, cp, ri, v, b)
+        Q, q, sc = s.export()
+        X, info = s.solve(tol=tol)
+    assert info[0].rel_kkt <= tol
+    for i, j in [(0, 0), (0, 1), (5, 299), (150, 151), (299, 299)] + \
+            [(int(a), int(c)) for a, c in g.integers(0, n, (40, 2))]:
+        h_ii = S.gram_entry(cp, ri, v, i, i)
+        h_jj = S.gram_entry(cp, ri, v, j, j)
+        qo = 1.0 if i == j else S.gram_entry(cp, ri, v, i, j) / np.sqrt(h_ii * h_jj)
+        assert abs(Q[i, j] - qo) <= 2.0 ** -22 + 3 * 2000 * 2.0 ** -24, (i, j, Q[i, j], qo)
+    for j in (0, 77, 299):
+        qo = -S.atb_entry(cp, ri, v, b, j) / np.sqrt(S.gram_entry(cp, ri, v, j, j))
+        assert abs(q[0, j] - qo) <= 1e-12 * max(1.0, abs(qo))
+    rel, F = S.kkt_residual_csc(d, n, cp, ri, v, b, X[0])
+    assert rel <= tol, rel
+    assert F == pytest.approx(info[0].objective, rel=1e-10)
 
 
 @pytest.mark.parametrize("d,n,band,density", [(3000, 700, 400, 0.2), (130, 129, 40, 0.5)])
