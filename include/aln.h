@@ -188,9 +188,10 @@ aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_
  * vals may be NULL when nnz = 0.  Only the stored entries are read: the column
  * statistics and Aᵀb come from them, and with SPLIT_BF16 and a single-RHS
  * solver the Gram multiplies, per pair of 128-column tiles, only the 64-row
- * blocks stored in both — the same Q as from the dense matrix, for work
- * proportional to the occupied block pairs.  With F32 values, SPLIT_BF16, a
- * single-RHS solver and k ≤ 4, no dense copy of A is made: the FP64 KKT pass
+ * blocks stored in both — the Q of the dense matrix up to the grouping of its
+ * FP32 sums, for work proportional to the occupied block pairs.  With F32
+ * values, SPLIT_BF16, a single-RHS solver and k ≤ 4, no dense copy of A is
+ * made: the FP64 KKT pass
  * reads the CSC arrays and the packed blocks (whose split terms add up exactly
  * to the entries), so device CSC arrays are kept by pointer and must stay
  * valid until the next prepare or aln_destroy.  Otherwise (F64 values, FP64

@@ -15,7 +15,9 @@
 //                   Gram copies verbatim (pack_index).
 // The Gram (launch_sgram_tc, gemm_tc.cu) multiplies, for each tile pair, only
 // the K blocks occupied in both column tiles: a block that is zero in either
-// operand adds exactly zero to H = AᵀA, so Q is the same as from the dense A.
+// operand adds exactly zero to H = AᵀA, so Q is that of the dense A up to how
+// its FP32 sums are grouped (pairs with many common blocks are split over
+// several CTAs, from a work list built by k_csc_pairs / k_csc_items).
 #include "common.cuh"
 #include "kernels.cuh"
 
