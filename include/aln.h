@@ -191,10 +191,9 @@ aln_status aln_prepare(aln_ctx* ctx, const void* A, int64_t d, int64_t n, int64_
  * blocks stored in both — the Q of the dense matrix up to the grouping of its
  * FP32 sums, for work proportional to the occupied block pairs.  With F32
  * values, SPLIT_BF16, a single-RHS solver and k ≤ 4, no dense copy of A is
- * made: the FP64 KKT pass
- * reads the CSC arrays and the packed blocks (whose split terms add up exactly
- * to the entries), so device CSC arrays are kept by pointer and must stay
- * valid until the next prepare or aln_destroy.  Otherwise (F64 values, FP64
+ * made: the FP64 KKT pass reads the CSC arrays and the packed blocks (whose
+ * split terms add up exactly to the entries), so device CSC arrays are kept
+ * by pointer and must stay valid until the next prepare or aln_destroy.  Otherwise (F64 values, FP64
  * precision, the many-right-hand-side solver, k > 4) a dense column-major copy
  * of A (d·n elements) is made on the device.  The call synchronises the
  * stream twice (structure check; sizing of the packed blocks).  Afterwards
