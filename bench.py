@@ -511,12 +511,20 @@ def run_ours(args):
         if alg == aln.ALG_ANTILOP and w["prec"] == "split_bf16":
             ldq = (n + 127) // 128 * 128
             traffic = 1.002 * n * ldq * 4
+        note = ("the rows of Q read stay in the 129 MB L2 between iterations, so frac can "
+                "exceed 1")
+        iters_avg = avg(lambda s: s.iterations)
+        us_it = it_ms * 1e3 / iters_avg if iters_avg > 0 else None
+        if esz * n * n < 4e6:
+            note = (f"latency-bound, not bandwidth-bound: Q ({esz * n * n / 1e3:.0f} KB) stays "
+                    f"on chip and an iteration ({us_it:.1f} us) is five dependent phases "
+                    "separated by grid-wide reductions, so this fraction is not a meaningful "
+                    "efficiency; see us_per_iteration")
         rooflines.append({"bound": "hbm", "kernel": kname,
                           "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                           "traffic": traffic, "peak_kind": f"{pk_kind} hbm copy",
                           "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
-                          "note": "the rows of Q read stay in the 129 MB L2 between "
-                                  "iterations, so frac can exceed 1"})
+                          "us_per_iteration": us_it, "note": note})
     else:
         # tensor FLOPs of the batched products: 3 split products of 2·n² per
         # running column (W = Qḡ) and per clipped column (U = Qe)
