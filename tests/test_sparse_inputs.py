@@ -39,3 +39,18 @@ def test_dense_and_csc_round_trip():
     np.testing.assert_array_equal(cp, p.col_ptr)
     np.testing.assert_array_equal(ri, p.row_idx)
     np.testing.assert_array_equal(v, p.vals)
+
+
+def test_bench_block_pair_count_matches_brute_force():
+    """The block-sparse Gram's algorithmic work in bench.py: occupied
+    (64-row block, tile pair) combinations, counted by brute force."""
+    import bench
+    p = W.banded_tall(d=3000, n=300, band=500, density=0.05, seed=12)
+    off, diag = bench.sgram_block_products(p)
+    cols = np.repeat(np.arange(p.n), np.diff(p.col_ptr))
+    T = (p.n + 127) // 128
+    occ = [set() for _ in range(T)]
+    for r, c in zip(p.row_idx.tolist(), cols.tolist()):
+        occ[c // 128].add(r // 64)
+    assert diag == sum(len(o) for o in occ)
+    assert off == sum(len(occ[i] & occ[j]) for i in range(T) for j in range(i))
