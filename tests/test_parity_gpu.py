@@ -487,3 +487,59 @@ def test_batched_edge_columns(aln):
         rel, _ = O.kkt_residual(A64, B[c].astype(np.float64), X[c])
         assert rel <= 1e-8
         assert info2[c].iters <= max(3, info[c].iters // 4)
+
+
+# ------------------------------------------------------- full-size configurations
+def test_full_size_lopsided_single(aln):
+    """The default workload at full size (20000×5000) in the launch
+    configuration bench.py times (device inputs, tol 1e-6): 64 sampled Q
+    entries and 32 q entries against the oracle's single-entry definitions
+    (FP64 products of two columns), the solution's FP64 KKT residual and
+    objective by the oracle from A, and x ⪰ 0."""
+    import torch
+    p = W.lopsided_single()
+    A, b = p.A, p.B[0]
+    At = torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t()
+    Bt = torch.from_numpy(np.ascontiguousarray(p.B)).cuda()
+    with aln.Solver("split_bf16") as s:
+        s.prepare(At, Bt)
+        Q, q, sc = s.export()
+        X, info = s.solve(tol=1e-6)
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    norms = np.sqrt(np.einsum("ij,ij->j", A64, A64))
+    r = np.random.default_rng(51)
+    for i, j in list(r.integers(0, p.n, (62, 2))) + [(0, 4999), (4999, 4999)]:
+        qo = 1.0 if i == j else A64[:, i] @ A64[:, j] / (norms[i] * norms[j])
+        assert abs(Q[i, j] - qo) <= _split_bound(p.d), (i, j)
+    for j in r.integers(0, p.n, 32):
+        qo = -(A64[:, j] @ b64) / norms[j]
+        assert abs(q[0, j] - qo) <= 1e-12 * max(1.0, abs(qo))
+    np.testing.assert_allclose(sc, norms, rtol=1e-13)
+    assert info[0].status == aln.RHS_CONVERGED
+    rel, F = O.kkt_residual(A64, b64, X[0])
+    assert rel <= 1e-6 and np.all(X[0] >= 0.0)
+    np.testing.assert_allclose(info[0].rel_kkt, rel, rtol=1e-6)
+    np.testing.assert_allclose(info[0].objective, F, rtol=1e-9)
+
+
+def test_full_size_shared_multi_rhs(aln):
+    """The multi-RHS configuration at full size (10000×1000, k = 4096) in the
+    launch configuration bench.py times: every column's reported FP64 KKT
+    residual ≤ 1e-6; 24 sampled columns' residual and objective by the
+    oracle from A, matching the reported ones; X ⪰ 0."""
+    import torch
+    p = W.shared_multi_rhs()
+    At = torch.from_numpy(np.ascontiguousarray(p.A.T)).cuda().t()
+    Bt = torch.from_numpy(np.ascontiguousarray(p.B)).cuda()
+    with aln.Solver("split_bf16") as s:
+        s.prepare(At, Bt)
+        X, info = s.solve(tol=1e-6)
+    assert max(i.rel_kkt for i in info) <= 1e-6
+    assert np.all(X >= 0.0)
+    A64 = p.A.astype(np.float64)
+    for c in np.random.default_rng(52).choice(p.k, 24, replace=False):
+        b64 = p.B[c].astype(np.float64)
+        rel, F = O.kkt_residual(A64, b64, X[c])
+        assert rel <= 1e-6, (c, rel)
+        np.testing.assert_allclose(info[c].rel_kkt, rel, rtol=1e-6, atol=1e-13)
+        np.testing.assert_allclose(info[c].objective, F, rtol=1e-9)
