@@ -123,3 +123,45 @@ def test_warmstart_errors(aln):
         with pytest.raises(aln.AlnError) as e:
             aln.aln_warmstart_init(s.ctx, 0, 0)
         assert e.value.code == aln.ERR_INVALID_ARG
+
+
+def test_full_size_warm_start_configuration(aln):
+    """The warm-start configuration's A (8000×2000, lopsided column scales)
+    and the bench's network width (4096), trained on 16384 solved right-hand
+    sides: every one of 256 held-out warm solves meets FP64 KKT ≤ 1e-6 (8 of
+    them by the oracle from A), every start point is feasible and no worse
+    than the origin (the start is Alg. 2's exact line search along the
+    prediction), and the start points match the oracle's prediction with the
+    same weights."""
+    d, n = 8000, 2000
+    train = W.warmstart_family(d=d, n=n, k=16384, seed=1005)
+    held = W.warmstart_family(d=d, n=n, k=256, seed=1005, rhs_seed=1005 + 7919)
+    with aln.Solver("split_bf16") as s:
+        s.prepare(train.A, train.B)
+        X, info = s.solve(tol=1e-6)
+        _, q, sc = s.export()
+        s.warmstart_train(q, X * sc[None, :], epochs=20, batch=256, hidden=4096, lr=1e-3,
+                          seed=7)
+        params = s.warmstart_get()
+        s.prepare(held.A, held.B)
+        Qh, qh, sh = s.export()
+        X0, kept = s.warmstart_predict()
+        Xw, iw = s.solve(tol=1e-6, X0=X0)
+    assert max(i.rel_kkt for i in iw) <= 1e-6
+    assert np.all(X0 >= 0.0)
+    A64 = held.A.astype(np.float64)
+    for c in np.random.default_rng(53).choice(held.k, 8, replace=False):
+        b64 = held.B[c].astype(np.float64)
+        rel, _ = O.kkt_residual(A64, b64, Xw[c])
+        assert rel <= 1e-6, (c, rel)
+        f0 = O.nnls_objective(A64, b64, np.zeros(n))
+        assert O.nnls_objective(A64, b64, X0[c]) <= f0 * (1 + 1e-6), c
+    p64 = {k: params[k].astype(np.float64) for k in MO.PARAM_NAMES}
+    st64 = {"mu": params["mu"].astype(np.float64), "sd": params["sd"].astype(np.float64),
+            "tau": params["tau"]}
+    cols = np.arange(16)
+    y0o = MO.predict(p64, qh[cols], sh, Qh, st64)
+    y0 = (X0 * sh[None, :])[cols]
+    both = (np.abs(y0o).sum(axis=1) > 0) & (kept[cols] == 1)
+    assert both.sum() >= 8
+    assert _rel(y0[both], y0o[both]) <= 3e-2
