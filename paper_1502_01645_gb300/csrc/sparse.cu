@@ -12,7 +12,11 @@
 //                   column tile (a popcount prefix per bitmap word);
 //   k_csc_pack      the exact three-term BF16 split of every entry, written
 //                   into its box in the pre-swizzled layout the tensor-core
-//                   Gram copies verbatim (pack_index).
+//                   Gram copies verbatim (pack_index);
+//   k_csc_pairs / k_csc_items  the Gram's work list: the common blocks of
+//                   every tile pair, and chunks of them for the CTAs;
+//   k_csc_kkt_ax / k_csc_kkt_grad  the FP64 KKT pass without a dense copy of
+//                   A (r = Ax − b from the packed boxes, Aᵀr from the entries).
 // The Gram (launch_sgram_tc, gemm_tc.cu) multiplies, for each tile pair, only
 // the K blocks occupied in both column tiles: a block that is zero in either
 // operand adds exactly zero to H = AᵀA, so Q is that of the dense A up to how
