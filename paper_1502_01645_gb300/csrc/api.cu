@@ -465,6 +465,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     c->prepared = 0;
     c->grouped = 0;
     c->csc_kkt = 0;
+    c->q_tmask = nullptr;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     // A on the host, single-problem split path with q fused in the column
@@ -601,6 +602,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     c->prepared = 0;
     c->grouped = 0;
     c->csc_kkt = 0;
+    c->q_tmask = nullptr;
     c->stats.prepare_ms = c->stats.gram_ms = 0.0;
     const size_t esz = elt(dtype);
     const bool dev_ptr = is_device_ptr(col_ptr);
@@ -649,9 +651,11 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     const size_t b_lp = sparse_gram ? round_up((size_t)P * 4, 256) : 0;
     const size_t b_it = sparse_gram ? round_up((size_t)(P + c->num_sms + 1) * sizeof(SItem), 256) : 0;
     const size_t b_tk = sparse_gram ? round_up((size_t)P * 4, 256) + 256 : 0;
+    const int qtw = (int)ceil_div(T, 32);
+    const size_t b_qm = sparse_gram ? round_up((size_t)T * qtw * 4, 256) : 0;
     const size_t b_copy = dev_ptr ? 0 : b_cp + b_ri + b_v;
     ALN_CHECK(ensure(&c->csc_pool, &c->csc_bytes,
-                     b_copy + 2 * b_occ + b_cnt + b_fp + b_lp + b_it + b_tk + 256));
+                     b_copy + 2 * b_occ + b_cnt + b_fp + b_lp + b_it + b_tk + b_qm + 256));
     uint8_t* cp8 = (uint8_t*)c->csc_pool;
     const int64_t* cp = col_ptr;
     const int32_t* ri = row_idx;
@@ -679,6 +683,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     SItem* items = (SItem*)(cp8 + 2 * b_occ + b_cnt + b_fp + b_lp);
     unsigned int* ticket = (unsigned int*)(cp8 + 2 * b_occ + b_cnt + b_fp + b_lp + b_it);
     int64_t* meta = (int64_t*)((uint8_t*)ticket + round_up((size_t)P * 4, 256));
+    uint32_t* qmask = (uint32_t*)(cp8 + 2 * b_occ + b_cnt + b_fp + b_lp + b_it + b_tk);
 
     // dense column-major copy of A (16-byte columns) where a later step reads
     // it: the FP64 Gram, the many-right-hand-side solver, q for k > 4, or the
@@ -728,6 +733,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
         // number the occupied boxes, size the pack, scatter the split terms
         ALN_TRY(launch_csc_number(occ, W, T, wbase, cnt, toff, c->stream));
         ALN_TRY(launch_csc_worklist(occ, W, T, c->num_sms, Lp, items, meta, c->stream));
+        ALN_TRY(launch_csc_qmask(Lp, T, qmask, c->stream));
         ALN_TRY(cudaMemcpyAsync(pin, toff + T, 8, cudaMemcpyDeviceToHost, c->stream));
         ALN_TRY(cudaMemcpyAsync(pin + 1, meta, 16, cudaMemcpyDeviceToHost, c->stream));
         ALN_TRY(cudaStreamSynchronize(c->stream));
@@ -749,7 +755,9 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
         ALN_TRY(launch_sgram_tc(c->opt.gram_split, items, nitems, occ, W, wbase, toff, hi, mid, lo,
                                 n, c->inv_s, (float*)c->Q, ldq, (float*)c->sp_part, ticket,
                                 c->flags + 1, c->stream));
-        c->launches += 6;
+        c->launches += 7;
+        c->q_tmask = qmask;  // the Alg. 2 products skip Q's zero tiles
+        c->q_tw = qtw;
         if (no_dense) {  // the KKT pass reads these until the next prepare
             c->csc_cp = cp;
             c->csc_ri = ri;
@@ -779,6 +787,7 @@ aln_status aln_prepare_grouped(aln_ctx* c, int32_t count, const aln_problem* pro
     if (!c || !probs || count < 1 || count > (1 << 20)) return ALN_ERR_INVALID_ARG;
     if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
     c->csc_kkt = 0;
+    c->q_tmask = nullptr;
     int64_t cols = 0;
     for (int32_t p = 0; p < count; ++p) {
         const aln_problem& q = probs[p];

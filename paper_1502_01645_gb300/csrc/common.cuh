@@ -234,6 +234,10 @@ struct aln_ctx {
     size_t csc_box_bytes = 0;  // one split term's packed boxes in A_hi
     void* sp_part = nullptr;   // split-K partial tiles of the block-sparse Gram
     size_t sp_part_bytes = 0;
+    // tiles of Q that may be non-zero (block-sparse Gram; null = all): bit rt
+    // of q_tmask[ct·q_tw + rt/32] for row tile rt, column tile ct (128 wide)
+    const uint32_t* q_tmask = nullptr;
+    int q_tw = 0;
 
     // iteration workspace (element type follows the precision)
     void* qv = nullptr;       // q of the right-hand side being solved (iteration type)

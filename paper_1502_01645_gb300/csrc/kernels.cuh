@@ -189,6 +189,8 @@ cudaError_t launch_csc_number(const uint32_t* occ, int W, int64_t T, int32_t* wb
 // of pair p; pairs with Lp > 0 split into chunks of ≤ KC = max(16, ⌈ΣLp /
 // num_sms⌉) blocks.  meta[0] = items written (≤ P + num_sms), meta[1] =
 // partial slots used (≤ 2·num_sms).
+// Non-zero tiles of Q from the pair counts Lp (T·⌈T/32⌉ words, zeroed here).
+cudaError_t launch_csc_qmask(const int32_t* Lp, int64_t T, uint32_t* mask, cudaStream_t st);
 cudaError_t launch_csc_worklist(const uint32_t* occ, int W, int64_t T, int num_sms, int32_t* Lp,
                                 SItem* items, int64_t* meta, cudaStream_t st);
 cudaError_t launch_csc_pack(const int64_t* cp, const int32_t* ri, const void* v, int32_t dtype,

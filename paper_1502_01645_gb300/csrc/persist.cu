@@ -462,16 +462,31 @@ struct ReplArgs {
     double* kitem;   // 2 × CT·R     (curvature shares, by parity)
     PersistSync* sync;
     IterState* st;
+    // nullable: bit rt of tmask[ct·tw + rt/32] set when the 128×128 tile
+    // (row tile rt, column tile ct) of Q may be non-zero (tiles of Q known to
+    // be zero, from a block-sparse Gram, are skipped by the products)
+    const uint32_t* tmask;
+    int tw;
 };
 
+// Is the 128×128 tile of Q holding row j, column tile ct possibly non-zero?
+__device__ __forceinline__ bool tile_nz(const uint32_t* __restrict__ tm_ct, int j) {
+    const int rt = j >> 7;
+    return (__ldg(tm_ct + (rt >> 5)) >> (rt & 31)) & 1u;
+}
+
 // Partial Σ_{j ∈ group rg, v_j ≠ 0} v_j Q[j, tile ct] with v in shared memory;
-// written to dst[rg][tile]; returns the partial in threads < TILE.
+// written to dst[rg][tile]; returns the partial in threads < TILE.  With
+// tmask, rows whose tile of Q in column tile ct is zero are skipped (their
+// terms are exact zeros), FP32 tiles of 128 columns only.
 template <typename T, bool DIFF = false>
 __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, int n,
                                          int rows_per_group, const T* v, int ct, int rg,
                                          T* __restrict__ dst, T* red,
                                          const double* __restrict__ add = nullptr,
-                                         const T* vsub = nullptr) {
+                                         const T* vsub = nullptr,
+                                         const uint32_t* __restrict__ tmask = nullptr,
+                                         int tw = 0) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
@@ -485,10 +500,12 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
     T acc[VN];
 #pragma unroll
     for (int c = 0; c < VN; ++c) acc[c] = T(0);
+    const uint32_t* tm = tmask ? tmask + (int64_t)ct * tw : nullptr;
     for (int base = r0; base < r1; base += 32) {
         const int jl = base + lane;
         // the multiplied vector is v, or v − vsub (DIFF)
-        const T vl = jl < r1 ? (DIFF ? v[jl] - vsub[jl] : v[jl]) : T(0);
+        T vl = jl < r1 ? (DIFF ? v[jl] - vsub[jl] : v[jl]) : T(0);
+        if (tm && vl != T(0) && !tile_nz(tm, jl)) vl = T(0);
         unsigned int m = __ballot_sync(0xffffffffu, vl != T(0));
         while (m) {  // warp-uniform
             T vv[kPU];
@@ -695,19 +712,23 @@ __device__ __forceinline__ void clipped_list(int n, const T* e, int* list, int* 
     __syncthreads();
 }
 
-// g[i] += Σ_k e[list[k]] · Q[list[k]][i] for all i < n (rows in list order).
+// g[i] += Σ_k e[list[k]] · Q[list[k]][i] for all i < n (rows in list order);
+// with tmask, the tiles of Q known to be zero are not read (FP32 only).
 template <typename T>
 __device__ __forceinline__ void add_rows(const T* __restrict__ Q, int64_t ldq, int n,
-                                         const int* list, int count, const T* e, T* g) {
+                                         const int* list, int count, const T* e, T* g,
+                                         const uint32_t* __restrict__ tmask = nullptr,
+                                         int tw = 0) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     for (int i = threadIdx.x * VN; i < n; i += blockDim.x * VN) {
         T acc[VN];
 #pragma unroll
         for (int c = 0; c < VN; ++c) acc[c] = T(0);
+        const uint32_t* tm = tmask ? tmask + (int64_t)(i >> 7) * tw : nullptr;
 #pragma unroll
         for (int k = 0; k < kLocalClip; ++k) {
-            if (k < count) {
+            if (k < count && (!tm || tile_nz(tm, list[k]))) {
                 const int j = list[k];
                 const V q = __ldg(reinterpret_cast<const V*>(Q + (int64_t)j * ldq + i));
                 const T ej = e[j];
@@ -803,7 +824,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         // w-partials and curvature shares of this block's items
         for (int it = blockIdx.x; it < items; it += G) {
             const int ct = it % a.CT, rg = it / a.CT;
-            const T pw = mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red);
+            const T pw = mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red,
+                                        nullptr, nullptr, a.tmask, a.tw);
             const int64_t i = (int64_t)ct * TILE + threadIdx.x;
             const T prod = (threadIdx.x < TILE && i < n) ? sgb[i] * pw : T(0);
             const double k = block_sum_td<T>(prod, s_t);
@@ -891,14 +913,15 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             // of Q (listed in index order, so all blocks add in the same
             // order) — no product pass over the grid and no barrier.
             clipped_list(n, sw, s_clip, si);
-            add_rows(a.Q, a.ldq, n, s_clip, nclip, sw, sg);
+            add_rows(a.Q, a.ldq, n, s_clip, nclip, sw, sg, a.tmask, a.tw);
             __syncthreads();
             ++nclip_iters;
         } else if (nclip > 0) {
             // Q e crosses blocks: partials, barrier, every block sums them
             for (int it = blockIdx.x; it < items; it += G) {
                 const int ct = it % a.CT, rg = it / a.CT;
-                (void)mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2, red);
+                (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2, red,
+                                     nullptr, nullptr, a.tmask, a.tw);
             }
             if (!(ok = grid_barrier(a.sync, bar += G))) break;
             sum_partials(a.part2, a.R, a.ldq, n, sg, true);
@@ -961,6 +984,9 @@ cudaError_t launch_alg2_persist(aln_ctx* c) {
         r.kitem = c->p_kpart;
         r.sync = (PersistSync*)c->p_sync;
         r.st = c->st;
+        // zero tiles of Q from the block-sparse Gram (FP32, 128-wide tiles)
+        r.tmask = sizeof(T) == 4 ? c->q_tmask : nullptr;
+        r.tw = c->q_tw;
         const size_t smem = repl_smem_bytes<T>(c->ldq);
         cudaError_t e = cudaFuncSetAttribute(k_alg2_repl<T>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

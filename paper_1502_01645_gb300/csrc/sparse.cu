@@ -278,6 +278,19 @@ __global__ void __launch_bounds__(kCscThreads) k_csc_items(const int32_t* __rest
     }
 }
 
+// Non-zero tiles of Q: every pair with a common block marks its tile and
+// the mirror, bit rt of mask[ct·tw + rt/32] (mask zeroed beforehand).
+__global__ void __launch_bounds__(kCscThreads) k_csc_qmask(const int32_t* __restrict__ Lp,
+                                                           int64_t P, int tw,
+                                                           uint32_t* __restrict__ mask) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P || Lp[p] == 0) return;
+    int I, J;
+    tri_pair(p, I, J);
+    atomicOr(&mask[(int64_t)J * tw + (I >> 5)], 1u << (I & 31));
+    atomicOr(&mask[(int64_t)I * tw + (J >> 5)], 1u << (J & 31));
+}
+
 // Float-pair accumulator on the FP32 pipe (this GPU's FP64 pipe is narrow):
 // += a·(h + l) with the product's rounding error from an FMA (TwoProduct) and
 // the addition's from TwoSum kept in c (Ogita, Rump & Oishi 2005).
@@ -498,6 +511,15 @@ cudaError_t launch_csc_worklist(const uint32_t* occ, int W, int64_t T, int num_s
     const int64_t P = T * (T + 1) / 2;
     k_csc_pairs<<<(unsigned)ceil_div(P, kCscWarps), kCscThreads, 0, st>>>(occ, W, P, Lp);
     k_csc_items<<<1, kCscThreads, 0, st>>>(Lp, P, num_sms, items, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_qmask(const int32_t* Lp, int64_t T, uint32_t* mask, cudaStream_t st) {
+    const int64_t P = T * (T + 1) / 2;
+    const int tw = (int)ceil_div(T, 32);
+    cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)T * tw * 4, st);
+    if (e != cudaSuccess) return e;
+    k_csc_qmask<<<(unsigned)ceil_div(P, kCscThreads), kCscThreads, 0, st>>>(Lp, P, tw, mask);
     return cudaGetLastError();
 }
 
