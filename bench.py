@@ -104,6 +104,9 @@ def parse():
     ap.add_argument("--hidden", type=int, default=4096, help="warm-start network width")
     ap.add_argument("--gram-split", type=int, default=0,
                     help="BF16 terms of the split Gram (2 or 3; 0: library default)")
+    ap.add_argument("--seeds", type=int, default=None,
+                    help="problems per step, seeds seed..seed+S-1 (default 8 for "
+                         "lopsided_single: its iteration count moves with the seed; 1 otherwise)")
     ap.add_argument("--refine-gain", type=int, default=0,
                     help="decades each inner FP32 run aims below the last FP64 residual "
                          "(0: library default, <0: every run aims at tol)")
@@ -119,6 +122,33 @@ def workload(args):
     w["name"] = args.workload
     w["desc"] = w["desc"].format(**w)
     return w
+
+
+def seed_count(args, w):
+    if args.seeds is not None:
+        return max(1, args.seeds)
+    return 8 if w["name"] == "lopsided_single" else 1
+
+
+def problem_seeds(w, S, rank=0):
+    """The seeds of one step's problems: seed .. seed+S-1 (rank r adds 1000·r)."""
+    return [w["seed"] + 1000 * rank + i for i in range(S)]
+
+
+def _generate_one(w, seed):
+    return generate(dict(w, seed=seed))
+
+
+def generate_many(w, seeds):
+    """Problems for several seeds, drawn in parallel by spawned workers (never
+    forked: the caller may already hold a CUDA context)."""
+    if len(seeds) == 1:
+        return [generate(dict(w, seed=seeds[0]))]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = min(len(seeds), max(1, (os.cpu_count() or 2) // 2))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_generate_one, [w] * len(seeds), seeds))
 
 
 def generate(w, rank=0):
@@ -149,6 +179,24 @@ def peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return FALLBACK_PEAKS, "fallback"
+
+
+_L2 = None
+
+
+def l2_peak():
+    """L2 read bandwidth measured live on this GPU (64 MiB resident buffer,
+    best of three probes of 20 reads each), or None if the probe fails."""
+    global _L2
+    if _L2 is None:
+        try:
+            from paper_1502_01645_gb300 import aln
+            best = max(aln.aln_l2_read_bandwidth(64 << 20, 20) for _ in range(3))
+            _L2 = {"l2_read_gbs": best, "kind": "measured live: streaming ld.global.cg "
+                                                 "reads of a 64 MiB L2-resident buffer"}
+        except Exception as e:  # pragma: no cover - only on a GPU
+            _L2 = {"error": str(e)}
+    return _L2 if "l2_read_gbs" in _L2 else None
 
 
 # ------------------------------------------------------------------ multi-rank
@@ -235,29 +283,35 @@ def blas_threads():
 def cpu_sample(w, p):
     """The FP64 oracle, as it stands, on a bounded sample of the workload.
 
-    Single RHS: the NNLS sub-problem on the first m = n/2 columns of A (same d
-    and b), solved to the workload's tolerance; the oracle's Gram and dense
-    Alg. 2 products grow as n², so the full-size time is t·(n/m)².
-    Many RHS: the first 16 right-hand sides on the full A, time ×(k/16).
-    Returns (seconds for one full step, description)."""
+    Single RHS, Alg. 2: the whole problem (A, b of the first seed), Gram and
+    iterations, solved to the workload's tolerance; no extrapolation.  Anti+Acc
+    (thousands of iterations): the sub-problem on the first m = n/2 columns,
+    scaled by (n/m)², which assumes the iteration count of the half-width
+    problem (stated in the sample).  Many RHS: the first 16 right-hand sides on
+    the full A, time ×(k/16).  Returns (seconds for one full step, description)."""
     import numpy as np
     from oracle import nnls as O
     if w["k"] == 1:
-        m = max(1, w["n"] // 2)
+        acc = w.get("algorithm") == "anti_acc"
+        m = max(1, w["n"] // 2) if acc else w["n"]
         A64 = np.asarray(p.A[:, :m], dtype=np.float64, order="F")
         b64 = np.asarray(p.B[0], dtype=np.float64)
-        acc = w.get("algorithm") == "anti_acc"
         t0 = time.perf_counter()
         if acc:
             from oracle import acc as AC
-            AC.anti_acc(A64, b64, tol=w["tol"], max_iter=400000)
+            res = AC.anti_acc(A64, b64, tol=w["tol"], max_iter=400000)
         else:
-            O.antilop(A64, b64, tol=w["tol"])
+            res = O.antilop(A64, b64, tol=w["tol"])
         t = time.perf_counter() - t0
+        it = res[1].iters if isinstance(res, tuple) and hasattr(res[1], "iters") else None
+        if not acc:
+            return t, (f"oracle antilop on the whole {w['d']}x{w['n']} problem (seed "
+                       f"{w['seed']}): Gram + {it} Alg. 2 iterations in {t:.2f} s, "
+                       "not extrapolated")
         scale = (w["n"] / m) ** 2
-        name = "anti_acc" if acc else "antilop"
-        return t * scale, (f"oracle {name} on A[:, :{m}] (d={w['d']}) in {t:.2f} s, "
-                           f"x (n/m)^2 = {scale:.0f} for the full size")
+        return t * scale, (f"oracle anti_acc on A[:, :{m}] (d={w['d']}): {it} iterations in "
+                           f"{t:.2f} s, extrapolated x (n/m)^2 = {scale:.0f} to the full size "
+                           "assuming the same iteration count")
     A64 = np.asarray(p.A, dtype=np.float64, order="F")
     s = 16
     t0 = time.perf_counter()
@@ -307,9 +361,16 @@ def run_reference(args):
         return 0
     w = workload(args)
     w["algorithm"] = args.algorithm
-    p = None if w["name"] == "nmf" else generate(w)
+    S = seed_count(args, w)
+    seeds = problem_seeds(w, S)
+    # the seed set of our arm: step i solves the problem of seed i mod S
+    probs = [None] if w["name"] == "nmf" else generate_many(w, seeds)
+    p = probs[0]
     times, desc = [], ""
     for i in range(args.warmup + args.steps):
+        if S > 1:
+            p = probs[i % S]
+            w["seed"] = seeds[i % S]
         if w["name"] == "uneven_batch":
             t, desc = cpu_sample_grouped(w, p)
         elif w["name"] == "paper_tcases":
@@ -332,9 +393,10 @@ def run_reference(args):
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "d": w["d"], "n": w["n"], "k": w["k"],
-                   "tol": w["tol"], "seed": w["seed"]},
+                   "tol": w["tol"], "seed": seeds[0], "seeds": seeds},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc + (f"; step i takes seed {seeds[0]} + (i mod {S})"
+                                           if S > 1 else "")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -373,20 +435,30 @@ def run_ours(args):
     if w["name"] == "banded_tall":
         return run_banded(args, w, world, rank, local)
     d, n, k, tol = w["d"], w["n"], w["k"], w["tol"]
-    p = generate(w, rank)
-    A_np, B_np = p.A, p.B
-    At = torch.from_numpy(np.ascontiguousarray(A_np.T)).cuda().t()  # (d, n) column-major
-    Bt = torch.from_numpy(np.ascontiguousarray(B_np)).cuda()
+    S = seed_count(args, w)
+    seeds = problem_seeds(w, S, rank)
+    probs = generate_many(w, seeds)
+    p = probs[0]
+    dev = [(torch.from_numpy(np.ascontiguousarray(q.A.T)).cuda().t(),   # (d, n) column-major
+            torch.from_numpy(np.ascontiguousarray(q.B)).cuda()) for q in probs]
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     alg = aln.ALG_ANTI_ACC if args.algorithm == "anti_acc" else aln.ALG_ANTILOP
     solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
                         gram_split=args.gram_split, algorithm=alg)
+    sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(S)]
 
     def step():
-        solver.prepare(At, Bt)
-        _, info = solver.solve(tol=tol, X=Xt)
-        return info, solver.stats()
+        """One step: every problem of the seed set prepared and solved."""
+        out = []
+        for i, (At, Bt) in enumerate(dev):
+            sev[i][0].record(stream)
+            solver.prepare(At, Bt)
+            _, info = solver.solve(tol=tol, X=Xt)
+            sev[i][1].record(stream)
+            out.append((info, solver.stats()))
+        return out
 
     for _ in range(args.warmup):
         step()
@@ -405,11 +477,18 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     stats, worst, iters = [], 0.0, []
+    seed_ms = [[] for _ in range(S)]
+    seed_iters = [0] * S
     for _ in range(args.steps):
-        info, st = step()
-        stats.append(st)
-        worst = max(worst, max(i.rel_kkt for i in info))
-        iters.append(max(i.iters for i in info))
+        res = step()
+        for i, (info, st) in enumerate(res):
+            stats.append(st)
+            worst = max(worst, max(x.rel_kkt for x in info))
+            seed_iters[i] = max(x.iters for x in info)
+        iters.append([max(x.iters for x in info) for info, _ in res])
+        torch.cuda.synchronize()
+        for i in range(S):
+            seed_ms[i].append(sev[i][0].elapsed_time(sev[i][1]))
     ev1.record(stream)
     barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -419,7 +498,8 @@ def run_ours(args):
         raise SystemExit(f"invalid run: rel KKT {worst:.3e} above {tol}")
 
     tmax = max_over_ranks(elapsed, world)
-    value = job_rate(k, args.steps, world, tmax)
+    value = job_rate(k * S, args.steps, world, tmax)
+    seed_rate = [k * 1e3 / statistics.median(v) for v in seed_ms]
 
     def avg(f):
         return sum(f(s) for s in stats) / len(stats)
@@ -427,56 +507,69 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers (pinned) ----
     e2e = None
     if not args.no_e2e:
-        A_h = torch.from_numpy(np.ascontiguousarray(A_np.T)).pin_memory().t()
-        B_h = torch.from_numpy(np.ascontiguousarray(B_np)).pin_memory()
+        host = [(torch.from_numpy(np.ascontiguousarray(q.A.T)).pin_memory().t(),
+                 torch.from_numpy(np.ascontiguousarray(q.B)).pin_memory()) for q in probs]
         X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
-        k_e2e = max(3, min(args.steps, 5))
+        k_e2e = max(3, min(args.steps, 5)) if S == 1 else 2
         hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
                              gram_split=args.gram_split, algorithm=alg)
-        hsolver.prepare(A_h, B_h)
+        hsolver.prepare(*host[0])
         hsolver.solve(tol=tol, X=X_h)
         barrier()
         t0 = time.perf_counter()
+        hworst = 0.0
         for _ in range(k_e2e):
-            hsolver.prepare(A_h, B_h)
-            _, hinfo = hsolver.solve(tol=tol, X=X_h)
+            for A_h, B_h in host:
+                hsolver.prepare(A_h, B_h)
+                _, hinfo = hsolver.solve(tol=tol, X=X_h)
+                hworst = max(hworst, max(x.rel_kkt for x in hinfo))
         barrier()
         te = time.perf_counter() - t0
         hsolver.close()
-        e2e = {"value": job_rate(k, k_e2e, world, max_over_ranks(te, world)), "unit": UNIT,
-               "h2d_bytes_per_step": int(A_np.nbytes + B_np.nbytes),
-               "d2h_bytes_per_step": int(k * n * 8), "steps": k_e2e,
-               "rel_kkt_max": max(i.rel_kkt for i in hinfo)}
+        e2e = {"value": job_rate(k * S, k_e2e, world, max_over_ranks(te, world)), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(q.A.nbytes + q.B.nbytes for q in probs)),
+               "d2h_bytes_per_step": int(S * k * n * 8), "steps": k_e2e,
+               "rel_kkt_max": hworst}
 
     # ---- plain FP64 method on the same workload (the metric's comparison) ----
     plain = None
     if not args.no_plain and w["prec"] != "fp64":
         kp_rhs = min(k, 16)          # the FP64 method solves one RHS at a time
         psolver = aln.Solver("fp64", stream=stream.cuda_stream)
-        Bp = Bt[:kp_rhs].contiguous()
         Xp = torch.zeros((kp_rhs, n), dtype=torch.float64, device="cuda")
-        psolver.prepare(At, Bp)
+        psolver.prepare(dev[0][0], dev[0][1][:kp_rhs].contiguous())
         psolver.solve(tol=tol, X=Xp)
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        e0.record(stream)
-        for _ in range(reps):
-            psolver.prepare(At, Bp)
-            _, pinfo = psolver.solve(tol=tol, X=Xp)
-        e1.record(stream)
-        barrier()
-        tp = e0.elapsed_time(e1) / 1e3 / reps          # one prepare + kp_rhs solves
-        pst = psolver.stats()
+        reps = 2 if S == 1 else 1
+        p_ms, p_iters, p_rel, p_gram = [], [], 0.0, []
+        for At, Bt in dev:
+            Bp = Bt[:kp_rhs].contiguous()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                psolver.prepare(At, Bp)
+                _, pinfo = psolver.solve(tol=tol, X=Xp)
+            e1.record(stream)
+            barrier()
+            tp = e0.elapsed_time(e1) / 1e3 / reps      # one prepare + kp_rhs solves
+            pst = psolver.stats()
+            per_rhs = (tp - pst.prepare_ms / 1e3) / kp_rhs
+            p_ms.append((pst.prepare_ms / 1e3 + per_rhs * k) * 1e3)   # the whole workload
+            p_gram.append(pst.gram_ms)
+            p_iters.append(max(i.iters for i in pinfo))
+            p_rel = max(p_rel, max(i.rel_kkt for i in pinfo))
         psolver.close()
-        per_rhs = (tp - pst.prepare_ms / 1e3) / kp_rhs
-        full = pst.prepare_ms / 1e3 + per_rhs * k        # the whole workload's solves
-        plain = {"value": k / full, "unit": UNIT, "ms_per_step": full * 1e3,
-                 "gram_ms": pst.gram_ms, "rhs_timed": kp_rhs, "repeats": reps,
-                 "iters_max": max(i.iters for i in pinfo),
-                 "rel_kkt_max": max(i.rel_kkt for i in pinfo),
+        p_rate = [k * 1e3 / t for t in p_ms]
+        plain = {"value": k * S * 1e3 / sum(p_ms), "unit": UNIT,
+                 "ms_per_step": sum(p_ms), "gram_ms": statistics.mean(p_gram),
+                 "rhs_timed": kp_rhs, "repeats": reps,
+                 "iters_max": max(p_iters), "rel_kkt_max": p_rel,
                  "note": "FP64 Gram + FP64 Alg. 2 one right-hand side at a time"
                          + ("" if kp_rhs == k else f"; {kp_rhs} timed, scaled to {k}")}
+        if S > 1:
+            plain.update({"iters_per_seed": p_iters,
+                          "solves_per_s_per_seed": [round(r, 4) for r in p_rate],
+                          "median_solves_per_s": statistics.median(p_rate)})
 
     solver.close()
     if rank != 0:
@@ -486,17 +579,20 @@ def run_ours(args):
 
     pk, pk_kind = peaks()
     hbm = float(pk["hbm_gbs"])
-    peak_tc = float(pk["bf16_tflops_sustained"])
+    peak_burst = float(pk["bf16_tflops"])
     gram = avg(lambda s: s.gram_ms)
     it_ms = avg(lambda s: s.iterate_ms)
     rooflines = []
     if w["prec"] == "split_bf16" and k == 1:
-        flops = 6.0 * d * n * (n + 1)          # six split products over n(n+1)/2 entries
+        # issued tensor FLOPs: six split products over the n(n+1)/2 distinct
+        # entries; the Gram runs 2 ms alone between other kernels, so it is
+        # compared with the burst peak
+        flops = 6.0 * d * n * (n + 1)
         ach = flops / (gram / 1e3) / 1e12
         rooflines.append({"bound": "tensor", "kernel": "k_gram_tc (split-BF16 Gram)",
-                          "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s",
-                          "frac": ach / peak_tc, "traffic": None,
-                          "peak_kind": f"{pk_kind} bf16 sustained",
+                          "achieved": ach, "peak": peak_burst, "unit": "TFLOP/s",
+                          "frac": ach / peak_burst, "traffic": None,
+                          "peak_kind": f"{pk_kind} bf16 burst",
                           "algorithmic_per_launch": flops, "avg_launch_ms": gram})
     if k == 1:
         esz = 8 if w["prec"] == "fp64" else 4
@@ -517,14 +613,19 @@ def run_ours(args):
         us_it = it_ms * 1e3 / iters_avg if iters_avg > 0 else None
         if esz * n * n < 4e6:
             note = (f"latency-bound, not bandwidth-bound: Q ({esz * n * n / 1e3:.0f} KB) stays "
-                    f"on chip and an iteration ({us_it:.1f} us) is five dependent phases "
-                    "separated by grid-wide reductions, so this fraction is not a meaningful "
-                    "efficiency; see us_per_iteration")
-        rooflines.append({"bound": "hbm", "kernel": kname,
-                          "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                          "traffic": traffic, "peak_kind": f"{pk_kind} hbm copy",
-                          "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
-                          "us_per_iteration": us_it, "note": note})
+                    f"on chip and an iteration ({us_it:.1f} us) is a chain of dependent phases "
+                    "separated by block- or cluster-wide reductions, so this fraction is not a "
+                    "meaningful efficiency; see us_per_iteration")
+        roof = {"bound": "hbm", "kernel": kname,
+                "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "peak_kind": f"{pk_kind} hbm copy",
+                "algorithmic_per_launch": qbytes, "avg_launch_ms": it_ms,
+                "us_per_iteration": us_it, "note": note}
+        l2 = l2_peak()
+        if l2:
+            roof["l2"] = {"peak_gbs": l2["l2_read_gbs"], "frac": ach / l2["l2_read_gbs"],
+                          "peak_kind": l2["kind"]}
+        rooflines.append(roof)
     else:
         # tensor FLOPs of the batched products: 3 split products of 2·n² per
         # running column (W = Qḡ) and per clipped column (U = Qe)
@@ -533,9 +634,9 @@ def run_ours(args):
         ach = flops / (it_ms / 1e3) / 1e12 if it_ms > 0 else 0.0
         rooflines.append({"bound": "tensor",
                           "kernel": "batched Alg. 2 phase (k_bgemm_tc W and U + mask/update)",
-                          "achieved": ach, "peak": peak_tc, "unit": "TFLOP/s",
-                          "frac": ach / peak_tc, "traffic": None,
-                          "peak_kind": f"{pk_kind} bf16 sustained",
+                          "achieved": ach, "peak": peak_burst, "unit": "TFLOP/s",
+                          "frac": ach / peak_burst, "traffic": None,
+                          "peak_kind": f"{pk_kind} bf16 burst",
                           "algorithmic_per_launch": flops, "avg_launch_ms": it_ms})
     rooflines.sort(key=lambda r: -r["avg_launch_ms"])
 
@@ -545,13 +646,17 @@ def run_ours(args):
         cpu = {"value": k / ts, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                "sample": desc}
 
+    last = stats[-1]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if w["prec"] == "fp64" else "bf16 split + f32", "data": "synthetic",
         "config": {"workload": w["desc"], "d": d, "n": n, "k": k, "tol": tol,
-                   "seed": w["seed"],
+                   "seed": w["seed"], "seeds": seeds,
+                   "step": (f"prepare + solve of each of {S} problems (seeds {seeds[0]}.."
+                            f"{seeds[-1]}); value = all solves / total time"
+                            if S > 1 else "prepare + solve of one problem"),
                    "form": (("FP64 Gram + FP64 " if w["prec"] == "fp64" else
                              "3-term split-BF16 tcgen05 Gram, FP32 ")
                             + ("Anti+Acc (power iteration for L, Nesterov projected "
@@ -559,22 +664,26 @@ def run_ours(args):
                             + ("" if w["prec"] == "fp64" else
                                ", FP64 scale/KKT/refinement")),
                    "algorithm": args.algorithm,
-                   "lipschitz": (stats[-1].lipschitz if alg == aln.ALG_ANTI_ACC else None),
-                   "power_products": (int(stats[-1].power_products)
+                   "lipschitz": (last.lipschitz if alg == aln.ALG_ANTI_ACC else None),
+                   "power_products": (int(last.power_products)
                                       if alg == aln.ALG_ANTI_ACC else None),
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2" if A_np.nbytes > 129e6 else
+                   "l2": "inputs larger than L2" if p.A.nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",
                    "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
                    "solve_ms": avg(lambda s: s.solve_ms), "iterate_ms": it_ms,
-                   "kkt_ms": avg(lambda s: s.kkt_ms), "iters_max": iters,
+                   "kkt_ms": avg(lambda s: s.kkt_ms),
+                   "iters_per_seed": seed_iters,
+                   "solves_per_s_per_seed": [round(r, 2) for r in seed_rate],
+                   "median_solves_per_s": statistics.median(seed_rate),
                    "rel_kkt_max": worst,
                    "phase_us_per_iteration": (
-                       None if k != 1 or stats[-1].iterations == 0 else
+                       None if k != 1 or last.iterations == 0 else
                        dict(zip(("step", "product", "barrier", "gather_mask", "unused")
                                 if alg == aln.ALG_ANTI_ACC else
                                 ("product", "barrier", "update", "clipped", "mask"),
-                                [round(stats[-1].phase_us[i] / stats[-1].iterations, 3)
+                                [round(sum(s.phase_us[i] for s in stats) /
+                                       max(1, sum(s.iterations for s in stats)), 3)
                                  for i in range(5)])))},
         "roofline": rooflines[0],
         "roofline_secondary": rooflines[1] if len(rooflines) > 1 else None,
@@ -584,6 +693,9 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if plain and S > 1:
+        line["config"]["chosen_over_plain_median"] = (statistics.median(seed_rate) /
+                                                      plain["median_solves_per_s"])
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

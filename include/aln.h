@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define ALN_VERSION 100
+#define ALN_VERSION 200
 
 typedef enum aln_status {
     ALN_OK = 0,
@@ -142,7 +142,19 @@ typedef struct aln_options {
                              single blocks take the rest; 1 = no clusters, 2, 4
                              or 8; 0 = default 4 */
     int32_t algorithm;    /* aln_algorithm; default ALN_ALG_ANTILOP */
-    int32_t reserved;
+    int32_t wait_limit_us; /* limit of one device-side wait of the persistent
+                             solver kernels (a grid barrier), in microseconds;
+                             when it expires the kernel stops every block,
+                             leaves no work in flight and aln_solve returns
+                             ALN_ERR_TIMEOUT (the context stays usable);
+                             0 = default 2 000 000 (2 s) */
+    int32_t test_barrier_skew; /* FOR TESTS ONLY, 0 in normal use: every grid
+                             barrier of the persistent solver kernels waits for
+                             this many arrivals more than the grid provides, so
+                             the first wait expires after wait_limit_us and the
+                             timeout path runs (no fault, no hang); must be
+                             0..1024 */
+    int32_t reserved[2];
 } aln_options;
 
 typedef struct aln_solve_info {
@@ -384,6 +396,13 @@ typedef struct aln_stats {
     int64_t power_products;  /* products Qv that power iteration took */
 } aln_stats;
 
+/* Change the device-wait options of an existing context (aln_options'
+ * wait_limit_us and test_barrier_skew, same meaning and ranges); they apply
+ * from the next launch on.  Not in the paper: the bounded waits are how the
+ * persistent kernels of this library report a stalled grid instead of
+ * hanging.  Errors: INVALID_ARG. */
+aln_status aln_set_wait_limit(aln_ctx* ctx, int32_t wait_limit_us, int32_t test_barrier_skew);
+
 /* Copy the statistics of this context into *out.  Errors: INVALID_ARG. */
 aln_status aln_get_stats(aln_ctx* ctx, aln_stats* out);
 
@@ -406,11 +425,15 @@ aln_status aln_get_stats(aln_ctx* ctx, aln_stats* out);
  *   b      d entries, same dtype                         (device memory)
  *   x      n entries, FP64, x ≥ 0                        (device memory)
  *   out    2 doubles                                     (device memory)
+ * Unlike the context calls, this one takes device (or managed) memory only:
+ * a host pointer in any of the four gives ALN_ERR_INVALID_ARG before anything
+ * is launched.
  *   stream cudaStream_t the work is enqueued on (NULL = legacy stream); the
  *          call returns without synchronizing.
  * Limits: 3n + 2d + 520 ≤ ALN_NOALLOC_SCRATCH_DOUBLES, otherwise
  * ALN_ERR_INVALID_ARG and nothing is launched (use aln_kkt_residual instead).
- * A NaN or Inf in A or b makes both outputs NaN.
+ * A NaN or Inf in A, b or x makes both outputs NaN (the call still returns
+ * ALN_OK: the check runs on the GPU and the call does not synchronize).
  * The first call on each device looks up the device address of the scratch
  * array (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls share the one array and each call
@@ -420,6 +443,15 @@ aln_status aln_get_stats(aln_ctx* ctx, aln_stats* out);
 aln_status aln_kkt_residual_noalloc(const void* A, int64_t d, int64_t n, int64_t lda,
                                     int32_t dtype, const void* b, const double* x, double* out,
                                     void* stream);
+
+/* Measurement helper, not in the paper: the L2 read bandwidth of the current
+ * device in GB/s, from `reps` streaming reads (16-byte loads cached in L2
+ * only, every SM) of a `bytes` buffer that stays resident in L2, timed with
+ * CUDA events after three warm-up reads.  The Alg. 2 products read Q from L2
+ * once it fits there, so this is their ceiling.  The call allocates and frees
+ * its own buffer and stream and synchronizes.  Requires 1 MiB ≤ bytes ≤ ¾ of
+ * the L2 size and reps ≥ 1.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+aln_status aln_l2_read_bandwidth(int64_t bytes, int32_t reps, double* gbs);
 
 /* Destroy a context and free its workspace (NULL is accepted). */
 void aln_destroy(aln_ctx* ctx);

@@ -31,7 +31,8 @@ EXPORTS = (
     "aln_export_scaled", "aln_get_stats", "aln_destroy", "aln_status_string", "aln_version",
     "aln_kkt_residual_noalloc", "aln_prepare_grouped", "aln_default_train_opts",
     "aln_warmstart_init", "aln_warmstart_params", "aln_warmstart_grad", "aln_warmstart_train",
-    "aln_warmstart_predict", "aln_nmf", "aln_prepare_csc",
+    "aln_warmstart_predict", "aln_nmf", "aln_prepare_csc", "aln_set_wait_limit",
+    "aln_l2_read_bandwidth",
 )
 
 
@@ -41,7 +42,8 @@ class AlnOptions(ctypes.Structure):
                 ("stagnation", ctypes.c_int32), ("iter_kernel", ctypes.c_int32),
                 ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32),
                 ("gram_split", ctypes.c_int32), ("group_cluster", ctypes.c_int32),
-                ("algorithm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("algorithm", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("test_barrier_skew", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class AlnSolveInfo(ctypes.Structure):
@@ -133,6 +135,10 @@ def load(path: str | None = None):
     lib.aln_nmf.argtypes = [vp, vp, i64, i64, i64, i64, dp, i64, dp, i64, i32, ctypes.c_double,
                             i32, dp]
     lib.aln_nmf.restype = ctypes.c_int
+    lib.aln_set_wait_limit.argtypes = [vp, i32, i32]
+    lib.aln_set_wait_limit.restype = ctypes.c_int
+    lib.aln_l2_read_bandwidth.argtypes = [i64, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.aln_l2_read_bandwidth.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -244,6 +250,18 @@ def aln_nmf(ctx, V, m, n, ldv, r, W, ldw, H, ldh, outer, tol, max_iter, objectiv
 
 def aln_warmstart_predict(ctx, X0, ldx, kept) -> None:
     _check(load().aln_warmstart_predict(ctx, _ptr(X0), ldx, _ptr(kept)), "aln_warmstart_predict")
+
+
+def aln_set_wait_limit(ctx, wait_limit_us, test_barrier_skew=0) -> None:
+    _check(load().aln_set_wait_limit(ctx, wait_limit_us, test_barrier_skew),
+           "aln_set_wait_limit")
+
+
+def aln_l2_read_bandwidth(nbytes=64 << 20, reps=20) -> float:
+    """Measured L2 read bandwidth of the current device (GB/s)."""
+    v = ctypes.c_double()
+    _check(load().aln_l2_read_bandwidth(nbytes, reps, ctypes.byref(v)), "aln_l2_read_bandwidth")
+    return v.value
 
 
 def aln_get_stats(ctx) -> AlnStats:
@@ -416,6 +434,9 @@ class Solver:
         s = np.zeros(self.n)
         aln_export_scaled(self.ctx, Q, self.n, q, self.n, s)
         return Q, q, s
+
+    def set_wait_limit(self, wait_limit_us, test_barrier_skew=0):
+        aln_set_wait_limit(self.ctx, wait_limit_us, test_barrier_skew)
 
     def stats(self) -> AlnStats:
         return aln_get_stats(self.ctx)

@@ -380,6 +380,8 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.gram_split != 2 && o.gram_split != 3) return ALN_ERR_INVALID_ARG;
     if (o.algorithm != ALN_ALG_ANTILOP && o.algorithm != ALN_ALG_ANTI_ACC)
         return ALN_ERR_INVALID_ARG;
+    if (o.wait_limit_us < 0 || o.test_barrier_skew < 0 || o.test_barrier_skew > 1024)
+        return ALN_ERR_INVALID_ARG;
     if (o.group_cluster == 0) o.group_cluster = 4;
     if (o.group_cluster != 1 && o.group_cluster != 2 && o.group_cluster != 4 &&
         o.group_cluster != 8)
@@ -934,6 +936,14 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     ALN_TRY(cudaStreamSynchronize(c->stream));
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]) == cudaSuccess) c->stats.solve_ms = ms;
+    return ALN_OK;
+}
+
+aln_status aln_set_wait_limit(aln_ctx* c, int32_t wait_limit_us, int32_t test_barrier_skew) {
+    if (!c || wait_limit_us < 0 || test_barrier_skew < 0 || test_barrier_skew > 1024)
+        return ALN_ERR_INVALID_ARG;
+    c->opt.wait_limit_us = wait_limit_us;
+    c->opt.test_barrier_skew = test_barrier_skew;
     return ALN_OK;
 }
 

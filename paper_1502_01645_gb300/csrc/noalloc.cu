@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(kNaThreads) k_na_grad(const TA* __restrict__ A
         const double gi = acc / si;
         const bool P = x[i] * si > 0.0 || gi < 0.0;
         L.gb2[i] = P ? gi * gi : 0.0;
+        if (!isfinite(x[i])) atomicOr(L.flag, 1);
     }
 }
 
@@ -172,6 +173,18 @@ __global__ void k_na_final(int64_t n, int nf, NaLayout L, double* __restrict__ o
         out[0] = bad ? (double)NAN : (den > 0.0 ? num / den : num);
         out[1] = bad ? (double)NAN : 0.5 * f;
     }
+}
+
+// True when p is device (or managed) memory.  A host pointer handed to the
+// kernels below would be dereferenced on the GPU, so every argument is checked
+// before anything is launched (cudaPointerGetAttributes allocates nothing).
+bool na_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 // Device address of the scratch array, looked up once per device with that
@@ -220,6 +233,8 @@ extern "C" aln_status aln_kkt_residual_noalloc(const void* A, int64_t d, int64_t
     if (!A || !b || !x || !out) return ALN_ERR_INVALID_ARG;
     if (d < 1 || n < 1 || lda < d) return ALN_ERR_INVALID_ARG;
     if (dtype != ALN_DTYPE_F32 && dtype != ALN_DTYPE_F64) return ALN_ERR_INVALID_ARG;
+    if (!na_device_ptr(A) || !na_device_ptr(b) || !na_device_ptr(x) || !na_device_ptr(out))
+        return ALN_ERR_INVALID_ARG;  // host memory: the kernels cannot read it
     // fixed part: flag block (8) + s, qm, gb2 (3n) + fpart (512) + r (d) + rpart (CG·d)
     const int64_t fixed = 8 + 3 * n + kNaFparts + d;
     if (n > kNoallocDoubles || d > kNoallocDoubles || fixed + d > kNoallocDoubles)

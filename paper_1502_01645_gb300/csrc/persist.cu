@@ -37,9 +37,14 @@ namespace aln {
 constexpr int kPThreads = 1024;
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPU = 4;                          // Q rows in flight per warp (64 KB per SM)
-constexpr uint64_t kBarrierNs = 2000000000ull;  // 2 s per barrier wait
+constexpr uint64_t kBarrierNs = 2000000000ull;  // default limit of one barrier wait: 2 s
 constexpr int kStatusTimeout = -1;              // state status after a barrier timeout
 constexpr int kMaxItems = 64 * 1024;
+
+// Limit of one grid-barrier wait for this context's launches.
+inline uint64_t barrier_wait_ns(const aln_ctx* c) {
+    return c->opt.wait_limit_us > 0 ? (uint64_t)c->opt.wait_limit_us * 1000ull : kBarrierNs;
+}
 
 __device__ __forceinline__ uint64_t p_globaltimer() {
     uint64_t t;
@@ -63,7 +68,8 @@ struct PersistSync {
 // (relaxed loads, one per lane), and once their sum reaches `target` (this
 // barrier's completion count, tracked identically by every block) each
 // polling lane issues an acquire fence before the block continues.
-__device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target) {
+__device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target,
+                                             uint64_t wait_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -95,7 +101,7 @@ __device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target
                 const uint64_t t = p_globaltimer();
                 if (t0 == 0) {
                     t0 = t;
-                } else if (t - t0 > kBarrierNs) {
+                } else if (t - t0 > wait_ns) {
                     atomicExch(&s->timeout, 1u);
                     stop = 1;
                 }
@@ -134,6 +140,8 @@ struct PersistArgs {
     unsigned int* ticket;  // CT
     PersistSync* sync;
     IterState* st;
+    uint64_t wait_ns;      // limit of one grid-barrier wait
+    unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
 // Partial of Σ_{j ∈ group rg, v_j ≠ 0} v_j Q[j, tile ct] into part[rg][tile].
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
         const T yi = in ? __ldcg(a.y + i) : T(0), gi = in ? __ldcg(a.g + i) : T(0);
         tile_mask(a, ct, in, yi, gi, sd, si);
     }
-    bool ok = grid_barrier(a.sync, bar += G);
+    bool ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns);
 
     IterState* st = a.st;
     const double eps = st->eps;
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
             const double k = tile_sum<TILE>((double)gbi * (double)pw, sd);
             if (threadIdx.x == 0) __stcg(a.kitem + it, k);
         }
-        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
 
         // (c) step, projection, gradient update, provisional mask
         if (threadIdx.x < 32) {
@@ -373,7 +381,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
             tile_mask(a, ct, in, yn, gn, sd, si);
         }
         ++iter;
-        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
 
         // (d) clipped correction g += Q e (only when something was clipped)
         if (threadIdx.x < 32) {
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_persist(PersistArgs<T> a)
                 }
                 __syncthreads();
             }
-            if (!(ok = grid_barrier(a.sync, bar += G))) break;
+            if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
         }
     }
 
@@ -467,6 +475,8 @@ struct ReplArgs {
     // be zero, from a block-sparse Gram, are skipped by the products)
     const uint32_t* tmask;
     int tw;
+    uint64_t wait_ns;      // limit of one grid-barrier wait
+    unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
 // Is the 128×128 tile of Q holding row j, column tile ct possibly non-zero?
@@ -832,7 +842,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             if (threadIdx.x == 0) __stcg(kitem + it, k);
         }
         lap(0);
-        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
         lap(1);
 
         // every block: κ (warp 0) while the other warps gather w, α,
@@ -923,7 +933,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2, red,
                                      nullptr, nullptr, a.tmask, a.tw);
             }
-            if (!(ok = grid_barrier(a.sync, bar += G))) break;
+            if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
             sum_partials(a.part2, a.R, a.ldq, n, sg, true);
             __syncthreads();
             ++nclip_iters;
@@ -983,6 +993,8 @@ cudaError_t launch_alg2_persist(aln_ctx* c) {
         r.part2 = (T*)c->part + (int64_t)2 * c->p_R * c->ldq;
         r.kitem = c->p_kpart;
         r.sync = (PersistSync*)c->p_sync;
+        r.wait_ns = barrier_wait_ns(c);
+        r.skew = (unsigned int)c->opt.test_barrier_skew;
         r.st = c->st;
         // zero tiles of Q from the block-sparse Gram (FP32, 128-wide tiles)
         r.tmask = sizeof(T) == 4 ? c->q_tmask : nullptr;
@@ -1014,6 +1026,8 @@ cudaError_t launch_alg2_persist(aln_ctx* c) {
     a.clip = c->p_clip;
     a.ticket = c->p_ticket;
     a.sync = (PersistSync*)c->p_sync;
+    a.wait_ns = barrier_wait_ns(c);
+    a.skew = (unsigned int)c->opt.test_barrier_skew;
     a.st = c->st;
     if ((int64_t)a.CT * a.R > kMaxItems) return cudaErrorInvalidValue;
     void* args[] = {&a};
@@ -1086,6 +1100,8 @@ struct AccArgs {
     int window;       // stagnation window (iterations without a new best ‖ḡ‖²)
     PersistSync* sync;
     IterState* st;
+    uint64_t wait_ns;      // limit of one grid-barrier wait
+    unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
 // ḡ over the replicated vectors: ‖ḡ‖², |P| and the number of non-zero
@@ -1242,7 +1258,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_acc_repl(AccArgs<T> a) {
         }
         ++iter;
         lap(1);
-        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
         lap(2);
         sum_partials(part, a.R, a.ldq, n, sg, true);  // sg still holds ∇f(x_{k−1})
         __syncthreads();
@@ -1288,6 +1304,8 @@ struct PowerArgs {
     int max_steps;
     PersistSync* sync;
     double* out;
+    uint64_t wait_ns;      // limit of one grid-barrier wait
+    unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
 template <typename T>
@@ -1323,7 +1341,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_power_repl(PowerArgs<T> a) {
             (void)mv_item_rep(a.Q, a.ldq, n, a.rows_per_group, sv, ct, rg, part, red);
         }
         ++t;
-        if (!(ok = grid_barrier(a.sync, bar += G))) break;
+        if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
         sum_partials(part, a.R, a.ldq, n, su, false);
         __syncthreads();
         T pr = T(0), pu = T(0);
@@ -1389,6 +1407,8 @@ cudaError_t launch_acc_persist(aln_ctx* c) {
     // iteration has no such stop.
     r.window = sizeof(T) == 8 ? (1 << 30) : 10 * c->opt.stagnation;
     r.sync = (PersistSync*)c->p_sync;
+    r.wait_ns = barrier_wait_ns(c);
+    r.skew = (unsigned int)c->opt.test_barrier_skew;
     r.st = c->st;
     cudaError_t e = cudaFuncSetAttribute(k_acc_repl<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1419,6 +1439,8 @@ cudaError_t launch_power(aln_ctx* c, double tol, int max_steps, double* out) {
     r.tol = tol;
     r.max_steps = max_steps;
     r.sync = (PersistSync*)c->p_sync;
+    r.wait_ns = barrier_wait_ns(c);
+    r.skew = (unsigned int)c->opt.test_barrier_skew;
     r.out = out;
     cudaError_t e = cudaFuncSetAttribute(k_power_repl<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,0 +1,92 @@
+// aln_l2_read_bandwidth: the L2 read rate this GPU sustains over a buffer that
+// stays resident in L2, measured with CUDA events.  It is the ceiling of the
+// Alg. 2 products once Q fits in L2 (the single-problem loop reads the passive
+// rows of an L2-resident Q every iteration), so the benchmark reports those
+// kernels against it beside the HBM copy peak.
+//
+// The kernel is a plain streaming read: every SM runs blocks that read 16-byte
+// vectors with ld.global.cg (cached in L2, not in L1) in a grid-stride loop,
+// and fold them into one word per block so that the loads are not removed.
+#include "common.cuh"
+
+namespace aln {
+namespace {
+
+constexpr int kProbeThreads = 512;
+
+__global__ void __launch_bounds__(kProbeThreads) k_l2_read(const float4* __restrict__ buf,
+                                                           int64_t nvec, float* __restrict__ sink) {
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four independent loads in flight per thread
+    for (; i + 3 * stride < nvec; i += 4 * stride) {
+        const float4 a = __ldcg(buf + i);
+        const float4 b = __ldcg(buf + i + stride);
+        const float4 c = __ldcg(buf + i + 2 * stride);
+        const float4 d = __ldcg(buf + i + 3 * stride);
+        acc += ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)) +
+               ((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w));
+    }
+    for (; i < nvec; i += stride) {
+        const float4 a = __ldcg(buf + i);
+        acc += (a.x + a.y) + (a.z + a.w);
+    }
+    if (acc == 1.2345e-30f) sink[blockIdx.x] = acc;  // never true for the zeroed buffer
+}
+
+}  // namespace
+}  // namespace aln
+
+extern "C" aln_status aln_l2_read_bandwidth(int64_t bytes, int32_t reps, double* gbs) {
+    using namespace aln;
+    if (!gbs || bytes < (1 << 20) || reps < 1) return ALN_ERR_INVALID_ARG;
+    *gbs = 0.0;
+    int dev = 0, sms = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ALN_ERR_CUDA;
+    }
+    if (bytes > (int64_t)l2 * 3 / 4) return ALN_ERR_INVALID_ARG;  // must stay L2-resident
+    bytes = bytes / 16 * 16;
+    void* buf = nullptr;
+    float* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st = nullptr;
+    aln_status rc = ALN_OK;
+    const int blocks = sms * 4;
+    if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess ||
+        cudaMalloc((void**)&sink, (size_t)blocks * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        rc = ALN_ERR_OUT_OF_MEMORY;
+    }
+    if (rc == ALN_OK &&
+        (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+         cudaMemsetAsync(buf, 0, (size_t)bytes, st) != cudaSuccess))
+        rc = ALN_ERR_CUDA;
+    if (rc == ALN_OK) {
+        const int64_t nvec = bytes / 16;
+        for (int w = 0; w < 3; ++w)  // bring the buffer into L2
+            k_l2_read<<<blocks, kProbeThreads, 0, st>>>((const float4*)buf, nvec, sink);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+            k_l2_read<<<blocks, kProbeThreads, 0, st>>>((const float4*)buf, nvec, sink);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) !=
+                                                           cudaSuccess || ms <= 0.f)
+            rc = ALN_ERR_CUDA;
+        else
+            *gbs = (double)bytes * reps / (ms * 1e-3) / 1e9;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (buf) cudaFree(buf);
+    if (sink) cudaFree(sink);
+    cudaGetLastError();
+    return rc;
+}

@@ -42,7 +42,7 @@ def test_library_targets_sm103a_only():
 
 def test_host_only_entry_points(lib):
     from paper_1502_01645_gb300 import aln
-    assert aln.aln_version() == 100
+    assert aln.aln_version() == 200
     o = aln.aln_default_options()
     assert o.precision == aln.PREC_SPLIT_BF16 and o.max_refine == 8 and o.stagnation == 100
     assert aln.status_string(aln.ERR_NONFINITE) == "ALN_ERR_NONFINITE"
@@ -69,10 +69,12 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
     # option checks come before any CUDA call
     for field, bad in (("gram_split", 4), ("group_cluster", 3), ("group_cluster", 16),
-                       ("refine_gain", 17), ("iter_kernel", 3)):
+                       ("refine_gain", 17), ("iter_kernel", 3), ("wait_limit_us", -1),
+                       ("test_barrier_skew", -1), ("test_barrier_skew", 1025)):
         o = aln.aln_default_options()
         setattr(o, field, bad)
         assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
+    assert lib.aln_set_wait_limit(None, 1000, 0) == aln.ERR_INVALID_ARG
     lib.aln_destroy(None)  # accepted
 
 

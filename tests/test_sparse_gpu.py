@@ -331,3 +331,42 @@ def test_csc_kkt_pass_matches_oracle(aln, d, n, band, density):
         assert got[c][0][0] == pytest.approx(ref[c][0][0], rel=1e-10), c
         assert got[c][1][0] == pytest.approx(ref[c][1][0], rel=1e-12), c
     assert got[2][0][0] == pytest.approx(1.0, rel=1e-12)
+
+
+def _rule_tiles(p):
+    """Tile pairs (I, J) of 128 columns whose columns share an occupied 64-row
+    block: the only tiles the block-sparse Gram multiplies, and the tiles the
+    Alg. 2 products read on a CSC context (the rule of the bench's
+    q_tile_fraction)."""
+    cols = np.repeat(np.arange(p.n), np.diff(p.col_ptr))
+    tiles = (p.n + 127) // 128
+    occ = np.zeros((tiles, (p.d + 63) // 64), dtype=np.int64)
+    occ[cols // 128, p.row_idx // 64] = 1
+    return (occ @ occ.T) > 0
+
+
+@pytest.mark.parametrize("d,n,band,density", [(3000, 700, 400, 0.2), (6000, 1000, 300, 0.3)])
+def test_csc_nonzero_tiles_lie_in_the_skip_rule(aln, d, n, band, density):
+    """Every 128×128 tile of Q with a non-zero entry belongs to a pair of
+    column tiles that share an occupied 64-row block, and every tile outside
+    that set is exactly zero — so the products that skip those tiles skip
+    only exact zeros.  The problem has several tile pairs whose row windows
+    never meet."""
+    p = W.banded_tall(d=d, n=n, band=band, density=density, seed=41)
+    Q, _, _ = _export_csc(aln, p)
+    rule = _rule_tiles(p)
+    T = rule.shape[0]
+    assert not rule.all(), "the case must have zero tile pairs"
+    nz = np.zeros((T, T), dtype=bool)
+    for I in range(T):
+        for J in range(T):
+            blk = Q[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128]
+            nz[I, J] = bool(np.any(blk != 0.0))
+    assert not np.any(nz & ~rule), "a non-zero tile outside the skip rule"
+    # the oracle's dense Q is zero exactly outside the rule too (up to pairs
+    # whose shared blocks hold no common row: those are zero in both)
+    Qo, _, _ = _oracle(p)
+    for I in range(T):
+        for J in range(T):
+            if not rule[I, J]:
+                assert np.all(Qo[I * 128:(I + 1) * 128, J * 128:(J + 1) * 128] == 0.0)
