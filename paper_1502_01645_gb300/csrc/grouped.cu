@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "blockops.cuh"
+#include "cluster.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -202,45 +203,7 @@ struct GSolveArgs {
     int smem_bytes;
 };
 
-// --- thread-block clusters (large problems, several CTAs per problem) ------
-__device__ __forceinline__ int cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return (int)r;
-}
-__device__ __forceinline__ int cluster_ctas() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return (int)r;
-}
-// Address of `p` (this CTA's shared memory) in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t cluster_addr(const void* p, int rank) {
-    uint32_t a = (uint32_t)__cvta_generic_to_shared(p), r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ float ld_cluster(uint32_t addr, float) {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ double ld_cluster(uint32_t addr, double) {
-    double v;
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_cluster(uint32_t addr, int v) {
-    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-// Hardware barrier over every thread of every CTA in the cluster, with
-// release/acquire ordering of shared-memory writes across the cluster.  All
-// CTAs of a cluster take the same branches (their state is replicated
-// bit-for-bit and every decision is derived from it), so each reaches every
-// barrier.
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                     : "memory");
-}
+// --- thread-block clusters (large problems, several CTAs per problem): cluster.cuh
 
 // w (+)= Q·v over the listed columns for every row.  With CL, CTA `rank` of
 // the cluster computes rows [rank·S, rank·S + S) into its exchange buffer xb,

@@ -30,6 +30,7 @@
 // wait is bounded (2 s on %globaltimer); on expiry the kernel flags a timeout
 // and every block leaves the loop.
 #include "common.cuh"
+#include "gridsync.cuh"
 #include "kernels.cuh"
 
 namespace aln {
@@ -37,87 +38,7 @@ namespace aln {
 constexpr int kPThreads = 1024;
 constexpr int kPWarps = kPThreads / 32;
 constexpr int kPU = 4;                          // Q rows in flight per warp (64 KB per SM)
-constexpr uint64_t kBarrierNs = 2000000000ull;  // default limit of one barrier wait: 2 s
-constexpr int kStatusTimeout = -1;              // state status after a barrier timeout
 constexpr int kMaxItems = 64 * 1024;
-
-// Limit of one grid-barrier wait for this context's launches.
-inline uint64_t barrier_wait_ns(const aln_ctx* c) {
-    return c->opt.wait_limit_us > 0 ? (uint64_t)c->opt.wait_limit_us * 1000ull : kBarrierNs;
-}
-
-__device__ __forceinline__ uint64_t p_globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-constexpr int kSyncLanes = 8;  // arrival counters, one 128-byte line each
-
-struct PersistSync {
-    // monotonic arrivals spread over kSyncLanes counters (block b adds to
-    // counter b mod kSyncLanes, so the arrivals do not queue on one L2 line);
-    // barrier k completes when their sum reaches k·G
-    unsigned int count[kSyncLanes][32];
-    unsigned int timeout;  // set by the first block whose wait expired
-    unsigned int pad[31];
-};
-
-// Grid barrier over the co-resident grid (cooperative launch).  Arrival is a
-// release reduction on the block's counter; warp 0 then polls all counters
-// (relaxed loads, one per lane), and once their sum reaches `target` (this
-// barrier's completion count, tracked identically by every block) each
-// polling lane issues an acquire fence before the block continues.
-__device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target,
-                                             uint64_t wait_ns) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        if (lane == 0)
-            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(
-                             &s->count[blockIdx.x % kSyncLanes][0]),
-                         "r"(1u)
-                         : "memory");
-        int ok = 1;
-        unsigned int spins = 0;
-        uint64_t t0 = 0;
-        for (;;) {
-            unsigned int v = 0;
-            if (lane < kSyncLanes)
-                asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v)
-                             : "l"(&s->count[lane][0])
-                             : "memory");
-#pragma unroll
-            for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            v = __shfl_sync(0xffffffffu, v, 0);
-            if ((int)(v - target) >= 0) {
-                if (lane < kSyncLanes) asm volatile("fence.acq_rel.gpu;" ::: "memory");
-                break;
-            }
-            __nanosleep(32);
-            int stop = 0;
-            if (lane == 0 && (++spins & 1023u) == 0) {
-                const uint64_t t = p_globaltimer();
-                if (t0 == 0) {
-                    t0 = t;
-                } else if (t - t0 > wait_ns) {
-                    atomicExch(&s->timeout, 1u);
-                    stop = 1;
-                }
-                if (*(volatile unsigned int*)&s->timeout) stop = 1;
-            }
-            if (__shfl_sync(0xffffffffu, stop, 0)) {
-                ok = 0;
-                break;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 template <typename T>
 struct PersistArgs {
@@ -655,6 +576,21 @@ __device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb
 
 constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
 
+// The step α = γ/κ in the iteration type.  FP64: the quotient itself.  FP32:
+// formed on the FP32 pipe (GB300's FP64 divide is a long dependent sequence
+// on a narrow pipe): the quotient of the leading FP32 parts of γ and κ,
+// corrected once with the residual of their FP32-pair splits (one Newton
+// step of the division), within an FP32 ulp or so of (float)(γ/κ).
+template <typename T>
+__device__ __forceinline__ T step_quotient(double gam, double kap) {
+    if (sizeof(T) == 8) return (T)(gam / kap);
+    const float gh = (float)gam, kh = (float)kap;
+    const float gl = (float)(gam - (double)gh), kl = (float)(kap - (double)kh);
+    const float q = __fdiv_rn(gh, kh);
+    const float r = fmaf(-q, kh, gh) + fmaf(-q, kl, gl);
+    return (T)(q + __fdiv_rn(r, kh));
+}
+
 // dst[j] (+)= Σ_r part[r][j] for j < n, r in order.  16-byte loads, two
 // vectors per thread per pass, so that for n up to 8·blockDim.x (FP32) one
 // pass issues all of a thread's loads at once (the partials were written by
@@ -848,9 +784,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         // every block: κ (warp 0) while the other warps gather w, α,
         // projected update, gradient update
         if (threadIdx.x < 32) {
-            double k2 = 0.0;
-            for (int i = threadIdx.x; i < items; i += 32) k2 += __ldcg(kitem + i);
-            k2 = warp_sum(k2);
+            // four independent accumulators per lane, then a pairwise and
+            // a shuffle tree: the FP64 adds form a short dependent chain
+            double kv[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+            for (int i = threadIdx.x, m = 0; i < items; i += 32, m = (m + 1) & 3)
+                kv[m] += __ldcg(kitem + i);
+            double k2 = warp_sum((kv[0] + kv[1]) + (kv[2] + kv[3]));
             if (threadIdx.x == 0) {
                 int stop = 0;
                 if (!isfinite(k2)) {
@@ -860,7 +800,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                     status = ALN_RHS_CURVATURE;
                     stop = 1;
                 }
-                s_alpha = stop ? T(0) : (T)(gam / k2);
+                s_alpha = stop ? T(0) : step_quotient<T>(gam, k2);
                 s_flag = stop;
             }
         }

@@ -4,29 +4,29 @@
 // rows of an L2-resident Q every iteration), so the benchmark reports those
 // kernels against it beside the HBM copy peak.
 //
-// The kernel is a plain streaming read: every SM runs blocks that read 16-byte
-// vectors with ld.global.cg (cached in L2, not in L1) in a grid-stride loop,
-// and fold them into one word per block so that the loads are not removed.
+// The kernel is a plain streaming read: every SM runs two 1024-thread blocks
+// that keep eight 16-byte ld.global.cg loads (cached in L2, not in L1) in
+// flight per thread in a grid-stride loop, and fold them into one word per
+// block so that the loads are not removed.
 #include "common.cuh"
 
 namespace aln {
 namespace {
 
-constexpr int kProbeThreads = 512;
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeLoads = 8;  // independent 16-byte loads in flight per thread
 
 __global__ void __launch_bounds__(kProbeThreads) k_l2_read(const float4* __restrict__ buf,
                                                            int64_t nvec, float* __restrict__ sink) {
     float acc = 0.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    // four independent loads in flight per thread
-    for (; i + 3 * stride < nvec; i += 4 * stride) {
-        const float4 a = __ldcg(buf + i);
-        const float4 b = __ldcg(buf + i + stride);
-        const float4 c = __ldcg(buf + i + 2 * stride);
-        const float4 d = __ldcg(buf + i + 3 * stride);
-        acc += ((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)) +
-               ((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w));
+    for (; i + (kProbeLoads - 1) * stride < nvec; i += kProbeLoads * stride) {
+        float4 v[kProbeLoads];
+#pragma unroll
+        for (int u = 0; u < kProbeLoads; ++u) v[u] = __ldcg(buf + i + u * stride);
+#pragma unroll
+        for (int u = 0; u < kProbeLoads; ++u) acc += (v[u].x + v[u].y) + (v[u].z + v[u].w);
     }
     for (; i < nvec; i += stride) {
         const float4 a = __ldcg(buf + i);
@@ -56,7 +56,7 @@ extern "C" aln_status aln_l2_read_bandwidth(int64_t bytes, int32_t reps, double*
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaStream_t st = nullptr;
     aln_status rc = ALN_OK;
-    const int blocks = sms * 4;
+    const int blocks = sms * 2;
     if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess ||
         cudaMalloc((void**)&sink, (size_t)blocks * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
