@@ -121,8 +121,12 @@ typedef struct aln_options {
     int32_t row_groups;   /* row groups of the single-RHS matvec; 0 = auto */
     int32_t stagnation;   /* stop an inner run after this many iterations without a
                              new smallest ‖ḡ‖² (§5 stop rule); 0 = default 100 */
-    int32_t iter_kernel;  /* persistent Alg. 2 kernel: 0 auto (replicated state when
-                             the vectors fit in shared memory), 1 tiled, 2 replicated */
+    int32_t iter_kernel;  /* persistent Alg. 2 kernel: 0 auto (FP64 with n up to
+                             about 460: one thread-block cluster holding Q in
+                             shared memory; else replicated state when the
+                             vectors fit in shared memory; else tiled),
+                             1 tiled, 2 replicated, 3 one cluster (FP64 only,
+                             falls back to 0's choice where Q does not fit) */
     int32_t batch_min;    /* SPLIT_BF16 with at least this many right-hand sides
                              runs the batched solver (all columns advance together,
                              tcgen05 products Q·Ḡ); 0 = default 8 */

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaln.so")
 SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "iter.cu", "persist.cu", "kkt.cu", "noalloc.cu",
-           "batch.cu", "grouped.cu", "mlp.cu", "nmf.cu", "sparse.cu", "probe.cu"]
+           "batch.cu", "grouped.cu", "mlp.cu", "nmf.cu", "sparse.cu", "probe.cu",
+           "small64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -138,6 +138,16 @@ aln_status alloc_workspace(aln_ctx* c) {
     c->p_ticket = (unsigned int*)take(ct * 8);
     c->p_sync = take(persist_sync_bytes());
     ALN_TRY(cudaMemsetAsync(c->iter_pool, 0, c->iter_bytes, c->stream));
+    // A small FP64 problem runs its loop on one thread-block cluster
+    // (iter_kernel 0 = auto or 3).
+    c->p_small = 0;
+    if (fp64(c) && c->opt.algorithm == ALN_ALG_ANTILOP &&
+        (c->opt.iter_kernel == 0 || c->opt.iter_kernel == 3)) {
+        int optin = 0;
+        ALN_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                       c->device));
+        c->p_small = small64_fits(c, optin) ? 1 : 0;
+    }
 
     // KKT: x64 (ldq), g64 (ldq), r64 (d), rpart (CG·d), parts, out
     const int64_t row_blocks = ceil_div(d, 1024);  // k_kkt_ax: 4 rows × 256 threads
@@ -174,6 +184,8 @@ aln_status run_until_done(aln_ctx* c) {
     ALN_TRY(cudaEventRecord(c->ev[6], c->stream));
     if (c->opt.algorithm == ALN_ALG_ANTI_ACC)
         ALN_TRY(fp64(c) ? launch_acc_persist<double>(c) : launch_acc_persist<float>(c));
+    else if (c->p_small && c->opt.test_barrier_skew == 0)  // (the knob tests grid barriers)
+        ALN_TRY(launch_alg2_small64(c));
     else
         ALN_TRY(fp64(c) ? launch_alg2_persist<double>(c) : launch_alg2_persist<float>(c));
     ALN_TRY(cudaEventRecord(c->ev[7], c->stream));
@@ -188,7 +200,7 @@ aln_status run_until_done(aln_ctx* c) {
     c->stats.clipped_rows += c->st_host->sum_clip;
     c->stats.product_bytes += (double)(fp64(c) ? 8 : 4) * (double)c->n *
                               (double)(c->st_host->sum_passive + c->st_host->sum_clip);
-    if (c->p_repl) {
+    if (c->p_repl || c->p_small) {
         for (int k = 0; k < 5; ++k) c->stats.phase_us[k] += 1e-3 * (double)c->st_host->phase_ns[k];
         c->stats.clipped_iterations += (int32_t)c->st_host->phase_ns[5];
     }
@@ -371,7 +383,7 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.precision != ALN_PREC_FP64 && o.precision != ALN_PREC_SPLIT_BF16)
         return ALN_ERR_INVALID_ARG;
     if (o.max_refine < 0 || o.persist_blocks < 0 || o.row_groups < 0 || o.stagnation < 0 ||
-        o.iter_kernel < 0 || o.iter_kernel > 2 || o.batch_min < 0)
+        o.iter_kernel < 0 || o.iter_kernel > 3 || o.batch_min < 0)
         return ALN_ERR_INVALID_ARG;
     if (o.stagnation == 0) o.stagnation = 100;
     if (o.batch_min == 0) o.batch_min = 8;
@@ -444,7 +456,7 @@ void aln_destroy(aln_ctx* c) {
     mlp_free(c);
     nmf_free(c);
     void* bufs[] = {c->A_copy, c->B_copy,    c->Q,        c->prep_pool, c->A_hi,
-                    c->iter_pool, c->kkt_pool, c->csc_pool, c->sp_part};
+                    c->iter_pool, c->kkt_pool, c->csc_pool, c->sp_part, c->g64_work};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->den_host) cudaFreeHost(c->den_host);
@@ -580,9 +592,12 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
         ;  // the Gram ran chunk by chunk above
     else if (c->batched)
         ALN_CHECK(batch_prepare(c));
-    else if (f64)
-        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
-    else
+    else if (f64) {
+        ALN_CHECK(ensure(&c->g64_work, &c->g64_work_bytes,
+                         gram64_split_bytes(d, n, c->num_sms)));
+        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream,
+                              (double*)c->g64_work, c->g64_work_bytes, c->num_sms));
+    } else
         ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
                                (float*)c->Q, ldq, c->flags + 1, c->stream, 0, -1, gpart, gticket,
                                gsplit));
@@ -774,7 +789,10 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     } else if (c->batched) {
         ALN_CHECK(batch_prepare(c));
     } else {
-        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream));
+        ALN_CHECK(ensure(&c->g64_work, &c->g64_work_bytes,
+                         gram64_split_bytes(d, n, c->num_sms)));
+        ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream,
+                              (double*)c->g64_work, c->g64_work_bytes, c->num_sms));
         ++c->launches;
     }
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));

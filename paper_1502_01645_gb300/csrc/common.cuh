@@ -232,6 +232,8 @@ struct aln_ctx {
     double* csc_fpart = nullptr;
     int csc_W = 0;
     size_t csc_box_bytes = 0;  // one split term's packed boxes in A_hi
+    void* g64_work = nullptr;  // split-K partial tiles of the FP64 Gram (small n)
+    size_t g64_work_bytes = 0;
     void* sp_part = nullptr;   // split-K partial tiles of the block-sparse Gram
     size_t sp_part_bytes = 0;
     // tiles of Q that may be non-zero (block-sparse Gram; null = all): bit rt
@@ -272,6 +274,7 @@ struct aln_ctx {
     // persistent Alg. 2 kernel geometry and its per-tile partials
     int p_CT = 0, p_R = 0, p_G = 0;
     int p_repl = 0;  // 1: replicated-state kernel (vectors fit in shared memory)
+    int p_small = 0; // 1: FP64 loop on one thread-block cluster (small n, small64.cu)
     double lipschitz = -1.0;  // Anti+Acc: L = λ_max(Q) estimate (< 0: not computed)
     int power_products = 0;   // products of the power iteration that gave it
     double* p_gpart = nullptr;

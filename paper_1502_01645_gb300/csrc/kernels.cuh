@@ -8,6 +8,7 @@
 namespace aln {
 
 constexpr int MODE_GRAM = 0;
+constexpr int MODE_PART = 3;  // raw partial tile of a K range (split-K Gram)
 constexpr int MODE_QVEC = 1;
 constexpr int MODE_AXPY = 2;
 
@@ -20,8 +21,14 @@ cudaError_t launch_check_finite(const void* X, int32_t dtype, int64_t rows, int6
                                 int64_t ld, int* flags, cudaStream_t st);
 cudaError_t launch_denominators(const double* q64, int64_t n, int64_t ldq, int64_t k, double* den,
                                 cudaStream_t st);
+// FP64 Gram → Q.  With a workspace (`work`, `work_bytes`) and fewer lower-
+// triangle tiles than `num_sms`, the K range is split over several CTAs per
+// tile whose partial tiles are added in chunk order by a second kernel
+// (deterministic); gram64_split_bytes gives the workspace that needs.
 cudaError_t launch_gram64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
-                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st);
+                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st,
+                          double* work = nullptr, size_t work_bytes = 0, int num_sms = 0);
+size_t gram64_split_bytes(int64_t d, int64_t n, int num_sms);
 cudaError_t launch_qvec64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
                           const void* B, int64_t k, int64_t ldb, const double* inv_s, double* q64,
                           int64_t ldq, cudaStream_t st);
@@ -174,6 +181,9 @@ cudaError_t launch_power(aln_ctx* c, double tol, int max_steps, double* out);
 template <typename T>
 int persist_max_blocks(int num_sms, int64_t ldq, int* repl);
 size_t persist_sync_bytes();
+// small64.cu — the FP64 Alg. 2 loop of one small problem on one cluster
+bool small64_fits(const aln_ctx* c, int optin_smem);
+cudaError_t launch_alg2_small64(aln_ctx* c);
 
 // sparse.cu — Alg. 1 from a CSC matrix (col_ptr int64[n+1], row_idx int32,
 // values of dtype); see the kernels there.

@@ -161,8 +161,14 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
     __shared__ double Xs[kG64K][kG64Tile];
     __shared__ double Ys[kG64K][kG64Tile];
     int tm, tn;
+    int64_t kbeg = 0, kend = K;
     if (MODE == MODE_GRAM) {
         tri_decode(blockIdx.x, tm, tn);
+    } else if (MODE == MODE_PART) {
+        // tiles_m = lower-triangle tiles T, ldo = the K-chunk length
+        tri_decode(blockIdx.x % tiles_m, tm, tn);
+        kbeg = (int64_t)(blockIdx.x / tiles_m) * ldo;
+        kend = min(K, kbeg + ldo);
     } else {
         tm = blockIdx.x % tiles_m;
         tn = blockIdx.x / tiles_m;
@@ -175,15 +181,15 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-    for (int64_t k0 = 0; k0 < K; k0 += kG64K) {
+    for (int64_t k0 = kbeg; k0 < kend; k0 += kG64K) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = threadIdx.x + 256 * u;
             const int kk = e & 15, ii = e >> 4;
             const int64_t gk = k0 + kk;
             const int64_t gi = i0 + ii, gj = j0 + ii;
-            Xs[kk][ii] = (gi < M && gk < K) ? (double)X[gi * ldx + gk] : 0.0;
-            Ys[kk][ii] = (gj < N && gk < K) ? (double)Y[gj * ldy + gk] : 0.0;
+            Xs[kk][ii] = (gi < M && gk < kend) ? (double)X[gi * ldx + gk] : 0.0;
+            Ys[kk][ii] = (gj < N && gk < kend) ? (double)Y[gj * ldy + gk] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -201,6 +207,14 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
         __syncthreads();
     }
 
+    if (MODE == MODE_PART) {  // the raw partial tile of this K chunk
+        double* t = out + (int64_t)blockIdx.x * kG64Tile * kG64Tile;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) t[(ty + 16 * a) * kG64Tile + tx + 16 * b] = acc[a][b];
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int64_t i = i0 + ty + 16 * a;
@@ -248,8 +262,14 @@ __global__ void __launch_bounds__(256) k_atb32_dot2(const float* __restrict__ X,
     __shared__ float Xs[kG64K][kG64Tile];
     __shared__ float Ys[kG64K][kG64Tile];
     int tm, tn;
+    int64_t kbeg = 0, kend = K;
     if (MODE == MODE_GRAM) {
         tri_decode(blockIdx.x, tm, tn);
+    } else if (MODE == MODE_PART) {
+        // tiles_m = lower-triangle tiles T, ldo = the K-chunk length
+        tri_decode(blockIdx.x % tiles_m, tm, tn);
+        kbeg = (int64_t)(blockIdx.x / tiles_m) * ldo;
+        kend = min(K, kbeg + ldo);
     } else {
         tm = blockIdx.x % tiles_m;
         tn = blockIdx.x / tiles_m;
@@ -500,10 +520,64 @@ cudaError_t launch_denominators(const double* q64, int64_t n, int64_t ldq, int64
     return cudaGetLastError();
 }
 
+// Split-K finish: tile t of Q is the sum of its `chunks` partial tiles in
+// chunk order, then the MODE_GRAM epilogue (scaling, unit diagonal, mirror).
+__global__ void __launch_bounds__(256) k_gram64_finish(const double* __restrict__ part, int T,
+                                                        int chunks, int64_t n,
+                                                        const double* __restrict__ inv_s,
+                                                        double* __restrict__ out, int64_t ldo) {
+    int tm, tn;
+    tri_decode(blockIdx.x, tm, tn);
+    constexpr int kTT = kG64Tile * kG64Tile;
+    for (int e = threadIdx.x; e < kTT; e += blockDim.x) {
+        const int64_t i = (int64_t)tm * kG64Tile + e / kG64Tile;
+        const int64_t j = (int64_t)tn * kG64Tile + e % kG64Tile;
+        if (i >= n || j >= n || j > i) continue;
+        double acc = 0.0;
+        for (int ch = 0; ch < chunks; ++ch) acc += part[((int64_t)ch * T + blockIdx.x) * kTT + e];
+        double v = acc * inv_s[i] * inv_s[j];
+        if (i == j) v = acc != 0.0 ? 1.0 : 0.0;
+        out[i * ldo + j] = v;
+        out[j * ldo + i] = v;
+    }
+}
+
+// K chunks of the split Gram: one wave of CTAs over the lower-triangle tiles,
+// each chunk at least 64 rows of A; 1 (no split) when the tiles fill the GPU.
+static int gram64_chunks(int64_t d, int64_t n, int num_sms) {
+    const int64_t tm = ceil_div(n, kG64Tile);
+    const int64_t T = tm * (tm + 1) / 2;
+    if (num_sms <= 0 || 2 * T > num_sms) return 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(num_sms / T, ceil_div(d, 64)));
+}
+
+size_t gram64_split_bytes(int64_t d, int64_t n, int num_sms) {
+    const int ch = gram64_chunks(d, n, num_sms);
+    if (ch <= 1) return 0;
+    const int64_t tm = ceil_div(n, kG64Tile);
+    return (size_t)ch * (size_t)(tm * (tm + 1) / 2) * kG64Tile * kG64Tile * sizeof(double);
+}
+
 cudaError_t launch_gram64(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
-                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st) {
+                          const double* inv_s, double* Q, int64_t ldq, cudaStream_t st,
+                          double* work, size_t work_bytes, int num_sms) {
     const int64_t tm = ceil_div(n, kG64Tile);
     const int64_t tiles = tm * (tm + 1) / 2;
+    const int chunks = gram64_chunks(d, n, num_sms);
+    if (chunks > 1 && work && work_bytes >= gram64_split_bytes(d, n, num_sms)) {
+        // few tiles (small n): split the K range so that every SM works
+        const int64_t kc = round_up(ceil_div(d, (int64_t)chunks), kG64K);
+        const int nch = (int)ceil_div(d, kc);
+        const unsigned grid = (unsigned)(tiles * nch);
+        if (dtype == ALN_DTYPE_F32)
+            k_atb64<float, float, MODE_PART><<<grid, 256, 0, st>>>(
+                (const float*)A, lda, (const float*)A, lda, d, n, n, (int)tiles, inv_s, work, kc);
+        else
+            k_atb64<double, double, MODE_PART><<<grid, 256, 0, st>>>(
+                (const double*)A, lda, (const double*)A, lda, d, n, n, (int)tiles, inv_s, work, kc);
+        k_gram64_finish<<<(unsigned)tiles, 256, 0, st>>>(work, (int)tiles, nch, n, inv_s, Q, ldq);
+        return cudaGetLastError();
+    }
     if (dtype == ALN_DTYPE_F32)
         k_atb64<float, float, MODE_GRAM><<<(unsigned)tiles, 256, 0, st>>>(
             (const float*)A, lda, (const float*)A, lda, d, n, n, (int)tm, inv_s, Q, ldq);

@@ -69,7 +69,7 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
     # option checks come before any CUDA call
     for field, bad in (("gram_split", 4), ("group_cluster", 3), ("group_cluster", 16),
-                       ("refine_gain", 17), ("iter_kernel", 3), ("wait_limit_us", -1),
+                       ("refine_gain", 17), ("iter_kernel", 4), ("wait_limit_us", -1),
                        ("test_barrier_skew", -1), ("test_barrier_skew", 1025)):
         o = aln.aln_default_options()
         setattr(o, field, bad)
