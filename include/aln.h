@@ -282,19 +282,23 @@ aln_status aln_export_scaled(aln_ctx* ctx, double* Q, int64_t ldq, double* q, in
 /* ---------------------------------------------------------------------------
  * Learned start point (not in the paper: Alg. 2 starts at x⁰ = 0 in §3, and a
  * given x⁰ maps to y⁰ = x⁰·√H_ii by Eq. Rescaling).  A network predicts y⁰ in
- * the scaled space from q for a fixed A:
- *   u  = [ (q/‖q‖ − μ)/σ ; z ],  μ, σ per entry over the training set,
- *        z_j = (log s_j − mean)/std over j (std := 1 if 0)
- *   h1 = relu(W1 u + b1), h2 = relu(W2 h1 + b2), [ŷ ; ℓ] = W3 h2 + b3
+ * the scaled space from q for a fixed A (a fixed scaled matrix Q):
+ *   z  = −Q⁻¹q, the unconstrained minimiser of ½yᵀQy + qᵀy (Q⁻¹ formed once
+ *        per network on the GPU by a Newton–Schulz iteration in FP32)
+ *   u  = [ (q/‖q‖ − μ)/σ ; (z/‖q‖ − μz)/σz ],  μ, σ, μz, σz per entry over
+ *        the training set (both parts 0 when q = 0)
+ *   h1 = relu(W1 u + b1), h2 = relu(W2 h1 + b2), [r ; ℓ′] = W3 h2 + b3
+ *   ŷ  = r + e ⊙ ẑ,  ℓ = ℓ′ + f ⊙ ẑ,  ẑ = z/(τ‖q‖)  (per-entry skips)
  *   d  = relu(ŷ)·[ℓ > 0], y⁰ = α*·d with α* = max(0, −qᵀd/dᵀQd), the exact
  *        line search of Alg. 2 from 0 along d, so f(y⁰) ≤ f(0) = 0
- * W1 is hidden×2n, W2 hidden×hidden, W3 2n×hidden (row-major, FP32 master
- * copies; products in BF16 on the tensor cores with FP32 accumulation).
+ * W1 is hidden×2n, W2 hidden×hidden, W3 2n×hidden (row-major), e and f have
+ * n entries (FP32 master copies; the layer products in BF16 on the tensor
+ * cores with FP32 accumulation, z in FP32).
  * Training minimises mean (ŷ − y* / (τ‖q‖))² + mean BCE(ℓ, [y* > 0]) with
- * Adam; τ is the RMS of y* / ‖q‖ over the training set.
+ * Adam over every parameter; τ is the RMS of y* / ‖q‖ over the training set.
  * All calls need a context prepared with aln_prepare (not grouped); the
- * network belongs to that A (its n and scale factors) and survives later
- * aln_prepare calls with new right-hand sides.
+ * network belongs to that A (its n and Q⁻¹) and survives later aln_prepare
+ * calls with new right-hand sides.
  * ------------------------------------------------------------------------- */
 typedef struct aln_train_opts {
     int32_t epochs;   /* passes over the training pairs; default 10 */
@@ -311,20 +315,25 @@ typedef struct aln_train_opts {
 
 void aln_default_train_opts(aln_train_opts* opts);
 
-/* Create (or re-create) the network for the prepared n with He-uniform
- * weights from `seed` and zero biases.  hidden ≥ 1.
- * Errors: INVALID_ARG, NOT_PREPARED, OUT_OF_MEMORY, CUDA. */
+/* Create (or re-create) the network for the prepared A: He-uniform weights
+ * from `seed`, zero biases, skips e = 1 and f = 4 (ŷ follows ẑ and ℓ its
+ * sign), and Q⁻¹ of the prepared Q (Newton–Schulz from I/‖Q‖∞ until
+ * ‖I − Q·X‖_F < 1e-4 or stops falling; Q must be positive definite, as it is
+ * for A of full column rank).  hidden ≥ 1.
+ * Errors: INVALID_ARG, NOT_PREPARED, NONFINITE (the iteration diverged: Q
+ * singular), OUT_OF_MEMORY, CUDA. */
 aln_status aln_warmstart_init(aln_ctx* ctx, int32_t hidden, uint64_t seed);
 
 /* Copy the FP32 parameters in (set = 1) or out (set = 0); any pointer may be
  * NULL to skip that tensor; host or device memory.  Shapes as above, biases
- * of length hidden, hidden, 2n; mu, sd (n each) and tau (1) are the feature
- * and target normalisation (defaults 0, 1, 1; the first aln_warmstart_train
- * sets them from its training set unless they were set here).
+ * of length hidden, hidden, 2n, skips e, f of length n; mu, sd, muz, sdz (n
+ * each) and tau (1) are the feature and target normalisation (defaults 0, 1,
+ * 0, 1, 1; the first aln_warmstart_train sets them from its training set
+ * unless they were set here).
  * Errors: INVALID_ARG (no network), CUDA. */
 aln_status aln_warmstart_params(aln_ctx* ctx, int32_t set, float* W1, float* b1, float* W2,
-                                float* b2, float* W3, float* b3, float* mu, float* sd,
-                                float* tau);
+                                float* b2, float* W3, float* b3, float* e, float* f, float* mu,
+                                float* sd, float* muz, float* sdz, float* tau);
 
 /* One forward and backward pass without an update, on `count` pairs:
  * Qb (count×n, the scaled q of each right-hand side, row-major FP64) and Yb
@@ -333,7 +342,7 @@ aln_status aln_warmstart_params(aln_ctx* ctx, int32_t set, float* W1, float* b1,
  * Errors: INVALID_ARG, TIMEOUT, OUT_OF_MEMORY, CUDA. */
 aln_status aln_warmstart_grad(aln_ctx* ctx, const double* Qb, const double* Yb, int64_t count,
                               double* loss, float* gW1, float* gb1, float* gW2, float* gb2,
-                              float* gW3, float* gb3);
+                              float* gW3, float* gb3, float* ge, float* gf);
 
 /* Train on `count` pairs (Qtrain, Ytrain as in aln_warmstart_grad; host or
  * device).  Creates the network first when there is none.  epoch_loss: NULL

@@ -7,70 +7,94 @@ CUDA library and imports nothing from it.
 
 The paper starts Alg. 2 at x⁰ = 0 and maps a start point with y⁰ = x⁰·√H_ii
 (Eq. Rescaling, Fig. 2).  A learned start point is not in the paper; this
-module defines the one the library implements, in plain numpy float64:
+module defines the one the library implements, in plain numpy float64.  For a
+fixed A (so a fixed scaled matrix Q of Eq. NQPQ) and a right-hand side with
+scaled linear term q:
 
-  features   u = [ (q/‖q‖ − μ)/σ ; z ],  z_j = (log s_j − mean log s)/std log s
-             (q is the scaled linear term of Eq. NQPQ for one right-hand side,
-             s_j = √H_jj; μ_j, σ_j are the mean and standard deviation of
-             q_j/‖q‖ over the training set (σ_j := 1 if 0); z depends on A
-             only, std := 1 if it is 0; the q-part is q/‖q‖ = 0 when q = 0)
+  direction  z = −Q⁻¹q, the unconstrained minimiser of ½yᵀQy + qᵀy (Q is
+             positive definite when A has full column rank)
+  features   u = [ (q/‖q‖ − μ)/σ ; (z/‖q‖ − μz)/σz ]  (μ, σ, μz, σz per entry
+             over the training set, σ := 1 where 0; both parts are 0 when
+             q = 0)
   network    h1 = relu(W1 u + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3,
-             o = [ ŷ ; ℓ ]  (ŷ and the logits ℓ have n entries each)
-  start      direction d = relu(ŷ)·[ℓ > 0], then the exact line search of
-             Alg. 2 along it from 0: y⁰ = α*·d, α* = max(0, −qᵀd / dᵀQd)
-             (0 when dᵀQd = 0).  So f(y⁰) = ½y⁰ᵀQy⁰ + qᵀy⁰ ≤ f(0): the start is
-             never worse than x⁰ = 0, and y⁰ = 0 when the direction does not
-             descend.
-  loss       L = mean (ŷ − y*/(τ‖q‖))² + mean BCE(ℓ, [y* > 0]), both means over
-             the batch and the n outputs; BCE(ℓ, c) = log(1 + e^ℓ) − c·ℓ;
+             o = [ r ; ℓ′ ]  (n entries each), and per-entry skips from the
+             direction in the target's scale, ẑ = z/(τ‖q‖):
+             ŷ = r + e ⊙ ẑ,   ℓ = ℓ′ + f ⊙ ẑ
+  start      d = relu(ŷ)·[ℓ > 0], then the exact line search of Alg. 2 along
+             it from 0: y⁰ = α*·d, α* = max(0, −qᵀd / dᵀQd) (0 when
+             dᵀQd = 0), so f(y⁰) ≤ f(0) and y⁰ = 0 when d does not descend
+  loss       L = mean (ŷ − y*/(τ‖q‖))² + mean BCE(ℓ, [y* > 0]), means over the
+             batch and the n outputs; BCE(ℓ, c) = log(1 + e^ℓ) − c·ℓ;
              τ = RMS of y*/‖q‖ over the training set (1 if 0)
-  training   Adam (Kingma & Ba 2015) with bias correction.
+  training   Adam (Kingma & Ba 2015) with bias correction, every parameter
+             (W1, b1, W2, b2, W3, b3, e, f).
 
-Parameters are a dict {W1, b1, W2, b2, W3, b3}; W_l has shape (out, in).  The
-normalisation statistics (μ, σ, τ) are a dict {mu, sd, tau}; None means
-μ = 0, σ = 1, τ = 1.
+The inverse Q⁻¹ is computed once per A (``numpy.linalg.inv`` here); it is a
+feature transform, not a parameter.  Parameters are a dict {W1, b1, W2, b2, W3,
+b3, e, f}; W_l has shape (out, in).  The normalisation statistics are a dict
+{mu, sd, muz, sdz, tau}; None means μ = μz = 0, σ = σz = 1, τ = 1.
 """
 from __future__ import annotations
 
 import numpy as np
 
-PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3")
+PARAM_NAMES = ("W1", "b1", "W2", "b2", "W3", "b3", "e", "f")
+SKIP_INIT = (1.0, 4.0)  # e, f at initialisation: ŷ follows ẑ, ℓ its sign
 
 
 def _unit(q):
     qn = np.linalg.norm(q, axis=1)
-    qpart = np.zeros_like(q)
+    inv = np.zeros_like(qn)
     nz = qn > 0
-    qpart[nz] = q[nz] / qn[nz, None]
-    return qpart, qn
+    inv[nz] = 1.0 / qn[nz]
+    return qn, inv
 
 
-def stats(q, Y):
-    """μ, σ of q/‖q‖ per entry and τ = RMS of y*/‖q‖, over a training set."""
+def direction(q, Qinv):
+    """z = −Q⁻¹q for a batch of q (B, n)."""
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    qpart, qn = _unit(q)
-    sd = qpart.std(axis=0)
+    return -(q @ np.asarray(Qinv, dtype=np.float64).T)
+
+
+def stats(q, Y, Qinv):
+    """μ, σ of q/‖q‖, μz, σz of z/‖q‖ per entry and τ = RMS of y*/‖q‖ over a
+    training set."""
+    q = np.atleast_2d(np.asarray(q, dtype=np.float64))
+    qn, inv = _unit(q)
+    qp = q * inv[:, None]
+    zp = direction(q, Qinv) * inv[:, None]
+    sd = qp.std(axis=0)
     sd[sd == 0] = 1.0
+    sdz = zp.std(axis=0)
+    sdz[sdz == 0] = 1.0
     T, _ = targets(Y, qn)
     tau = float(np.sqrt(np.mean(T ** 2)))
-    return {"mu": qpart.mean(axis=0), "sd": sd, "tau": tau if tau > 0 else 1.0}
+    return {"mu": qp.mean(axis=0), "sd": sd, "muz": zp.mean(axis=0), "sdz": sdz,
+            "tau": tau if tau > 0 else 1.0}
 
 
-def features(q, s, st=None):
-    """u = [(q/‖q‖ − μ)/σ ; z] for a batch of q (B, n) and scale factors s (n,)."""
+def features(q, Qinv, st=None):
+    """(u, ‖q‖, ẑ) for a batch of q (B, n): u = [(q/‖q‖ − μ)/σ ; (z/‖q‖ − μz)/σz]
+    and the skip input ẑ = z/(τ‖q‖) (0 where q = 0)."""
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    s = np.asarray(s, dtype=np.float64)
-    qpart, qn = _unit(q)
+    qn, inv = _unit(q)
+    qp = q * inv[:, None]
+    zp = direction(q, Qinv) * inv[:, None]
+    tau = 1.0
     if st is not None:
-        qpart = (qpart - st["mu"]) / st["sd"]
-    ls = np.log(s)
-    sd = ls.std()
-    z = (ls - ls.mean()) / (sd if sd > 0 else 1.0)
-    return np.hstack([qpart, np.broadcast_to(z, q.shape)]), qn
+        qp = (qp - st["mu"]) / st["sd"]
+        zp_n = (zp - st["muz"]) / st["sdz"]
+        tau = st["tau"]
+    else:
+        zp_n = zp
+    qp[qn == 0] = 0.0
+    zp_n[qn == 0] = 0.0
+    return np.hstack([qp, zp_n]), qn, zp / tau
 
 
 def init_params(n_in, hidden, n_out, seed=0):
-    """He-uniform weights, zero biases (any start is valid for the oracle)."""
+    """He-uniform weights, zero biases, skips at SKIP_INIT (any start is valid
+    for the oracle)."""
     r = np.random.default_rng(seed)
     p = {}
     dims = [(hidden, n_in), (hidden, hidden), (n_out, hidden)]
@@ -78,16 +102,22 @@ def init_params(n_in, hidden, n_out, seed=0):
         lim = np.sqrt(6.0 / i)
         p[f"W{l}"] = r.uniform(-lim, lim, (o, i))
         p[f"b{l}"] = np.zeros(o)
+    n = n_out // 2
+    p["e"] = np.full(n, SKIP_INIT[0])
+    p["f"] = np.full(n, SKIP_INIT[1])
     return p
 
 
-def forward(p, U):
-    """The network on a batch U (B, 2n); returns the output and the cache."""
+def forward(p, U, zt):
+    """The network on a batch U (B, 2n) with skip input zt (B, n); returns
+    o = [ŷ ; ℓ] (skips included) and the cache."""
     Z1 = U @ p["W1"].T + p["b1"]
     H1 = np.maximum(Z1, 0.0)
     Z2 = H1 @ p["W2"].T + p["b2"]
     H2 = np.maximum(Z2, 0.0)
     O = H2 @ p["W3"].T + p["b3"]
+    n = O.shape[1] // 2
+    O = np.hstack([O[:, :n] + p["e"] * zt, O[:, n:] + p["f"] * zt])
     return O, (U, Z1, H1, Z2, H2)
 
 
@@ -96,23 +126,26 @@ def bce(logit, c):
     return np.maximum(logit, 0.0) - logit * c + np.log1p(np.exp(-np.abs(logit)))
 
 
-def loss(p, U, T, C):
-    """L for targets T = y*/‖q‖ and classes C = [y* > 0], both (B, n)."""
-    O, _ = forward(p, U)
+def loss(p, U, zt, T, C):
+    """L for targets T = y*/(τ‖q‖) and classes C = [y* > 0], both (B, n)."""
+    O, _ = forward(p, U, zt)
     n = T.shape[1]
     yh, lg = O[:, :n], O[:, n:]
     return float(np.mean((yh - T) ** 2) + np.mean(bce(lg, C)))
 
 
-def loss_and_grad(p, U, T, C):
+def loss_and_grad(p, U, zt, T, C):
     """L and its gradient with respect to every parameter (backpropagation)."""
-    O, (U, Z1, H1, Z2, H2) = forward(p, U)
+    O, (U, Z1, H1, Z2, H2) = forward(p, U, zt)
     B, n = T.shape
     yh, lg = O[:, :n], O[:, n:]
     L = float(np.mean((yh - T) ** 2) + np.mean(bce(lg, C)))
     m = B * n
-    dO = np.hstack([2.0 * (yh - T) / m, (1.0 / (1.0 + np.exp(-lg)) - C) / m])
-    g = {"W3": dO.T @ H2, "b3": dO.sum(axis=0)}
+    dy = 2.0 * (yh - T) / m
+    dl = (1.0 / (1.0 + np.exp(-lg)) - C) / m
+    dO = np.hstack([dy, dl])
+    g = {"W3": dO.T @ H2, "b3": dO.sum(axis=0),
+         "e": (dy * zt).sum(axis=0), "f": (dl * zt).sum(axis=0)}
     dH2 = dO @ p["W3"]
     dZ2 = dH2 * (Z2 > 0)
     g["W2"] = dZ2.T @ H1
@@ -151,12 +184,12 @@ def targets(Y, qn, tau=1.0):
     return T, (Y > 0).astype(np.float64)
 
 
-def predict(p, q, s, Q, st=None):
+def predict(p, q, Qinv, Q, st=None):
     """Start points y⁰ (B, n) in the scaled space: the predicted direction
     scaled by the exact line search from 0 (α* ≥ 0)."""
     q = np.atleast_2d(np.asarray(q, dtype=np.float64))
-    U, _ = features(q, s, st)
-    O, _ = forward(p, U)
+    U, _, zt = features(q, Qinv, st)
+    O, _ = forward(p, U, zt)
     n = q.shape[1]
     d = np.maximum(O[:, :n], 0.0) * (O[:, n:] > 0)
     num = -np.einsum("bi,bi->b", q, d)
@@ -167,12 +200,12 @@ def predict(p, q, s, Q, st=None):
     return alpha[:, None] * d
 
 
-def train(p, Qs, Ys, s, epochs=1, batch=256, lr=1e-3, seed=0, st=None):
+def train(p, Qs, Ys, Qinv, epochs=1, batch=256, lr=1e-3, seed=0, st=None):
     """Minibatch Adam over (q, y*) pairs; returns the mean loss of each epoch.
-    ``st`` (normalisation statistics) defaults to stats(Qs, Ys)."""
+    ``st`` (normalisation statistics) defaults to stats(Qs, Ys, Qinv)."""
     if st is None:
-        st = stats(Qs, Ys)
-    U, qn = features(Qs, s, st)
+        st = stats(Qs, Ys, Qinv)
+    U, qn, zt = features(Qs, Qinv, st)
     T, C = targets(Ys, qn, st["tau"])
     ad = adam_init(p)
     r = np.random.default_rng(seed)
@@ -182,7 +215,7 @@ def train(p, Qs, Ys, s, epochs=1, batch=256, lr=1e-3, seed=0, st=None):
         tot, cnt = 0.0, 0
         for i in range(0, len(U), batch):
             idx = perm[i:i + batch]
-            L, g = loss_and_grad(p, U[idx], T[idx], C[idx])
+            L, g = loss_and_grad(p, U[idx], zt[idx], T[idx], C[idx])
             adam_step(p, g, ad, lr=lr)
             tot += L * len(idx)
             cnt += len(idx)

@@ -124,9 +124,9 @@ def load(path: str | None = None):
     lib.aln_default_train_opts.restype = None
     lib.aln_warmstart_init.argtypes = [vp, i32, ctypes.c_uint64]
     lib.aln_warmstart_init.restype = ctypes.c_int
-    lib.aln_warmstart_params.argtypes = [vp, i32] + [vp] * 9
+    lib.aln_warmstart_params.argtypes = [vp, i32] + [vp] * 13
     lib.aln_warmstart_params.restype = ctypes.c_int
-    lib.aln_warmstart_grad.argtypes = [vp, dp, dp, i64, dp] + [vp] * 6
+    lib.aln_warmstart_grad.argtypes = [vp, dp, dp, i64, dp] + [vp] * 8
     lib.aln_warmstart_grad.restype = ctypes.c_int
     lib.aln_warmstart_train.argtypes = [vp, dp, dp, i64, ctypes.POINTER(AlnTrainOpts), dp]
     lib.aln_warmstart_train.restype = ctypes.c_int
@@ -444,17 +444,20 @@ class Solver:
     # ------------------------------------------------------------ warm start
     def warmstart_shapes(self, hidden):
         n2 = 2 * self.n
-        return [(hidden, n2), (hidden,), (hidden, hidden), (hidden,), (n2, hidden), (n2,)]
+        return [(hidden, n2), (hidden,), (hidden, hidden), (hidden,), (n2, hidden), (n2,),
+                (self.n,), (self.n,)]
 
     def warmstart_init(self, hidden=1024, seed=0):
         aln_warmstart_init(self.ctx, hidden, seed)
         self.hidden = hidden
 
-    _WS_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3", "mu", "sd", "tau")
+    _WS_PARAMS = ("W1", "b1", "W2", "b2", "W3", "b3", "e", "f")
+    _WS_KEYS = _WS_PARAMS + ("mu", "sd", "muz", "sdz", "tau")
 
     def warmstart_set(self, params):
-        """params: dict with any of W1, b1, W2, b2, W3, b3 (oracle shapes), mu,
-        sd (n) and tau (scalar); missing keys are left as they are."""
+        """params: dict with any of W1, b1, W2, b2, W3, b3, e, f (oracle
+        shapes), mu, sd, muz, sdz (n) and tau (scalar); missing keys are left
+        as they are."""
         ts = []
         for k in self._WS_KEYS:
             v = params.get(k)
@@ -463,7 +466,7 @@ class Solver:
         aln_warmstart_params(self.ctx, 1, ts)
 
     def warmstart_get(self):
-        shapes = self.warmstart_shapes(self.hidden) + [(self.n,), (self.n,), (1,)]
+        shapes = self.warmstart_shapes(self.hidden) + [(self.n,)] * 4 + [(1,)]
         ts = [np.zeros(sh, np.float32) for sh in shapes]
         aln_warmstart_params(self.ctx, 0, ts)
         out = dict(zip(self._WS_KEYS, ts))
@@ -476,7 +479,7 @@ class Solver:
         loss = np.zeros(1)
         gs = [np.zeros(sh, np.float32) for sh in self.warmstart_shapes(self.hidden)]
         aln_warmstart_grad(self.ctx, Qb, Yb, Qb.shape[0], loss, gs)
-        return float(loss[0]), dict(zip(("W1", "b1", "W2", "b2", "W3", "b3"), gs))
+        return float(loss[0]), dict(zip(self._WS_PARAMS, gs))
 
     def warmstart_train(self, Qt, Yt, **opts):
         o = aln_default_train_opts()

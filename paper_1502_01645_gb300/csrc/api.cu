@@ -1074,21 +1074,21 @@ aln_status aln_warmstart_init(aln_ctx* c, int32_t hidden, uint64_t seed) {
 }
 
 aln_status aln_warmstart_params(aln_ctx* c, int32_t set, float* W1, float* b1, float* W2,
-                                float* b2, float* W3, float* b3, float* mu, float* sd,
-                                float* tau) {
+                                float* b2, float* W3, float* b3, float* e, float* f, float* mu,
+                                float* sd, float* muz, float* sdz, float* tau) {
     ALN_CHECK(ws_ready(c));
     if (mlp_n(c) != c->n) return ALN_ERR_INVALID_ARG;
-    float* t[9] = {W1, b1, W2, b2, W3, b3, mu, sd, tau};
+    float* t[13] = {W1, b1, W2, b2, W3, b3, e, f, mu, sd, muz, sdz, tau};
     return mlp_params(c, set ? 1 : 0, t);
 }
 
 aln_status aln_warmstart_grad(aln_ctx* c, const double* Qb, const double* Yb, int64_t count,
                               double* loss, float* gW1, float* gb1, float* gW2, float* gb2,
-                              float* gW3, float* gb3) {
+                              float* gW3, float* gb3, float* ge, float* gf) {
     ALN_CHECK(ws_ready(c));
     if (!Qb || !Yb || count < 1 || count > (1 << 20) || mlp_n(c) != c->n)
         return ALN_ERR_INVALID_ARG;
-    float* g[6] = {gW1, gb1, gW2, gb2, gW3, gb3};
+    float* g[8] = {gW1, gb1, gW2, gb2, gW3, gb3, ge, gf};
     return mlp_grad(c, Qb, Yb, count, loss, g);
 }
 

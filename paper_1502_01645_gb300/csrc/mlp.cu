@@ -1,23 +1,29 @@
 // Learned start point for Alg. 2 (§3).  The paper starts at x⁰ = 0 and maps
 // a given start with y⁰ = x⁰·√H_ii (Eq. Rescaling, Fig. 2); this file adds a
-// small network that predicts y⁰ from the scaled right-hand side q:
+// small network that predicts y⁰ from the scaled right-hand side q of a fixed
+// A (so a fixed scaled matrix Q):
 //
-//   u  = [ (q/‖q‖ − μ)/σ ; z ],  μ, σ per entry over the training set,
-//        z_j = standardised log s_j (fixed for a fixed A)
-//   h1 = relu(W1 u + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3 = [ŷ ; ℓ]
+//   z  = −Q⁻¹q, the unconstrained minimiser of ½yᵀQy + qᵀy; Q⁻¹ is formed
+//        once per network by a Newton–Schulz iteration (FP32 GEMMs)
+//   u  = [ (q/‖q‖ − μ)/σ ; (z/‖q‖ − μz)/σz ],  μ, σ, μz, σz per entry over
+//        the training set
+//   h1 = relu(W1 u + b1),  h2 = relu(W2 h1 + b2),  [r ; ℓ′] = W3 h2 + b3,
+//   ŷ  = r + e ⊙ ẑ,  ℓ = ℓ′ + f ⊙ ẑ  with ẑ = z/(τ‖q‖) (per-entry skips)
 //   d  = relu(ŷ)·[ℓ > 0],  y⁰ = α*·d with the exact line search of Alg. 2
 //        from 0, α* = max(0, −qᵀd/dᵀQd), so f(y⁰) ≤ f(0)
 //
 // trained with Adam on L = mean (ŷ − y*/(τ‖q‖))² + mean BCE(ℓ, [y* > 0]),
 // τ = RMS of y*/‖q‖ over the training set.
 //
-// Every product is one tcgen05 GEMM kernel, D = A·Bᵀ with both operands
-// K-major BF16 (TMA, 128-byte swizzle, 4-stage ring, FP32 accumulation in
-// tensor memory) and a fused epilogue: bias + ReLU (+ transposed copy),
-// bias only (FP32), ReLU-masked gradient (+ transposed copy), or plain FP32.
-// The backward products need Aᵀ-shaped operands; they are produced by the
-// epilogues (transposed copies) and by the Adam kernel (Wᵀ next to W), so
-// every product keeps K contiguous.  Master weights and Adam moments are FP32.
+// The network's products are one tcgen05 GEMM kernel, D = A·Bᵀ with both
+// operands K-major BF16 (TMA, 128-byte swizzle, 4-stage ring, FP32
+// accumulation in tensor memory) and a fused epilogue: bias + ReLU (+
+// transposed copy), bias only (FP32), ReLU-masked gradient (+ transposed
+// copy), or plain FP32.  The backward products need Aᵀ-shaped operands; they
+// are produced by the epilogues (transposed copies) and by the Adam kernel
+// (Wᵀ next to W), so every product keeps K contiguous.  Master weights and
+// Adam moments are FP32.  The direction z needs more than BF16 (Q has
+// condition numbers in the thousands): Q⁻¹ and z come from an FP32 SIMT GEMM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -230,39 +236,139 @@ __global__ void k_mlp_init(float* __restrict__ W, int64_t rows, int64_t cols, fl
     }
 }
 
-// z_j = (log s_j − mean)/std over j (std := 1 when 0); one block.
-__global__ void k_mlp_zfeat(const double* __restrict__ s, int n, float* __restrict__ z) {
-    __shared__ double scratch[32];
-    __shared__ double s_mu, s_sd;
-    double a = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) a += log(s[j]);
-    a = block_sum(a, scratch);
-    if (threadIdx.x == 0) s_mu = a / n;
-    __syncthreads();
-    const double mu = s_mu;
-    double v = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double t = log(s[j]) - mu;
-        v += t * t;
+// C = α·A·B + β·Cin for row-major FP32 matrices (A M×K, B K×N), on the FP32
+// pipe: 128×128 tiles, K steps of 8 through shared memory, 8×8 outputs per
+// thread (rows ty·4 + {0..3} and +64, columns tx·4 + {0..3} and +64).
+constexpr int kSgT = 128;
+constexpr int kSgK = 8;
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, float alpha,
+                                               const float* __restrict__ A, int64_t lda,
+                                               const float* __restrict__ B, int64_t ldb,
+                                               float beta, const float* __restrict__ Cin,
+                                               int64_t ldcin, float* __restrict__ C,
+                                               int64_t ldc) {
+    __shared__ __align__(16) float As[kSgK][kSgT];
+    __shared__ __align__(16) float Bs[kSgK][kSgT];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * kSgT, n0 = (int64_t)blockIdx.x * kSgT;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += kSgK) {
+        // A tile 128×8 (stored transposed), B tile 8×128: 4 values each per thread
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            const int ar = e >> 3, ak = e & 7;
+            const int64_t gm = m0 + ar;
+            const int gk = k0 + ak;
+            As[ak][ar] = (gm < M && gk < K) ? A[gm * lda + gk] : 0.f;
+            const int bk = e >> 7, bc = e & 127;
+            const int64_t gn = n0 + bc;
+            const int gk2 = k0 + bk;
+            Bs[bk][bc] = (gn < N && gk2 < K) ? B[(int64_t)gk2 * ldb + gn] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kSgK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
     }
-    v = block_sum(v, scratch);
-    if (threadIdx.x == 0) {
-        const double sd = sqrt(v / n);
-        s_sd = sd > 0.0 ? sd : 1.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t cc = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+            if (cc >= N) continue;
+            float v = alpha * acc[i][j];
+            if (beta != 0.f) v = fmaf(beta, Cin[r * ldcin + cc], v);
+            C[r * ldc + cc] = v;
+        }
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x) z[j] = (float)((log(s[j]) - mu) / s_sd);
 }
 
-// u_b = [(q_b/‖q_b‖ − μ)/σ ; z] in BF16 for the rows idx[b] of Q (FP64, row
-// stride ldq); qn[b] = ‖q_b‖.  One block per row.
+// Q (FP32 or FP64, row stride ldq) → dense FP32 n×n, and the row sums of
+// |Q| (one block per row) for the Newton–Schulz start.
+template <typename T>
+__global__ void __launch_bounds__(256) k_q_to_f32(const T* __restrict__ Q, int64_t ldq, int n,
+                                                  float* __restrict__ out,
+                                                  double* __restrict__ rowabs) {
+    __shared__ double scratch[32];
+    const int i = blockIdx.x;
+    double a = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = (double)Q[(int64_t)i * ldq + j];
+        out[(int64_t)i * n + j] = (float)v;
+        a += fabs(v);
+    }
+    a = block_sum(a, scratch);
+    if (threadIdx.x == 0) rowabs[i] = a;
+}
+
+// X = I/‖Q‖∞ (‖Q‖∞ = the largest row sum of |Q|, ≥ λ_max for symmetric Q),
+// the Newton–Schulz start; one grid over the n×n entries.
+__global__ void k_ns_start(const double* __restrict__ rowabs, int n, float* __restrict__ X) {
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m = fmax(m, rowabs[i]);
+        s_inv = m > 0.0 ? 1.0 / m : 1.0;
+    }
+    __syncthreads();
+    const int64_t total = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        X[e] = (e / n == e % n) ? (float)s_inv : 0.f;
+}
+
+// R = I − T in place, and per-block partial sums of ‖R‖_F² (one block per row).
+__global__ void __launch_bounds__(256) k_ns_resid(float* __restrict__ T, int n,
+                                                  double* __restrict__ part) {
+    __shared__ double scratch[32];
+    const int i = blockIdx.x;
+    double a = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const float r = (i == j ? 1.f : 0.f) - T[(int64_t)i * n + j];
+        T[(int64_t)i * n + j] = r;
+        a = fma((double)r, (double)r, a);
+    }
+    a = block_sum(a, scratch);
+    if (threadIdx.x == 0) part[i] = a;
+}
+
+// Σ part[0..np) in a fixed order (one block).
+__global__ void k_sum_parts(const double* __restrict__ part, int np, double* __restrict__ out) {
+    __shared__ double scratch[32];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) a += part[i];
+    a = block_sum(a, scratch);
+    if (threadIdx.x == 0) *out = a;
+}
+
+// First half of the features for the rows idx[b] of Q (FP64, row stride ldq):
+// qn[b] = ‖q_b‖, u_b[0..n) = (q_b/‖q_b‖ − μ)/σ in BF16, and the FP32 unit
+// row q_b/‖q_b‖ (0 when q_b = 0) for the direction product.  One block per row.
 __global__ void __launch_bounds__(256) k_mlp_features(const double* __restrict__ Qs, int64_t ldq,
                                                       const int* __restrict__ idx, int n,
-                                                      const float* __restrict__ z,
                                                       const float* __restrict__ mu,
                                                       const float* __restrict__ sd,
                                                       __nv_bfloat16* __restrict__ U, int64_t ldu,
-                                                      float* __restrict__ qn) {
+                                                      float* __restrict__ qn,
+                                                      float* __restrict__ Qn, int64_t ldqn) {
     __shared__ double scratch[32];
     __shared__ double s_inv;
     const int b = blockIdx.x;
@@ -279,9 +385,75 @@ __global__ void __launch_bounds__(256) k_mlp_features(const double* __restrict__
     const double inv = s_inv;
     __nv_bfloat16* u = U + (int64_t)b * ldu;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        u[j] = __float2bfloat16_rn(((float)(q[j] * inv) - mu[j]) / sd[j]);
-        u[n + j] = __float2bfloat16_rn(z[j]);
+        const float qv = (float)(q[j] * inv);
+        u[j] = __float2bfloat16_rn(inv > 0.0 ? (qv - mu[j]) / sd[j] : 0.f);
+        if (Qn) Qn[(int64_t)b * ldqn + j] = qv;
     }
+}
+
+// Second half of the features from the direction rows zp_b = z_b/‖q_b‖ (the
+// rows idx[b] of Zp, or row b): u_b[n..2n) = (zp − μz)/σz in BF16 (0 when
+// q_b = 0), and the skip input ẑ_b = zp_b/τ (FP32).
+__global__ void __launch_bounds__(256) k_mlp_zfeatures(const float* __restrict__ Zp,
+                                                       int64_t ldz, const int* __restrict__ idx,
+                                                       int n, const float* __restrict__ qn,
+                                                       const float* __restrict__ muz,
+                                                       const float* __restrict__ sdz,
+                                                       float inv_tau,
+                                                       __nv_bfloat16* __restrict__ U, int64_t ldu,
+                                                       float* __restrict__ Zt, int64_t ldzt) {
+    const int b = blockIdx.x;
+    const float* z = Zp + (int64_t)(idx ? idx[b] : b) * ldz;
+    const bool live = qn[b] > 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const float zv = live ? z[j] : 0.f;
+        U[(int64_t)b * ldu + n + j] = __float2bfloat16_rn(live ? (zv - muz[j]) / sdz[j] : 0.f);
+        Zt[(int64_t)b * ldzt + j] = zv * inv_tau;
+    }
+}
+
+// Per-entry skips: o_b[j] += e_j·ẑ_bj, o_b[n + j] += f_j·ẑ_bj.
+__global__ void k_mlp_skip(float* __restrict__ O, int64_t ldo, const float* __restrict__ Zt,
+                           int64_t ldzt, const float* __restrict__ e, const float* __restrict__ f,
+                           int B, int n) {
+    const int64_t total = (int64_t)B * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(t / n), j = (int)(t - (int64_t)b * n);
+        const float zt = Zt[(int64_t)b * ldzt + j];
+        O[(int64_t)b * ldo + j] += e[j] * zt;
+        O[(int64_t)b * ldo + n + j] += f[j] * zt;
+    }
+}
+
+// Column sums of the direction rows over a chunk (FP64, one thread per column,
+// rows in order), added to the running sums s1 (Σ zp) and s2 (Σ zp²).
+__global__ void k_zmoments(const float* __restrict__ Zp, int64_t ldz, int rows, int n,
+                           const float* __restrict__ qn, double* __restrict__ s1,
+                           double* __restrict__ s2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double a = 0.0, c = 0.0;
+    for (int r = 0; r < rows; ++r) {
+        const double z = qn[r] > 0.f ? (double)Zp[(int64_t)r * ldz + j] : 0.0;
+        a += z;
+        c = fma(z, z, c);
+    }
+    s1[j] += a;
+    s2[j] += c;
+}
+
+// μz = s1/count, σz = sqrt(s2/count − μz²) (σz := 1 when 0).
+__global__ void k_zmoments_final(const double* __restrict__ s1, const double* __restrict__ s2,
+                                 int64_t count, int n, float* __restrict__ muz,
+                                 float* __restrict__ sdz) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double m = s1[j] / (double)count;
+    const double v = fmax(s2[j] / (double)count - m * m, 0.0);
+    const double sd = sqrt(v);
+    muz[j] = (float)m;
+    sdz[j] = sd > 0.0 ? (float)sd : 1.f;
 }
 
 // out[c][r] = in[r][c] for an R×C BF16 matrix, 32×32 tiles through shared memory.
@@ -303,17 +475,22 @@ __global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int64_t l
 // Loss terms and dL/do for a batch: o = [ŷ ; ℓ] (FP32, B × 2n), targets
 // y*/(τ‖q‖) from the rows idx[b] of Y (FP64, y* in the scaled space) and qn.  Writes dO in
 // BF16 (row-major and transposed) and one loss partial per block.
+// With Zt, also the skip gradients' block partials: pe[by·n + j] = Σ_b
+// dL/dŷ_bj·ẑ_bj and pf likewise with dL/dℓ_bj, over the block's 32 rows.
 __global__ void k_mlp_loss(const float* __restrict__ O, int64_t ldo, const double* __restrict__ Y,
                            int64_t ldy, const int* __restrict__ idx, const float* __restrict__ qn,
                            int B, int n, float inv_m, float tau, __nv_bfloat16* __restrict__ dO,
                            int64_t ldd,
                            __nv_bfloat16* __restrict__ dOT, int64_t lddt,
-                           double* __restrict__ part) {
+                           double* __restrict__ part, const float* __restrict__ Zt,
+                           int64_t ldzt, float* __restrict__ pe, float* __restrict__ pf) {
     __shared__ float t1[32][33], t2[32][33];
     __shared__ double scratch[32];
+    __shared__ float se[8][32], sf[8][32];
     const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 × 8
     double acc = 0.0;
+    float ae = 0.0f, af = 0.0f;
     for (int k = ty; k < 32; k += blockDim.y) {
         const int b = b0 + k, j = j0 + tx;
         float d1 = 0.0f, d2 = 0.0f;
@@ -331,11 +508,27 @@ __global__ void k_mlp_loss(const float* __restrict__ O, int64_t ldo, const doubl
             d2 = (1.0f / (1.0f + expf(-lg)) - c) * inv_m;
             dO[(int64_t)b * ldd + j] = __float2bfloat16_rn(d1);
             dO[(int64_t)b * ldd + n + j] = __float2bfloat16_rn(d2);
+            if (Zt) {
+                const float zt = Zt[(int64_t)b * ldzt + j];
+                ae = fmaf(d1, zt, ae);
+                af = fmaf(d2, zt, af);
+            }
         }
         t1[k][tx] = d1;
         t2[k][tx] = d2;
     }
+    se[ty][tx] = ae;
+    sf[ty][tx] = af;
     __syncthreads();
+    if (Zt && ty == 0 && j0 + tx < n) {
+        float a1 = 0.0f, a2 = 0.0f;
+        for (int k = 0; k < 8; ++k) {
+            a1 += se[k][tx];
+            a2 += sf[k][tx];
+        }
+        pe[(int64_t)blockIdx.y * n + j0 + tx] = a1;
+        pf[(int64_t)blockIdx.y * n + j0 + tx] = a2;
+    }
     for (int k = ty; k < 32; k += blockDim.y) {
         const int j = j0 + k, b = b0 + tx;
         if (b < B && j < n) {
@@ -364,6 +557,16 @@ __global__ void k_mlp_loss_sum(const double* __restrict__ part, int np, double i
     for (int i = threadIdx.x; i < np; i += blockDim.x) a += part[i];
     a = block_sum(a, scratch);
     if (threadIdx.x == 0) *out = a * inv_m;
+}
+
+// g[j] = Σ_y part[y·n + j] over the row blocks in order (skip gradients).
+__global__ void k_colsum_parts(const float* __restrict__ part, int ny, int n,
+                               float* __restrict__ g) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double a = 0.0;
+    for (int y = 0; y < ny; ++y) a += (double)part[(int64_t)y * n + j];
+    g[j] = (float)a;
 }
 
 // g[r] = Σ_c X[r][c] (bias gradient from a transposed BF16 gradient).
@@ -400,7 +603,7 @@ __global__ void k_adam(float* __restrict__ W, float* __restrict__ m, float* __re
             const float w = W[e] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
             W[e] = w;
             const __nv_bfloat16 h = __float2bfloat16_rn(w);
-            Wh[r * ldh + c] = h;
+            if (Wh) Wh[r * ldh + c] = h;
             tile[k][threadIdx.x] = h;
         }
     }
@@ -593,9 +796,14 @@ struct Mlp {
     int n = 0, hidden = 0;
     int64_t in = 0, out = 0;     // 2n
     Tensor W[3], b[3];
-    float* z = nullptr;
+    Tensor e, f;                 // per-entry skips from ẑ to ŷ and to ℓ (n each)
+    float* Minv = nullptr;       // Q⁻¹ (n×n FP32, Newton–Schulz)
+    int ns_iters = 0;            // Newton–Schulz iterations it took
+    double ns_resid = 0.0;       // ‖I − Q·Q⁻¹‖_F at the end
     float* mu = nullptr;         // feature normalisation (n), σ (n), τ (1)
     float* sd = nullptr;
+    float* muz = nullptr;        // direction-feature normalisation (n each)
+    float* sdz = nullptr;
     float* tau = nullptr;
     float tau_host = 1.0f;
     bool stats_set = false;      // μ, σ, τ taken from a training set or set
@@ -611,6 +819,8 @@ struct Mlp {
                   *H2T = nullptr, *dO = nullptr, *dOT = nullptr, *dZ2 = nullptr, *dZ2T = nullptr,
                   *dZ1 = nullptr, *dZ1T = nullptr, *Y0h = nullptr, *Qh = nullptr;
     float *O = nullptr, *Y0 = nullptr, *QY = nullptr, *qn = nullptr;
+    float *Qn = nullptr, *Zp = nullptr, *Zt = nullptr;  // unit q rows, z/‖q‖, ẑ (B × ldY)
+    float *pe = nullptr, *pf = nullptr;                 // skip-gradient block partials
     double* part = nullptr;
     double* lossv = nullptr;
     int* idx = nullptr;
@@ -657,9 +867,13 @@ aln_status alloc_weights(aln_ctx* c, Mlp* M) {
         for (int k = 0; k < 4; ++k) add((size_t)R * 4);                 // bias w m v g
         add((size_t)ld8(R) * 2);                                        // bias h (unused)
     }
-    add((size_t)M->n * 4);  // z
+    for (int k = 0; k < 2; ++k)
+        for (int t = 0; t < 4; ++t) add((size_t)M->n * 4);           // e, f: w m v g
+    add((size_t)M->n * M->n * 4);  // Q⁻¹
     add((size_t)M->n * 4);  // mu
     add((size_t)M->n * 4);  // sd
+    add((size_t)M->n * 4);  // muz
+    add((size_t)M->n * 4);  // sdz
     add(4);                 // tau
     if (cudaMalloc(&M->wpool, total) != cudaSuccess) {
         cudaGetLastError();
@@ -699,9 +913,21 @@ aln_status alloc_weights(aln_ctx* c, Mlp* M) {
         b.ldh = ld8(R);
         b.h = (__nv_bfloat16*)take((size_t)b.ldh * 2);
     }
-    M->z = (float*)take((size_t)M->n * 4);
+    for (int k = 0; k < 2; ++k) {
+        Tensor& T = k == 0 ? M->e : M->f;
+        T.R = 1;
+        T.C = M->n;
+        T.w = (float*)take((size_t)M->n * 4);
+        T.m = (float*)take((size_t)M->n * 4);
+        T.v = (float*)take((size_t)M->n * 4);
+        T.g = (float*)take((size_t)M->n * 4);
+        T.ldg = M->n;
+    }
+    M->Minv = (float*)take((size_t)M->n * M->n * 4);
     M->mu = (float*)take((size_t)M->n * 4);
     M->sd = (float*)take((size_t)M->n * 4);
+    M->muz = (float*)take((size_t)M->n * 4);
+    M->sdz = (float*)take((size_t)M->n * 4);
     M->tau = (float*)take(4);
     return ALN_OK;
 }
@@ -730,6 +956,8 @@ aln_status alloc_acts(aln_ctx* c, Mlp* M, int B) {
         (size_t)Bc * M->ldY * 2, (size_t)n * M->ldQh * 2,                       // Y0h Qh
         (size_t)Bc * M->ldO * 4, (size_t)Bc * M->ldY * 4, (size_t)Bc * M->ldY * 4,  // O Y0 QY
         (size_t)Bc * 4,                                                         // qn
+        (size_t)Bc * M->ldY * 4, (size_t)Bc * M->ldY * 4, (size_t)Bc * M->ldY * 4,  // Qn Zp Zt
+        (size_t)ceil_div(Bc, 32) * n * 4, (size_t)ceil_div(Bc, 32) * n * 4,     // pe pf
         (size_t)ceil_div(n, 32) * ceil_div(Bc, 32) * 8 + 64,                    // part
         64,                                                                     // loss
         (size_t)Bc * 4,                                                         // idx
@@ -768,6 +996,11 @@ aln_status alloc_acts(aln_ctx* c, Mlp* M, int B) {
     M->Y0 = (float*)take();
     M->QY = (float*)take();
     M->qn = (float*)take();
+    M->Qn = (float*)take();
+    M->Zp = (float*)take();
+    M->Zt = (float*)take();
+    M->pe = (float*)take();
+    M->pf = (float*)take();
     M->part = (double*)take();
     M->lossv = (double*)take();
     M->idx = (int*)take();
@@ -803,6 +1036,85 @@ GemmArgs args0() {
     return a;
 }
 
+// C = α·A·B + β·Cin (row-major FP32) on the FP32 pipe.
+aln_status sgemm(aln_ctx* c, int Mr, int N, int K, float alpha, const float* A, int64_t lda,
+                 const float* B, int64_t ldb, float beta, const float* Cin, int64_t ldcin,
+                 float* C, int64_t ldc) {
+    const dim3 grid((unsigned)ceil_div(N, kSgT), (unsigned)ceil_div(Mr, kSgT));
+    k_sgemm<<<grid, 256, 0, c->stream>>>(Mr, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C,
+                                         ldc);
+    M_TRY(cudaGetLastError());
+    c->launches += 1;
+    return ALN_OK;
+}
+
+// Q⁻¹ of the prepared Q by the Newton–Schulz iteration X ← X(2I − QX)
+// (Schulz 1933): with X₀ = I/‖Q‖∞ every eigenvalue of R₀ = I − QX₀ lies in
+// [0, 1) for a positive definite Q, and R_{k+1} = R_k², so the residual
+// squares every step once it is below 1.  Each step: T = Q·X, R = I − T,
+// X ← X + X·R (two FP32 GEMMs).  It stops when ‖R‖_F < 1e-4, when ‖R‖_F has
+// stopped falling (the FP32 floor, about cond(Q)·2⁻²⁴·√n), or after 100 steps.
+aln_status ns_inverse(aln_ctx* c, Mlp* M) {
+    const int n = M->n;
+    const size_t nn = (size_t)n * n;
+    float *Q32 = nullptr, *T = nullptr, *X2 = nullptr;
+    double* part = nullptr;
+    aln_status st = ALN_OK;
+    if (cudaMalloc(&Q32, nn * 4) != cudaSuccess || cudaMalloc(&T, nn * 4) != cudaSuccess ||
+        cudaMalloc(&X2, nn * 4) != cudaSuccess ||
+        cudaMalloc(&part, ((size_t)n + 8) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        st = ALN_ERR_OUT_OF_MEMORY;
+    }
+    double* rsum = part + n;
+    float* X = M->Minv;
+    if (st == ALN_OK) {
+        if (c->opt.precision == ALN_PREC_FP64)
+            k_q_to_f32<double><<<n, 256, 0, c->stream>>>((const double*)c->Q, c->ldq, n, Q32, part);
+        else
+            k_q_to_f32<float><<<n, 256, 0, c->stream>>>((const float*)c->Q, c->ldq, n, Q32, part);
+        k_ns_start<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)nn, 256), 8192), 256, 0,
+                     c->stream>>>(part, n, X);
+        if (cudaGetLastError() != cudaSuccess) st = ALN_ERR_CUDA;
+        c->launches += 2;
+    }
+    double prev = 1e300;
+    int it = 0;
+    for (; st == ALN_OK && it < 100; ++it) {
+        st = sgemm(c, n, n, n, 1.f, Q32, n, X, n, 0.f, nullptr, 0, T, n);
+        if (st != ALN_OK) break;
+        k_ns_resid<<<n, 256, 0, c->stream>>>(T, n, part);
+        k_sum_parts<<<1, 256, 0, c->stream>>>(part, n, rsum);
+        c->launches += 2;
+        st = sgemm(c, n, n, n, 1.f, X, n, T, n, 1.f, X, n, X2, n);
+        if (st != ALN_OK) break;
+        if (cudaMemcpyAsync(M->hloss, rsum, 8, cudaMemcpyDeviceToHost, c->stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(X, X2, nn * 4, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            st = ALN_ERR_CUDA;
+            break;
+        }
+        const double r = std::sqrt(std::max(*M->hloss, 0.0));
+        M->ns_resid = r;
+        if (!std::isfinite(r)) {
+            st = ALN_ERR_NONFINITE;
+            break;
+        }
+        if (r < 1e-4 || (r < 1.0 && r > 0.5 * prev)) {
+            ++it;
+            break;
+        }
+        prev = r;
+    }
+    M->ns_iters = it;
+    if (Q32) cudaFree(Q32);
+    if (T) cudaFree(T);
+    if (X2) cudaFree(X2);
+    if (part) cudaFree(part);
+    return st;
+}
+
 // Forward pass of a batch already in M->U (B rows).  With `train`, also the
 // transposed activations the backward products need.
 aln_status forward(aln_ctx* c, Mlp* M, int B, bool train) {
@@ -825,6 +1137,10 @@ aln_status forward(aln_ctx* c, Mlp* M, int B, bool train) {
     a.out_f = M->O;
     a.ld_f = M->ldO;
     M_CHECK(gemm<EPI_LINEAR>(c, M->H2, M->ldH, M->W[2].h, M->W[2].ldh, B, M->out, M->hidden, a));
+    k_mlp_skip<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)B * M->n, 256), 8192), 256, 0,
+                 c->stream>>>(M->O, M->ldO, M->Zt, M->ldY, M->e.w, M->f.w, B, M->n);
+    M_TRY(cudaGetLastError());
+    c->launches += 1;
     return ALN_OK;
 }
 
@@ -837,11 +1153,15 @@ aln_status backward(aln_ctx* c, Mlp* M, int B, const double* Y, int64_t ldy, con
     const dim3 lg((unsigned)ceil_div(n, 32), (unsigned)ceil_div(B, 32));
     k_mlp_loss<<<lg, dim3(32, 8), 0, c->stream>>>(M->O, M->ldO, Y, ldy, idx, M->qn, B, n, inv_m,
                                                  M->tau_host, M->dO, M->ldO, M->dOT, M->ldOT,
-                                                 M->part);
+                                                 M->part, M->Zt, M->ldY, M->pe, M->pf);
     k_mlp_loss_sum<<<1, 256, 0, c->stream>>>(M->part, (int)(lg.x * lg.y), (double)inv_m,
                                             M->lossv);
+    k_colsum_parts<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(M->pe, (int)lg.y, n,
+                                                                    M->e.g);
+    k_colsum_parts<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(M->pf, (int)lg.y, n,
+                                                                    M->f.g);
     M_TRY(cudaGetLastError());
-    c->launches += 2;
+    c->launches += 4;
     // layer 3: dW3 = dOᵀ·H2, db3 = Σ_b dO, dZ2 = (dO·W3) ⊙ [h2 > 0]
     GemmArgs a = args0();
     a.out_f = M->W[2].g;
@@ -882,10 +1202,29 @@ aln_status backward(aln_ctx* c, Mlp* M, int B, const double* Y, int64_t ldy, con
     return ALN_OK;
 }
 
+// Features of B rows of Q (rows idx[b] of Qs, or row b): u (and its
+// transpose for training), ‖q‖ and the skip input ẑ.  The direction rows
+// z/‖q‖ come from Zrows (precomputed, same indexing) or, when it is null,
+// from one FP32 product −(q/‖q‖)·Q⁻¹ of the batch.
 aln_status features(aln_ctx* c, Mlp* M, const double* Qs, int64_t ldq, const int* idx, int B,
-                    bool transpose) {
-    k_mlp_features<<<B, 256, 0, c->stream>>>(Qs, ldq, idx, M->n, M->z, M->mu, M->sd, M->U,
-                                             M->ldU, M->qn);
+                    bool transpose, const float* Zrows = nullptr) {
+    k_mlp_features<<<B, 256, 0, c->stream>>>(Qs, ldq, idx, M->n, M->mu, M->sd, M->U, M->ldU,
+                                             M->qn, Zrows ? nullptr : M->Qn, M->ldY);
+    c->launches += 1;
+    M_TRY(cudaGetLastError());
+    const float* Z = Zrows;
+    int64_t ldz = M->n;
+    const int* zidx = idx;
+    if (!Z) {
+        // Q⁻¹ is symmetric up to its FP32 rounding: rows times Q⁻¹
+        M_CHECK(sgemm(c, B, M->n, M->n, -1.f, M->Qn, M->ldY, M->Minv, M->n, 0.f, nullptr, 0,
+                      M->Zp, M->ldY));
+        Z = M->Zp;
+        ldz = M->ldY;
+        zidx = nullptr;
+    }
+    k_mlp_zfeatures<<<B, 256, 0, c->stream>>>(Z, ldz, zidx, M->n, M->qn, M->muz, M->sdz,
+                                              1.0f / M->tau_host, M->U, M->ldU, M->Zt, M->ldY);
     c->launches += 1;
     if (transpose) {
         const dim3 grid((unsigned)ceil_div(M->in, 32), (unsigned)ceil_div(B, 32));
@@ -922,8 +1261,15 @@ aln_status adam_all(aln_ctx* c, Mlp* M, const aln_train_opts& o) {
                                                      k == 0 ? T.t : nullptr, T.ldt);
         }
     }
+    for (int k = 0; k < 2; ++k) {
+        Tensor& T = k == 0 ? M->e : M->f;
+        const dim3 g((unsigned)ceil_div(T.C, 32), 1);
+        k_adam<<<g, dim3(32, 8), 0, c->stream>>>(T.w, T.m, T.v, T.g, T.ldg, T.R, T.C, (float)o.lr,
+                                                 (float)o.beta1, (float)o.beta2, (float)o.eps, c1,
+                                                 c2, nullptr, 0, nullptr, 0);
+    }
     M_TRY(cudaGetLastError());
-    c->launches += 6;
+    c->launches += 8;
     return ALN_OK;
 }
 
@@ -1015,58 +1361,54 @@ aln_status mlp_init(aln_ctx* c, int hidden, uint64_t seed) {
         k_mlp_init<<<(unsigned)std::min<int64_t>(ceil_div(W.R * W.C, 256), 4096), 256, 0,
                      c->stream>>>(W.w, W.R, W.C, lim, seed + 0x1000193ull * (uint64_t)(l + 1));
     }
-    k_mlp_zfeat<<<1, 1024, 0, c->stream>>>(c->s, (int)c->n, M->z);
-    k_fill<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M->n, 256), 1024)), 256, 0,
-             c->stream>>>(M->sd, M->n, 1.0f);
+    const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M->n, 256), 1024));
+    k_fill<<<gn, 256, 0, c->stream>>>(M->sd, M->n, 1.0f);
+    k_fill<<<gn, 256, 0, c->stream>>>(M->sdz, M->n, 1.0f);
+    k_fill<<<gn, 256, 0, c->stream>>>(M->e.w, M->n, 1.0f);   // ŷ follows ẑ
+    k_fill<<<gn, 256, 0, c->stream>>>(M->f.w, M->n, 4.0f);   // ℓ follows its sign
     k_fill<<<1, 32, 0, c->stream>>>(M->tau, 1, 1.0f);
     M->tau_host = 1.0f;
     M_TRY(cudaGetLastError());
-    c->launches += 6;
+    c->launches += 8;
     M_CHECK(refresh_copies(c, M));
+    M_CHECK(ns_inverse(c, M));
     M_TRY(cudaStreamSynchronize(c->stream));
     return ALN_OK;
 }
 
+// t = {W1, b1, W2, b2, W3, b3, e, f, mu, sd, muz, sdz, tau}; null entries
+// are skipped.
 aln_status mlp_params(aln_ctx* c, int set, float* const* t) {
     Mlp* M = (Mlp*)c->mlp;
-    // normalisation statistics: μ (n), σ (n), τ (1)
-    float* dst3[3] = {M->mu, M->sd, M->tau};
-    const size_t len3[3] = {(size_t)M->n, (size_t)M->n, 1};
-    for (int k = 0; k < 3; ++k) {
-        float* p = t[6 + k];
-        if (!p) continue;
-        const bool dev = is_dev_ptr(p);
+    auto copy = [&](float* p, float* dev, size_t count) -> aln_status {
+        if (!p) return ALN_OK;
+        const bool d = is_dev_ptr(p);
         if (set)
-            M_TRY(cudaMemcpyAsync(dst3[k], p, len3[k] * 4,
-                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+            M_TRY(cudaMemcpyAsync(dev, p, count * 4,
+                                  d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                   c->stream));
         else
-            M_TRY(cudaMemcpyAsync(p, dst3[k], len3[k] * 4,
-                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+            M_TRY(cudaMemcpyAsync(p, dev, count * 4,
+                                  d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   c->stream));
+        return ALN_OK;
+    };
+    for (int l = 0; l < 3; ++l) {
+        M_CHECK(copy(t[2 * l], M->W[l].w, (size_t)M->W[l].R * M->W[l].C));
+        M_CHECK(copy(t[2 * l + 1], M->b[l].w, (size_t)M->b[l].C));
     }
-    if (set && (t[6] || t[7] || t[8])) M->stats_set = true;
-    if (set && t[8]) {
+    M_CHECK(copy(t[6], M->e.w, (size_t)M->n));
+    M_CHECK(copy(t[7], M->f.w, (size_t)M->n));
+    M_CHECK(copy(t[8], M->mu, (size_t)M->n));
+    M_CHECK(copy(t[9], M->sd, (size_t)M->n));
+    M_CHECK(copy(t[10], M->muz, (size_t)M->n));
+    M_CHECK(copy(t[11], M->sdz, (size_t)M->n));
+    M_CHECK(copy(t[12], M->tau, 1));
+    if (set && (t[8] || t[9] || t[10] || t[11] || t[12])) M->stats_set = true;
+    if (set && t[12]) {
         M_TRY(cudaMemcpyAsync(M->hflag + 2, M->tau, 4, cudaMemcpyDeviceToHost, c->stream));
         M_TRY(cudaStreamSynchronize(c->stream));
         std::memcpy(&M->tau_host, M->hflag + 2, 4);
-    }
-    for (int l = 0; l < 3; ++l) {
-        for (int k = 0; k < 2; ++k) {
-            float* p = t[2 * l + k];
-            if (!p) continue;
-            const Tensor& T = k == 0 ? M->W[l] : M->b[l];
-            const size_t bytes = (size_t)T.R * T.C * 4;
-            const bool dev = is_dev_ptr(p);
-            if (set)
-                M_TRY(cudaMemcpyAsync(T.w, p, bytes,
-                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                      c->stream));
-            else
-                M_TRY(cudaMemcpyAsync(p, T.w, bytes,
-                                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                      c->stream));
-        }
     }
     if (set) {
         M_CHECK(refresh_copies(c, M));
@@ -1102,16 +1444,14 @@ aln_status mlp_grad(aln_ctx* c, const double* Qs, const double* Ys, int64_t coun
         st = cudaMemcpy(loss, M->lossv, 8, cudaMemcpyDeviceToHost) == cudaSuccess ? ALN_OK
                                                                                   : ALN_ERR_CUDA;
     if (st == ALN_OK) {
-        for (int l = 0; l < 3 && st == ALN_OK; ++l) {
-            for (int k = 0; k < 2; ++k) {
-                float* p = grads[2 * l + k];
-                if (!p) continue;
-                const Tensor& T = k == 0 ? M->W[l] : M->b[l];
-                if (cudaMemcpy(p, T.g, (size_t)T.R * T.C * 4, cudaMemcpyDefault) != cudaSuccess) {
-                    st = ALN_ERR_CUDA;
-                    break;
-                }
-            }
+        const Tensor* ts[8] = {&M->W[0], &M->b[0], &M->W[1], &M->b[1],
+                               &M->W[2], &M->b[2], &M->e,    &M->f};
+        for (int k = 0; k < 8 && st == ALN_OK; ++k) {
+            float* p = grads[k];
+            if (!p) continue;
+            const Tensor& T = *ts[k];
+            if (cudaMemcpy(p, T.g, (size_t)T.R * T.C * 4, cudaMemcpyDefault) != cudaSuccess)
+                st = ALN_ERR_CUDA;
         }
     }
     if (tq) cudaFree(tq);
@@ -1143,7 +1483,40 @@ aln_status mlp_train(aln_ctx* c, const double* Qs, const double* Ys, int64_t cou
         return x ^ (x >> 31);
     };
     if (st == ALN_OK) M_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
-    if (st == ALN_OK && !M->stats_set) st = training_stats(c, M, Qd, Yd, count);
+    const bool need_stats = !M->stats_set;
+    if (st == ALN_OK && need_stats) st = training_stats(c, M, Qd, Yd, count);
+    // The direction rows z/‖q‖ of the whole training set, once (FP32
+    // products of Bcap rows at a time), with their column moments when the
+    // statistics come from this set.
+    float* Ztrain = nullptr;
+    double* zs = nullptr;
+    if (st == ALN_OK && (cudaMalloc(&Ztrain, (size_t)count * n * 4) != cudaSuccess ||
+                         cudaMalloc(&zs, (size_t)2 * n * 8) != cudaSuccess)) {
+        cudaGetLastError();
+        st = ALN_ERR_OUT_OF_MEMORY;
+    }
+    if (st == ALN_OK && need_stats &&
+        cudaMemsetAsync(zs, 0, (size_t)2 * n * 8, c->stream) != cudaSuccess)
+        st = ALN_ERR_CUDA;
+    for (int64_t r0 = 0; st == ALN_OK && r0 < count; r0 += M->Bcap) {
+        const int rows = (int)std::min<int64_t>(M->Bcap, count - r0);
+        k_mlp_features<<<rows, 256, 0, c->stream>>>(Qd + r0 * n, n, nullptr, n, M->mu, M->sd,
+                                                    M->U, M->ldU, M->qn, M->Qn, M->ldY);
+        c->launches += 1;
+        st = sgemm(c, rows, n, n, -1.f, M->Qn, M->ldY, M->Minv, n, 0.f, nullptr, 0,
+                   Ztrain + r0 * n, n);
+        if (st == ALN_OK && need_stats) {
+            k_zmoments<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(Ztrain + r0 * n, n, rows,
+                                                                         n, M->qn, zs, zs + n);
+            c->launches += 1;
+        }
+    }
+    if (st == ALN_OK && need_stats) {
+        k_zmoments_final<<<(unsigned)ceil_div(n, 256), 256, 0, c->stream>>>(zs, zs + n, count, n,
+                                                                           M->muz, M->sdz);
+        c->launches += 1;
+        if (cudaGetLastError() != cudaSuccess) st = ALN_ERR_CUDA;
+    }
     std::vector<double> losses;
     for (int ep = 0; st == ALN_OK && ep < o.epochs; ++ep) {
         for (int64_t i = 0; i < count; ++i) perm[i] = (int)i;
@@ -1165,7 +1538,7 @@ aln_status mlp_train(aln_ctx* c, const double* Qs, const double* Ys, int64_t cou
         for (int64_t bi = 0; bi < nb && st == ALN_OK; ++bi) {
             const int64_t off = bi * B;
             const int Bb = (int)std::min<int64_t>(B, count - off);
-            st = features(c, M, Qd, n, perm_dev + off, Bb, true);
+            st = features(c, M, Qd, n, perm_dev + off, Bb, true, Ztrain);
             if (st == ALN_OK) st = forward(c, M, Bb, true);
             if (st == ALN_OK) st = backward(c, M, Bb, Yd, n, perm_dev + off);
             if (st == ALN_OK) st = adam_all(c, M, o);
@@ -1193,6 +1566,8 @@ aln_status mlp_train(aln_ctx* c, const double* Qs, const double* Ys, int64_t cou
     if (st == ALN_OK && epoch_loss)
         for (size_t i = 0; i < losses.size(); ++i) epoch_loss[i] = losses[i];
     if (perm_dev) cudaFree(perm_dev);
+    if (Ztrain) cudaFree(Ztrain);
+    if (zs) cudaFree(zs);
     if (tq) cudaFree(tq);
     if (ty) cudaFree(ty);
     return st;

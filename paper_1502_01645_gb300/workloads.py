@@ -160,6 +160,48 @@ def warmstart_family(d=8000, n=2000, k=1024, support=(50, 400), seed=1005, rhs_s
                    {"d": d, "n": n, "k": k, "dtype": "f32"})
 
 
+def warmstart_family_device(d=8000, n=2000, k=1024, support=(50, 400), seed=1005,
+                            rhs_seed=None, device="cuda"):
+    """The warm-start family with its right-hand sides formed on a torch
+    device, for training sets of hundreds of thousands of columns (the numpy
+    path's dense FP64 product takes minutes there).  A is the numpy path's
+    for the same seed (bit for bit).  The supports and values of x_true come
+    from the same numpy stream as the numpy path; b = A x_true is formed in
+    FP32 on the device and the 1% noise (standard deviation 0.01·‖Ax‖/√d per
+    column) from a torch generator seeded from the stream, so the columns
+    follow the same recipe but are not bitwise the numpy path's.  Returns
+    (A as numpy FP32 Fortran, B as a (k, d) FP32 device tensor)."""
+    import torch
+    rng = _rng(seed)
+    A = np.asfortranarray(_lopsided_A(rng, d, n).astype(np.float32))
+    r2 = rng if rhs_seed is None else _rng(rhs_seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(r2.integers(0, 2 ** 62)))
+    At = torch.from_numpy(np.ascontiguousarray(A.T)).to(device)      # (n, d)
+    B = torch.empty((k, d), dtype=torch.float32, device=device)
+    step = 16384
+    top = support[1]
+    for c0 in range(0, k, step):
+        kc = min(step, k - c0)
+        # support: the m smallest of n uniform keys per column (a uniform
+        # random m-subset), values Exp(1)
+        sizes = r2.integers(support[0], support[1] + 1, size=kc)
+        keys = r2.random((kc, n))
+        part = np.argpartition(keys, top - 1, axis=1)[:, :top]
+        order = np.take_along_axis(part, np.argsort(np.take_along_axis(keys, part, 1), 1), 1)
+        vals = r2.exponential(1.0, (kc, top))
+        take = np.arange(top)[None, :] < sizes[:, None]
+        X = np.zeros((kc, n), dtype=np.float32)
+        rows = np.broadcast_to(np.arange(kc)[:, None], order.shape)
+        X[rows[take], order[take]] = vals[take]
+        Xc = torch.from_numpy(X).to(device)
+        clean = Xc @ At
+        scale = 0.01 * torch.linalg.vector_norm(clean, dim=1, keepdim=True) / np.sqrt(d)
+        noise = torch.randn(clean.shape, generator=gen, device=device, dtype=torch.float32)
+        B[c0:c0 + kc] = clean + scale * noise
+    return A, B
+
+
 # §5, Table 1: the six test-case kinds — sign of A and x* (+ non-negative,
 # ± mixed) and the lengths of the vectors A_k (SAM same, RAN random, VAR
 # various).
