@@ -110,7 +110,33 @@ def parse():
     ap.add_argument("--refine-gain", type=int, default=0,
                     help="decades each inner FP32 run aims below the last FP64 residual "
                          "(0: library default, <0: every run aims at tol)")
+    ap.add_argument("--group-graph", type=int, default=0, choices=[0, 1],
+                    help="grouped solver: 1 = each solve as one captured CUDA graph")
+    ap.add_argument("--autotune", type=int, default=0, choices=[0, 1, 2],
+                    help="launch geometry from the autotune cache (1) or measured on a "
+                         "miss and recorded (2); the measuring solve is a warm-up step")
+    ap.add_argument("--autotune-cache", default=".aln_autotune.json",
+                    help="JSON cache file of the autotuner")
     return ap.parse_args()
+
+
+def opts_config(args):
+    """Non-default library options, for the config record."""
+    o = {}
+    if args.group_graph:
+        o["group_graph"] = 1
+    if args.autotune:
+        o["autotune"] = args.autotune
+    return o
+
+
+def lib_opts(args):
+    """Library options every solver of the timed path shares."""
+    o = dict(refine_gain=args.refine_gain, gram_split=args.gram_split,
+             group_graph=args.group_graph, autotune=args.autotune)
+    if args.autotune:
+        o["autotune_cache"] = args.autotune_cache
+    return o
 
 
 def workload(args):
@@ -450,8 +476,7 @@ def run_ours(args):
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     alg = aln.ALG_ANTI_ACC if args.algorithm == "anti_acc" else aln.ALG_ANTILOP
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split, algorithm=alg)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args), algorithm=alg)
     sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(S)]
 
@@ -517,8 +542,7 @@ def run_ours(args):
                  torch.from_numpy(np.ascontiguousarray(q.B)).pin_memory()) for q in probs]
         X_h = torch.zeros((k, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5)) if S == 1 else 2
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                             gram_split=args.gram_split, algorithm=alg)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args), algorithm=alg)
         hsolver.prepare(*host[0])
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -673,7 +697,7 @@ def run_ours(args):
                    "lipschitz": (last.lipschitz if alg == aln.ALG_ANTI_ACC else None),
                    "power_products": (int(last.power_products)
                                       if alg == aln.ALG_ANTI_ACC else None),
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": "inputs larger than L2" if p.A.nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",
                    "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
@@ -725,8 +749,7 @@ def run_grouped(args, w, world, rank, local):
             torch.from_numpy(np.ascontiguousarray(p.B[0])).cuda()) for p in probs]
     Xt = torch.zeros(N, dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
     recs = aln.Solver.grouped_records(dev)
 
     def step():
@@ -775,8 +798,7 @@ def run_grouped(args, w, world, rank, local):
                  torch.from_numpy(np.ascontiguousarray(p.B[0])).pin_memory()) for p in probs]
         hrecs = aln.Solver.grouped_records(host)
         X_h = torch.zeros(N, dtype=torch.float64).pin_memory()
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
         hsolver.prepare_grouped(records=hrecs)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -872,7 +894,7 @@ def run_grouped(args, w, world, rank, local):
                    "form": "grouped: split-BF16 tcgen05 Gram (bulk-copy tiles), FP32 Alg. 2 "
                            "one problem per block, n >= 512 out of shared memory on "
                            "4-block clusters (concurrent stream), FP64 scale/KKT/refinement",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": "inputs larger than L2" if nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",
                    "prepare_ms": avg(lambda s: s.prepare_ms), "gram_ms": gram,
@@ -918,8 +940,7 @@ def run_tcases(args, w, world, rank, local):
     Xt = torch.zeros((1, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
     alg = aln.ALG_ANTI_ACC if args.algorithm == "anti_acc" else aln.ALG_ANTILOP
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split, algorithm=alg)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args), algorithm=alg)
 
     def step():
         out = []
@@ -965,8 +986,7 @@ def run_tcases(args, w, world, rank, local):
         host = [(torch.from_numpy(np.ascontiguousarray(p.A.T)).pin_memory().t(),
                  torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()) for p in probs]
         X_h = torch.zeros((1, n), dtype=torch.float64).pin_memory()
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                             gram_split=args.gram_split, algorithm=alg)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args), algorithm=alg)
         for A_h, b_h in host[:2]:  # warm the context (buffers, streams, attributes)
             hsolver.prepare(A_h, b_h)
             hsolver.solve(tol=tol, X=X_h, max_iter=400000)
@@ -1034,7 +1054,7 @@ def run_tcases(args, w, world, rank, local):
                    "form": "3-term split-BF16 tcgen05 Gram, FP32 "
                            + ("Anti+Acc" if alg == aln.ALG_ANTI_ACC else "Alg. 2")
                            + ", FP64 scale/KKT/refinement; sub-tests one after another",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": "inputs larger than L2",
                    "per_case": per_case, "rel_kkt_max": worst},
         "roofline": rooflines[0],
@@ -1088,8 +1108,7 @@ def run_nmf(args, w, world, rank, local):
     Wd = torch.from_numpy(np.ascontiguousarray(W0.T)).cuda().t()
     Hd = torch.from_numpy(np.ascontiguousarray(H0.T)).cuda().t()
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
 
     def step():
         return solver.nmf(Vd, Wd, Hd, outer=outer, tol=tol)
@@ -1162,7 +1181,7 @@ def run_nmf(args, w, world, rank, local):
                    "form": "aln_nmf: H-step and W-step each a batched multi-RHS solve "
                            "(split-BF16 Gram, tcgen05 products, FP64 checks), warm-started",
                    "objective": [float(v) for v in obj],
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": "inputs larger than L2" if V.nbytes > 129e6 else
                          "inputs smaller than L2 (timed as resident data)",
                    "last_w_step_iterations": int(st.iterations)},
@@ -1250,8 +1269,7 @@ def run_banded(args, w, world, rank, local):
     Bt = torch.from_numpy(np.ascontiguousarray(p.B)).cuda()
     Xt = torch.zeros((1, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
 
     def step():
         solver.prepare_csc(d, cp, ri, vv, Bt)
@@ -1308,8 +1326,7 @@ def run_banded(args, w, world, rank, local):
         hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
         X_h = torch.zeros((1, n), dtype=torch.float64).pin_memory()
         k_e2e = max(3, min(args.steps, 5))
-        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                             gram_split=args.gram_split)
+        hsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
         hsolver.prepare_csc(d, hcp, hri, hvv, hB)
         hsolver.solve(tol=tol, X=X_h)
         barrier()
@@ -1329,8 +1346,7 @@ def run_banded(args, w, world, rank, local):
     dense = plain = None
     if not args.no_plain:
         Ad = torch.from_numpy(np.ascontiguousarray(p.dense().T)).cuda().t()
-        dsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                             gram_split=args.gram_split)
+        dsolver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
         dsolver.prepare(Ad, Bt)
         dsolver.solve(tol=tol, X=Xt)
         barrier()
@@ -1422,7 +1438,7 @@ def run_banded(args, w, world, rank, local):
                    "seed": w["seed"],
                    "form": "aln_prepare_csc: block-sparse 3-term split-BF16 tcgen05 Gram, "
                            "FP32 Alg. 2, FP64 scale/KKT/refinement",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": f"inputs ({csc_bytes / 1e6:.1f} MB of CSC arrays and b) smaller "
                          "than L2: a 256 MB buffer is written before every step, outside "
                          "the per-step CUDA event pairs that are summed",
@@ -1466,16 +1482,18 @@ def run_warmstart(args, w, world, rank, local):
     At = torch.from_numpy(np.ascontiguousarray(held.A.T)).cuda().t()
     Bt = torch.from_numpy(np.ascontiguousarray(held.B)).cuda()
     stream = torch.cuda.Stream()
-    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, refine_gain=args.refine_gain,
-                        gram_split=args.gram_split)
+    solver = aln.Solver(w["prec"], stream=stream.cuda_stream, **lib_opts(args))
 
     # ---- training set and training (not timed) ----
     t0 = time.perf_counter()
-    solver.prepare(At, Btr)
+    # (the library works on its own stream: every tensor it writes or reads
+    # is filled on torch's stream first, so synchronise before handing over)
     Xtr = torch.zeros((w["train"], n), dtype=torch.float64, device="cuda")
-    solver.solve(tol=tol, X=Xtr)
     Qtr = torch.zeros((w["train"], n), dtype=torch.float64, device="cuda")
     s_dev = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    solver.prepare(At, Btr)
+    solver.solve(tol=tol, X=Xtr)
     aln.aln_export_scaled(solver.ctx, None, n, Qtr, n, s_dev)
     Ytr = Xtr * s_dev[None, :]
     torch.cuda.synchronize()
@@ -1490,6 +1508,7 @@ def run_warmstart(args, w, world, rank, local):
 
     X0 = torch.zeros((k, n), dtype=torch.float64, device="cuda")
     Xt = torch.zeros((k, n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
 
     def step(warm):
         solver.prepare(At, Bt)
@@ -1622,7 +1641,7 @@ def run_warmstart(args, w, world, rank, local):
                    "train_data_s": t_data, "train_set_s": t_gen, "train_s": t_train,
                    "form": "learned start (tcgen05 BF16 network) + split-BF16 tcgen05 Gram and "
                            "batched products, FP32 Alg. 2, FP64 KKT/refinement",
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}", **opts_config(args),
                    "l2": "inputs smaller than L2 (timed as resident data)",
                    "prepare_ms": avg(lambda s: s.prepare_ms), "iterate_ms": it_ms,
                    "kkt_ms": avg(lambda s: s.kkt_ms), "solve_ms": avg(lambda s: s.solve_ms),

@@ -158,7 +158,30 @@ typedef struct aln_options {
                              the first wait expires after wait_limit_us and the
                              timeout path runs (no fault, no hang); must be
                              0..1024 */
-    int32_t reserved[2];
+    int32_t group_graph;  /* grouped solver: 1 = run each aln_solve as one CUDA graph
+                             (captured on the first solve of a layout, replayed by
+                             later ones with the same tol, max_iter and start
+                             kind): the refinement rounds become max_refine fixed
+                             rounds that pass over finished problems, with the same
+                             results problem by problem; 0 = host-driven rounds */
+    int32_t autotune;     /* launch geometry chosen per shape by measurement, kept
+                             in the JSON file autotune_cache: 0 off; 1 use the
+                             cached choice of the shape (the options above
+                             where there is none); 2 as 1, and on a miss the
+                             first aln_solve of the shape measures the
+                             candidates (whole solves, or a 64-iteration probe
+                             for one problem), records the fastest and then
+                             solves.  Tuned per shape: blocks and row groups of
+                             the persistent Alg. 2 kernel (one problem),
+                             group_cluster (grouped problems), the batched
+                             solver's iterations per captured chunk and its
+                             hand-off of the last running columns; an autotuned
+                             choice replaces persist_blocks and group_cluster.
+                             Results remain Alg. 2's; only the geometry moves */
+    const char* autotune_cache; /* path of the JSON cache file (copied by aln_create;
+                             required when autotune > 0, else
+                             ALN_ERR_INVALID_ARG); written by renaming a
+                             temporary file next to it */
 } aln_options;
 
 typedef struct aln_solve_info {

@@ -43,7 +43,8 @@ class AlnOptions(ctypes.Structure):
                 ("batch_min", ctypes.c_int32), ("refine_gain", ctypes.c_int32),
                 ("gram_split", ctypes.c_int32), ("group_cluster", ctypes.c_int32),
                 ("algorithm", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("test_barrier_skew", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("test_barrier_skew", ctypes.c_int32), ("group_graph", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("autotune_cache", ctypes.c_char_p)]
 
 
 class AlnSolveInfo(ctypes.Structure):
@@ -305,6 +306,9 @@ class Solver:
         o = aln_default_options()
         o.precision = {"fp64": PREC_FP64, "split_bf16": PREC_SPLIT_BF16}[precision]
         for k, v in opts.items():
+            if k == "autotune_cache" and isinstance(v, str):
+                v = v.encode()
+                self._cache_path = v   # keep the bytes alive with the context
             setattr(o, k, v)
         if stream is None:
             try:

@@ -73,6 +73,10 @@ aln_status resolve_input(aln_ctx* c, const void* src, int64_t rows, int64_t cols
     return ALN_OK;
 }
 
+}  // namespace
+
+namespace aln {
+
 // Iteration and KKT workspace for the current (n, d, precision).
 aln_status alloc_workspace(aln_ctx* c) {
     const size_t T = fp64(c) ? 8 : 4;
@@ -94,6 +98,7 @@ aln_status alloc_workspace(aln_ctx* c) {
     const int64_t blocks_wanted = c->opt.persist_blocks > 0 ? c->opt.persist_blocks : c->num_sms;
     int pR = (int)std::max<int64_t>(1, std::min<int64_t>(blocks_wanted / col_tiles,
                                                          ceil_div(n, 32)));
+    if (c->tune_pR > 0) pR = c->tune_pR;  // the autotuner's choice
     c->p_R = std::min(pR, 64);
     // The replicated-state kernel is used whenever its vectors fit in shared
     // memory, unless the options ask for the tiled one.
@@ -206,6 +211,10 @@ aln_status run_until_done(aln_ctx* c) {
     }
     return ALN_OK;
 }
+
+}  // namespace aln
+
+namespace {
 
 // Anti+Acc: L = λ_max(Q) of the prepared Q by the power iteration, once per
 // prepare.  Needs the replicated layout (else ALN_ERR_UNSUPPORTED).
@@ -392,7 +401,10 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
     if (o.gram_split != 2 && o.gram_split != 3) return ALN_ERR_INVALID_ARG;
     if (o.algorithm != ALN_ALG_ANTILOP && o.algorithm != ALN_ALG_ANTI_ACC)
         return ALN_ERR_INVALID_ARG;
-    if (o.wait_limit_us < 0 || o.test_barrier_skew < 0 || o.test_barrier_skew > 1024)
+    if (o.wait_limit_us < 0 || o.test_barrier_skew < 0 || o.test_barrier_skew > 1024 ||
+        o.group_graph < 0 || o.group_graph > 1 || o.autotune < 0 || o.autotune > 2)
+        return ALN_ERR_INVALID_ARG;
+    if (o.autotune > 0 && (!o.autotune_cache || !o.autotune_cache[0]))
         return ALN_ERR_INVALID_ARG;
     if (o.group_cluster == 0) o.group_cluster = 4;
     if (o.group_cluster != 1 && o.group_cluster != 2 && o.group_cluster != 4 &&
@@ -400,7 +412,10 @@ aln_status aln_create(aln_ctx** out, const aln_options* opt, void* stream) {
         return ALN_ERR_INVALID_ARG;
     aln_ctx* c = new (std::nothrow) aln_ctx();
     if (!c) return ALN_ERR_OUT_OF_MEMORY;
+    if (o.autotune_cache) c->tune_path = o.autotune_cache;  // a copy: the caller's may go
+    o.autotune_cache = nullptr;
     c->opt = o;
+    c->user_opt = o;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
             cudaSuccess ||
@@ -835,6 +850,7 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     if (c->grouped) {
         if (!X || !(tol > 0.0) || !std::isfinite(tol)) return ALN_ERR_INVALID_ARG;
         if (max_iter <= 0) max_iter = 20000;
+        ALN_CHECK(autotune_solve(c, tol, max_iter, X, 0, X0));
         c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
         c->stats.passive_rows = c->stats.clipped_rows = 0;
         c->stats.clipped_iterations = 0;
@@ -855,6 +871,7 @@ aln_status aln_solve(aln_ctx* c, double tol, int32_t max_iter, double* X, int64_
     const bool x_dev = is_device_ptr(X);
     const bool x0_dev = X0 ? is_device_ptr(X0) : false;
     const bool f64 = fp64(c);
+    ALN_CHECK(autotune_solve(c, tol, max_iter, X, ldx, X0));
     c->stats.solve_ms = c->stats.kkt_ms = c->stats.iterate_ms = 0.0;
     c->stats.passive_rows = c->stats.clipped_rows = 0;
     c->stats.clipped_iterations = 0;

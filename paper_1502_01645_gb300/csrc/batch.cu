@@ -944,6 +944,13 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     BatchWork* b = (BatchWork*)c->batch;
     BatchState& s = b->s;
     const int64_t k = b->k;
+    // iterations per captured chunk: 8, or the autotuner's choice
+    const int chunk = c->tune_chunk > 0 ? c->tune_chunk : 8;
+    if (!b->small_vpl && chunk != b->chunk) {
+        b->chunk = chunk;
+        aln_status cs = bw_capture(c, b);
+        if (cs != ALN_OK) return cs;
+    }
     const double* X0dev = nullptr;
     if (X0) {  // stage the start points in X64 (ld = ldq) and check them
         if (cudaMemcpy2DAsync(b->X64, c->ldq * 8, X0, ldx * 8, c->n * 8, k,
@@ -989,7 +996,7 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     const size_t tsmem = bblock_smem(c->ldq);
     const bool tail_ok = !b->small_vpl && tsmem + 1024 <= (size_t)optin;
-    const int64_t tail_max = 2LL * c->num_sms;
+    const int64_t tail_max = c->tune_tail > 0 ? (int64_t)c->tune_tail : 2LL * c->num_sms;
     auto run_tail = [&](int64_t running) -> aln_status {
         if (cudaFuncSetAttribute(k_bblock, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tsmem) != cudaSuccess ||

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <string>
+
 #include "aln.h"
 
 namespace aln {
@@ -302,4 +304,15 @@ struct aln_ctx {
     cudaEvent_t copy_ev[64] = {};
     aln_stats stats = {};
     int64_t launches = 0;
+
+    // autotune (autotune.cu): the cache file, the options as the caller gave
+    // them (restored for a shape with no cached choice), the shape whose
+    // choice is in force, and the choices that have no public option
+    std::string tune_path;
+    aln_options user_opt;
+    std::string tuned_key;
+    int tune_pR = 0;     // row groups of the persistent Alg. 2 kernel (0 = derived)
+    int tune_chunk = 0;  // batched solver: iterations per captured chunk (0 = 8)
+    int tune_tail = 0;   // batched solver: running columns handed to one block each
+                         // (0 = 2 per SM)
 };

@@ -201,6 +201,8 @@ struct GSolveArgs {
     int max_iter;
     int window;
     int smem_bytes;
+    const int* run;        // nullable: problems p with run[p] = 0 are passed over
+                           // (the graph-captured refinement rounds)
 };
 
 // --- thread-block clusters (large problems, several CTAs per problem): cluster.cuh
@@ -417,8 +419,12 @@ __global__ void __launch_bounds__(kGThreads, 1) k_galg2(GSolveArgs<T> a) {
     __shared__ int s_p;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int k = atomicAdd(a.queue, 1);
-            s_p = k < a.nactive ? a.order[k] : -1;
+            int p;
+            do {
+                const int k = atomicAdd(a.queue, 1);
+                p = k < a.nactive ? a.order[k] : -1;
+            } while (p >= 0 && a.run && a.run[p] == 0);
+            s_p = p;
         }
         __syncthreads();
         const int p = s_p;
@@ -439,8 +445,11 @@ __global__ void __launch_bounds__(kGThreads, 1) k_galg2c(GSolveArgs<T> a) {
     cluster_sync();  // every CTA of the cluster has started
     for (;;) {
         if (rank == 0 && threadIdx.x == 0) {
-            const int k = atomicAdd(a.queue, 1);
-            const int p = k < a.nactive ? a.order[k] : -1;
+            int p;
+            do {
+                const int k = atomicAdd(a.queue, 1);
+                p = k < a.nactive ? a.order[k] : -1;
+            } while (p >= 0 && a.run && a.run[p] == 0);
             for (int r = 0; r < C; ++r) st_cluster(cluster_addr(&s_p, r), p);
         }
         cluster_sync();
@@ -732,6 +741,11 @@ struct GroupWork {
     std::vector<aln_problem> last;  // records of the last layout
     int last_prec = -1;
     bool reuse_ok = false;          // last layout used device inputs only
+    // graph of the whole solve (aln_options.group_graph): the rounds as one
+    // captured launch sequence, valid for the key it was captured with
+    cudaGraphExec_t graph = nullptr;
+    double graph_tol = -1.0;
+    int graph_max_iter = -1, graph_x0 = -1, graph_cs = -1;
 };
 
 bool is_dev(const void* p) {
@@ -780,9 +794,49 @@ unsigned grid_for(int64_t work, int threads, int cap) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
+// Host-side state of the solver launches, made once before any of them (and
+// before a stream capture): the side stream with its events, and the number
+// of co-resident clusters of k_galg2c for the current cluster size.
 template <typename T>
-aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, int gmode, int max_iter) {
+aln_status launch_state(aln_ctx* c, GroupWork* g) {
+    if (!g->side) {
+        G_TRY(cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking));
+        G_TRY(cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming));
+        G_TRY(cudaEventCreateWithFlags(&g->join, cudaEventDisableTiming));
+    }
+    G_TRY(cudaFuncSetAttribute(k_galg2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               g->smem_bytes));
+    G_TRY(cudaFuncSetAttribute(k_galg2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               g->smem_bytes));
+    if (g->max_clusters < 0 && g->cluster_size > 1) {
+        const int CS = g->cluster_size;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = CS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kGThreads);
+        cfg.dynamicSmemBytes = g->smem_bytes;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(CS * (c->num_sms / CS));
+        int m = 0;
+        if (cudaOccupancyMaxActiveClusters(&m, k_galg2c<T>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            m = 0;
+        }
+        g->max_clusters = m;
+    }
+    return ALN_OK;
+}
+
+template <typename T>
+aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, int gmode, int max_iter,
+                      const int* run = nullptr) {
     GSolveArgs<T> a;
+    a.run = run;
     a.gp = g->gp;
     a.order = g->order;
     a.nactive = nactive;
@@ -949,6 +1003,15 @@ aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_
 
 }  // namespace
 
+void group_shape(const aln_ctx* c, int* count, int64_t* sum_n, int64_t* max_n) {
+    const GroupWork* g = (const GroupWork*)c->group;
+    *count = g->count;
+    *sum_n = g->sum_n;
+    int64_t m = 0;
+    for (int p = 0; p < g->count; ++p) m = std::max<int64_t>(m, g->hp[p].n);
+    *max_n = m;
+}
+
 void group_free(aln_ctx* c) {
     GroupWork* g = (GroupWork*)c->group;
     if (!g) return;
@@ -958,6 +1021,7 @@ void group_free(aln_ctx* c) {
     if (g->fork) cudaEventDestroy(g->fork);
     if (g->join) cudaEventDestroy(g->join);
     if (g->side) cudaStreamDestroy(g->side);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
     delete g;
     c->group = nullptr;
     c->grouped = 0;
@@ -1175,6 +1239,8 @@ aln_status group_prepare(aln_ctx* c, int32_t count, const aln_problem* probs, in
     G_TRY(cudaEventRecord(c->ev[0], c->stream));
     if (!same) {
         g->reuse_ok = false;
+        if (g->graph) cudaGraphExecDestroy(g->graph);  // its pointers are the old layout's
+        g->graph = nullptr;
         G_CHECK(group_layout(c, g, count, probs, dtype));
     }
     G_TRY(cudaMemsetAsync(g->flags, 0, 4 * sizeof(int), c->stream));
@@ -1270,14 +1336,16 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
         x0 = g->x64;
     }
     const unsigned gv = grid_for(N, 256, 8 * c->num_sms);
-    k_ginit<<<gv, 256, 0, c->stream>>>(g->gp, count, N, x0, g->s, (double*)g->y, g->stat,
-                                       g->fin, g->rounds, g->tgt,
-                                       inner_target(tol, 0.5, 1.0,
-                                                    (f64 || c->opt.refine_gain == 0)
-                                                        ? -1
-                                                        : c->opt.refine_gain));
-    G_TRY(cudaGetLastError());
-    c->launches += 1;
+    if (!c->opt.group_graph) {
+        k_ginit<<<gv, 256, 0, c->stream>>>(g->gp, count, N, x0, g->s, (double*)g->y, g->stat,
+                                           g->fin, g->rounds, g->tgt,
+                                           inner_target(tol, 0.5, 1.0,
+                                                        (f64 || c->opt.refine_gain == 0)
+                                                            ? -1
+                                                            : c->opt.refine_gain));
+        G_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
     G_CHECK(upload_order(c, g, g->order_all));
     HostView h = host_view(g);
     std::vector<int> next;
@@ -1288,7 +1356,62 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
     // later runs restart from the exact FP64 gradient.
     int gmode = 0;
     double iter_ms = 0.0, kkt_ms = 0.0;
-    for (int round = 0;; ++round) {
+    if (c->opt.group_graph) {
+        G_CHECK(f64 ? launch_state<double>(c, g) : launch_state<float>(c, g));
+        const bool same = g->graph && g->graph_tol == tol && g->graph_max_iter == max_iter &&
+                          g->graph_x0 == (x0 ? 1 : 0) && g->graph_cs == g->cluster_size;
+        if (!same) {
+            if (g->graph) cudaGraphExecDestroy(g->graph);
+            g->graph = nullptr;
+            // the launch sequence of a whole solve: the start, round 0 over
+            // every problem, then max_refine rounds over every problem that
+            // pass over those the last FP64 check finished (again[p] = 0);
+            // a problem is final after at most max_refine refinements, so
+            // the result equals the host-driven loop's, problem by problem
+            cudaGraph_t gr = nullptr;
+            G_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            aln_status st = ALN_OK;
+            k_ginit<<<gv, 256, 0, c->stream>>>(g->gp, count, N, x0, g->s, (double*)g->y, g->stat,
+                                               g->fin, g->rounds, g->tgt,
+                                               inner_target(tol, 0.5, 1.0,
+                                                            (f64 || c->opt.refine_gain == 0)
+                                                                ? -1
+                                                                : c->opt.refine_gain));
+            for (int round = 0; st == ALN_OK && round <= c->opt.max_refine; ++round) {
+                st = f64 ? run_solver<double>(c, g, count, round ? 1 : 0, max_iter,
+                                              round ? g->again : nullptr)
+                         : run_solver<float>(c, g, count, round ? 1 : 0, max_iter,
+                                             round ? g->again : nullptr);
+                if (st != ALN_OK) break;
+                k_gunscale<<<gv, 256, 0, c->stream>>>(g->gp, count, N, (const double*)g->y, g->s,
+                                                      g->x64);
+                st = kkt_pass(c, g, tol, max_iter, c->opt.max_refine, 1);
+            }
+            const cudaError_t ec = cudaStreamEndCapture(c->stream, &gr);
+            if (st == ALN_OK && ec == cudaSuccess)
+                st = cudaGraphInstantiate(&g->graph, gr, 0) == cudaSuccess ? ALN_OK : ALN_ERR_CUDA;
+            else if (st == ALN_OK)
+                st = ALN_ERR_CUDA;
+            if (gr) cudaGraphDestroy(gr);
+            if (st != ALN_OK) {
+                cudaGetLastError();
+                g->graph = nullptr;
+                return st;
+            }
+            g->graph_tol = tol;
+            g->graph_max_iter = max_iter;
+            g->graph_x0 = x0 ? 1 : 0;
+            g->graph_cs = g->cluster_size;
+        }
+        G_TRY(cudaEventRecord(c->ev[6], c->stream));
+        G_TRY(cudaGraphLaunch(g->graph, c->stream));
+        G_TRY(cudaEventRecord(c->ev[7], c->stream));
+        G_TRY(cudaStreamSynchronize(c->stream));
+        float a = 0.f;
+        if (cudaEventElapsedTime(&a, c->ev[6], c->ev[7]) == cudaSuccess) iter_ms = a;
+        c->launches += 1;
+    }
+    for (int round = 0; !c->opt.group_graph; ++round) {
         G_TRY(cudaEventRecord(c->ev[6], c->stream));
         G_CHECK(f64 ? run_solver<double>(c, g, nactive, gmode, max_iter)
                     : run_solver<float>(c, g, nactive, gmode, max_iter));

@@ -138,6 +138,8 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
 aln_status group_kkt(aln_ctx* c, const double* X, double* rel_kkt, double* objective);
 aln_status group_export(aln_ctx* c, double* Q, double* q, double* s);
 void group_free(aln_ctx* c);
+// problems, Σ n_p and max n_p of the grouped layout
+void group_shape(const aln_ctx* c, int* count, int64_t* sum_n, int64_t* max_n);
 
 // mlp.cu — learned start point
 aln_status mlp_init(aln_ctx* c, int hidden, uint64_t seed);
@@ -217,6 +219,15 @@ cudaError_t launch_csc_kkt(const int64_t* cp, const int32_t* ri, const float* v,
                            const __nv_bfloat16* lo, const double* x, const float* b,
                            const double* s, double* r, float* rh, float* rl, double* fpart,
                            double* g64, double* gpart, cudaStream_t st);
+
+// api.cu — workspace of the single-problem solver and one persistent run
+aln_status alloc_workspace(aln_ctx* c);
+aln_status run_until_done(aln_ctx* c);
+
+// autotune.cu — launch geometry from the JSON cache, measured on a miss
+// (autotune = 2); called by aln_solve before the solver runs
+aln_status autotune_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t ldx,
+                          const double* X0);
 
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);

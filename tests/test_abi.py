@@ -70,10 +70,15 @@ def test_null_and_invalid_arguments_are_rejected_without_a_device(lib):
     # option checks come before any CUDA call
     for field, bad in (("gram_split", 4), ("group_cluster", 3), ("group_cluster", 16),
                        ("refine_gain", 17), ("iter_kernel", 4), ("wait_limit_us", -1),
-                       ("test_barrier_skew", -1), ("test_barrier_skew", 1025)):
+                       ("test_barrier_skew", -1), ("test_barrier_skew", 1025),
+                       ("group_graph", 2), ("group_graph", -1), ("autotune", 3),
+                       ("autotune", -1), ("autotune", 1), ("autotune", 2)):
         o = aln.aln_default_options()
-        setattr(o, field, bad)
+        setattr(o, field, bad)  # autotune 1 and 2 without a cache path are invalid too
         assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
+    o = aln.aln_default_options()
+    o.autotune, o.autotune_cache = 1, b""
+    assert lib.aln_create(ctypes.byref(ctx), ctypes.byref(o), None) == aln.ERR_INVALID_ARG
     assert lib.aln_set_wait_limit(None, 1000, 0) == aln.ERR_INVALID_ARG
     lib.aln_destroy(None)  # accepted
 
