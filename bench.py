@@ -714,7 +714,10 @@ def run_ours(args):
                                 ("product", "barrier", "update", "clipped", "mask"),
                                 [round(sum(s.phase_us[i] for s in stats) /
                                        max(1, sum(s.iterations for s in stats)), 3)
-                                 for i in range(5)])))},
+                                 for i in range(5)]))),
+                   "batched_ms": (None if k == 1 else
+                                  {"chunks": round(avg(lambda s: s.phase_us[0]) / 1e3, 3),
+                                   "tail": round(avg(lambda s: s.phase_us[1]) / 1e3, 3)})},
         "roofline": rooflines[0],
         "roofline_secondary": rooflines[1] if len(rooflines) > 1 else None,
         "cpu_baseline": cpu,

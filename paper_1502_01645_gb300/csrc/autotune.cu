@@ -430,10 +430,12 @@ aln_status tune_batched(aln_ctx* c, double tol, int max_iter, double* X, int64_t
         ch <= 64.0 && tl >= 1.0 && tl <= 64.0 * S) {
         c->tune_chunk = (int)ch;
         c->tune_tail = (int)tl;
+        double bu = 0.0;  // optional: iterations per tail launch
+        c->tune_budget = get(f, "tail_budget", &bu) && bu >= 1.0 && bu <= 1e6 ? (int)bu : 0;
         c->tuned_key = key;
         return ALN_OK;
     }
-    c->tune_chunk = c->tune_tail = 0;
+    c->tune_chunk = c->tune_tail = c->tune_budget = 0;
     if (c->opt.autotune < 2) {
         c->tuned_key = key;
         return ALN_OK;

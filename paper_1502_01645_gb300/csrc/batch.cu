@@ -23,6 +23,9 @@
 namespace aln {
 
 constexpr int kBThreads = 256;
+// Tail launches: iterations a column runs before the cluster size is chosen
+// again (the last launch, at the largest cluster, has no budget).
+constexpr int kTailBudget = 64;
 
 // Q (FP32, [n][ldq]) → hi/lo BF16 [n][ldk], zero-padded columns n..ldk.
 __global__ void k_qsplit(const double* __restrict__ Q64, int64_t ldq, int64_t n, int64_t ldk,
@@ -543,149 +546,62 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
 }
 
 // ---------------------------------------------------------------------------
-// Tail of the batched phase: one 1024-thread block per running column.
-// Once few columns are still running, each batched iteration is dominated by
-// launch and tile latency (about 30-90 µs per iteration whatever the count),
-// while one block runs a column's iteration from L2-resident Q32 in a few
-// µs.  The block takes the next running column from a queue (counters[2]),
-// runs Alg. 2 on it to its stop with the same rules and per-column state as
-// k_bmask / k_bupdate (FP32 iterate, FP64 sums of the step scalars), and
-// writes y, g and the state back for the FP64 check.
-__global__ void __launch_bounds__(kGThreads, 1) k_bblock(BatchState s, const float* __restrict__ Q32) {
-    extern __shared__ __align__(16) uint8_t bsm[];
-    __shared__ GRed<float> rs;
-    __shared__ int s_c, s_flag;
-    __shared__ float s_alpha;
-    const int n = (int)s.n;
-    const int ldq = (int)s.ldq;
-    float* sy = reinterpret_cast<float*>(bsm);
-    float* sg = sy + ldq;
-    float* sgb = sg + ldq;
-    float* sw = sgb + ldq;  // w = Qḡ, then e
-    int* lp = reinterpret_cast<int*>(sw + ldq);
-    int* lc = lp + ldq;
-    float* red = reinterpret_cast<float*>(lc + ldq);
-    for (;;) {
-        if (threadIdx.x == 0) s_c = atomicAdd(&s.counters[2], 1);
-        __syncthreads();
-        const int64_t c = s_c;
-        __syncthreads();
-        if (c >= s.k) break;
-        if (s.colst[c] >= 0) continue;  // block-uniform
-        for (int i = threadIdx.x; i < ldq; i += blockDim.x) {
-            sy[i] = i < n ? s.Y[c * s.ldq + i] : 0.0f;
-            sg[i] = i < n ? s.G[c * s.ldq + i] : 0.0f;
-            sw[i] = 0.0f;
-        }
-        __syncthreads();
-        int it = s.iters[c], best_iter = s.best_iter[c], status = -1;
-        double best = s.best[c];
-        const double eps = s.eps[c];
-        const int max_iter = s.limits[0], window = s.limits[1];
-        unsigned long long rowsP = 0, rowsC = 0, clipIt = 0;
-        double gam;
-        int cntP, cntL;
-        gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
-        for (;;) {
-            if (threadIdx.x == 0) {
-                int st = -1;
-                if (!isfinite(gam)) st = ALN_RHS_NONFINITE;
-                else if (cntP == 0) st = ALN_RHS_EMPTY_PASSIVE;
-                else if (gam < eps || gam == 0.0) st = ALN_RHS_CONVERGED;
-                else if (it >= max_iter) st = ALN_RHS_MAXITER;
-                else if (it - best_iter > window) st = ALN_RHS_STAGNATED;
-                if (st < 0 && gam < best) {
-                    best = gam;
-                    best_iter = it;
-                }
-                status = st;
-                s_flag = st >= 0;
-            }
-            __syncthreads();
-            if (s_flag) break;
-            rowsP += (unsigned long long)cntP;
-            // w = Qḡ over the listed rows, κ = ḡᵀw, α = γ/κ
-            gmv(Q32, ldq, 0, n, lp, cntL, sgb, sw, false, red);
-            float kp = 0.0f;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fmaf(sgb[i], sw[i], kp);
-            double kap;
-            int u1, u2;
-            (void)block_totals(&rs, kp, 0, 0, &kap, &u1, &u2);
-            if (threadIdx.x == 0) {
-                int st = -1;
-                if (!isfinite(kap)) st = ALN_RHS_NONFINITE;
-                else if (kap <= 0.0) st = ALN_RHS_CURVATURE;
-                s_alpha = st >= 0 ? 0.0f : (float)(gam / kap);
-                if (st >= 0) status = st;
-                s_flag = st >= 0;
-            }
-            __syncthreads();
-            if (s_flag) break;
-            const float a = s_alpha;
-            // y⁺ = [y − αḡ]₊, g ← g − αw, e on the clipped set (then g += Qe)
-            int nclip = 0;
-            {
-                const int lane = threadIdx.x & 31;
-                int c0, c1;
-                warp_chunks(n, c0, c1);
-                int cl = 0;
-                for (int ch = c0; ch < c1; ++ch) {
-                    const int i = ch * 32 + lane;
-                    float ei = 0.0f;
-                    if (i < n) {
-                        const float yi = sy[i];
-                        const float step = a * sgb[i];
-                        float yn = yi - step;
-                        if (yn < 0.0f) {
-                            ei = step - yi;
-                            yn = 0.0f;
-                        }
-                        sy[i] = yn;
-                        sg[i] = sg[i] - a * sw[i];
-                        sw[i] = ei;
-                    }
-                    cl += __popc(__ballot_sync(0xffffffffu, ei != 0.0f));
-                }
-                double vt;
-                int ct;
-                int base = block_totals(&rs, 0.0f, 0, cl, &vt, &ct, &nclip);
-                for (int ch = c0; ch < c1; ++ch) {
-                    const int i = ch * 32 + lane;
-                    const bool nz = i < n && sw[i] != 0.0f;
-                    const unsigned int m = __ballot_sync(0xffffffffu, nz);
-                    if (nz) lc[base + __popc(m & ((1u << lane) - 1u))] = i;
-                    base += __popc(m);
-                }
-                __syncthreads();
-            }
-            ++it;
-            if (nclip > 0) {
-                rowsC += (unsigned long long)nclip;
-                ++clipIt;
-                gmv(Q32, ldq, 0, n, lc, nclip, sw, sg, true, red);
-            }
-            gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            s.Y[c * s.ldq + i] = sy[i];
-            s.G[c * s.ldq + i] = sg[i];
-        }
-        if (threadIdx.x == 0) {
-            s.colst[c] = status;
-            s.iters[c] = it;
-            s.best[c] = best;
-            s.best_iter[c] = best_iter;
-            atomicAdd(&s.rows[0], rowsP);
-            atomicAdd(&s.rows[1], rowsC);
-            atomicAdd(&s.rows[2], clipIt);
-        }
-        __syncthreads();
+// Tail of the batched phase.  Once few columns are still running, a batched
+// iteration is bound by launch and tile latency (about 30-90 µs whatever the
+// count), and the last columns run hundreds of iterations more than the
+// median one.  They go to the grouped solver's kernels: each running column
+// is one problem (shared Q, its own q, y and stop state), solved by one CTA
+// or, as the count drops, by a thread-block cluster that splits each product
+// over its CTAs; the launches are cut into iteration budgets so that the
+// cluster size can grow as columns finish.
+// ---------------------------------------------------------------------------
+
+// Hand-off: y and g of every running column in FP64 (the grouped kernels keep
+// y as an FP32 pair and g in FP32), its record, its inner target relative to ‖min(q,0)‖ (so that
+// (tgt·den)² is the column's ε), and the list of running columns.
+__global__ void k_btail_in(BatchState s, const double* __restrict__ den, double* __restrict__ Y64,
+                           double* __restrict__ G64, GStat* __restrict__ st,
+                           double* __restrict__ tgt, int* __restrict__ order,
+                           int* __restrict__ cnt) {
+    const int64_t c = blockIdx.x;
+    if (s.colst[c] >= 0) return;
+    for (int64_t i = threadIdx.x; i < s.ldq; i += blockDim.x) {
+        const bool in = i < s.n;
+        Y64[c * s.ldq + i] = in ? (double)s.Y[c * s.ldq + i] : 0.0;
+        G64[c * s.ldq + i] = in ? (double)s.G[c * s.ldq + i] : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        GStat z = {};
+        z.iters = s.iters[c];
+        z.status = -1;
+        st[c] = z;
+        const double d = den[c] > 0.0 ? den[c] : 1.0;
+        tgt[c] = sqrt(s.eps[c]) / d;
+        order[atomicAdd(cnt, 1)] = (int)c;
     }
 }
 
-static size_t bblock_smem(int64_t ldq) {
-    return (size_t)ldq * (4 * sizeof(float) + 2 * sizeof(int)) +
-           (size_t)kGWarps * 32 * 4 * sizeof(float);
+// After a tail launch (one block per listed column): y back in FP32; paused
+// columns are listed again for the next launch, the others take their final
+// inner status and add their row counts.
+__global__ void k_btail_out(BatchState s, const double* __restrict__ Y64,
+                            const GStat* __restrict__ st, const int* __restrict__ order,
+                            int* __restrict__ order2, int* __restrict__ cnt2) {
+    const int64_t c = order[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x)
+        s.Y[c * s.ldq + i] = (float)Y64[c * s.ldq + i];
+    if (threadIdx.x == 0) {
+        const GStat g = st[c];
+        s.iters[c] = g.iters;
+        if (g.status == kRhsPaused) {
+            order2[atomicAdd(cnt2, 1)] = (int)c;
+        } else {
+            s.colst[c] = g.status;
+            atomicAdd(&s.rows[0], (unsigned long long)g.sum_passive);
+            atomicAdd(&s.rows[1], (unsigned long long)g.sum_clip);
+            atomicAdd(&s.rows[2], (unsigned long long)g.clip_iters);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -719,6 +635,15 @@ struct BatchWork {
     cudaGraphExec_t graph = nullptr;
     int chunk = 8;
     int small_vpl = 0;            // n ≤ 128: entries per lane of k_bsmall (1, 2, 4), else 0
+    // tail (grouped kernels): one problem record per column, records, inner
+    // targets, two column lists, counters [0] listed, [1] relisted, [2] queue
+    void* tail = nullptr;
+    size_t tail_bytes = 0;
+    GProb* tgp = nullptr;
+    GStat* tstat = nullptr;
+    double* ttgt = nullptr;
+    int* torder = nullptr;
+    int* tcnt = nullptr;
 };
 
 static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
@@ -827,6 +752,52 @@ static cudaError_t bw_iteration(aln_ctx* c, BatchWork* b) {
                            c->stream);
 }
 
+__global__ void k_btail_records(GProb* __restrict__ gp, int64_t k, int64_t d, int64_t n,
+                                int64_t ldq) {
+    const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= k) return;
+    GProb g = {};
+    g.d = (int32_t)d;
+    g.n = (int32_t)n;
+    g.ldq = (int32_t)ldq;
+    g.qoff = 0;
+    g.voff = col * ldq;
+    g.foff = col * ldq;
+    gp[col] = g;
+}
+
+// Buffers of the tail and its problem records: column c is a problem of n
+// unknowns over the shared Q (qoff 0), its q and y at c·ldq.
+static aln_status bw_tail_alloc(aln_ctx* c, BatchWork* b) {
+    const int64_t k = b->k;
+    const size_t need = round_up(k * sizeof(GProb), 256) + round_up(k * sizeof(GStat), 256) +
+                        round_up(k * 8, 256) + round_up(2 * k * 4, 256) + 256;
+    if (b->tail_bytes < need) {
+        if (b->tail) cudaFree(b->tail);
+        b->tail = nullptr;
+        b->tail_bytes = 0;
+        if (cudaMalloc(&b->tail, need) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        b->tail_bytes = need;
+    }
+    uint8_t* p = (uint8_t*)b->tail;
+    b->tgp = (GProb*)p;
+    p += round_up(k * sizeof(GProb), 256);
+    b->tstat = (GStat*)p;
+    p += round_up(k * sizeof(GStat), 256);
+    b->ttgt = (double*)p;
+    p += round_up(k * 8, 256);
+    b->torder = (int*)p;
+    p += round_up(2 * k * 4, 256);
+    b->tcnt = (int*)p;
+    k_btail_records<<<(unsigned)ceil_div(k, 256), 256, 0, c->stream>>>(b->tgp, k, c->d, b->n,
+                                                                          b->ldq);
+    c->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? ALN_OK : ALN_ERR_CUDA;
+}
+
 static aln_status bw_capture(aln_ctx* c, BatchWork* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -851,6 +822,7 @@ void batch_free(aln_ctx* c) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->pool) cudaFree(b->pool);
+    if (b->tail) cudaFree(b->tail);
     if (b->host) cudaFreeHost(b->host);
     delete b;
     c->batch = nullptr;
@@ -870,6 +842,8 @@ aln_status batch_prepare(aln_ctx* c) {
         }
     }
     aln_status st = bw_alloc(c, b);
+    if (st != ALN_OK) return st;
+    st = bw_tail_alloc(c, b);
     if (st != ALN_OK) return st;
     const cudaError_t eg =
         c->dtype == ALN_DTYPE_F32
@@ -991,21 +965,50 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         c->launches += 3;
     }
     const int max_refine = c->opt.max_refine;
-    // tail: at most tail_max running columns go to k_bblock (one block each)
+    // tail: at most tail_max running columns go to the grouped kernels
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-    const size_t tsmem = bblock_smem(c->ldq);
-    const bool tail_ok = !b->small_vpl && tsmem + 1024 <= (size_t)optin;
+    const bool tail_ok = !b->small_vpl && tail_smem_bytes(c->ldq, false) + 1024 <= (size_t)optin;
+    const bool tail_cl = tail_ok && tail_smem_bytes(c->ldq, true) + 1024 <= (size_t)optin;
     const int64_t tail_max = c->tune_tail > 0 ? (int64_t)c->tune_tail : 2LL * c->num_sms;
-    auto run_tail = [&](int64_t running) -> aln_status {
-        if (cudaFuncSetAttribute(k_bblock, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tsmem) != cudaSuccess ||
-            cudaMemsetAsync(s.counters + 2, 0, sizeof(int), c->stream) != cudaSuccess)
+    const int budget = c->tune_budget > 0 ? c->tune_budget : kTailBudget;
+    auto run_tail = [&]() -> aln_status {
+        int* cur = b->torder;
+        int* nxt = b->torder + k;
+        if (cudaMemsetAsync(b->tcnt, 0, 2 * sizeof(int), c->stream) != cudaSuccess)
             return ALN_ERR_CUDA;
-        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(running, c->num_sms));
-        k_bblock<<<grid, kGThreads, tsmem, c->stream>>>(s, (const float*)c->Q);
-        if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
+        // (G64 is free until the FP64 check: it carries g between launches)
+        k_btail_in<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->den, b->Y64, b->G64,
+                                                             b->tstat, b->ttgt, cur, b->tcnt);
         c->launches += 1;
+        if (cudaMemcpyAsync(b->host + 2, b->tcnt, sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return ALN_ERR_CUDA;
+        int count = b->host[2];
+        while (count > 0) {
+            // the largest cluster that still gives every column its own
+            // CTAs; no budget once the cluster cannot grow any more
+            int cs = 1;
+            while (tail_cl && cs < 8 && (int64_t)count * cs * 2 <= c->num_sms) cs *= 2;
+            const int bud = (cs < 8 && count > 1) ? budget : 0;
+            aln_status ts = tail_launch(c, b->tgp, cur, count, b->tcnt + 2, (const float*)c->Q,
+                                        c->ldq, c->q64, c->den, b->Y64, b->G64, b->tstat,
+                                        b->ttgt, max_iter, bud, cs);
+            if (ts != ALN_OK) return ts;
+            if (cudaMemsetAsync(b->tcnt + 1, 0, sizeof(int), c->stream) != cudaSuccess)
+                return ALN_ERR_CUDA;
+            k_btail_out<<<(unsigned)count, kBThreads, 0, c->stream>>>(s, b->Y64, b->tstat, cur,
+                                                                      nxt, b->tcnt + 1);
+            c->launches += 1;
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(b->host + 2, b->tcnt + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                                c->stream) != cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess)
+                return ALN_ERR_CUDA;
+            count = b->host[2];
+            std::swap(cur, nxt);
+        }
         return ALN_OK;
     };
     int64_t active = k;  // running columns at the start of a round
@@ -1041,7 +1044,8 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         }
         bool handed = false;
         if (tail_ok && active <= tail_max) {  // few columns: no batched chunk at all
-            aln_status ts = run_tail(active);
+            cudaEventRecord(c->ev[10], c->stream);
+            aln_status ts = run_tail();
             if (ts != ALN_OK) return ts;
             handed = true;
             l = bound;
@@ -1054,8 +1058,9 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
                 cudaStreamSynchronize(c->stream) != cudaSuccess)
                 return ALN_ERR_CUDA;
             if (b->host[0] == 0) break;
-            if (tail_ok && b->host[0] <= tail_max) {  // the rest, one block per column
-                aln_status ts = run_tail(b->host[0]);
+            if (tail_ok && b->host[0] <= tail_max) {  // the rest: the tail
+                cudaEventRecord(c->ev[10], c->stream);
+                aln_status ts = run_tail();
                 if (ts != ALN_OK) return ts;
                 handed = true;
                 break;
@@ -1063,9 +1068,12 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
         }
         cudaEventRecord(c->ev[9], c->stream);
         cudaEventSynchronize(c->ev[9]);
-        float ms = 0.f;
+        float ms = 0.f, tms = 0.f;
         if (cudaEventElapsedTime(&ms, c->ev[8], c->ev[9]) == cudaSuccess)
             c->stats.iterate_ms += ms;
+        if (handed && cudaEventElapsedTime(&tms, c->ev[10], c->ev[9]) == cudaSuccess)
+            c->stats.phase_us[1] += 1e3 * tms;
+        c->stats.phase_us[0] += 1e3 * (ms - (handed ? tms : 0.f));
         if (!b->small_vpl && !handed && l == bound) return ALN_ERR_TIMEOUT;
         int restarted = 0;
         aln_status st = bw_check(c, b, tol, max_refine, &restarted);

@@ -297,7 +297,7 @@ struct aln_ctx {
     void* nmf = nullptr;     // aln_nmf work buffers (nmf.cu)
 
     // statistics (aln_get_stats)
-    cudaEvent_t ev[10] = {};
+    cudaEvent_t ev[12] = {};
     // host-input prepare: A copied in column chunks on copy_stream, each
     // chunk's column statistics and Gram tile rows run as it lands
     cudaStream_t copy_stream = nullptr;
@@ -313,6 +313,7 @@ struct aln_ctx {
     std::string tuned_key;
     int tune_pR = 0;     // row groups of the persistent Alg. 2 kernel (0 = derived)
     int tune_chunk = 0;  // batched solver: iterations per captured chunk (0 = 8)
-    int tune_tail = 0;   // batched solver: running columns handed to one block each
+    int tune_tail = 0;   // batched solver: running columns handed to the tail
                          // (0 = 2 per SM)
+    int tune_budget = 0; // batched tail: iterations per launch (0 = 64)
 };

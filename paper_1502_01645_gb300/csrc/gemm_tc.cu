@@ -166,20 +166,15 @@ __device__ __forceinline__ void gram_store(const float (&acc)[BM], int64_t row, 
     }
 }
 
-// One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
-// The loader is taken by value: a loader may keep a cursor over the K blocks
-// it copies (k_sgram_tc); load() is called for the blocks in order.
-//
-// Split K (part ≠ null): this CTA is chunk c of S of its tile pair; it writes
-// its unscaled partial tile to part + c·128² (part points at the pair's first
-// slot), and the pair's last chunk to arrive on *ticket adds the S partials
-// in slot order — a fixed order, whichever CTA is last — and stores the tile.
+// One 128×128 output tile of a split product, accumulated in FP32 registers:
+// acc[c] of the promotion warps (warp w ≥ 2 holds tile row 32·(w mod 4) +
+// lane) = Σ_K A[row]·B[c] over the num_kb K blocks the loader copies (A and B
+// boxes of NS terms each; diag: B = A, one set of boxes).  Sets up and frees
+// its barriers and tensor memory; returns false (uniformly) when a bounded
+// wait expired — nothing is then in flight and acc is incomplete.
 template <int NS, class Loader>
-__device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
-                                           int64_t n0, int64_t n, const double* __restrict__ inv_s,
-                                           float* __restrict__ Q, int64_t ldq,
-                                           int* timeout_flag, float* part = nullptr, int S = 1,
-                                           int c = 0, unsigned int* ticket = nullptr) {
+__device__ __forceinline__ bool promoted_tile(Loader& ld, int num_kb, bool diag,
+                                              float (&acc)[BM]) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     using C = GramCfg<NS>;
@@ -189,9 +184,7 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
     uint64_t* tempty = tfull + 2;
     uint64_t* done = tempty + 2;
     uint32_t* tmem_slot = (uint32_t*)(done + 1);
-    __shared__ float s_cs[BM];
     __shared__ int s_abort;
-    __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -207,10 +200,6 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < BM) {
-        const int64_t j = n0 + threadIdx.x;
-        s_cs[threadIdx.x] = j < n ? (float)inv_s[j] : 0.0f;
-    }
     if (warp == 1) {
         tmem_alloc(tmem_slot, G3_TMEM_COLS);
         tmem_relinquish();
@@ -219,7 +208,6 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    float acc[BM];
 #pragma unroll
     for (int c = 0; c < BM; ++c) acc[c] = 0.0f;
 
@@ -285,49 +273,78 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
     }
     tc_fence_after();
     __syncthreads();
-    if (!s_abort && part == nullptr) {
-        if (warp >= 2)
-            gram_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
-    } else if (!s_abort) {
-        const int row = 32 * (warp & 3) + lane;
-        if (warp >= 2) {
-            float4* dst = reinterpret_cast<float4*>(part + ((int64_t)c * BM + row) * BM);
-#pragma unroll
-            for (int t = 0; t < BM / 4; ++t)
-                __stcg(dst + t, make_float4(acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
-                                            acc[4 * t + 3]));
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (unsigned int)(S - 1);
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            if (warp >= 2) {
-#pragma unroll
-                for (int t = 0; t < BM; ++t) acc[t] = 0.0f;
-                for (int q = 0; q < S; ++q) {
-                    const float4* src =
-                        reinterpret_cast<const float4*>(part + ((int64_t)q * BM + row) * BM);
-#pragma unroll
-                    for (int t = 0; t < BM / 4; ++t) {
-                        const float4 v = __ldcg(src + t);
-                        acc[4 * t] += v.x;
-                        acc[4 * t + 1] += v.y;
-                        acc[4 * t + 2] += v.z;
-                        acc[4 * t + 3] += v.w;
-                    }
-                }
-                gram_store(acc, m0 + row, n0, diag, n, inv_s, s_cs, Q, ldq);
-            }
-            if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
-        }
-    } else if (threadIdx.x == 0) {
-        atomicExch(timeout_flag, 1);
-    }
+    const bool ok = !s_abort;
     tc_fence_before();
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
+    return ok;
+}
+
+// One lower-triangle output tile of Q = D⁻¹HD⁻¹ (rows m0.., columns n0..).
+// The loader is taken by value: a loader may keep a cursor over the K blocks
+// it copies (k_sgram_tc); load() is called for the blocks in order.
+//
+// Split K (part ≠ null): this CTA is chunk c of S of its tile pair; it writes
+// its unscaled partial tile to part + c·128² (part points at the pair's first
+// slot), and the pair's last chunk to arrive on *ticket adds the S partials
+// in slot order — a fixed order, whichever CTA is last — and stores the tile.
+template <int NS, class Loader>
+__device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
+                                           int64_t n0, int64_t n, const double* __restrict__ inv_s,
+                                           float* __restrict__ Q, int64_t ldq,
+                                           int* timeout_flag, float* part = nullptr, int S = 1,
+                                           int c = 0, unsigned int* ticket = nullptr) {
+    __shared__ float s_cs[BM];
+    __shared__ int s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < BM) {  // visible after promoted_tile's first barrier
+        const int64_t j = n0 + threadIdx.x;
+        s_cs[threadIdx.x] = j < n ? (float)inv_s[j] : 0.0f;
+    }
+    float acc[BM];
+    const bool ok = promoted_tile<NS>(ld, num_kb, diag, acc);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicExch(timeout_flag, 1);
+        return;
+    }
+    if (part == nullptr) {
+        if (warp >= 2)
+            gram_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
+        return;
+    }
+    const int row = 32 * (warp & 3) + lane;
+    if (warp >= 2) {
+        float4* dst = reinterpret_cast<float4*>(part + ((int64_t)c * BM + row) * BM);
+#pragma unroll
+        for (int t = 0; t < BM / 4; ++t)
+            __stcg(dst + t, make_float4(acc[4 * t], acc[4 * t + 1], acc[4 * t + 2],
+                                        acc[4 * t + 3]));
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (unsigned int)(S - 1);
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (warp >= 2) {
+#pragma unroll
+            for (int t = 0; t < BM; ++t) acc[t] = 0.0f;
+            for (int q = 0; q < S; ++q) {
+                const float4* src =
+                    reinterpret_cast<const float4*>(part + ((int64_t)q * BM + row) * BM);
+#pragma unroll
+                for (int t = 0; t < BM / 4; ++t) {
+                    const float4 v = __ldcg(src + t);
+                    acc[4 * t] += v.x;
+                    acc[4 * t + 1] += v.y;
+                    acc[4 * t + 2] += v.z;
+                    acc[4 * t + 3] += v.w;
+                }
+            }
+            gram_store(acc, m0 + row, n0, diag, n, inv_s, s_cs, Q, ldq);
+        }
+        if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
+    }
 }
 
 template <int NS>

@@ -41,16 +41,6 @@ constexpr int kKeySlot = 0, kKeyV = 1, kKeyR = 2;
 constexpr int kGCluster = 4;
 constexpr int kGClusterMinN = 512;
 
-struct GStat {
-    int32_t iters;        // Alg. 2 iterations, summed over rounds
-    int32_t status;       // inner stop reason of the last run (aln_rhs_status)
-    int32_t clip_iters;   // iterations that needed the clipped correction
-    int32_t npassive;     // |P| at the end of the last run
-    int64_t sum_passive;  // Σ |P_k| (rows of Q read for Qḡ)
-    int64_t sum_clip;     // Σ |C_k|
-    double gbar2;         // ‖ḡ‖² (iteration precision) at the end of the last run
-};
-
 template <int KEY>
 __device__ __forceinline__ int64_t gkey(const GProb& g) {
     return KEY == kKeySlot ? g.slot : (KEY == kKeyV ? g.voff : g.roff);
@@ -203,6 +193,10 @@ struct GSolveArgs {
     int smem_bytes;
     const int* run;        // nullable: problems p with run[p] = 0 are passed over
                            // (the graph-captured refinement rounds)
+    int budget;            // > 0: a problem stops with kRhsPaused after this many
+                           // iterations of this launch (the batched solver's tail)
+    double* gout;          // nullable, packed (voff): g at the end of the run, so
+                           // that a paused problem resumes with it (gmode 1)
 };
 
 // --- thread-block clusters (large problems, several CTAs per problem): cluster.cuh
@@ -294,6 +288,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
 
     const double eps = sf * sf;
     const int max_iter = a.max_iter, window = a.window;
+    const int iter0 = st.iters;
     int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
     double best = 1.0 / 0.0;
     int64_t sum_passive = 0, sum_clip = 0;
@@ -309,6 +304,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
             else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
             else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
+            else if (a.budget > 0 && iter - iter0 >= a.budget) status = kRhsPaused;
             else stop = 0;
             if (!stop && gam < best) {
                 best = gam;
@@ -398,8 +394,10 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
         gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
     }
     if (!CL || rank == 0)
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
             a.y[P.foff + i] = (double)sy[i] + (double)syl[i];
+            if (a.gout) a.gout[P.voff + i] = (double)sg[i];
+        }
     if (threadIdx.x == 0 && (!CL || rank == 0)) {
         st.iters = iter;
         st.status = status;
@@ -837,6 +835,8 @@ aln_status run_solver(aln_ctx* c, GroupWork* g, int nactive, int gmode, int max_
                       const int* run = nullptr) {
     GSolveArgs<T> a;
     a.run = run;
+    a.budget = 0;
+    a.gout = nullptr;
     a.gp = g->gp;
     a.order = g->order;
     a.nactive = nactive;
@@ -1002,6 +1002,78 @@ aln_status kkt_pass(aln_ctx* c, GroupWork* g, double tol, int max_iter, int max_
 }
 
 }  // namespace
+
+size_t tail_smem_bytes(int64_t ldq, bool cluster) {
+    return (size_t)round_up(gsolve_static_bytes<float>((int)ldq, cluster), 128);
+}
+
+// Alg. 2 on `count` columns that share one FP32 Q (the batched solver's
+// tail): column order[i] is problem order[i] of the grouped kernels (gp holds
+// one record per column: qoff 0, voff = foff = column·ldq), solved by one CTA
+// (cs = 1) or by a cluster of cs CTAs, from y (FP64, in/out) and the
+// gradient g (FP64, in/out: the batched phase's FP32 gradient carried on, not
+// re-formed from y, whose FP32 product would cost the accuracy the refinement
+// rounds buy); budget > 0 pauses a column after that many iterations of this
+// launch (status kRhsPaused).
+aln_status tail_launch(aln_ctx* c, const GProb* gp, const int* order, int count, int* queue,
+                       const float* Q, int64_t ldq, const double* q64, const double* den,
+                       double* y, double* g, GStat* stat, const double* tgt, int max_iter,
+                       int budget, int cs) {
+    if (count <= 0) return ALN_OK;
+    if (cs != 1 && cs != 2 && cs != 4 && cs != 8) return ALN_ERR_INVALID_ARG;
+    GSolveArgs<float> a;
+    a.gp = gp;
+    a.order = order;
+    a.nactive = count;
+    a.queue = queue;
+    a.Q = Q;
+    a.q64 = q64;
+    a.g64 = g;
+    a.gout = g;
+    a.den = den;
+    a.y = y;
+    a.stat = stat;
+    a.tgt = tgt;
+    a.gmode = 1;
+    a.max_iter = max_iter;
+    a.window = c->opt.stagnation;
+    a.run = nullptr;
+    a.budget = budget;
+    a.smem_bytes = (int)tail_smem_bytes(ldq, cs > 1);
+    G_TRY(cudaMemsetAsync(queue, 0, sizeof(int), c->stream));
+    if (cs == 1) {
+        G_TRY(cudaFuncSetAttribute(k_galg2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   a.smem_bytes));
+        const unsigned grid = (unsigned)std::min(count, c->num_sms);
+        k_galg2<float><<<grid, kGThreads, a.smem_bytes, c->stream>>>(a);
+        G_TRY(cudaGetLastError());
+        c->launches += 1;
+        return ALN_OK;
+    }
+    G_TRY(cudaFuncSetAttribute(k_galg2c<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               a.smem_bytes));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kGThreads);
+    cfg.dynamicSmemBytes = a.smem_bytes;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(cs * (c->num_sms / cs));
+    int m = 0;
+    if (cudaOccupancyMaxActiveClusters(&m, k_galg2c<float>, &cfg) != cudaSuccess || m <= 0) {
+        cudaGetLastError();
+        return ALN_ERR_UNSUPPORTED;
+    }
+    cfg.gridDim = dim3(cs * std::min(count, m));
+    G_TRY(cudaLaunchKernelEx(&cfg, k_galg2c<float>, a));
+    c->launches += 1;
+    return ALN_OK;
+}
 
 void group_shape(const aln_ctx* c, int* count, int64_t* sum_n, int64_t* max_n) {
     const GroupWork* g = (const GroupWork*)c->group;

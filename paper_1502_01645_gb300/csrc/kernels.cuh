@@ -90,6 +90,8 @@ cudaError_t launch_sgram_tc(int nsplit, const SItem* items, int64_t nitems, cons
 
 // W = Q·V (mode 0, with per-column curvature partials) or g += Q·V (mode 1)
 // over the compacted columns of a batch (batch.cu).
+// q, v: the three BF16 split terms (h, m, l) of Q ([n][ldk]) and of the
+// compacted columns ([kmax][ldk]).
 cudaError_t launch_bgemm_tc(int mode, const __nv_bfloat16* q_hi, const __nv_bfloat16* q_lo,
                             int64_t n, int64_t ldk, const __nv_bfloat16* v_hi,
                             const __nv_bfloat16* v_lo, int64_t kmax, const int* ncols,
@@ -112,6 +114,20 @@ struct GProb {
     int64_t roff;      // first entry in packed d-vectors (Σ_{q<p} d_q)
     int64_t slot;      // first column slot of the prepare grid (Σ_{q<p} 128·T_q)
 };
+// Per-problem record of the grouped Alg. 2 kernels (also the batched tail).
+struct GStat {
+    int32_t iters;        // Alg. 2 iterations, summed over rounds
+    int32_t status;       // inner stop reason of the last run (aln_rhs_status,
+                          // or kRhsPaused)
+    int32_t clip_iters;   // iterations that needed the clipped correction
+    int32_t npassive;     // |P| at the end of the last run
+    int64_t sum_passive;  // Σ |P_k| (rows of Q read for Qḡ)
+    int64_t sum_clip;     // Σ |C_k|
+    double gbar2;         // ‖ḡ‖² (iteration precision) at the end of the last run
+};
+// Inner status of a run stopped by its iteration budget (not a stop rule of
+// Alg. 2: the problem continues in the next launch).
+constexpr int32_t kRhsPaused = 64;
 // One lower-triangle output tile (tm ≥ tn) of one problem's Gram.
 struct GTile {
     int32_t p, tm, tn, pad;
@@ -138,6 +154,14 @@ aln_status group_solve(aln_ctx* c, double tol, int max_iter, double* X, const do
 aln_status group_kkt(aln_ctx* c, const double* X, double* rel_kkt, double* objective);
 aln_status group_export(aln_ctx* c, double* Q, double* q, double* s);
 void group_free(aln_ctx* c);
+// Alg. 2 on columns sharing one FP32 Q by the grouped kernels (one CTA or a
+// cluster of cs per column); the batched solver's tail
+aln_status tail_launch(aln_ctx* c, const GProb* gp, const int* order, int count, int* queue,
+                       const float* Q, int64_t ldq, const double* q64, const double* den,
+                       double* y, double* g, GStat* stat, const double* tgt, int max_iter,
+                       int budget, int cs);
+// Dynamic shared memory of one tail CTA for row length ldq
+size_t tail_smem_bytes(int64_t ldq, bool cluster);
 // problems, Σ n_p and max n_p of the grouped layout
 void group_shape(const aln_ctx* c, int* count, int64_t* sum_n, int64_t* max_n);
 

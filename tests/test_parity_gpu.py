@@ -405,9 +405,10 @@ def test_batched_multi_rhs_matches_oracle(aln):
 
 def test_batched_phase_then_tail(aln):
     """More columns than the tail threshold (2 per SM): the tcgen05 batched
-    phase runs first and hands the last columns to the per-column block
-    kernel; every column meets the FP64 KKT gate and agrees with the single
-    right-hand-side path."""
+    phase runs first and hands the last columns to the tail (one CTA per
+    column, then thread-block clusters as columns finish, in budgeted
+    launches); every column meets the FP64 KKT gate and agrees with the
+    single right-hand-side path."""
     p = W.shared_multi_rhs(d=1200, n=180, k=420, seed=38)
     with aln.Solver("split_bf16") as s:
         s.prepare(p.A, p.B)
