@@ -84,122 +84,181 @@ __global__ void k_breset(int* counters) {
     counters[1] = 0;
 }
 
+// Mask and update run one 128-thread block per column: each block's work is a
+// short chain of dependent steps (scan, block reduction, one thread's
+// decision and atomics, split), so more resident blocks per SM hide more of
+// its latency than wider blocks would.  Both read and write the column
+// vectors as float4 (ldq is a multiple of 128; entries n..ldq are zero).
+constexpr int kBMThreads = 128;
+constexpr int kBMWarps = kBMThreads / 32;
+
+// 4 FP32 values → their BF16 hi and lo parts (v = hi + lo + O(2⁻¹⁶|v|)).
+__device__ __forceinline__ void split4(float4 v, uint2* hi, uint2* lo) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    const __nv_bfloat162 l0 = __floats2bfloat162_rn(v.x - f0.x, v.y - f0.y);
+    const __nv_bfloat162 l1 = __floats2bfloat162_rn(v.z - f1.x, v.w - f1.y);
+    uint2 H, L;
+    H.x = *reinterpret_cast<const unsigned int*>(&h0);
+    H.y = *reinterpret_cast<const unsigned int*>(&h1);
+    L.x = *reinterpret_cast<const unsigned int*>(&l0);
+    L.y = *reinterpret_cast<const unsigned int*>(&l1);
+    *hi = H;
+    *lo = L;
+}
+
+// Split row p of the compacted operand from v (float4 entries < n4, zero
+// beyond, up to ldk).
+__device__ __forceinline__ void split_row(const BatchState& s, int p, const float4* v, int n4) {
+    uint2* hi = reinterpret_cast<uint2*>(s.Vhi + (int64_t)p * s.ldk);
+    uint2* lo = reinterpret_cast<uint2*>(s.Vlo + (int64_t)p * s.ldk);
+    const int k4 = (int)(s.ldk >> 2);
+    for (int i = threadIdx.x; i < k4; i += kBMThreads)
+        split4(i < n4 ? v[i] : make_float4(0.f, 0.f, 0.f, 0.f), hi + i, lo + i);
+}
+
 // One block per column: mask, γ, |P|, stop rules, compaction, split of ḡ.
-__global__ void __launch_bounds__(kBThreads) k_bmask(BatchState s) {
-    __shared__ double sc[32];
-    __shared__ int si[32];
+__global__ void __launch_bounds__(kBMThreads) k_bmask(BatchState s) {
+    __shared__ double sc[kBMWarps];
+    __shared__ int si[kBMWarps];
     __shared__ int s_slot;
     const int64_t c = blockIdx.x;
     if (s.colst[c] >= 0) return;
-    const float* y = s.Y + c * s.ldq;
-    const float* g = s.G + c * s.ldq;
-    float* gb = s.GB + c * s.ldq;
+    // the column's stop state, loaded before the scan so that its latency
+    // overlaps it (thread 0 decides)
+    int it = 0, best_it = 0, lim_it = 0, lim_win = 0;
+    double eps = 0.0, best = 0.0;
+    if (threadIdx.x == 0) {
+        it = s.iters[c];
+        best_it = s.best_iter[c];
+        eps = s.eps[c];
+        best = s.best[c];
+        lim_it = s.limits[0];
+        lim_win = s.limits[1];
+    }
+    const float4* y4 = reinterpret_cast<const float4*>(s.Y + c * s.ldq);
+    const float4* g4 = reinterpret_cast<const float4*>(s.G + c * s.ldq);
+    float4* gb4 = reinterpret_cast<float4*>(s.GB + c * s.ldq);
+    const int n4 = (int)((s.n + 3) >> 2);
     // FP32 partial sums (GB300's FP64 pipe is narrow); thread 0 adds the
-    // eight warp sums in FP64.
+    // warp sums in FP64.
     float vf = 0.0f;
     int cnt = 0;
-    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
-        const float yi = y[i], gi = g[i];
-        const bool P = yi > 0.0f || gi < 0.0f;
-        const float b = P ? gi : 0.0f;
-        gb[i] = b;
-        vf = fmaf(b, b, vf);
-        cnt += P ? 1 : 0;
+    for (int i = threadIdx.x; i < n4; i += kBMThreads) {
+        const float4 y = y4[i], g = g4[i];
+        float4 b;
+        const bool p0 = y.x > 0.0f || g.x < 0.0f, p1 = y.y > 0.0f || g.y < 0.0f;
+        const bool p2 = y.z > 0.0f || g.z < 0.0f, p3 = y.w > 0.0f || g.w < 0.0f;
+        b.x = p0 ? g.x : 0.0f;
+        b.y = p1 ? g.y : 0.0f;
+        b.z = p2 ? g.z : 0.0f;
+        b.w = p3 ? g.w : 0.0f;
+        gb4[i] = b;
+        vf = fmaf(b.x, b.x, vf);
+        vf = fmaf(b.y, b.y, vf);
+        vf = fmaf(b.z, b.z, vf);
+        vf = fmaf(b.w, b.w, vf);
+        cnt += (int)p0 + (int)p1 + (int)p2 + (int)p3;
     }
-    double v = 0.0;
-    {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) vf += __shfl_xor_sync(0xffffffffu, vf, o);
-        const int x = warp_sum_i(cnt);
-        if (lane == 0) {
-            sc[wid] = (double)vf;
-            si[wid] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
-                t += si[w2];
-                v += sc[w2];
-            }
-            cnt = t;
-        }
+    for (int o = 16; o > 0; o >>= 1) vf += __shfl_xor_sync(0xffffffffu, vf, o);
+    cnt = warp_sum_i(cnt);
+    if (lane == 0) {
+        sc[wid] = (double)vf;
+        si[wid] = cnt;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double v = 0.0;
+        int t = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kBMWarps; ++w2) {
+            t += si[w2];
+            v += sc[w2];
+        }
         int status = -1;
-        const int it = s.iters[c];
         if (!isfinite(v)) status = ALN_RHS_NONFINITE;
-        else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
-        else if (v < s.eps[c] || v == 0.0) status = ALN_RHS_CONVERGED;
-        else if (it >= s.limits[0]) status = ALN_RHS_MAXITER;
-        else if (it - s.best_iter[c] > s.limits[1]) status = ALN_RHS_STAGNATED;
+        else if (t == 0) status = ALN_RHS_EMPTY_PASSIVE;
+        else if (v < eps || v == 0.0) status = ALN_RHS_CONVERGED;
+        else if (it >= lim_it) status = ALN_RHS_MAXITER;
+        else if (it - best_it > lim_win) status = ALN_RHS_STAGNATED;
         int slot = -1;
         if (status >= 0) {
             s.colst[c] = status;
         } else {
-            if (v < s.best[c]) {
+            if (v < best) {
                 s.best[c] = v;
                 s.best_iter[c] = it;
             }
             s.gamma[c] = v;
             slot = atomicAdd(&s.counters[0], 1);
             s.map_act[slot] = (int)c;
-            atomicAdd(&s.rows[0], (unsigned long long)cnt);
+            atomicAdd(&s.rows[0], (unsigned long long)t);
         }
         s_slot = slot;
     }
-    __syncthreads();
+    __syncthreads();  // also orders the ḡ stores above before the split reads them
     const int p = s_slot;
     if (p < 0) return;
-    __nv_bfloat16* hi = s.Vhi + (int64_t)p * s.ldk;
-    __nv_bfloat16* lo = s.Vlo + (int64_t)p * s.ldk;
-    for (int64_t i = threadIdx.x; i < s.ldk; i += blockDim.x) {
-        const float b = i < s.n ? gb[i] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(b);
-        hi[i] = h;
-        lo[i] = __float2bfloat16_rn(b - __bfloat162float(h));
-    }
+    split_row(s, p, gb4, n4);
 }
 
 // One block per running column (compact slot p): α, projection, g update, e.
-__global__ void __launch_bounds__(kBThreads) k_bupdate(BatchState s) {
-    __shared__ int si[32];
+__global__ void __launch_bounds__(kBMThreads) k_bupdate(BatchState s) {
+    __shared__ int si[kBMWarps];
     __shared__ int s_slot;
     __shared__ float s_alpha;
     const int p = blockIdx.x;
     if (p >= s.counters[0]) return;
     const int64_t c = s.map_act[p];
-    if (threadIdx.x == 0) {
-        double kap = 0.0;
-        for (int m = 0; m < s.mtiles; ++m) kap += s.kpart[(int64_t)m * s.k + p];
-        float a = 0.0f;
-        if (!isfinite(kap)) s.colst[c] = ALN_RHS_NONFINITE;
-        else if (kap <= 0.0) s.colst[c] = ALN_RHS_CURVATURE;
-        else a = (float)(s.gamma[c] / kap);
-        s_alpha = a;
+    if (threadIdx.x < 32) {
+        // κ = Σ of the row tiles' curvature partials, in FP64, lanes in parallel
+        const double gam = threadIdx.x == 0 ? s.gamma[c] : 0.0;
+        double kp = 0.0;
+        for (int m = threadIdx.x; m < s.mtiles; m += 32) kp += s.kpart[(int64_t)m * s.k + p];
+        const double kap = warp_sum(kp);
+        if (threadIdx.x == 0) {
+            float a = 0.0f;
+            if (!isfinite(kap)) s.colst[c] = ALN_RHS_NONFINITE;
+            else if (kap <= 0.0) s.colst[c] = ALN_RHS_CURVATURE;
+            else a = (float)(gam / kap);
+            s_alpha = a;
+        }
     }
     __syncthreads();
     const float a = s_alpha;
     if (a == 0.0f) return;
-    float* y = s.Y + c * s.ldq;
-    float* g = s.G + c * s.ldq;
-    float* e = s.E + c * s.ldq;
-    const float* gb = s.GB + c * s.ldq;
-    const float* w = s.W + (int64_t)p * s.ldq;
+    float4* y4 = reinterpret_cast<float4*>(s.Y + c * s.ldq);
+    float4* g4 = reinterpret_cast<float4*>(s.G + c * s.ldq);
+    float4* e4 = reinterpret_cast<float4*>(s.E + c * s.ldq);
+    const float4* gb4 = reinterpret_cast<const float4*>(s.GB + c * s.ldq);
+    const float4* w4 = reinterpret_cast<const float4*>(s.W + (int64_t)p * s.ldq);
+    const int n4 = (int)((s.n + 3) >> 2);
     int clipped = 0;
-    for (int64_t i = threadIdx.x; i < s.n; i += blockDim.x) {
-        const float yi = y[i];
-        const float step = a * gb[i];
-        float yn = yi - step, ei = 0.0f;
+    auto step1 = [&](float& y, float& e, float& g, float b, float w) {
+        const float st = a * b;
+        float yn = y - st;
+        e = 0.0f;
         if (yn < 0.0f) {
-            ei = step - yi;
+            e = st - y;
             yn = 0.0f;
             ++clipped;
         }
-        y[i] = yn;
-        e[i] = ei;
-        g[i] = g[i] - a * w[i];
+        y = yn;
+        g = g - a * w;
+    };
+    for (int i = threadIdx.x; i < n4; i += kBMThreads) {
+        float4 y = y4[i], g = g4[i], e;
+        const float4 b = gb4[i], w = w4[i];
+        step1(y.x, e.x, g.x, b.x, w.x);
+        step1(y.y, e.y, g.y, b.y, w.y);
+        step1(y.z, e.z, g.z, b.z, w.z);
+        step1(y.w, e.w, g.w, b.w, w.w);
+        y4[i] = y;
+        e4[i] = e;
+        g4[i] = g;
     }
     {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -208,7 +267,8 @@ __global__ void __launch_bounds__(kBThreads) k_bupdate(BatchState s) {
         __syncthreads();
         if (threadIdx.x == 0) {
             int t = 0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += si[w2];
+#pragma unroll
+            for (int w2 = 0; w2 < kBMWarps; ++w2) t += si[w2];
             s.iters[c] += 1;
             int slot = -1;
             if (t > 0) {
@@ -223,14 +283,7 @@ __global__ void __launch_bounds__(kBThreads) k_bupdate(BatchState s) {
     }
     const int q = s_slot;
     if (q < 0) return;
-    __nv_bfloat16* hi = s.Vhi + (int64_t)q * s.ldk;
-    __nv_bfloat16* lo = s.Vlo + (int64_t)q * s.ldk;
-    for (int64_t i = threadIdx.x; i < s.ldk; i += blockDim.x) {
-        const float v = i < s.n ? e[i] : 0.0f;
-        const __nv_bfloat16 h = __float2bfloat16_rn(v);
-        hi[i] = h;
-        lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
-    }
+    split_row(s, q, e4, n4);
 }
 
 // Start state of every column: y = s·x0 (0 without a start point), g = q
@@ -741,12 +794,12 @@ static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
 static cudaError_t bw_iteration(aln_ctx* c, BatchWork* b) {
     BatchState& s = b->s;
     k_breset<<<1, 1, 0, c->stream>>>(s.counters);
-    k_bmask<<<(unsigned)b->k, kBThreads, 0, c->stream>>>(s);
+    k_bmask<<<(unsigned)b->k, kBMThreads, 0, c->stream>>>(s);
     cudaError_t e = launch_bgemm_tc(0, b->Qhi, b->Qlo, b->n, b->ldk, s.Vhi, s.Vlo, b->k,
                                     s.counters, s.map_act, b->ldq, s.W, s.GB, s.kpart, nullptr,
                                     c->flags + 1, c->stream);
     if (e != cudaSuccess) return e;
-    k_bupdate<<<(unsigned)b->k, kBThreads, 0, c->stream>>>(s);
+    k_bupdate<<<(unsigned)b->k, kBMThreads, 0, c->stream>>>(s);
     return launch_bgemm_tc(1, b->Qhi, b->Qlo, b->n, b->ldk, s.Vhi, s.Vlo, b->k, s.counters + 1,
                            s.map_clip, b->ldq, nullptr, nullptr, nullptr, s.G, c->flags + 1,
                            c->stream);
