@@ -552,6 +552,24 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
             ALN_TRY(cudaMemsetAsync(gticket, 0, (size_t)pairs * 4, c->stream));
         }
     }
+    // without split K, the pairs past the last full wave of the Gram run as
+    // stream-K (equal K shares per SM) in the launch that ends the triangle
+    float* skp = nullptr;
+    unsigned int* skt = nullptr;
+    if (!f64 && !c->batched && gsplit == 1) {
+        const int64_t tiles = ceil_div(n, 128), pairs = tiles * (tiles + 1) / 2;
+        const int64_t tail = gram_sk_tail(pairs, c->num_sms);
+        // host input launches the Gram by column chunks: stream-K only when
+        // the last chunk holds the whole tail, so that both inputs give the
+        // same Q bits
+        const int64_t r0 = (n - 1) / chunk_cols * chunk_cols / 128;
+        if (tail > 0 && tail <= pairs - r0 * (r0 + 1) / 2) {
+            ALN_CHECK(ensure(&c->sp_part, &c->sp_part_bytes, gram_sk_bytes(pairs, c->num_sms)));
+            skp = (float*)c->sp_part;
+            skt = (unsigned int*)((uint8_t*)c->sp_part + gram_sk_part_bytes(pairs, c->num_sms));
+            ALN_TRY(cudaMemsetAsync(skt, 0, (size_t)tail * 4, c->stream));
+        }
+    }
 
     // Alg. 1: scale factors, q, (split), Gram
     ALN_TRY(cudaEventRecord(c->ev[0], c->stream));
@@ -586,7 +604,8 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
             if (c0 == 0) ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
             ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
                                    (float*)c->Q, ldq, c->flags + 1, c->stream, c0 / 128,
-                                   c1 == n ? tiles : c1 / 128, gpart, gticket, gsplit));
+                                   c1 == n ? tiles : c1 / 128, gpart, gticket, gsplit, skp, skt,
+                                   c->num_sms));
             c->launches += 2;
         }
     } else {
@@ -612,10 +631,11 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
                          gram64_split_bytes(d, n, c->num_sms)));
         ALN_TRY(launch_gram64(c->A, dtype, d, n, lda, c->inv_s, (double*)c->Q, ldq, c->stream,
                               (double*)c->g64_work, c->g64_work_bytes, c->num_sms));
-    } else
+    } else {
         ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
                                (float*)c->Q, ldq, c->flags + 1, c->stream, 0, -1, gpart, gticket,
-                               gsplit));
+                               gsplit, skp, skt, c->num_sms));
+    }
     ALN_TRY(cudaEventRecord(c->ev[2], c->stream));
     c->launches += 4 + (kc == 0 ? 1 : 0);
 

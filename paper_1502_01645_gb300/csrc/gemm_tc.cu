@@ -169,12 +169,17 @@ __device__ __forceinline__ void gram_store(const float (&acc)[BM], int64_t row, 
 // One 128×128 output tile of a split product, accumulated in FP32 registers:
 // acc[c] of the promotion warps (warp w ≥ 2 holds tile row 32·(w mod 4) +
 // lane) = Σ_K A[row]·B[c] over the num_kb K blocks the loader copies (A and B
-// boxes of NS terms each; diag: B = A, one set of boxes).  Sets up and frees
-// its barriers and tensor memory; returns false (uniformly) when a bounded
-// wait expired — nothing is then in flight and acc is incomplete.
+// boxes of NS terms each; diag: B = A, one set of boxes).  Sets up its
+// barriers; returns false (uniformly) when a bounded wait expired — nothing is
+// then in flight and acc is incomplete.  Tensor memory (G3_TMEM_COLS columns):
+// `tmem_given` when the caller holds it (a CTA that runs several tiles
+// allocates once — no allocation may follow the relinquish of the permit),
+// else allocated and freed here.
+constexpr uint32_t kNoTmem = 0xffffffffu;
+
 template <int NS, class Loader>
 __device__ __forceinline__ bool promoted_tile(Loader& ld, int num_kb, bool diag,
-                                              float (&acc)[BM]) {
+                                              float (&acc)[BM], uint32_t tmem_given = kNoTmem) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     using C = GramCfg<NS>;
@@ -200,14 +205,15 @@ __device__ __forceinline__ bool promoted_tile(Loader& ld, int num_kb, bool diag,
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    const bool own = tmem_given == kNoTmem;
+    if (own && warp == 1) {
         tmem_alloc(tmem_slot, G3_TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = own ? *tmem_slot : tmem_given;
 #pragma unroll
     for (int c = 0; c < BM; ++c) acc[c] = 0.0f;
 
@@ -276,7 +282,7 @@ __device__ __forceinline__ bool promoted_tile(Loader& ld, int num_kb, bool diag,
     const bool ok = !s_abort;
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
+    if (own && warp == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
     return ok;
 }
 
@@ -288,12 +294,16 @@ __device__ __forceinline__ bool promoted_tile(Loader& ld, int num_kb, bool diag,
 // its unscaled partial tile to part + c·128² (part points at the pair's first
 // slot), and the pair's last chunk to arrive on *ticket adds the S partials
 // in slot order — a fixed order, whichever CTA is last — and stores the tile.
+//
+// Returns false (uniformly) after a timeout.  Ends with a block barrier, so a
+// CTA may run several tiles in turn (tmem: as for promoted_tile).
 template <int NS, class Loader>
-__device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
+__device__ __forceinline__ bool gram_tile(Loader ld, int num_kb, bool diag, int64_t m0,
                                            int64_t n0, int64_t n, const double* __restrict__ inv_s,
                                            float* __restrict__ Q, int64_t ldq,
                                            int* timeout_flag, float* part = nullptr, int S = 1,
-                                           int c = 0, unsigned int* ticket = nullptr) {
+                                           int c = 0, unsigned int* ticket = nullptr,
+                                           uint32_t tmem = kNoTmem) {
     __shared__ float s_cs[BM];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,15 +312,16 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
         s_cs[threadIdx.x] = j < n ? (float)inv_s[j] : 0.0f;
     }
     float acc[BM];
-    const bool ok = promoted_tile<NS>(ld, num_kb, diag, acc);
+    const bool ok = promoted_tile<NS>(ld, num_kb, diag, acc, tmem);
     if (!ok) {
         if (threadIdx.x == 0) atomicExch(timeout_flag, 1);
-        return;
+        return false;
     }
     if (part == nullptr) {
         if (warp >= 2)
             gram_store(acc, m0 + 32 * (warp & 3) + lane, n0, diag, n, inv_s, s_cs, Q, ldq);
-        return;
+        __syncthreads();  // s_cs is rewritten by the next tile of this CTA
+        return true;
     }
     const int row = 32 * (warp & 3) + lane;
     if (warp >= 2) {
@@ -345,6 +356,8 @@ __device__ __forceinline__ void gram_tile(Loader ld, int num_kb, bool diag, int6
         }
         if (threadIdx.x == 0) *ticket = 0u;  // ready for the next launch
     }
+    __syncthreads();  // s_cs and s_last are rewritten by the next tile of this CTA
+    return true;
 }
 
 template <int NS>
@@ -366,6 +379,67 @@ struct TmaLoader {
         }
     }
 };
+
+// Stream-K pass over the pairs [t0, t0 + R) (the last partial wave): CTA b of
+// G takes the K blocks [⌊bW/G⌋, ⌊(b+1)W/G⌋) of the W = R·num_kb blocks laid
+// out pair after pair, one pair segment at a time.  A pair whose blocks span
+// several CTAs is summed from their partial tiles in CTA order (a fixed
+// order) by the last of them to finish.
+struct GramSK {
+    int64_t R;
+    int G;
+    int maxseg;
+    float* part;            // R × maxseg partial tiles
+    unsigned int* ticket;   // R
+};
+
+__device__ __forceinline__ int64_t sk_owner(int64_t x, int64_t W, int G) {
+    // the CTA b with ⌊bW/G⌋ ≤ x < ⌊(b+1)W/G⌋
+    int64_t b = x * G / W;
+    while (b + 1 < G && (b + 1) * W / G <= x) ++b;
+    while (b > 0 && b * W / G > x) --b;
+    return b;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(G3_THREADS, 1)
+    k_gram_sk(const __grid_constant__ CUtensorMap m_hi, const __grid_constant__ CUtensorMap m_mid,
+              const __grid_constant__ CUtensorMap m_lo, GramArgs p, GramSK sk) {
+    const int64_t nkb = p.num_kb, W = sk.R * nkb;
+    const int64_t b = blockIdx.x;
+    const int64_t g0 = b * W / sk.G, g1 = (b + 1) * W / sk.G;
+    if (g0 >= g1) return;  // uniform: no work, no tensor memory
+    // tensor memory for every segment of this CTA, allocated once
+    __shared__ uint32_t s_tmem;
+    if (threadIdx.x >> 5 == 1) {
+        tmem_alloc(&s_tmem, G3_TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    for (int64_t g = g0; g < g1;) {
+        const int64_t tl = g / nkb;  // pair of the tail
+        const int64_t kb0 = g - tl * nkb;
+        const int64_t kb1 = min(nkb, g1 - tl * nkb);
+        const int64_t first = sk_owner(tl * nkb, W, sk.G);
+        const int64_t last = sk_owner((tl + 1) * nkb - 1, W, sk.G);
+        const int nseg = (int)(last - first + 1), seg = (int)(b - first);
+        int tm, tn;
+        tri_decode(p.t0 + tl, tm, tn);
+        const TmaLoader<NS> ld{&m_hi, &m_mid, &m_lo, tm * BM, tn * BM, (int)kb0};
+        float* part = nseg > 1 ? sk.part + tl * sk.maxseg * (int64_t)(BM * BM) : nullptr;
+        if (!gram_tile<NS>(ld, (int)(kb1 - kb0), tm == tn, (int64_t)tm * BM, (int64_t)tn * BM,
+                           p.n, p.inv_s, p.Q, p.ldq, p.timeout_flag, part, nseg, seg,
+                           sk.ticket + tl, tmem))
+            break;  // timed out: nothing in flight (the flag is set)
+        g = tl * nkb + kb1;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x >> 5 == 1) tmem_dealloc(tmem, G3_TMEM_COLS);
+}
 
 template <int NS>
 __global__ void __launch_bounds__(G3_THREADS, 1)
@@ -724,7 +798,8 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0, int64_t row1, float* part,
-                           unsigned int* ticket, int split) {
+                           unsigned int* ticket, int split, float* sk_part,
+                           unsigned int* sk_ticket, int num_sms) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
@@ -763,10 +838,36 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     a.part = part;
     a.ticket = ticket;
     const unsigned grid = (unsigned)(pairs * a.S);
+    // stream-K for the last partial wave of the whole matrix, in the launch
+    // that ends the triangle (when all of that wave's pairs are in it): the
+    // same split whether the matrix came in one launch or in row chunks
+    int64_t R = 0;
+    if (a.S == 1 && row1 == tiles && sk_part && sk_ticket) {
+        R = gram_sk_tail(tiles * (tiles + 1) / 2, num_sms);
+        if (R > pairs) R = 0;
+    }
+    const unsigned full = R > 0 ? (unsigned)(pairs - R) : grid;  // R > 0 only with S = 1
     if (nsplit == 3)
-        k_gram_tc<3><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+        k_gram_tc<3><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
     else
-        k_gram_tc<2><<<grid, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+        k_gram_tc<2><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+    if (R > 0) {
+        static bool sk_attr[2] = {false, false};
+        if (!sk_attr[nsplit - 2]) {
+            cudaError_t e = cudaFuncSetAttribute(nsplit == 3 ? k_gram_sk<3> : k_gram_sk<2>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 G3_SMEM_BYTES);
+            if (e != cudaSuccess) return e;
+            sk_attr[nsplit - 2] = true;
+        }
+        GramArgs t = a;
+        t.t0 = a.t0 + (int64_t)full;  // = tiles·(tiles+1)/2 − R
+        GramSK sk{R, num_sms, gram_sk_maxseg(R, num_sms), sk_part, sk_ticket};
+        if (nsplit == 3)
+            k_gram_sk<3><<<(unsigned)num_sms, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, t, sk);
+        else
+            k_gram_sk<2><<<(unsigned)num_sms, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, t, sk);
+    }
     return cudaGetLastError();
 }
 

@@ -56,11 +56,35 @@ cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, in
 // per pair of the launch (left zeroed).  The chunking, and so the rounding of
 // every entry, depends only on `split`: launches over different row ranges
 // with the same split give the same Q as one launch over all rows.
+// sk_part / sk_ticket (nullable; a whole-matrix launch without split K only):
+// buffers of gram_sk_bytes for the stream-K pass over the last partial wave.
 cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
                            const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
                            const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
                            cudaStream_t st, int64_t row0 = 0, int64_t row1 = -1,
-                           float* part = nullptr, unsigned int* ticket = nullptr, int split = 1);
+                           float* part = nullptr, unsigned int* ticket = nullptr, int split = 1,
+                           float* sk_part = nullptr, unsigned int* sk_ticket = nullptr,
+                           int num_sms = 0);
+// Stream-K for the Gram's last wave: with `pairs` tile pairs (one CTA per SM
+// resident), the pairs past the last full wave (0 if none) are run by one CTA
+// per SM, each taking an equal share of their K blocks; a pair split over
+// several CTAs is summed from partial tiles (at most gram_sk_maxseg each).
+inline int64_t gram_sk_tail(int64_t pairs, int num_sms) {
+    if (num_sms <= 0 || pairs <= num_sms) return 0;
+    return pairs % num_sms;
+}
+inline int gram_sk_maxseg(int64_t tail, int num_sms) {
+    return tail > 0 ? (int)((num_sms + tail - 1) / tail) + 1 : 0;
+}
+// Partial tiles, then one ticket per tail pair.
+inline size_t gram_sk_part_bytes(int64_t pairs, int num_sms) {
+    const int64_t r = gram_sk_tail(pairs, num_sms);
+    return (size_t)r * gram_sk_maxseg(r, num_sms) * 128 * 128 * 4;
+}
+inline size_t gram_sk_bytes(int64_t pairs, int num_sms) {
+    const int64_t r = gram_sk_tail(pairs, num_sms);
+    return r > 0 ? gram_sk_part_bytes(pairs, num_sms) + (size_t)((r * 4 + 255) / 256 * 256) : 0;
+}
 // Chunks per tile pair for the Gram of a matrix with `pairs` tile pairs over
 // num_kb K blocks: enough CTAs to cover the SMs when the pairs alone do not
 // (tall, narrow A), with at least 16 K blocks per chunk.

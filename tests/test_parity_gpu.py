@@ -55,9 +55,13 @@ def test_fp64_scaled_problem_matches_oracle(aln, d, n):
     np.testing.assert_array_equal(np.diag(Q), 1.0)
 
 
-@pytest.mark.parametrize("d,n", [(700, 300), (64, 128), (1000, 129), (130, 1), (257, 400)])
+@pytest.mark.parametrize("d,n", [(700, 300), (64, 128), (1000, 129), (130, 1), (257, 400),
+                                 (1500, 2304)])
 def test_split_bf16_gram_matches_oracle(aln, d, n):
-    """tcgen05 Gram: several 128-tiles plus a ragged tail in n and in d."""
+    """tcgen05 Gram: several 128-tiles plus a ragged tail in n and in d;
+    n = 2304 has 171 tile pairs, more than one wave, so the pairs past the
+    last full wave run as stream-K (pairs split over several CTAs and summed
+    from partial tiles)."""
     r = np.random.default_rng(7 * d + n)
     A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
     A = np.asfortranarray(A64.astype(np.float32))
