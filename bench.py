@@ -629,7 +629,9 @@ def run_ours(args):
         qbytes = esz * n * avg(lambda s: s.passive_rows + s.clipped_rows)  # §4.2: n·S(n)
         ach = qbytes / (it_ms / 1e3) / 1e9 if it_ms > 0 else 0.0
         kname = ("k_acc_repl (persistent Anti+Acc loop)" if alg == aln.ALG_ANTI_ACC else
-                 "k_alg2_repl (persistent Alg. 2 loop)")
+                 {1: "k_alg2_persist (persistent Alg. 2 loop, tiled state)",
+                  3: "k_alg2_small64 (FP64 Alg. 2 loop on one thread-block cluster)"}.get(
+                     int(stats[-1].iter_kernel), "k_alg2_repl (persistent Alg. 2 loop)"))
         # DRAM traffic per launch of k_alg2_repl<float>: one ncu capture at
         # 12000x3000 read 36.94 MB = 1.002 x n*ldq*4 (Q once; later iterations
         # hit L2), so a launch moves 1.002 x n*ldq*4 bytes at any size

@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define ALN_VERSION 200
+#define ALN_VERSION 201
 
 typedef enum aln_status {
     ALN_OK = 0,
@@ -432,6 +432,10 @@ typedef struct aln_stats {
     double lipschitz;        /* ALN_ALG_ANTI_ACC: L = λ_max(Q) estimate of the power
                                 iteration for the prepared Q (0 before the first solve) */
     int64_t power_products;  /* products Qv that power iteration took */
+    int32_t iter_kernel;     /* single-problem path of the last prepare: the kernel
+                                aln_solve runs (1 tiled, 2 replicated state, 3 one
+                                cluster, FP64; 0 for the batched and grouped paths) */
+    int32_t reserved2;
 } aln_stats;
 
 /* Change the device-wait options of an existing context (aln_options'

@@ -61,7 +61,8 @@ class AlnStats(ctypes.Structure):
                 ("clipped_rows", ctypes.c_int64), ("persist_blocks", ctypes.c_int32),
                 ("clipped_iterations", ctypes.c_int32), ("phase_us", ctypes.c_double * 5),
                 ("product_bytes", ctypes.c_double), ("lipschitz", ctypes.c_double),
-                ("power_products", ctypes.c_int64)]
+                ("power_products", ctypes.c_int64), ("iter_kernel", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32)]
 
 
 class AlnProblem(ctypes.Structure):

@@ -1007,6 +1007,11 @@ aln_status aln_get_stats(aln_ctx* c, aln_stats* out) {
     *out = c->stats;
     out->kernel_launches = c->launches;
     out->persist_blocks = c->p_G;
+    out->iter_kernel = (c->batched || c->grouped || !c->prepared) ? 0
+                       : c->p_small                                ? 3
+                       : c->p_repl                                 ? 2
+                                                                   : 1;
+    out->reserved2 = 0;
     return ALN_OK;
 }
 

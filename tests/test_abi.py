@@ -42,7 +42,7 @@ def test_library_targets_sm103a_only():
 
 def test_host_only_entry_points(lib):
     from paper_1502_01645_gb300 import aln
-    assert aln.aln_version() == 200
+    assert aln.aln_version() == 201
     o = aln.aln_default_options()
     assert o.precision == aln.PREC_SPLIT_BF16 and o.max_refine == 8 and o.stagnation == 100
     assert aln.status_string(aln.ERR_NONFINITE) == "ALN_ERR_NONFINITE"

@@ -164,13 +164,15 @@ def _parity_fp64(x, A, b, x_star):
 
 
 def test_fp64_solve_uniform_small(aln):
-    """The plain FP64 configuration: A 1000×200 U[0,1], half of x_true zero."""
+    """The plain FP64 configuration: A 1000×200 U[0,1], half of x_true zero
+    (n = 200: the loop runs on one thread-block cluster)."""
     p = W.uniform_small()
     A, b = p.A, p.B[0]
     x_star, _, _, _ = O.reference_solution(A, b)
     with aln.Solver("fp64") as s:
         s.prepare(A, b)
         X, info = s.solve(tol=1e-12)
+        assert s.stats().iter_kernel == 3
     assert info[0].status == aln.RHS_CONVERGED
     assert info[0].rel_kkt <= 1e-12
     _parity_fp64(X[0], A, b, x_star)
