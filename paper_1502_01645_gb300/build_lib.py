@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libaln.so")
 SOURCES = ["api.cu", "prep.cu", "gemm_tc.cu", "iter.cu", "persist.cu", "kkt.cu", "noalloc.cu",
            "batch.cu", "grouped.cu", "mlp.cu", "nmf.cu", "sparse.cu", "probe.cu",
-           "small64.cu", "autotune.cu"]
+           "small64.cu", "autotune.cu", "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

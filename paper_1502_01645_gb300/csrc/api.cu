@@ -278,6 +278,16 @@ __global__ void k_copy_to_f64(const TS* __restrict__ src, int64_t lds, double* _
 // Shared by aln_prepare and aln_prepare_csc (c->d, c->dtype set): Q (zeroed
 // when its shape changes), s, inv_s, q64, den, flags, the pinned copy of den,
 // and the choice of the many-right-hand-side solver.
+// q = −D⁻¹AᵀB for FP32 A and B to FP64 accuracy (the batched FP64 checks
+// need it): exact BF16 digit products on the tensor cores.
+static aln_status qvec32(aln_ctx* c, int64_t d, int64_t n, int64_t lda, int64_t k, int64_t ldb) {
+    ALN_CHECK(ensure(&c->oz_work, &c->oz_work_bytes, oz_work_bytes(d, n, k)));
+    ALN_TRY(launch_oz_atb((const float*)c->A, lda, (const float*)c->B, ldb, d, n, k, c->inv_s,
+                          c->q64, c->ldq, c->oz_work, c->oz_work_bytes, c->flags + 1, c->stream));
+    c->launches += 3;
+    return ALN_OK;
+}
+
 static aln_status prep_buffers(aln_ctx* c, int64_t n, int64_t k) {
     const bool f64 = fp64(c);
     const int64_t ldq = round_up(n, 128);
@@ -471,7 +481,8 @@ void aln_destroy(aln_ctx* c) {
     mlp_free(c);
     nmf_free(c);
     void* bufs[] = {c->A_copy, c->B_copy,    c->Q,        c->prep_pool, c->A_hi,
-                    c->iter_pool, c->kkt_pool, c->csc_pool, c->sp_part, c->g64_work};
+                    c->iter_pool, c->kkt_pool, c->csc_pool, c->sp_part, c->g64_work,
+                    c->oz_work};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->den_host) cudaFreeHost(c->den_host);
@@ -613,9 +624,8 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
                                 ldq, c->flags, hi, mid, lo, c->ldk, c->stream));
     }
     if (kc == 0) {
-        if (c->batched && dtype == ALN_DTYPE_F32)  // FP64-accurate, on the FP32 pipe
-            ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
-                                       c->inv_s, c->q64, ldq, c->stream));
+        if (c->batched && dtype == ALN_DTYPE_F32)  // FP64-accurate, exact digit products
+            ALN_CHECK(qvec32(c, d, n, lda, k, ldb));
         else
             ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
                                   c->stream));
@@ -772,8 +782,7 @@ aln_status aln_prepare_csc(aln_ctx* c, int64_t d, int64_t n, const int64_t* col_
     c->launches += 3;
     if (kc == 0) {
         if (c->batched && dtype == ALN_DTYPE_F32)
-            ALN_TRY(launch_qvec32_dot2((const float*)c->A, d, n, lda, (const float*)c->B, k, ldb,
-                                       c->inv_s, c->q64, ldq, c->stream));
+            ALN_CHECK(qvec32(c, d, n, lda, k, ldb));
         else
             ALN_TRY(launch_qvec64(c->A, dtype, d, n, lda, c->B, k, ldb, c->inv_s, c->q64, ldq,
                                   c->stream));

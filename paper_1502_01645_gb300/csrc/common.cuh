@@ -236,6 +236,8 @@ struct aln_ctx {
     size_t csc_box_bytes = 0;  // one split term's packed boxes in A_hi
     void* g64_work = nullptr;  // split-K partial tiles of the FP64 Gram (small n)
     size_t g64_work_bytes = 0;
+    void* oz_work = nullptr;   // digits and exponents of the exact-product q (batched)
+    size_t oz_work_bytes = 0;
     void* sp_part = nullptr;   // split-K partial tiles of the block-sparse Gram
     size_t sp_part_bytes = 0;
     // tiles of Q that may be non-zero (block-sparse Gram; null = all): bit rt

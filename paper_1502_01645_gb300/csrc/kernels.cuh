@@ -277,6 +277,15 @@ aln_status run_until_done(aln_ctx* c);
 aln_status autotune_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t ldx,
                           const double* X0);
 
+// ozaki.cu — FP64-accurate out[j·ldo + i] = −inv_s[i]·Σ_t X[i·ldx + t]·Y[j·ldy + t]
+// for FP32 X (m columns) and Y (n columns) of d rows, by exact BF16 digit
+// products on the tensor cores; work: oz_work_bytes(d, m, n) bytes of device
+// memory (digits and exponents).
+size_t oz_work_bytes(int64_t d, int64_t m, int64_t n);
+cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
+                          int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
+                          void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st);
+
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);
 

@@ -1,0 +1,375 @@
+// FP64-accurate C = XᵀY on the tensor cores (the q = −D⁻¹Aᵀb of Alg. 1 for
+// many right-hand sides, Eq. NQPQ), by exact integer products.
+//
+// Every column of X (and of Y) is written as 2^e · Σ_{s=1..6} d_s 2^{−8s}
+// with e the column's exponent (max |x| < 2^e) and integer digits
+// |d_s| ≤ 255 taken by truncation, 8 bits at a time: 48 bits below the
+// column's largest entry, the rest (< 2^{e−48}) dropped.  A digit is exact in
+// BF16, a product of two digits (< 2^16) is exact in FP32, and a sum of up to
+// 256 of them stays below 2^24, so the tensor core's FP32 accumulation of
+// digit products is EXACT as long as an accumulator gathers at most 2^24
+// worth of them.  Then
+//     C_ij = 2^{e_i + f_j} Σ_{σ=2..8} 2^{−8σ} Σ_{s+u=σ} Σ_t d_s(x_ti) d_u(y_tj)
+// keeping the digit pairs with s + u ≤ 8 (26 pairs): the dropped pairs and the
+// truncated digits each stay below about 2^{−48}·Σ_t |x_ti|·max|y_j|, the
+// error of a Dot2 sum on the FP32 pipe.  This is the fixed-point splitting of Ozaki, Ogita,
+// Oishi and Rump (2012) for error-free matrix products, here with BF16
+// digits on tcgen05.
+//
+// One CTA computes a 128 (columns of X) × 64 (columns of Y) tile.  Per 64-wide
+// K block, two half steps:
+//   X half: digits 1–3 of X with digits 1–6 of Y (17 pairs, σ = 2..8),
+//   Y half: digits 4–6 of X with digits 1–4 of Y (9 pairs, σ = 5..8),
+// each into fresh TMEM accumulators, one per σ (64 columns each); no
+// accumulator holds more than 3 pairs × 64 products (< 2^24).  After each
+// half step eight promotion warps read the accumulators (integers in FP32),
+// scale them by 2^{−8σ} (exact) and add them into a double-float
+// accumulator (hi + lo, TwoSum), about 48 bits — the FP32 pipe, not this
+// GPU's narrow FP64 pipe.  The epilogue writes −(hi + lo)·2^{e+f}·inv_s in
+// FP64.
+//
+// Roles (320 threads): warp 0 (one lane) loads, warp 1 (one lane) issues the
+// MMAs, warps 2–9 promote (warp w: TMEM lanes 32·(w mod 4), output columns
+// 32·((w − 2) / 4) + 0..31).  Every wait is bounded; on expiry the CTA sets
+// *timeout_flag, drains its own copies and MMAs, frees tensor memory and
+// leaves without storing.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace aln {
+namespace tc {
+namespace {
+
+constexpr int kOzS = 6;                    // digits per value
+constexpr int kOzSig = 8;                  // largest digit-pair order s + u kept
+constexpr int kOzN = 64;                   // output columns per CTA (Y side)
+constexpr int kOzThreads = 320;
+constexpr int kOzATile = BM * BK * 2;      // 16 KiB: 128 rows × 64 K
+constexpr int kOzBTile = kOzN * BK * 2;    // 8 KiB:   64 rows × 64 K
+// half-step buffers: X half = 3 A tiles + 6 B tiles, Y half = 3 A + 4 B
+constexpr int kOzXBytes = 3 * kOzATile + 6 * kOzBTile;  // 96 KiB
+constexpr int kOzYBytes = 3 * kOzATile + 4 * kOzBTile;  // 80 KiB
+constexpr int kOzSmem = kOzXBytes + kOzYBytes + 1024 + 256;
+constexpr uint32_t kOzTmemCols = 512;      // 7 accumulators × 64 columns, rounded up
+constexpr int kOzFlush = 16;               // half steps (8 K blocks) per FP64 flush
+
+struct OzArgs {
+    int num_kb;            // 64-wide K blocks
+    int64_t m, n;          // columns of X (rows of C), columns of Y
+    const int* ex;         // [m] exponents of X's columns
+    const int* ey;         // [n] exponents of Y's columns
+    const double* inv_s;   // [m] factor of row i of C
+    double* out;           // C[j][i] at out[j·ldo + i] (negated, scaled)
+    int64_t ldo;
+    int* timeout_flag;
+};
+
+struct OzMaps {
+    CUtensorMap x[kOzS];   // digits of X, [m][ldk], box 64 × 128
+    CUtensorMap y[kOzS];   // digits of Y, [n][ldk], box 64 × 64
+};
+
+// d ← d·2^{−8σ} added into the pair (hi, lo) (TwoSum; lo gathers the errors).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
+// MMAs of one half step: pairs (s, u) with s in [S0, S0 + 3) and s + u ≤ 8,
+// digit s of X at a + (s − S0)·A tile, digit u of Y at b + (u − 1)·B tile,
+// accumulator σ − 2 at column (σ − 2)·64.
+template <int S0>
+__device__ __forceinline__ void oz_half(uint32_t tmem, uint32_t a, uint32_t b) {
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, kOzN);
+    bool fresh[kOzSig - 1] = {true, true, true, true, true, true, true};
+#pragma unroll
+    for (int si = 0; si < 3; ++si) {
+        const int s = S0 + si;
+#pragma unroll
+        for (int u = 1; u <= kOzS; ++u) {
+            if (s + u > kOzSig) continue;
+            const int acc = s + u - 2;
+            const uint32_t d = tmem + (uint32_t)(acc * kOzN);
+            const uint32_t ab = a + (uint32_t)(si * kOzATile);
+            const uint32_t bb = b + (uint32_t)((u - 1) * kOzBTile);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                umma_bf16(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(bb + kk * 32), idesc,
+                          (fresh[acc] && kk == 0) ? 0u : 1u);
+            }
+            fresh[acc] = false;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant__ OzMaps maps,
+                                                         OzArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* bufX = smem;
+    uint8_t* bufY = smem + kOzXBytes;
+    uint64_t* bars = (uint64_t*)(smem + kOzXBytes + kOzYBytes);
+    uint64_t* full = bars;         // [2]: X, Y tiles landed
+    uint64_t* empty = bars + 2;    // [2]: X, Y tiles consumed by the MMAs
+    uint64_t* tfull = bars + 4;    // accumulators ready (one per half step)
+    uint64_t* tempty = bars + 5;   // accumulators drained (8 promotion warps)
+    uint64_t* done = bars + 6;
+    uint32_t* tmem_slot = (uint32_t*)(bars + 7);
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * kOzN;
+    const int H = 2 * p.num_kb;  // half steps
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], 1);
+        }
+        mbar_init(tfull, 1);
+        mbar_init(tempty, 8);
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, kOzTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    float hi[32], lo[32];
+    double acc[32];  // the pairs are flushed here every kOzFlush half steps
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        hi[j] = lo[j] = 0.0f;
+        acc[j] = 0.0;
+    }
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int h = 0; h < H; ++h) {
+            const int t = h & 1, kb = h >> 1;  // t = 0: X half, 1: Y half
+            if (h >= 2 && !mbar_wait(&empty[t], ((h >> 1) - 1) & 1)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            uint8_t* buf = t == 0 ? bufX : bufY;
+            const int nb = t == 0 ? 6 : 4;
+            mbar_expect_tx(&full[t], 3 * kOzATile + nb * kOzBTile);
+            const int x = kb * BK;
+#pragma unroll
+            for (int si = 0; si < 3; ++si)
+                tma_load_2d(buf + si * kOzATile, &maps.x[3 * t + si], &full[t], x, (int)m0);
+            for (int u = 0; u < nb; ++u)
+                tma_load_2d(buf + 3 * kOzATile + u * kOzBTile, &maps.y[u], &full[t], x, (int)n0);
+            ++issued;
+        }
+        // our own copies in flight: the last two (bounded wait)
+        for (int h = max(0, issued - 2); h < issued; ++h)
+            if (!mbar_wait(&full[h & 1], (h >> 1) & 1)) s_abort = 1;
+    } else if (warp == 1 && lane == 0) {
+        int h = 0;
+        for (; h < H; ++h) {
+            const int t = h & 1;
+            if (!mbar_wait(&full[t], (h >> 1) & 1) ||
+                (h >= 1 && !mbar_wait(tempty, (h - 1) & 1))) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int*)&s_abort) break;
+            tc_fence_after();
+            const uint32_t a = smem_u32(t == 0 ? bufX : bufY);
+            if (t == 0)
+                oz_half<1>(tmem, a, a + 3 * kOzATile);
+            else
+                oz_half<4>(tmem, a, a + 3 * kOzATile);
+            umma_commit(&empty[t]);
+            umma_commit(tfull);
+        }
+        if (h > 0) umma_commit(done);
+    } else if (warp >= 2) {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * half);
+        for (int h = 0; h < H; ++h) {
+            if (!mbar_wait(tfull, h & 1)) {
+                s_abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const int t = h & 1;
+            // accumulators σ = 2..8 (X half) or 5..8 (Y half)
+            for (int sg = t == 0 ? 2 : 5; sg <= kOzSig; ++sg) {
+                const float scale = __int_as_float((127 - 8 * sg) << 23);  // 2^{−8σ}
+                float v[32];
+                tmem_ld16(tb + (uint32_t)((sg - 2) * kOzN), v);
+                tmem_ld16(tb + (uint32_t)((sg - 2) * kOzN + 16), v + 16);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) df_add(hi[j], lo[j], v[j] * scale);
+            }
+            if ((h + 1) % kOzFlush == 0) {
+                // FP64 flush: the pair's own rounding stays that of a few
+                // K blocks (a handful of FP64 adds per K block, off the MMA
+                // path)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    acc[j] += (double)hi[j] + (double)lo[j];
+                    hi[j] = lo[j] = 0.0f;
+                }
+            } else {
+                // renormalise the pairs once per half step
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float s = hi[j] + lo[j];
+                    lo[j] = lo[j] - (s - hi[j]);
+                    hi[j] = s;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty);
+            if (*(volatile int*)&s_abort) break;
+        }
+    }
+    __syncwarp();
+    if (warp == 1 && H > 0) {
+        if (!mbar_wait(done, 0)) s_abort = 1;  // no MMA in flight past this point
+    }
+    tc_fence_after();
+    __syncthreads();
+    const bool ok = !s_abort;
+    if (ok && warp >= 2) {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int64_t i = m0 + 32 * q + lane;
+        if (i < p.m) {
+            const int ei = p.ex[i];
+            const double f = -p.inv_s[i];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t c = n0 + 32 * half + j;
+                if (c < p.n) {
+                    const double v = acc[j] + ((double)hi[j] + (double)lo[j]);
+                    p.out[c * p.ldo + i] = ldexp(v, ei + p.ey[c]) * f;
+                }
+            }
+        }
+    } else if (!ok && threadIdx.x == 0) {
+        atomicExch(p.timeout_flag, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, kOzTmemCols);
+}
+
+// Column exponents and digits: one block per column of X (d rows, stride
+// ld): e = the exponent with max |x| < 2^e (0 for a zero column), then the six
+// truncated 8-bit digits of x·2^{−e}, written K-major [col][ldk] per digit
+// (zero beyond d).
+template <typename T>
+__global__ void __launch_bounds__(256) k_oz_split(const T* __restrict__ X, int64_t ld, int64_t d,
+                                                  int64_t ldk, int* __restrict__ ex,
+                                                  __nv_bfloat16* __restrict__ dig,
+                                                  int64_t dstride) {
+    __shared__ float smax[8];
+    const int64_t col = blockIdx.x;
+    const T* x = X + col * ld;
+    float mx = 0.0f;
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) mx = fmaxf(mx, fabsf((float)x[t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) mx = fmaxf(mx, smax[w]);
+    int e = 0;
+    if (mx > 0.0f) (void)frexpf(mx, &e);  // mx = m·2^e, m in [0.5, 1)
+    if (threadIdx.x == 0) ex[col] = e;
+    for (int64_t t = threadIdx.x; t < ldk; t += blockDim.x) {
+        float v = t < d ? ldexpf((float)x[t], -e) : 0.0f;  // |v| < 1, exact
+#pragma unroll
+        for (int s = 0; s < kOzS; ++s) {
+            v *= 256.0f;
+            const float dv = truncf(v);
+            v -= dv;
+            dig[(int64_t)s * dstride + col * ldk + t] = __float2bfloat16_rn(dv);
+        }
+    }
+}
+
+// K-major BF16 digits [rows][ldk], box 64 (K) × box_rows.
+bool oz_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t K, int64_t rows, int64_t ld,
+            int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+}  // namespace
+}  // namespace tc
+
+size_t oz_work_bytes(int64_t d, int64_t m, int64_t n) {
+    const int64_t ldk = round_up(d, tc::BK);
+    return (size_t)(6 * (m + n) * ldk * 2) + (size_t)round_up((m + n) * 4, 256) + 1024;
+}
+
+cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
+                          int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
+                          void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st) {
+    using namespace tc;
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (!work || work_bytes < oz_work_bytes(d, m, n)) return cudaErrorInvalidValue;
+    const int64_t ldk = round_up(d, BK);
+    uint8_t* w = (uint8_t*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
+    __nv_bfloat16* dx = (__nv_bfloat16*)w;                 // 6 × [m][ldk]
+    __nv_bfloat16* dy = dx + 6 * m * ldk;                  // 6 × [n][ldk]
+    int* ex = (int*)(dy + 6 * n * ldk);
+    int* ey = ex + m;
+    k_oz_split<float><<<(unsigned)m, 256, 0, st>>>(X, ldx, d, ldk, ex, dx, m * ldk);
+    k_oz_split<float><<<(unsigned)n, 256, 0, st>>>(Y, ldy, d, ldk, ey, dy, n * ldk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    OzMaps maps;
+    for (int s = 0; s < 6; ++s)
+        if (!oz_map(&maps.x[s], dx + s * m * ldk, ldk, m, ldk, BM) ||
+            !oz_map(&maps.y[s], dy + s * n * ldk, ldk, n, ldk, kOzN))
+            return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_oz_atb, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    OzArgs a;
+    a.num_kb = (int)(ldk / BK);
+    a.m = m;
+    a.n = n;
+    a.ex = ex;
+    a.ey = ey;
+    a.inv_s = inv_s;
+    a.out = out;
+    a.ldo = ldo;
+    a.timeout_flag = timeout_flag;
+    const dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, kOzN));
+    k_oz_atb<<<grid, kOzThreads, kOzSmem, st>>>(maps, a);
+    return cudaGetLastError();
+}
+
+}  // namespace aln

@@ -374,9 +374,10 @@ def test_multiple_rhs_each_match_oracle(aln):
 
 # ------------------------------------------------------------- batched solver
 def test_batched_prepare_matches_oracle(aln):
-    """Batched prepare: q and the scaled matrix come from FP32-pipe Dot2
-    products (compensated, FP64-level accuracy); q and s to 1e-12, Q (kept
-    in FP32 for the iteration) to FP32 rounding."""
+    """Batched prepare: q from exact BF16 digit products on the tensor cores
+    and the scaled matrix from FP32-pipe Dot2 products (both FP64-level
+    accuracy); q and s to 1e-12, Q (kept in FP32 for the iteration) to FP32
+    rounding."""
     p = W.shared_multi_rhs(d=1300, n=257, k=70, seed=37)
     with aln.Solver("split_bf16") as s:
         s.prepare(p.A, p.B)
@@ -388,6 +389,34 @@ def test_batched_prepare_matches_oracle(aln):
     np.testing.assert_allclose(q, qo, rtol=0, atol=1e-12 * np.abs(qo).max())
     np.testing.assert_allclose(Q, Qo, rtol=0, atol=2.0 ** -23)
     np.testing.assert_array_equal(Q, Q.T)
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_batched_q_from_digit_products(aln, signed):
+    """q = −D⁻¹Aᵀb of the batched prepare (exact 8-bit digit products on the
+    tensor cores, 48 bits per value, pairs of order ≤ 8) against FP64, entry
+    by entry, relative to Σ_t |a_ti b_t| / s_i (the natural scale of a
+    compensated product): columns six decades apart, a zero column, mixed
+    signs, d, n and k ragged against the 64 × 128 × 64 tiles."""
+    r = np.random.default_rng(91 + signed)
+    d, n, k = 997, 130, 70
+    A = r.random((d, n)) * np.exp(r.uniform(np.log(1e-3), np.log(1e3), n))[None, :]
+    B = r.standard_normal((k, d)) if signed else r.random((k, d))
+    if signed:
+        A *= r.choice([-1.0, 1.0], size=A.shape)
+    A[:, 5] = 0.0
+    A = np.asfortranarray(A.astype(np.float32))
+    B = np.ascontiguousarray(B.astype(np.float32))
+    with aln.Solver("split_bf16") as s:
+        s.prepare(A, B)
+        _, q, sc = s.export()
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    norms = np.sqrt((A64 * A64).sum(axis=0))
+    safe = np.where(norms > 0, norms, 1.0)
+    qo = -(B64 @ A64) / safe[None, :]
+    scale = (np.abs(B64) @ np.abs(A64)) / safe[None, :]
+    assert np.all(np.abs(q - qo) <= 1e-13 * scale + 1e-300)
+    assert np.all(q[:, 5] == 0.0)
 
 
 def test_batched_multi_rhs_matches_oracle(aln):
