@@ -13,7 +13,8 @@
 //   U = Q·E   (k_bgemm_tc) added to g for the clipped columns only.
 //
 // The FP64 check of every column uses the FP64 scaled matrix Q64 and the
-// FP64 q: g64 = Q64 y + q (one FP64 product for all columns), then
+// FP64 q: g64 = Q64 y + q (one FP64-accurate product for all columns, exact
+// BF16 digit products on the tensor cores, ozaki.cu), then
 // rel_c = ‖ḡ64_c‖/‖min(q_c, 0)‖ and ½‖Ax − b‖² = ½yᵀg64 + ½qᵀy + ½‖b‖².
 // Columns above tol restart from y_c with g_c = g64_c (refinement).
 #include "blockops.cuh"
@@ -691,8 +692,6 @@ struct BatchWork {
     double* obj = nullptr;
     int* react = nullptr;
     int* host = nullptr;          // pinned: [0] running count, [1] re-activated
-    float* Qp = nullptr;          // Q64 as FP32 pairs: hi [ldq·ldq], then lo
-    float* Yp = nullptr;          // Y64 as FP32 pairs: hi [k·ldq], then lo
     BatchState s{};
     cudaGraphExec_t graph = nullptr;
     int chunk = 8;
@@ -730,8 +729,7 @@ static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
         (size_t)k * 4, (size_t)k * 4, (size_t)k * 4,         // map_act, map_clip, rounds
         (size_t)k * 8, (size_t)k * 8, (size_t)k * 8,         // best, eps, gamma
         (size_t)k * 4, (size_t)k * 8, (size_t)k * 8,         // fin, rel, obj
-        64, 64, 64, 64,                                      // counters, rows, limits, react
-        (size_t)ldq * ldq * 8, d8};                          // Qp, Yp (FP32 pairs)
+        64, 64, 64, 64};                                     // counters, rows, limits, react
     size_t total = 0;
     for (size_t x : sizes) total += round_up(x, 256);
     if (b->pool_bytes < total) {
@@ -792,9 +790,7 @@ static aln_status bw_alloc(aln_ctx* c, BatchWork* b) {
     s.rows = (unsigned long long*)take(64);
     s.limits = (int*)take(64);
     b->react = (int*)take(64);
-    b->Qp = (float*)take((size_t)ldq * ldq * 8);
-    b->Yp = (float*)take(d8);
-    if (!b->react || !b->Qp || !b->Yp || taken != (int)(sizeof(sizes) / sizeof(sizes[0])))
+    if (!b->react || taken != (int)(sizeof(sizes) / sizeof(sizes[0])))
         return ALN_ERR_CUDA;  // layout and size table disagree: never launch on it
     if (cudaMemsetAsync(b->pool, 0, b->pool_bytes, c->stream) != cudaSuccess) return ALN_ERR_CUDA;
     return ALN_OK;
@@ -916,9 +912,6 @@ aln_status batch_prepare(aln_ctx* c) {
     if (eg != cudaSuccess) return ALN_ERR_CUDA;
     k_qsplit<<<(unsigned)c->n, kBThreads, 0, c->stream>>>(b->Q64, c->ldq, c->n, b->ldk,
                                                         (float*)c->Q, b->Qhi, b->Qlo);
-    if (launch_split_f64(b->Q64, c->ldq * c->ldq, b->Qp, b->Qp + c->ldq * c->ldq, c->stream) !=
-        cudaSuccess)
-        return ALN_ERR_CUDA;
     k_bnorm2<<<(unsigned)c->k, kBThreads, 0, c->stream>>>(c->B, c->dtype, c->d, c->ldb, b->bn2);
     c->launches += 3;
     if (cudaGetLastError() != cudaSuccess) return ALN_ERR_CUDA;
@@ -935,6 +928,29 @@ __global__ void k_bsetg(BatchState s, const double* __restrict__ G64) {
 }
 
 
+// G64 = Q64·Y64 + q for every column, FP64-accurate (exact BF16 digit
+// products on the tensor cores; the digits keep 48 bits below each row of
+// Q64 and each y).
+static aln_status bw_qy(aln_ctx* c, BatchWork* b) {
+    const size_t need = oz_work_bytes(c->n, c->n, b->k);
+    if (c->oz_work_bytes < need) {
+        if (c->oz_work) cudaFree(c->oz_work);
+        c->oz_work = nullptr;
+        c->oz_work_bytes = 0;
+        if (cudaMalloc(&c->oz_work, need) != cudaSuccess) {
+            cudaGetLastError();
+            return ALN_ERR_OUT_OF_MEMORY;
+        }
+        c->oz_work_bytes = need;
+    }
+    if (launch_oz_product(1, ALN_DTYPE_F64, b->Q64, c->ldq, ALN_DTYPE_F64, b->Y64, c->ldq, c->n,
+                          c->n, b->k, c->q64, b->G64, c->ldq, c->oz_work, c->oz_work_bytes,
+                          c->flags + 1, c->stream) != cudaSuccess)
+        return ALN_ERR_CUDA;
+    c->launches += 3;
+    return ALN_OK;
+}
+
 // FP64 check of every not-yet-final column; returns how many were restarted.
 static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine, int* restarted) {
     BatchState& s = b->s;
@@ -942,13 +958,11 @@ static aln_status bw_check(aln_ctx* c, BatchWork* b, double tol, int max_refine,
     cudaEventRecord(c->ev[6], c->stream);
     k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64,
                                                          b->small_vpl ? s.E : nullptr);
-    // g = Q y + q in FP64 accuracy (FP32 pairs on the FP32 pipe)
-    const int64_t ky = k * c->ldq;
-    if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
-        launch_gemm_pairs_axpy(b->Qp, b->Qp + c->ldq * c->ldq, c->ldq, b->Yp, b->Yp + ky, c->ldq,
-                               c->n, c->n, k, c->q64, b->G64, c->ldq,
-                           c->stream) != cudaSuccess)
-        return ALN_ERR_CUDA;
+    // g = Q y + q in FP64 accuracy (exact digit products on the tensor cores)
+    {
+        aln_status gs = bw_qy(c, b);
+        if (gs != ALN_OK) return gs;
+    }
     cudaMemsetAsync(b->react, 0, sizeof(int), c->stream);
     k_bcheck<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64, b->Y64, c->q64, b->bn2, c->den,
                                                        tol,
@@ -1020,12 +1034,8 @@ aln_status batch_solve(aln_ctx* c, double tol, int max_iter, double* X, int64_t 
     if (X0dev) {  // g = Q y0 + q, in FP64, for a start point
         k_bunscale<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, c->s, b->X64, b->Y64,
                                                              b->small_vpl ? s.E : nullptr);
-        const int64_t ky = k * c->ldq;
-        if (launch_split_f64(b->Y64, ky, b->Yp, b->Yp + ky, c->stream) != cudaSuccess ||
-            launch_gemm_pairs_axpy(b->Qp, b->Qp + c->ldq * c->ldq, c->ldq, b->Yp, b->Yp + ky,
-                                   c->ldq, c->n, c->n, k, c->q64, b->G64,
-                               c->ldq, c->stream) != cudaSuccess)
-            return ALN_ERR_CUDA;
+        aln_status gs = bw_qy(c, b);
+        if (gs != ALN_OK) return gs;
         k_bsetg<<<(unsigned)k, kBThreads, 0, c->stream>>>(s, b->G64);
         c->launches += 3;
     }

@@ -35,13 +35,6 @@ cudaError_t launch_qvec64(const void* A, int32_t dtype, int64_t d, int64_t n, in
 
 cudaError_t launch_gram32_dot2(const float* A, int64_t d, int64_t n, int64_t lda,
                                const double* inv_s, double* Q, int64_t ldq, cudaStream_t st);
-cudaError_t launch_qvec32_dot2(const float* A, int64_t d, int64_t n, int64_t lda, const float* B,
-                               int64_t k, int64_t ldb, const double* inv_s, double* q64,
-                               int64_t ldq, cudaStream_t st);
-cudaError_t launch_split_f64(const double* v, int64_t m, float* hi, float* lo, cudaStream_t st);
-cudaError_t launch_gemm_pairs_axpy(const float* Xh, const float* Xl, int64_t ldx, const float* Yh,
-                                   const float* Yl, int64_t ldy, int64_t K, int64_t M, int64_t N,
-                                   const double* add, double* out, int64_t ldo, cudaStream_t st);
 cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                int64_t K, int64_t M, int64_t N, const double* add, double* out,
                                int64_t ldo, cudaStream_t st);
@@ -285,6 +278,13 @@ size_t oz_work_bytes(int64_t d, int64_t m, int64_t n);
 cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
                           int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
                           void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st);
+// The same products for FP32 or FP64 inputs (xtype, ytype: aln_dtype; FP64
+// values keep their leading 48 bits): mode 0 writes −C_ij·vec[i], mode 1
+// writes C_ij + vec[j·ldo + i] (the FP64 check's g = Q·y + q).
+cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ldx,
+                              int32_t ytype, const void* Y, int64_t ldy, int64_t d, int64_t m,
+                              int64_t n, const double* vec, double* out, int64_t ldo, void* work,
+                              size_t work_bytes, int* timeout_flag, cudaStream_t st);
 
 // kkt.cu — FP64 KKT residual straight from A
 cudaError_t launch_kkt(aln_ctx* c, const double* x64, const void* b, double den, double* out2);

@@ -56,14 +56,16 @@ constexpr int kOzYBytes = 3 * kOzATile + 4 * kOzBTile;  // 80 KiB
 constexpr int kOzSmem = kOzXBytes + kOzYBytes + 1024 + 256;
 constexpr uint32_t kOzTmemCols = 512;      // 7 accumulators × 64 columns, rounded up
 constexpr int kOzFlush = 16;               // half steps (8 K blocks) per FP64 flush
+constexpr int kOzQvec = 0;                 // out = −C·inv_s
+constexpr int kOzAxpy = 1;                 // out = C + vec
 
 struct OzArgs {
     int num_kb;            // 64-wide K blocks
     int64_t m, n;          // columns of X (rows of C), columns of Y
     const int* ex;         // [m] exponents of X's columns
     const int* ey;         // [n] exponents of Y's columns
-    const double* inv_s;   // [m] factor of row i of C
-    double* out;           // C[j][i] at out[j·ldo + i] (negated, scaled)
+    const double* vec;     // kOzQvec: inv_s [m]; kOzAxpy: the added term, as out
+    double* out;           // at out[j·ldo + i]: −C_ij·inv_s[i] or C_ij + vec[j·ldo + i]
     int64_t ldo;
     int* timeout_flag;
 };
@@ -109,6 +111,7 @@ __device__ __forceinline__ void oz_half(uint32_t tmem, uint32_t a, uint32_t b) {
     }
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant__ OzMaps maps,
                                                          OzArgs p) {
     extern __shared__ uint8_t smem_raw[];
@@ -253,13 +256,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
         const int64_t i = m0 + 32 * q + lane;
         if (i < p.m) {
             const int ei = p.ex[i];
-            const double f = -p.inv_s[i];
+            const double f = MODE == kOzQvec ? -p.vec[i] : 1.0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int64_t c = n0 + 32 * half + j;
                 if (c < p.n) {
-                    const double v = acc[j] + ((double)hi[j] + (double)lo[j]);
-                    p.out[c * p.ldo + i] = ldexp(v, ei + p.ey[c]) * f;
+                    const double v = ldexp(acc[j] + ((double)hi[j] + (double)lo[j]), ei + p.ey[c]);
+                    const int64_t o = c * p.ldo + i;
+                    p.out[o] = MODE == kOzQvec ? v * f : v + p.vec[o];
                 }
             }
         }
@@ -280,29 +284,31 @@ __global__ void __launch_bounds__(256) k_oz_split(const T* __restrict__ X, int64
                                                   int64_t ldk, int* __restrict__ ex,
                                                   __nv_bfloat16* __restrict__ dig,
                                                   int64_t dstride) {
-    __shared__ float smax[8];
+    __shared__ T smax[8];
     const int64_t col = blockIdx.x;
     const T* x = X + col * ld;
-    float mx = 0.0f;
-    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) mx = fmaxf(mx, fabsf((float)x[t]));
+    T mx = T(0);
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) mx = fmax(mx, fabs(x[t]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
     __syncthreads();
-    mx = 0.0f;
+    mx = T(0);
 #pragma unroll
-    for (int w = 0; w < 8; ++w) mx = fmaxf(mx, smax[w]);
+    for (int w = 0; w < 8; ++w) mx = fmax(mx, smax[w]);
     int e = 0;
-    if (mx > 0.0f) (void)frexpf(mx, &e);  // mx = m·2^e, m in [0.5, 1)
+    if (mx > T(0)) (void)frexp(mx, &e);  // mx = m·2^e, m in [0.5, 1)
     if (threadIdx.x == 0) ex[col] = e;
+    // digits in the input's own precision: every step is exact (|v| < 1
+    // times 256, truncation, subtraction of the integer part)
     for (int64_t t = threadIdx.x; t < ldk; t += blockDim.x) {
-        float v = t < d ? ldexpf((float)x[t], -e) : 0.0f;  // |v| < 1, exact
+        T v = t < d ? ldexp(x[t], -e) : T(0);
 #pragma unroll
         for (int s = 0; s < kOzS; ++s) {
-            v *= 256.0f;
-            const float dv = truncf(v);
+            v *= T(256);
+            const T dv = trunc(v);
             v -= dv;
-            dig[(int64_t)s * dstride + col * ldk + t] = __float2bfloat16_rn(dv);
+            dig[(int64_t)s * dstride + col * ldk + t] = __float2bfloat16_rn((float)dv);
         }
     }
 }
@@ -330,20 +336,32 @@ size_t oz_work_bytes(int64_t d, int64_t m, int64_t n) {
     return (size_t)(6 * (m + n) * ldk * 2) + (size_t)round_up((m + n) * 4, 256) + 1024;
 }
 
-cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
-                          int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
-                          void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st) {
+cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ldx,
+                              int32_t ytype, const void* Y, int64_t ldy, int64_t d, int64_t m,
+                              int64_t n, const double* vec, double* out, int64_t ldo, void* work,
+                              size_t work_bytes, int* timeout_flag, cudaStream_t st) {
     using namespace tc;
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (!work || work_bytes < oz_work_bytes(d, m, n)) return cudaErrorInvalidValue;
+    if (!work || work_bytes < oz_work_bytes(d, m, n) || (mode != kOzQvec && mode != kOzAxpy))
+        return cudaErrorInvalidValue;
     const int64_t ldk = round_up(d, BK);
     uint8_t* w = (uint8_t*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
     __nv_bfloat16* dx = (__nv_bfloat16*)w;                 // 6 × [m][ldk]
     __nv_bfloat16* dy = dx + 6 * m * ldk;                  // 6 × [n][ldk]
     int* ex = (int*)(dy + 6 * n * ldk);
     int* ey = ex + m;
-    k_oz_split<float><<<(unsigned)m, 256, 0, st>>>(X, ldx, d, ldk, ex, dx, m * ldk);
-    k_oz_split<float><<<(unsigned)n, 256, 0, st>>>(Y, ldy, d, ldk, ey, dy, n * ldk);
+    if (xtype == ALN_DTYPE_F32)
+        k_oz_split<float><<<(unsigned)m, 256, 0, st>>>((const float*)X, ldx, d, ldk, ex, dx,
+                                                         m * ldk);
+    else
+        k_oz_split<double><<<(unsigned)m, 256, 0, st>>>((const double*)X, ldx, d, ldk, ex, dx,
+                                                          m * ldk);
+    if (ytype == ALN_DTYPE_F32)
+        k_oz_split<float><<<(unsigned)n, 256, 0, st>>>((const float*)Y, ldy, d, ldk, ey, dy,
+                                                         n * ldk);
+    else
+        k_oz_split<double><<<(unsigned)n, 256, 0, st>>>((const double*)Y, ldy, d, ldk, ey, dy,
+                                                          n * ldk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     OzMaps maps;
@@ -351,11 +369,12 @@ cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t l
         if (!oz_map(&maps.x[s], dx + s * m * ldk, ldk, m, ldk, BM) ||
             !oz_map(&maps.y[s], dy + s * n * ldk, ldk, n, ldk, kOzN))
             return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_oz_atb, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+    static bool attr[2] = {false, false};
+    const auto fn = mode == kOzQvec ? k_oz_atb<kOzQvec> : k_oz_atb<kOzAxpy>;
+    if (!attr[mode]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr[mode] = true;
     }
     OzArgs a;
     a.num_kb = (int)(ldk / BK);
@@ -363,13 +382,20 @@ cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t l
     a.n = n;
     a.ex = ex;
     a.ey = ey;
-    a.inv_s = inv_s;
+    a.vec = vec;
     a.out = out;
     a.ldo = ldo;
     a.timeout_flag = timeout_flag;
     const dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, kOzN));
-    k_oz_atb<<<grid, kOzThreads, kOzSmem, st>>>(maps, a);
+    fn<<<grid, kOzThreads, kOzSmem, st>>>(maps, a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
+                          int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
+                          void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st) {
+    return launch_oz_product(tc::kOzQvec, ALN_DTYPE_F32, X, ldx, ALN_DTYPE_F32, Y, ldy, d, m, n,
+                             inv_s, out, ldo, work, work_bytes, timeout_flag, st);
 }
 
 }  // namespace aln

@@ -244,8 +244,8 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
 // The same products for FP32 inputs with FP64-level accuracy on the FP32
 // pipe: every multiply-add is a Dot2 step (TwoProduct by FMA + TwoSum, Ogita,
 // Rump & Oishi 2005), so each output carries a float pair (s, c) and is
-// rounded to FP64 as s + c.  Used by the batched prepare, where q and the
-// FP64 scaled matrix of the checks must be FP64-accurate but the FP64 pipe of
+// rounded to FP64 as s + c.  Used by the batched prepare for the FP64 scaled
+// matrix of the checks, which must be FP64-accurate while the FP64 pipe of
 // this GPU is the bottleneck.  Same tiling and epilogues as k_atb64.  The
 // pairs are flushed into FP64 sums every kDot2Flush terms: the rounding of the
 // FP32 compensation term grows with the number of terms it gathers (about
@@ -350,106 +350,6 @@ __global__ void __launch_bounds__(256) k_atb32_dot2(const float* __restrict__ X,
     }
 }
 
-// ---------------------------------------------------------------------------
-// out = XᵀY + add for FP64 X, Y given as FP32 pairs (v = hi + lo, ~48 bits):
-// per multiply-add the exact product hi·hi (TwoProduct by FMA), the cross
-// terms hi·lo + lo·hi in the compensation, TwoSum into the running pair;
-// pairs flushed to FP64 every kDot2Flush terms.  The FP64 checks of the
-// batched solver use it for g = Q·Y + q: the FP64 SIMT product was the
-// largest part of those checks on this GPU's narrow FP64 pipe.
-// ---------------------------------------------------------------------------
-__global__ void k_split_f64(const double* __restrict__ v, int64_t m, float* __restrict__ hi,
-                            float* __restrict__ lo) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float h = (float)v[i];
-        hi[i] = h;
-        lo[i] = (float)(v[i] - (double)h);
-    }
-}
-
-__global__ void __launch_bounds__(256) k_atb_pairs_axpy(
-    const float* __restrict__ Xh, const float* __restrict__ Xl, int64_t ldx,
-    const float* __restrict__ Yh, const float* __restrict__ Yl, int64_t ldy, int64_t K, int64_t M,
-    int64_t N, int tiles_m, const double* __restrict__ add, double* __restrict__ out,
-    int64_t ldo) {
-    __shared__ float Xs[2][kG64K][kG64Tile];
-    __shared__ float Ys[2][kG64K][kG64Tile];
-    const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-    const int64_t i0 = (int64_t)tm * kG64Tile, j0 = (int64_t)tn * kG64Tile;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float s[4][4], c[4][4];
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            s[a][b] = c[a][b] = 0.0f;
-            acc[a][b] = 0.0;
-        }
-    for (int64_t k0 = 0; k0 < K; k0 += kG64K) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = threadIdx.x + 256 * u;
-            const int kk = e & 15, ii = e >> 4;
-            const int64_t gk = k0 + kk;
-            const int64_t gi = i0 + ii, gj = j0 + ii;
-            const bool xv = gi < M && gk < K, yv = gj < N && gk < K;
-            Xs[0][kk][ii] = xv ? Xh[gi * ldx + gk] : 0.0f;
-            Xs[1][kk][ii] = xv ? Xl[gi * ldx + gk] : 0.0f;
-            Ys[0][kk][ii] = yv ? Yh[gj * ldy + gk] : 0.0f;
-            Ys[1][kk][ii] = yv ? Yl[gj * ldy + gk] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 2
-        for (int kk = 0; kk < kG64K; ++kk) {
-            float xh[4], xl[4], yh[4], yl[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                xh[a] = Xs[0][kk][ty + 16 * a];
-                xl[a] = Xs[1][kk][ty + 16 * a];
-            }
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                yh[b] = Ys[0][kk][tx + 16 * b];
-                yl[b] = Ys[1][kk][tx + 16 * b];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const float p = mul_rn(xh[a], yh[b]);
-                    const float ep = fmaf(xh[a], yh[b], -p);
-                    const float cross = fmaf(xh[a], yl[b], fmaf(xl[a], yh[b], ep));
-                    const float t = s[a][b] + p;
-                    const float z = t - s[a][b];
-                    c[a][b] += ((s[a][b] - (t - z)) + (p - z)) + cross;
-                    s[a][b] = t;
-                }
-        }
-        __syncthreads();
-        if ((k0 + kG64K) % kDot2Flush == 0 || k0 + kG64K >= K) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b] += (double)s[a][b] + (double)c[a][b];
-                    s[a][b] = c[a][b] = 0.0f;
-                }
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int64_t i = i0 + ty + 16 * a;
-        if (i >= M) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int64_t j = j0 + tx + 16 * b;
-            if (j < N) out[j * ldo + i] = acc[a][b] + add[j * ldo + i];
-        }
-    }
-}
-
 // ----------------------------------------------------------------------------
 // Host launchers
 // ----------------------------------------------------------------------------
@@ -461,14 +361,6 @@ cudaError_t launch_gram32_dot2(const float* A, int64_t d, int64_t n, int64_t lda
     return cudaGetLastError();
 }
 
-cudaError_t launch_qvec32_dot2(const float* A, int64_t d, int64_t n, int64_t lda, const float* B,
-                               int64_t k, int64_t ldb, const double* inv_s, double* q64,
-                               int64_t ldq, cudaStream_t st) {
-    const int64_t tm = ceil_div(n, kG64Tile), tn = ceil_div(k, kG64Tile);
-    k_atb32_dot2<MODE_QVEC><<<(unsigned)(tm * tn), 256, 0, st>>>(A, lda, B, ldb, d, n, k, (int)tm,
-                                                                 inv_s, q64, ldq);
-    return cudaGetLastError();
-}
 cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
                             const void* B, int kc, int64_t ldb, double* s, double* inv_s,
                             double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
@@ -595,21 +487,6 @@ cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, in
     const int64_t tm = ceil_div(M, kG64Tile), tn = ceil_div(N, kG64Tile);
     k_atb64<double, double, MODE_AXPY><<<(unsigned)(tm * tn), 256, 0, st>>>(
         X, ldx, Y, ldy, K, M, N, (int)tm, add, out, ldo);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_split_f64(const double* v, int64_t m, float* hi, float* lo, cudaStream_t st) {
-    k_split_f64<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 256), 4096)), 256,
-                  0, st>>>(v, m, hi, lo);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_gemm_pairs_axpy(const float* Xh, const float* Xl, int64_t ldx, const float* Yh,
-                                   const float* Yl, int64_t ldy, int64_t K, int64_t M, int64_t N,
-                                   const double* add, double* out, int64_t ldo, cudaStream_t st) {
-    const int64_t tm = ceil_div(M, kG64Tile), tn = ceil_div(N, kG64Tile);
-    k_atb_pairs_axpy<<<(unsigned)(tm * tn), 256, 0, st>>>(Xh, Xl, ldx, Yh, Yl, ldy, K, M, N,
-                                                          (int)tm, add, out, ldo);
     return cudaGetLastError();
 }
 
