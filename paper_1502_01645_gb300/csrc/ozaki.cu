@@ -36,6 +36,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <utility>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -111,7 +113,9 @@ __device__ __forceinline__ void oz_half(uint32_t tmem, uint32_t a, uint32_t b) {
     }
 }
 
-template <int MODE>
+// TR: X and Y were swapped by the launcher (C is computed transposed), so
+// tile row i is output column and tile column c output row.
+template <int MODE, bool TR>
 __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant__ OzMaps maps,
                                                          OzArgs p) {
     extern __shared__ uint8_t smem_raw[];
@@ -256,14 +260,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
         const int64_t i = m0 + 32 * q + lane;
         if (i < p.m) {
             const int ei = p.ex[i];
-            const double f = MODE == kOzQvec ? -p.vec[i] : 1.0;
+            const double f = (MODE == kOzQvec && !TR) ? -p.vec[i] : 1.0;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int64_t c = n0 + 32 * half + j;
                 if (c < p.n) {
                     const double v = ldexp(acc[j] + ((double)hi[j] + (double)lo[j]), ei + p.ey[c]);
-                    const int64_t o = c * p.ldo + i;
-                    p.out[o] = MODE == kOzQvec ? v * f : v + p.vec[o];
+                    const int64_t o = TR ? i * p.ldo + c : c * p.ldo + i;
+                    if (MODE == kOzQvec)
+                        p.out[o] = v * (TR ? -p.vec[c] : f);
+                    else
+                        p.out[o] = v + p.vec[o];
                 }
             }
         }
@@ -344,6 +351,15 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
     if (m <= 0 || n <= 0) return cudaSuccess;
     if (!work || work_bytes < oz_work_bytes(d, m, n) || (mode != kOzQvec && mode != kOzAxpy))
         return cudaErrorInvalidValue;
+    // a narrow X (fewer columns than a 128-row tile) and a wide Y: compute Cᵀ,
+    // so the wide side fills the 128-row tiles
+    const bool tr = m < BM && n >= BM;
+    if (tr) {
+        std::swap(X, Y);
+        std::swap(ldx, ldy);
+        std::swap(xtype, ytype);
+        std::swap(m, n);
+    }
     const int64_t ldk = round_up(d, BK);
     uint8_t* w = (uint8_t*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
     __nv_bfloat16* dx = (__nv_bfloat16*)w;                 // 6 × [m][ldk]
@@ -369,12 +385,13 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
         if (!oz_map(&maps.x[s], dx + s * m * ldk, ldk, m, ldk, BM) ||
             !oz_map(&maps.y[s], dy + s * n * ldk, ldk, n, ldk, kOzN))
             return cudaErrorInvalidValue;
-    static bool attr[2] = {false, false};
-    const auto fn = mode == kOzQvec ? k_oz_atb<kOzQvec> : k_oz_atb<kOzAxpy>;
-    if (!attr[mode]) {
+    static bool attr[2][2] = {{false, false}, {false, false}};
+    const auto fn = mode == kOzQvec ? (tr ? k_oz_atb<kOzQvec, true> : k_oz_atb<kOzQvec, false>)
+                                    : (tr ? k_oz_atb<kOzAxpy, true> : k_oz_atb<kOzAxpy, false>);
+    if (!attr[mode][tr]) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
         if (e != cudaSuccess) return e;
-        attr[mode] = true;
+        attr[mode][tr] = true;
     }
     OzArgs a;
     a.num_kb = (int)(ldk / BK);

@@ -391,15 +391,17 @@ def test_batched_prepare_matches_oracle(aln):
     np.testing.assert_array_equal(Q, Q.T)
 
 
-@pytest.mark.parametrize("signed", [False, True])
-def test_batched_q_from_digit_products(aln, signed):
+@pytest.mark.parametrize("signed,d,n,k", [(False, 997, 130, 70), (True, 997, 130, 70),
+                                          (True, 700, 60, 300)])
+def test_batched_q_from_digit_products(aln, signed, d, n, k):
     """q = −D⁻¹Aᵀb of the batched prepare (exact 8-bit digit products on the
     tensor cores, 48 bits per value, pairs of order ≤ 8) against FP64, entry
     by entry, relative to Σ_t |a_ti b_t| / s_i (the natural scale of a
     compensated product): columns six decades apart, a zero column, mixed
-    signs, d, n and k ragged against the 64 × 128 × 64 tiles."""
-    r = np.random.default_rng(91 + signed)
-    d, n, k = 997, 130, 70
+    signs, d, n and k ragged against the 64 × 128 × 64 tiles; n = 60 < 128
+    with k = 300 runs the product transposed (the wide side on the 128-row
+    tiles)."""
+    r = np.random.default_rng(91 + signed + n)
     A = r.random((d, n)) * np.exp(r.uniform(np.log(1e-3), np.log(1e3), n))[None, :]
     B = r.standard_normal((k, d)) if signed else r.random((k, d))
     if signed:
