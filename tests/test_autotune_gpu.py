@@ -104,6 +104,25 @@ def test_single_problem_tuning_is_recorded_reused_and_correct(aln, tmp_path):
         _check(A, b, x, 1e-9)
 
 
+def test_fp64_single_problem_tuning(aln, tmp_path):
+    """The plain FP64 method (replicated-state kernel, n = 600) tuned and
+    solved to tol 1e-12: FP64 parity with the oracle's optimum as in the
+    untuned FP64 tests (‖Δx‖∞/‖x*‖∞ ≤ 1e-8)."""
+    cache = tmp_path / "tune.json"
+    r = np.random.default_rng(67)
+    A = np.asfortranarray(r.random((1500, 600)))
+    x = np.where(r.random(600) < 0.5, 0.0, r.random(600))
+    b = A @ x + 0.01 * r.standard_normal(1500)
+    with aln.Solver("fp64", autotune=2, autotune_cache=str(cache)) as s:
+        s.prepare(A, b)
+        X, info = s.solve(tol=1e-12)
+        assert s.stats().iter_kernel == 2
+    assert any(k.startswith("single fp64 n=600 ") for k in _entries(cache))
+    assert info[0].rel_kkt <= 1e-12
+    x_star, _, _, _ = O.reference_solution(A, b)
+    assert np.abs(X[0] - x_star).max() <= 1e-8 * np.abs(x_star).max()
+
+
 def test_cached_choice_applies_only_to_its_shape(aln, tmp_path):
     """A shape with no entry runs the caller's geometry under autotune = 1."""
     cache = tmp_path / "tune.json"

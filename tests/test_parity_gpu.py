@@ -112,13 +112,16 @@ def test_split_bf16_gram_tall_narrow_split_k(aln, device_a):
     assert rel <= 1e-9, rel
 
 
-@pytest.mark.parametrize("d,n", [(3000, 2300), (20000, 300), (40000, 1300)])
+@pytest.mark.parametrize("d,n", [(3000, 2300), (20000, 300), (40000, 1300), (5000, 4224)])
 def test_host_and_device_input_give_the_same_result(aln, d, n):
     """Host A is copied in column chunks and each chunk's Gram tile rows run
     as it lands; device A takes one launch.  The tiles' K chunking (split K
-    for tall, narrow A) is fixed by the whole matrix, so both give the same
-    Q bits, the same iterations and the same solution: 3 chunk launches
-    without split K, 1 with, and 2 with."""
+    for tall, narrow A; stream-K for the pairs past the last full wave) is
+    fixed by the whole matrix, so both give the same Q bits, the same
+    iterations and the same solution: 3 chunk launches without split K and
+    with stream-K (n = 2300: 19 tail pairs, all in the last chunk), 1 and 2
+    with split K, and 5 with stream-K off (n = 4224: 105 tail pairs, more
+    than the last chunk's 33)."""
     import torch
     r = np.random.default_rng(d + n)
     A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
