@@ -886,6 +886,22 @@ void batch_free(aln_ctx* c) {
     c->batch = nullptr;
 }
 
+// The FP64 scaled matrix of the checks from FP32 A by exact digit products.
+static cudaError_t oz_gram(aln_ctx* c, BatchWork* b) {
+    const size_t need = oz_work_bytes(c->d, c->n, c->n);
+    if (c->oz_work_bytes < need) {
+        if (c->oz_work) cudaFree(c->oz_work);
+        c->oz_work = nullptr;
+        c->oz_work_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->oz_work, need);
+        if (e != cudaSuccess) return e;
+        c->oz_work_bytes = need;
+    }
+    c->launches += 4;
+    return launch_oz_gram((const float*)c->A, c->lda, c->d, c->n, c->inv_s, b->Q64, c->ldq,
+                          c->oz_work, c->oz_work_bytes, c->flags + 1, c->stream);
+}
+
 // Alg. 1 for a batch: s and q in FP64 (prepare kernels), Q64 in FP64 (kept for
 // the checks), Q in FP32 and its BF16 split for the tensor-core iteration.
 aln_status batch_prepare(aln_ctx* c) {
@@ -905,8 +921,7 @@ aln_status batch_prepare(aln_ctx* c) {
     if (st != ALN_OK) return st;
     const cudaError_t eg =
         c->dtype == ALN_DTYPE_F32
-            ? launch_gram32_dot2((const float*)c->A, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq,
-                                 c->stream)
+            ? oz_gram(c, b)
             : launch_gram64(c->A, c->dtype, c->d, c->n, c->lda, c->inv_s, b->Q64, c->ldq,
                             c->stream);
     if (eg != cudaSuccess) return ALN_ERR_CUDA;

@@ -278,6 +278,11 @@ size_t oz_work_bytes(int64_t d, int64_t m, int64_t n);
 cudaError_t launch_oz_atb(const float* X, int64_t ldx, const float* Y, int64_t ldy, int64_t d,
                           int64_t m, int64_t n, const double* inv_s, double* out, int64_t ldo,
                           void* work, size_t work_bytes, int* timeout_flag, cudaStream_t st);
+// Q = D⁻¹AᵀAD⁻¹ (the batched checks' FP64 scaled matrix) by the same exact
+// products: exactly symmetric, unit diagonal (0 for a zero column).
+cudaError_t launch_oz_gram(const float* A, int64_t lda, int64_t d, int64_t n,
+                           const double* inv_s, double* Q, int64_t ldq, void* work,
+                           size_t work_bytes, int* timeout_flag, cudaStream_t st);
 // The same products for FP32 or FP64 inputs (xtype, ytype: aln_dtype; FP64
 // values keep their leading 48 bits): mode 0 writes −C_ij·vec[i], mode 1
 // writes C_ij + vec[j·ldo + i] (the FP64 check's g = Q·y + q).

@@ -60,6 +60,8 @@ constexpr uint32_t kOzTmemCols = 512;      // 7 accumulators × 64 columns, roun
 constexpr int kOzFlush = 16;               // half steps (8 K blocks) per FP64 flush
 constexpr int kOzQvec = 0;                 // out = −C·inv_s
 constexpr int kOzAxpy = 1;                 // out = C + vec
+constexpr int kOzGram = 2;                 // X = Y: out[c·ldo + i] = C·inv_s_i·inv_s_c for
+                                           // i ≥ c (diagonal 1, or 0 for a zero column)
 
 struct OzArgs {
     int num_kb;            // 64-wide K blocks
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
         if (i < p.m) {
             const int ei = p.ex[i];
             const double f = (MODE == kOzQvec && !TR) ? -p.vec[i] : 1.0;
+            (void)f;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int64_t c = n0 + 32 * half + j;
@@ -269,8 +272,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
                     const int64_t o = TR ? i * p.ldo + c : c * p.ldo + i;
                     if (MODE == kOzQvec)
                         p.out[o] = v * (TR ? -p.vec[c] : f);
-                    else
+                    else if (MODE == kOzAxpy)
                         p.out[o] = v + p.vec[o];
+                    else if (i >= c)  // kOzGram: one triangle, mirrored afterwards
+                        p.out[o] = i == c ? (v != 0.0 ? 1.0 : 0.0) : v * p.vec[i] * p.vec[c];
                 }
             }
         }
@@ -349,11 +354,12 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
                               size_t work_bytes, int* timeout_flag, cudaStream_t st) {
     using namespace tc;
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (!work || work_bytes < oz_work_bytes(d, m, n) || (mode != kOzQvec && mode != kOzAxpy))
+    if (!work || work_bytes < oz_work_bytes(d, m, n) ||
+        (mode != kOzQvec && mode != kOzAxpy && mode != kOzGram))
         return cudaErrorInvalidValue;
     // a narrow X (fewer columns than a 128-row tile) and a wide Y: compute Cᵀ,
     // so the wide side fills the 128-row tiles
-    const bool tr = m < BM && n >= BM;
+    const bool tr = mode != kOzGram && m < BM && n >= BM;
     if (tr) {
         std::swap(X, Y);
         std::swap(ldx, ldy);
@@ -385,9 +391,10 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
         if (!oz_map(&maps.x[s], dx + s * m * ldk, ldk, m, ldk, BM) ||
             !oz_map(&maps.y[s], dy + s * n * ldk, ldk, n, ldk, kOzN))
             return cudaErrorInvalidValue;
-    static bool attr[2][2] = {{false, false}, {false, false}};
-    const auto fn = mode == kOzQvec ? (tr ? k_oz_atb<kOzQvec, true> : k_oz_atb<kOzQvec, false>)
-                                    : (tr ? k_oz_atb<kOzAxpy, true> : k_oz_atb<kOzAxpy, false>);
+    static bool attr[3][2] = {{false, false}, {false, false}, {false, false}};
+    const auto fn = mode == kOzQvec  ? (tr ? k_oz_atb<kOzQvec, true> : k_oz_atb<kOzQvec, false>)
+                    : mode == kOzGram ? k_oz_atb<kOzGram, false>
+                                      : (tr ? k_oz_atb<kOzAxpy, true> : k_oz_atb<kOzAxpy, false>);
     if (!attr[mode][tr]) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
         if (e != cudaSuccess) return e;
@@ -405,6 +412,27 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
     a.timeout_flag = timeout_flag;
     const dim3 grid((unsigned)ceil_div(m, BM), (unsigned)ceil_div(n, kOzN));
     fn<<<grid, kOzThreads, kOzSmem, st>>>(maps, a);
+    return cudaGetLastError();
+}
+
+namespace tc {
+namespace {
+// Q[i][j] = Q[j][i] for i < j (the lower triangle written by kOzGram: entry
+// (row c, column i ≥ c) at out[c·ldo + i]).
+__global__ void k_oz_mirror(double* __restrict__ Q, int64_t n, int64_t ldq) {
+    const int64_t i = blockIdx.x;
+    for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) Q[j * ldq + i] = Q[i * ldq + j];
+}
+}  // namespace
+}  // namespace tc
+
+cudaError_t launch_oz_gram(const float* A, int64_t lda, int64_t d, int64_t n,
+                           const double* inv_s, double* Q, int64_t ldq, void* work,
+                           size_t work_bytes, int* timeout_flag, cudaStream_t st) {
+    cudaError_t e = launch_oz_product(tc::kOzGram, ALN_DTYPE_F32, A, lda, ALN_DTYPE_F32, A, lda,
+                                      d, n, n, inv_s, Q, ldq, work, work_bytes, timeout_flag, st);
+    if (e != cudaSuccess || n <= 1) return e;
+    tc::k_oz_mirror<<<(unsigned)n, 256, 0, st>>>(Q, n, ldq);
     return cudaGetLastError();
 }
 
