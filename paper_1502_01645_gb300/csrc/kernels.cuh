@@ -33,8 +33,6 @@ cudaError_t launch_qvec64(const void* A, int32_t dtype, int64_t d, int64_t n, in
                           const void* B, int64_t k, int64_t ldb, const double* inv_s, double* q64,
                           int64_t ldq, cudaStream_t st);
 
-cudaError_t launch_gram32_dot2(const float* A, int64_t d, int64_t n, int64_t lda,
-                               const double* inv_s, double* Q, int64_t ldq, cudaStream_t st);
 cudaError_t launch_gemm64_axpy(const double* X, int64_t ldx, const double* Y, int64_t ldy,
                                int64_t K, int64_t M, int64_t N, const double* add, double* out,
                                int64_t ldo, cudaStream_t st);

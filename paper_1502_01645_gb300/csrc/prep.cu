@@ -240,127 +240,9 @@ __global__ void __launch_bounds__(256) k_atb64(const TX* __restrict__ X, int64_t
     }
 }
 
-// ---------------------------------------------------------------------------
-// The same products for FP32 inputs with FP64-level accuracy on the FP32
-// pipe: every multiply-add is a Dot2 step (TwoProduct by FMA + TwoSum, Ogita,
-// Rump & Oishi 2005), so each output carries a float pair (s, c) and is
-// rounded to FP64 as s + c.  Used by the batched prepare for the FP64 scaled
-// matrix of the checks, which must be FP64-accurate while the FP64 pipe of
-// this GPU is the bottleneck.  Same tiling and epilogues as k_atb64.  The
-// pairs are flushed into FP64 sums every kDot2Flush terms: the rounding of the
-// FP32 compensation term grows with the number of terms it gathers (about
-// m·u²·Σ|x·y| after m terms, u = 2⁻²⁴), so flushing bounds m by the chunk
-// instead of by the whole inner dimension.
-// ---------------------------------------------------------------------------
-constexpr int kDot2Flush = 128;
-template <int MODE>
-__global__ void __launch_bounds__(256) k_atb32_dot2(const float* __restrict__ X, int64_t ldx,
-                                                    const float* __restrict__ Y, int64_t ldy,
-                                                    int64_t K, int64_t M, int64_t N, int tiles_m,
-                                                    const double* __restrict__ inv_s,
-                                                    double* __restrict__ out, int64_t ldo) {
-    __shared__ float Xs[kG64K][kG64Tile];
-    __shared__ float Ys[kG64K][kG64Tile];
-    int tm, tn;
-    int64_t kbeg = 0, kend = K;
-    if (MODE == MODE_GRAM) {
-        tri_decode(blockIdx.x, tm, tn);
-    } else if (MODE == MODE_PART) {
-        // tiles_m = lower-triangle tiles T, ldo = the K-chunk length
-        tri_decode(blockIdx.x % tiles_m, tm, tn);
-        kbeg = (int64_t)(blockIdx.x / tiles_m) * ldo;
-        kend = min(K, kbeg + ldo);
-    } else {
-        tm = blockIdx.x % tiles_m;
-        tn = blockIdx.x / tiles_m;
-    }
-    const int64_t i0 = (int64_t)tm * kG64Tile, j0 = (int64_t)tn * kG64Tile;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float s[4][4], c[4][4];
-    double acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            s[a][b] = c[a][b] = 0.0f;
-            acc[a][b] = 0.0;
-        }
-
-    for (int64_t k0 = 0; k0 < K; k0 += kG64K) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int e = threadIdx.x + 256 * u;
-            const int kk = e & 15, ii = e >> 4;
-            const int64_t gk = k0 + kk;
-            const int64_t gi = i0 + ii, gj = j0 + ii;
-            Xs[kk][ii] = (gi < M && gk < K) ? X[gi * ldx + gk] : 0.0f;
-            Ys[kk][ii] = (gj < N && gk < K) ? Y[gj * ldy + gk] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kG64K; ++kk) {
-            float xa[4], yb[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) xa[a] = Xs[kk][ty + 16 * a];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) yb[b] = Ys[kk][tx + 16 * b];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const float p = mul_rn(xa[a], yb[b]);
-                    const float ep = fmaf(xa[a], yb[b], -p);
-                    const float t = s[a][b] + p;
-                    const float z = t - s[a][b];
-                    c[a][b] += ((s[a][b] - (t - z)) + (p - z)) + ep;
-                    s[a][b] = t;
-                }
-        }
-        __syncthreads();
-        if ((k0 + kG64K) % kDot2Flush == 0 || k0 + kG64K >= K) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    acc[a][b] += (double)s[a][b] + (double)c[a][b];
-                    s[a][b] = c[a][b] = 0.0f;
-                }
-        }
-    }
-
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int64_t i = i0 + ty + 16 * a;
-        if (i >= M) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int64_t j = j0 + tx + 16 * b;
-            if (j >= N) continue;
-            const double v0 = acc[a][b];
-            if (MODE == MODE_GRAM) {
-                if (j > i) continue;
-                double v = v0 * inv_s[i] * inv_s[j];
-                if (i == j) v = v0 != 0.0 ? 1.0 : 0.0;
-                out[i * ldo + j] = v;
-                out[j * ldo + i] = v;
-            } else {
-                out[j * ldo + i] = -v0 * inv_s[i];
-            }
-        }
-    }
-}
-
 // ----------------------------------------------------------------------------
 // Host launchers
 // ----------------------------------------------------------------------------
-cudaError_t launch_gram32_dot2(const float* A, int64_t d, int64_t n, int64_t lda,
-                               const double* inv_s, double* Q, int64_t ldq, cudaStream_t st) {
-    const int64_t tm = ceil_div(n, kG64Tile);
-    k_atb32_dot2<MODE_GRAM><<<(unsigned)(tm * (tm + 1) / 2), 256, 0, st>>>(
-        A, lda, A, lda, d, n, n, (int)tm, inv_s, Q, ldq);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_colstats(const void* A, int32_t dtype, int64_t d, int64_t n, int64_t lda,
                             const void* B, int kc, int64_t ldb, double* s, double* inv_s,
                             double* q64, int64_t ldq, int* flags, __nv_bfloat16* hi,
