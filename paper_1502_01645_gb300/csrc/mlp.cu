@@ -828,6 +828,12 @@ struct Mlp {
     int qh_n = -1;
     int* hflag = nullptr;        // pinned
     double* hloss = nullptr;     // pinned
+    // prediction outputs kept between calls (no allocation per prediction):
+    // the kept flags, and the start points when the caller's X0 is on the host
+    int* kept = nullptr;
+    int64_t kept_cap = 0;
+    double* xtmp = nullptr;
+    size_t xtmp_bytes = 0;
 };
 
 #define M_TRY(call)                                          \
@@ -852,6 +858,8 @@ void free_mlp(Mlp* m) {
     if (m->wpool) cudaFree(m->wpool);
     if (m->apool) cudaFree(m->apool);
     if (m->hflag) cudaFreeHost(m->hflag);
+    if (m->kept) cudaFree(m->kept);
+    if (m->xtmp) cudaFree(m->xtmp);
     delete m;
 }
 
@@ -1593,14 +1601,29 @@ aln_status mlp_predict(aln_ctx* c, double* X0, int64_t ldx, int* kept) {
     }
     const bool x_dev = is_dev_ptr(X0);
     double* xdst = X0;
-    double* tmp = nullptr;
     if (!x_dev) {
-        M_TRY(cudaMalloc(&tmp, (size_t)k * n * 8));
-        xdst = tmp;
+        const size_t bytes = (size_t)k * n * 8;
+        if (M->xtmp_bytes < bytes) {
+            if (M->xtmp) cudaFree(M->xtmp);
+            M->xtmp = nullptr;
+            M->xtmp_bytes = 0;
+            M_TRY(cudaMalloc(&M->xtmp, bytes));
+            M->xtmp_bytes = bytes;
+        }
+        xdst = M->xtmp;
     }
     const int64_t ldd = x_dev ? ldx : n;
     int* kept_dev = nullptr;
-    if (kept) M_TRY(cudaMalloc(&kept_dev, (size_t)k * sizeof(int)));
+    if (kept) {
+        if (M->kept_cap < k) {
+            if (M->kept) cudaFree(M->kept);
+            M->kept = nullptr;
+            M->kept_cap = 0;
+            M_TRY(cudaMalloc(&M->kept, (size_t)k * sizeof(int)));
+            M->kept_cap = k;
+        }
+        kept_dev = M->kept;
+    }
     M_TRY(cudaMemsetAsync(c->flags + 1, 0, sizeof(int), c->stream));
     aln_status st = ALN_OK;
     for (int64_t b0 = 0; b0 < k && st == ALN_OK; b0 += chunk) {
@@ -1624,8 +1647,8 @@ aln_status mlp_predict(aln_ctx* c, double* X0, int64_t ldx, int* kept) {
         if (cudaGetLastError() != cudaSuccess) st = ALN_ERR_CUDA;
     }
     if (st == ALN_OK && !x_dev &&
-        cudaMemcpy2DAsync(X0, ldx * 8, tmp, n * 8, n * 8, k, cudaMemcpyDeviceToHost, c->stream) !=
-            cudaSuccess)
+        cudaMemcpy2DAsync(X0, ldx * 8, xdst, n * 8, n * 8, k, cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess)
         st = ALN_ERR_CUDA;
     if (st == ALN_OK && kept &&
         cudaMemcpyAsync(kept, kept_dev, (size_t)k * sizeof(int),
@@ -1633,8 +1656,6 @@ aln_status mlp_predict(aln_ctx* c, double* X0, int64_t ldx, int* kept) {
                         c->stream) != cudaSuccess)
         st = ALN_ERR_CUDA;
     if (st == ALN_OK) st = check_flags(c);
-    if (tmp) cudaFree(tmp);
-    if (kept_dev) cudaFree(kept_dev);
     return st;
 }
 
