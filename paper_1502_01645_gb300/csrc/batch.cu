@@ -944,7 +944,7 @@ __global__ void k_bsetg(BatchState s, const double* __restrict__ G64) {
 
 
 // G64 = Q64·Y64 + q for every column, FP64-accurate (exact BF16 digit
-// products on the tensor cores; the digits keep 48 bits below each row of
+// products on the tensor cores; the digits keep 49 bits below each row of
 // Q64 and each y).
 static aln_status bw_qy(aln_ctx* c, BatchWork* b) {
     const size_t need = oz_work_bytes(c->n, c->n, b->k);

@@ -1,32 +1,32 @@
 // FP64-accurate C = XᵀY on the tensor cores (the q = −D⁻¹Aᵀb of Alg. 1 for
 // many right-hand sides, Eq. NQPQ), by exact integer products.
 //
-// Every column of X (and of Y) is written as 2^e · Σ_{s=1..6} d_s 2^{−8s}
-// with e the column's exponent (max |x| < 2^e) and integer digits
-// |d_s| ≤ 255 taken by truncation, 8 bits at a time: 48 bits below the
-// column's largest entry, the rest (< 2^{e−48}) dropped.  A digit is exact in
-// BF16, a product of two digits (< 2^16) is exact in FP32, and a sum of up to
-// 256 of them stays below 2^24, so the tensor core's FP32 accumulation of
-// digit products is EXACT as long as an accumulator gathers at most 2^24
-// worth of them.  Then
-//     C_ij = 2^{e_i + f_j} Σ_{σ=2..8} 2^{−8σ} Σ_{s+u=σ} Σ_t d_s(x_ti) d_u(y_tj)
-// keeping the digit pairs with s + u ≤ 8 (26 pairs): the dropped pairs and the
-// truncated digits each stay below about 2^{−48}·Σ_t |x_ti|·max|y_j|, the
-// error of a Dot2 sum on the FP32 pipe.  This is the fixed-point splitting of Ozaki, Ogita,
-// Oishi and Rump (2012) for error-free matrix products, here with BF16
-// digits on tcgen05.
+// Every column of X (and of Y) is written as 2^e · Σ_{s=1..7} d_s 2^{−7s}
+// with e the column's exponent (max |x| < 2^e) and integer digits taken by
+// rounding to nearest, 7 bits at a time (|d_1| ≤ 128, |d_s| ≤ 64 after it):
+// 49 bits below the column's largest entry, the rest (≤ 2^{e−50}) dropped.
+// Rounded digits carry both signs, so the dropped parts have no bias.  A digit
+// is exact in BF16, a product of two digits (≤ 2^14) is exact in FP32, and a
+// sum of up to 1024 of them stays within 2^24, so the tensor core's FP32
+// accumulation of digit products is EXACT.  Then
+//     C_ij = 2^{e_i + f_j} Σ_{σ=2..8} 2^{−7σ} Σ_{s+u=σ} Σ_t d_s(x_ti) d_u(y_tj)
+// keeping the digit pairs with s + u ≤ 8 (28 pairs): the dropped pairs and the
+// rounded-off tails each stay below about 2^{−49}·2^{e_i+f_j} per term, the
+// error of a Dot2 sum on the FP32 pipe.  This is the fixed-point splitting of
+// Ozaki, Ogita, Oishi and Rump (2012) for error-free matrix products, here
+// with BF16 digits on tcgen05.
 //
 // One CTA computes a 128 (columns of X) × 64 (columns of Y) tile.  Per 64-wide
 // K block, two half steps:
-//   X half: digits 1–3 of X with digits 1–6 of Y (17 pairs, σ = 2..8),
-//   Y half: digits 4–6 of X with digits 1–4 of Y (9 pairs, σ = 5..8),
-// each into fresh TMEM accumulators, one per σ (64 columns each); no
-// accumulator holds more than 3 pairs × 64 products (< 2^24).  After each
-// half step eight promotion warps read the accumulators (integers in FP32),
-// scale them by 2^{−8σ} (exact) and add them into a double-float
+//   X half: digits 1–4 of X with digits 1–7 of Y (22 pairs, σ = 2..8),
+//   Y half: digits 5–7 of X with digits 1–3 of Y (6 pairs, σ = 6..8),
+// into TMEM accumulators, one per σ (64 columns each), kept over two K blocks
+// (128 products per pair): at most 7 pairs × 128 products of ≤ 2^14, below
+// 2^24.  Then eight promotion warps read the accumulators (integers in FP32),
+// scale them by 2^{−7σ} (exact) and add them into a double-float
 // accumulator (hi + lo, TwoSum), about 48 bits — the FP32 pipe, not this
-// GPU's narrow FP64 pipe.  The epilogue writes −(hi + lo)·2^{e+f}·inv_s in
-// FP64.
+// GPU's narrow FP64 pipe — while the loads of the next K blocks go on.  The
+// epilogue writes the FP64 result.
 //
 // Roles (320 threads): warp 0 (one lane) loads, warp 1 (one lane) issues the
 // MMAs, warps 2–9 promote (warp w: TMEM lanes 32·(w mod 4), output columns
@@ -46,18 +46,22 @@ namespace aln {
 namespace tc {
 namespace {
 
-constexpr int kOzS = 6;                    // digits per value
+constexpr int kOzS = 7;                    // digits per value
+constexpr int kOzBits = 7;                 // bits per digit
 constexpr int kOzSig = 8;                  // largest digit-pair order s + u kept
+constexpr int kOzXA = 4;                   // digits of X in the X half step (the rest in Y)
+constexpr int kOzYB = 3;                   // digits of Y in the Y half step
 constexpr int kOzN = 64;                   // output columns per CTA (Y side)
 constexpr int kOzThreads = 320;
 constexpr int kOzATile = BM * BK * 2;      // 16 KiB: 128 rows × 64 K
 constexpr int kOzBTile = kOzN * BK * 2;    // 8 KiB:   64 rows × 64 K
-// half-step buffers: X half = 3 A tiles + 6 B tiles, Y half = 3 A + 4 B
-constexpr int kOzXBytes = 3 * kOzATile + 6 * kOzBTile;  // 96 KiB
-constexpr int kOzYBytes = 3 * kOzATile + 4 * kOzBTile;  // 80 KiB
+// half-step buffers: X half = 4 A tiles + 7 B tiles, Y half = 3 A + 3 B
+constexpr int kOzXBytes = kOzXA * kOzATile + kOzS * kOzBTile;              // 120 KiB
+constexpr int kOzYBytes = (kOzS - kOzXA) * kOzATile + kOzYB * kOzBTile;    // 72 KiB
 constexpr int kOzSmem = kOzXBytes + kOzYBytes + 1024 + 256;
 constexpr uint32_t kOzTmemCols = 512;      // 7 accumulators × 64 columns, rounded up
-constexpr int kOzFlush = 16;               // half steps (8 K blocks) per FP64 flush
+constexpr int kOzPromo = 4;                // half steps (2 K blocks) per promotion
+constexpr int kOzFlush = 4;                // promotions (8 K blocks) per FP64 flush
 constexpr int kOzQvec = 0;                 // out = −C·inv_s
 constexpr int kOzAxpy = 1;                 // out = C + vec
 constexpr int kOzGram = 2;                 // X = Y: out[c·ldo + i] = C·inv_s_i·inv_s_c for
@@ -79,7 +83,7 @@ struct OzMaps {
     CUtensorMap y[kOzS];   // digits of Y, [n][ldk], box 64 × 64
 };
 
-// d ← d·2^{−8σ} added into the pair (hi, lo) (TwoSum; lo gathers the errors).
+// x added into the pair (hi, lo) (TwoSum; lo gathers the errors).
 __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     const float s = hi + x;
     const float bp = s - hi;
@@ -88,29 +92,29 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     lo += err;
 }
 
-// MMAs of one half step: pairs (s, u) with s in [S0, S0 + 3) and s + u ≤ 8,
+// MMAs of one half step: pairs (s, u) with s in [S0, S1] and s + u ≤ 8,
 // digit s of X at a + (s − S0)·A tile, digit u of Y at b + (u − 1)·B tile,
-// accumulator σ − 2 at column (σ − 2)·64.
-template <int S0>
-__device__ __forceinline__ void oz_half(uint32_t tmem, uint32_t a, uint32_t b) {
+// accumulator σ − 2 at column (σ − 2)·64.  `start` (X half only): the first
+// half step of a promotion block, where each accumulator's first MMA
+// overwrites it; that MMA is the pair (1, σ − 1), which exists for every
+// σ = 2..8.
+template <int S0, int S1>
+__device__ __forceinline__ void oz_half(uint32_t tmem, uint32_t a, uint32_t b, bool start) {
     constexpr uint32_t idesc = idesc_bf16_f32(BM, kOzN);
-    bool fresh[kOzSig - 1] = {true, true, true, true, true, true, true};
 #pragma unroll
-    for (int si = 0; si < 3; ++si) {
-        const int s = S0 + si;
+    for (int s = S0; s <= S1; ++s) {
 #pragma unroll
         for (int u = 1; u <= kOzS; ++u) {
             if (s + u > kOzSig) continue;
-            const int acc = s + u - 2;
-            const uint32_t d = tmem + (uint32_t)(acc * kOzN);
-            const uint32_t ab = a + (uint32_t)(si * kOzATile);
+            const uint32_t d = tmem + (uint32_t)((s + u - 2) * kOzN);
+            const uint32_t ab = a + (uint32_t)((s - S0) * kOzATile);
             const uint32_t bb = b + (uint32_t)((u - 1) * kOzBTile);
+            const bool fresh = S0 == 1 && s == 1 && start;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
                 umma_bf16(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(bb + kk * 32), idesc,
-                          (fresh[acc] && kk == 0) ? 0u : 1u);
+                          (fresh && kk == 0) ? 0u : 1u);
             }
-            fresh[acc] = false;
         }
     }
 }
@@ -127,14 +131,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
     uint64_t* bars = (uint64_t*)(smem + kOzXBytes + kOzYBytes);
     uint64_t* full = bars;         // [2]: X, Y tiles landed
     uint64_t* empty = bars + 2;    // [2]: X, Y tiles consumed by the MMAs
-    uint64_t* tfull = bars + 4;    // accumulators ready (one per half step)
+    uint64_t* tfull = bars + 4;    // accumulators ready (one per promotion block)
     uint64_t* tempty = bars + 5;   // accumulators drained (8 promotion warps)
     uint64_t* done = bars + 6;
     uint32_t* tmem_slot = (uint32_t*)(bars + 7);
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * kOzN;
-    const int H = 2 * p.num_kb;  // half steps
+    const int H = 2 * p.num_kb;                      // half steps
+    const int NB = (H + kOzPromo - 1) / kOzPromo;    // promotion blocks
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
     const uint32_t tmem = *tmem_slot;
 
     float hi[32], lo[32];
-    double acc[32];  // the pairs are flushed here every kOzFlush half steps
+    double acc[32];  // the pairs are flushed here every kOzFlush promotions
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
         hi[j] = lo[j] = 0.0f;
@@ -174,14 +179,16 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
             }
             if (*(volatile int*)&s_abort) break;
             uint8_t* buf = t == 0 ? bufX : bufY;
-            const int nb = t == 0 ? 6 : 4;
-            mbar_expect_tx(&full[t], 3 * kOzATile + nb * kOzBTile);
+            const int na = t == 0 ? kOzXA : kOzS - kOzXA;  // digits of X
+            const int s0 = t == 0 ? 0 : kOzXA;
+            const int nb = t == 0 ? kOzS : kOzYB;           // digits of Y
+            mbar_expect_tx(&full[t], na * kOzATile + nb * kOzBTile);
             const int x = kb * BK;
-#pragma unroll
-            for (int si = 0; si < 3; ++si)
-                tma_load_2d(buf + si * kOzATile, &maps.x[3 * t + si], &full[t], x, (int)m0);
+            for (int si = 0; si < na; ++si)
+                tma_load_2d(buf + si * kOzATile, &maps.x[s0 + si], &full[t], x, (int)m0);
             for (int u = 0; u < nb; ++u)
-                tma_load_2d(buf + 3 * kOzATile + u * kOzBTile, &maps.y[u], &full[t], x, (int)n0);
+                tma_load_2d(buf + na * kOzATile + u * kOzBTile, &maps.y[u], &full[t], x,
+                            (int)n0);
             ++issued;
         }
         // our own copies in flight: the last two (bounded wait)
@@ -190,9 +197,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
     } else if (warp == 1 && lane == 0) {
         int h = 0;
         for (; h < H; ++h) {
-            const int t = h & 1;
+            const int t = h & 1, blk = h / kOzPromo;
+            const bool start = h % kOzPromo == 0;
             if (!mbar_wait(&full[t], (h >> 1) & 1) ||
-                (h >= 1 && !mbar_wait(tempty, (h - 1) & 1))) {
+                (start && blk >= 1 && !mbar_wait(tempty, (blk - 1) & 1))) {
                 s_abort = 1;
                 break;
             }
@@ -200,33 +208,32 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
             tc_fence_after();
             const uint32_t a = smem_u32(t == 0 ? bufX : bufY);
             if (t == 0)
-                oz_half<1>(tmem, a, a + 3 * kOzATile);
+                oz_half<1, kOzXA>(tmem, a, a + kOzXA * kOzATile, start);
             else
-                oz_half<4>(tmem, a, a + 3 * kOzATile);
+                oz_half<kOzXA + 1, kOzS>(tmem, a, a + (kOzS - kOzXA) * kOzATile, false);
             umma_commit(&empty[t]);
-            umma_commit(tfull);
+            if (h % kOzPromo == kOzPromo - 1 || h == H - 1) umma_commit(tfull);
         }
         if (h > 0) umma_commit(done);
     } else if (warp >= 2) {
         const int q = warp & 3, half = (warp - 2) >> 2;
         const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * half);
-        for (int h = 0; h < H; ++h) {
-            if (!mbar_wait(tfull, h & 1)) {
+        for (int blk = 0; blk < NB; ++blk) {
+            if (!mbar_wait(tfull, blk & 1)) {
                 s_abort = 1;
                 break;
             }
             tc_fence_after();
-            const int t = h & 1;
-            // accumulators σ = 2..8 (X half) or 5..8 (Y half)
-            for (int sg = t == 0 ? 2 : 5; sg <= kOzSig; ++sg) {
-                const float scale = __int_as_float((127 - 8 * sg) << 23);  // 2^{−8σ}
+            // accumulators σ = 2..8 (every order occurs in each block)
+            for (int sg = 2; sg <= kOzSig; ++sg) {
+                const float scale = __int_as_float((127 - kOzBits * sg) << 23);  // 2^{−7σ}
                 float v[32];
                 tmem_ld16(tb + (uint32_t)((sg - 2) * kOzN), v);
                 tmem_ld16(tb + (uint32_t)((sg - 2) * kOzN + 16), v + 16);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) df_add(hi[j], lo[j], v[j] * scale);
             }
-            if ((h + 1) % kOzFlush == 0) {
+            if ((blk + 1) % kOzFlush == 0) {
                 // FP64 flush: the pair's own rounding stays that of a few
                 // K blocks (a handful of FP64 adds per K block, off the MMA
                 // path)
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
                     hi[j] = lo[j] = 0.0f;
                 }
             } else {
-                // renormalise the pairs once per half step
+                // renormalise the pairs once per promotion
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const float s = hi[j] + lo[j];
@@ -288,9 +295,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_atb(const __grid_constant_
 }
 
 // Column exponents and digits: one block per column of X (d rows, stride
-// ld): e = the exponent with max |x| < 2^e (0 for a zero column), then the six
-// truncated 8-bit digits of x·2^{−e}, written K-major [col][ldk] per digit
-// (zero beyond d).
+// ld): e = the exponent with max |x| < 2^e (0 for a zero column), then the
+// seven 7-bit digits of x·2^{−e}, each rounded to nearest (the remainder
+// stays in [−1/2, 1/2]), written K-major [col][ldk] per digit (zero beyond
+// d).
 template <typename T>
 __global__ void __launch_bounds__(256) k_oz_split(const T* __restrict__ X, int64_t ld, int64_t d,
                                                   int64_t ldk, int* __restrict__ ex,
@@ -311,14 +319,14 @@ __global__ void __launch_bounds__(256) k_oz_split(const T* __restrict__ X, int64
     int e = 0;
     if (mx > T(0)) (void)frexp(mx, &e);  // mx = m·2^e, m in [0.5, 1)
     if (threadIdx.x == 0) ex[col] = e;
-    // digits in the input's own precision: every step is exact (|v| < 1
-    // times 256, truncation, subtraction of the integer part)
+    // digits in the input's own precision: every step is exact (|v| ≤ 1
+    // times 128, rounding to an integer, subtraction of that integer)
     for (int64_t t = threadIdx.x; t < ldk; t += blockDim.x) {
         T v = t < d ? ldexp(x[t], -e) : T(0);
 #pragma unroll
         for (int s = 0; s < kOzS; ++s) {
-            v *= T(256);
-            const T dv = trunc(v);
+            v *= T(1 << kOzBits);
+            const T dv = rint(v);
             v -= dv;
             dig[(int64_t)s * dstride + col * ldk + t] = __float2bfloat16_rn((float)dv);
         }
@@ -345,7 +353,7 @@ bool oz_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t K, int64_t rows, 
 
 size_t oz_work_bytes(int64_t d, int64_t m, int64_t n) {
     const int64_t ldk = round_up(d, tc::BK);
-    return (size_t)(6 * (m + n) * ldk * 2) + (size_t)round_up((m + n) * 4, 256) + 1024;
+    return (size_t)(tc::kOzS * (m + n) * ldk * 2) + (size_t)round_up((m + n) * 4, 256) + 1024;
 }
 
 cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ldx,
@@ -368,9 +376,9 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
     }
     const int64_t ldk = round_up(d, BK);
     uint8_t* w = (uint8_t*)(((uintptr_t)work + 255) & ~(uintptr_t)255);
-    __nv_bfloat16* dx = (__nv_bfloat16*)w;                 // 6 × [m][ldk]
-    __nv_bfloat16* dy = dx + 6 * m * ldk;                  // 6 × [n][ldk]
-    int* ex = (int*)(dy + 6 * n * ldk);
+    __nv_bfloat16* dx = (__nv_bfloat16*)w;                 // kOzS × [m][ldk]
+    __nv_bfloat16* dy = dx + kOzS * m * ldk;               // kOzS × [n][ldk]
+    int* ex = (int*)(dy + kOzS * n * ldk);
     int* ey = ex + m;
     if (xtype == ALN_DTYPE_F32)
         k_oz_split<float><<<(unsigned)m, 256, 0, st>>>((const float*)X, ldx, d, ldk, ex, dx,
@@ -387,7 +395,7 @@ cudaError_t launch_oz_product(int mode, int32_t xtype, const void* X, int64_t ld
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     OzMaps maps;
-    for (int s = 0; s < 6; ++s)
+    for (int s = 0; s < kOzS; ++s)
         if (!oz_map(&maps.x[s], dx + s * m * ldk, ldk, m, ldk, BM) ||
             !oz_map(&maps.y[s], dy + s * n * ldk, ldk, n, ldk, kOzN))
             return cudaErrorInvalidValue;

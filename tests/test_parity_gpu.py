@@ -397,8 +397,8 @@ def test_batched_prepare_matches_oracle(aln):
 @pytest.mark.parametrize("signed,d,n,k", [(False, 997, 130, 70), (True, 997, 130, 70),
                                           (True, 700, 60, 300)])
 def test_batched_q_from_digit_products(aln, signed, d, n, k):
-    """q = −D⁻¹Aᵀb of the batched prepare (exact 8-bit digit products on the
-    tensor cores, 48 bits per value, pairs of order ≤ 8) against FP64, entry
+    """q = −D⁻¹Aᵀb of the batched prepare (exact 7-bit digit products on the
+    tensor cores, 49 bits per value, pairs of order ≤ 8) against FP64, entry
     by entry, relative to Σ_t |a_ti b_t| / s_i (the natural scale of a
     compensated product): columns six decades apart, a zero column, mixed
     signs, d, n and k ragged against the 64 × 128 × 64 tiles; n = 60 < 128
