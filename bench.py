@@ -713,7 +713,7 @@ def run_ours(args):
                        None if k != 1 or last.iterations == 0 else
                        dict(zip(("step", "product", "barrier", "gather_mask", "unused")
                                 if alg == aln.ALG_ANTI_ACC else
-                                ("product", "barrier", "update", "clipped", "mask"),
+                                ("product", "barrier", "update", "clipped", "unused"),
                                 [round(sum(s.phase_us[i] for s in stats) /
                                        max(1, sum(s.iterations for s in stats)), 3)
                                  for i in range(5)]))),

@@ -422,8 +422,10 @@ typedef struct aln_stats {
     int32_t persist_blocks;  /* grid of the persistent kernel */
     int32_t clipped_iterations; /* iterations that needed the clipped correction Qe */
     double phase_us[5];      /* block 0's time in the persistent kernel, per phase:
-                                product Qḡ, grid barrier, update, clipped
-                                correction, mask (replicated-state kernel);
+                                product Qḡ, grid barrier, update (with the
+                                gather of Qḡ and the new mask), clipped
+                                correction (with its mask), 0 (replicated-state
+                                kernel);
                                 batched solver: [0] the batched chunks, [1] the
                                 per-column tail, summed over rounds */
     double product_bytes;    /* algorithmic bytes of Q the Alg. 2 products of the

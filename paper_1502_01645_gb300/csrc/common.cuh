@@ -49,6 +49,16 @@ __device__ __forceinline__ float vget(const float4& v, int i) {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 __device__ __forceinline__ double vget(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4& v, int i, float x) {
+    if (i == 0) v.x = x;
+    else if (i == 1) v.y = x;
+    else if (i == 2) v.z = x;
+    else v.w = x;
+}
+__device__ __forceinline__ void vset(double2& v, int i, double x) {
+    if (i == 0) v.x = x;
+    else v.y = x;
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -506,12 +506,13 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 template <typename T>
 __device__ __forceinline__ double block_sum_td(T v, double* sc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T* sv = reinterpret_cast<T*>(sc);  // the warp partials in T, widened by warp 0
     v = warp_sum_t(v);
     __syncthreads();
-    if (lane == 0) sc[wid] = (double)v;
+    if (lane == 0) sv[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        double x = lane < (int)(blockDim.x >> 5) ? sc[lane] : 0.0;
+        double x = lane < (int)(blockDim.x >> 5) ? (double)sv[lane] : 0.0;
         x = warp_sum(x);
         if (lane == 0) sc[32] = x;
     }
@@ -521,31 +522,35 @@ __device__ __forceinline__ double block_sum_td(T v, double* sc) {
 
 // One block reduction for the update step: the FP32 value v (partials in T
 // within warps, the 32 warp partials added in FP64 by warp 0, the same tree
-// as block_sum_td) and two counts.  sd holds 33 doubles, si 66 ints.
+// as block_sum_td) and two counts.  The counts travel packed in one int
+// (a + 2^16·b: both stay below 2^15 here, since the replicated-state kernels
+// hold n < 2^14 entries).  The warp partials of v are stored in T and
+// widened by warp 0 alone (exact, and one FP64 instruction instead of one per
+// warp on the narrow FP64 pipe).  With v_if_b_zero, the FP64 sum is formed
+// only when the total b is 0 (*v_out is 0 otherwise).  sd holds 33 doubles,
+// si 66 ints.
 template <typename T>
 __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* si, double* v_out,
-                                           int* a_out, int* b_out) {
+                                           int* a_out, int* b_out, bool v_if_b_zero = false) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T* sv = reinterpret_cast<T*>(sd);  // the warp partials, in T
     v = warp_sum_t(v);
-    a = warp_sum_i(a);
-    b = warp_sum_i(b);
+    int ab = warp_sum_i(a + (b << 16));
     __syncthreads();  // earlier readers of sd / si are done
     if (lane == 0) {
-        sd[wid] = (double)v;
-        si[wid] = a;
-        si[32 + wid] = b;
+        sv[wid] = v;
+        si[wid] = ab;
     }
     __syncthreads();
     if (wid == 0) {
         const int nw = (int)(blockDim.x >> 5);
-        double x = lane < nw ? sd[lane] : 0.0;
-        int xa = lane < nw ? si[lane] : 0, xb = lane < nw ? si[32 + lane] : 0;
-        x = warp_sum(x);
-        xa = warp_sum_i(xa);
-        xb = warp_sum_i(xb);
+        ab = warp_sum_i(lane < nw ? si[lane] : 0);
+        const int xb = ab >> 16;
+        double x = 0.0;
+        if (!v_if_b_zero || xb == 0) x = warp_sum(lane < nw ? (double)sv[lane] : 0.0);
         if (lane == 0) {
             sd[32] = x;
-            si[64] = xa;
+            si[64] = ab & 0xffff;
             si[65] = xb;
         }
     }
@@ -553,6 +558,36 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
     *v_out = sd[32];
     *a_out = si[64];
     *b_out = si[65];
+}
+
+// Σ v over the first TILE threads (the rest hold 0), in FP64 by thread 0 —
+// the same tree as block_sum_td over these warps (the xor shuffle tree of
+// the warp partials, with the zero partials of the other warps left out);
+// the result is valid in thread 0 only.  sc holds 33 doubles.
+template <typename T, int TILE>
+__device__ __forceinline__ double tile_sum_td(T v, double* sc) {
+    constexpr int NW = TILE / 32;
+    static_assert(NW >= 1 && (NW & (NW - 1)) == 0, "TILE: a power-of-two number of warps");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T* sv = reinterpret_cast<T*>(sc);
+    __syncthreads();  // earlier readers of sc are done
+    if (wid < NW) {
+        v = warp_sum_t(v);
+        if (lane == 0) sv[wid] = v;
+    }
+    __syncthreads();
+    double x = 0.0;
+    if (threadIdx.x == 0) {
+        double p[NW];
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) p[w2] = (double)sv[w2];
+#pragma unroll
+        for (int o = NW / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int i = 0; i < o; ++i) p[i] = p[i] + p[i + o];
+        x = p[0];
+    }
+    return x;
 }
 
 // Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
@@ -658,20 +693,146 @@ __device__ __forceinline__ void clipped_list(int n, const T* e, int* list, int* 
     __syncthreads();
 }
 
-// g[i] += Σ_k e[list[k]] · Q[list[k]][i] for all i < n (rows in list order);
-// with tmask, the tiles of Q known to be zero are not read (FP32 only).
+// One vector (entries j = v·VN + c, 16 bytes) of the update of (c):
+// y⁺ = [y − αḡ]₊ (a float pair in FP32: TwoSum, then renormalise), e = the
+// clipped part (e_j = y⁺_j − (y_j − αḡ_j) where y_j − αḡ_j < 0), g ← g − αw,
+// and the mask of the new point as if nothing was clipped (ḡ, and the
+// partials of ‖ḡ‖², |P| and the clipped count).  Entries j ≥ n stay zero.
 template <typename T>
-__device__ __forceinline__ void add_rows(const T* __restrict__ Q, int64_t ldq, int n,
-                                         const int* list, int count, const T* e, T* g,
-                                         const uint32_t* __restrict__ tmask = nullptr,
-                                         int tw = 0) {
+__device__ __forceinline__ void update_vec(int v, int n, T aT, const T (&w)[Vec16<T>::N], T* sy,
+                                           T* syl, T* sg, T* sgb, T* se, T& v2, int& cP,
+                                           int& clipped) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
-    for (int i = threadIdx.x * VN; i < n; i += blockDim.x * VN) {
+    constexpr bool DF = sizeof(T) == 4;
+    V* py = reinterpret_cast<V*>(sy) + v;
+    V* pyl = reinterpret_cast<V*>(syl) + v;
+    V* pg = reinterpret_cast<V*>(sg) + v;
+    V* pgb = reinterpret_cast<V*>(sgb) + v;
+    const V y4 = *py, g4 = *pg, gb4 = *pgb;
+    V yl4 = {};
+    if (DF) yl4 = *pyl;
+    V yo, ylo, go, gbo, eo;
+#pragma unroll
+    for (int c = 0; c < VN; ++c) {
+        const bool in = v * VN + c < n;
+        const T yi = vget(y4, c);
+        T yn, nl = T(0), ej = T(0);
+        if (DF) {
+            const T step = __fmul_rn((float)aT, (float)vget(gb4, c));
+            const T s1 = yi - step;
+            const T bb = s1 - yi;
+            const T er = (yi - (s1 - bb)) + (-step - bb);
+            const T t = vget(yl4, c) + er;
+            yn = s1 + t;
+            nl = t - (yn - s1);
+            if (yn < T(0)) {  // clipped: y⁺ = 0, e = y⁺ − (y − αḡ)
+                ej = -(yn + nl);
+                yn = T(0);
+                nl = T(0);
+                clipped += in ? 1 : 0;
+            }
+        } else {
+            const T step = aT * vget(gb4, c);
+            yn = yi - step;
+            if (yn < T(0)) {
+                ej = step - yi;
+                yn = T(0);
+                clipped += in ? 1 : 0;
+            }
+        }
+        const T gn = vget(g4, c) - aT * w[c];
+        const bool P = in && (yn > T(0) || gn < T(0));
+        const T gb = P ? gn : T(0);
+        v2 = fma(gb, gb, v2);
+        cP += P ? 1 : 0;
+        vset(yo, c, in ? yn : T(0));
+        vset(ylo, c, in ? nl : T(0));
+        vset(go, c, in ? gn : T(0));
+        vset(gbo, c, gb);
+        vset(eo, c, in ? ej : T(0));
+    }
+    *py = yo;
+    if (DF) *pyl = ylo;
+    *pg = go;
+    *pgb = gbo;
+    reinterpret_cast<V*>(se)[v] = eo;
+}
+
+// g ← g + acc for one vector, then its mask (ḡ, and the partials of ‖ḡ‖²
+// and |P|).  Entries j ≥ n stay zero.
+template <typename T>
+__device__ __forceinline__ void add_mask_vec(int v, int n, const T (&acc)[Vec16<T>::N],
+                                             const T* sy, T* sg, T* sgb, T& v2, int& cP) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    V* pg = reinterpret_cast<V*>(sg) + v;
+    const V y4 = reinterpret_cast<const V*>(sy)[v], g4 = *pg;
+    V go, gbo;
+#pragma unroll
+    for (int c = 0; c < VN; ++c) {
+        const bool in = v * VN + c < n;
+        const T gi = vget(g4, c) + acc[c];
+        const bool P = in && (vget(y4, c) > T(0) || gi < T(0));
+        const T gb = P ? gi : T(0);
+        v2 = fma(gb, gb, v2);
+        cP += P ? 1 : 0;
+        vset(go, c, in ? gi : T(0));
+        vset(gbo, c, gb);
+    }
+    *pg = go;
+    reinterpret_cast<V*>(sgb)[v] = gbo;
+}
+
+// The clipped correction from the grid's partials, in the same pass as the
+// mask: g ← g + Σ_r part[r] (r in order), ḡ, and the partials of ‖ḡ‖², |P|.
+// Two vectors per thread per pass keep 2R loads in flight.
+template <typename T>
+__device__ __forceinline__ void add_partials_mask(const T* __restrict__ part, int R, int64_t ldq,
+                                                  int n, const T* sy, T* sg, T* sgb, T& v2,
+                                                  int& cP) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    const int nv = (n + VN - 1) / VN, nt = (int)blockDim.x;
+    for (int v0 = threadIdx.x; v0 < nv; v0 += 2 * nt) {
+        const int v1 = v0 + nt;
+        T a0[VN], a1[VN];
+#pragma unroll
+        for (int c = 0; c < VN; ++c) a0[c] = a1[c] = T(0);
+#pragma unroll 2
+        for (int r = 0; r < R; ++r) {
+            const V* row = reinterpret_cast<const V*>(part + (int64_t)r * ldq);
+            const V x0 = __ldcg(row + v0);
+            const V x1 = v1 < nv ? __ldcg(row + v1) : V{};
+#pragma unroll
+            for (int c = 0; c < VN; ++c) {
+                a0[c] += vget(x0, c);
+                a1[c] += vget(x1, c);
+            }
+        }
+        add_mask_vec<T>(v0, n, a0, sy, sg, sgb, v2, cP);
+        if (v1 < nv) add_mask_vec<T>(v1, n, a1, sy, sg, sgb, v2, cP);
+    }
+}
+
+// The clipped correction from the few clipped rows of Q (list order), in
+// the same pass as the mask; with tmask, tiles of Q known to be zero are not
+// read (FP32 only).
+template <typename T>
+__device__ __forceinline__ void add_rows_mask(const T* __restrict__ Q, int64_t ldq, int n,
+                                              const int* list, int count, const T* e,
+                                              const T* sy, T* sg, T* sgb,
+                                              const uint32_t* __restrict__ tmask, int tw, T& v2,
+                                              int& cP) {
+    using V = typename Vec16<T>::type;
+    constexpr int VN = Vec16<T>::N;
+    const int nv = (n + VN - 1) / VN;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const int64_t i = (int64_t)v * VN;
         T acc[VN];
 #pragma unroll
         for (int c = 0; c < VN; ++c) acc[c] = T(0);
-        const uint32_t* tm = tmask ? tmask + (int64_t)(i >> 7) * tw : nullptr;
+        const uint32_t* tm = tmask ? tmask + (i >> 7) * tw : nullptr;
 #pragma unroll
         for (int k = 0; k < kLocalClip; ++k) {
             if (k < count && (!tm || tile_nz(tm, list[k]))) {
@@ -682,9 +843,7 @@ __device__ __forceinline__ void add_rows(const T* __restrict__ Q, int64_t ldq, i
                 for (int c = 0; c < VN; ++c) acc[c] = fma(ej, vget(q, c), acc[c]);
             }
         }
-#pragma unroll
-        for (int c = 0; c < VN; ++c)
-            if (i + c < n) g[i + c] += acc[c];
+        add_mask_vec<T>(v, n, acc, sy, sg, sgb, v2, cP);
     }
 }
 
@@ -702,7 +861,6 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     // near the optimum are far below ulp(y)); FP64 needs no low part.
     constexpr bool DF = sizeof(T) == 4;
     T* syl = red + kPWarps * TILE;
-    __shared__ double sd[32];
     __shared__ int si[32];
     __shared__ double s_t[33];
     __shared__ int s_i3[66];
@@ -714,10 +872,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     const int n = a.n;
     unsigned int bar = 0;
 
+    // entries n..ldq stay zero throughout (the vector passes read them)
     for (int j = threadIdx.x; j < a.ldq; j += blockDim.x) {
         sy[j] = j < n ? __ldcg(a.y + j) : T(0);
         if (DF) syl[j] = j < n ? __ldcg(a.ylo + j) : T(0);
         sg[j] = j < n ? __ldcg(a.g + j) : T(0);
+        sgb[j] = T(0);
         sw[j] = T(0);
     }
     __syncthreads();
@@ -730,13 +890,25 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     IterState* st = a.st;
     const double eps = st->eps;
     const int max_iter = st->max_iter, window = st->window;
-    double best = 1.0 / 0.0;
-    int best_iter = 0, iter = 0, status = ALN_RHS_MAXITER;
-    long long sum_passive = 0, sum_clip = 0;
-    uint64_t prof[5] = {0, 0, 0, 0, 0};  // block 0's phase times (ns)
-    int nclip_iters = 0;
+    // thread 0's bookkeeping lives in shared memory, not in registers of
+    // every thread (the kernel runs at the 64-register limit of 1024 threads)
+    __shared__ double s_best;
+    __shared__ int s_best_iter, s_nclip_iters;
+    __shared__ long long s_sum_passive, s_sum_clip;
+    __shared__ uint64_t s_prof[5], s_tprev;  // block 0's phase times (ns)
+    if (threadIdx.x == 0) {
+        s_best = 1.0 / 0.0;
+        s_best_iter = s_nclip_iters = 0;
+        s_sum_passive = s_sum_clip = 0;
+        for (int k = 0; k < 5; ++k) s_prof[k] = 0;
+    }
+    int iter = 0, status = ALN_RHS_MAXITER;
     bool ok = true;
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    constexpr int VN = Vec16<T>::N;
+    const int nv = (n + VN - 1) / VN;             // 16-byte vectors of the state
+    const int tid = (int)threadIdx.x - 32;        // gather / update threads: warps 1..
+    const int nt = (int)blockDim.x - 32;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -745,11 +917,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
             else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
-            else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
+            else if (iter - s_best_iter > window) status = ALN_RHS_STAGNATED;
             else stop = 0;
-            if (!stop && gam < best) {
-                best = gam;
-                best_iter = iter;
+            if (!stop && gam < s_best) {
+                s_best = gam;
+                s_best_iter = iter;
             }
             s_flag = stop;
         }
@@ -758,12 +930,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         const int par = iter & 1;
         T* part = a.part + (int64_t)par * a.R * a.ldq;
         double* kitem = a.kitem + (int64_t)par * items;
-        uint64_t t_prev = timer ? p_globaltimer() : 0;
+        if (timer) s_tprev = p_globaltimer();
         auto lap = [&](int k) {
             if (timer) {
                 const uint64_t t = p_globaltimer();
-                prof[k] += t - t_prev;
-                t_prev = t;
+                s_prof[k] += t - s_tprev;
+                s_tprev = t;
             }
         };
 
@@ -774,15 +946,21 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                                         nullptr, nullptr, a.tmask, a.tw);
             const int64_t i = (int64_t)ct * TILE + threadIdx.x;
             const T prod = (threadIdx.x < TILE && i < n) ? sgb[i] * pw : T(0);
-            const double k = block_sum_td<T>(prod, s_t);
+            const double k = tile_sum_td<T, TILE>(prod, s_t);
             if (threadIdx.x == 0) __stcg(kitem + it, k);
         }
         lap(0);
         if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
         lap(1);
 
-        // every block: κ (warp 0) while the other warps gather w, α,
-        // projected update, gradient update
+        // every block: κ (warp 0) while warps 1.. gather their vectors of
+        // w = Σ_r partials (r in order) into registers — two per thread,
+        // any further ones through sw — then α, the projected update, the
+        // gradient update and the new mask, vector by vector
+        T w0[VN], w1[VN];
+#pragma unroll
+        for (int c = 0; c < VN; ++c) w0[c] = w1[c] = T(0);
+        const int v0 = tid, v1 = tid + nt;
         if (threadIdx.x < 32) {
             // four independent accumulators per lane, then a pairwise and
             // a shuffle tree: the FP64 adds form a short dependent chain
@@ -803,89 +981,91 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 s_alpha = stop ? T(0) : step_quotient<T>(gam, k2);
                 s_flag = stop;
             }
+        } else {
+            using V = typename Vec16<T>::type;
+            if (v0 < nv) {
+#pragma unroll 2
+                for (int r = 0; r < a.R; ++r) {
+                    const V* row = reinterpret_cast<const V*>(part + (int64_t)r * a.ldq);
+                    const V x0 = __ldcg(row + v0);
+                    const V x1 = v1 < nv ? __ldcg(row + v1) : V{};
+#pragma unroll
+                    for (int c = 0; c < VN; ++c) {
+                        w0[c] += vget(x0, c);
+                        w1[c] += vget(x1, c);
+                    }
+                }
+            }
+            for (int v = tid + 2 * nt; v < nv; v += nt) {
+                T acc[VN];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) acc[c] = T(0);
+                for (int r = 0; r < a.R; ++r) {
+                    const V x = __ldcg(reinterpret_cast<const V*>(part + (int64_t)r * a.ldq) + v);
+#pragma unroll
+                    for (int c = 0; c < VN; ++c) acc[c] += vget(x, c);
+                }
+                V o;
+#pragma unroll
+                for (int c = 0; c < VN; ++c) vset(o, c, acc[c]);
+                reinterpret_cast<V*>(sw)[v] = o;
+            }
         }
-        sum_partials(part, a.R, a.ldq, n, sw, false, 32);
         __syncthreads();
         if (s_flag) break;
         const T aT = s_alpha;
-        sum_passive += cnt;
+        if (threadIdx.x == 0) s_sum_passive += cnt;
         // The mask of the new point is formed in the same pass; it is final
-        // when nothing was clipped (then g needs no correction).
+        // when nothing was clipped (then g needs no correction).  sw takes e.
         int clipped = 0, cP = 0;
         T v2 = T(0);
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const T yi = sy[j];
-            T yn, ej = T(0);
-            if (DF) {
-                // (sy, syl) − αḡ exactly: TwoSum, then renormalise
-                const T step = __fmul_rn((float)aT, (float)sgb[j]);
-                const T s1 = yi - step;
-                const T bb = s1 - yi;
-                const T er = (yi - (s1 - bb)) + (-step - bb);
-                const T t = syl[j] + er;
-                yn = s1 + t;
-                T nl = t - (yn - s1);
-                if (yn < T(0)) {  // clipped: y⁺ = 0, e = y⁺ − (y − αḡ)
-                    ej = -(yn + nl);
-                    yn = T(0);
-                    nl = T(0);
-                    ++clipped;
-                }
-                syl[j] = nl;
-            } else {
-                const T step = aT * sgb[j];
-                yn = yi - step;
-                if (yn < T(0)) {
-                    ej = step - yi;
-                    yn = T(0);
-                    ++clipped;
-                }
+        if (tid >= 0) {
+            if (v0 < nv) update_vec<T>(v0, n, aT, w0, sy, syl, sg, sgb, sw, v2, cP, clipped);
+            if (v1 < nv) update_vec<T>(v1, n, aT, w1, sy, syl, sg, sgb, sw, v2, cP, clipped);
+            for (int v = tid + 2 * nt; v < nv; v += nt) {
+                T wv[VN];
+#pragma unroll
+                for (int c = 0; c < VN; ++c) wv[c] = sw[(int64_t)v * VN + c];
+                update_vec<T>(v, n, aT, wv, sy, syl, sg, sgb, sw, v2, cP, clipped);
             }
-            const T gn = sg[j] - aT * sw[j];
-            sy[j] = yn;
-            sg[j] = gn;
-            sw[j] = ej;  // w is consumed; the buffer now holds e
-            const bool P = yn > T(0) || gn < T(0);
-            const T gb = P ? gn : T(0);
-            sgb[j] = gb;
-            v2 = fma(gb, gb, v2);
-            cP += P ? 1 : 0;
         }
         double gam2;
         int cnt2, nclip;
-        block_sum3<T>(v2, cP, clipped, s_t, s_i3, &gam2, &cnt2, &nclip);  // identical in every block
+        // identical in every block; ‖ḡ‖² is formed only when nothing was
+        // clipped (else the clipped correction's mask replaces it)
+        block_sum3<T>(v2, cP, clipped, s_t, s_i3, &gam2, &cnt2, &nclip, true);
         ++iter;
-        sum_clip += nclip;
+        if (threadIdx.x == 0) s_sum_clip += nclip;
         lap(2);
 
-        if (nclip > 0 && nclip <= kLocalClip) {
-            // Few clipped rows: every block forms Qe itself from those rows
-            // of Q (listed in index order, so all blocks add in the same
-            // order) — no product pass over the grid and no barrier.
-            clipped_list(n, sw, s_clip, si);
-            add_rows(a.Q, a.ldq, n, s_clip, nclip, sw, sg, a.tmask, a.tw);
-            __syncthreads();
-            ++nclip_iters;
-        } else if (nclip > 0) {
-            // Q e crosses blocks: partials, barrier, every block sums them
-            for (int it = blockIdx.x; it < items; it += G) {
-                const int ct = it % a.CT, rg = it / a.CT;
-                (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2, red,
-                                     nullptr, nullptr, a.tmask, a.tw);
-            }
-            if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
-            sum_partials(a.part2, a.R, a.ldq, n, sg, true);
-            __syncthreads();
-            ++nclip_iters;
-        }
-        lap(3);
         if (nclip > 0) {
-            mask_all(n, sy, sg, sgb, s_t, s_i3, &gam, &cnt);
+            // g ← g + Qe and the mask of the new point, in one pass
+            T v3 = T(0);
+            int cP3 = 0, unused;
+            if (nclip <= kLocalClip) {
+                // Few clipped rows: every block forms Qe itself from those
+                // rows of Q (listed in index order, so all blocks add in the
+                // same order) — no product pass over the grid and no barrier.
+                clipped_list(n, sw, s_clip, si);
+                add_rows_mask<T>(a.Q, a.ldq, n, s_clip, nclip, sw, sy, sg, sgb, a.tmask, a.tw,
+                                 v3, cP3);
+            } else {
+                // Q e crosses blocks: partials, barrier, every block sums them
+                for (int it = blockIdx.x; it < items; it += G) {
+                    const int ct = it % a.CT, rg = it / a.CT;
+                    (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sw, ct, rg, a.part2,
+                                         red, nullptr, nullptr, a.tmask, a.tw);
+                }
+                if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
+                add_partials_mask<T>(a.part2, a.R, a.ldq, n, sy, sg, sgb, v3, cP3);
+            }
+            block_sum3<T>(v3, cP3, 0, s_t, s_i3, &gam, &cnt, &unused);
+            if (threadIdx.x == 0) ++s_nclip_iters;
         } else {
             gam = gam2;
             cnt = cnt2;
         }
-        lap(4);
+        lap(3);
     }
 
     if (blockIdx.x == 0) {
@@ -900,12 +1080,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             st->status = ok ? status : kStatusTimeout;
             st->gbar2 = gam;
             st->npassive = cnt;
-            st->best_g2 = best;
-            st->best_iter = best_iter;
-            st->sum_passive = sum_passive;
-            st->sum_clip = sum_clip;
-            for (int k = 0; k < 5; ++k) st->phase_ns[k] = prof[k];
-            st->phase_ns[5] = (uint64_t)nclip_iters;  // iterations that took the clipped path
+            st->best_g2 = s_best;
+            st->best_iter = s_best_iter;
+            st->sum_passive = s_sum_passive;
+            st->sum_clip = s_sum_clip;
+            for (int k = 0; k < 5; ++k) st->phase_ns[k] = s_prof[k];
+            st->phase_ns[5] = (uint64_t)s_nclip_iters;  // iterations that took the clipped path
         }
     }
 }
