@@ -37,7 +37,8 @@ struct PersistSync {
 // release reduction on the block's counter; warp 0 then polls all counters
 // (relaxed loads, one per lane), and once their sum reaches `target` (this
 // barrier's completion count, tracked identically by every block) each
-// polling lane issues an acquire fence before the block continues.
+// polling lane re-reads its counter with an acquire load before the block
+// continues.
 __device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target,
                                              uint64_t wait_ns) {
     __shared__ int s_ok;
@@ -62,10 +63,20 @@ __device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target
             for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             v = __shfl_sync(0xffffffffu, v, 0);
             if ((int)(v - target) >= 0) {
-                if (lane < kSyncLanes) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+                // acquire: re-read each counter with an acquire load (it reads
+                // from the release sequence of every arrival added to it), a
+                // lighter order than a full fence; the block barrier below
+                // carries it to the other threads
+                if (lane < kSyncLanes) {
+                    unsigned int u;
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(u)
+                                 : "l"(&s->count[lane][0])
+                                 : "memory");
+                    (void)u;
+                }
                 break;
             }
-            __nanosleep(32);
+            __nanosleep(8);
             int stop = 0;
             if (lane == 0 && (++spins & 1023u) == 0) {
                 const uint64_t t = p_globaltimer();

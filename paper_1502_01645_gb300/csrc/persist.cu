@@ -698,10 +698,10 @@ __device__ __forceinline__ void clipped_list(int n, const T* e, int* list, int* 
 // clipped part (e_j = y⁺_j − (y_j − αḡ_j) where y_j − αḡ_j < 0), g ← g − αw,
 // and the mask of the new point as if nothing was clipped (ḡ, and the
 // partials of ‖ḡ‖², |P| and the clipped count).  Entries j ≥ n stay zero.
-template <typename T>
-__device__ __forceinline__ void update_vec(int v, int n, T aT, const T (&w)[Vec16<T>::N], T* sy,
-                                           T* syl, T* sg, T* sgb, T* se, T& v2, int& cP,
-                                           int& clipped) {
+template <typename T, bool TAIL>
+__device__ __forceinline__ void update_vec_(int v, int n, T aT, const T (&w)[Vec16<T>::N], T* sy,
+                                            T* syl, T* sg, T* sgb, T* se, T& v2, int& cP,
+                                            int& clipped) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr bool DF = sizeof(T) == 4;
@@ -715,7 +715,7 @@ __device__ __forceinline__ void update_vec(int v, int n, T aT, const T (&w)[Vec1
     V yo, ylo, go, gbo, eo;
 #pragma unroll
     for (int c = 0; c < VN; ++c) {
-        const bool in = v * VN + c < n;
+        const bool in = !TAIL || v * VN + c < n;
         const T yi = vget(y4, c);
         T yn, nl = T(0), ej = T(0);
         if (DF) {
@@ -758,12 +758,22 @@ __device__ __forceinline__ void update_vec(int v, int n, T aT, const T (&w)[Vec1
     *pgb = gbo;
     reinterpret_cast<V*>(se)[v] = eo;
 }
+// The vectors wholly below n skip the per-entry bounds selects.
+template <typename T>
+__device__ __forceinline__ void update_vec(int v, int n, T aT, const T (&w)[Vec16<T>::N], T* sy,
+                                           T* syl, T* sg, T* sgb, T* se, T& v2, int& cP,
+                                           int& clipped) {
+    if ((v + 1) * Vec16<T>::N <= n)
+        update_vec_<T, false>(v, n, aT, w, sy, syl, sg, sgb, se, v2, cP, clipped);
+    else
+        update_vec_<T, true>(v, n, aT, w, sy, syl, sg, sgb, se, v2, cP, clipped);
+}
 
 // g ← g + acc for one vector, then its mask (ḡ, and the partials of ‖ḡ‖²
 // and |P|).  Entries j ≥ n stay zero.
-template <typename T>
-__device__ __forceinline__ void add_mask_vec(int v, int n, const T (&acc)[Vec16<T>::N],
-                                             const T* sy, T* sg, T* sgb, T& v2, int& cP) {
+template <typename T, bool TAIL>
+__device__ __forceinline__ void add_mask_vec_(int v, int n, const T (&acc)[Vec16<T>::N],
+                                              const T* sy, T* sg, T* sgb, T& v2, int& cP) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     V* pg = reinterpret_cast<V*>(sg) + v;
@@ -771,7 +781,7 @@ __device__ __forceinline__ void add_mask_vec(int v, int n, const T (&acc)[Vec16<
     V go, gbo;
 #pragma unroll
     for (int c = 0; c < VN; ++c) {
-        const bool in = v * VN + c < n;
+        const bool in = !TAIL || v * VN + c < n;
         const T gi = vget(g4, c) + acc[c];
         const bool P = in && (vget(y4, c) > T(0) || gi < T(0));
         const T gb = P ? gi : T(0);
@@ -782,6 +792,14 @@ __device__ __forceinline__ void add_mask_vec(int v, int n, const T (&acc)[Vec16<
     }
     *pg = go;
     reinterpret_cast<V*>(sgb)[v] = gbo;
+}
+template <typename T>
+__device__ __forceinline__ void add_mask_vec(int v, int n, const T (&acc)[Vec16<T>::N],
+                                             const T* sy, T* sg, T* sgb, T& v2, int& cP) {
+    if ((v + 1) * Vec16<T>::N <= n)
+        add_mask_vec_<T, false>(v, n, acc, sy, sg, sgb, v2, cP);
+    else
+        add_mask_vec_<T, true>(v, n, acc, sy, sg, sgb, v2, cP);
 }
 
 // The clipped correction from the grid's partials, in the same pass as the
