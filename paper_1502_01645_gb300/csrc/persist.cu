@@ -400,6 +400,14 @@ struct ReplArgs {
     unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
+// Warp sum in the iteration type (xor tree: every lane gets the sum).
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Is the 128×128 tile of Q holding row j, column tile ct possibly non-zero?
 __device__ __forceinline__ bool tile_nz(const uint32_t* __restrict__ tm_ct, int j) {
     const int rt = j >> 7;
@@ -410,6 +418,12 @@ __device__ __forceinline__ bool tile_nz(const uint32_t* __restrict__ tm_ct, int 
 // written to dst[rg][tile]; returns the partial in threads < TILE.  With
 // tmask, rows whose tile of Q in column tile ct is zero are skipped (their
 // terms are exact zeros), FP32 tiles of 128 columns only.
+//
+// With ksc (a 33-double scratch), the item's curvature share
+// κ_item = Σ_{i ∈ tile} v_i·partial_i is formed in the same block-barrier
+// steps: warp sums over the TILE threads, then thread 0 adds the warp sums in
+// FP64 (the xor tree of those sums, the zero ones of other warps left out)
+// into *kappa (thread 0 only).
 template <typename T, bool DIFF = false>
 __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, int n,
                                          int rows_per_group, const T* v, int ct, int rg,
@@ -417,7 +431,8 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
                                          const double* __restrict__ add = nullptr,
                                          const T* vsub = nullptr,
                                          const uint32_t* __restrict__ tmask = nullptr,
-                                         int tw = 0) {
+                                         int tw = 0, double* ksc = nullptr,
+                                         double* kappa = nullptr) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
@@ -463,6 +478,8 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
     for (int c = 0; c < VN; ++c) red[warp * TILE + lane * VN + c] = acc[c];
     __syncthreads();
     T s = T(0);
+    constexpr int NW = TILE / 32;
+    T* sv = reinterpret_cast<T*>(ksc);
     if (threadIdx.x < TILE) {
 #pragma unroll 8
         for (int w2 = 0; w2 < kPWarps; ++w2) s += red[w2 * TILE + threadIdx.x];
@@ -470,8 +487,22 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
         const int64_t i = (int64_t)ct * TILE + threadIdx.x;
         if (add && rg == 0 && i < n) s += (T)add[i];
         __stcg(dst + (int64_t)rg * ldq + i, s);
+        if (ksc) {
+            const T pk = warp_sum_t(i < n ? v[i] * s : T(0));
+            if (lane == 0) sv[warp] = pk;
+        }
     }
     __syncthreads();
+    if (ksc && threadIdx.x == 0) {
+        double pw[NW];
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) pw[w2] = (double)sv[w2];
+#pragma unroll
+        for (int o = NW / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int i2 = 0; i2 < o; ++i2) pw[i2] = pw[i2] + pw[i2 + o];
+        *kappa = pw[0];
+    }
     return s;
 }
 
@@ -488,21 +519,16 @@ __device__ __forceinline__ double block_sum_bcast(double v, double* sc) {
     return s;
 }
 
-// GB300's FP64 pipe is narrow: an FP64 instruction issued by all 1024
-// threads of a block costs microseconds.  The per-iteration reductions
-// therefore run in the iteration type T across lanes and warps, and only the
-// final sum over the warp partials (and any division) is done in FP64, by one
-// thread, then broadcast through shared memory.
-template <typename T>
-__device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-// The same tree with the 32 warp partials added in FP64 by warp 0: the
-// scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ, α = γ/κ) need more than FP32 —
-// with FP32 scalars the FP32 iteration drifted from the true gradient by
-// about 10⁻⁴ (relative) and needed several times more iterations.
+// GB300's FP64 pipe is narrow: an FP64 instruction costs a warp about 16
+// cycles of its SM's FP64 unit even with one active lane, and instructions
+// of different warps queue there.  The per-iteration reductions therefore
+// run in the iteration type T across lanes and warps (warp_sum_t), and only
+// the final sum over the warp partials (and any division) is done in FP64,
+// by one warp, then broadcast through shared memory: the warp partials are
+// widened by that warp alone.  The scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ,
+// α = γ/κ) need more than FP32 — with FP32 scalars the FP32 iteration
+// drifted from the true gradient by about 10⁻⁴ (relative) and needed several
+// times more iterations.
 template <typename T>
 __device__ __forceinline__ double block_sum_td(T v, double* sc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -535,7 +561,7 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* sv = reinterpret_cast<T*>(sd);  // the warp partials, in T
     v = warp_sum_t(v);
-    int ab = warp_sum_i(a + (b << 16));
+    int ab = (int)__reduce_add_sync(0xffffffffu, (unsigned)(a + (b << 16)));  // one redux
     __syncthreads();  // earlier readers of sd / si are done
     if (lane == 0) {
         sv[wid] = v;
@@ -544,7 +570,7 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
     __syncthreads();
     if (wid == 0) {
         const int nw = (int)(blockDim.x >> 5);
-        ab = warp_sum_i(lane < nw ? si[lane] : 0);
+        ab = (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < nw ? si[lane] : 0));
         const int xb = ab >> 16;
         double x = 0.0;
         if (!v_if_b_zero || xb == 0) x = warp_sum(lane < nw ? (double)sv[lane] : 0.0);
@@ -558,36 +584,6 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
     *v_out = sd[32];
     *a_out = si[64];
     *b_out = si[65];
-}
-
-// Σ v over the first TILE threads (the rest hold 0), in FP64 by thread 0 —
-// the same tree as block_sum_td over these warps (the xor shuffle tree of
-// the warp partials, with the zero partials of the other warps left out);
-// the result is valid in thread 0 only.  sc holds 33 doubles.
-template <typename T, int TILE>
-__device__ __forceinline__ double tile_sum_td(T v, double* sc) {
-    constexpr int NW = TILE / 32;
-    static_assert(NW >= 1 && (NW & (NW - 1)) == 0, "TILE: a power-of-two number of warps");
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    T* sv = reinterpret_cast<T*>(sc);
-    __syncthreads();  // earlier readers of sc are done
-    if (wid < NW) {
-        v = warp_sum_t(v);
-        if (lane == 0) sv[wid] = v;
-    }
-    __syncthreads();
-    double x = 0.0;
-    if (threadIdx.x == 0) {
-        double p[NW];
-#pragma unroll
-        for (int w2 = 0; w2 < NW; ++w2) p[w2] = (double)sv[w2];
-#pragma unroll
-        for (int o = NW / 2; o >= 1; o >>= 1)
-#pragma unroll
-            for (int i = 0; i < o; ++i) p[i] = p[i] + p[i + o];
-        x = p[0];
-    }
-    return x;
 }
 
 // Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
@@ -960,11 +956,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         // w-partials and curvature shares of this block's items
         for (int it = blockIdx.x; it < items; it += G) {
             const int ct = it % a.CT, rg = it / a.CT;
-            const T pw = mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red,
-                                        nullptr, nullptr, a.tmask, a.tw);
-            const int64_t i = (int64_t)ct * TILE + threadIdx.x;
-            const T prod = (threadIdx.x < TILE && i < n) ? sgb[i] * pw : T(0);
-            const double k = tile_sum_td<T, TILE>(prod, s_t);
+            double k = 0.0;
+            (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red,
+                                 nullptr, nullptr, a.tmask, a.tw, s_t, &k);
             if (threadIdx.x == 0) __stcg(kitem + it, k);
         }
         lap(0);
