@@ -632,13 +632,14 @@ def run_ours(args):
                  {1: "k_alg2_persist (persistent Alg. 2 loop, tiled state)",
                   3: "k_alg2_small64 (FP64 Alg. 2 loop on one thread-block cluster)"}.get(
                      int(stats[-1].iter_kernel), "k_alg2_repl (persistent Alg. 2 loop)"))
-        # DRAM traffic per launch of k_alg2_repl<float>: one ncu capture at
-        # 12000x3000 read 36.94 MB = 1.002 x n*ldq*4 (Q once; later iterations
-        # hit L2), so a launch moves 1.002 x n*ldq*4 bytes at any size
+        # DRAM traffic per launch of k_alg2_repl<float>: one ncu capture of the
+        # current kernel at 12000x3000 read 36.97 MB = 1.003 x n*ldq*4 (Q once;
+        # later iterations hit L2), so a launch moves 1.003 x n*ldq*4 bytes at
+        # any size
         traffic = None
         if alg == aln.ALG_ANTILOP and w["prec"] == "split_bf16":
             ldq = (n + 127) // 128 * 128
-            traffic = 1.002 * n * ldq * 4
+            traffic = 1.003 * n * ldq * 4
         note = ("the rows of Q read stay in the 129 MB L2 between iterations, so frac can "
                 "exceed 1")
         iters_avg = avg(lambda s: s.iterations)
