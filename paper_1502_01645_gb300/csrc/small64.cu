@@ -60,7 +60,7 @@ struct S64Args {
     const double* Q;
     int64_t ldq;
     int n;
-    int S;        // slice length, ⌈n/C⌉
+    int S;        // slice length, ⌈n/C⌉ (≤ 64: the first ⌈S/32⌉ warps hold it)
     double* y;    // in/out (global)
     double* g;    // in/out (global)
     IterState* st;
@@ -119,6 +119,35 @@ __device__ __forceinline__ void s_allgather(const double* slice, double* full, i
     }
 }
 
+// Sums over the slice (held by the first nsw warps; the others hold zeros):
+// warp sums in those warps, then thread 0 adds them in warp order.  The
+// totals are valid in thread 0 only (the caller publishes them from there).
+// GB300's FP64 unit is narrow (about 16 cycles per warp instruction even
+// with few active lanes), so no warp outside the slice issues FP64 work.
+__device__ __forceinline__ void s_sum0(double v, int c, int nsw, double* sd, int* si, double* v_out,
+                                       int* c_out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < nsw) {
+        v = warp_sum(v);
+        c = (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
+        if (lane == 0) {
+            sd[warp] = v;
+            si[warp] = c;
+        }
+    }
+    __syncthreads();
+    double t = 0.0;
+    int tc = 0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < nsw; ++w) {
+            t += sd[w];
+            tc += si[w];
+        }
+    }
+    *v_out = t;
+    *c_out = tc;
+}
+
 // out_i = Σ_{j: v_j ≠ 0} Qs[j][i] v_j for the slice rows (lane ↔ row, two
 // rows per lane; warp ↔ a contiguous range of j, two accumulators per row to
 // halve the dependent FP64 chain), warp partials added in warp order.
@@ -144,7 +173,7 @@ __device__ __forceinline__ void s_product(const double* Qs, int S, int n, const 
         par ^= 1;
     }
     red[warp * kSMaxS + i0] = a0 + a1;
-    red[warp * kSMaxS + i1] = b0 + b1;
+    if (i1 < S) red[warp * kSMaxS + i1] = b0 + b1;  // rows ≥ S are never read
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += blockDim.x) {
         double s = 0.0;
@@ -155,13 +184,15 @@ __device__ __forceinline__ void s_product(const double* Qs, int S, int n, const 
     __syncthreads();
 }
 
-// Mask of the slice: ḡ = g on P(y); returns (in every thread) ‖ḡ‖² and |P|
-// of the slice after a block reduction (warp 0, FP64 tree).
+// Mask of the slice: ḡ = g on P(y); returns (in thread 0) ‖ḡ‖² and |P| of
+// the slice (S ≤ 64 entries: the first nsw warps, one entry per thread).
 __device__ __forceinline__ void s_mask(const double* y, const double* g, double* gb, int len,
-                                       int S, double* sd, int* si, double* g2, int* cnt) {
+                                       int S, int nsw, double* sd, int* si, double* g2,
+                                       int* cnt) {
     double v = 0.0;
     int c = 0;
-    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const int i = threadIdx.x;
+    if (i < S) {
         if (i < len) {
             const bool P = y[i] > 0.0 || g[i] < 0.0;
             const double b = P ? g[i] : 0.0;
@@ -172,29 +203,14 @@ __device__ __forceinline__ void s_mask(const double* y, const double* g, double*
             gb[i] = 0.0;
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    c = warp_sum_i(c);
-    if (lane == 0) {
-        sd[warp] = v;
-        si[warp] = c;
-    }
-    __syncthreads();
-    double t = 0.0;
-    int tc = 0;
-#pragma unroll
-    for (int w = 0; w < kSWarps; ++w) {
-        t += sd[w];
-        tc += si[w];
-    }
-    *g2 = t;
-    *cnt = tc;
+    s_sum0(v, c, nsw, sd, si, g2, cnt);
     __syncthreads();
 }
 
 __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
     extern __shared__ __align__(16) double smd[];
     const int S = a.S, n = a.n;
+    const int nsw = (S + 31) / 32;  // warps holding the slice
     const int rank = cluster_rank();
     const int s0 = min(n, rank * S), len = min(n, s0 + S) - s0;
     double* Qs = smd;                      // n × S: Qs[j][i] = Q[j][s0 + i]
@@ -242,7 +258,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
     {
         double g2;
         int c;
-        s_mask(sy, sg, sgb, len, S, sd, si, &g2, &c);
+        s_mask(sy, sg, sgb, len, S, nsw, sd, si, &g2, &c);
         SRec m{g2, c, 0};
         s_exchange(&slot[2], m, &tot);  // its cluster barrier also publishes sgb
         s_allgather(sgb, gfull, n, S, rank);
@@ -274,15 +290,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         s_product(Qs, S, n, gfull, red, sw);
         S64_TRACE(1);
         double kp = 0.0;
-        for (int i = threadIdx.x; i < len; i += blockDim.x) kp = fma(sgb[i], sw[i], kp);
+        if ((int)threadIdx.x < len) kp = sgb[threadIdx.x] * sw[threadIdx.x];
         {
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            kp = warp_sum(kp);
-            if (lane == 0) sd[warp] = kp;
-            __syncthreads();
-            kp = 0.0;
-#pragma unroll
-            for (int w = 0; w < kSWarps; ++w) kp += sd[w];
+            int unused;
+            s_sum0(kp, 0, nsw, sd, si, &kp, &unused);
         }
         S64_TRACE(2);
         // (2) κ over the cluster, α
@@ -332,24 +343,10 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
             }
         }
         {
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            v2 = warp_sum(v2);
-            cP = warp_sum_i(cP);
-            clipped = warp_sum_i(clipped);
-            if (lane == 0) {
-                sd[warp] = v2;
-                si[warp] = cP | (clipped << 16);
-            }
-            __syncthreads();
-            v2 = 0.0;
-            cP = 0;
-            clipped = 0;
-#pragma unroll
-            for (int w = 0; w < kSWarps; ++w) {
-                v2 += sd[w];
-                cP += si[w] & 0xffff;
-                clipped += si[w] >> 16;
-            }
+            int packed;  // |P| and |C| of the slice, packed (each ≤ 64)
+            s_sum0(v2, cP | (clipped << 16), nsw, sd, si, &v2, &packed);
+            cP = packed & 0xffff;
+            clipped = packed >> 16;
         }
         ++iter;
         S64_TRACE(5);
@@ -375,7 +372,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         __syncthreads();
         double g2;
         int c;
-        s_mask(sy, sg, sgb, len, S, sd, si, &g2, &c);
+        s_mask(sy, sg, sgb, len, S, nsw, sd, si, &g2, &c);
         s_exchange(&slot[2], SRec{g2, c, 0}, &tot);
         s_allgather(sgb, gfull, n, S, rank);
         __syncthreads();
