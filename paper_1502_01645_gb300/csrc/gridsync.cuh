@@ -72,7 +72,7 @@ __device__ __forceinline__ bool grid_barrier(PersistSync* s, unsigned int target
                     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(u)
                                  : "l"(&s->count[lane][0])
                                  : "memory");
-                    (void)u;
+                    asm volatile("" ::"r"(u));  // the value itself is not needed
                 }
                 break;
             }

@@ -400,6 +400,88 @@ struct ReplArgs {
     unsigned int skew;     // extra arrivals every barrier waits for (tests: 0 normally)
 };
 
+// Scalars of the step (γ, κ and their sums) in the FP32 kernel: normalised
+// FP32 pairs hi + lo (|lo| ≤ ulp(hi)/2, about 48 significant bits), added
+// with TwoSum (Knuth) and renormalised with Fast2Sum (Dekker), in the
+// accurate form of double-float addition (Hida, Li and Bailey's QD
+// library): GB300's FP64 unit is narrow, and the FP32 pipe forms these in a
+// few dependent FP32 adds.  The FP64 kernel keeps FP64 scalars.
+struct DF {
+    float hi, lo;
+};
+template <typename T> struct ScT;
+template <> struct ScT<float> { using type = DF; };
+template <> struct ScT<double> { using type = double; };
+template <typename T> using Sc = typename ScT<T>::type;
+
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| ≥ |b|
+    const float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF sc_add(DF a, DF b) {
+    DF s = df_two_sum(a.hi, b.hi);
+    const DF t = df_two_sum(a.lo, b.lo);
+    s = df_fast_two_sum(s.hi, s.lo + t.hi);
+    return df_fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ double sc_add(double a, double b) { return a + b; }
+// A scalar from one value of the iteration type (exact).
+__device__ __forceinline__ void sc_set(DF& o, float v) { o = DF{v, 0.0f}; }
+__device__ __forceinline__ void sc_set(double& o, float v) { o = (double)v; }
+__device__ __forceinline__ void sc_set(double& o, double v) { o = v; }
+__device__ __forceinline__ DF sc_shfl_xor(DF a, int o) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ double sc_shfl_xor(double a, int o) {
+    return __shfl_xor_sync(0xffffffffu, a, o);
+}
+// Xor-tree warp sum (every lane gets the same value: the addition is
+// commutative in both forms).
+template <typename S>
+__device__ __forceinline__ S sc_warp_sum(S x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = sc_add(x, sc_shfl_xor(x, o));
+    return x;
+}
+// Comparisons of normalised pairs are lexicographic.
+__device__ __forceinline__ bool sc_lt(DF a, DF b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool sc_lt(double a, double b) { return a < b; }
+__device__ __forceinline__ bool sc_finite(DF a) { return isfinite(a.hi) && isfinite(a.lo); }
+__device__ __forceinline__ bool sc_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool sc_nonpos(DF a) { return a.hi <= 0.0f; }
+__device__ __forceinline__ bool sc_nonpos(double a) { return a <= 0.0; }
+__device__ __forceinline__ bool sc_zero(DF a) { return a.hi == 0.0f; }
+__device__ __forceinline__ bool sc_zero(double a) { return a == 0.0; }
+__device__ __forceinline__ double sc_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double sc_double(double a) { return a; }
+template <typename S> __device__ __forceinline__ S sc_of_double(double x);
+template <> __device__ __forceinline__ DF sc_of_double<DF>(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
+template <> __device__ __forceinline__ double sc_of_double<double>(double x) { return x; }
+template <typename S> __device__ __forceinline__ S sc_inf();
+template <> __device__ __forceinline__ DF sc_inf<DF>() { return DF{__int_as_float(0x7f800000), 0.0f}; }
+template <> __device__ __forceinline__ double sc_inf<double>() { return 1.0 / 0.0; }
+// Scalars through global memory (8 bytes either way), past L1.
+__device__ __forceinline__ void sc_stcg(double* p, DF v) {
+    __stcg(reinterpret_cast<float2*>(p), make_float2(v.hi, v.lo));
+}
+__device__ __forceinline__ void sc_stcg(double* p, double v) { __stcg(p, v); }
+template <typename S> __device__ __forceinline__ S sc_ldcg(const double* p);
+template <> __device__ __forceinline__ DF sc_ldcg<DF>(const double* p) {
+    const float2 f = __ldcg(reinterpret_cast<const float2*>(p));
+    return DF{f.x, f.y};
+}
+template <> __device__ __forceinline__ double sc_ldcg<double>(const double* p) { return __ldcg(p); }
+
 // Warp sum in the iteration type (xor tree: every lane gets the sum).
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
@@ -424,7 +506,7 @@ __device__ __forceinline__ bool tile_nz(const uint32_t* __restrict__ tm_ct, int 
 // steps: warp sums over the TILE threads, then thread 0 adds the warp sums in
 // FP64 (the xor tree of those sums, the zero ones of other warps left out)
 // into *kappa (thread 0 only).
-template <typename T, bool DIFF = false>
+template <typename T, bool DIFF = false, typename S = double>
 __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, int n,
                                          int rows_per_group, const T* v, int ct, int rg,
                                          T* __restrict__ dst, T* red,
@@ -432,7 +514,7 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
                                          const T* vsub = nullptr,
                                          const uint32_t* __restrict__ tmask = nullptr,
                                          int tw = 0, double* ksc = nullptr,
-                                         double* kappa = nullptr) {
+                                         S* kappa = nullptr) {
     using V = typename Vec16<T>::type;
     constexpr int VN = Vec16<T>::N;
     constexpr int TILE = 32 * VN;
@@ -494,13 +576,13 @@ __device__ __forceinline__ T mv_item_rep(const T* __restrict__ Q, int64_t ldq, i
     }
     __syncthreads();
     if (ksc && threadIdx.x == 0) {
-        double pw[NW];
+        S pw[NW];
 #pragma unroll
-        for (int w2 = 0; w2 < NW; ++w2) pw[w2] = (double)sv[w2];
+        for (int w2 = 0; w2 < NW; ++w2) sc_set(pw[w2], sv[w2]);
 #pragma unroll
         for (int o = NW / 2; o >= 1; o >>= 1)
 #pragma unroll
-            for (int i2 = 0; i2 < o; ++i2) pw[i2] = pw[i2] + pw[i2 + o];
+            for (int i2 = 0; i2 < o; ++i2) pw[i2] = sc_add(pw[i2], pw[i2 + o]);
         *kappa = pw[0];
     }
     return s;
@@ -523,12 +605,13 @@ __device__ __forceinline__ double block_sum_bcast(double v, double* sc) {
 // cycles of its SM's FP64 unit even with one active lane, and instructions
 // of different warps queue there.  The per-iteration reductions therefore
 // run in the iteration type T across lanes and warps (warp_sum_t), and only
-// the final sum over the warp partials (and any division) is done in FP64,
-// by one warp, then broadcast through shared memory: the warp partials are
-// widened by that warp alone.  The scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ,
-// α = γ/κ) need more than FP32 — with FP32 scalars the FP32 iteration
-// drifted from the true gradient by about 10⁻⁴ (relative) and needed several
-// times more iterations.
+// the final sum over the warp partials is done wider, by one warp, then
+// broadcast through shared memory: the warp partials are widened by that
+// warp alone — to FP64 here (block_sum_td), or to the scalar type of the
+// replicated kernel (block_sum3: FP32 pairs in the FP32 kernel).  The
+// scalars of the step (γ = ‖ḡ‖², κ = ḡᵀQḡ, α = γ/κ) need more than FP32 —
+// with FP32 scalars the FP32 iteration drifted from the true gradient by
+// about 10⁻⁴ (relative) and needed several times more iterations.
 template <typename T>
 __device__ __forceinline__ double block_sum_td(T v, double* sc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -546,17 +629,17 @@ __device__ __forceinline__ double block_sum_td(T v, double* sc) {
     return sc[32];
 }
 
-// One block reduction for the update step: the FP32 value v (partials in T
-// within warps, the 32 warp partials added in FP64 by warp 0, the same tree
-// as block_sum_td) and two counts.  The counts travel packed in one int
+// One block reduction for the update step: the value v (partials in T
+// within warps, the 32 warp partials added in the scalar type S by warp 0,
+// the same tree as block_sum_td) and two counts.  The counts travel packed in one int
 // (a + 2^16·b: both stay below 2^15 here, since the replicated-state kernels
 // hold n < 2^14 entries).  The warp partials of v are stored in T and
 // widened by warp 0 alone (exact, and one FP64 instruction instead of one per
-// warp on the narrow FP64 pipe).  With v_if_b_zero, the FP64 sum is formed
+// warp on the narrow FP64 pipe).  With v_if_b_zero, the wide sum is formed
 // only when the total b is 0 (*v_out is 0 otherwise).  sd holds 33 doubles,
 // si 66 ints.
-template <typename T>
-__device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* si, double* v_out,
+template <typename T, typename S = double>
+__device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* si, S* v_out,
                                            int* a_out, int* b_out, bool v_if_b_zero = false) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     T* sv = reinterpret_cast<T*>(sd);  // the warp partials, in T
@@ -572,25 +655,30 @@ __device__ __forceinline__ void block_sum3(T v, int a, int b, double* sd, int* s
         const int nw = (int)(blockDim.x >> 5);
         ab = (int)__reduce_add_sync(0xffffffffu, (unsigned)(lane < nw ? si[lane] : 0));
         const int xb = ab >> 16;
-        double x = 0.0;
-        if (!v_if_b_zero || xb == 0) x = warp_sum(lane < nw ? (double)sv[lane] : 0.0);
+        S x;
+        sc_set(x, T(0));
+        if (!v_if_b_zero || xb == 0) {
+            S lv;
+            sc_set(lv, lane < nw ? sv[lane] : T(0));
+            x = sc_warp_sum(lv);
+        }
         if (lane == 0) {
-            sd[32] = x;
+            *reinterpret_cast<S*>(sd + 32) = x;
             si[64] = ab & 0xffff;
             si[65] = xb;
         }
     }
     __syncthreads();
-    *v_out = sd[32];
+    *v_out = *reinterpret_cast<const S*>(sd + 32);
     *a_out = si[64];
     *b_out = si[65];
 }
 
 // Mask of the whole replicated state: ḡ = g on P(y); returns ‖ḡ‖² and |P|
 // (fixed reduction tree, identical in every block; si holds 66 ints).
-template <typename T>
+template <typename T, typename S = double>
 __device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb, double* st,
-                                         int* si, double* g2_out, int* cnt_out) {
+                                         int* si, S* g2_out, int* cnt_out) {
     T v = T(0);
     int c = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -602,7 +690,7 @@ __device__ __forceinline__ void mask_all(int n, const T* sy, const T* sg, T* sgb
         c += P ? 1 : 0;
     }
     int unused;
-    block_sum3<T>(v, c, 0, st, si, g2_out, cnt_out, &unused);
+    block_sum3<T, S>(v, c, 0, st, si, g2_out, cnt_out, &unused);
 }
 
 constexpr int kLocalClip = 8;  // clipped rows a block multiplies by itself
@@ -620,6 +708,13 @@ __device__ __forceinline__ T step_quotient(double gam, double kap) {
     const float q = __fdiv_rn(gh, kh);
     const float r = fmaf(-q, kh, gh) + fmaf(-q, kl, gl);
     return (T)(q + __fdiv_rn(r, kh));
+}
+// The same from FP32-pair scalars (no FP64 at all).
+template <typename T>
+__device__ __forceinline__ T step_quotient(DF gam, DF kap) {
+    const float q = __fdiv_rn(gam.hi, kap.hi);
+    const float r = fmaf(-q, kap.hi, gam.hi) + fmaf(-q, kap.lo, gam.lo);
+    return (T)(q + __fdiv_rn(r, kap.hi));
 }
 
 // dst[j] (+)= Σ_r part[r][j] for j < n, r in order.  16-byte loads, two
@@ -895,23 +990,24 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         sw[j] = T(0);
     }
     __syncthreads();
-    double gam;  // step scalars in FP64, accumulated from FP32 partials
+    using S = Sc<T>;  // step scalars: FP32 pairs (FP32 kernel) or FP64
+    S gam;
     int cnt;
-    mask_all(n, sy, sg, sgb, s_t, s_i3, &gam, &cnt);
+    mask_all<T, S>(n, sy, sg, sgb, s_t, s_i3, &gam, &cnt);
 
     // Scalar control state lives in thread 0 (FP64 compares and the division
     // are issued once, not by every thread).
     IterState* st = a.st;
-    const double eps = st->eps;
+    const S eps = sc_of_double<S>(st->eps);
     const int max_iter = st->max_iter, window = st->window;
     // thread 0's bookkeeping lives in shared memory, not in registers of
     // every thread (the kernel runs at the 64-register limit of 1024 threads)
-    __shared__ double s_best;
+    __shared__ S s_best;
     __shared__ int s_best_iter, s_nclip_iters;
     __shared__ long long s_sum_passive, s_sum_clip;
     __shared__ uint64_t s_prof[5], s_tprev;  // block 0's phase times (ns)
     if (threadIdx.x == 0) {
-        s_best = 1.0 / 0.0;
+        s_best = sc_inf<S>();
         s_best_iter = s_nclip_iters = 0;
         s_sum_passive = s_sum_clip = 0;
         for (int k = 0; k < 5; ++k) s_prof[k] = 0;
@@ -927,13 +1023,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
     for (;;) {
         if (threadIdx.x == 0) {
             int stop = 1;
-            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            if (!sc_finite(gam)) status = ALN_RHS_NONFINITE;
             else if (cnt == 0) status = ALN_RHS_EMPTY_PASSIVE;
-            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
+            else if (sc_lt(gam, eps) || sc_zero(gam)) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
             else if (iter - s_best_iter > window) status = ALN_RHS_STAGNATED;
             else stop = 0;
-            if (!stop && gam < s_best) {
+            if (!stop && sc_lt(gam, s_best)) {
                 s_best = gam;
                 s_best_iter = iter;
             }
@@ -956,10 +1052,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         // w-partials and curvature shares of this block's items
         for (int it = blockIdx.x; it < items; it += G) {
             const int ct = it % a.CT, rg = it / a.CT;
-            double k = 0.0;
-            (void)mv_item_rep<T>(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part, red,
-                                 nullptr, nullptr, a.tmask, a.tw, s_t, &k);
-            if (threadIdx.x == 0) __stcg(kitem + it, k);
+            S k;
+            sc_set(k, T(0));
+            (void)mv_item_rep<T, false, S>(a.Q, a.ldq, n, a.rows_per_group, sgb, ct, rg, part,
+                                           red, nullptr, nullptr, a.tmask, a.tw, s_t, &k);
+            if (threadIdx.x == 0) sc_stcg(kitem + it, k);
         }
         lap(0);
         if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
@@ -976,17 +1073,19 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
         if (threadIdx.x < 32) {
             // four independent accumulators per lane, then a pairwise and
             // a shuffle tree: the FP64 adds form a short dependent chain
-            double kv[4] = {0.0, 0.0, 0.0, 0.0};
+            S kv[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) sc_set(kv[m], T(0));
 #pragma unroll 4
             for (int i = threadIdx.x, m = 0; i < items; i += 32, m = (m + 1) & 3)
-                kv[m] += __ldcg(kitem + i);
-            double k2 = warp_sum((kv[0] + kv[1]) + (kv[2] + kv[3]));
+                kv[m] = sc_add(kv[m], sc_ldcg<S>(kitem + i));
+            const S k2 = sc_warp_sum(sc_add(sc_add(kv[0], kv[1]), sc_add(kv[2], kv[3])));
             if (threadIdx.x == 0) {
                 int stop = 0;
-                if (!isfinite(k2)) {
+                if (!sc_finite(k2)) {
                     status = ALN_RHS_NONFINITE;
                     stop = 1;
-                } else if (k2 <= 0.0) {
+                } else if (sc_nonpos(k2)) {
                     status = ALN_RHS_CURVATURE;
                     stop = 1;
                 }
@@ -1041,11 +1140,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 update_vec<T>(v, n, aT, wv, sy, syl, sg, sgb, sw, v2, cP, clipped);
             }
         }
-        double gam2;
+        S gam2;
         int cnt2, nclip;
         // identical in every block; ‖ḡ‖² is formed only when nothing was
         // clipped (else the clipped correction's mask replaces it)
-        block_sum3<T>(v2, cP, clipped, s_t, s_i3, &gam2, &cnt2, &nclip, true);
+        block_sum3<T, S>(v2, cP, clipped, s_t, s_i3, &gam2, &cnt2, &nclip, true);
         ++iter;
         if (threadIdx.x == 0) s_sum_clip += nclip;
         lap(2);
@@ -1071,7 +1170,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
                 if (!(ok = grid_barrier(a.sync, (bar += G) + a.skew, a.wait_ns))) break;
                 add_partials_mask<T>(a.part2, a.R, a.ldq, n, sy, sg, sgb, v3, cP3);
             }
-            block_sum3<T>(v3, cP3, 0, s_t, s_i3, &gam, &cnt, &unused);
+            block_sum3<T, S>(v3, cP3, 0, s_t, s_i3, &gam, &cnt, &unused);
             if (threadIdx.x == 0) ++s_nclip_iters;
         } else {
             gam = gam2;
@@ -1090,9 +1189,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_alg2_repl(ReplArgs<T> a) {
             st->iter = iter;
             st->done = 1;
             st->status = ok ? status : kStatusTimeout;
-            st->gbar2 = gam;
+            st->gbar2 = sc_double(gam);
             st->npassive = cnt;
-            st->best_g2 = s_best;
+            st->best_g2 = sc_double(s_best);
             st->best_iter = s_best_iter;
             st->sum_passive = s_sum_passive;
             st->sum_clip = s_sum_clip;
