@@ -547,7 +547,7 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     // narrow A) each pair's K range runs over several CTAs.  The split is fixed
     // by the whole matrix, so host input (launched chunk by chunk below) and
     // device input (one launch) give the same Q
-    const int64_t chunk_cols = std::max<int64_t>(1024, round_up(ceil_div(n, 63), 128));
+    const int64_t chunk_cols = std::max<int64_t>(512, round_up(ceil_div(n, 63), 128));
     float* gpart = nullptr;
     unsigned int* gticket = nullptr;
     int gsplit = 1;
@@ -570,11 +570,10 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
     if (!f64 && !c->batched && gsplit == 1) {
         const int64_t tiles = ceil_div(n, 128), pairs = tiles * (tiles + 1) / 2;
         const int64_t tail = gram_sk_tail(pairs, c->num_sms);
-        // host input launches the Gram by column chunks: stream-K only when
-        // the last chunk holds the whole tail, so that both inputs give the
-        // same Q bits
-        const int64_t r0 = (n - 1) / chunk_cols * chunk_cols / 128;
-        if (tail > 0 && tail <= pairs - r0 * (r0 + 1) / 2) {
+        // host input launches the Gram in whole waves as the chunks arrive,
+        // so the launch that ends the triangle always holds the whole tail:
+        // both inputs give the same Q bits
+        if (tail > 0) {
             ALN_CHECK(ensure(&c->sp_part, &c->sp_part_bytes, gram_sk_bytes(pairs, c->num_sms)));
             skp = (float*)c->sp_part;
             skt = (unsigned int*)((uint8_t*)c->sp_part + gram_sk_part_bytes(pairs, c->num_sms));
@@ -596,10 +595,14 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
         // previous users of the A buffer)
         ALN_TRY(cudaEventRecord(c->copy_ev[0], c->stream));
         ALN_TRY(cudaStreamWaitEvent(c->copy_stream, c->copy_ev[0], 0));
-        // chunks of at least 1024 columns: a Gram launch lasts at least one
-        // tile's full K loop (about 0.4 ms at d = 20000) whatever its size
+        // A Gram launch lasts at least one tile pair's full K loop (about
+        // 0.4 ms at d = 20000) whatever its size, so the pairs that a chunk
+        // completes wait until they fill whole waves (the SM count, one CTA
+        // per SM); the chunk that ends the matrix launches the rest, with
+        // the stream-K tail.  Each pair is computed alike in any launch.
         const int64_t per = chunk_cols;
         const int64_t tiles = ceil_div(n, 128);
+        int64_t launched = 0;  // tile pairs launched (triangle order)
         int e = 1;
         for (int64_t c0 = 0; c0 < n; c0 += per, ++e) {
             const int64_t c1 = std::min(n, c0 + per);
@@ -613,11 +616,19 @@ aln_status aln_prepare(aln_ctx* c, const void* A, int64_t d, int64_t n, int64_t 
                                     c->inv_s + c0, c->q64 + c0, ldq, c->flags, hi + c0 * c->ldk,
                                     mid + c0 * c->ldk, lo + c0 * c->ldk, c->ldk, c->stream));
             if (c0 == 0) ALN_TRY(cudaEventRecord(c->ev[1], c->stream));
-            ALN_TRY(launch_gram_tc(c->opt.gram_split, hi, mid, lo, d, n, c->ldk, c->inv_s,
-                                   (float*)c->Q, ldq, c->flags + 1, c->stream, c0 / 128,
-                                   c1 == n ? tiles : c1 / 128, gpart, gticket, gsplit, skp, skt,
-                                   c->num_sms));
-            c->launches += 2;
+            const int64_t r1 = c1 == n ? tiles : c1 / 128;  // tile rows complete
+            int64_t upto = r1 * (r1 + 1) / 2;                // pairs ready
+            if (c1 < n && gsplit == 1)
+                upto = launched + (upto - launched) / c->num_sms * c->num_sms;
+            if (upto > launched) {
+                ALN_TRY(launch_gram_tc_pairs(c->opt.gram_split, hi, mid, lo, d, n, c->ldk,
+                                             c->inv_s, (float*)c->Q, ldq, c->flags + 1,
+                                             c->stream, launched, upto, gpart, gticket, gsplit,
+                                             skp, skt, c->num_sms));
+                launched = upto;
+                ++c->launches;
+            }
+            ++c->launches;
         }
     } else {
         ALN_TRY(launch_colstats(c->A, dtype, d, n, lda, c->B, kc, ldb, c->s, c->inv_s, c->q64,

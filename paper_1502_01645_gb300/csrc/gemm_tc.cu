@@ -800,6 +800,22 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            cudaStream_t st, int64_t row0, int64_t row1, float* part,
                            unsigned int* ticket, int split, float* sk_part,
                            unsigned int* sk_ticket, int num_sms) {
+    const int64_t tiles = ceil_div(n, tc::BM);
+    if (row1 < 0 || row1 > tiles) row1 = tiles;
+    if (row0 < 0 || row0 >= row1) return cudaSuccess;
+    // tiles (I, J ≤ I) with row0 ≤ I < row1 are the contiguous range
+    // [row0(row0+1)/2, row1(row1+1)/2) of the triangle order
+    return launch_gram_tc_pairs(nsplit, hi, mid, lo, d, n, ldk, inv_s, Q, ldq, timeout_flag, st,
+                                row0 * (row0 + 1) / 2, row1 * (row1 + 1) / 2, part, ticket,
+                                split, sk_part, sk_ticket, num_sms);
+}
+
+cudaError_t launch_gram_tc_pairs(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                                 const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
+                                 const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
+                                 cudaStream_t st, int64_t p0, int64_t p1, float* part,
+                                 unsigned int* ticket, int split, float* sk_part,
+                                 unsigned int* sk_ticket, int num_sms) {
     using namespace tc;
     // TMA rules: 16-byte aligned base and row stride; x coordinates are
     // multiples of 64 BF16 (128 bytes) by construction.
@@ -827,13 +843,11 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     a.Q = Q;
     a.ldq = ldq;
     a.timeout_flag = timeout_flag;
-    const int64_t tiles = ceil_div(n, BM);
-    if (row1 < 0 || row1 > tiles) row1 = tiles;
-    if (row0 < 0 || row0 >= row1) return cudaSuccess;
-    // tiles (I, J ≤ I) with row0 ≤ I < row1 are the contiguous range
-    // [row0(row0+1)/2, row1(row1+1)/2) of the triangle order
-    a.t0 = row0 * (row0 + 1) / 2;
-    const int64_t pairs = row1 * (row1 + 1) / 2 - a.t0;
+    const int64_t tiles = ceil_div(n, BM), total = tiles * (tiles + 1) / 2;
+    if (p1 < 0 || p1 > total) p1 = total;
+    if (p0 < 0 || p0 >= p1) return cudaSuccess;
+    a.t0 = p0;
+    const int64_t pairs = p1 - p0;
     a.S = (part && ticket && split > 1) ? split : 1;
     a.part = part;
     a.ticket = ticket;
@@ -842,15 +856,17 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
     // that ends the triangle (when all of that wave's pairs are in it): the
     // same split whether the matrix came in one launch or in row chunks
     int64_t R = 0;
-    if (a.S == 1 && row1 == tiles && sk_part && sk_ticket) {
-        R = gram_sk_tail(tiles * (tiles + 1) / 2, num_sms);
+    if (a.S == 1 && p1 == total && sk_part && sk_ticket) {
+        R = gram_sk_tail(total, num_sms);
         if (R > pairs) R = 0;
     }
     const unsigned full = R > 0 ? (unsigned)(pairs - R) : grid;  // R > 0 only with S = 1
-    if (nsplit == 3)
-        k_gram_tc<3><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
-    else
-        k_gram_tc<2><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+    if (full > 0) {  // a launch may hold the stream-K tail alone
+        if (nsplit == 3)
+            k_gram_tc<3><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+        else
+            k_gram_tc<2><<<full, G3_THREADS, G3_SMEM_BYTES, st>>>(mh, mm, ml, a);
+    }
     if (R > 0) {
         static bool sk_attr[2] = {false, false};
         if (!sk_attr[nsplit - 2]) {

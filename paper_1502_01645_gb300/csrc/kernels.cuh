@@ -56,6 +56,17 @@ cudaError_t launch_gram_tc(int nsplit, const __nv_bfloat16* hi, const __nv_bfloa
                            float* part = nullptr, unsigned int* ticket = nullptr, int split = 1,
                            float* sk_part = nullptr, unsigned int* sk_ticket = nullptr,
                            int num_sms = 0);
+// The same over the tile pairs [p0, p1) of the triangle order (pair
+// I(I+1)/2 + J is tile (I, J ≤ I)).  Each pair is one CTA's whole K loop (or
+// `split` CTAs' chunks), so any partition of the pairs into launches gives the
+// same Q; the stream-K pass runs in the launch that ends the triangle when it
+// holds the whole tail.
+cudaError_t launch_gram_tc_pairs(int nsplit, const __nv_bfloat16* hi, const __nv_bfloat16* mid,
+                                 const __nv_bfloat16* lo, int64_t d, int64_t n, int64_t ldk,
+                                 const double* inv_s, float* Q, int64_t ldq, int* timeout_flag,
+                                 cudaStream_t st, int64_t p0, int64_t p1, float* part,
+                                 unsigned int* ticket, int split, float* sk_part,
+                                 unsigned int* sk_ticket, int num_sms);
 // Stream-K for the Gram's last wave: with `pairs` tile pairs (one CTA per SM
 // resident), the pairs past the last full wave (0 if none) are run by one CTA
 // per SM, each taking an equal share of their K blocks; a pair split over

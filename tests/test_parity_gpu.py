@@ -114,14 +114,14 @@ def test_split_bf16_gram_tall_narrow_split_k(aln, device_a):
 
 @pytest.mark.parametrize("d,n", [(3000, 2300), (20000, 300), (40000, 1300), (5000, 4224)])
 def test_host_and_device_input_give_the_same_result(aln, d, n):
-    """Host A is copied in column chunks and each chunk's Gram tile rows run
-    as it lands; device A takes one launch.  The tiles' K chunking (split K
-    for tall, narrow A; stream-K for the pairs past the last full wave) is
-    fixed by the whole matrix, so both give the same Q bits, the same
-    iterations and the same solution: 3 chunk launches without split K and
-    with stream-K (n = 2300: 19 tail pairs, all in the last chunk), 1 and 2
-    with split K, and 5 with stream-K off (n = 4224: 105 tail pairs, more
-    than the last chunk's 33)."""
+    """Host A is copied in 512-column chunks, and the Gram's tile pairs run
+    in whole waves as the chunks land (the rest with the last chunk); device
+    A takes one launch.  Each pair's K chunking (split K for tall, narrow A;
+    stream-K for the pairs past the last full wave) is fixed by the whole
+    matrix, so both give the same Q bits, the same iterations and the same
+    solution: n = 2300 (5 chunks, pairs deferred to whole waves, 19
+    stream-K pairs), n = 300 and 1300 with split K (every chunk launches
+    what it completes), n = 4224 (9 chunks, 105 stream-K pairs)."""
     import torch
     r = np.random.default_rng(d + n)
     A64 = r.random((d, n)) * np.exp(r.uniform(np.log(1e-2), np.log(1e2), n))[None, :]
