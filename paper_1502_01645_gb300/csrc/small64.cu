@@ -149,8 +149,12 @@ __device__ __forceinline__ void s_sum0(double v, int c, int nsw, double* sd, int
 }
 
 // out_i = Σ_{j: v_j ≠ 0} Qs[j][i] v_j for the slice rows (lane ↔ row, two
-// rows per lane; warp ↔ a contiguous range of j, two accumulators per row to
-// halve the dependent FP64 chain), warp partials added in warp order.
+// rows per lane; warp ↔ a contiguous range of j), warp partials added in
+// warp order.  The non-zero j of a 32-wide chunk are compacted with a ballot
+// (an integer test of the bits: ±0 have no other bits set) and taken two at a
+// time, one per accumulator (the k-th non-zero j of the range goes to
+// accumulator k mod 2), so the FP64 unit — narrow on this GPU and the bound
+// of this loop — sees only the FMAs themselves, with two independent chains.
 __device__ __forceinline__ void s_product(const double* Qs, int S, int n, const double* v,
                                           double* red, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -158,22 +162,48 @@ __device__ __forceinline__ void s_product(const double* Qs, int S, int n, const 
     const int j0 = warp * per, j1 = min(n, j0 + per);
     double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
     const int i0 = lane, i1 = lane + 32;
-    int par = 0;
-    for (int j = j0; j < j1; ++j) {
-        const double vj = v[j];
-        if (vj == 0.0) continue;  // warp-uniform
-        const double* col = Qs + (int64_t)j * S;
-        if (par == 0) {
-            if (i0 < S) a0 = fma(col[i0], vj, a0);
-            if (i1 < S) b0 = fma(col[i1], vj, b0);
-        } else {
-            if (i0 < S) a1 = fma(col[i0], vj, a1);
-            if (i1 < S) b1 = fma(col[i1], vj, b1);
+    const bool in0 = i0 < S, in1 = S > 32 && i1 < S;
+    bool odd = false;  // the next non-zero j goes to accumulator 1
+    for (int base = j0; base < j1; base += 32) {
+        const int jl = base + lane;
+        const bool nz = jl < j1 && (__double_as_longlong(v[jl]) << 1) != 0;
+        unsigned int m = __ballot_sync(0xffffffffu, nz);
+        if (odd && m) {  // one j to accumulator 1 first (warp-uniform)
+            const int j = base + __ffs(m) - 1;
+            m &= m - 1;
+            const double vj = v[j];
+            const double* col = Qs + (int64_t)j * S;
+            if (in0) a1 = fma(col[i0], vj, a1);
+            if (in1) b1 = fma(col[i1], vj, b1);
+            odd = false;
         }
-        par ^= 1;
+        while (m) {
+            const int ja = base + __ffs(m) - 1;
+            m &= m - 1;
+            const double va = v[ja];
+            const double* ca = Qs + (int64_t)ja * S;
+            if (m) {
+                const int jb = base + __ffs(m) - 1;
+                m &= m - 1;
+                const double vb = v[jb];
+                const double* cb = Qs + (int64_t)jb * S;
+                if (in0) {
+                    a0 = fma(ca[i0], va, a0);
+                    a1 = fma(cb[i0], vb, a1);
+                }
+                if (in1) {
+                    b0 = fma(ca[i1], va, b0);
+                    b1 = fma(cb[i1], vb, b1);
+                }
+            } else {
+                if (in0) a0 = fma(ca[i0], va, a0);
+                if (in1) b0 = fma(ca[i1], va, b0);
+                odd = true;
+            }
+        }
     }
     red[warp * kSMaxS + i0] = a0 + a1;
-    if (i1 < S) red[warp * kSMaxS + i1] = b0 + b1;  // rows ≥ S are never read
+    if (in1) red[warp * kSMaxS + i1] = b0 + b1;  // rows ≥ S are never read
     __syncthreads();
     for (int i = threadIdx.x; i < S; i += blockDim.x) {
         double s = 0.0;
