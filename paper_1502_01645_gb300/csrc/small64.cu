@@ -5,7 +5,8 @@
 // The plain FP64 method on a small problem is latency-bound: the grid-wide
 // kernel pays a grid barrier and several FP64 reductions of the whole vector
 // per iteration, while the work is a few tens of thousands of FMAs.  Here the
-// C = 8 CTAs of one cluster split the rows of Q: CTA r keeps the columns
+// C CTAs of one cluster (8, or 16 when n ≤ 256 and 16-CTA clusters fit)
+// split the rows of Q: CTA r keeps the columns
 // [r·S, r·S + S) of Q (rows, since Q is symmetric) for every j, i.e.
 // Qs[j][i] = Q[j][r·S + i], the slice of every state vector (y, g, w, e), and
 // a full copy of ḡ (and of e when rows were clipped) gathered through
@@ -51,7 +52,8 @@
 namespace aln {
 namespace {
 
-constexpr int kSC = 8;            // CTAs of the cluster
+constexpr int kSC = 8;            // CTAs of the cluster (the portable size)
+constexpr int kSC16 = 16;         // the non-portable size, for n ≤ 16·16
 constexpr int kSThreads = 256;    // 8 warps
 constexpr int kSWarps = kSThreads / 32;
 constexpr int kSMaxS = 64;        // slice rows per CTA (two per lane)
@@ -74,6 +76,7 @@ struct SRec {
 
 // Publish this CTA's record, cluster barrier, warp 0 adds the C records in
 // rank order; lanes < C each load one record.  Totals land in *tot.
+template <int C>
 __device__ __forceinline__ void s_exchange(SRec* slot, const SRec& mine, SRec* tot) {
     if (threadIdx.x == 0) *slot = mine;
     cluster_sync();
@@ -81,15 +84,15 @@ __device__ __forceinline__ void s_exchange(SRec* slot, const SRec& mine, SRec* t
         const int lane = threadIdx.x;
         double v = 0.0;
         int cnt = 0, clip = 0;
-        if (lane < kSC) {
+        if (lane < C) {
             const uint32_t b = cluster_addr(slot, lane);
             v = ld_cluster(b + (uint32_t)offsetof(SRec, v), 0.0);
             cnt = ld_cluster(b + (uint32_t)offsetof(SRec, cnt), 0);
             clip = ld_cluster(b + (uint32_t)offsetof(SRec, clip), 0);
         }
-        // pairwise tree over the 8 ranks (fixed order)
+        // pairwise tree over the C ranks (fixed order)
 #pragma unroll
-        for (int o = 1; o < kSC; o <<= 1) {
+        for (int o = 1; o < C; o <<= 1) {
             const double ov = __shfl_down_sync(0xffffffffu, v, o);
             const int oc = __shfl_down_sync(0xffffffffu, cnt, o);
             const int ol = __shfl_down_sync(0xffffffffu, clip, o);
@@ -155,8 +158,61 @@ __device__ __forceinline__ void s_sum0(double v, int c, int nsw, double* sd, int
 // time, one per accumulator (the k-th non-zero j of the range goes to
 // accumulator k mod 2), so the FP64 unit — narrow on this GPU and the bound
 // of this loop — sees only the FMAs themselves, with two independent chains.
+template <int C>
 __device__ __forceinline__ void s_product(const double* Qs, int S, int n, const double* v,
-                                          double* red, double* out) {
+                                          double* red, double* out);
+
+// The 16-CTA form (S ≤ 16 rows per CTA): a half-warp per j, so one FMA
+// instruction serves two j of the compacted list (lane = 16·h + row, half h
+// takes the j of its parity).  Each step takes up to four j: the first pair
+// into accumulator 0, the second into accumulator 1 (two independent FMA
+// chains); the halves are added at the end (half 0 + half 1).
+__device__ __forceinline__ void s_product_packed(const double* Qs, int S, int n, const double* v,
+                                                 double* red, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = (n + kSWarps - 1) / kSWarps;
+    const int j0 = warp * per, j1 = min(n, j0 + per);
+    const int h = lane >> 4, i = lane & 15;
+    const bool in = i < S;
+    double a0 = 0.0, a1 = 0.0;
+    for (int base = j0; base < j1; base += 32) {
+        const int jl = base + lane;
+        const bool nz = jl < j1 && (__double_as_longlong(v[jl]) << 1) != 0;
+        unsigned int m = __ballot_sync(0xffffffffu, nz);
+        while (m) {  // warp-uniform
+            int q[4];  // the next four j of the list (−1 past its end)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                q[t] = m ? base + __ffs(m) - 1 : -1;
+                m &= m - 1;  // no-op once m is 0
+            }
+            const int ja = h == 0 ? q[0] : q[1], jb = h == 0 ? q[2] : q[3];
+            if (in && ja >= 0) a0 = fma(Qs[(int64_t)ja * S + i], v[ja], a0);
+            if (in && jb >= 0) a1 = fma(Qs[(int64_t)jb * S + i], v[jb], a1);
+        }
+    }
+    double acc = a0 + a1;
+    acc += __shfl_down_sync(0xffffffffu, acc, 16);  // half 0 + half 1
+    if (lane < 16) red[warp * kSMaxS + lane] = acc;
+    __syncthreads();
+    for (int r = threadIdx.x; r < S; r += blockDim.x) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kSWarps; ++w) s += red[w * kSMaxS + r];
+        out[r] = s;
+    }
+    __syncthreads();
+}
+
+template <>
+__device__ __forceinline__ void s_product<kSC16>(const double* Qs, int S, int n, const double* v,
+                                                 double* red, double* out) {
+    s_product_packed(Qs, S, n, v, red, out);
+}
+
+template <>
+__device__ __forceinline__ void s_product<kSC>(const double* Qs, int S, int n, const double* v,
+                                               double* red, double* out) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = (n + kSWarps - 1) / kSWarps;
     const int j0 = warp * per, j1 = min(n, j0 + per);
@@ -237,6 +293,7 @@ __device__ __forceinline__ void s_mask(const double* y, const double* g, double*
     __syncthreads();
 }
 
+template <int C>
 __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
     extern __shared__ __align__(16) double smd[];
     const int S = a.S, n = a.n;
@@ -290,7 +347,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         int c;
         s_mask(sy, sg, sgb, len, S, nsw, sd, si, &g2, &c);
         SRec m{g2, c, 0};
-        s_exchange(&slot[2], m, &tot);  // its cluster barrier also publishes sgb
+        s_exchange<C>(&slot[2], m, &tot);  // its cluster barrier also publishes sgb
         s_allgather(sgb, gfull, n, S, rank);
         __syncthreads();
         gam = tot.v;
@@ -317,7 +374,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         S64_TRACE(0);
 
         // (1) w on the slice, κ share
-        s_product(Qs, S, n, gfull, red, sw);
+        s_product<C>(Qs, S, n, gfull, red, sw);
         S64_TRACE(1);
         double kp = 0.0;
         if ((int)threadIdx.x < len) kp = sgb[threadIdx.x] * sw[threadIdx.x];
@@ -327,7 +384,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         }
         S64_TRACE(2);
         // (2) κ over the cluster, α
-        s_exchange(&slot[0], SRec{kp, 0, 0}, &tot);
+        s_exchange<C>(&slot[0], SRec{kp, 0, 0}, &tot);
         S64_TRACE(3);
         if (threadIdx.x == 0) {
             const double k2 = tot.v;
@@ -380,7 +437,7 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         }
         ++iter;
         S64_TRACE(5);
-        s_exchange(&slot[1], SRec{v2, cP, clipped}, &tot);  // publishes sgb and e too
+        s_exchange<C>(&slot[1], SRec{v2, cP, clipped}, &tot);  // publishes sgb and e too
         S64_TRACE(6);
         const int nclip = tot.clip;
         sum_clip += nclip;
@@ -397,13 +454,13 @@ __global__ void __launch_bounds__(kSThreads, 1) k_alg2_small64(S64Args a) {
         s_allgather(sw, efull, n, S, rank);
         __syncthreads();
         // (into su: peers may still be reading this CTA's e in sw)
-        s_product(Qs, S, n, efull, red, su);
+        s_product<C>(Qs, S, n, efull, red, su);
         for (int i = threadIdx.x; i < len; i += blockDim.x) sg[i] += su[i];
         __syncthreads();
         double g2;
         int c;
         s_mask(sy, sg, sgb, len, S, nsw, sd, si, &g2, &c);
-        s_exchange(&slot[2], SRec{g2, c, 0}, &tot);
+        s_exchange<C>(&slot[2], SRec{g2, c, 0}, &tot);
         s_allgather(sgb, gfull, n, S, rank);
         __syncthreads();
         gam = tot.v;
@@ -455,32 +512,83 @@ bool small64_fits(const aln_ctx* c, int optin_smem) {
     return s64_smem_bytes((int)n, S) + 4096 <= (size_t)optin_smem;
 }
 
+namespace {
+template <int C>
+cudaError_t launch_small64_c(const S64Args& a, size_t smem, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kSThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_alg2_small64<C>, a);
+}
+
+// Can a 16-CTA cluster of the kernel with this shared memory be resident?
+// (Non-portable size: asked once per device and size class.)
+bool cluster16_fits(size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    static int known[64] = {};      // 0 unknown, 1 yes, 2 no
+    static size_t known_smem[64] = {};
+    if (known[dev] != 0 && known_smem[dev] >= smem) return known[dev] == 1;
+    bool ok = cudaFuncSetAttribute(k_alg2_small64<kSC16>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(k_alg2_small64<kSC16>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem) == cudaSuccess;
+    if (ok) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        cfg.gridDim = dim3(kSC16);
+        cfg.blockDim = dim3(kSThreads);
+        cfg.dynamicSmemBytes = smem;
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kSC16;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        ok = cudaOccupancyMaxActiveClusters(&nc, k_alg2_small64<kSC16>, &cfg) == cudaSuccess &&
+             nc >= 1;
+    }
+    cudaGetLastError();  // a refused size leaves no error behind
+    known[dev] = ok ? 1 : 2;
+    known_smem[dev] = smem;
+    return ok;
+}
+}  // namespace
+
+// 16 CTAs when every CTA holds at most 16 rows (n ≤ 256) and such a cluster
+// fits on the GPU (each FP64 FMA instruction then serves two j); else 8.
 cudaError_t launch_alg2_small64(aln_ctx* c) {
     S64Args a;
     a.Q = (const double*)c->Q;
     a.ldq = c->ldq;
     a.n = (int)c->n;
-    a.S = (int)ceil_div(c->n, (int64_t)kSC);
     a.y = (double*)c->y;
     a.g = (double*)c->g;
     a.st = c->st;
+    const int S16 = (int)ceil_div(c->n, (int64_t)kSC16);
+    if (S16 <= 16) {
+        a.S = S16;
+        const size_t smem = s64_smem_bytes(a.n, a.S);
+        if (cluster16_fits(smem)) return launch_small64_c<kSC16>(a, smem, c->stream);
+    }
+    a.S = (int)ceil_div(c->n, (int64_t)kSC);
     const size_t smem = s64_smem_bytes(a.n, a.S);
-    cudaError_t e = cudaFuncSetAttribute(k_alg2_small64,
+    cudaError_t e = cudaFuncSetAttribute(k_alg2_small64<kSC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(kSC);
-    cfg.blockDim = dim3(kSThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = c->stream;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kSC;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_alg2_small64, a);
+    return launch_small64_c<kSC>(a, smem, c->stream);
 }
 
 }  // namespace aln
