@@ -40,7 +40,7 @@ __device__ __forceinline__ int gwarp_scan_excl(int v, int* total) {
 // Shared scratch of the block-wide reductions and list builders.
 template <typename T>
 struct GRed {
-    double wsum[kGWarps];
+    T wsum[kGWarps];  // warp partials in the iteration type (widened by warp 0)
     int wcnt[kGWarps];
     int wlist[kGWarps];
     int base[kGWarps];
@@ -58,24 +58,26 @@ __device__ __forceinline__ void warp_chunks(int n, int& c0, int& c1) {
 
 // Reduce per-warp (value, count, list count) and give each warp its list
 // base; every thread receives the totals.  The value's warp partials are
-// added in FP64 by warp 0 alone: the step scalars (γ = ‖ḡ‖², κ = ḡᵀQḡ) need
-// more than FP32 — with FP32 scalars the FP32 iteration drifts from the true
-// gradient and needs several times more iterations — while FP64 work by every
-// warp would cost microseconds on this GPU's narrow FP64 pipe.
+// widened and added in FP64 by warp 0 alone: the step scalars (γ = ‖ḡ‖²,
+// κ = ḡᵀQḡ) need more than FP32 — with FP32 scalars the FP32 iteration
+// drifts from the true gradient and needs several times more iterations —
+// while an FP64 instruction costs a warp about 16 cycles of its SM's narrow
+// FP64 unit even with one active lane, so no other warp issues one.  With
+// need_v false (a count only) the FP64 sum is skipped and *vt is 0.
 template <typename T>
 __device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, double* vt,
-                                            int* ct, int* lt) {
+                                            int* ct, int* lt, bool need_v = true) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    v = gwarp_sum(v);
+    if (need_v) v = gwarp_sum(v);
     __syncthreads();  // earlier readers of r are done
     if (lane == 0) {
-        r->wsum[wid] = (double)v;
+        r->wsum[wid] = v;
         r->wcnt[wid] = cnt;
         r->wlist[wid] = lcnt;
     }
     __syncthreads();
     if (wid == 0) {
-        const double x = warp_sum(r->wsum[lane]);
+        const double x = need_v ? warp_sum((double)r->wsum[lane]) : 0.0;
         const int c = gwarp_sum_i(r->wcnt[lane]);
         int total;
         r->base[lane] = gwarp_scan_excl(r->wlist[lane], &total);
@@ -141,7 +143,7 @@ __device__ __forceinline__ int glist(int n, const T* v, int* list, GRed<T>* r) {
     }
     double vt;
     int ct, lt;
-    int base = block_totals(r, T(0), 0, cl, &vt, &ct, &lt);
+    int base = block_totals(r, T(0), 0, cl, &vt, &ct, &lt, false);
     for (int c = c0; c < c1; ++c) {
         const int i = c * 32 + lane;
         const bool nz = i < n && v[i] != T(0);

@@ -377,7 +377,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
             }
             double vt;
             int ct;
-            int base = block_totals(&rs, T(0), 0, cl, &vt, &ct, &nclip);
+            int base = block_totals(&rs, T(0), 0, cl, &vt, &ct, &nclip, false);
             for (int c = c0; c < c1; ++c) {
                 const int i = c * 32 + lane;
                 const bool nz = i < n && sw[i] != T(0);
