@@ -18,6 +18,7 @@
 // rel_c = ‖ḡ64_c‖/‖min(q_c, 0)‖ and ½‖Ax − b‖² = ½yᵀg64 + ½qᵀy + ½‖b‖².
 // Columns above tol restart from y_c with g_c = g64_c (refinement).
 #include "blockops.cuh"
+#include "dfloat.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -394,18 +395,14 @@ __global__ void __launch_bounds__(kBThreads) k_bcheck(
 // iteration; for n this small each column's products are a few thousand
 // FMAs, so a warp runs the loop alone: Q (FP32, n × n) staged in shared
 // memory once per block, y and g in registers (VPL entries per lane),
-// ḡ_j broadcast by shuffles, the sums of γ and κ in FP64 across lanes.  The
+// ḡ_j broadcast by shuffles, the sums of γ and κ as FP32 pairs across lanes
+// (normalised double-float: the SM's FP64 unit is narrow, and many columns'
+// warps share it), α = γ/κ from the pairs.  The
 // iterate is a float pair y = yh + yl (yh in Y, yl in E, which this path
 // does not otherwise use): the FP64 refinement then converges below the
 // FP32 rounding of y, as in the grouped kernel.
 // Same stop rules and per-column state as k_bmask / k_bupdate, so the FP64
 // checks and refinement (k_bcheck) follow unchanged.
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Σ_{k < cnt} v[list[k]] · Q[list[k], i] for the lane's rows i = lane + 32u:
 // the listed rows of the staged Q, four list entries in flight per step.
 template <int VPL>
@@ -489,8 +486,10 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
             g[v] = i < n ? Gc[i] : 0.0f;
         }
         int it = s.iters[c], best_iter = s.best_iter[c];
-        double best = s.best[c];
-        const double eps = s.eps[c];
+        // step scalars as normalised FP32 pairs: the FP64 unit is narrow,
+        // and this kernel keeps many columns' warps on each SM
+        DF best = sc_of_double<DF>(s.best[c]);
+        const DF eps = sc_of_double<DF>(s.eps[c]);
         const int max_iter = s.limits[0], window = s.limits[1];
         unsigned long long rowsP = 0, rowsC = 0, clipIt = 0;
         int status;
@@ -506,15 +505,15 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
                 v2 = fmaf(gb[v], gb[v], v2);
                 cntP += __popc(__ballot_sync(0xffffffffu, P));
             }
-            const double gam = warp_sum_d((double)v2);
+            const DF gam = sc_warp_sum(DF{v2, 0.0f});
             status = -1;
-            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            if (!sc_finite(gam)) status = ALN_RHS_NONFINITE;
             else if (cntP == 0) status = ALN_RHS_EMPTY_PASSIVE;
-            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
+            else if (sc_lt(gam, eps) || sc_zero(gam)) status = ALN_RHS_CONVERGED;
             else if (it >= max_iter) status = ALN_RHS_MAXITER;
             else if (it - best_iter > window) status = ALN_RHS_STAGNATED;
             if (status >= 0) break;
-            if (gam < best) {
+            if (sc_lt(gam, best)) {
                 best = gam;
                 best_iter = it;
             }
@@ -531,16 +530,16 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
             float kp = 0.0f;
 #pragma unroll
             for (int v = 0; v < VPL; ++v) kp = fmaf(gb[v], w[v], kp);
-            const double kap = warp_sum_d((double)kp);
-            if (!isfinite(kap)) {
+            const DF kap = sc_warp_sum(DF{kp, 0.0f});
+            if (!sc_finite(kap)) {
                 status = ALN_RHS_NONFINITE;
                 break;
             }
-            if (kap <= 0.0) {
+            if (sc_nonpos(kap)) {
                 status = ALN_RHS_CURVATURE;
                 break;
             }
-            const float a = (float)(gam / kap);
+            const float a = df_quotient(gam, kap);
             // y⁺ = [y − αḡ]₊, e on the clipped set, g ← g − αw (+ Qe below)
             float e[VPL];
             int nclip = 0;
@@ -590,7 +589,7 @@ __global__ void __launch_bounds__(256) k_bsmall(BatchState s, const float* __res
         if (lane == 0) {
             s.colst[c] = status;
             s.iters[c] = it;
-            s.best[c] = best;
+            s.best[c] = sc_double(best);
             s.best_iter[c] = best_iter;
             atomicAdd(&s.rows[0], rowsP);
             atomicAdd(&s.rows[1], rowsC);
