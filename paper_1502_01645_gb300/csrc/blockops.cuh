@@ -6,6 +6,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace aln {
 
@@ -44,7 +45,7 @@ struct GRed {
     int wcnt[kGWarps];
     int wlist[kGWarps];
     int base[kGWarps];
-    double tsum;
+    double tsum;  // the total, in the caller's scalar type (8 bytes either way)
     int tcnt, tlist;
 };
 
@@ -58,15 +59,16 @@ __device__ __forceinline__ void warp_chunks(int n, int& c0, int& c1) {
 
 // Reduce per-warp (value, count, list count) and give each warp its list
 // base; every thread receives the totals.  The value's warp partials are
-// widened and added in FP64 by warp 0 alone: the step scalars (γ = ‖ḡ‖²,
+// widened and added by warp 0 alone, in the scalar type S (FP64, or
+// normalised FP32 pairs in the FP32 kernels): the step scalars (γ = ‖ḡ‖²,
 // κ = ḡᵀQḡ) need more than FP32 — with FP32 scalars the FP32 iteration
 // drifts from the true gradient and needs several times more iterations —
 // while an FP64 instruction costs a warp about 16 cycles of its SM's narrow
-// FP64 unit even with one active lane, so no other warp issues one.  With
-// need_v false (a count only) the FP64 sum is skipped and *vt is 0.
-template <typename T>
-__device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, double* vt,
-                                            int* ct, int* lt, bool need_v = true) {
+// FP64 unit even with one active lane.  With need_v false (a count only) the
+// wide sum is skipped and *vt is 0.
+template <typename T, typename S = double>
+__device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, S* vt, int* ct,
+                                            int* lt, bool need_v = true) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (need_v) v = gwarp_sum(v);
     __syncthreads();  // earlier readers of r are done
@@ -77,18 +79,24 @@ __device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, 
     }
     __syncthreads();
     if (wid == 0) {
-        const double x = need_v ? warp_sum((double)r->wsum[lane]) : 0.0;
+        S x;
+        sc_set(x, T(0));
+        if (need_v) {
+            S lv;
+            sc_set(lv, r->wsum[lane]);
+            x = sc_warp_sum(lv);
+        }
         const int c = gwarp_sum_i(r->wcnt[lane]);
         int total;
         r->base[lane] = gwarp_scan_excl(r->wlist[lane], &total);
         if (lane == 0) {
-            r->tsum = x;
+            *reinterpret_cast<S*>(&r->tsum) = x;
             r->tcnt = c;
             r->tlist = total;
         }
     }
     __syncthreads();
-    *vt = r->tsum;
+    *vt = *reinterpret_cast<const S*>(&r->tsum);
     *ct = r->tcnt;
     *lt = r->tlist;
     return r->base[wid];
@@ -97,9 +105,9 @@ __device__ __forceinline__ int block_totals(GRed<T>* r, T v, int cnt, int lcnt, 
 // Passive set of Alg. 2 (strict: y_i > 0 or g_i < 0), ḡ = g on P, ‖ḡ‖²,
 // |P|, and the ascending list of i with ḡ_i ≠ 0 (the columns of Q the
 // product needs).
-template <typename T>
+template <typename T, typename S = double>
 __device__ __forceinline__ void gmask(int n, const T* sy, const T* sg, T* sgb, int* list,
-                                      GRed<T>* r, double* gam, int* cntP, int* cntL) {
+                                      GRed<T>* r, S* gam, int* cntP, int* cntL) {
     const int lane = threadIdx.x & 31;
     int c0, c1;
     warp_chunks(n, c0, c1);
@@ -119,7 +127,7 @@ __device__ __forceinline__ void gmask(int n, const T* sy, const T* sg, T* sgb, i
         cp += __popc(__ballot_sync(0xffffffffu, P));
         cl += __popc(__ballot_sync(0xffffffffu, gb != T(0)));
     }
-    int base = block_totals(r, v, cp, cl, gam, cntP, cntL);
+    int base = block_totals<T, S>(r, v, cp, cl, gam, cntP, cntL);
     for (int c = c0; c < c1; ++c) {
         const int i = c * 32 + lane;
         const bool nz = i < n && sgb[i] != T(0);

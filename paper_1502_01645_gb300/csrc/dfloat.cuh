@@ -88,6 +88,11 @@ template <> __device__ __forceinline__ DF sc_ldcg<DF>(const double* p) {
 }
 template <> __device__ __forceinline__ double sc_ldcg<double>(const double* p) { return __ldcg(p); }
 
+// The step quotient in the kernel's scalar type (FP64: the quotient itself).
+__device__ __forceinline__ double sc_quot(double a, double b) { return a / b; }
+__device__ __forceinline__ float df_quotient(DF a, DF b);
+__device__ __forceinline__ float sc_quot(DF a, DF b) { return df_quotient(a, b); }
+
 // a/b in FP32 from pairs: the quotient of the leading parts, corrected once
 // with the residual of the pairs (one Newton step of the division), within
 // an FP32 ulp or so of the rounded quotient.

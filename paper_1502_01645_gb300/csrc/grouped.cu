@@ -291,27 +291,31 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
         __syncthreads();
     }
 
-    const double eps = sf * sf;
+    // step scalars: normalised FP32 pairs in the FP32 kernel (the SM's FP64
+    // unit is narrow and up to two 1024-thread blocks share it), FP64 in the
+    // FP64 kernel
+    using SC = Sc<T>;
+    const SC eps = sc_of_double<SC>(sf * sf);
     const int max_iter = a.max_iter, window = a.window;
     const int iter0 = st.iters;
     int iter = st.iters, best_iter = st.iters, status = ALN_RHS_MAXITER;
-    double best = 1.0 / 0.0;
+    SC best = sc_inf<SC>();
     int64_t sum_passive = 0, sum_clip = 0;
     int clip_iters = 0;
-    double gam;
+    SC gam;
     int cntP, cntL;
-    gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+    gmask<T, SC>(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
     for (;;) {
         if (threadIdx.x == 0) {
             int stop = 1;
-            if (!isfinite(gam)) status = ALN_RHS_NONFINITE;
+            if (!sc_finite(gam)) status = ALN_RHS_NONFINITE;
             else if (cntP == 0) status = ALN_RHS_EMPTY_PASSIVE;
-            else if (gam < eps || gam == 0.0) status = ALN_RHS_CONVERGED;
+            else if (sc_lt(gam, eps) || sc_zero(gam)) status = ALN_RHS_CONVERGED;
             else if (iter >= max_iter) status = ALN_RHS_MAXITER;
             else if (iter - best_iter > window) status = ALN_RHS_STAGNATED;
             else if (a.budget > 0 && iter - iter0 >= a.budget) status = kRhsPaused;
             else stop = 0;
-            if (!stop && gam < best) {
+            if (!stop && sc_lt(gam, best)) {
                 best = gam;
                 best_iter = iter;
             }
@@ -323,19 +327,19 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
         product<T, CL>(Qp, ldq, n, lp, cntL, sgb, sw, false, red, xb(), rank, S);
         T kp = T(0);
         for (int i = threadIdx.x; i < n; i += blockDim.x) kp = fma(sgb[i], sw[i], kp);
-        double kap;
+        SC kap;
         int unused_c, unused_l;
-        (void)block_totals(&rs, kp, 0, 0, &kap, &unused_c, &unused_l);
+        (void)block_totals<T, SC>(&rs, kp, 0, 0, &kap, &unused_c, &unused_l);
         if (threadIdx.x == 0) {
             int stop = 0;
-            if (!isfinite(kap)) {
+            if (!sc_finite(kap)) {
                 status = ALN_RHS_NONFINITE;
                 stop = 1;
-            } else if (kap <= 0.0) {
+            } else if (sc_nonpos(kap)) {
                 status = ALN_RHS_CURVATURE;
                 stop = 1;
             }
-            s_alpha = stop ? T(0) : (T)(gam / kap);
+            s_alpha = stop ? T(0) : (T)sc_quot(gam, kap);
             s_flag = stop;
         }
         __syncthreads();
@@ -396,7 +400,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
                 product<T, CL>(Qp, ldq, n, lc, nclip, sw, sg, true, red, xb(), rank, S);
             ++clip_iters;
         }
-        gmask(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
+        gmask<T, SC>(n, sy, sg, sgb, lp, &rs, &gam, &cntP, &cntL);
     }
     if (!CL || rank == 0)
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -410,7 +414,7 @@ __device__ void solve_one(const GSolveArgs<T>& a, int p, uint8_t* sm, int rank, 
         st.npassive = cntP;
         st.sum_passive += sum_passive;
         st.sum_clip += sum_clip;
-        st.gbar2 = gam;
+        st.gbar2 = sc_double(gam);
         a.stat[p] = st;
     }
     __syncthreads();
